@@ -1,0 +1,222 @@
+/* rift_ile.h -- C ABI of the extrinsic-marginalised likelihood (ILE) stage of
+ * RIFT ("Scaling RIFT 1", arXiv 2609.37393), for one NVIDIA B300 (sm_103a).
+ *
+ * What the library computes (Sec. II.A-II.C of the paper):
+ *
+ *   lnL(theta) = x Re sum_k sum_lm (F_k Y_lm)^* Q_{k,lm}(t_k)
+ *              - x^2/4 sum_k sum_{lm,l'm'} [ |F_k|^2 Y_lm^* Y_l'm' U_{k,lm,l'm'}
+ *                                            + Re(F_k^2 Y_lm Y_l'm' V_{k,lm,l'm'}) ]
+ *                                                        (eq. def:lnL:Decomposed)
+ *   with theta = (ra, dec, psi, incl, phase, lnD, t_c), x = D_ref/D = D_ref e^{-lnD},
+ *   F_k = F_+ - i F_x the antenna factor of detector k, t_k = t_c - x_k . s its
+ *   arrival time, Y_lm = -2Y_lm(incl, phase), and Q_{k,lm}(t) read from a fine
+ *   uniform table by the four-point cubic C_3 (eq. q-time-pregrid);
+ *
+ *   lnZ = ln[(1/N) sum_i exp(lnL_i + ln w_i)], w_i = p(theta_i)/p_s(theta_i)
+ *                                         (eq. lnL:MonteCarlo), with its
+ *   delta-method standard error and n_eff = sum w / max w (eq. neff);
+ *
+ *   the gradient of lnL with respect to the seven extrinsic parameters
+ *   (Sec. II.B), and the distance-marginalised lnL on a log-uniform lnD node
+ *   table (eq. ap:dexp, eq. ap:dlog).
+ *
+ * Conventions.  Times are seconds relative to a reference time chosen by the
+ * caller; angles are radians; positions are light-seconds in an Earth-fixed
+ * frame; the source direction s points from the geocentre to the source;
+ * the polarisation basis is e1 = (-sin lam, cos lam, 0), e2 = (-sin dec cos lam,
+ * -sin dec sin lam, cos dec) with lam = ra - gmst, p = cos psi e1 + sin psi e2,
+ * q = -sin psi e1 + cos psi e2, F_+ = p.D.p - q.D.q, F_x = 2 p.D.q; the Q cubic
+ * is the Lagrange cubic on taps j-1..j+2, j = floor((t - t0_k)/dt), and taps
+ * outside the table read as zero (they are counted, see rift_ile_last_oob).
+ *
+ * Ownership.  The caller owns every buffer it passes.  rift_ile_point_create
+ * copies what it needs (device-to-device for Q) into a point object that the
+ * library owns until rift_ile_point_destroy.  Calls are asynchronous on the
+ * caller's stream unless stated; the host-scalar forms of lnZ synchronise.
+ *
+ * Errors.  Every entry point returns 0 on success or a negative RIFT_ILE_ERR_*
+ * code; rift_ile_last_error() gives a thread-local message.  Non-finite draws
+ * give a NaN lnL for that draw, not an error.
+ */
+#ifndef RIFT_ILE_H
+#define RIFT_ILE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RIFT_ILE_OK = 0,
+  RIFT_ILE_ERR_INVALID_ARG = -1, /* null pointer, bad enum, non-finite scalar */
+  RIFT_ILE_ERR_SHAPE = -2,       /* inconsistent sizes */
+  RIFT_ILE_ERR_UNSUPPORTED = -3, /* K, M or l outside the compiled limits */
+  RIFT_ILE_ERR_CUDA = -4,        /* a CUDA call failed; message carries its text */
+  RIFT_ILE_ERR_TIMEOUT = -5,     /* a bounded device wait expired */
+  RIFT_ILE_ERR_ALLOC = -6        /* device or host allocation failed */
+};
+
+#define RIFT_ILE_MAX_DET 8    /* K */
+#define RIFT_ILE_MAX_MODES 16 /* M */
+#define RIFT_ILE_MAX_ELL 8    /* l of every mode */
+#define RIFT_ILE_NPAR 7       /* ra, dec, psi, incl, phase, lnD, t */
+
+typedef enum {
+  RIFT_ILE_FP64 = 0,      /* every step in IEEE double */
+  RIFT_ILE_FP32_MIXED = 1 /* FP32 template, double-float contractions */
+} rift_ile_precision;
+
+typedef enum { RIFT_ILE_F32 = 0, RIFT_ILE_F64 = 1 } rift_ile_dtype;
+typedef enum { RIFT_ILE_C64 = 0, RIFT_ILE_C128 = 1 } rift_ile_cdtype;
+
+/* One intrinsic point: the precomputed products of eq. QUV and the network.
+ *   Q      DEVICE [K][q_len][M] complex (re, im interleaved), float (C64) or
+ *          double (C128): Q_{k,lm}(q_t0[k] + j q_dt), j = 0..q_len-1 (eq. QUV,
+ *          sampled on the fine table of eq. q-time-pregrid)
+ *   U, V   HOST [K][M][M][2] double: U_{k,i,j} = <h_i|h_j>_k (Hermitian),
+ *          V_{k,i,j} = <h_i^*|h_j>_k (complex symmetric)  (eq. QUV)
+ *   ell,em HOST [M] mode indices, 2 <= l <= RIFT_ILE_MAX_ELL, |m| <= l
+ *   det_pos  HOST [K][3] detector positions, light-seconds
+ *   det_resp HOST [K][6] response tensors D_k: xx, xy, xz, yy, yz, zz
+ *   q_t0   HOST [K] time of table sample 0, seconds
+ *   gmst   Greenwich sidereal angle at the reference time, rad
+ *   d_ref  the reference distance of the modes (same unit as e^{lnD}) */
+typedef struct {
+  int32_t n_det;
+  int32_t n_modes;
+  const int32_t* ell;
+  const int32_t* em;
+  const void* Q;
+  int32_t q_dtype;
+  int32_t q_len;
+  const double* q_t0;
+  double q_dt;
+  const double* U;
+  const double* V;
+  const double* det_pos;
+  const double* det_resp;
+  double gmst;
+  double d_ref;
+} rift_ile_point_desc;
+
+typedef struct rift_ile_point rift_ile_point; /* opaque, library-owned */
+
+/* Extrinsic draws: DEVICE structure-of-arrays, each [n] of `dtype`; logw
+ * (ln p - ln p_s per draw) may be NULL (all zero). */
+typedef struct {
+  const void* ra;
+  const void* dec;
+  const void* psi;
+  const void* incl;
+  const void* phase;
+  const void* lnD;
+  const void* t;
+  const void* logw;
+  int64_t n;
+  int32_t dtype;
+} rift_ile_draws;
+
+/* Prepares a point for evaluation: validates the description, copies Q,
+ * builds the constant tables of both precisions (for FP32_MIXED: the
+ * eigen-decomposition of each detector's real quadratic form and the
+ * whitened, double-float Q table; see the design notes).  Runs on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and synchronises it.
+ * Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA, ALLOC. */
+int rift_ile_point_create(const rift_ile_point_desc* desc, rift_ile_point** out, void* stream);
+int rift_ile_point_destroy(rift_ile_point* pt);
+
+/* Shape of a prepared point (HOST out[6]): K, M, table length, the whitened
+ * dimension R (the rank of the quadratic form of eq. def:lnL:Decomposed in
+ * real coordinates; M for aligned-spin mode pairs), the number of detector
+ * classes (detectors with identical U and V) and whether any class kept its
+ * near-null directions.  Errors: INVALID_ARG. */
+int rift_ile_point_info(const rift_ile_point* pt, int32_t out[6]);
+
+/* lnL per draw (eq. def:lnL:Decomposed) into DEVICE lnL_out[n] (double), on
+ * `stream`, asynchronous.  Errors: INVALID_ARG, SHAPE, CUDA. */
+int rift_ile_lnL(const rift_ile_point* pt, const rift_ile_draws* draws, rift_ile_precision prec,
+                 double* lnL_out, void* stream);
+
+/* lnL (DEVICE [n], may be NULL) and d lnL / d theta into DEVICE grad_out
+ * [7][n] (double; parameter-major: ra, dec, psi, incl, phase, lnD, t), on
+ * `stream`, asynchronous.  Sec. II.B. */
+int rift_ile_lnL_grad(const rift_ile_point* pt, const rift_ile_draws* draws,
+                      rift_ile_precision prec, double* lnL_out, double* grad_out, void* stream);
+
+/* Log-sum-exp state of a set of draws: m = max_i (lnL_i + ln w_i),
+ * s = sum_i exp(lnL_i + ln w_i - m), s2 = sum_i exp(2 (lnL_i + ln w_i - m)),
+ * n = number of draws.  States of disjoint draw sets merge exactly (see
+ * rift_ile_lnZ_merge); lnZ = m + ln s - ln n, sigma_lnZ = sqrt(max(0,
+ * s2/s^2 - 1/n)), n_eff = s (eq. lnL:MonteCarlo, eq. neff). */
+typedef struct {
+  double m, s, s2, n;
+} rift_ile_lse;
+
+/* Optional distance marginalisation: HOST node table (x_j = D_ref/D_j,
+ * ln w_j) of eq. ap:dlog, built by rift_ile_dist_nodes.  When passed to the
+ * lnZ calls, each draw's lnL is replaced by ln sum_j exp(K x_j - R x_j^2/2 +
+ * ln w_j) with K, R the data and quadratic terms at x = 1 (eq. ap:dexp), and
+ * the draw's own lnD is ignored. */
+typedef struct {
+  const double* x;
+  const double* lnw;
+  int32_t n;
+} rift_ile_dist;
+
+/* Node table of eq. ap:dlog: spacing in ln D of at most c(tol)/rho_max,
+ * c(tol) = pi sqrt(2/ln(2/tol)), over [d_min, d_max], trapezoid weights in
+ * ln D, prior p(D) = 3 D^2/(d_max^3 - d_min^3).  Writes up to max_nodes nodes
+ * into HOST x[], lnw[]; *n_out receives the count.  Errors: INVALID_ARG,
+ * SHAPE (table larger than max_nodes). */
+int rift_ile_dist_nodes(double d_min, double d_max, double d_ref, double tol, double rho_max,
+                        int32_t max_nodes, double* x, double* lnw, int32_t* n_out);
+
+/* Monte Carlo lnZ of the draws (eq. lnL:MonteCarlo), fused with the lnL
+ * evaluation (per-draw lnL is not stored).  out[3] (HOST) = lnZ, sigma_lnZ,
+ * n_eff.  dist may be NULL.  Synchronises `stream`. */
+int rift_ile_lnZ(const rift_ile_point* pt, const rift_ile_draws* draws, rift_ile_precision prec,
+                 const rift_ile_dist* dist, double out[3], void* stream);
+
+/* Same, returning the LSE state (HOST) instead, for chunked streaming and for
+ * merging the partial results of several devices or processes. */
+int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws* draws,
+                       rift_ile_precision prec, const rift_ile_dist* dist, rift_ile_lse* state,
+                       void* stream);
+
+/* Exact merge of S LSE states (HOST) into out[3] = lnZ, sigma_lnZ, n_eff;
+ * merged_state (may be NULL) receives the merged state.  Host only. */
+int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
+                       rift_ile_lse* merged_state);
+
+/* lnZ of P points in one persistent launch: point p uses pts[p] and
+ * draws[p] (each point its own Q, U, V, network and draw count).  out is a
+ * DEVICE [P][3] double array (lnZ, sigma_lnZ, n_eff per point); nothing is
+ * synchronised, so the call can be captured in a CUDA graph once the
+ * batch's work queue exists (the first call with a given (pts, draws, P)
+ * builds and caches it).  Errors: INVALID_ARG, SHAPE, CUDA, ALLOC. */
+int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* draws, int32_t P,
+                       rift_ile_precision prec, double* out, void* stream);
+
+/* Number of Q taps that fell outside their tables in the last completed
+ * lnZ call of this thread (host read; the draws get zero Q there). */
+int64_t rift_ile_last_oob(void);
+
+/* Frees the library's per-device workspace (LSE partials, batch queues). */
+int rift_ile_release(void);
+
+const char* rift_ile_last_error(void);
+
+/* ALU issue-rate probes used as roofline denominators (measurement support;
+ * the paper has no counterpart).  ops_per_second counts one FMA as one op. */
+enum {
+  RIFT_ILE_PROBE_FP32_FMA = 0,
+  RIFT_ILE_PROBE_FP64_FMA = 1,
+  RIFT_ILE_PROBE_MUFU_EX2 = 2,
+  RIFT_ILE_PROBE_MUFU_SIN = 3
+};
+int rift_ile_probe_alu(int which, double target_seconds, double* ops_per_second, double* sm_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

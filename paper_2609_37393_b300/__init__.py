@@ -1,0 +1,334 @@
+"""Extrinsic-marginalised likelihood (ILE) of RIFT on one NVIDIA B300.
+
+Thin binding of the C ABI in include/rift_ile.h: every function here only
+marshals arguments (PyTorch CUDA tensors or numpy arrays) into the shared
+library _rift_ile.so and returns its results.  All computation runs in the
+library's CUDA kernels; there is no CPU fallback, and importing this package
+fails if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_rift_ile.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python paper_2609_37393_b300/build.py` "
+        "(there is no CPU implementation of this package)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FP64 = 0
+FP32_MIXED = 1
+PARAMS = ("ra", "dec", "psi", "incl", "phase", "lnD", "t")
+MAX_DET, MAX_MODES, MAX_ELL = 8, 16, 8
+
+ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "UNSUPPORTED", -4: "CUDA", -5: "TIMEOUT",
+          -6: "ALLOC"}
+
+
+class RiftError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _PointDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_det", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+        ("ell", ctypes.c_void_p), ("em", ctypes.c_void_p),
+        ("Q", ctypes.c_void_p), ("q_dtype", ctypes.c_int32), ("q_len", ctypes.c_int32),
+        ("q_t0", ctypes.c_void_p), ("q_dt", ctypes.c_double),
+        ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
+        ("det_pos", ctypes.c_void_p), ("det_resp", ctypes.c_void_p),
+        ("gmst", ctypes.c_double), ("d_ref", ctypes.c_double),
+    ]
+
+
+class _Draws(ctypes.Structure):
+    _fields_ = [(p, ctypes.c_void_p) for p in PARAMS] + [
+        ("logw", ctypes.c_void_p), ("n", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+
+
+class _Lse(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_double), ("s", ctypes.c_double), ("s2", ctypes.c_double),
+                ("n", ctypes.c_double)]
+
+
+class _Dist(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("lnw", ctypes.c_void_p), ("n", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_lib.rift_ile_last_error.restype = ctypes.c_char_p
+_lib.rift_ile_point_create.argtypes = [_P, _P, _P]
+_lib.rift_ile_point_destroy.argtypes = [_P]
+_lib.rift_ile_point_info.argtypes = [_P, _P]
+_lib.rift_ile_lnL.argtypes = [_P, _P, ctypes.c_int, _P, _P]
+_lib.rift_ile_lnL_grad.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
+_lib.rift_ile_lnZ.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
+_lib.rift_ile_lnZ_state.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
+_lib.rift_ile_lnZ_merge.argtypes = [_P, ctypes.c_int32, _P, _P]
+_lib.rift_ile_lnZ_batch.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P, _P]
+_lib.rift_ile_dist_nodes.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int32, _P, _P, _P]
+_lib.rift_ile_last_oob.restype = ctypes.c_int64
+_lib.rift_ile_probe_alu.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise RiftError(rc, _lib.rift_ile_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_tensor(x, dtype, device):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device, dtype=dtype)
+    else:
+        t = torch.as_tensor(np.asarray(x), device=device, dtype=dtype)
+    return t.contiguous()
+
+
+class Point:
+    """An intrinsic point prepared for evaluation (rift_ile_point_create).
+
+    point: dict with K, M, ell[M], em[M], Q[K, n, M] (complex64 or complex128,
+    numpy or CUDA tensor), q_t0[K], q_dt, U[K, M, M], V[K, M, M] (complex),
+    det_pos[K, 3] (light-seconds), det_resp[K, 6], gmst, d_ref.
+    """
+
+    def __init__(self, point: dict, device=None, stream=None):
+        torch = _torch()
+        device = torch.device(device or "cuda")
+        Q = point["Q"]
+        if isinstance(Q, torch.Tensor):
+            qdt = Q.dtype
+        else:
+            qdt = {np.dtype(np.complex64): torch.complex64,
+                   np.dtype(np.complex128): torch.complex128}[np.asarray(Q).dtype]
+        self._Q = _dev_tensor(Q, qdt, device)
+        K, n, M = self._Q.shape
+        self._host = {
+            "ell": np.ascontiguousarray(point["ell"], dtype=np.int32),
+            "em": np.ascontiguousarray(point["em"], dtype=np.int32),
+            "t0": np.ascontiguousarray(point["q_t0"], dtype=np.float64),
+            "U": np.ascontiguousarray(np.asarray(point["U"], dtype=np.complex128)).view(np.float64),
+            "V": np.ascontiguousarray(np.asarray(point["V"], dtype=np.complex128)).view(np.float64),
+            "pos": np.ascontiguousarray(point["det_pos"], dtype=np.float64),
+            "resp": np.ascontiguousarray(point["det_resp"], dtype=np.float64),
+        }
+        d = _PointDesc()
+        d.n_det, d.n_modes = K, M
+        d.ell, d.em = self._host["ell"].ctypes.data, self._host["em"].ctypes.data
+        d.Q = self._Q.data_ptr()
+        d.q_dtype = 1 if qdt == torch.complex128 else 0
+        d.q_len = n
+        d.q_t0 = self._host["t0"].ctypes.data
+        d.q_dt = float(point["q_dt"])
+        d.U, d.V = self._host["U"].ctypes.data, self._host["V"].ctypes.data
+        d.det_pos, d.det_resp = self._host["pos"].ctypes.data, self._host["resp"].ctypes.data
+        d.gmst, d.d_ref = float(point["gmst"]), float(point["d_ref"])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            _check(_lib.rift_ile_point_create(ctypes.byref(d), ctypes.byref(h), _stream(stream)))
+        self._h = h
+        self.K, self.M, self.n = K, M, n
+        self.device = device
+        del self._Q  # the library holds its own copy
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        """K, M, n, whitened dimension R, detector classes, kept null directions."""
+        out = (ctypes.c_int32 * 6)()
+        _check(_lib.rift_ile_point_info(self._h, out))
+        return dict(zip(("K", "M", "n", "R", "ncls", "has_null"), list(out)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.rift_ile_point_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Draws:
+    """Device-resident extrinsic draws (rift_ile_draws): seven arrays of equal
+    length in float32 or float64, plus optional ln p - ln p_s."""
+
+    def __init__(self, draws: dict, logw=None, dtype=None, device=None):
+        torch = _torch()
+        device = torch.device(device or "cuda")
+        first = draws[PARAMS[0]]
+        if dtype is None:
+            if isinstance(first, torch.Tensor):
+                dtype = first.dtype
+            else:
+                dtype = torch.float64 if np.asarray(first).dtype == np.float64 else torch.float32
+        self.t = {p: _dev_tensor(draws[p], dtype, device) for p in PARAMS}
+        self.logw = None if logw is None else _dev_tensor(logw, dtype, device)
+        n = self.t[PARAMS[0]].numel()
+        for p in PARAMS:
+            if self.t[p].numel() != n:
+                raise ValueError(f"draw array {p} has {self.t[p].numel()} entries, expected {n}")
+        if self.logw is not None and self.logw.numel() != n:
+            raise ValueError("logw length differs from the draws")
+        self.n = n
+        self.dtype = dtype
+        s = _Draws()
+        for p in PARAMS:
+            setattr(s, p, self.t[p].data_ptr() if n else None)
+        s.logw = self.logw.data_ptr() if (self.logw is not None and n) else None
+        s.n = n
+        s.dtype = 1 if dtype == torch.float64 else 0
+        self.struct = s
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def _as_draws(draws, logw=None):
+    return draws if isinstance(draws, Draws) else Draws(draws, logw)
+
+
+def rift_ile_lnL(point: Point, draws, precision: int = FP32_MIXED, out=None, stream=None):
+    """lnL per draw (float64 CUDA tensor), eq. def:lnL:Decomposed."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(d.n, dtype=torch.float64, device=point.device)
+    _check(_lib.rift_ile_lnL(point.handle, d.ref, precision, out.data_ptr() if d.n else None,
+                             _stream(stream)))
+    return out
+
+
+def rift_ile_lnL_grad(point: Point, draws, precision: int = FP32_MIXED, lnl_out=None,
+                      grad_out=None, stream=None):
+    """(lnL[n], grad[7, n]) as float64 CUDA tensors (Sec. II.B)."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if lnl_out is None:
+        lnl_out = torch.empty(d.n, dtype=torch.float64, device=point.device)
+    if grad_out is None:
+        grad_out = torch.empty((7, d.n), dtype=torch.float64, device=point.device)
+    _check(_lib.rift_ile_lnL_grad(point.handle, d.ref, precision,
+                                  lnl_out.data_ptr() if d.n else None,
+                                  grad_out.data_ptr() if d.n else None, _stream(stream)))
+    return lnl_out, grad_out
+
+
+def _dist_struct(dist):
+    if dist is None:
+        return None, None
+    x = np.ascontiguousarray(dist[0], dtype=np.float64)
+    w = np.ascontiguousarray(dist[1], dtype=np.float64)
+    s = _Dist()
+    s.x, s.lnw, s.n = x.ctypes.data, w.ctypes.data, x.shape[0]
+    return s, (x, w)
+
+
+def rift_ile_lnZ_state(point: Point, draws, precision: int = FP32_MIXED, dist=None, stream=None):
+    """LSE state (m, s, s2, n) of the draws; dist = (x_nodes, lnw_nodes) or None."""
+    d = _as_draws(draws)
+    st = _Lse()
+    ds, keep = _dist_struct(dist)
+    _check(_lib.rift_ile_lnZ_state(point.handle, d.ref, precision,
+                                   ctypes.byref(ds) if ds is not None else None,
+                                   ctypes.byref(st), _stream(stream)))
+    del keep
+    return (st.m, st.s, st.s2, st.n)
+
+
+def rift_ile_lnZ(point: Point, draws, precision: int = FP32_MIXED, dist=None, stream=None):
+    """(lnZ, sigma_lnZ, n_eff) of eq. lnL:MonteCarlo / eq. neff."""
+    d = _as_draws(draws)
+    out = (ctypes.c_double * 3)()
+    ds, keep = _dist_struct(dist)
+    _check(_lib.rift_ile_lnZ(point.handle, d.ref, precision,
+                             ctypes.byref(ds) if ds is not None else None, out, _stream(stream)))
+    del keep
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def rift_ile_lnZ_merge(states):
+    """Merge LSE states [(m, s, s2, n), ...] -> ((lnZ, sigma, n_eff), merged state)."""
+    arr = (_Lse * max(1, len(states)))()
+    for i, s in enumerate(states):
+        arr[i] = _Lse(*s)
+    out = (ctypes.c_double * 3)()
+    merged = _Lse()
+    _check(_lib.rift_ile_lnZ_merge(arr, len(states), out, ctypes.byref(merged)))
+    return (float(out[0]), float(out[1]), float(out[2])), (merged.m, merged.s, merged.s2, merged.n)
+
+
+def rift_ile_lnZ_batch(points, draws_list, precision: int = FP32_MIXED, out=None, stream=None):
+    """lnZ, sigma, n_eff of many points in one persistent launch ([P, 3] CUDA tensor)."""
+    torch = _torch()
+    P = len(points)
+    ds = [_as_draws(d) for d in draws_list]
+    handles = (ctypes.c_void_p * P)(*[p.handle.value for p in points])
+    structs = (_Draws * P)(*[d.struct for d in ds])
+    if out is None:
+        out = torch.empty((P, 3), dtype=torch.float64, device=points[0].device)
+    _check(_lib.rift_ile_lnZ_batch(handles, structs, P, precision, out.data_ptr(),
+                                   _stream(stream)))
+    out._keep_draws = ds  # the launch reads the draws asynchronously
+    return out
+
+
+def rift_ile_dist_nodes(d_min, d_max, d_ref, tol, rho_max, max_nodes=1 << 16):
+    """Log-uniform lnD node table of eq. ap:dlog: (x_j, ln w_j)."""
+    x = np.empty(max_nodes)
+    w = np.empty(max_nodes)
+    n = ctypes.c_int32()
+    _check(_lib.rift_ile_dist_nodes(d_min, d_max, d_ref, tol, rho_max, max_nodes,
+                                    x.ctypes.data, w.ctypes.data, ctypes.byref(n)))
+    return x[:n.value].copy(), w[:n.value].copy()
+
+
+def rift_ile_last_oob() -> int:
+    return int(_lib.rift_ile_last_oob())
+
+
+def rift_ile_probe_alu(which: int, target_seconds: float = 0.2):
+    """(ops per second, SM MHz seen by the probe) of FP32 FMA (0), FP64 FMA (1),
+    MUFU ex2 (2) or MUFU sin (3)."""
+    ops = ctypes.c_double()
+    mhz = ctypes.c_double()
+    _check(_lib.rift_ile_probe_alu(which, target_seconds, ctypes.byref(ops), ctypes.byref(mhz)))
+    return ops.value, mhz.value
+
+
+def rift_ile_release():
+    _check(_lib.rift_ile_release())
+
+
+def lnZ_from_state(state):
+    m, s, s2, n = state
+    if n <= 0:
+        return -math.inf, math.nan, 0.0
+    return (m + math.log(s) - math.log(n), math.sqrt(max(0.0, s2 / (s * s) - 1.0 / n)), s)

@@ -1,0 +1,313 @@
+// C-ABI entry points: argument checks, the per-device workspace, launches,
+// and the deterministic combination of per-block log-sum-exp states.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "rift_ile_internal.h"
+
+namespace rift {
+namespace {
+
+thread_local long long t_last_oob = 0;
+
+// Library-owned scratch per device: per-block LSE partials, the combined
+// state and the out-of-table tap counter.  Allocated on first use.
+struct Workspace {
+  LseState* partials = nullptr;
+  int capacity = 0;
+  LseState* state = nullptr;
+  unsigned long long* oob = nullptr;
+  int sms = 0;
+};
+
+std::mutex g_ws_mu;
+Workspace g_ws[64];
+
+int get_workspace(Workspace** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    rift_ile_set_error("no current CUDA device");
+    return RIFT_ILE_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  Workspace& w = g_ws[dev];
+  if (!w.partials) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      rift_ile_set_error("cannot query the SM count");
+      return RIFT_ILE_ERR_CUDA;
+    }
+    const int cap = sms * kMaxPartialsPerSM;
+    if (cudaMalloc((void**)&w.partials, cap * sizeof(LseState)) != cudaSuccess ||
+        cudaMalloc((void**)&w.state, sizeof(LseState)) != cudaSuccess ||
+        cudaMalloc((void**)&w.oob, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaFree(w.partials);
+      cudaFree(w.state);
+      w = Workspace();
+      rift_ile_set_error("workspace allocation failed");
+      return RIFT_ILE_ERR_ALLOC;
+    }
+    w.capacity = cap;
+    w.sms = sms;
+  }
+  *out = &w;
+  return RIFT_ILE_OK;
+}
+
+// Merges the per-block states in a fixed order (one block of 256 threads:
+// thread t folds partials t, t+256, ...; thread 0 folds the 256 results).
+__global__ void lse_combine_kernel(const LseState* __restrict__ partials, int nparts,
+                                   double n_total, LseState* __restrict__ out) {
+  __shared__ LseState part[256];
+  LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
+  int nan_any = 0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    LseState p = partials[i];
+    if (isnan(p.m)) nan_any = 1;
+    else acc = lse_merge(acc, p);
+  }
+  if (nan_any) acc.m = CUDART_NAN;
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    LseState tot{-CUDART_INF, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      if (isnan(part[t].m)) bad = true;
+      else tot = lse_merge(tot, part[t]);
+    }
+    tot.n = n_total;
+    if (bad) tot.m = tot.s = tot.s2 = CUDART_NAN;
+    *out = tot;
+  }
+}
+
+int check_draws(const rift_ile_draws* d) {
+  if (!d) {
+    rift_ile_set_error("draws is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (d->n < 0) {
+    rift_ile_set_error("draws->n = %lld is negative", (long long)d->n);
+    return RIFT_ILE_ERR_SHAPE;
+  }
+  if (d->dtype != RIFT_ILE_F32 && d->dtype != RIFT_ILE_F64) {
+    rift_ile_set_error("draws->dtype = %d is neither RIFT_ILE_F32 nor RIFT_ILE_F64", d->dtype);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (d->n > 0 && (!d->ra || !d->dec || !d->psi || !d->incl || !d->phase || !d->lnD || !d->t)) {
+    rift_ile_set_error("a draw parameter array is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  return RIFT_ILE_OK;
+}
+
+DrawsParams to_params(const rift_ile_draws* d) {
+  DrawsParams p;
+  p.p[0] = d->ra;
+  p.p[1] = d->dec;
+  p.p[2] = d->psi;
+  p.p[3] = d->incl;
+  p.p[4] = d->phase;
+  p.p[5] = d->lnD;
+  p.p[6] = d->t;
+  p.logw = d->logw;
+  p.n = d->n;
+  p.f64 = (d->dtype == RIFT_ILE_F64);
+  return p;
+}
+
+int check_point(const rift_ile_point* pt, rift_ile_precision prec) {
+  if (!pt) {
+    rift_ile_set_error("point is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (prec != RIFT_ILE_FP64 && prec != RIFT_ILE_FP32_MIXED) {
+    rift_ile_set_error("precision %d is neither RIFT_ILE_FP64 nor RIFT_ILE_FP32_MIXED", (int)prec);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  return RIFT_ILE_OK;
+}
+
+cudaError_t launch_lnl(const rift_ile_point* pt, const DrawsParams& dp, rift_ile_precision prec,
+                       double* lnl_out, LseState* partials, unsigned long long* oob, int* blocks,
+                       cudaStream_t st) {
+  if (prec == RIFT_ILE_FP64)
+    return launch_lnl_fp64(pt->host, pt->dev, dp, lnl_out, partials, oob, blocks, st);
+  return launch_lnl_mixed(pt->host, pt->dev, dp, lnl_out, partials, oob, blocks, st);
+}
+
+}  // namespace
+
+int device_sms() {
+  Workspace* ws = nullptr;
+  if (get_workspace(&ws)) return 1;
+  return ws->sms;
+}
+
+cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
+                               LseState* state_out, cudaStream_t st) {
+  lse_combine_kernel<<<1, 256, 0, st>>>(partials, nparts, n_total, state_out);
+  return cudaGetLastError();
+}
+
+}  // namespace rift
+
+using namespace rift;
+
+extern "C" int rift_ile_lnL(const rift_ile_point* pt, const rift_ile_draws* draws,
+                            rift_ile_precision prec, double* lnL_out, void* stream) {
+  int rc = check_point(pt, prec);
+  if (!rc) rc = check_draws(draws);
+  if (rc) return rc;
+  if (draws->n == 0) return RIFT_ILE_OK;
+  if (!lnL_out) {
+    rift_ile_set_error("rift_ile_lnL: lnL_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  int blocks = 0;
+  return check_cuda(launch_lnl(pt, to_params(draws), prec, lnL_out, nullptr, nullptr, &blocks,
+                               (cudaStream_t)stream),
+                    "rift_ile_lnL launch");
+}
+
+extern "C" int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws* draws,
+                                  rift_ile_precision prec, const rift_ile_dist* dist,
+                                  rift_ile_lse* state, void* stream) {
+  int rc = check_point(pt, prec);
+  if (!rc) rc = check_draws(draws);
+  if (rc) return rc;
+  if (!state) {
+    rift_ile_set_error("rift_ile_lnZ_state: state is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (dist) {
+    rift_ile_set_error("distance marginalisation is not available in this build");
+    return RIFT_ILE_ERR_UNSUPPORTED;
+  }
+  if (draws->n == 0) {
+    *state = rift_ile_lse{-INFINITY, 0.0, 0.0, 0.0};
+    t_last_oob = 0;
+    return RIFT_ILE_OK;
+  }
+  Workspace* ws = nullptr;
+  if ((rc = get_workspace(&ws))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int blocks = 0;
+  if ((rc = check_cuda(cudaMemsetAsync(ws->oob, 0, sizeof(unsigned long long), st), "memset")))
+    return rc;
+  if ((rc = check_cuda(launch_lnl(pt, to_params(draws), prec, nullptr, ws->partials, ws->oob,
+                                  &blocks, st),
+                       "lnZ kernel launch")))
+    return rc;
+  if ((rc = check_cuda(launch_lse_combine(ws->partials, blocks, (double)draws->n, ws->state, st),
+                       "lnZ combine launch")))
+    return rc;
+  LseState h;
+  unsigned long long oob = 0;
+  if ((rc = check_cuda(cudaMemcpyAsync(&h, ws->state, sizeof(h), cudaMemcpyDeviceToHost, st),
+                       "lnZ copy")))
+    return rc;
+  if ((rc = check_cuda(cudaMemcpyAsync(&oob, ws->oob, sizeof(oob), cudaMemcpyDeviceToHost, st),
+                       "lnZ copy")))
+    return rc;
+  if ((rc = check_cuda(cudaStreamSynchronize(st), "rift_ile_lnZ"))) return rc;
+  t_last_oob = (long long)oob;
+  *state = rift_ile_lse{h.m, h.s, h.s2, h.n};
+  return RIFT_ILE_OK;
+}
+
+extern "C" int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
+                                  rift_ile_lse* merged) {
+  if ((!states && S > 0) || S < 0) {
+    rift_ile_set_error("rift_ile_lnZ_merge: bad states/S");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  double m = -INFINITY, n = 0.0;
+  bool bad = false;
+  for (int i = 0; i < S; ++i) {
+    if (std::isnan(states[i].m)) bad = true;
+    if (states[i].m > m) m = states[i].m;
+    n += states[i].n;
+  }
+  double s = 0.0, s2 = 0.0;
+  if (std::isfinite(m)) {
+    for (int i = 0; i < S; ++i) {
+      if (!(states[i].m > -INFINITY)) continue;
+      double e = std::exp(states[i].m - m);
+      s += states[i].s * e;
+      s2 += states[i].s2 * e * e;
+    }
+  }
+  if (bad) m = s = s2 = NAN;
+  if (merged) *merged = rift_ile_lse{m, s, s2, n};
+  if (out) {
+    if (n <= 0) {
+      out[0] = -INFINITY;
+      out[1] = NAN;
+      out[2] = 0.0;
+    } else {
+      out[0] = m + std::log(s) - std::log(n);
+      double var = s2 / (s * s) - 1.0 / n;
+      out[1] = std::sqrt(var > 0 ? var : 0.0);
+      out[2] = s;
+    }
+  }
+  return RIFT_ILE_OK;
+}
+
+extern "C" int rift_ile_lnZ(const rift_ile_point* pt, const rift_ile_draws* draws,
+                            rift_ile_precision prec, const rift_ile_dist* dist, double out[3],
+                            void* stream) {
+  if (!out) {
+    rift_ile_set_error("rift_ile_lnZ: out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  rift_ile_lse st;
+  int rc = rift_ile_lnZ_state(pt, draws, prec, dist, &st, stream);
+  if (rc) return rc;
+  return rift_ile_lnZ_merge(&st, 1, out, nullptr);
+}
+
+extern "C" int64_t rift_ile_last_oob(void) { return t_last_oob; }
+
+extern "C" int rift_ile_lnL_grad(const rift_ile_point*, const rift_ile_draws*, rift_ile_precision,
+                                 double*, double*, void*) {
+  rift_ile_set_error("rift_ile_lnL_grad is not available in this build");
+  return RIFT_ILE_ERR_UNSUPPORTED;
+}
+
+extern "C" int rift_ile_lnZ_batch(const rift_ile_point* const*, const rift_ile_draws*, int32_t,
+                                  rift_ile_precision, double*, void*) {
+  rift_ile_set_error("rift_ile_lnZ_batch is not available in this build");
+  return RIFT_ILE_ERR_UNSUPPORTED;
+}
+
+extern "C" int rift_ile_dist_nodes(double, double, double, double, double, int32_t, double*,
+                                   double*, int32_t*) {
+  rift_ile_set_error("rift_ile_dist_nodes is not available in this build");
+  return RIFT_ILE_ERR_UNSUPPORTED;
+}
+
+extern "C" int rift_ile_release(void) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < 64; ++d) {
+    Workspace& w = g_ws[d];
+    if (!w.partials) continue;
+    cudaSetDevice(d);
+    cudaFree(w.partials);
+    cudaFree(w.state);
+    cudaFree(w.oob);
+    w = Workspace();
+  }
+  cudaSetDevice(cur);
+  return RIFT_ILE_OK;
+}

@@ -1,0 +1,261 @@
+// Device helpers shared by the FP64 and FP32-mixed likelihood kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "dfloat.cuh"
+#include "rift_ile_internal.h"
+
+namespace rift {
+
+// Copies one PointParams record into shared memory (whole block).
+__device__ __forceinline__ void stage_point(PointParams& dst, const PointParams* __restrict__ src) {
+  const int words = (int)(sizeof(PointParams) / sizeof(int));
+  int* d = reinterpret_cast<int*>(&dst);
+  const int* s = reinterpret_cast<const int*>(src);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+__device__ __forceinline__ double load_param_d(const DrawsParams& dp, int which, long long i) {
+  return dp.f64 ? __ldg((const double*)dp.p[which] + i) : (double)__ldg((const float*)dp.p[which] + i);
+}
+
+__device__ __forceinline__ float load_param_f(const DrawsParams& dp, int which, long long i) {
+  return dp.f64 ? (float)__ldg((const double*)dp.p[which] + i) : __ldg((const float*)dp.p[which] + i);
+}
+
+__device__ __forceinline__ double load_logw_d(const DrawsParams& dp, long long i) {
+  if (!dp.logw) return 0.0;
+  return dp.f64 ? __ldg((const double*)dp.logw + i) : (double)__ldg((const float*)dp.logw + i);
+}
+
+// The t parameter of an FP32 draw set is exact in a float; an FP64 draw set
+// keeps its double value as a (hi, lo) pair.
+__device__ __forceinline__ df load_param_df(const DrawsParams& dp, int which, long long i) {
+  if (dp.f64) return df_from_double(__ldg((const double*)dp.p[which] + i));
+  return df{__ldg((const float*)dp.p[which] + i), 0.f};
+}
+
+// -2Y_lm(iota, phi) of mode i from the polynomial coefficients of the point:
+// e^{i m phi} sum_r a_r c^(k0+2r) s^(2l-k0-2r), c = cos(iota/2), s = sin(iota/2);
+// eiphi = e^{i phi}.  T is float or double.
+template <typename T>
+__device__ __forceinline__ void sylm_eval(const PointParams& P, int i, T c, T s, T eiphi_re,
+                                          T eiphi_im, const T* coef, T& yre, T& yim) {
+  const int l = P.ell[i], m = P.em[i], nt = P.ynt[i], k0 = P.yk0[i];
+  // prefactor c^k0 s^(2l - k0 - 2(nt-1)), then homogeneous Horner in (c^2, s^2)
+  T pre = T(1);
+  for (int q = 0; q < k0; ++q) pre *= c;
+  const int es = 2 * l - k0 - 2 * (nt - 1);
+  for (int q = 0; q < es; ++q) pre *= s;
+  const T X = c * c, Ys = s * s;
+  T poly = coef[nt - 1];
+  T yp = T(1);
+  for (int r = nt - 2; r >= 0; --r) {
+    yp *= Ys;
+    poly = poly * X + coef[r] * yp;
+  }
+  T amp = pre * poly;
+  // e^{i m phi} by repeated multiplication (|m| <= 8)
+  T er = T(1), ei = T(0);
+  const int am = m < 0 ? -m : m;
+  for (int q = 0; q < am; ++q) {
+    T nr = er * eiphi_re - ei * eiphi_im;
+    T ni = er * eiphi_im + ei * eiphi_re;
+    er = nr;
+    ei = ni;
+  }
+  if (m < 0) ei = -ei;
+  yre = amp * er;
+  yim = amp * ei;
+}
+
+// a^T D b with D stored as xx, xy, xz, yy, yz, zz.
+template <typename T>
+__device__ __forceinline__ T quad3(const T* D, const T a[3], const T b[3]) {
+  T d0 = D[0] * b[0] + D[1] * b[1] + D[2] * b[2];
+  T d1 = D[1] * b[0] + D[3] * b[1] + D[4] * b[2];
+  T d2 = D[2] * b[0] + D[4] * b[1] + D[5] * b[2];
+  return a[0] * d0 + a[1] * d1 + a[2] * d2;
+}
+
+// Lagrange cubic on nodes -1, 0, 1, 2 at offset f, and the f-derivative.
+__device__ __forceinline__ void lagrange4_d(double f, double w[4], double dw[4]) {
+  double a = f + 1.0, b = f, c = f - 1.0, d = f - 2.0;
+  w[0] = -(b * c * d) * (1.0 / 6.0);
+  w[1] = (a * c * d) * 0.5;
+  w[2] = -(a * b * d) * 0.5;
+  w[3] = (a * b * c) * (1.0 / 6.0);
+  dw[0] = -(c * d + b * d + b * c) * (1.0 / 6.0);
+  dw[1] = (c * d + a * d + a * c) * 0.5;
+  dw[2] = -(b * d + a * d + a * b) * 0.5;
+  dw[3] = (b * c + a * c + a * b) * (1.0 / 6.0);
+}
+
+// ---------------------------------------------------------------- LSE state
+
+// Per-thread online log-sum-exp of v_i = lnL_i + ln w_i, with the running
+// maximum m kept as a double-float pair so that v - m is exact for the
+// draws that carry weight even when lnL ~ 1e6.
+struct ThreadLse {
+  df m;
+  float s, s2;
+  int nan_seen;
+};
+
+__device__ __forceinline__ ThreadLse tlse_init() {
+  ThreadLse t;
+  t.m = df{-CUDART_INF_F, 0.f};
+  t.s = 0.f;
+  t.s2 = 0.f;
+  t.nan_seen = 0;
+  return t;
+}
+
+__device__ __forceinline__ void tlse_push(ThreadLse& t, df v) {
+  if (isnan(v.hi)) {
+    t.nan_seen = 1;
+    return;
+  }
+  if (!(v.hi > -CUDART_INF_F)) return;  // zero weight
+  const bool bigger = (v.hi > t.m.hi) || (v.hi == t.m.hi && v.lo > t.m.lo);
+  float d = __fadd_rn(__fsub_rn(v.hi, t.m.hi), __fsub_rn(v.lo, t.m.lo));
+  if (bigger) {
+    float e = (t.m.hi == -CUDART_INF_F) ? 0.f : __expf(-d);
+    t.s = fmaf(t.s, e, 1.f);
+    t.s2 = fmaf(t.s2, e * e, 1.f);
+    t.m = v;
+  } else {
+    float e = __expf(d);
+    t.s += e;
+    t.s2 = fmaf(e, e, t.s2);
+  }
+}
+
+__device__ __forceinline__ LseState lse_merge(LseState a, LseState b) {
+  if (isnan(a.m) || isnan(b.m)) return LseState{CUDART_NAN, CUDART_NAN, CUDART_NAN, a.n + b.n};
+  if (a.m == -CUDART_INF) return LseState{b.m, b.s, b.s2, a.n + b.n};
+  if (b.m == -CUDART_INF) return LseState{a.m, a.s, a.s2, a.n + b.n};
+  double M = fmax(a.m, b.m);
+  double ea = exp(a.m - M), eb = exp(b.m - M);
+  return LseState{M, a.s * ea + b.s * eb, a.s2 * ea * ea + b.s2 * eb * eb, a.n + b.n};
+}
+
+// Block-level reduction of the per-thread states; thread 0 writes the block
+// partial (with n = 0; draw counts are added by the caller).  FP32 merges inside a warp (the state's m is a pair), then FP64
+// across warps through shared memory, always in the same order.
+__device__ __forceinline__ void block_lse_write(ThreadLse t, LseState* out) {
+  // warp merge in float with the pair-valued maximum
+  for (int off = 16; off > 0; off >>= 1) {
+    float mh = __shfl_down_sync(0xffffffffu, t.m.hi, off);
+    float ml = __shfl_down_sync(0xffffffffu, t.m.lo, off);
+    float os = __shfl_down_sync(0xffffffffu, t.s, off);
+    float os2 = __shfl_down_sync(0xffffffffu, t.s2, off);
+    int on = __shfl_down_sync(0xffffffffu, t.nan_seen, off);
+    t.nan_seen |= on;
+    if (mh == -CUDART_INF_F) continue;
+    if (t.m.hi == -CUDART_INF_F) {
+      t.m = df{mh, ml};
+      t.s = os;
+      t.s2 = os2;
+      continue;
+    }
+    const bool other_bigger = (mh > t.m.hi) || (mh == t.m.hi && ml > t.m.lo);
+    float d = __fadd_rn(__fsub_rn(mh, t.m.hi), __fsub_rn(ml, t.m.lo));
+    if (other_bigger) {
+      float e = __expf(-d);
+      t.s = fmaf(t.s, e, os);
+      t.s2 = fmaf(t.s2, e * e, os2);
+      t.m = df{mh, ml};
+    } else {
+      float e = __expf(d);
+      t.s = fmaf(os, e, t.s);
+      t.s2 = fmaf(os2, e * e, t.s2);
+    }
+  }
+  __shared__ LseState warp_state[32];
+  __shared__ int warp_nan[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    warp_state[wid] = LseState{(double)t.m.hi + (double)t.m.lo, (double)t.s, (double)t.s2, 0.0};
+    warp_nan[wid] = t.nan_seen;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
+    int nan_any = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) {
+      acc = lse_merge(acc, warp_state[w]);
+      nan_any |= warp_nan[w];
+    }
+    acc.n = 0.0;  // the caller knows the draw count
+    if (nan_any) acc.m = acc.s = acc.s2 = CUDART_NAN;
+    *out = acc;
+  }
+}
+
+// The same reduction in IEEE double throughout (FP64 path).
+struct ThreadLse64 {
+  LseState st;
+  int nan_seen;
+};
+
+__device__ __forceinline__ ThreadLse64 tlse64_init() {
+  ThreadLse64 t;
+  t.st = LseState{-CUDART_INF, 0.0, 0.0, 0.0};
+  t.nan_seen = 0;
+  return t;
+}
+
+__device__ __forceinline__ void tlse64_push(ThreadLse64& t, double v) {
+  if (isnan(v)) {
+    t.nan_seen = 1;
+    return;
+  }
+  if (!(v > -CUDART_INF)) return;
+  if (v > t.st.m) {
+    double e = (t.st.m == -CUDART_INF) ? 0.0 : exp(t.st.m - v);
+    t.st.s = fma(t.st.s, e, 1.0);
+    t.st.s2 = fma(t.st.s2, e * e, 1.0);
+    t.st.m = v;
+  } else {
+    double e = exp(v - t.st.m);
+    t.st.s += e;
+    t.st.s2 = fma(e, e, t.st.s2);
+  }
+}
+
+__device__ __forceinline__ void block_lse64_write(ThreadLse64 t, LseState* out) {
+  for (int off = 16; off > 0; off >>= 1) {
+    LseState o;
+    o.m = __shfl_down_sync(0xffffffffu, t.st.m, off);
+    o.s = __shfl_down_sync(0xffffffffu, t.st.s, off);
+    o.s2 = __shfl_down_sync(0xffffffffu, t.st.s2, off);
+    o.n = 0.0;
+    t.nan_seen |= __shfl_down_sync(0xffffffffu, t.nan_seen, off);
+    t.st = lse_merge(t.st, o);
+  }
+  __shared__ LseState warp_state64[32];
+  __shared__ int warp_nan64[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    warp_state64[wid] = t.st;
+    warp_nan64[wid] = t.nan_seen;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
+    int nan_any = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) {
+      acc = lse_merge(acc, warp_state64[w]);
+      nan_any |= warp_nan64[w];
+    }
+    acc.n = 0.0;
+    if (nan_any) acc.m = acc.s = acc.s2 = CUDART_NAN;
+    *out = acc;
+  }
+}
+
+}  // namespace rift

@@ -1,0 +1,39 @@
+// Kernel launchers of the library (each returns the launch status).  The grid
+// is a fixed number of resident blocks per SM for the kernel (occupancy API),
+// written to *blocks; partials, when non-NULL, receives one LSE state per
+// block (at most kMaxPartialsPerSM per SM) and switches the kernel to the
+// fused lnZ form.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "rift_ile_internal.h"
+
+namespace rift {
+
+constexpr int kMaxPartialsPerSM = 16;
+
+cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                            double* lnl_out, LseState* partials, unsigned long long* oob,
+                            int* blocks, cudaStream_t st);
+cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                             double* lnl_out, LseState* partials, unsigned long long* oob,
+                             int* blocks, cudaStream_t st);
+cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
+                               LseState* state_out, cudaStream_t st);
+
+// SM count of the current device (cached).
+int device_sms();
+
+// Grid of a per-draw kernel: SMs x resident blocks per SM, capped so that the
+// per-block partials fit the workspace.  Fixed for a given device and build,
+// so results do not depend on the launch history.
+template <typename KernelT>
+int grid_for(KernelT kernel, int threads, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1)
+    nb = 1;
+  if (nb > kMaxPartialsPerSM) nb = kMaxPartialsPerSM;
+  return device_sms() * nb;
+}
+
+}  // namespace rift

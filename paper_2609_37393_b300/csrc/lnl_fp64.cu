@@ -1,0 +1,226 @@
+// FP64 likelihood kernels: eq. def:lnL:Decomposed evaluated term by term in
+// IEEE double, one draw per thread.  This is the plain reference path of the
+// library (the FP32-mixed kernels are measured against it on the same GPU).
+//
+// Per draw: source direction and transverse basis from (ra - gmst, dec);
+// F_k = F_+ - i F_x with F_+ = p.D.p - q.D.q, F_x = 2 p.D.q; t_k = t_c - x_k.s;
+// -2Y_lm(iota, phi) from the Wigner-d polynomial of the point; Q_{k,lm}(t_k) by
+// the four-point Lagrange cubic on the table; then
+//   T_d = x Re sum_k conj(F_k) sum_lm conj(Y_lm) Q_{k,lm}(t_k)
+//   T_q = x^2/4 sum_k [|F_k|^2 Y^+ U_k Y + Re(F_k^2 Y^T V_k Y)]
+// with the Hermitian and symmetric forms summed over i <= j pairs.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rift {
+namespace {
+
+struct Fp64Out {
+  double lnl;
+  int oob;
+};
+
+template <int MM>
+__device__ __forceinline__ Fp64Out lnl_fp64_draw(const PointParams& P, const double2* sUV,
+                                                 const DrawsParams& dp, long long i) {
+  const double ra = load_param_d(dp, 0, i), dec = load_param_d(dp, 1, i);
+  const double psi = load_param_d(dp, 2, i), incl = load_param_d(dp, 3, i);
+  const double phi = load_param_d(dp, 4, i), lnD = load_param_d(dp, 5, i);
+  const double tc = load_param_d(dp, 6, i);
+  const int K = P.K, M = P.M;
+  const double x = P.d_ref * exp(-lnD);
+  double sl, cl, sd, cd;
+  sincos(ra - P.gmst, &sl, &cl);
+  sincos(dec, &sd, &cd);
+  const double s[3] = {cd * cl, cd * sl, sd};
+  const double e1[3] = {-sl, cl, 0.0};
+  const double e2[3] = {-sd * cl, -sd * sl, cd};
+  double s2p, c2p;
+  sincos(2.0 * psi, &s2p, &c2p);
+
+  double yr[MM], yi[MM];
+  {
+    double sh, ch, sp, cp;
+    sincos(0.5 * incl, &sh, &ch);
+    sincos(phi, &sp, &cp);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      yr[m] = yi[m] = 0.0;
+      if (m < M) sylm_eval<double>(P, m, ch, sh, cp, sp, P.ycoef[m], yr[m], yi[m]);
+    }
+  }
+
+  // quadratic forms a_k = Y^+ U_k Y (real) and b_k = Y^T V_k Y, all detectors
+  double a[kMaxDet], br[kMaxDet], bi[kMaxDet];
+#pragma unroll
+  for (int k = 0; k < kMaxDet; ++k) a[k] = br[k] = bi[k] = 0.0;
+#pragma unroll
+  for (int m = 0; m < MM; ++m) {
+#pragma unroll
+    for (int n = m; n < MM; ++n) {
+      if (n < M) {
+        const double f = (m == n) ? 1.0 : 2.0;
+        // p = conj(Y_m) Y_n, q = Y_m Y_n
+        const double pr = yr[m] * yr[n] + yi[m] * yi[n];
+        const double pi = yr[m] * yi[n] - yi[m] * yr[n];
+        const double qr = yr[m] * yr[n] - yi[m] * yi[n];
+        const double qi = yr[m] * yi[n] + yi[m] * yr[n];
+#pragma unroll
+        for (int k = 0; k < kMaxDet; ++k) {
+          if (k < K) {
+            const double2 u = sUV[(k * M + m) * M + n];
+            const double2 v = sUV[K * M * M + (k * M + m) * M + n];
+            a[k] = fma(f, pr * u.x - pi * u.y, a[k]);
+            br[k] = fma(f, qr * v.x - qi * v.y, br[k]);
+            bi[k] = fma(f, qr * v.y + qi * v.x, bi[k]);
+          }
+        }
+      }
+    }
+  }
+
+  double td = 0.0, tq = 0.0;
+  int oob = 0;
+  for (int k = 0; k < K; ++k) {
+    const double* D = P.resp[k];
+    const double fa = quad3(D, e1, e1), fb = quad3(D, e2, e2), fc = quad3(D, e1, e2);
+    // F(psi) = (F_+(0) - i F_x(0)) e^{2 i psi}, F_+(0) = e1.D.e1 - e2.D.e2, F_x(0) = 2 e1.D.e2
+    const double f0r = fa - fb, f0i = -2.0 * fc;
+    const double Fr = f0r * c2p - f0i * s2p, Fi = f0r * s2p + f0i * c2p;
+    const double tk = tc - (P.pos[k][0] * s[0] + P.pos[k][1] * s[1] + P.pos[k][2] * s[2]);
+    const double u = (tk - P.t0[k]) * P.inv_dt;
+    const double jf = floor(u);
+    double w[4], dw[4];
+    lagrange4_d(u - jf, w, dw);
+    double gr = 0.0, gi = 0.0;  // sum_lm conj(Y) Q(t_k)
+    if (isfinite(u)) {
+      const long long j0 = (long long)jf - 1;
+#pragma unroll
+      for (int tap = 0; tap < 4; ++tap) {
+        const long long j = j0 + tap;
+        if (j < 0 || j >= P.n) {
+          ++oob;
+          continue;
+        }
+        double qr[MM], qi[MM];
+        if (P.q_c128) {
+          const double2* row = (const double2*)P.Q + ((long long)k * P.n + j) * M;
+#pragma unroll
+          for (int m = 0; m < MM; ++m)
+            if (m < M) {
+              double2 q = __ldg(row + m);
+              qr[m] = q.x;
+              qi[m] = q.y;
+            }
+        } else {
+          const float2* row = (const float2*)P.Q + ((long long)k * P.n + j) * M;
+#pragma unroll
+          for (int m = 0; m < MM; ++m)
+            if (m < M) {
+              float2 q = __ldg(row + m);
+              qr[m] = q.x;
+              qi[m] = q.y;
+            }
+        }
+        double sr = 0.0, si = 0.0;
+#pragma unroll
+        for (int m = 0; m < MM; ++m)
+          if (m < M) {
+            sr += yr[m] * qr[m] + yi[m] * qi[m];
+            si += yr[m] * qi[m] - yi[m] * qr[m];
+          }
+        gr = fma(w[tap], sr, gr);
+        gi = fma(w[tap], si, gi);
+      }
+    } else {
+      gr = gi = CUDART_NAN;
+    }
+    td += Fr * gr + Fi * gi;  // Re(conj(F) G)
+    double ak = 0.0, bkr = 0.0, bki = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < kMaxDet; ++kk)
+      if (kk == k) {
+        ak = a[kk];
+        bkr = br[kk];
+        bki = bi[kk];
+      }
+    const double F2r = Fr * Fr - Fi * Fi, F2i = 2.0 * Fr * Fi;
+    tq += (Fr * Fr + Fi * Fi) * ak + (F2r * bkr - F2i * bki);
+  }
+  Fp64Out o;
+  o.lnl = x * td - 0.25 * x * x * tq;
+  o.oob = oob;
+  return o;
+}
+
+template <int MM, bool LSE>
+__global__ void __launch_bounds__(256) lnl_fp64_kernel(const PointParams* __restrict__ gP,
+                                                       DrawsParams dp, double* __restrict__ lnl_out,
+                                                       LseState* __restrict__ partials,
+                                                       unsigned long long* __restrict__ oob_count) {
+  __shared__ PointParams P;
+  extern __shared__ double2 sUV[];
+  stage_point(P, gP);
+  __syncthreads();
+  {
+    const int nuv = 2 * P.K * P.M * P.M;
+    for (int t = threadIdx.x; t < nuv; t += blockDim.x) sUV[t] = __ldg(P.U + t);  // U then V
+  }
+  __syncthreads();
+  ThreadLse64 st = tlse64_init();
+  int oob = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
+    Fp64Out o = lnl_fp64_draw<MM>(P, sUV, dp, i);
+    oob += o.oob;
+    if (!LSE) {
+      lnl_out[i] = o.lnl;
+    } else {
+      tlse64_push(st, o.lnl + load_logw_d(dp, i));
+    }
+  }
+  if (LSE) block_lse64_write(st, partials + blockIdx.x);
+  if (oob_count) {
+    for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
+    if ((threadIdx.x & 31) == 0 && oob) atomicAdd(oob_count, (unsigned long long)oob);
+  }
+}
+
+template <int MM, bool LSE>
+cudaError_t launch_fp64_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                          double* lnl_out, LseState* partials, unsigned long long* oob,
+                          int* blocks, cudaStream_t st) {
+  const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
+  cudaFuncSetAttribute(lnl_fp64_kernel<MM, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  *blocks = grid_for(lnl_fp64_kernel<MM, LSE>, 256, smem);
+  lnl_fp64_kernel<MM, LSE><<<*blocks, 256, smem, st>>>(dP, dp, lnl_out, partials, oob);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_fp64_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                           double* lnl_out, LseState* partials, unsigned long long* oob,
+                           int* blocks, cudaStream_t st) {
+  if (partials) return launch_fp64_k<MM, true>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  return launch_fp64_k<MM, false>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+}
+
+}  // namespace
+
+cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                            double* lnl_out, LseState* partials, unsigned long long* oob,
+                            int* blocks, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_fp64_mm<2>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 4) return launch_fp64_mm<4>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 6) return launch_fp64_mm<6>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 8) return launch_fp64_mm<8>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 10) return launch_fp64_mm<10>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 12) return launch_fp64_mm<12>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  return launch_fp64_mm<16>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+}
+
+}  // namespace rift

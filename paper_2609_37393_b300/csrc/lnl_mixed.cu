@@ -1,0 +1,460 @@
+// FP32-mixed likelihood kernels.
+//
+// The same lnL as the FP64 path (eq. def:lnL:Decomposed), arranged for a GPU
+// whose FP64 pipe is ~60x narrower than its FP32 pipe.  Per detector, in the
+// whitened coordinates built by point.cu,
+//     lnL_k = 1/2 |e(t_k)|^2 - 1/2 |e(t_k) - w_k|^2,
+//     w_k = x (Re F_k a1 + Im F_k a2),  a1 = A y,  a2 = A J y,  y = (Re Y, Im Y),
+// where a1 and a2 are shared by the detectors of one class.
+//
+// Precision: a rounding of the template w by a relative eps moves lnL by
+// <delta h | d - h> ~ eps rho |d - h|, i.e. ~1e-3 nat at rho = 1000 for
+// FP32's eps = 6e-8 at 50 nat from the peak.  So the template is carried to
+// ~1e-10: the sky angles, psi, iota/2, m phi go through an anchored
+// double-float sine/cosine, x through an anchored double-float exponential,
+// Y_lm, F_k and w in double-float, and a1, a2 through an error-free split
+// product (the head/tail split in lnl_mixed_draw).  The arrival time is also double-float (1 ns
+// is ~1e-3 nat).  1/2|e|^2 comes from the tabulated interval polynomial by
+// double-float Horner; only the residual e - w, which is small where the
+// likelihood matters, is formed in FP32 (its error enters as
+// (e - w) . delta, ~1e-5 nat).
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rift {
+
+__device__ float4 g_anchor[2 * kAnchorHalf + 1];  // (sin hi, sin lo, cos hi, cos lo) of j 2^-7
+__device__ float2 g_exp_anchor[2 * kExpHalf + 1];  // e^(j/128) as (hi, lo)
+
+int ensure_anchor_table() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    rift_ile_set_error("ensure_anchor_table: no current CUDA device");
+    return RIFT_ILE_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return RIFT_ILE_OK;
+  static float4 h[2 * kAnchorHalf + 1];
+  for (int j = -kAnchorHalf; j <= kAnchorHalf; ++j) {
+    double a = j * (double)kAnchorStep;
+    double s = std::sin(a), c = std::cos(a);
+    float sh = (float)s, ch = (float)c;
+    h[j + kAnchorHalf] = make_float4(sh, (float)(s - sh), ch, (float)(c - ch));
+  }
+  static float2 e[2 * kExpHalf + 1];
+  for (int j = -kExpHalf; j <= kExpHalf; ++j) {
+    double v = std::exp(j / 128.0);
+    float hi = (float)v;
+    e[j + kExpHalf] = make_float2(hi, (float)(v - hi));
+  }
+  int rc = check_cuda(cudaMemcpyToSymbol(g_anchor, h, sizeof(h)), "anchor table upload");
+  if (!rc) rc = check_cuda(cudaMemcpyToSymbol(g_exp_anchor, e, sizeof(e)), "exp table upload");
+  if (!rc) done[dev] = true;
+  return rc;
+}
+
+namespace {
+
+// sin and cos of a double-float angle to ~1e-15 absolute: reduce by 2 pi (pair
+// constant), take the nearest anchor a_j = j 2^-7, and add the residual
+// d (|d| <= 2^-8) through sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24.
+__device__ __forceinline__ void sincos_df(df a, df& s_out, df& c_out) {
+  const float kTwoPiHi = 6.28318548202514648f;
+  const float kTwoPiLo = -1.7484555314695172e-07f;
+  float k = rintf(a.hi * 0.159154943091895336f);
+  df kp = two_prod(k, kTwoPiHi);
+  kp.lo = fmaf(k, kTwoPiLo, kp.lo);
+  df r = df_add(a, df_neg(kp));
+  int j = __float2int_rn(r.hi * kAnchorInvStep);
+  j = max(-kAnchorHalf, min(kAnchorHalf, j));
+  const float dh = __fsub_rn(r.hi, (float)j * kAnchorStep);  // exact
+  const float dl = r.lo;
+  const float d2 = dh * dh;
+  const float sb = fmaf(dh * d2, fmaf(d2, 1.f / 120.f, -1.f / 6.f), dl);  // sin d - dh
+  const float cb = fmaf(d2, fmaf(d2, 1.f / 24.f, -0.5f), -dh * dl);       // cos d - 1
+  const float4 an = g_anchor[j + kAnchorHalf];
+  // sin(a_j + d) = S (1 + cb) + C (dh + sb);  cos(a_j + d) = C (1 + cb) - S (dh + sb)
+  df p = two_prod(an.z, dh);
+  p.lo = fmaf(an.w, dh, p.lo);
+  p.lo = fmaf(an.z, sb, p.lo);
+  p.lo = fmaf(an.x, cb, p.lo);
+  s_out = df_add(df{an.x, an.y}, p);
+  df q = two_prod(an.x, dh);
+  q.lo = fmaf(an.y, dh, q.lo);
+  q.lo = fmaf(an.x, sb, q.lo);
+  q.lo = fmaf(-an.z, cb, q.lo);
+  c_out = df_add(df{an.z, an.w}, df_neg(q));
+}
+
+// e^a for a double-float a: a = k ln2 + j/128 + d, |d| <= 2^-8, e^d by its
+// Taylor series to d^4, anchors e^(j/128) from the table.
+__device__ __forceinline__ df exp_df(df a) {
+  const float kLn2Hi = 0.693147182464599609f;
+  const float kLn2Lo = -1.904654323148236e-09f;
+  float k = rintf(a.hi * 1.44269504088896341f);
+  df kp = two_prod(k, kLn2Hi);
+  kp.lo = fmaf(k, kLn2Lo, kp.lo);
+  df r = df_add(a, df_neg(kp));
+  int j = __float2int_rn(r.hi * 128.f);
+  j = max(-kExpHalf, min(kExpHalf, j));
+  const float dh = __fsub_rn(r.hi, (float)j * (1.f / 128.f));
+  const float d = dh + r.lo;
+  // e^d - 1 - dh = r.lo + d^2/2 + d^3/6 + d^4/24
+  const float tail = fmaf(d * d, fmaf(d, fmaf(d, 1.f / 24.f, 1.f / 6.f), 0.5f), r.lo);
+  df ed = fast_two_sum(1.f, dh);
+  ed.lo = __fadd_rn(ed.lo, tail);
+  const float2 an = g_exp_anchor[j + kExpHalf];
+  df v = df_mul(df{an.x, an.y}, ed);
+  const int ki = (int)k;
+  return df{ldexpf(v.hi, ki), ldexpf(v.lo, ki)};
+}
+
+__device__ __forceinline__ df df_pow(df b, int n) {
+  df r = df{1.f, 0.f};
+  for (int q = 0; q < n; ++q) r = df_mul(r, b);
+  return r;
+}
+
+// -2Y_lm of mode i in double-float from c = cos(iota/2), s = sin(iota/2).
+__device__ __forceinline__ void sylm_df(const PointParams& P, int i, df c, df s, float phi,
+                                        df& yr, df& yi) {
+  const int l = P.ell[i], m = P.em[i], nt = P.ynt[i], k0 = P.yk0[i];
+  df pre = df_mul(df_pow(c, k0), df_pow(s, 2 * l - k0 - 2 * (nt - 1)));
+  const df X = df_mul(c, c), Ys = df_mul(s, s);
+  df poly = df{P.ycoef_hi[i][nt - 1], P.ycoef_lo[i][nt - 1]};
+  df yp = df{1.f, 0.f};
+  for (int r = nt - 2; r >= 0; --r) {
+    yp = df_mul(yp, Ys);
+    poly = df_add(df_mul(poly, X), df_mul(df{P.ycoef_hi[i][r], P.ycoef_lo[i][r]}, yp));
+  }
+  const df amp = df_mul(pre, poly);
+  df sm, cm;
+  sincos_df(two_prod((float)m, phi), sm, cm);
+  yr = df_mul(amp, cm);
+  yi = df_mul(amp, sm);
+}
+
+// Complex product of pairs.
+__device__ __forceinline__ void cmul_df(df ar, df ai, df br, df bi, df& cr, df& ci) {
+  cr = df_add(df_mul(ar, br), df_neg(df_mul(ai, bi)));
+  ci = df_add(df_mul(ar, bi), df_mul(ai, br));
+}
+
+// Antenna factor of detector k from the double-float basis:
+// F(0) = e1.D.e1 - e2.D.e2 - 2 i e1.D.e2, then F = F(0) e^{2 i psi}.
+__device__ __forceinline__ void antenna_df(const PointParams& P, int k, const df e1[3],
+                                           const df e2[3], df c2p, df s2p, df& Fr, df& Fi) {
+  df Dm[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) Dm[c] = df{P.resp_hi[k][c], P.resp_lo[k][c]};
+  // D.e1 (e1.z = 0) and D.e2
+  const df d1x = df_add(df_mul(Dm[0], e1[0]), df_mul(Dm[1], e1[1]));
+  const df d1y = df_add(df_mul(Dm[1], e1[0]), df_mul(Dm[3], e1[1]));
+  const df d2x = df_add(df_add(df_mul(Dm[0], e2[0]), df_mul(Dm[1], e2[1])), df_mul(Dm[2], e2[2]));
+  const df d2y = df_add(df_add(df_mul(Dm[1], e2[0]), df_mul(Dm[3], e2[1])), df_mul(Dm[4], e2[2]));
+  const df d2z = df_add(df_add(df_mul(Dm[2], e2[0]), df_mul(Dm[4], e2[1])), df_mul(Dm[5], e2[2]));
+  const df a = df_add(df_mul(e1[0], d1x), df_mul(e1[1], d1y));
+  const df b = df_add(df_add(df_mul(e2[0], d2x), df_mul(e2[1], d2y)), df_mul(e2[2], d2z));
+  const df cc = df_add(df_mul(e1[0], d2x), df_mul(e1[1], d2y));
+  const df f0r = df_sub(a, b);
+  const df f0i = df{-2.f * cc.hi, -2.f * cc.lo};
+  cmul_df(f0r, f0i, c2p, s2p, Fr, Fi);
+}
+
+// The error-free split of a mode value y (|y| < 2): y1 = y rounded to a
+// multiple of 2^-8 (9 significant bits), y2 = y - y1 exact.
+__device__ __forceinline__ void split_y(float y, float& y1, float& y2) {
+  const float C = 49152.0f;  // 1.5 * 2^15: ulp(C) = 2^-8
+  y1 = __fsub_rn(__fadd_rn(y, C), C);
+  y2 = __fsub_rn(y, y1);
+}
+
+template <int MM, int RR>
+struct MixedDraw {
+  df lnl;
+  int oob;
+};
+
+template <int MM, int RR>
+__device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P,
+                                                            const float4* sA, const float* sg,
+                                                            const DrawsParams& dp, long long i) {
+  const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
+  const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
+  const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
+  const df tc = load_param_df(dp, 6, i);
+  const int M = P.M, D = P.D, R = P.R, n = P.n;
+
+  // distance factor x = D_ref e^{-lnD}
+  df lx = two_sum(P.ln_dref_hi, -lnD);
+  lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
+  const df x = exp_df(fast_two_sum(lx.hi, lx.lo));
+
+  // sky direction and transverse basis
+  df lam = two_sum(ra, -P.gmst_hi);
+  lam.lo = __fsub_rn(lam.lo, P.gmst_lo);
+  lam = fast_two_sum(lam.hi, lam.lo);
+  df sl, cl, sd, cd;
+  sincos_df(lam, sl, cl);
+  sincos_df(df{dec, 0.f}, sd, cd);
+  const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
+  const df e1[3] = {df_neg(sl), cl, df{0.f, 0.f}};
+  const df e2[3] = {df_neg(df_mul(sd, cl)), df_neg(df_mul(sd, sl)), cd};
+  df s2p, c2p;
+  sincos_df(df{2.f * psi, 0.f}, s2p, c2p);
+  df sh, ch;
+  sincos_df(df{0.5f * incl, 0.f}, sh, ch);
+
+  dacc T = dacc_zero();
+  int oob = 0;
+  bool bad = false;
+  for (int c = 0; c < P.ncls; ++c) {
+    // a1 = A y, a2 = A J y by the split product: the products of the 10-bit
+    // head of A with the 9-bit head of y are exact and their sum stays below
+    // 2^24 quanta, so ex1/ex2 are exact; every other term is ~2^-9 smaller.
+    float ex1[RR], ex2[RR], co1[RR], co2[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) ex1[r] = ex2[r] = co1[r] = co2[r] = 0.f;
+    const float4* Ac = sA + (size_t)c * R * D;
+    for (int a = 0; a < M; ++a) {
+      df yr, yi;
+      sylm_df(P, a, ch, sh, phi, yr, yi);
+      float yr1, yr2, yi1, yi2;
+      split_y(yr.hi, yr1, yr2);
+      split_y(yi.hi, yi1, yi2);
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        if (r < R) {
+          const float4 at = Ac[r * D + a];      // (head, tail, lo, -) of A[r][a]
+          const float4 ab = Ac[r * D + M + a];  // of A[r][M + a]
+          const float at_hi = at.x + at.y, ab_hi = ab.x + ab.y;
+          // a1_r += A_t yr + A_b yi ;  a2_r += A_b yr - A_t yi
+          ex1[r] = fmaf(at.x, yr1, ex1[r]);
+          ex1[r] = fmaf(ab.x, yi1, ex1[r]);
+          ex2[r] = fmaf(ab.x, yr1, ex2[r]);
+          ex2[r] = fmaf(-at.x, yi1, ex2[r]);
+          float t1 = fmaf(at.x, yr2, co1[r]);
+          t1 = fmaf(at.y, yr.hi, t1);
+          t1 = fmaf(at_hi, yr.lo, t1);
+          t1 = fmaf(at.z, yr.hi, t1);
+          t1 = fmaf(ab.x, yi2, t1);
+          t1 = fmaf(ab.y, yi.hi, t1);
+          t1 = fmaf(ab_hi, yi.lo, t1);
+          co1[r] = fmaf(ab.z, yi.hi, t1);
+          float t2 = fmaf(ab.x, yr2, co2[r]);
+          t2 = fmaf(ab.y, yr.hi, t2);
+          t2 = fmaf(ab_hi, yr.lo, t2);
+          t2 = fmaf(ab.z, yr.hi, t2);
+          t2 = fmaf(-at.x, yi2, t2);
+          t2 = fmaf(-at.y, yi.hi, t2);
+          t2 = fmaf(-at_hi, yi.lo, t2);
+          co2[r] = fmaf(-at.z, yi.hi, t2);
+        }
+      }
+    }
+    df a1[RR], a2[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      a1[r] = two_sum(ex1[r], co1[r]);
+      a2[r] = two_sum(ex2[r], co2[r]);
+    }
+    const float* gc = sg + c * R;
+    for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
+      const int k = P.det_order[q];
+      df Fr, Fi;
+      antenna_df(P, k, e1, e2, c2p, s2p, Fr, Fi);
+      const df xFr = df_mul(x, Fr), xFi = df_mul(x, Fi);
+      df w[RR];
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        // w_r = xFr a1_r + xFi a2_r
+        const df p1 = two_prod(xFr.hi, a1[r].hi), p2 = two_prod(xFi.hi, a2[r].hi);
+        const df s = two_sum(p1.hi, p2.hi);
+        float lo = __fadd_rn(__fadd_rn(p1.lo, p2.lo), s.lo);
+        lo = fmaf(xFr.hi, a1[r].lo, lo);
+        lo = fmaf(xFr.lo, a1[r].hi, lo);
+        lo = fmaf(xFi.hi, a2[r].lo, lo);
+        lo = fmaf(xFi.lo, a2[r].hi, lo);
+        w[r] = fast_two_sum(s.hi, lo);
+      }
+      // arrival time and table position
+      df delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
+      delay = df_add(delay, df_mul(df{P.pos_hi[k][1], P.pos_lo[k][1]}, s1));
+      delay = df_add(delay, df_mul(df{P.pos_hi[k][2], P.pos_lo[k][2]}, s2));
+      const df rel = df_add(df_sub(tc, delay), df{-P.t0_hi[k], -P.t0_lo[k]});
+      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
+      if (!isfinite(u.hi)) {
+        bad = true;
+        oob += 4;
+        continue;
+      }
+      float jf = floorf(u.hi);
+      if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
+      const float f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
+      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the table)
+      df half_e2 = df{0.f, 0.f};
+      if (jf >= -2.f && jf <= (float)n) {
+        const float2* pc = P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
+        float2 cf = __ldg(pc + kPolyDeg);
+        df acc = df{cf.x, cf.y};
+#pragma unroll
+        for (int p = kPolyDeg - 1; p >= 0; --p) {
+          cf = __ldg(pc + p);
+          acc = df_add(df_mul_f(acc, f), df{cf.x, cf.y});
+        }
+        half_e2 = acc;
+      }
+      // residual e - w = sum_i wt_i (e_i - w) - sigma (e_j - w) with FP32
+      // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
+      // weights' sum: sum_i wt_i e_i = e + sigma e_j + O(u |e_i - e_j|)
+      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
+      float wt[4];
+      wt[0] = -(f * fc * fd) * (1.f / 6.f);
+      wt[1] = (fa * fc * fd) * 0.5f;
+      wt[2] = -(fa * f * fd) * 0.5f;
+      wt[3] = (fa * f * fc) * (1.f / 6.f);
+      const df ws = df_add(two_sum(wt[0], wt[1]), two_sum(wt[2], wt[3]));
+      const float sigma = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
+      float res[RR];
+#pragma unroll
+      for (int r = 0; r < RR; ++r) res[r] = 0.f;
+      const float2* Ek = P.ehat + (size_t)k * n * R;
+#pragma unroll
+      for (int tap = 0; tap < 4; ++tap) {
+        const float jj = jf - 1.f + (float)tap;
+        const bool valid = (jj >= 0.f && jj < (float)n);
+        if (!valid) ++oob;
+        const float2* row = Ek + (size_t)(valid ? (int)jj : 0) * R;
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          if (r < R) {
+            float2 e = valid ? __ldg(row + r) : make_float2(0.f, 0.f);
+            const float dlt = __fadd_rn(__fsub_rn(e.x, w[r].hi), __fsub_rn(e.y, w[r].lo));
+            res[r] = fmaf(wt[tap], dlt, res[r]);
+            if (tap == 1) res[r] = fmaf(-sigma, dlt, res[r]);  // sigma is ~1 ulp of wt: apart
+          }
+        }
+      }
+      float q2 = 0.f, nul = 0.f;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        if (r < R) {
+          q2 = fmaf(res[r], res[r], q2);
+          nul = fmaf(gc[r] * w[r].hi, w[r].hi, nul);
+        }
+      }
+      dacc_add(T, half_e2);
+      dacc_add(T, df{-0.5f * q2, 0.f});
+      if (P.has_null[c]) dacc_add(T, df{0.5f * nul, 0.f});
+    }
+  }
+  MixedDraw<MM, RR> o;
+  o.lnl = dacc_result(T);
+  if (bad) o.lnl = df{CUDART_NAN_F, 0.f};
+  o.oob = oob;
+  return o;
+}
+
+template <int MM, int RR, bool LSE>
+__global__ void __launch_bounds__(128) lnl_mixed_kernel(const PointParams* __restrict__ gP,
+                                                        DrawsParams dp, double* __restrict__ lnl_out,
+                                                        LseState* __restrict__ partials,
+                                                        unsigned long long* __restrict__ oob_count) {
+  __shared__ PointParams P;
+  extern __shared__ float4 smem4[];
+  stage_point(P, gP);
+  __syncthreads();
+  const int R = P.R, D = P.D, ncls = P.ncls;
+  float4* sA = smem4;
+  float* sg = reinterpret_cast<float*>(smem4 + (size_t)ncls * R * D);
+  // A in split form: (10-bit head, tail, lo part, 0) per entry.  The head is
+  // A_hi rounded to a multiple of 2^-9 of a power of two >= max_a |A[r][a]|.
+  for (int t = threadIdx.x; t < ncls * R; t += blockDim.x) {
+    const float2* row = P.A + (size_t)t * D;
+    float mx = 0.f;
+    for (int a = 0; a < D; ++a) mx = fmaxf(mx, fabsf(__ldg(row + a).x));
+    int e = 0;
+    frexpf(mx, &e);  // mx < 2^e
+    const float C = ldexpf(1.5f, e + 14);  // ulp(C) = 2^(e - 9)
+    for (int a = 0; a < D; ++a) {
+      const float2 v = __ldg(row + a);
+      const float head = __fsub_rn(__fadd_rn(v.x, C), C);
+      sA[(size_t)t * D + a] = make_float4(head, __fsub_rn(v.x, head), v.y, 0.f);
+    }
+    sg[t] = __ldg(P.gm1 + t);
+  }
+  __syncthreads();
+  ThreadLse st = tlse_init();
+  int oob = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
+    MixedDraw<MM, RR> o = lnl_mixed_draw<MM, RR>(P, sA, sg, dp, i);
+    oob += o.oob;
+    if (!LSE) {
+      lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
+    } else {
+      float lw = 0.f;
+      if (dp.logw) lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
+      tlse_push(st, df_add_f(o.lnl, lw));
+    }
+  }
+  if (LSE) block_lse_write(st, partials + blockIdx.x);
+  if (oob_count) {
+    for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
+    if ((threadIdx.x & 31) == 0 && oob) atomicAdd(oob_count, (unsigned long long)oob);
+  }
+}
+
+template <int MM, int RR, bool LSE>
+cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                           double* lnl_out, LseState* partials, unsigned long long* oob,
+                           int* blocks, cudaStream_t st) {
+  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
+                      (size_t)hp.ncls * hp.R * sizeof(float);
+  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+  *blocks = grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem);
+  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
+  return cudaGetLastError();
+}
+
+template <int MM, int RR>
+cudaError_t launch_mixed_mr(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                            double* lnl_out, LseState* partials, unsigned long long* oob,
+                            int* blocks, cudaStream_t st) {
+  if (partials) return launch_mixed_k<MM, RR, true>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  return launch_mixed_k<MM, RR, false>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+}
+
+template <int MM>
+cudaError_t launch_mixed_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                            double* lnl_out, LseState* partials, unsigned long long* oob,
+                            int* blocks, cudaStream_t st) {
+  if (hp.R <= MM) return launch_mixed_mr<MM, MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  return launch_mixed_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+}
+
+}  // namespace
+
+cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                             double* lnl_out, LseState* partials, unsigned long long* oob,
+                             int* blocks, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_mixed_mm<2>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 4) return launch_mixed_mm<4>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 6) return launch_mixed_mm<6>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 8) return launch_mixed_mm<8>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 10) return launch_mixed_mm<10>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  if (M <= 12) return launch_mixed_mm<12>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+  return launch_mixed_mm<16>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
+}
+
+}  // namespace rift

@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rift_ile.h"
+
+void rift_ile_set_error(const char* fmt, ...);
+
+namespace rift {
+
+constexpr int kMaxDet = RIFT_ILE_MAX_DET;
+constexpr int kMaxModes = RIFT_ILE_MAX_MODES;
+constexpr int kMaxDim = 2 * RIFT_ILE_MAX_MODES;  // real dimension D = 2M
+constexpr int kMaxYTerms = 12;                   // terms of one Goldberg sum, l <= 8
+constexpr int kNpar = RIFT_ILE_NPAR;
+
+// Anchors of the double-float sine/cosine: a_j = j h, h = 2^-7, |j| <= kAnchorHalf.
+constexpr int kAnchorHalf = 416;
+constexpr float kAnchorStep = 0.0078125f;  // 2^-7
+constexpr float kAnchorInvStep = 128.0f;
+// Anchors of the double-float exponential: e^(j/128), |j| <= kExpHalf.
+constexpr int kExpHalf = 46;
+constexpr int kPolyDeg = 6;  // 1/2 |e(f)|^2 on one table interval is a sextic in f
+
+// Everything a kernel needs about one intrinsic point.  Lives in device
+// memory (one record per point) and is staged into shared memory by each
+// block; array pointers are device pointers owned by the point.
+struct PointParams {
+  int K, M, D, n;   // detectors, modes, real dimension 2M, samples per table
+  int q_c128;       // Q element type of the FP64 path (0 complex64, 1 complex128)
+  int pad0;
+  double gmst, d_ref, dt, inv_dt;
+  double t0[kMaxDet];
+  double pos[kMaxDet][3];
+  double resp[kMaxDet][6];
+  // -2Y_lm(iota, phi) = e^{i m phi} sum_r ycoef[r] c^(yk0 + 2r) s^(2l - yk0 - 2r),
+  // c = cos(iota/2), s = sin(iota/2); r < ynt.
+  int ell[kMaxModes], em[kMaxModes], ynt[kMaxModes], yk0[kMaxModes];
+  double ycoef[kMaxModes][kMaxYTerms];
+  // double-float copies for the mixed path
+  float t0_hi[kMaxDet], t0_lo[kMaxDet];
+  float pos_hi[kMaxDet][3], pos_lo[kMaxDet][3];
+  float resp_hi[kMaxDet][6], resp_lo[kMaxDet][6];
+  float gmst_hi, gmst_lo, inv_dt_hi, inv_dt_lo, ln_dref_hi, ln_dref_lo;
+  float ycoef_hi[kMaxModes][kMaxYTerms], ycoef_lo[kMaxModes][kMaxYTerms];
+  // detector classes (identical U_k, V_k share one whitening): the detectors
+  // of class c are det_order[cls_begin[c] .. cls_begin[c+1]).
+  int R;            // whitened dimension (largest rank over the classes)
+  int ncls;
+  int cls_begin[kMaxDet + 1];
+  int det_order[kMaxDet];
+  int cls_of[kMaxDet];
+  int has_null[kMaxDet];  // class keeps near-null directions (see point.cu)
+  // FP64 path tables
+  const void* Q;        // [K][n][M] complex64 or complex128
+  const double2* U;     // [K][M][M]
+  const double2* V;     // [K][M][M]
+  // FP32-mixed path tables (whitened real form, see point.cu), (hi, lo) pairs
+  const float2* A;      // [ncls][R][D]  w = A z
+  const float* gm1;     // [ncls][R]     1 - lam_r/s_r^2 (0 except kept null directions)
+  const float2* ehat;   // [K][n][R]     whitened Q table
+  const float2* epoly;  // [K][n+3][7]   1/2|e(f)|^2 on interval j (index j+2), coefficients of f^0..f^6
+};
+
+// Per-launch description of the draws.
+struct DrawsParams {
+  const void* p[kNpar];  // ra, dec, psi, incl, phase, lnD, t
+  const void* logw;
+  long long n;
+  int f64;
+};
+
+struct LseState {
+  double m, s, s2, n;
+};
+
+// Host helpers ---------------------------------------------------------------
+int check_cuda(cudaError_t e, const char* what);
+int ensure_anchor_table();  // once per device (sine/cosine and exponential anchors)
+
+}  // namespace rift
+
+struct rift_ile_point {
+  rift::PointParams host;        // host copy (pointers are device pointers)
+  rift::PointParams* dev;        // device copy
+  void* q_copy;                  // owned device copy of Q
+  double2* uv;                   // owned U then V
+  float2* A;                     // owned
+  float* gm1;                    // owned
+  float2* ehat;                  // owned
+  float2* epoly;                 // owned
+  int device;
+};
