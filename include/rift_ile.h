@@ -183,6 +183,23 @@ int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws* draws,
                        rift_ile_precision prec, const rift_ile_dist* dist, rift_ile_lse* state,
                        void* stream);
 
+/* rift_ile_lnZ_state without any allocation (the paper has no counterpart:
+ * this is a deployment variant).  For callers that may not allocate device
+ * memory while they run: a framework that owns the device heap through its
+ * own pool and forbids other cudaMalloc/cudaFree calls, or a time-critical
+ * loop where an allocation could block or fail.  Same arguments and result
+ * as rift_ile_lnZ_state with dist = NULL; it never calls cudaMalloc,
+ * cudaFree or an allocating library routine.  Its scratch (per-block LSE
+ * partials, about 128 KB) is a fixed static device array that every GPU
+ * loading the library holds until exit; a device with more than 256 SMs is
+ * rejected with RIFT_ILE_ERR_UNSUPPORTED.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make it before any stream capture.  All calls on a device
+ * share the array: calls whose work overlaps on the GPU race and must be
+ * serialised.  Synchronises `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_ile_draws* draws,
+                               rift_ile_precision prec, rift_ile_lse* state, void* stream);
+
 /* Exact merge of S LSE states (HOST) into out[3] = lnZ, sigma_lnZ, n_eff;
  * merged_state (may be NULL) receives the merged state.  Host only. */
 int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],

@@ -36,4 +36,22 @@ int grid_for(KernelT kernel, int threads, size_t smem) {
   return device_sms() * nb;
 }
 
+// The same launches with the SM count given by the caller, for code that must
+// not touch the library's workspace (grid = sms x resident blocks per SM, at
+// most kMaxPartialsPerSM per SM).
+template <typename KernelT>
+int grid_for_sms(KernelT kernel, int threads, size_t smem, int sms) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1)
+    nb = 1;
+  if (nb > kMaxPartialsPerSM) nb = kMaxPartialsPerSM;
+  return sms * nb;
+}
+cudaError_t launch_lnl_fp64_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                double* lnl_out, LseState* partials, unsigned long long* oob,
+                                int sms, int* blocks, cudaStream_t st);
+cudaError_t launch_lnl_mixed_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                 double* lnl_out, LseState* partials, unsigned long long* oob,
+                                 int sms, int* blocks, cudaStream_t st);
+
 }  // namespace rift

@@ -223,4 +223,40 @@ cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const 
   return launch_fp64_mm<16>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
 }
 
+namespace {
+
+template <int MM, bool LSE>
+cudaError_t launch_fp64_k_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                              double* lnl_out, LseState* partials, unsigned long long* oob,
+                              int sms, int* blocks, cudaStream_t st) {
+  const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
+  cudaFuncSetAttribute(lnl_fp64_kernel<MM, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  *blocks = grid_for_sms(lnl_fp64_kernel<MM, LSE>, 256, smem, sms);
+  lnl_fp64_kernel<MM, LSE><<<*blocks, 256, smem, st>>>(dP, dp, lnl_out, partials, oob);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_fp64_mm_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                               double* lnl_out, LseState* partials, unsigned long long* oob,
+                               int sms, int* blocks, cudaStream_t st) {
+  if (partials) return launch_fp64_k_sms<MM, true>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  return launch_fp64_k_sms<MM, false>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+}
+
+}  // namespace
+
+cudaError_t launch_lnl_fp64_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                double* lnl_out, LseState* partials, unsigned long long* oob,
+                                int sms, int* blocks, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_fp64_mm_sms<2>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 4) return launch_fp64_mm_sms<4>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 6) return launch_fp64_mm_sms<6>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 8) return launch_fp64_mm_sms<8>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 10) return launch_fp64_mm_sms<10>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 12) return launch_fp64_mm_sms<12>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  return launch_fp64_mm_sms<16>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+}
+
 }  // namespace rift

@@ -457,4 +457,46 @@ cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const
   return launch_mixed_mm<16>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
 }
 
+namespace {
+
+template <int MM, int RR, bool LSE>
+cudaError_t launch_mixed_k_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                               double* lnl_out, LseState* partials, unsigned long long* oob,
+                               int sms, int* blocks, cudaStream_t st) {
+  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
+                      (size_t)hp.ncls * hp.R * sizeof(float);
+  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+  *blocks = grid_for_sms(lnl_mixed_kernel<MM, RR, LSE>, 128, smem, sms);
+  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_mixed_mm_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                double* lnl_out, LseState* partials, unsigned long long* oob,
+                                int sms, int* blocks, cudaStream_t st) {
+  const bool wide = hp.R > MM;
+  if (partials)
+    return wide ? launch_mixed_k_sms<MM, 2 * MM, true>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st)
+                : launch_mixed_k_sms<MM, MM, true>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  return wide ? launch_mixed_k_sms<MM, 2 * MM, false>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st)
+              : launch_mixed_k_sms<MM, MM, false>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+}
+
+}  // namespace
+
+cudaError_t launch_lnl_mixed_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                 double* lnl_out, LseState* partials, unsigned long long* oob,
+                                 int sms, int* blocks, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_mixed_mm_sms<2>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 4) return launch_mixed_mm_sms<4>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 6) return launch_mixed_mm_sms<6>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 8) return launch_mixed_mm_sms<8>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 10) return launch_mixed_mm_sms<10>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  if (M <= 12) return launch_mixed_mm_sms<12>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+  return launch_mixed_mm_sms<16>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+}
+
 }  // namespace rift
