@@ -277,10 +277,22 @@ extern "C" int rift_ile_lnZ(const rift_ile_point* pt, const rift_ile_draws* draw
 
 extern "C" int64_t rift_ile_last_oob(void) { return t_last_oob; }
 
-extern "C" int rift_ile_lnL_grad(const rift_ile_point*, const rift_ile_draws*, rift_ile_precision,
-                                 double*, double*, void*) {
-  rift_ile_set_error("rift_ile_lnL_grad is not available in this build");
-  return RIFT_ILE_ERR_UNSUPPORTED;
+extern "C" int rift_ile_lnL_grad(const rift_ile_point* pt, const rift_ile_draws* draws,
+                                 rift_ile_precision prec, double* lnL_out, double* grad_out,
+                                 void* stream) {
+  int rc = check_point(pt, prec);
+  if (!rc) rc = check_draws(draws);
+  if (rc) return rc;
+  if (draws->n == 0) return RIFT_ILE_OK;
+  if (!grad_out) {
+    rift_ile_set_error("rift_ile_lnL_grad: grad_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const DrawsParams dp = to_params(draws);
+  cudaError_t e = (prec == RIFT_ILE_FP64)
+                      ? launch_grad_fp64(pt->host, pt->dev, dp, lnL_out, grad_out, (cudaStream_t)stream)
+                      : launch_grad_mixed(pt->host, pt->dev, dp, lnL_out, grad_out, (cudaStream_t)stream);
+  return check_cuda(e, "rift_ile_lnL_grad launch");
 }
 
 extern "C" int rift_ile_lnZ_batch(const rift_ile_point* const*, const rift_ile_draws*, int32_t,

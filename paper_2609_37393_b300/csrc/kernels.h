@@ -18,6 +18,11 @@ cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const 
 cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                              double* lnl_out, LseState* partials, unsigned long long* oob,
                              int* blocks, cudaStream_t st);
+// lnL (lnl_out may be NULL) and its gradient, grad_out[7][n].
+cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                              double* lnl_out, double* grad_out, cudaStream_t st);
+cudaError_t launch_grad_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                             double* lnl_out, double* grad_out, cudaStream_t st);
 cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
                                LseState* state_out, cudaStream_t st);
 

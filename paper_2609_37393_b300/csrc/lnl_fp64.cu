@@ -208,6 +208,247 @@ cudaError_t launch_fp64_mm(const PointParams& hp, const PointParams* dP, const D
   return launch_fp64_k<MM, false>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
 }
 
+// ---------------------------------------------------------------- gradient
+
+// lnL and d lnL / d(ra, dec, psi, iota, phase, lnD, t_c) of one draw in FP64,
+// the chain rule of eq. def:lnL:Decomposed written out:
+//   T_d = x sum_k Re(conj F_k G_k), G_k = sum_lm conj(Y_lm) Q_k,lm(t_k),
+//   T_q = x^2/4 sum_k [|F_k|^2 a_k + Re(F_k^2 b_k)], a_k = Y^+ U_k Y, b_k = Y^T V_k Y,
+// with dF_k from the derivatives of the transverse basis, dY/d phase = i m Y,
+// dY/d iota from the Wigner-d polynomial, dQ/dt from the cubic's slope, and
+// da_k = 2 Re(dY^+ U_k Y), db_k = 2 dY^T V_k Y (U Hermitian, V symmetric as
+// eq. QUV makes them).
+template <int MM>
+__device__ __forceinline__ double lnl_fp64_grad_draw(const PointParams& P, const double2* sUV,
+                                                     const DrawsParams& dp, long long i,
+                                                     double g[kNpar]) {
+  const double ra = load_param_d(dp, 0, i), dec = load_param_d(dp, 1, i);
+  const double psi = load_param_d(dp, 2, i), incl = load_param_d(dp, 3, i);
+  const double phi = load_param_d(dp, 4, i), lnD = load_param_d(dp, 5, i);
+  const double tc = load_param_d(dp, 6, i);
+  const int K = P.K, M = P.M;
+  const double x = P.d_ref * exp(-lnD);
+  double sl, cl, sd, cd;
+  sincos(ra - P.gmst, &sl, &cl);
+  sincos(dec, &sd, &cd);
+  const double s[3] = {cd * cl, cd * sl, sd};
+  const double ds_ra[3] = {-cd * sl, cd * cl, 0.0};
+  const double ds_dec[3] = {-sd * cl, -sd * sl, cd};
+  const double e1[3] = {-sl, cl, 0.0};
+  const double e2[3] = {-sd * cl, -sd * sl, cd};
+  const double de1_ra[3] = {-cl, -sl, 0.0};
+  const double de2_ra[3] = {sd * sl, -sd * cl, 0.0};
+  const double de2_dec[3] = {-cd * cl, -cd * sl, -sd};
+  double s2p, c2p;
+  sincos(2.0 * psi, &s2p, &c2p);
+
+  double yr[MM], yi[MM], dyr[MM], dyi[MM];
+  {
+    double sh, ch, sp, cp;
+    sincos(0.5 * incl, &sh, &ch);
+    sincos(phi, &sp, &cp);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      yr[m] = yi[m] = dyr[m] = dyi[m] = 0.0;
+      if (m < M) {
+        sylm_eval<double>(P, m, ch, sh, cp, sp, P.ycoef[m], yr[m], yi[m]);
+        // d/d iota of sum_r a_r c^p s^q, p = k0 + 2r, q = 2l - p
+        const int l = P.ell[m], nt = P.ynt[m], k0 = P.yk0[m], em = P.em[m];
+        double damp = 0.0;
+        for (int r = 0; r < nt; ++r) {
+          const int pp = k0 + 2 * r, qq = 2 * l - pp;
+          double cpm = 1.0, sqm = 1.0;
+          for (int u = 0; u < pp - 1; ++u) cpm *= ch;
+          for (int u = 0; u < qq - 1; ++u) sqm *= sh;
+          double t = 0.0;
+          if (pp > 0) t -= pp * cpm * (qq > 0 ? sqm * sh : 1.0) * sh;
+          if (qq > 0) t += qq * (pp > 0 ? cpm * ch : 1.0) * ch * sqm;
+          damp += 0.5 * P.ycoef[m][r] * t;
+        }
+        double er = 1.0, ei = 0.0;
+        const int am = em < 0 ? -em : em;
+        for (int u = 0; u < am; ++u) {
+          const double nr = er * cp - ei * sp, ni = er * sp + ei * cp;
+          er = nr;
+          ei = ni;
+        }
+        if (em < 0) ei = -ei;
+        dyr[m] = damp * er;
+        dyi[m] = damp * ei;
+      }
+    }
+  }
+
+  double td = 0.0, tq = 0.0;
+  double gd[kNpar], gq[kNpar];
+#pragma unroll
+  for (int p = 0; p < kNpar; ++p) gd[p] = gq[p] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double* D = P.resp[k];
+    // F(0) = e1.D.e1 - e2.D.e2 - 2 i e1.D.e2 and its ra, dec derivatives
+    const double f0r = quad3(D, e1, e1) - quad3(D, e2, e2), f0i = -2.0 * quad3(D, e1, e2);
+    const double f0r_ra = 2.0 * quad3(D, de1_ra, e1) - 2.0 * quad3(D, de2_ra, e2);
+    const double f0i_ra = -2.0 * (quad3(D, de1_ra, e2) + quad3(D, e1, de2_ra));
+    const double f0r_dec = -2.0 * quad3(D, de2_dec, e2);
+    const double f0i_dec = -2.0 * quad3(D, e1, de2_dec);
+    const double Fr = f0r * c2p - f0i * s2p, Fi = f0r * s2p + f0i * c2p;
+    const double Fr_ra = f0r_ra * c2p - f0i_ra * s2p, Fi_ra = f0r_ra * s2p + f0i_ra * c2p;
+    const double Fr_dec = f0r_dec * c2p - f0i_dec * s2p, Fi_dec = f0r_dec * s2p + f0i_dec * c2p;
+    const double Fr_psi = -2.0 * Fi, Fi_psi = 2.0 * Fr;
+    const double tk = tc - (P.pos[k][0] * s[0] + P.pos[k][1] * s[1] + P.pos[k][2] * s[2]);
+    const double dt_ra = -(P.pos[k][0] * ds_ra[0] + P.pos[k][1] * ds_ra[1]);
+    const double dt_dec = -(P.pos[k][0] * ds_dec[0] + P.pos[k][1] * ds_dec[1] + P.pos[k][2] * ds_dec[2]);
+    const double u = (tk - P.t0[k]) * P.inv_dt;
+    const double jf = floor(u);
+    double w[4], dw[4];
+    lagrange4_d(u - jf, w, dw);
+    // G = sum conj(Y) Q, Gt = sum conj(Y) dQ/dt, Gi = sum conj(dY_iota) Q, Gp = sum conj(dY_phase) Q
+    double Gr = 0, Gi_ = 0, Gtr = 0, Gti = 0, Gir = 0, Gii = 0, Gpr = 0, Gpi = 0;
+    if (isfinite(u)) {
+      const long long j0 = (long long)jf - 1;
+      for (int tap = 0; tap < 4; ++tap) {
+        const long long j = j0 + tap;
+        if (j < 0 || j >= P.n) continue;
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+          if (m < M) {
+            double qr, qi;
+            if (P.q_c128) {
+              const double2 q = __ldg((const double2*)P.Q + ((long long)k * P.n + j) * M + m);
+              qr = q.x;
+              qi = q.y;
+            } else {
+              const float2 q = __ldg((const float2*)P.Q + ((long long)k * P.n + j) * M + m);
+              qr = q.x;
+              qi = q.y;
+            }
+            const double wq = w[tap], dq = dw[tap] * P.inv_dt;
+            const double cr = yr[m] * qr + yi[m] * qi, ci = yr[m] * qi - yi[m] * qr;  // conj(Y) Q
+            Gr = fma(wq, cr, Gr);
+            Gi_ = fma(wq, ci, Gi_);
+            Gtr = fma(dq, cr, Gtr);
+            Gti = fma(dq, ci, Gti);
+            Gir = fma(wq, dyr[m] * qr + dyi[m] * qi, Gir);
+            Gii = fma(wq, dyr[m] * qi - dyi[m] * qr, Gii);
+            const double em = (double)P.em[m];  // dY/d phase = i m Y: conj = -i m conj(Y)
+            Gpr = fma(wq, em * ci, Gpr);
+            Gpi = fma(wq, -em * cr, Gpi);
+          }
+        }
+      }
+    } else {
+      Gr = CUDART_NAN;
+    }
+    // data term and its derivatives: Re(conj(A) B) = Ar Br + Ai Bi
+    const double dre = Fr * Gr + Fi * Gi_;
+    td += dre;
+    const double dt_term = Fr * Gtr + Fi * Gti;
+    gd[0] += Fr_ra * Gr + Fi_ra * Gi_ + dt_term * dt_ra;
+    gd[1] += Fr_dec * Gr + Fi_dec * Gi_ + dt_term * dt_dec;
+    gd[2] += Fr_psi * Gr + Fi_psi * Gi_;
+    gd[3] += Fr * Gir + Fi * Gii;
+    gd[4] += Fr * Gpr + Fi * Gpi;
+    gd[6] += dt_term;
+    // quadratic forms: rows (U Y)_m and (V Y)_m formed on the fly
+    const double2* Uk = sUV + (size_t)k * M * M;
+    const double2* Vk = sUV + (size_t)K * M * M + (size_t)k * M * M;
+    double a = 0, da_i = 0, da_p = 0, br = 0, bi = 0, dbi_r = 0, dbi_i = 0, dbp_r = 0, dbp_i = 0;
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      if (m < M) {
+        double uyr = 0, uyi = 0, vyr = 0, vyi = 0;
+#pragma unroll
+        for (int n2 = 0; n2 < MM; ++n2) {
+          if (n2 < M) {
+            const double2 uu = Uk[m * M + n2], vv = Vk[m * M + n2];
+            uyr += uu.x * yr[n2] - uu.y * yi[n2];
+            uyi += uu.x * yi[n2] + uu.y * yr[n2];
+            vyr += vv.x * yr[n2] - vv.y * yi[n2];
+            vyi += vv.x * yi[n2] + vv.y * yr[n2];
+          }
+        }
+        const double em = (double)P.em[m];
+        const double pyr = -em * yi[m], pyi = em * yr[m];  // dY/d phase
+        a += yr[m] * uyr + yi[m] * uyi;                    // Re(conj(Y) UY)
+        da_i += 2.0 * (dyr[m] * uyr + dyi[m] * uyi);
+        da_p += 2.0 * (pyr * uyr + pyi * uyi);
+        br += yr[m] * vyr - yi[m] * vyi;                   // Y (VY)
+        bi += yr[m] * vyi + yi[m] * vyr;
+        dbi_r += 2.0 * (dyr[m] * vyr - dyi[m] * vyi);
+        dbi_i += 2.0 * (dyr[m] * vyi + dyi[m] * vyr);
+        dbp_r += 2.0 * (pyr * vyr - pyi * vyi);
+        dbp_i += 2.0 * (pyr * vyi + pyi * vyr);
+      }
+    }
+    const double F2 = Fr * Fr + Fi * Fi, F2r = Fr * Fr - Fi * Fi, F2i = 2.0 * Fr * Fi;
+    tq += F2 * a + (F2r * br - F2i * bi);
+    // d(|F|^2) = 2 Re(conj F dF);  d(F^2 b) = 2 F dF b
+    auto quad_dF = [&](double dFr, double dFi) {
+      const double dF2 = 2.0 * (Fr * dFr + Fi * dFi);
+      const double pr = 2.0 * (Fr * dFr - Fi * dFi), pi = 2.0 * (Fr * dFi + Fi * dFr);  // 2 F dF
+      return dF2 * a + (pr * br - pi * bi);
+    };
+    gq[0] += quad_dF(Fr_ra, Fi_ra);
+    gq[1] += quad_dF(Fr_dec, Fi_dec);
+    gq[2] += quad_dF(Fr_psi, Fi_psi);
+    gq[3] += F2 * da_i + (F2r * dbi_r - F2i * dbi_i);
+    gq[4] += F2 * da_p + (F2r * dbp_r - F2i * dbp_i);
+  }
+  const double q4 = 0.25 * x * x;
+#pragma unroll
+  for (int p = 0; p < kNpar; ++p) g[p] = x * gd[p] - q4 * gq[p];
+  g[5] = -x * td + 2.0 * q4 * tq;
+  return x * td - q4 * tq;
+}
+
+template <int MM>
+__global__ void __launch_bounds__(256) grad_fp64_kernel(const PointParams* __restrict__ gP,
+                                                        DrawsParams dp, double* __restrict__ lnl_out,
+                                                        double* __restrict__ grad_out) {
+  __shared__ PointParams P;
+  extern __shared__ double2 sUV[];
+  stage_point(P, gP);
+  __syncthreads();
+  {
+    const int nuv = 2 * P.K * P.M * P.M;
+    for (int t = threadIdx.x; t < nuv; t += blockDim.x) sUV[t] = __ldg(P.U + t);
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
+    double g[kNpar];
+    const double v = lnl_fp64_grad_draw<MM>(P, sUV, dp, i, g);
+    if (lnl_out) lnl_out[i] = v;
+#pragma unroll
+    for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = g[p];
+  }
+}
+
+template <int MM>
+cudaError_t launch_grad_fp64_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                double* lnl_out, double* grad_out, cudaStream_t st) {
+  const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
+  cudaFuncSetAttribute(grad_fp64_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  const int blocks = grid_for(grad_fp64_kernel<MM>, 256, smem);
+  grad_fp64_kernel<MM><<<blocks, 256, smem, st>>>(dP, dp, lnl_out, grad_out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_grad_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                             double* lnl_out, double* grad_out, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_grad_fp64_mm<2>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 4) return launch_grad_fp64_mm<4>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 6) return launch_grad_fp64_mm<6>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 8) return launch_grad_fp64_mm<8>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 10) return launch_grad_fp64_mm<10>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 12) return launch_grad_fp64_mm<12>(hp, dP, dp, lnl_out, grad_out, st);
+  return launch_grad_fp64_mm<16>(hp, dP, dp, lnl_out, grad_out, st);
+}
+
+namespace {
 }  // namespace
 
 cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,

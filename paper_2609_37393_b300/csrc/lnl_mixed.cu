@@ -27,6 +27,21 @@
 #include "common.cuh"
 #include "kernels.h"
 
+// Tuning knobs (compile-time): the minimum resident blocks per SM given to
+// __launch_bounds__, and whether the large double-float helpers are real
+// calls (smaller code, fewer instruction-cache misses) or inlined.
+#ifndef RIFT_MIXED_MIN_BLOCKS
+#define RIFT_MIXED_MIN_BLOCKS 4
+#endif
+#ifndef RIFT_MIXED_NOINLINE
+#define RIFT_MIXED_NOINLINE 0
+#endif
+#if RIFT_MIXED_NOINLINE
+#define RIFT_HELPER __device__ __noinline__
+#else
+#define RIFT_HELPER __device__ __forceinline__
+#endif
+
 namespace rift {
 
 __device__ float4 g_anchor[2 * kAnchorHalf + 1];  // (sin hi, sin lo, cos hi, cos lo) of j 2^-7
@@ -66,7 +81,7 @@ namespace {
 // sin and cos of a double-float angle to ~1e-15 absolute: reduce by 2 pi (pair
 // constant), take the nearest anchor a_j = j 2^-7, and add the residual
 // d (|d| <= 2^-8) through sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24.
-__device__ __forceinline__ void sincos_df(df a, df& s_out, df& c_out) {
+RIFT_HELPER void sincos_df(df a, df& s_out, df& c_out) {
   const float kTwoPiHi = 6.28318548202514648f;
   const float kTwoPiLo = -1.7484555314695172e-07f;
   float k = rintf(a.hi * 0.159154943091895336f);
@@ -96,7 +111,7 @@ __device__ __forceinline__ void sincos_df(df a, df& s_out, df& c_out) {
 
 // e^a for a double-float a: a = k ln2 + j/128 + d, |d| <= 2^-8, e^d by its
 // Taylor series to d^4, anchors e^(j/128) from the table.
-__device__ __forceinline__ df exp_df(df a) {
+RIFT_HELPER df exp_df(df a) {
   const float kLn2Hi = 0.693147182464599609f;
   const float kLn2Lo = -1.904654323148236e-09f;
   float k = rintf(a.hi * 1.44269504088896341f);
@@ -123,23 +138,21 @@ __device__ __forceinline__ df df_pow(df b, int n) {
   return r;
 }
 
-// -2Y_lm of mode i in double-float from c = cos(iota/2), s = sin(iota/2).
-__device__ __forceinline__ void sylm_df(const PointParams& P, int i, df c, df s, float phi,
-                                        df& yr, df& yi) {
-  const int l = P.ell[i], m = P.em[i], nt = P.ynt[i], k0 = P.yk0[i];
+// |-2Y_lm| part of mode i in double-float from c = cos(iota/2), s = sin(iota/2):
+// sum_r a_r c^(k0+2r) s^(2l-k0-2r) (the Wigner-d polynomial of the point).
+RIFT_HELPER df sylm_amp_df(const PointParams& P, int i, df c, df s) {
+  const int l = P.ell[i], nt = P.ynt[i], k0 = P.yk0[i];
   df pre = df_mul(df_pow(c, k0), df_pow(s, 2 * l - k0 - 2 * (nt - 1)));
-  const df X = df_mul(c, c), Ys = df_mul(s, s);
   df poly = df{P.ycoef_hi[i][nt - 1], P.ycoef_lo[i][nt - 1]};
-  df yp = df{1.f, 0.f};
-  for (int r = nt - 2; r >= 0; --r) {
-    yp = df_mul(yp, Ys);
-    poly = df_add(df_mul(poly, X), df_mul(df{P.ycoef_hi[i][r], P.ycoef_lo[i][r]}, yp));
+  if (nt > 1) {
+    const df X = df_mul(c, c), Ys = df_mul(s, s);
+    df yp = df{1.f, 0.f};
+    for (int r = nt - 2; r >= 0; --r) {
+      yp = df_mul(yp, Ys);
+      poly = df_add(df_mul(poly, X), df_mul(df{P.ycoef_hi[i][r], P.ycoef_lo[i][r]}, yp));
+    }
   }
-  const df amp = df_mul(pre, poly);
-  df sm, cm;
-  sincos_df(two_prod((float)m, phi), sm, cm);
-  yr = df_mul(amp, cm);
-  yi = df_mul(amp, sm);
+  return df_mul(pre, poly);
 }
 
 // Complex product of pairs.
@@ -148,25 +161,111 @@ __device__ __forceinline__ void cmul_df(df ar, df ai, df br, df bi, df& cr, df& 
   ci = df_add(df_mul(ar, bi), df_mul(ai, br));
 }
 
-// Antenna factor of detector k from the double-float basis:
-// F(0) = e1.D.e1 - e2.D.e2 - 2 i e1.D.e2, then F = F(0) e^{2 i psi}.
-__device__ __forceinline__ void antenna_df(const PointParams& P, int k, const df e1[3],
-                                           const df e2[3], df c2p, df s2p, df& Fr, df& Fi) {
-  df Dm[6];
+// Sky functions shared by all detectors: with e1 = (-sl, cl, 0) and
+// e2 = (-sd cl, -sd sl, cd) (sl, cl = sin, cos of ra - gmst; sd, cd of dec),
+//   F_+(0) = e1.D.e1 - e2.D.e2 = Dxx b0 + Dyy b1 + Dxy b2 + Dxz b3 + Dyz b4 + Dzz b5,
+//   F_x(0) = 2 e1.D.e2 = (Dxx - Dyy) g0 + Dxy g1 + Dxz g2 + Dyz g3,
+// b = (sl^2 - sd^2 cl^2, cl^2 - sd^2 sl^2, -2 sl cl (1 + sd^2), 2 sd cd cl,
+//      2 sd cd sl, -cd^2),  g = (2 sd sl cl, 2 sd (sl^2 - cl^2), -2 sl cd, 2 cl cd).
+struct AntennaBasis {
+  df b[6], g[4];
+};
+
+RIFT_HELPER void antenna_basis(df sl, df cl, df sd, df cd, AntennaBasis& B) {
+  const df sl2 = df_mul(sl, sl), cl2 = df_mul(cl, cl), slcl = df_mul(sl, cl);
+  const df sd2 = df_mul(sd, sd), sdcd = df_mul(sd, cd), cd2 = df_mul(cd, cd);
+  B.b[0] = df_sub(sl2, df_mul(sd2, cl2));
+  B.b[1] = df_sub(cl2, df_mul(sd2, sl2));
+  const df t = df_mul(slcl, df_add_f(sd2, 1.f));
+  B.b[2] = df{-2.f * t.hi, -2.f * t.lo};
+  const df u = df_mul(sdcd, cl), v = df_mul(sdcd, sl);
+  B.b[3] = df{2.f * u.hi, 2.f * u.lo};
+  B.b[4] = df{2.f * v.hi, 2.f * v.lo};
+  B.b[5] = df_neg(cd2);
+  const df w = df_mul(sd, slcl);
+  B.g[0] = df{2.f * w.hi, 2.f * w.lo};
+  const df z = df_mul(sd, df_sub(sl2, cl2));
+  B.g[1] = df{2.f * z.hi, 2.f * z.lo};
+  const df a = df_mul(sl, cd), c = df_mul(cl, cd);
+  B.g[2] = df{-2.f * a.hi, -2.f * a.lo};
+  B.g[3] = df{2.f * c.hi, 2.f * c.lo};
+}
+
+// acc += a * b for pairs, the hi*hi product exact.
+__device__ __forceinline__ void dacc_fma_dd(dacc& acc, df a, df b) {
+  const df p = two_prod(a.hi, b.hi);
+  const df t = two_sum(acc.s, p.hi);
+  acc.s = t.hi;
+  float c = __fadd_rn(acc.c, __fadd_rn(t.lo, p.lo));
+  c = fmaf(a.hi, b.lo, c);
+  acc.c = fmaf(a.lo, b.hi, c);
+}
+
+// x F_k = x e^{2 i psi} (F_+(0) - i F_x(0)) of detector k, with xe = x e^{2 i psi}.
+RIFT_HELPER void antenna_df(const PointParams& P, int k, const AntennaBasis& B, df xer, df xei,
+                            df& xFr, df& xFi) {
+  dacc fp = dacc_zero(), fx = dacc_zero();
 #pragma unroll
-  for (int c = 0; c < 6; ++c) Dm[c] = df{P.resp_hi[k][c], P.resp_lo[k][c]};
-  // D.e1 (e1.z = 0) and D.e2
-  const df d1x = df_add(df_mul(Dm[0], e1[0]), df_mul(Dm[1], e1[1]));
-  const df d1y = df_add(df_mul(Dm[1], e1[0]), df_mul(Dm[3], e1[1]));
-  const df d2x = df_add(df_add(df_mul(Dm[0], e2[0]), df_mul(Dm[1], e2[1])), df_mul(Dm[2], e2[2]));
-  const df d2y = df_add(df_add(df_mul(Dm[1], e2[0]), df_mul(Dm[3], e2[1])), df_mul(Dm[4], e2[2]));
-  const df d2z = df_add(df_add(df_mul(Dm[2], e2[0]), df_mul(Dm[4], e2[1])), df_mul(Dm[5], e2[2]));
-  const df a = df_add(df_mul(e1[0], d1x), df_mul(e1[1], d1y));
-  const df b = df_add(df_add(df_mul(e2[0], d2x), df_mul(e2[1], d2y)), df_mul(e2[2], d2z));
-  const df cc = df_add(df_mul(e1[0], d2x), df_mul(e1[1], d2y));
-  const df f0r = df_sub(a, b);
-  const df f0i = df{-2.f * cc.hi, -2.f * cc.lo};
-  cmul_df(f0r, f0i, c2p, s2p, Fr, Fi);
+  for (int i = 0; i < 6; ++i) dacc_fma_dd(fp, df{P.acoef_hi[k][i], P.acoef_lo[k][i]}, B.b[i]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dacc_fma_dd(fx, df{P.acoef_hi[k][6 + i], P.acoef_lo[k][6 + i]}, B.g[i]);
+  const df f0r = dacc_result(fp), f0x = dacc_result(fx);
+  // (f0r - i f0x)(xer + i xei)
+  xFr = df_add(df_mul(f0r, xer), df_mul(f0x, xei));
+  xFi = df_sub(df_mul(f0r, xei), df_mul(f0x, xer));
+}
+
+// FP32 amplitude of mode i and its derivative with respect to iota (used by
+// the adjoint, whose terms multiply the small residual and need only FP32):
+// d/d iota [c^p s^q] = (-p c^(p-1) s^(q+1) + q c^(p+1) s^(q-1)) / 2.
+__device__ __forceinline__ void sylm_amp_grad_f(const PointParams& P, int i, float c, float s,
+                                                float& amp, float& damp) {
+  const int l = P.ell[i], nt = P.ynt[i], k0 = P.yk0[i];
+  amp = 0.f;
+  damp = 0.f;
+  for (int r = 0; r < nt; ++r) {
+    const int p = k0 + 2 * r, q = 2 * l - p;
+    float cp = 1.f, sq = 1.f;
+    for (int u = 0; u < p - 1; ++u) cp *= c;  // c^(p-1)
+    for (int u = 0; u < q - 1; ++u) sq *= s;  // s^(q-1)
+    const float a = P.ycoef_hi[i][r];
+    const float cpf = (p > 0) ? cp * c : 1.f, sqf = (q > 0) ? sq * s : 1.f;
+    amp = fmaf(a, cpf * sqf, amp);
+    float d = 0.f;
+    if (p > 0) d -= p * cp * sqf * s;
+    if (q > 0) d += q * cpf * c * sq;
+    damp = fmaf(0.5f * a, d, damp);
+  }
+}
+
+// d(beta_i)/d(ra), d(beta_i)/d(dec) and the same for gamma (FP32; see AntennaBasis).
+struct AntennaBasisGrad {
+  float ba[6], bd[6], ga[4], gd[4];
+};
+
+__device__ __forceinline__ void antenna_basis_grad(float sl, float cl, float sd, float cd,
+                                                   AntennaBasisGrad& G) {
+  const float sd2 = sd * sd, slcl = sl * cl, c2 = cl * cl - sl * sl, dd = cd * cd - sd * sd;
+  G.ba[0] = 2.f * slcl * (1.f + sd2);
+  G.bd[0] = -2.f * sd * cd * cl * cl;
+  G.ba[1] = -2.f * slcl * (1.f + sd2);
+  G.bd[1] = -2.f * sd * cd * sl * sl;
+  G.ba[2] = -2.f * c2 * (1.f + sd2);
+  G.bd[2] = -4.f * slcl * sd * cd;
+  G.ba[3] = -2.f * sd * cd * sl;
+  G.bd[3] = 2.f * dd * cl;
+  G.ba[4] = 2.f * sd * cd * cl;
+  G.bd[4] = 2.f * dd * sl;
+  G.ba[5] = 0.f;
+  G.bd[5] = 2.f * cd * sd;
+  G.ga[0] = 2.f * sd * c2;
+  G.gd[0] = 2.f * cd * slcl;
+  G.ga[1] = 8.f * sd * slcl;
+  G.gd[1] = -2.f * cd * c2;
+  G.ga[2] = -2.f * cl * cd;
+  G.gd[2] = 2.f * sl * sd;
+  G.ga[3] = -2.f * sl * cd;
+  G.gd[3] = -2.f * cl * sd;
 }
 
 // The error-free split of a mode value y (|y| < 2): y1 = y rounded to a
@@ -177,16 +276,25 @@ __device__ __forceinline__ void split_y(float y, float& y1, float& y2) {
   y2 = __fsub_rn(y, y1);
 }
 
-template <int MM, int RR>
 struct MixedDraw {
   df lnl;
   int oob;
+  double grad[kNpar];
 };
 
-template <int MM, int RR>
-__device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P,
-                                                            const float4* sA, const float* sg,
-                                                            const DrawsParams& dp, long long i) {
+// One draw: lnL, and with GRAD its gradient in (ra, dec, psi, incl, phase, lnD, t).
+//
+// Adjoint (Sec. II.B): with r_k = e_k - w_k and rho_k = r_k + gm1 w_k,
+//   d lnL = sum_k [ (P_k'(f)/dt - r_k . edot_k) dt_k + rho_k . dw_k ],
+// the first bracket being w_k . edot_k (computed as the exact polynomial
+// slope minus a small residual term); dw_k follows from w_k = Re(xF_k) a1 +
+// Im(xF_k) a2: rho_k . dw_k = d Re(xF_k) rho_k.a1 + d Im(xF_k) rho_k.a2 for the
+// sky angles, psi and lnD, and (A^T G1 + J^T A^T G2) . dy with
+// G1 = sum_k Re(xF_k) rho_k, G2 = sum_k Im(xF_k) rho_k for iota and phase.
+template <int MM, int RR, bool GRAD>
+__device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const float4* sA,
+                                                    const float* sg, const DrawsParams& dp,
+                                                    long long i) {
   const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
   const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
   const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
@@ -206,16 +314,31 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
   sincos_df(lam, sl, cl);
   sincos_df(df{dec, 0.f}, sd, cd);
   const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
-  const df e1[3] = {df_neg(sl), cl, df{0.f, 0.f}};
-  const df e2[3] = {df_neg(df_mul(sd, cl)), df_neg(df_mul(sd, sl)), cd};
+  AntennaBasis AB;
+  antenna_basis(sl, cl, sd, cd, AB);
   df s2p, c2p;
   sincos_df(df{2.f * psi, 0.f}, s2p, c2p);
+  const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
   df sh, ch;
   sincos_df(df{0.5f * incl, 0.f}, sh, ch);
 
   dacc T = dacc_zero();
   int oob = 0;
   bool bad = false;
+  // gradient accumulators: time-driven parts of (ra, dec, t) as pairs, the rest in FP32
+  dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
+  float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_incl = 0.f, g_phase = 0.f, g_lnd = 0.f;
+  AntennaBasisGrad ABG;
+  float dsa[3] = {0.f, 0.f, 0.f}, dsd[3] = {0.f, 0.f, 0.f};
+  if (GRAD) {
+    antenna_basis_grad(sl.hi, cl.hi, sd.hi, cd.hi, ABG);
+    // ds/d ra = (-cd sl, cd cl, 0), ds/d dec = (-sd cl, -sd sl, cd)
+    dsa[0] = -cd.hi * sl.hi;
+    dsa[1] = cd.hi * cl.hi;
+    dsd[0] = -sd.hi * cl.hi;
+    dsd[1] = -sd.hi * sl.hi;
+    dsd[2] = cd.hi;
+  }
   for (int c = 0; c < P.ncls; ++c) {
     // a1 = A y, a2 = A J y by the split product: the products of the 10-bit
     // head of A with the 9-bit head of y are exact and their sum stays below
@@ -224,9 +347,18 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
 #pragma unroll
     for (int r = 0; r < RR; ++r) ex1[r] = ex2[r] = co1[r] = co2[r] = 0.f;
     const float4* Ac = sA + (size_t)c * R * D;
+    int prev_am = -1;
+    df cm = df{1.f, 0.f}, sm = df{0.f, 0.f};
     for (int a = 0; a < M; ++a) {
-      df yr, yi;
-      sylm_df(P, a, ch, sh, phi, yr, yi);
+      // e^{i m phi}: reused across the +-m members of a mode pair
+      const int m = P.em[a], am = m < 0 ? -m : m;
+      if (am != prev_am) {
+        sincos_df(two_prod((float)am, phi), sm, cm);
+        prev_am = am;
+      }
+      const df amp = sylm_amp_df(P, a, ch, sh);
+      const df yr = df_mul(amp, cm);
+      const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
       float yr1, yr2, yi1, yi2;
       split_y(yr.hi, yr1, yr2);
       split_y(yi.hi, yi1, yi2);
@@ -267,11 +399,16 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
       a2[r] = two_sum(ex2[r], co2[r]);
     }
     const float* gc = sg + c * R;
+    df delay = df{0.f, 0.f};
+    float G1[GRAD ? RR : 1], G2[GRAD ? RR : 1];
+    if (GRAD) {
+#pragma unroll
+      for (int r = 0; r < RR; ++r) G1[r] = G2[r] = 0.f;
+    }
     for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
       const int k = P.det_order[q];
-      df Fr, Fi;
-      antenna_df(P, k, e1, e2, c2p, s2p, Fr, Fi);
-      const df xFr = df_mul(x, Fr), xFi = df_mul(x, Fi);
+      df xFr, xFi;
+      antenna_df(P, k, AB, xer, xei, xFr, xFi);
       df w[RR];
 #pragma unroll
       for (int r = 0; r < RR; ++r) {
@@ -285,10 +422,12 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
         lo = fmaf(xFi.lo, a2[r].hi, lo);
         w[r] = fast_two_sum(s.hi, lo);
       }
-      // arrival time and table position
-      df delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
-      delay = df_add(delay, df_mul(df{P.pos_hi[k][1], P.pos_lo[k][1]}, s1));
-      delay = df_add(delay, df_mul(df{P.pos_hi[k][2], P.pos_lo[k][2]}, s2));
+      // arrival time (shared by co-located detectors) and table position
+      if (!P.same_pos_prev[q]) {
+        delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
+        delay = df_add(delay, df_mul(df{P.pos_hi[k][1], P.pos_lo[k][1]}, s1));
+        delay = df_add(delay, df_mul(df{P.pos_hi[k][2], P.pos_lo[k][2]}, s2));
+      }
       const df rel = df_add(df_sub(tc, delay), df{-P.t0_hi[k], -P.t0_lo[k]});
       const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
       if (!isfinite(u.hi)) {
@@ -299,18 +438,31 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
       float jf = floorf(u.hi);
       if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
       const float f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
-      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the table)
-      df half_e2 = df{0.f, 0.f};
+      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the
+      // table) and, for the adjoint, its slope in f (Horner on both)
+      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
       if (jf >= -2.f && jf <= (float)n) {
         const float2* pc = P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
         float2 cf = __ldg(pc + kPolyDeg);
         df acc = df{cf.x, cf.y};
+        df dacc_p = df{0.f, 0.f};
 #pragma unroll
         for (int p = kPolyDeg - 1; p >= 0; --p) {
+          if (GRAD) {  // slope: d = d f + acc
+            df pr = two_prod(dacc_p.hi, f);
+            pr.lo = fmaf(dacc_p.lo, f, pr.lo);
+            const df sm3 = two_sum(pr.hi, acc.hi);
+            dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
+          }
+          // acc = acc f + c_p: exact product and sum of the high parts
           cf = __ldg(pc + p);
-          acc = df_add(df_mul_f(acc, f), df{cf.x, cf.y});
+          df pr = two_prod(acc.hi, f);
+          pr.lo = fmaf(acc.lo, f, pr.lo);
+          const df sm2 = two_sum(pr.hi, cf.x);
+          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf.y));
         }
         half_e2 = acc;
+        dhalf = dacc_p;
       }
       // residual e - w = sum_i wt_i (e_i - w) - sigma (e_j - w) with FP32
       // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
@@ -323,9 +475,21 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
       wt[3] = (fa * f * fc) * (1.f / 6.f);
       const df ws = df_add(two_sum(wt[0], wt[1]), two_sum(wt[2], wt[3]));
       const float sigma = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
-      float res[RR];
+      // derivative weights (adjoint only): d wt_i / df
+      float wtd[4] = {0.f, 0.f, 0.f, 0.f};
+      if (GRAD) {
+        wtd[0] = -(fc * fd + f * fd + f * fc) * (1.f / 6.f);
+        wtd[1] = (fc * fd + fa * fd + fa * fc) * 0.5f;
+        wtd[2] = -(f * fd + fa * fd + fa * f) * 0.5f;
+        wtd[3] = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
+      }
+      float res[RR], edr[GRAD ? RR : 1];
 #pragma unroll
       for (int r = 0; r < RR; ++r) res[r] = 0.f;
+      if (GRAD) {
+#pragma unroll
+        for (int r = 0; r < RR; ++r) edr[r] = 0.f;
+      }
       const float2* Ek = P.ehat + (size_t)k * n * R;
 #pragma unroll
       for (int tap = 0; tap < 4; ++tap) {
@@ -334,12 +498,23 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
         if (!valid) ++oob;
         const float2* row = Ek + (size_t)(valid ? (int)jj : 0) * R;
 #pragma unroll
-        for (int r = 0; r < RR; ++r) {
+        for (int r = 0; r < RR; r += 2) {
           if (r < R) {
-            float2 e = valid ? __ldg(row + r) : make_float2(0.f, 0.f);
-            const float dlt = __fadd_rn(__fsub_rn(e.x, w[r].hi), __fsub_rn(e.y, w[r].lo));
-            res[r] = fmaf(wt[tap], dlt, res[r]);
-            if (tap == 1) res[r] = fmaf(-sigma, dlt, res[r]);  // sigma is ~1 ulp of wt: apart
+            // rows hold R pairs, R even: two entries per 16-byte load
+            float4 e2 = valid ? __ldg(reinterpret_cast<const float4*>(row + r))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float d0 = __fadd_rn(__fsub_rn(e2.x, w[r].hi), __fsub_rn(e2.y, w[r].lo));
+            const float d1 = __fadd_rn(__fsub_rn(e2.z, w[r + 1].hi), __fsub_rn(e2.w, w[r + 1].lo));
+            res[r] = fmaf(wt[tap], d0, res[r]);
+            res[r + 1] = fmaf(wt[tap], d1, res[r + 1]);
+            if (tap == 1) {  // sigma is ~1 ulp of wt: applied apart
+              res[r] = fmaf(-sigma, d0, res[r]);
+              res[r + 1] = fmaf(-sigma, d1, res[r + 1]);
+            }
+            if (GRAD) {  // dt edot = sum_i wtd_i (e_i - w)  (the wtd sum to zero)
+              edr[r] = fmaf(wtd[tap], d0, edr[r]);
+              edr[r + 1] = fmaf(wtd[tap], d1, edr[r + 1]);
+            }
           }
         }
       }
@@ -354,20 +529,106 @@ __device__ __forceinline__ MixedDraw<MM, RR> lnl_mixed_draw(const PointParams& P
       dacc_add(T, half_e2);
       dacc_add(T, df{-0.5f * q2, 0.f});
       if (P.has_null[c]) dacc_add(T, df{0.5f * nul, 0.f});
+      if (GRAD) {
+        // time: d lnL_k / d t_k = (P'(f) - r . edot dt) / dt
+        float red = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          if (r < R) {
+            red = fmaf(res[r], edr[r], red);
+            const float rho = fmaf(gc[r], w[r].hi, res[r]);
+            g1 = fmaf(rho, a1[r].hi, g1);
+            g2 = fmaf(rho, a2[r].hi, g2);
+            G1[r] = fmaf(xFr.hi, rho, G1[r]);
+            G2[r] = fmaf(xFi.hi, rho, G2[r]);
+          }
+        }
+        const df dtk = df_mul(df_add_f(dhalf, -red), df{P.inv_dt_hi, P.inv_dt_lo});
+        const float dka = -(P.pos_hi[k][0] * dsa[0] + P.pos_hi[k][1] * dsa[1]);
+        const float dkd = -(P.pos_hi[k][0] * dsd[0] + P.pos_hi[k][1] * dsd[1] + P.pos_hi[k][2] * dsd[2]);
+        dacc_add(gt_t, dtk);
+        dacc_add(gt_ra, df_mul_f(dtk, dka));
+        dacc_add(gt_dec, df_mul_f(dtk, dkd));
+        // antenna: d(xF) = x e^{2 i psi} (dF+ - i dFx), d/d psi (xF) = 2 i xF
+        float dfpa = 0.f, dfpd = 0.f, dfxa = 0.f, dfxd = 0.f;
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+          dfpa = fmaf(P.acoef_hi[k][u], ABG.ba[u], dfpa);
+          dfpd = fmaf(P.acoef_hi[k][u], ABG.bd[u], dfpd);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dfxa = fmaf(P.acoef_hi[k][6 + u], ABG.ga[u], dfxa);
+          dfxd = fmaf(P.acoef_hi[k][6 + u], ABG.gd[u], dfxd);
+        }
+        // (dfp - i dfx)(xer + i xei)
+        const float dxra = dfpa * xer.hi + dfxa * xei.hi, dxia = dfpa * xei.hi - dfxa * xer.hi;
+        const float dxrd = dfpd * xer.hi + dfxd * xei.hi, dxid = dfpd * xei.hi - dfxd * xer.hi;
+        g_ra = fmaf(dxra, g1, fmaf(dxia, g2, g_ra));
+        g_dec = fmaf(dxrd, g1, fmaf(dxid, g2, g_dec));
+        g_psi = fmaf(-2.f * xFi.hi, g1, fmaf(2.f * xFr.hi, g2, g_psi));
+        g_lnd = fmaf(-xFr.hi, g1, fmaf(-xFi.hi, g2, g_lnd));
+      }
+    }
+    if (GRAD) {
+      // iota and phase through the modes: H = A^T G1 + J^T A^T G2 (FP32)
+      const float4* Ac2 = sA + (size_t)c * R * D;
+      const float ci = ch.hi, si = sh.hi;
+      float cmf = 1.f, smf = 0.f;
+      int prev = -1;
+      for (int a = 0; a < M; ++a) {
+        float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          if (r < R) {
+            const float4 at = Ac2[r * D + a], ab = Ac2[r * D + M + a];
+            const float ath = at.x + at.y, abh = ab.x + ab.y;
+            h1t = fmaf(G1[r], ath, h1t);
+            h1b = fmaf(G1[r], abh, h1b);
+            h2t = fmaf(G2[r], ath, h2t);
+            h2b = fmaf(G2[r], abh, h2b);
+          }
+        }
+        const float Hre = h1t + h2b, Him = h1b - h2t;
+        const int m = P.em[a], am = m < 0 ? -m : m;
+        if (am != prev) {
+          sincosf((float)am * phi, &smf, &cmf);
+          prev = am;
+        }
+        const float sgn = m < 0 ? -1.f : 1.f;
+        float amp, damp;
+        sylm_amp_grad_f(P, a, ci, si, amp, damp);
+        const float yre = amp * cmf, yim = sgn * amp * smf;
+        g_phase = fmaf((float)m, fmaf(-yim, Hre, yre * Him), g_phase);
+        g_incl = fmaf(damp * cmf, Hre, fmaf(sgn * damp * smf, Him, g_incl));
+      }
     }
   }
-  MixedDraw<MM, RR> o;
+  MixedDraw o;
   o.lnl = dacc_result(T);
   if (bad) o.lnl = df{CUDART_NAN_F, 0.f};
   o.oob = oob;
+  if (GRAD) {
+    const df a = dacc_result(gt_ra), b = dacc_result(gt_dec), t = dacc_result(gt_t);
+    o.grad[0] = (double)a.hi + (double)a.lo + (double)g_ra;
+    o.grad[1] = (double)b.hi + (double)b.lo + (double)g_dec;
+    o.grad[2] = g_psi;
+    o.grad[3] = g_incl;
+    o.grad[4] = g_phase;
+    o.grad[5] = g_lnd;
+    o.grad[6] = (double)t.hi + (double)t.lo;
+    if (bad)
+      for (int p = 0; p < kNpar; ++p) o.grad[p] = CUDART_NAN;
+  }
   return o;
 }
 
-template <int MM, int RR, bool LSE>
-__global__ void __launch_bounds__(128) lnl_mixed_kernel(const PointParams* __restrict__ gP,
+template <int MM, int RR, bool LSE, bool GRAD = false>
+__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(const PointParams* __restrict__ gP,
                                                         DrawsParams dp, double* __restrict__ lnl_out,
                                                         LseState* __restrict__ partials,
-                                                        unsigned long long* __restrict__ oob_count) {
+                                                        unsigned long long* __restrict__ oob_count,
+                                                        double* __restrict__ grad_out = nullptr) {
   __shared__ PointParams P;
   extern __shared__ float4 smem4[];
   stage_point(P, gP);
@@ -396,9 +657,13 @@ __global__ void __launch_bounds__(128) lnl_mixed_kernel(const PointParams* __res
   int oob = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
-    MixedDraw<MM, RR> o = lnl_mixed_draw<MM, RR>(P, sA, sg, dp, i);
+    MixedDraw o = lnl_mixed_draw<MM, RR, GRAD>(P, sA, sg, dp, i);
     oob += o.oob;
-    if (!LSE) {
+    if (GRAD) {
+      if (lnl_out) lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
+#pragma unroll
+      for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = o.grad[p];
+    } else if (!LSE) {
       lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
     } else {
       float lw = 0.f;
@@ -442,7 +707,39 @@ cudaError_t launch_mixed_mm(const PointParams& hp, const PointParams* dP, const 
   return launch_mixed_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
 }
 
+template <int MM, int RR>
+cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                 double* lnl_out, double* grad_out, cudaStream_t st) {
+  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
+                      (size_t)hp.ncls * hp.R * sizeof(float);
+  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, false, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const int blocks = grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem);
+  lnl_mixed_kernel<MM, RR, false, true><<<blocks, 128, smem, st>>>(dP, dp, lnl_out, nullptr, nullptr,
+                                                                   grad_out);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_mixed_grad_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                 double* lnl_out, double* grad_out, cudaStream_t st) {
+  if (hp.R <= MM) return launch_mixed_grad_mr<MM, MM>(hp, dP, dp, lnl_out, grad_out, st);
+  return launch_mixed_grad_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, grad_out, st);
+}
+
 }  // namespace
+
+cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                              double* lnl_out, double* grad_out, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_mixed_grad_mm<2>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 4) return launch_mixed_grad_mm<4>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 6) return launch_mixed_grad_mm<6>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 8) return launch_mixed_grad_mm<8>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 10) return launch_mixed_grad_mm<10>(hp, dP, dp, lnl_out, grad_out, st);
+  if (M <= 12) return launch_mixed_grad_mm<12>(hp, dP, dp, lnl_out, grad_out, st);
+  return launch_mixed_grad_mm<16>(hp, dP, dp, lnl_out, grad_out, st);
+}
 
 cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                              double* lnl_out, LseState* partials, unsigned long long* oob,

@@ -387,8 +387,12 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
   }
 
   split_df(std::log(d->d_ref), &P.ln_dref_hi, &P.ln_dref_lo);
-  for (int k = 0; k < K; ++k)
+  for (int k = 0; k < K; ++k) {
     for (int c = 0; c < 6; ++c) split_df(P.resp[k][c], &P.resp_hi[k][c], &P.resp_lo[k][c]);
+    const double* D = P.resp[k];  // xx, xy, xz, yy, yz, zz
+    const double coef[10] = {D[0], D[3], D[1], D[2], D[4], D[5], D[0] - D[3], D[1], D[2], D[4]};
+    for (int c = 0; c < 10; ++c) split_df(coef[c], &P.acoef_hi[k][c], &P.acoef_lo[k][c]);
+  }
   for (int i = 0; i < M; ++i)
     for (int r = 0; r < P.ynt[i]; ++r) split_df(P.ycoef[i][r], &P.ycoef_hi[i][r], &P.ycoef_lo[i][r]);
 
@@ -416,6 +420,11 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
         if (P.cls_of[k] == c) P.det_order[pos++] = k;
     }
     P.cls_begin[ncls] = pos;
+    for (int q = 0; q < K; ++q) {
+      const int k = P.det_order[q], kp = q ? P.det_order[q - 1] : -1;
+      P.same_pos_prev[q] = q > 0 && P.pos[k][0] == P.pos[kp][0] && P.pos[k][1] == P.pos[kp][1] &&
+                           P.pos[k][2] == P.pos[kp][2];
+    }
   }
 
   // ---- eigen-decomposition of each class's real quadratic form (descending).
@@ -542,6 +551,9 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
       }
       R = std::max(R, Rc[c]);
     }
+    // rows are padded to an even length (zero directions) so that the kernel
+    // can read two table entries per 16-byte load
+    R = (R + 1) & ~1;
     P.R = R;
     std::vector<float2> A((size_t)ncls * R * D, make_float2(0.f, 0.f));
     std::vector<float> gm1((size_t)ncls * R, 0.f);

@@ -42,6 +42,11 @@ struct PointParams {
   float t0_hi[kMaxDet], t0_lo[kMaxDet];
   float pos_hi[kMaxDet][3], pos_lo[kMaxDet][3];
   float resp_hi[kMaxDet][6], resp_lo[kMaxDet][6];
+  // antenna coefficients: F_+(0) = sum_i acoef[i] beta_i(ra, dec), i < 6
+  // (Dxx, Dyy, Dxy, Dxz, Dyz, Dzz) and F_x(0) = sum_i acoef[6 + i] gamma_i,
+  // i < 4 (Dxx - Dyy, Dxy, Dxz, Dyz); see antenna_basis in lnl_mixed.cu.
+  float acoef_hi[kMaxDet][10], acoef_lo[kMaxDet][10];
+  int same_pos_prev[kMaxDet];  // det_order[q] sits where det_order[q - 1] does
   float gmst_hi, gmst_lo, inv_dt_hi, inv_dt_lo, ln_dref_hi, ln_dref_lo;
   float ycoef_hi[kMaxModes][kMaxYTerms], ycoef_lo[kMaxModes][kMaxYTerms];
   // detector classes (identical U_k, V_k share one whitening): the detectors
