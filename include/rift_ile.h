@@ -171,6 +171,17 @@ typedef struct {
 int rift_ile_dist_nodes(double d_min, double d_max, double d_ref, double tol, double rho_max,
                         int32_t max_nodes, double* x, double* lnw, int32_t* n_out);
 
+/* Distance-marginalised lnL per draw into DEVICE lnL_out[n] (double):
+ * ln sum_j exp(K x_j - R x_j^2/2 + ln w_j), K and R the data and quadratic
+ * terms of the draw at x = 1 (eq. ap:dexp); the draw's lnD is ignored.  With
+ * grad_out (DEVICE [7][n], may be NULL) also its gradient, E[x] dK -
+ * E[x^2] dR / 2 over the node posterior (the lnD slot is 0).  The node table
+ * is copied to the device first (synchronous), then the kernel is enqueued
+ * on `stream`.  Errors: INVALID_ARG (NULL, non-finite or non-decreasing
+ * table), SHAPE, CUDA, ALLOC. */
+int rift_ile_lnL_dist(const rift_ile_point* pt, const rift_ile_draws* draws, rift_ile_precision prec,
+                      const rift_ile_dist* dist, double* lnL_out, double* grad_out, void* stream);
+
 /* Monte Carlo lnZ of the draws (eq. lnL:MonteCarlo), fused with the lnL
  * evaluation (per-draw lnL is not stored).  out[3] (HOST) = lnZ, sigma_lnZ,
  * n_eff.  dist may be NULL.  Synchronises `stream`. */
@@ -205,12 +216,26 @@ int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_ile_draws* d
 int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
                        rift_ile_lse* merged_state);
 
-/* lnZ of P points in one persistent launch: point p uses pts[p] and
- * draws[p] (each point its own Q, U, V, network and draw count).  out is a
- * DEVICE [P][3] double array (lnZ, sigma_lnZ, n_eff per point); nothing is
- * synchronised, so the call can be captured in a CUDA graph once the
- * batch's work queue exists (the first call with a given (pts, draws, P)
- * builds and caches it).  Errors: INVALID_ARG, SHAPE, CUDA, ALLOC. */
+/* lnZ of P points in one launch (the ILE stage over many intrinsic points,
+ * Sec. II.C): point p uses pts[p] and draws[p] (each point its own Q, U, V,
+ * network and draw count).  FP32_MIXED runs one persistent kernel whose
+ * resident blocks take (point, 4096-draw tile) items from a queue by an atomic
+ * ticket, one LSE state per item, merged per point in item order (the result
+ * does not depend on scheduling); FP64 runs the plain fused kernel once per
+ * point.  out is DEVICE [P][3] double: lnZ, sigma_lnZ, n_eff per point.
+ *
+ * rift_ile_batch_create builds the work queue and the device tables once
+ * (allocates, synchronous); rift_ile_batch_launch only enqueues a memset,
+ * the kernel(s) and the per-point combine on `stream`, so it can be captured
+ * in a CUDA graph and replayed; the draws must stay valid and unchanged in
+ * place between create and the last launch.  rift_ile_lnZ_batch is
+ * create + launch + synchronise + destroy.
+ * Errors: INVALID_ARG, SHAPE, CUDA, ALLOC. */
+typedef struct rift_ile_batch rift_ile_batch; /* opaque, library-owned */
+int rift_ile_batch_create(const rift_ile_point* const* pts, const rift_ile_draws* draws, int32_t P,
+                          rift_ile_precision prec, rift_ile_batch** out);
+int rift_ile_batch_launch(rift_ile_batch* batch, double* out, void* stream);
+int rift_ile_batch_destroy(rift_ile_batch* batch);
 int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* draws, int32_t P,
                        rift_ile_precision prec, double* out, void* stream);
 

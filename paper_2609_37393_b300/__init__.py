@@ -76,6 +76,10 @@ _lib.rift_ile_lnZ.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_state.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_merge.argtypes = [_P, ctypes.c_int32, _P, _P]
 _lib.rift_ile_lnZ_batch.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P, _P]
+_lib.rift_ile_batch_create.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P]
+_lib.rift_ile_batch_launch.argtypes = [_P, _P, _P]
+_lib.rift_ile_batch_destroy.argtypes = [_P]
+_lib.rift_ile_lnL_dist.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P]
 _lib.rift_ile_dist_nodes.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int32, _P, _P, _P]
 _lib.rift_ile_last_oob.restype = ctypes.c_int64
 _lib.rift_ile_probe_alu.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]
@@ -251,6 +255,24 @@ def _dist_struct(dist):
     return s, (x, w)
 
 
+def rift_ile_lnL_dist(point: Point, draws, dist, precision: int = FP32_MIXED, out=None,
+                      grad=False, grad_out=None, stream=None):
+    """Distance-marginalised lnL per draw (eq. ap:dexp on the node table
+    dist = (x, lnw)); with grad=True returns (lnL, grad[7, n])."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(d.n, dtype=torch.float64, device=point.device)
+    if grad and grad_out is None:
+        grad_out = torch.empty((7, d.n), dtype=torch.float64, device=point.device)
+    ds, keep = _dist_struct(dist)
+    _check(_lib.rift_ile_lnL_dist(point.handle, d.ref, precision, ctypes.byref(ds),
+                                  out.data_ptr() if d.n else None,
+                                  grad_out.data_ptr() if (grad and d.n) else None, _stream(stream)))
+    del keep
+    return (out, grad_out) if grad else out
+
+
 def rift_ile_lnZ_state(point: Point, draws, precision: int = FP32_MIXED, dist=None, stream=None):
     """LSE state (m, s, s2, n) of the draws; dist = (x_nodes, lnw_nodes) or None."""
     d = _as_draws(draws)
@@ -298,6 +320,42 @@ def rift_ile_lnZ_batch(points, draws_list, precision: int = FP32_MIXED, out=None
                                    _stream(stream)))
     out._keep_draws = ds  # the launch reads the draws asynchronously
     return out
+
+
+class Batch:
+    """A prepared multi-point lnZ (rift_ile_batch_create); launch() enqueues
+    the persistent kernel and the per-point combine (capturable in a CUDA
+    graph).  Keeps the points and draws alive while it exists."""
+
+    def __init__(self, points, draws_list, precision: int = FP32_MIXED):
+        self.points = list(points)
+        self.draws = [_as_draws(d) for d in draws_list]
+        P = len(self.points)
+        handles = (ctypes.c_void_p * P)(*[p.handle.value for p in self.points])
+        structs = (_Draws * P)(*[d.struct for d in self.draws])
+        h = ctypes.c_void_p()
+        _check(_lib.rift_ile_batch_create(handles, structs, P, precision, ctypes.byref(h)))
+        self._h = h
+        self.P = P
+        self.device = self.points[0].device
+
+    def launch(self, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.P, 3), dtype=torch.float64, device=self.device)
+        _check(_lib.rift_ile_batch_launch(self._h, out.data_ptr(), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.rift_ile_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rift_ile_dist_nodes(d_min, d_max, d_ref, tol, rho_max, max_nodes=1 << 16):

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -24,6 +25,12 @@ struct Workspace {
   LseState* state = nullptr;
   unsigned long long* oob = nullptr;
   int sms = 0;
+  // distance node table (grown on demand)
+  double* dist_x = nullptr;
+  double* dist_lnw = nullptr;
+  float2* dist_xdf = nullptr;
+  float* dist_lnwf = nullptr;
+  int dist_cap = 0;
 };
 
 std::mutex g_ws_mu;
@@ -86,6 +93,66 @@ __global__ void lse_combine_kernel(const LseState* __restrict__ partials, int np
     if (bad) tot.m = tot.s = tot.s2 = CUDART_NAN;
     *out = tot;
   }
+}
+
+// Copies a host node table into the workspace and describes it for the
+// kernels.  The nodes must be finite with x strictly decreasing (increasing D).
+int upload_dist(Workspace* ws, const rift_ile_dist* dist, cudaStream_t st, DistParams* out) {
+  if (!dist->x || !dist->lnw || dist->n < 1) {
+    rift_ile_set_error("distance table: NULL arrays or n < 1");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const int n = dist->n;
+  double lnw_max = -INFINITY;
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(dist->x[j]) || std::isnan(dist->lnw[j]) || dist->lnw[j] == INFINITY ||
+        (j > 0 && !(dist->x[j] < dist->x[j - 1]))) {
+      rift_ile_set_error("distance table: node %d is not finite or x is not strictly decreasing", j);
+      return RIFT_ILE_ERR_INVALID_ARG;
+    }
+    lnw_max = std::fmax(lnw_max, dist->lnw[j]);
+  }
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  if (ws->dist_cap < n) {
+    cudaFree(ws->dist_x);
+    cudaFree(ws->dist_lnw);
+    cudaFree(ws->dist_xdf);
+    cudaFree(ws->dist_lnwf);
+    ws->dist_x = ws->dist_lnw = nullptr;
+    ws->dist_xdf = nullptr;
+    ws->dist_lnwf = nullptr;
+    ws->dist_cap = 0;
+    if (cudaMalloc((void**)&ws->dist_x, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&ws->dist_lnw, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&ws->dist_xdf, n * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc((void**)&ws->dist_lnwf, n * sizeof(float)) != cudaSuccess) {
+      rift_ile_set_error("distance table allocation failed");
+      return RIFT_ILE_ERR_ALLOC;
+    }
+    ws->dist_cap = n;
+  }
+  std::vector<float2> xdf(n);
+  std::vector<float> lnwf(n);
+  for (int j = 0; j < n; ++j) {
+    const float hi = (float)dist->x[j];
+    xdf[j] = make_float2(hi, (float)(dist->x[j] - (double)hi));
+    lnwf[j] = (float)dist->lnw[j];
+  }
+  int rc;
+  if ((rc = check_cuda(cudaMemcpyAsync(ws->dist_x, dist->x, n * sizeof(double), cudaMemcpyHostToDevice, st), "table copy")) ||
+      (rc = check_cuda(cudaMemcpyAsync(ws->dist_lnw, dist->lnw, n * sizeof(double), cudaMemcpyHostToDevice, st), "table copy")) ||
+      (rc = check_cuda(cudaMemcpyAsync(ws->dist_xdf, xdf.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st), "table copy")) ||
+      (rc = check_cuda(cudaMemcpyAsync(ws->dist_lnwf, lnwf.data(), n * sizeof(float), cudaMemcpyHostToDevice, st), "table copy")))
+    return rc;
+  // the host staging vectors die here: finish the copies first
+  if ((rc = check_cuda(cudaStreamSynchronize(st), "table copy"))) return rc;
+  out->x = ws->dist_x;
+  out->lnw = ws->dist_lnw;
+  out->xdf = ws->dist_xdf;
+  out->lnwf = ws->dist_lnwf;
+  out->n = n;
+  out->lnw_max = lnw_max;
+  return RIFT_ILE_OK;
 }
 
 int check_draws(const rift_ile_draws* d) {
@@ -187,10 +254,6 @@ extern "C" int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws
     rift_ile_set_error("rift_ile_lnZ_state: state is NULL");
     return RIFT_ILE_ERR_INVALID_ARG;
   }
-  if (dist) {
-    rift_ile_set_error("distance marginalisation is not available in this build");
-    return RIFT_ILE_ERR_UNSUPPORTED;
-  }
   if (draws->n == 0) {
     *state = rift_ile_lse{-INFINITY, 0.0, 0.0, 0.0};
     t_last_oob = 0;
@@ -200,12 +263,18 @@ extern "C" int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws
   if ((rc = get_workspace(&ws))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   int blocks = 0;
+  DistParams dd{};
+  if (dist && (rc = upload_dist(ws, dist, st, &dd))) return rc;
   if ((rc = check_cuda(cudaMemsetAsync(ws->oob, 0, sizeof(unsigned long long), st), "memset")))
     return rc;
-  if ((rc = check_cuda(launch_lnl(pt, to_params(draws), prec, nullptr, ws->partials, ws->oob,
-                                  &blocks, st),
-                       "lnZ kernel launch")))
-    return rc;
+  cudaError_t le;
+  if (!dist)
+    le = launch_lnl(pt, to_params(draws), prec, nullptr, ws->partials, ws->oob, &blocks, st);
+  else if (prec == RIFT_ILE_FP64)
+    le = launch_lnl_fp64_dist(pt->host, pt->dev, to_params(draws), dd, nullptr, ws->partials, ws->oob, &blocks, st);
+  else
+    le = launch_lnl_mixed_dist(pt->host, pt->dev, to_params(draws), dd, nullptr, ws->partials, ws->oob, &blocks, st);
+  if ((rc = check_cuda(le, "lnZ kernel launch"))) return rc;
   if ((rc = check_cuda(launch_lse_combine(ws->partials, blocks, (double)draws->n, ws->state, st),
                        "lnZ combine launch")))
     return rc;
@@ -295,16 +364,66 @@ extern "C" int rift_ile_lnL_grad(const rift_ile_point* pt, const rift_ile_draws*
   return check_cuda(e, "rift_ile_lnL_grad launch");
 }
 
-extern "C" int rift_ile_lnZ_batch(const rift_ile_point* const*, const rift_ile_draws*, int32_t,
-                                  rift_ile_precision, double*, void*) {
-  rift_ile_set_error("rift_ile_lnZ_batch is not available in this build");
-  return RIFT_ILE_ERR_UNSUPPORTED;
+extern "C" int rift_ile_lnL_dist(const rift_ile_point* pt, const rift_ile_draws* draws,
+                                 rift_ile_precision prec, const rift_ile_dist* dist, double* lnL_out,
+                                 double* grad_out, void* stream) {
+  int rc = check_point(pt, prec);
+  if (!rc) rc = check_draws(draws);
+  if (rc) return rc;
+  if (!dist || !lnL_out) {
+    rift_ile_set_error("rift_ile_lnL_dist: dist or lnL_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  Workspace* ws = nullptr;
+  if ((rc = get_workspace(&ws))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  DistParams dd{};
+  if ((rc = upload_dist(ws, dist, st, &dd))) return rc;
+  if (draws->n == 0) return RIFT_ILE_OK;
+  int blocks = 0;
+  cudaError_t le;
+  if (grad_out)
+    le = (prec == RIFT_ILE_FP64)
+             ? launch_grad_fp64_dist(pt->host, pt->dev, to_params(draws), dd, lnL_out, grad_out, st)
+             : launch_grad_mixed_dist(pt->host, pt->dev, to_params(draws), dd, lnL_out, grad_out, st);
+  else
+    le = (prec == RIFT_ILE_FP64)
+             ? launch_lnl_fp64_dist(pt->host, pt->dev, to_params(draws), dd, lnL_out, nullptr, nullptr, &blocks, st)
+             : launch_lnl_mixed_dist(pt->host, pt->dev, to_params(draws), dd, lnL_out, nullptr, nullptr, &blocks, st);
+  return check_cuda(le, "rift_ile_lnL_dist launch");
 }
 
-extern "C" int rift_ile_dist_nodes(double, double, double, double, double, int32_t, double*,
-                                   double*, int32_t*) {
-  rift_ile_set_error("rift_ile_dist_nodes is not available in this build");
-  return RIFT_ILE_ERR_UNSUPPORTED;
+// Log-uniform node table in ln D (eq. ap:dlog): the spacing in ln D is the
+// largest h <= c(tol)/rho_max, c(tol) = pi sqrt(2/ln(2/tol)), that divides
+// [ln d_min, ln d_max] into whole steps; trapezoid weights in ln D; the prior
+// p(D) = 3 D^2/(d_max^3 - d_min^3) (uniform in Euclidean volume) enters with
+// the Jacobian D of D -> ln D: ln w_j = ln(h_j) + ln p(D_j) + ln D_j.
+extern "C" int rift_ile_dist_nodes(double d_min, double d_max, double d_ref, double tol,
+                                   double rho_max, int32_t max_nodes, double* x, double* lnw,
+                                   int32_t* n_out) {
+  if (!x || !lnw || !n_out || !(d_min > 0) || !(d_max > d_min) || !(d_ref > 0) || !(tol > 0) ||
+      !(tol < 2) || !(rho_max > 0) || max_nodes < 2) {
+    rift_ile_set_error("rift_ile_dist_nodes: invalid argument");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const double c = M_PI * std::sqrt(2.0 / std::log(2.0 / tol));
+  const double span = std::log(d_max / d_min);
+  const double steps = std::ceil(span * rho_max / c);
+  if (steps + 1 > max_nodes) {
+    rift_ile_set_error("rift_ile_dist_nodes: %.0f nodes exceed max_nodes = %d", steps + 1, max_nodes);
+    return RIFT_ILE_ERR_SHAPE;
+  }
+  const int n = (int)steps + 1;
+  const double h = span / steps;
+  const double ln_norm = std::log(3.0 / (d_max * d_max * d_max - d_min * d_min * d_min));
+  for (int j = 0; j < n; ++j) {
+    const double lnd = std::log(d_min) + j * h;
+    const double wt = (j == 0 || j == n - 1) ? 0.5 * h : h;
+    x[j] = d_ref * std::exp(-lnd);
+    lnw[j] = std::log(wt) + ln_norm + 3.0 * lnd;
+  }
+  *n_out = n;
+  return RIFT_ILE_OK;
 }
 
 extern "C" int rift_ile_release(void) {
@@ -318,6 +437,10 @@ extern "C" int rift_ile_release(void) {
     cudaFree(w.partials);
     cudaFree(w.state);
     cudaFree(w.oob);
+    cudaFree(w.dist_x);
+    cudaFree(w.dist_lnw);
+    cudaFree(w.dist_xdf);
+    cudaFree(w.dist_lnwf);
     w = Workspace();
   }
   cudaSetDevice(cur);

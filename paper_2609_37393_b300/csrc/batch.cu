@@ -1,0 +1,249 @@
+// lnZ of many intrinsic points in one persistent launch (rift_ile_lnZ_batch,
+// rift_ile_batch_*).  The paper's ILE stage evaluates the marginal likelihood
+// of many intrinsic points (Sec. II.C: each worker handles a set of points);
+// here their draws are cut into tiles, the (point, tile) items form a queue,
+// and resident blocks take items from it with an atomic ticket until it is
+// empty.  Each item leaves one LSE state; a second kernel merges the states of
+// each point in item order, so the result does not depend on which block took
+// which item.  No block waits on another.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rift {
+namespace {
+
+constexpr int kTileDraws = 4096;
+
+// Marks LSE states as empty (m = -inf).
+__global__ void fill_empty_kernel(LseState* __restrict__ st, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    st[i] = LseState{-CUDART_INF, 0.0, 0.0, 0.0};
+}
+
+// out[p] = (lnZ, sigma_lnZ, n_eff) from the states of point p's items
+// [first[p], first[p+1]), merged in item order.
+__global__ void batch_combine_kernel(const LseState* __restrict__ partials,
+                                     const int* __restrict__ first, const double* __restrict__ ndraws,
+                                     int P, double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
+  bool bad = false;
+  for (int i = first[p]; i < first[p + 1]; ++i) {
+    const LseState s = partials[i];
+    if (isnan(s.m)) bad = true;
+    else acc = lse_merge(acc, s);
+  }
+  const double n = ndraws[p];
+  double lnz, sig, neff;
+  if (bad) {
+    lnz = sig = neff = CUDART_NAN;
+  } else if (n <= 0.0 || !(acc.m > -CUDART_INF)) {
+    lnz = -CUDART_INF;
+    sig = CUDART_NAN;
+    neff = 0.0;
+  } else {
+    lnz = acc.m + log(acc.s) - log(n);
+    const double var = acc.s2 / (acc.s * acc.s) - 1.0 / n;
+    sig = sqrt(var > 0.0 ? var : 0.0);
+    neff = acc.s;
+  }
+  out[3 * p] = lnz;
+  out[3 * p + 1] = sig;
+  out[3 * p + 2] = neff;
+}
+
+template <typename T>
+int alloc_copy(T** dst, const T* src, size_t count, const char* what) {
+  if (cudaMalloc((void**)dst, std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
+    *dst = nullptr;
+    rift_ile_set_error("rift_ile_batch_create: allocation of %s failed", what);
+    return RIFT_ILE_ERR_ALLOC;
+  }
+  if (count && src) return check_cuda(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice), what);
+  return RIFT_ILE_OK;
+}
+
+}  // namespace
+}  // namespace rift
+
+using namespace rift;
+
+struct rift_ile_batch {
+  int P = 0;
+  int prec = 0;
+  // FP32-mixed persistent form
+  const PointParams** d_pts = nullptr;
+  DrawsParams* d_dps = nullptr;
+  BatchItem* d_items = nullptr;
+  int n_items = 0;
+  int* d_first = nullptr;
+  double* d_ndraws = nullptr;
+  unsigned int* d_head = nullptr;
+  LseState* d_partials = nullptr;
+  unsigned long long* d_oob = nullptr;
+  BatchKernelFn kernel = nullptr;
+  size_t smem = 0;
+  int blocks = 0;
+  // FP64 per-point form
+  std::vector<const rift_ile_point*> pts;
+  std::vector<DrawsParams> dps;
+  int parts_per_point = 0;
+};
+
+extern "C" int rift_ile_batch_destroy(rift_ile_batch* b) {
+  if (!b) return RIFT_ILE_OK;
+  cudaFree(b->d_pts);
+  cudaFree(b->d_dps);
+  cudaFree(b->d_items);
+  cudaFree(b->d_first);
+  cudaFree(b->d_ndraws);
+  cudaFree(b->d_head);
+  cudaFree(b->d_partials);
+  cudaFree(b->d_oob);
+  delete b;
+  return RIFT_ILE_OK;
+}
+
+extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rift_ile_draws* draws,
+                                     int32_t P, rift_ile_precision prec, rift_ile_batch** out) {
+  if (!out || !pts || !draws || P < 1) {
+    rift_ile_set_error("rift_ile_batch_create: bad arguments (P = %d)", P);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (prec != RIFT_ILE_FP64 && prec != RIFT_ILE_FP32_MIXED) {
+    rift_ile_set_error("rift_ile_batch_create: bad precision %d", (int)prec);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  rift_ile_batch* b = new rift_ile_batch();
+  b->P = P;
+  b->prec = prec;
+  std::vector<const PointParams*> hp(P);
+  std::vector<DrawsParams> hd(P);
+  std::vector<int> first(P + 1, 0);
+  std::vector<double> nd(P);
+  std::vector<BatchItem> items;
+  int maxM = 1, maxR = 2;
+  size_t smem = 0;
+  int rc = RIFT_ILE_OK;
+  for (int p = 0; p < P && !rc; ++p) {
+    const rift_ile_point* pt = pts[p];
+    const rift_ile_draws* d = draws + p;
+    if (!pt || d->n < 0 || (d->dtype != RIFT_ILE_F32 && d->dtype != RIFT_ILE_F64) ||
+        (d->n > 0 && (!d->ra || !d->dec || !d->psi || !d->incl || !d->phase || !d->lnD || !d->t))) {
+      rift_ile_set_error("rift_ile_batch_create: point or draws %d invalid", p);
+      rc = RIFT_ILE_ERR_INVALID_ARG;
+      break;
+    }
+    hp[p] = pt->dev;
+    DrawsParams& dp = hd[p];
+    dp.p[0] = d->ra;
+    dp.p[1] = d->dec;
+    dp.p[2] = d->psi;
+    dp.p[3] = d->incl;
+    dp.p[4] = d->phase;
+    dp.p[5] = d->lnD;
+    dp.p[6] = d->t;
+    dp.logw = d->logw;
+    dp.n = d->n;
+    dp.f64 = (d->dtype == RIFT_ILE_F64);
+    nd[p] = (double)d->n;
+    maxM = std::max(maxM, pt->host.M);
+    maxR = std::max(maxR, pt->host.R);
+    smem = std::max(smem, (size_t)pt->host.ncls * pt->host.R * pt->host.D * sizeof(float4) +
+                              (size_t)pt->host.ncls * pt->host.R * sizeof(float));
+    first[p] = (int)items.size();
+    for (long long a = 0; a < d->n; a += kTileDraws)
+      items.push_back(BatchItem{a, (int)std::min<long long>(kTileDraws, d->n - a), p});
+    b->pts.push_back(pt);
+  }
+  first[P] = (int)items.size();
+  b->dps = hd;
+  if (!rc && prec == RIFT_ILE_FP32_MIXED) {
+    b->n_items = (int)items.size();
+    b->kernel = batch_kernel_for(maxM, maxR);
+    b->smem = smem;
+    cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    b->blocks = grid_for(b->kernel, 128, smem);
+    if (!rc) rc = alloc_copy(&b->d_pts, hp.data(), P, "point table");
+    if (!rc) rc = alloc_copy(&b->d_dps, hd.data(), P, "draw table");
+    if (!rc) rc = alloc_copy(&b->d_items, items.data(), items.size(), "work queue");
+    if (!rc) rc = alloc_copy(&b->d_first, first.data(), P + 1, "item offsets");
+    if (!rc) rc = alloc_copy(&b->d_ndraws, nd.data(), P, "draw counts");
+    if (!rc) rc = alloc_copy(&b->d_head, (unsigned int*)nullptr, 1, "queue head");
+    if (!rc) rc = alloc_copy(&b->d_partials, (LseState*)nullptr, items.size(), "partials");
+    if (!rc) rc = alloc_copy(&b->d_oob, (unsigned long long*)nullptr, 1, "counter");
+  } else if (!rc) {
+    // FP64: one fused lnL -> LSE launch per point into its own slice of partials
+    b->parts_per_point = device_sms() * kMaxPartialsPerSM;
+    std::vector<int> f2(P + 1);
+    for (int p = 0; p <= P; ++p) f2[p] = p * b->parts_per_point;
+    if (!rc) rc = alloc_copy(&b->d_first, f2.data(), P + 1, "item offsets");
+    if (!rc) rc = alloc_copy(&b->d_ndraws, nd.data(), P, "draw counts");
+    if (!rc) rc = alloc_copy(&b->d_partials, (LseState*)nullptr, (size_t)P * b->parts_per_point, "partials");
+    if (!rc) rc = alloc_copy(&b->d_oob, (unsigned long long*)nullptr, 1, "counter");
+  }
+  if (rc) {
+    rift_ile_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return RIFT_ILE_OK;
+}
+
+extern "C" int rift_ile_batch_launch(rift_ile_batch* b, double* out, void* stream) {
+  if (!b || !out) {
+    rift_ile_set_error("rift_ile_batch_launch: NULL argument");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if ((rc = check_cuda(cudaMemsetAsync(b->d_oob, 0, sizeof(unsigned long long), st), "batch clear")))
+    return rc;
+  if (b->prec == RIFT_ILE_FP32_MIXED) {
+    if ((rc = check_cuda(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), st), "batch clear")))
+      return rc;
+    if (b->n_items > 0) {
+      b->kernel<<<b->blocks, 128, b->smem, st>>>(b->d_pts, b->d_dps, b->d_items, b->n_items,
+                                                 b->d_head, b->d_partials, b->d_oob);
+      if ((rc = check_cuda(cudaGetLastError(), "batch kernel launch"))) return rc;
+    }
+  } else {
+    // FP64: the plain path, one launch per point; unused partial slots are
+    // empty states
+    const long long np = (long long)b->P * b->parts_per_point;
+    fill_empty_kernel<<<(int)std::min<long long>((np + 255) / 256, 4096), 256, 0, st>>>(b->d_partials, np);
+    if ((rc = check_cuda(cudaGetLastError(), "batch clear"))) return rc;
+    for (int p = 0; p < b->P; ++p) {
+      if (b->dps[p].n == 0) continue;
+      int blocks = 0;
+      cudaError_t e = launch_lnl_fp64(b->pts[p]->host, b->pts[p]->dev, b->dps[p], nullptr,
+                                      b->d_partials + (size_t)p * b->parts_per_point, b->d_oob,
+                                      &blocks, st);
+      if ((rc = check_cuda(e, "batch FP64 launch"))) return rc;
+    }
+  }
+  batch_combine_kernel<<<(b->P + 127) / 128, 128, 0, st>>>(b->d_partials, b->d_first, b->d_ndraws,
+                                                           b->P, out);
+  return check_cuda(cudaGetLastError(), "batch combine launch");
+}
+
+extern "C" int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* draws,
+                                  int32_t P, rift_ile_precision prec, double* out, void* stream) {
+  rift_ile_batch* b = nullptr;
+  int rc = rift_ile_batch_create(pts, draws, P, prec, &b);
+  if (rc) return rc;
+  rc = rift_ile_batch_launch(b, out, stream);
+  if (!rc) rc = check_cuda(cudaStreamSynchronize((cudaStream_t)stream), "rift_ile_lnZ_batch");
+  rift_ile_batch_destroy(b);
+  return rc;
+}

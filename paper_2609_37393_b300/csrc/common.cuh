@@ -92,6 +92,84 @@ __device__ __forceinline__ void lagrange4_d(double f, double w[4], double dw[4])
   dw[3] = (b * c + a * c + a * b) * (1.0 / 6.0);
 }
 
+// ------------------------------------------------- distance marginalisation
+
+// Node of the table nearest x (x_j decreasing in j), by bisection.
+__device__ __forceinline__ int dist_nearest(const DistParams& dp, double x) {
+  int lo = 0, hi = dp.n - 1;
+  if (!(x < dp.x[0])) return 0;
+  if (!(x > dp.x[hi])) return hi;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (dp.x[mid] > x) lo = mid;
+    else hi = mid;
+  }
+  return (dp.x[lo] - x < x - dp.x[hi]) ? lo : hi;
+}
+
+// ln sum_j exp(K x_j - R x_j^2 / 2 + ln w_j) (eq. ap:dexp on the node table),
+// written as K^2/(2R) + ln sum_j exp(ln w_j - R (x_j - x*)^2 / 2), x* = K/R,
+// visiting only nodes whose term can exceed the running maximum minus 40:
+// from the node nearest x* outwards, stopping in each direction once
+// max_j ln w_j - R (x_j - x*)^2 / 2 is below that level (the quadratic only
+// grows away from x*), in IEEE double.  peak = K^2/(2R) is returned
+// separately; the return value is the node sum.  R <= 0
+// (no template power) sums every node of K x_j + ln w_j instead, relative to
+// peak = max_j K x_j.
+//
+// With ex (may be NULL) the node posterior moments E[x] and E[x^2] are
+// returned in ex[0], ex[1] (the distance-marginal gradient is
+// E[x] dK - E[x^2] dR / 2).
+__device__ __forceinline__ double dist_lse(const DistParams& dp, double K, double R, double xs,
+                                           double* peak, double* ex = nullptr) {
+  if (!(R > 0.0)) {
+    double m = -CUDART_INF;
+    for (int j = 0; j < dp.n; ++j) m = fmax(m, K * dp.x[j] - 0.5 * R * dp.x[j] * dp.x[j] + dp.lnw[j]);
+    double s = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int j = 0; j < dp.n; ++j) {
+      const double e = exp(K * dp.x[j] - 0.5 * R * dp.x[j] * dp.x[j] + dp.lnw[j] - m);
+      s += e;
+      s1 += e * dp.x[j];
+      s2 += e * dp.x[j] * dp.x[j];
+    }
+    *peak = 0.0;
+    if (ex) {
+      ex[0] = s1 / s;
+      ex[1] = s2 / s;
+    }
+    return m + log(s);
+  }
+  const int j0 = dist_nearest(dp, xs);
+  double m = -CUDART_INF, s = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int dir = -1; dir <= 1; dir += 2) {
+    for (int j = (dir < 0 ? j0 : j0 + 1); j >= 0 && j < dp.n; j += dir) {
+      const double xj = dp.x[j];
+      const double d = xj - xs;
+      const double q = 0.5 * R * d * d;
+      if (dp.lnw_max - q < m - 40.0) break;
+      const double t = dp.lnw[j] - q;
+      if (t > m) {
+        const double r = exp(m - t);
+        s = s * r + 1.0;
+        s1 = s1 * r + xj;
+        s2 = s2 * r + xj * xj;
+        m = t;
+      } else {
+        const double e = exp(t - m);
+        s += e;
+        s1 += e * xj;
+        s2 += e * xj * xj;
+      }
+    }
+  }
+  *peak = 0.5 * K * xs;
+  if (ex) {
+    ex[0] = s1 / s;
+    ex[1] = s2 / s;
+  }
+  return m + log(s);
+}
+
 // ---------------------------------------------------------------- LSE state
 
 // Per-thread online log-sum-exp of v_i = lnL_i + ln w_i, with the running
@@ -130,6 +208,21 @@ __device__ __forceinline__ void tlse_push(ThreadLse& t, df v) {
     t.s += e;
     t.s2 = fmaf(e, e, t.s2);
   }
+}
+
+// Pushes lnL + ln w with a float ln w that may be infinite: a zero weight
+// (ln w = -inf) is skipped unless lnL is NaN, +inf dominates; the pair sum
+// of a finite lnL and an infinite ln w would otherwise be NaN.
+__device__ __forceinline__ void tlse_push_lw(ThreadLse& t, df lnl, float lw) {
+  if (isnan(lw) || isnan(lnl.hi)) {
+    t.nan_seen = 1;
+    return;
+  }
+  if (isinf(lw)) {
+    if (lw > 0.f) tlse_push(t, df{CUDART_INF_F, 0.f});
+    return;
+  }
+  tlse_push(t, df_add_f(lnl, lw));
 }
 
 __device__ __forceinline__ LseState lse_merge(LseState a, LseState b) {

@@ -18,11 +18,38 @@ cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const 
 cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                              double* lnl_out, LseState* partials, unsigned long long* oob,
                              int* blocks, cudaStream_t st);
+// One work item of the batched lnZ: draws [begin, begin + count) of a point.
+struct BatchItem {
+  long long begin;
+  int count;
+  int point;
+};
+typedef void (*BatchKernelFn)(const PointParams* const*, const DrawsParams*, const BatchItem*, int,
+                              unsigned int*, LseState*, unsigned long long*);
+// The persistent FP32-mixed batch kernel for the largest M and R of a batch
+// (launch with 128 threads and the largest table smem of the batch).
+BatchKernelFn batch_kernel_for(int M, int R);
+
 // lnL (lnl_out may be NULL) and its gradient, grad_out[7][n].
 cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                               double* lnl_out, double* grad_out, cudaStream_t st);
 cudaError_t launch_grad_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                              double* lnl_out, double* grad_out, cudaStream_t st);
+// Distance-marginalised lnL (per draw into lnl_out, or fused into partials).
+cudaError_t launch_lnl_fp64_dist(const PointParams& hp, const PointParams* dP,
+                                 const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                 LseState* partials, unsigned long long* oob, int* blocks,
+                                 cudaStream_t st);
+cudaError_t launch_lnl_mixed_dist(const PointParams& hp, const PointParams* dP,
+                                  const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                  LseState* partials, unsigned long long* oob, int* blocks,
+                                  cudaStream_t st);
+cudaError_t launch_grad_fp64_dist(const PointParams& hp, const PointParams* dP,
+                                  const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                  double* grad_out, cudaStream_t st);
+cudaError_t launch_grad_mixed_dist(const PointParams& hp, const PointParams* dP,
+                                   const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                   double* grad_out, cudaStream_t st);
 cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
                                LseState* state_out, cudaStream_t st);
 

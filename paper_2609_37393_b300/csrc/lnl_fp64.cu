@@ -20,6 +20,7 @@ namespace {
 
 struct Fp64Out {
   double lnl;
+  double td, tq;  // data sum and quadratic sum at x = 1: lnL(x) = x td - x^2 tq / 4
   int oob;
 };
 
@@ -152,15 +153,18 @@ __device__ __forceinline__ Fp64Out lnl_fp64_draw(const PointParams& P, const dou
   }
   Fp64Out o;
   o.lnl = x * td - 0.25 * x * x * tq;
+  o.td = td;
+  o.tq = tq;
   o.oob = oob;
   return o;
 }
 
-template <int MM, bool LSE>
+template <int MM, bool LSE, bool DIST = false>
 __global__ void __launch_bounds__(256) lnl_fp64_kernel(const PointParams* __restrict__ gP,
                                                        DrawsParams dp, double* __restrict__ lnl_out,
                                                        LseState* __restrict__ partials,
-                                                       unsigned long long* __restrict__ oob_count) {
+                                                       unsigned long long* __restrict__ oob_count,
+                                                       DistParams dist = DistParams{}) {
   __shared__ PointParams P;
   extern __shared__ double2 sUV[];
   stage_point(P, gP);
@@ -176,6 +180,13 @@ __global__ void __launch_bounds__(256) lnl_fp64_kernel(const PointParams* __rest
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
     Fp64Out o = lnl_fp64_draw<MM>(P, sUV, dp, i);
     oob += o.oob;
+    if (DIST && !isnan(o.lnl)) {
+      // lnL(x) = K x - R x^2/2 with K = td, R = tq/2 (eq. ap:dexp), summed on the nodes
+      const double K = o.td, Rq = 0.5 * o.tq;
+      double peak;
+      const double nodes = dist_lse(dist, K, Rq, Rq > 0.0 ? K / Rq : 0.0, &peak);
+      o.lnl = peak + nodes;
+    }
     if (!LSE) {
       lnl_out[i] = o.lnl;
     } else {
@@ -187,6 +198,26 @@ __global__ void __launch_bounds__(256) lnl_fp64_kernel(const PointParams* __rest
     for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
     if ((threadIdx.x & 31) == 0 && oob) atomicAdd(oob_count, (unsigned long long)oob);
   }
+}
+
+template <int MM, bool LSE>
+cudaError_t launch_fp64_dist_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                               const DistParams& dist, double* lnl_out, LseState* partials,
+                               unsigned long long* oob, int* blocks, cudaStream_t st) {
+  const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
+  auto kern = lnl_fp64_kernel<MM, LSE, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  *blocks = grid_for(kern, 256, smem);
+  kern<<<*blocks, 256, smem, st>>>(dP, dp, lnl_out, partials, oob, dist);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_fp64_dist_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                const DistParams& dist, double* lnl_out, LseState* partials,
+                                unsigned long long* oob, int* blocks, cudaStream_t st) {
+  if (partials) return launch_fp64_dist_k<MM, true>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  return launch_fp64_dist_k<MM, false>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
 }
 
 template <int MM, bool LSE>
@@ -218,10 +249,13 @@ cudaError_t launch_fp64_mm(const PointParams& hp, const PointParams* dP, const D
 // dY/d iota from the Wigner-d polynomial, dQ/dt from the cubic's slope, and
 // da_k = 2 Re(dY^+ U_k Y), db_k = 2 dY^T V_k Y (U Hermitian, V symmetric as
 // eq. QUV makes them).
+// With raw != NULL the x-free sums are also returned: raw[0] = T_d/x,
+// raw[1] = 4 T_q/x^2, raw[2..8] = their derivatives of T_d/x, raw[9..15] of
+// 4 T_q / x^2 (slot 5, lnD, excluded).
 template <int MM>
 __device__ __forceinline__ double lnl_fp64_grad_draw(const PointParams& P, const double2* sUV,
                                                      const DrawsParams& dp, long long i,
-                                                     double g[kNpar]) {
+                                                     double g[kNpar], double* raw = nullptr) {
   const double ra = load_param_d(dp, 0, i), dec = load_param_d(dp, 1, i);
   const double psi = load_param_d(dp, 2, i), incl = load_param_d(dp, 3, i);
   const double phi = load_param_d(dp, 4, i), lnD = load_param_d(dp, 5, i);
@@ -398,13 +432,22 @@ __device__ __forceinline__ double lnl_fp64_grad_draw(const PointParams& P, const
 #pragma unroll
   for (int p = 0; p < kNpar; ++p) g[p] = x * gd[p] - q4 * gq[p];
   g[5] = -x * td + 2.0 * q4 * tq;
+  if (raw) {
+    raw[0] = td;
+    raw[1] = tq;
+    for (int p = 0; p < kNpar; ++p) {
+      raw[2 + p] = gd[p];
+      raw[9 + p] = gq[p];
+    }
+  }
   return x * td - q4 * tq;
 }
 
-template <int MM>
+template <int MM, bool DIST = false>
 __global__ void __launch_bounds__(256) grad_fp64_kernel(const PointParams* __restrict__ gP,
                                                         DrawsParams dp, double* __restrict__ lnl_out,
-                                                        double* __restrict__ grad_out) {
+                                                        double* __restrict__ grad_out,
+                                                        DistParams dist = DistParams{}) {
   __shared__ PointParams P;
   extern __shared__ double2 sUV[];
   stage_point(P, gP);
@@ -417,7 +460,21 @@ __global__ void __launch_bounds__(256) grad_fp64_kernel(const PointParams* __res
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
     double g[kNpar];
-    const double v = lnl_fp64_grad_draw<MM>(P, sUV, dp, i, g);
+    double v;
+    if (DIST) {
+      // lnL(x) = K x - R x^2 / 2 with K = T_d/x, R = T_q/(2 x^2) ... in raw
+      // sums: K = raw[0], R = raw[1]/2; gradient E[x] dK - E[x^2] dR / 2
+      double raw[16];
+      const double v0 = lnl_fp64_grad_draw<MM>(P, sUV, dp, i, g, raw);
+      const double K = raw[0], Rq = 0.5 * raw[1];
+      double peak, ex[2] = {0.0, 0.0};
+      const double nodes = dist_lse(dist, K, Rq, Rq > 0.0 ? K / Rq : 0.0, &peak, ex);
+      v = isnan(v0) ? v0 : peak + nodes;
+      for (int p = 0; p < kNpar; ++p) g[p] = ex[0] * raw[2 + p] - 0.25 * ex[1] * raw[9 + p];
+      g[5] = 0.0;
+    } else {
+      v = lnl_fp64_grad_draw<MM>(P, sUV, dp, i, g);
+    }
     if (lnl_out) lnl_out[i] = v;
 #pragma unroll
     for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = g[p];
@@ -434,7 +491,32 @@ cudaError_t launch_grad_fp64_mm(const PointParams& hp, const PointParams* dP, co
   return cudaGetLastError();
 }
 
+template <int MM>
+cudaError_t launch_grad_fp64_dist_mm(const PointParams& hp, const PointParams* dP,
+                                     const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                     double* grad_out, cudaStream_t st) {
+  const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
+  auto kern = grad_fp64_kernel<MM, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  const int blocks = grid_for(kern, 256, smem);
+  kern<<<blocks, 256, smem, st>>>(dP, dp, lnl_out, grad_out, dist);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_grad_fp64_dist(const PointParams& hp, const PointParams* dP,
+                                  const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                  double* grad_out, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_grad_fp64_dist_mm<2>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 4) return launch_grad_fp64_dist_mm<4>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 6) return launch_grad_fp64_dist_mm<6>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 8) return launch_grad_fp64_dist_mm<8>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 10) return launch_grad_fp64_dist_mm<10>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 12) return launch_grad_fp64_dist_mm<12>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  return launch_grad_fp64_dist_mm<16>(hp, dP, dp, dist, lnl_out, grad_out, st);
+}
 
 cudaError_t launch_grad_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                              double* lnl_out, double* grad_out, cudaStream_t st) {
@@ -450,6 +532,20 @@ cudaError_t launch_grad_fp64(const PointParams& hp, const PointParams* dP, const
 
 namespace {
 }  // namespace
+
+cudaError_t launch_lnl_fp64_dist(const PointParams& hp, const PointParams* dP,
+                                 const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                 LseState* partials, unsigned long long* oob, int* blocks,
+                                 cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_fp64_dist_mm<2>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 4) return launch_fp64_dist_mm<4>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 6) return launch_fp64_dist_mm<6>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 8) return launch_fp64_dist_mm<8>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 10) return launch_fp64_dist_mm<10>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 12) return launch_fp64_dist_mm<12>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  return launch_fp64_dist_mm<16>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+}
 
 cudaError_t launch_lnl_fp64(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                             double* lnl_out, LseState* partials, unsigned long long* oob,

@@ -277,10 +277,76 @@ __device__ __forceinline__ void split_y(float y, float& y1, float& y2) {
 }
 
 struct MixedDraw {
-  df lnl;
+  df lnl;      // lnL, or with DIST the data term K at x = 1
+  df R;        // with DIST: the quadratic coefficient R at x = 1 (lnL(x) = K x - R x^2/2)
   int oob;
   double grad[kNpar];
 };
+
+// Distance marginal of one draw from K and R (eq. ap:dexp, eq. ap:dlog):
+// K^2/(2R) in double-float plus the node sum of dist_lse, in FP32 offsets
+// from x* = K/R (see dist_lse in common.cuh for the window rule).
+__device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, float* ex = nullptr) {
+  if (!(R.hi > 0.f)) {
+    double peak, exd[2];
+    const double v = dist_lse(dp, df_to_double(K), df_to_double(R), 0.0, &peak, exd);
+    if (ex) {
+      ex[0] = (float)exd[0];
+      ex[1] = (float)exd[1];
+    }
+    return df_from_double(v);
+  }
+  // x* = K / R by one Newton correction of the float quotient
+  const float q0 = K.hi / R.hi;
+  df pr = two_prod(q0, R.hi);
+  pr.lo = fmaf(q0, R.lo, pr.lo);
+  const df rem = df_sub(K, pr);
+  const df xs = fast_two_sum(q0, rem.hi / R.hi);
+  // nearest node by bisection on the hi parts (x decreasing)
+  int lo = 0, hi = dp.n - 1;
+  if (!(xs.hi < dp.xdf[0].x)) {
+    hi = 0;
+  } else if (!(xs.hi > dp.xdf[dp.n - 1].x)) {
+    lo = dp.n - 1;
+  } else {
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (dp.xdf[mid].x > xs.hi) lo = mid;
+      else hi = mid;
+    }
+  }
+  const int j0 = (dp.xdf[lo].x - xs.hi < xs.hi - dp.xdf[hi].x) ? lo : hi;
+  float m = -CUDART_INF_F, s = 0.f, s1 = 0.f, s2 = 0.f;
+  const float halfR = 0.5f * R.hi;
+  const float lnw_max = (float)dp.lnw_max;
+  for (int dir = -1; dir <= 1; dir += 2) {
+    for (int j = (dir < 0 ? j0 : j0 + 1); j >= 0 && j < dp.n; j += dir) {
+      const float2 xj = __ldg(dp.xdf + j);
+      const float d = __fadd_rn(__fsub_rn(xj.x, xs.hi), __fsub_rn(xj.y, xs.lo));
+      const float q = halfR * d * d;
+      if (lnw_max - q < m - 40.f) break;
+      const float t = __ldg(dp.lnwf + j) - q;
+      if (t > m) {
+        const float r = __expf(m - t);
+        s = fmaf(s, r, 1.f);
+        s1 = fmaf(s1, r, xj.x);
+        s2 = fmaf(s2, r, xj.x * xj.x);
+        m = t;
+      } else {
+        const float e = __expf(t - m);
+        s += e;
+        s1 = fmaf(e, xj.x, s1);
+        s2 = fmaf(e * xj.x, xj.x, s2);
+      }
+    }
+  }
+  if (ex) {
+    ex[0] = s1 / s;
+    ex[1] = s2 / s;
+  }
+  const df peak = df_mul(K, xs);
+  return df_add_f(df{0.5f * peak.hi, 0.5f * peak.lo}, m + __logf(s));
+}
 
 // One draw: lnL, and with GRAD its gradient in (ra, dec, psi, incl, phase, lnD, t).
 //
@@ -291,10 +357,12 @@ struct MixedDraw {
 // Im(xF_k) a2: rho_k . dw_k = d Re(xF_k) rho_k.a1 + d Im(xF_k) rho_k.a2 for the
 // sky angles, psi and lnD, and (A^T G1 + J^T A^T G2) . dy with
 // G1 = sum_k Re(xF_k) rho_k, G2 = sum_k Im(xF_k) rho_k for iota and phase.
-template <int MM, int RR, bool GRAD>
+// With DIST the template is taken at the distance factor xin (1 for the
+// marginal's K and R) instead of D_ref e^{-lnD}.
+template <int MM, int RR, bool GRAD, bool DIST = false>
 __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const float4* sA,
                                                     const float* sg, const DrawsParams& dp,
-                                                    long long i) {
+                                                    long long i, df xin = df{1.f, 0.f}) {
   const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
   const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
   const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
@@ -304,7 +372,8 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   // distance factor x = D_ref e^{-lnD}
   df lx = two_sum(P.ln_dref_hi, -lnD);
   lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
-  const df x = exp_df(fast_two_sum(lx.hi, lx.lo));
+  // with distance marginalisation the terms are taken at x = 1
+  const df x = DIST ? xin : exp_df(fast_two_sum(lx.hi, lx.lo));
 
   // sky direction and transverse basis
   df lam = two_sum(ra, -P.gmst_hi);
@@ -323,6 +392,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   sincos_df(df{0.5f * incl, 0.f}, sh, ch);
 
   dacc T = dacc_zero();
+  dacc Racc = dacc_zero();  // DIST: R = sum_k (|w_k|^2 - sum_r gm1_r w_kr^2)
   int oob = 0;
   bool bad = false;
   // gradient accumulators: time-driven parts of (ra, dec, t) as pairs, the rest in FP32
@@ -528,7 +598,23 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       }
       dacc_add(T, half_e2);
       dacc_add(T, df{-0.5f * q2, 0.f});
-      if (P.has_null[c]) dacc_add(T, df{0.5f * nul, 0.f});
+      if (P.has_null[c] && !DIST) dacc_add(T, df{0.5f * nul, 0.f});
+      if (DIST) {
+        // K_k = e.w = 1/2|e|^2 + 1/2|w|^2 - 1/2|e - w|^2 (the first and last are in T
+        // already); R_k = |w|^2 - sum_r gm1_r w_r^2, with |w|^2 exact in pairs
+        dacc w2 = dacc_zero();
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          if (r < R) {
+            dacc_fma_ff(w2, w[r].hi, w[r].hi);
+            w2.c = fmaf(2.f * w[r].hi, w[r].lo, w2.c);
+          }
+        }
+        const df w2d = dacc_result(w2);
+        dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
+        dacc_add(Racc, w2d);
+        if (P.has_null[c]) dacc_add(Racc, df{-nul, 0.f});
+      }
       if (GRAD) {
         // time: d lnL_k / d t_k = (P'(f) - r . edot dt) / dt
         float red = 0.f, g1 = 0.f, g2 = 0.f;
@@ -606,6 +692,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   }
   MixedDraw o;
   o.lnl = dacc_result(T);
+  o.R = dacc_result(Racc);
   if (bad) o.lnl = df{CUDART_NAN_F, 0.f};
   o.oob = oob;
   if (GRAD) {
@@ -623,21 +710,14 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   return o;
 }
 
-template <int MM, int RR, bool LSE, bool GRAD = false>
-__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(const PointParams* __restrict__ gP,
-                                                        DrawsParams dp, double* __restrict__ lnl_out,
-                                                        LseState* __restrict__ partials,
-                                                        unsigned long long* __restrict__ oob_count,
-                                                        double* __restrict__ grad_out = nullptr) {
-  __shared__ PointParams P;
-  extern __shared__ float4 smem4[];
-  stage_point(P, gP);
-  __syncthreads();
+// Stages the whitening matrices of all classes into shared memory in split
+// form, (10-bit head, tail, lo part, 0) per entry: the head is A_hi rounded to
+// a multiple of 2^-9 of a power of two >= max_a |A[r][a]| (the error-free
+// product of lnl_mixed_draw relies on it), followed by gm1.  Whole block.
+__device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem4) {
   const int R = P.R, D = P.D, ncls = P.ncls;
   float4* sA = smem4;
   float* sg = reinterpret_cast<float*>(smem4 + (size_t)ncls * R * D);
-  // A in split form: (10-bit head, tail, lo part, 0) per entry.  The head is
-  // A_hi rounded to a multiple of 2^-9 of a power of two >= max_a |A[r][a]|.
   for (int t = threadIdx.x; t < ncls * R; t += blockDim.x) {
     const float2* row = P.A + (size_t)t * D;
     float mx = 0.f;
@@ -652,12 +732,44 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(c
     }
     sg[t] = __ldg(P.gm1 + t);
   }
+}
+
+template <int MM, int RR, bool LSE, bool GRAD = false, bool DIST = false>
+__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(const PointParams* __restrict__ gP,
+                                                        DrawsParams dp, double* __restrict__ lnl_out,
+                                                        LseState* __restrict__ partials,
+                                                        unsigned long long* __restrict__ oob_count,
+                                                        double* __restrict__ grad_out = nullptr,
+                                                        DistParams dist = DistParams{}) {
+  __shared__ PointParams P;
+  extern __shared__ float4 smem4[];
+  stage_point(P, gP);
   __syncthreads();
+  stage_split_A(P, smem4);
+  __syncthreads();
+  const float4* sA = smem4;
+  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.D);
   ThreadLse st = tlse_init();
   int oob = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
-    MixedDraw o = lnl_mixed_draw<MM, RR, GRAD>(P, sA, sg, dp, i);
+    MixedDraw o;
+    if (DIST && GRAD) {
+      // distance-marginal gradient: E[x] dK - E[x^2] dR / 2 equals (a / xbar)
+      // times the gradient at x = xbar = E[x^2]/E[x] (a = E[x]; the lnD slot is 0)
+      MixedDraw k1 = lnl_mixed_draw<MM, RR, false, true>(P, sA, sg, dp, i);
+      float ex[2] = {1.f, 1.f};
+      const df marg = isnan(k1.lnl.hi) ? k1.lnl : dist_marg_df(dist, k1.lnl, k1.R, ex);
+      const float xbar = ex[1] / ex[0], sc = ex[0] / xbar;
+      o = lnl_mixed_draw<MM, RR, true, true>(P, sA, sg, dp, i, df{xbar, 0.f});
+      for (int p = 0; p < kNpar; ++p) o.grad[p] *= sc;
+      o.grad[5] = 0.0;
+      o.lnl = marg;
+      o.oob = k1.oob;
+    } else {
+      o = lnl_mixed_draw<MM, RR, GRAD, DIST>(P, sA, sg, dp, i);
+      if (DIST) o.lnl = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R);
+    }
     oob += o.oob;
     if (GRAD) {
       if (lnl_out) lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
@@ -668,7 +780,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(c
     } else {
       float lw = 0.f;
       if (dp.logw) lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
-      tlse_push(st, df_add_f(o.lnl, lw));
+      tlse_push_lw(st, o.lnl, lw);
     }
   }
   if (LSE) block_lse_write(st, partials + blockIdx.x);
@@ -689,6 +801,31 @@ cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const D
   *blocks = grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem);
   lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
   return cudaGetLastError();
+}
+
+template <int MM, int RR, bool LSE>
+cudaError_t launch_mixed_dist_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                const DistParams& dist, double* lnl_out, LseState* partials,
+                                unsigned long long* oob, int* blocks, cudaStream_t st) {
+  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
+                      (size_t)hp.ncls * hp.R * sizeof(float);
+  auto kern = lnl_mixed_kernel<MM, RR, LSE, false, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  *blocks = grid_for(kern, 128, smem);
+  kern<<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob, nullptr, dist);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_mixed_dist_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                 const DistParams& dist, double* lnl_out, LseState* partials,
+                                 unsigned long long* oob, int* blocks, cudaStream_t st) {
+  const bool wide = hp.R > MM;
+  if (partials)
+    return wide ? launch_mixed_dist_k<MM, 2 * MM, true>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st)
+                : launch_mixed_dist_k<MM, MM, true>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  return wide ? launch_mixed_dist_k<MM, 2 * MM, false>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st)
+              : launch_mixed_dist_k<MM, MM, false>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
 }
 
 template <int MM, int RR>
@@ -728,6 +865,54 @@ cudaError_t launch_mixed_grad_mm(const PointParams& hp, const PointParams* dP, c
 }
 
 }  // namespace
+
+cudaError_t launch_lnl_mixed_dist(const PointParams& hp, const PointParams* dP,
+                                  const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                  LseState* partials, unsigned long long* oob, int* blocks,
+                                  cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_mixed_dist_mm<2>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 4) return launch_mixed_dist_mm<4>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 6) return launch_mixed_dist_mm<6>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 8) return launch_mixed_dist_mm<8>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 10) return launch_mixed_dist_mm<10>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  if (M <= 12) return launch_mixed_dist_mm<12>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  return launch_mixed_dist_mm<16>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+}
+
+template <int MM, int RR>
+cudaError_t launch_mixed_grad_dist_mr(const PointParams& hp, const PointParams* dP,
+                                      const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                      double* grad_out, cudaStream_t st) {
+  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
+                      (size_t)hp.ncls * hp.R * sizeof(float);
+  auto kern = lnl_mixed_kernel<MM, RR, false, true, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const int blocks = grid_for(kern, 128, smem);
+  kern<<<blocks, 128, smem, st>>>(dP, dp, lnl_out, nullptr, nullptr, grad_out, dist);
+  return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_mixed_grad_dist_mm(const PointParams& hp, const PointParams* dP,
+                                      const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                      double* grad_out, cudaStream_t st) {
+  if (hp.R <= MM) return launch_mixed_grad_dist_mr<MM, MM>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  return launch_mixed_grad_dist_mr<MM, 2 * MM>(hp, dP, dp, dist, lnl_out, grad_out, st);
+}
+
+cudaError_t launch_grad_mixed_dist(const PointParams& hp, const PointParams* dP,
+                                   const DrawsParams& dp, const DistParams& dist, double* lnl_out,
+                                   double* grad_out, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_mixed_grad_dist_mm<2>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 4) return launch_mixed_grad_dist_mm<4>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 6) return launch_mixed_grad_dist_mm<6>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 8) return launch_mixed_grad_dist_mm<8>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 10) return launch_mixed_grad_dist_mm<10>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  if (M <= 12) return launch_mixed_grad_dist_mm<12>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  return launch_mixed_grad_dist_mm<16>(hp, dP, dp, dist, lnl_out, grad_out, st);
+}
 
 cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                               double* lnl_out, double* grad_out, cudaStream_t st) {
@@ -794,6 +979,78 @@ cudaError_t launch_lnl_mixed_sms(const PointParams& hp, const PointParams* dP, c
   if (M <= 10) return launch_mixed_mm_sms<10>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
   if (M <= 12) return launch_mixed_mm_sms<12>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
   return launch_mixed_mm_sms<16>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
+}
+
+
+// ------------------------------------------------------------ batched lnZ
+
+namespace {
+
+// Persistent kernel of rift_ile_batch: resident blocks take (point, tile)
+// items from the queue with an atomic ticket, restage the point's tables when
+// the point changes, and leave one LSE state per item.  No block waits on
+// another: a block stops when the ticket passes the end of the queue.
+template <int MM, int RR>
+__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
+    lnz_batch_kernel(const PointParams* const* __restrict__ pts, const DrawsParams* __restrict__ dps,
+                     const BatchItem* __restrict__ items, int n_items, unsigned int* __restrict__ head,
+                     LseState* __restrict__ partials, unsigned long long* __restrict__ oob_count) {
+  __shared__ PointParams P;
+  __shared__ DrawsParams sdp;
+  __shared__ int s_item;
+  extern __shared__ float4 smem4[];
+  int cur = -1;
+  int oob = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const BatchItem it = items[item];
+    if (it.point != cur) {
+      stage_point(P, pts[it.point]);
+      if (threadIdx.x == 0) sdp = dps[it.point];
+      __syncthreads();
+      stage_split_A(P, smem4);
+      __syncthreads();
+      cur = it.point;
+    }
+    const float4* sA = smem4;
+    const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.D);
+    ThreadLse st = tlse_init();
+    const long long end = it.begin + it.count;
+    for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
+      MixedDraw o = lnl_mixed_draw<MM, RR, false>(P, sA, sg, sdp, i);
+      oob += o.oob;
+      float lw = 0.f;
+      if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
+      tlse_push_lw(st, o.lnl, lw);
+    }
+    block_lse_write(st, partials + item);  // ends with every thread past its use of s_item
+    __syncthreads();
+  }
+  if (oob_count) {
+    for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
+    if ((threadIdx.x & 31) == 0 && oob) atomicAdd(oob_count, (unsigned long long)oob);
+  }
+}
+
+template <int MM>
+BatchKernelFn pick_batch_kernel(int R) {
+  if (R <= MM) return lnz_batch_kernel<MM, MM>;
+  return lnz_batch_kernel<MM, 2 * MM>;
+}
+
+}  // namespace
+
+BatchKernelFn batch_kernel_for(int M, int R) {
+  if (M <= 2) return pick_batch_kernel<2>(R);
+  if (M <= 4) return pick_batch_kernel<4>(R);
+  if (M <= 6) return pick_batch_kernel<6>(R);
+  if (M <= 8) return pick_batch_kernel<8>(R);
+  if (M <= 10) return pick_batch_kernel<10>(R);
+  if (M <= 12) return pick_batch_kernel<12>(R);
+  return pick_batch_kernel<16>(R);
 }
 
 }  // namespace rift

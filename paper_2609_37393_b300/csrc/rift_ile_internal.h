@@ -76,6 +76,17 @@ struct DrawsParams {
   int f64;
 };
 
+// Distance marginalisation table on the device: nodes x_j = D_ref/D_j in
+// decreasing order (increasing D) with ln w_j; n == 0 means no marginalisation.
+struct DistParams {
+  const double* x;
+  const double* lnw;
+  const float2* xdf;   // x_j as (hi, lo) for the FP32-mixed path
+  const float* lnwf;   // ln w_j in FP32
+  int n;
+  double lnw_max;
+};
+
 struct LseState {
   double m, s, s2, n;
 };

@@ -165,6 +165,24 @@ def test_nan_draw_and_out_of_table(R, cfg1_small):
         assert math.isnan(R.rift_ile_lnZ(pt, d, prec)[0])
 
 
+def test_zero_prior_weight_draws(R, cfg1_small):
+    """Draws with ln w = -inf (outside the prior) carry no weight; +inf
+    dominates; NaN poisons lnZ, as in the oracle."""
+    point, exact, info, draws, logw = cfg1_small
+    lw = np.asarray(logw, dtype=np.float32).copy()
+    lw[::7] = -np.inf
+    pt = R.Point(point)
+    ref = O.lnZ(O.lnL(O.OraclePoint(point), draws), lw.astype(np.float64))
+    for prec, tol in ((0, 1e-9), (1, 1e-4)):
+        got = R.rift_ile_lnZ(pt, R.Draws(draws, lw), prec)
+        assert abs(got[0] - ref[0]) <= tol * max(1.0, abs(ref[0]) if prec == 0 else 1.0), (prec, got, ref)
+        assert abs(got[2] - ref[2]) <= 1e-4 * ref[2]
+    lw2 = lw.copy()
+    lw2[3] = np.nan
+    for prec in (0, 1):
+        assert np.isnan(R.rift_ile_lnZ(pt, R.Draws(draws, lw2), prec)[0])
+
+
 def test_deterministic(R, cfg1_small):
     point, exact, info, draws, logw = cfg1_small
     pt = R.Point(point)
