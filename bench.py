@@ -15,6 +15,15 @@ path, the ALU roofline of the kernel, sampled clocks and the FP64 CPU oracle
 as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ile|batch|event]
+
+--workload batch times the 512-point batching workload (2-5 detectors, 2-10
+modes, 8k-65k-sample tables, 1e4-1e6 draws per point): one persistent
+FP32-mixed launch replayed from a CUDA graph against one FP64 launch per
+point.  --workload event times the full 3G event (ET triangle + CE 40 km +
+CE 20 km, SNR 1000, +-50 ms table, 2^26 draws in 2^22 chunks): distance-
+marginalised forward+backward and lnZ, FP32-mixed against FP64.  The default
+(ile) is the headline line.
 """
 from __future__ import annotations
 
@@ -37,26 +46,74 @@ N_DRAWS = 1 << 22
 WORKLOAD = "3G ILE: ET triangle + CE40 (K=4), 10 modes, SNR 600, 2^22 float32 draws"
 
 
-def algorithmic_ops(K: int, M: int, R: int, ncls: int) -> dict:
-    """Declared FP32-pipe operation count of one draw of the FP32-mixed lnL
-    (the arithmetic the method needs at the stated precision, double-float
-    steps charged at their FP32 operation counts: two-sum 6, two-product 2,
-    pair product 7, pair sum 20, anchored sine/cosine 90, anchored exp 50).
-    Overheads (addressing, loads, branches, the draw loop) are not counted."""
-    df_mul, df_add, sincos, expo = 7, 20, 90, 50
-    sky = 2 * sincos + 4 * df_mul + 20            # lam, dec, s and e2 products
-    angles = 2 * sincos                           # 2 psi, iota/2
-    per_mode_y = sincos + 10 * df_mul + 2 * df_add  # e^{i m phi}, Wigner-d polynomial, Y
-    matvec = R * M * 22 + 6 * M + 12 * R          # split product a1, a2
-    antenna = 15 * df_mul + 10 * df_add + 4 * df_mul + 2 * df_add
-    w = 19 * R + 2 * df_mul
-    time_ = 4 * df_mul + 4 * df_add + 8
-    poly = 6 * (6 + df_add)
-    residual = 4 * R * 4 + R + 2 * R + 45
-    per_det = antenna + w + time_ + poly + residual
-    total = expo + sky + angles + ncls * (M * per_mode_y + matvec) + K * per_det + 40
+def algorithmic_ops(point: dict, R: int, ncls: int) -> dict:
+    """Declared FP32-pipe operation count of one draw of the FP32-mixed lnL ->
+    LSE pass for this point: every FP32 add, multiply and fused multiply-add
+    the method's arithmetic takes at the stated precision (one op each), with
+    the double-float steps at their operation counts (TwoSum 6, FastTwoSum 3,
+    TwoProduct 2, pair product 7, pair sum 20, compensated multiply-add 12,
+    anchored sine/cosine 82, anchored exponential 44).  Addressing, loads,
+    comparisons and control are not counted."""
+    K, M = int(point["K"]), int(point["M"])
+    ell = [int(v) for v in point["ell"]]
+    em = [int(v) for v in point["em"]]
+    sincos, expo, df_mul, df_add = 82, 44, 7, 20
+    # distance factor, sky angles, sky direction, antenna basis, 2 psi, iota
+    fixed = (10 + expo) + (10 + 2 * sincos + 2 * df_mul) + 187 + (sincos + 2 * df_mul) + sincos
+    # modes: Horner in cos(iota) (15 per degree), sin(iota) factor for odd m,
+    # Y = amp e^{i m phi} and its split, one sine/cosine per change of |m|
+    n_phase = sum(1 for a in range(M) if a == 0 or abs(em[a]) != abs(em[a - 1]))
+    modes = sum(15 * l for l in ell) + df_mul * sum(1 for m in em if m % 2) + M * (2 * df_mul + 8)
+    modes += n_phase * sincos
+    matvec = 12 * R * M + 12 * R  # split product a1, a2 (12 per entry) and their two-sums
+    antenna = 10 * 12 + 2 * 3 + 4 * df_mul + 2 * df_add
+    template = 16 * R
+    timing = 2 * df_add + df_mul + 3 + 6 * 14 + 3 + 16 + 32 + 2  # position, 1/2|e|^2 sextic, weights
+    residual = 4 * 3 * R + 2 * R + R + 16                  # taps, sigma and low part, |r|^2, T
+    per_det = antenna + template + timing + residual
+    n_pos = len({tuple(np.round(np.asarray(point["det_pos"], dtype=np.float64)[k], 12))
+                 for k in range(K)})
+    delay = n_pos * (3 * df_mul + 2 * df_add)
+    lse = 17
+    total = fixed + ncls * (modes + matvec) + K * per_det + delay + lse
     return {"ops_per_draw": int(total), "per_detector": int(per_det),
-            "per_class": int(M * per_mode_y + matvec)}
+            "per_class": int(modes + matvec), "fixed": int(fixed + delay + lse)}
+
+
+# Sources the FP32-mixed kernels are compiled from; a DRAM traffic figure from
+# an ncu capture is reported only while these are unchanged since the capture.
+KERNEL_SOURCES = ("lnl_mixed_impl.cuh", "common.cuh", "dfloat.cuh", "rift_ile_internal.h")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "lnl_mixed_kernel_3g_k4_m10_snr600.md")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2609_37393_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic():
+    """(DRAM bytes per launch, draws per launch) of the dominant kernel from the
+    committed ncu summary, or None when the kernel sources changed since."""
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith(("kernel_source_sha256", "dram_bytes_per_launch",
+                                                    "draws_per_launch")):
+            k, v = line.strip().strip("`").split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"]), float(vals["draws_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def plain_formula_flops(K: int, M: int) -> int:
@@ -85,6 +142,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # the timed region starts once the sampler is producing rows
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -175,19 +236,155 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def timed_events(torch, fn, reps, stream):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _batch_point(i):
+    import workload as W
+    point, exact, info, d, lw = W.config3_point(i)
+    return point, d, lw
+
+
+def _event_chunk(c):
+    import workload as W
+    if c == 0:
+        point, exact, info, d, lw = W.config4(n_draws=N_DRAWS, chunk=0)
+        return point, info, d, lw
+    _, _, info, _, _ = W.config4(n_draws=1, chunk=0)
+    # chunk c of the event: the same draw stream config4(chunk=c) uses
+    d, lw = W.mixture_draws(np.random.default_rng(W.seed_for(4, 1 + c)), info["prior"],
+                            info["truth"], info["sigma"], N_DRAWS)
+    return None, None, W.as_float(d, np.float32), lw.astype(np.float32)
+
+
+def host_map(fn, items):
+    """Synthetic inputs are generated on the host in a spawn pool (started
+    before the first CUDA call)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = max(1, min(len(items), (os.cpu_count() or 1), 32))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, items))
+
+
+def run_batch(args):
+    """The batching workload: lnZ of 512 points in one persistent launch."""
+    t0 = time.perf_counter()
+    gen = host_map(_batch_point, list(range(args.points)))
+    import torch
+    import paper_2609_37393_b300 as R
+    torch.cuda.set_device(0)
+    n_points = args.points
+    pts, draws = [], []
+    total = 0
+    for point, d, lw in gen:
+        pts.append(R.Point(point))
+        draws.append(R.Draws(d, lw))
+        total += len(d["t"])
+    del gen
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    b32 = R.Batch(pts, draws, R.FP32_MIXED)
+    out = b32.launch()
+    for _ in range(args.warmup):
+        b32.launch(out)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b32.launch(out)
+    with ClockSampler(0) as clocks:
+        ms32 = timed_events(torch, g.replay, args.steps, stream)
+    b64 = R.Batch(pts, draws, R.FP64)
+    out64 = b64.launch()
+    ms64 = timed_events(torch, lambda: b64.launch(out64), 1, stream)
+    o32, o64 = out.cpu().numpy(), out64.cpu().numpy()
+    line = {
+        "metric": "lnZ of 512 intrinsic points (batched persistent launch)",
+        "workload": "batch", "value": total / (ms32 * 1e-3), "unit": "draws/s",
+        "points": n_points, "total_draws": total, "ms_per_batch": ms32,
+        "points_per_s": n_points / (ms32 * 1e-3),
+        "fp64_per_point_ms": ms64, "fp64_draws_per_s": total / (ms64 * 1e-3),
+        "speedup_vs_fp64_per_point": ms64 / ms32,
+        "max_abs_dlnZ_vs_fp64": float(np.nanmax(np.abs(o32[:, 0] - o64[:, 0]))),
+        "gpu_launches": 2 * args.steps, "graph": True, "setup_s": setup_s,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_event(args):
+    """The full 3G event: 2^26 draws in 2^22 chunks, distance marginalised."""
+    chunks = args.chunks
+    gen = host_map(_event_chunk, list(range(chunks)))
+    import torch
+    import paper_2609_37393_b300 as R
+    torch.cuda.set_device(0)
+    point, info = gen[0][0], gen[0][1]
+    pt = R.Point(point)
+    rho = math.sqrt(info["rho2"])
+    nodes = R.rift_ile_dist_nodes(50.0, 200.0, 100.0, 1e-4, 1000.0)
+    dev = [R.Draws(g[2], g[3]) for g in gen]
+    del gen
+    stream = torch.cuda.current_stream()
+    lnl = torch.empty(N_DRAWS, dtype=torch.float64, device="cuda")
+    grad = torch.empty((7, N_DRAWS), dtype=torch.float64, device="cuda")
+
+    def fwd_bwd(prec):
+        for d in dev:
+            R.rift_ile_lnL_dist(pt, d, nodes, prec, out=lnl, grad=True, grad_out=grad)
+
+    def lnz(prec):
+        return R.rift_ile_lnZ_merge([R.rift_ile_lnZ_state(pt, d, prec, dist=nodes) for d in dev])[0]
+
+    with ClockSampler(0) as clocks:
+        ms_fb32 = timed_events(torch, lambda: fwd_bwd(R.FP32_MIXED), 2, stream)
+        ms_z32 = timed_events(torch, lambda: lnz(R.FP32_MIXED), 2, stream)
+    ms_fb64 = timed_events(torch, lambda: fwd_bwd(R.FP64), 1, stream)
+    ms_z64 = timed_events(torch, lambda: lnz(R.FP64), 1, stream)
+    z32, z64 = lnz(R.FP32_MIXED), lnz(R.FP64)
+    n = chunks * N_DRAWS
+    line = {
+        "metric": "full 3G event: distance-marginalised lnL draws/s (fwd+bwd)",
+        "workload": "event", "value": n / (ms_fb32 * 1e-3), "unit": "draws/s", "draws": n,
+        "chunks": chunks, "snr": rho, "dist_nodes": len(nodes[0]),
+        "fwd_bwd_ms": ms_fb32, "fp64_fwd_bwd_draws_per_s": n / (ms_fb64 * 1e-3),
+        "lnZ_draws_per_s": n / (ms_z32 * 1e-3), "fp64_lnZ_draws_per_s": n / (ms_z64 * 1e-3),
+        "speedup_fwd_bwd_vs_fp64": ms_fb64 / ms_fb32, "lnZ": z32[0], "abs_dlnZ_vs_fp64": abs(z32[0] - z64[0]),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="ile", choices=["ile", "batch", "event"])
+    ap.add_argument("--points", type=int, default=512)
+    ap.add_argument("--chunks", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "event":
+        run_event(args)
         return
 
     import torch
@@ -237,6 +434,8 @@ def main():
     ms = float(ms_t.item())
     value = world * N_DRAWS / (ms * 1e-3)
     lnz = R.lnZ_from_state(state)
+    # the path's one exchange step: every rank's 32-byte LSE state, merged
+    merged = R.lnZ_merge_ranks(state)[0] if dist is not None else lnz
 
     # ---- variants (outside the timed region; same GPU)
     def timed(fn, reps):
@@ -306,12 +505,15 @@ def main():
 
     # ---- roofline of the dominant kernel (the fused lnL -> LSE kernel)
     pinfo = pt.info()
-    ops = algorithmic_ops(K, M, pinfo["R"], pinfo["ncls"])
+    ops = algorithmic_ops(point, pinfo["R"], pinfo["ncls"])
     achieved = ops["ops_per_draw"] * N_DRAWS / (ms * 1e-3)
+    tr = captured_traffic()
+    # bytes per launch of this step's size (traffic grows with the draws)
+    traffic = None if tr is None else tr[0] * N_DRAWS / tr[1]
     roofline = {
         "bound": "alu", "achieved": achieved / 1e12, "peak": fp32_ops / 1e12,
         "unit": "Tops/s (FP32-pipe ops, one FMA = one op)", "frac": achieved / fp32_ops,
-        "traffic": None,
+        "traffic": traffic,
         "ops_per_draw": ops["ops_per_draw"],
         "peak_source": f"measured FP32 FMA issue rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu)",
         "plain_formula_flops_per_draw": plain_formula_flops(K, M),
@@ -337,6 +539,8 @@ def main():
             "gpu_launches": 2 * args.steps,
             "variants": variants,
             "precision": precision,
+            "lnZ_all_ranks": {"lnZ": merged[0], "sigma_lnZ": merged[1], "n_eff": merged[2],
+                              "draws": world * N_DRAWS},
             "roofline": roofline,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,

@@ -358,6 +358,73 @@ class Batch:
             pass
 
 
+def _make_autograd():
+    torch = _torch()
+
+    class LnLFunction(torch.autograd.Function):
+        """lnL per draw as a differentiable function of the seven extrinsic
+        parameter tensors (Sec. II.B: gradient-based extrinsic sampling).
+
+        When any parameter needs a gradient the forward launches the fused
+        lnL + adjoint kernel once and keeps the [7, n] gradient; with
+        recompute=True it launches the forward-only kernel and the backward
+        launches the adjoint kernel again on the saved parameters (less memory,
+        one more pass).  Backward returns grad_output * d lnL / d theta in the
+        parameters' dtype.  With a distance table the lnD component is zero."""
+
+        @staticmethod
+        def forward(ctx, point, precision, dist, recompute, *theta):
+            draws = Draws({p: x.detach() for p, x in zip(PARAMS, theta)})
+            need = any(ctx.needs_input_grad[4:])
+            ctx.point, ctx.precision, ctx.dist = point, precision, dist
+            ctx.dtypes = [x.dtype for x in theta]
+            ctx.grad = None
+            if need and recompute:
+                ctx.save_for_backward(*[x.detach() for x in theta])
+            if dist is not None:
+                if need and not recompute:
+                    lnl, ctx.grad = rift_ile_lnL_dist(point, draws, dist, precision, grad=True)
+                else:
+                    lnl = rift_ile_lnL_dist(point, draws, dist, precision)
+            elif need and not recompute:
+                lnl, ctx.grad = rift_ile_lnL_grad(point, draws, precision)
+            else:
+                lnl = rift_ile_lnL(point, draws, precision)
+            return lnl
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g = ctx.grad
+            if g is None:
+                theta = ctx.saved_tensors
+                draws = Draws(dict(zip(PARAMS, theta)))
+                if ctx.dist is not None:
+                    _, g = rift_ile_lnL_dist(ctx.point, draws, ctx.dist, ctx.precision, grad=True)
+                else:
+                    _, g = rift_ile_lnL_grad(ctx.point, draws, ctx.precision)
+            ctx.grad = None
+            grads = [None] * 4
+            for j in range(7):
+                grads.append((g[j] * grad_out).to(ctx.dtypes[j])
+                             if ctx.needs_input_grad[4 + j] else None)
+            return tuple(grads)
+
+    return LnLFunction
+
+
+_LnLFunction = None
+
+
+def lnL(point: Point, ra, dec, psi, incl, phase, lnD, t, precision: int = FP32_MIXED,
+        dist=None, recompute: bool = False):
+    """Differentiable lnL[n] (float64) of CUDA tensors of draws (torch autograd);
+    dist = (x_nodes, lnw_nodes) marginalises the distance (eq. ap:dexp)."""
+    global _LnLFunction
+    if _LnLFunction is None:
+        _LnLFunction = _make_autograd()
+    return _LnLFunction.apply(point, precision, dist, recompute, ra, dec, psi, incl, phase, lnD, t)
+
+
 def rift_ile_dist_nodes(d_min, d_max, d_ref, tol, rho_max, max_nodes=1 << 16):
     """Log-uniform lnD node table of eq. ap:dlog: (x_j, ln w_j)."""
     x = np.empty(max_nodes)
@@ -383,6 +450,29 @@ def rift_ile_probe_alu(which: int, target_seconds: float = 0.2):
 
 def rift_ile_release():
     _check(_lib.rift_ile_release())
+
+
+def shard_bounds(n: int, rank: int, world: int):
+    """Contiguous slice [a, b) of n draws (or points) owned by `rank` of
+    `world`: the draws of one point and the points of a batch are
+    independent, so ranks share nothing but the final LSE states."""
+    if world < 1 or not 0 <= rank < world or n < 0:
+        raise ValueError(f"bad shard request n={n} rank={rank} world={world}")
+    q, r = divmod(n, world)
+    a = rank * q + min(rank, r)
+    return a, a + q + (1 if rank < r else 0)
+
+
+def lnZ_merge_ranks(state, group=None):
+    """The one exchange step of a draw-sharded lnZ: every rank contributes its
+    LSE state (m, s, s2, n) and all ranks get ((lnZ, sigma, n_eff), merged
+    state) from rift_ile_lnZ_merge over the states in rank order (an
+    all-gather of 32 bytes per rank through torch.distributed)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    states = [None] * world
+    dist.all_gather_object(states, tuple(float(v) for v in state), group=group)
+    return rift_ile_lnZ_merge(states)
 
 
 def lnZ_from_state(state):

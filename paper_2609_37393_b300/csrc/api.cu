@@ -69,29 +69,17 @@ int get_workspace(Workspace** out) {
 
 // Merges the per-block states in a fixed order (one block of 256 threads:
 // thread t folds partials t, t+256, ...; thread 0 folds the 256 results).
-__global__ void lse_combine_kernel(const LseState* __restrict__ partials, int nparts,
-                                   double n_total, LseState* __restrict__ out) {
-  __shared__ LseState part[256];
+__global__ void __launch_bounds__(1024) lse_combine_kernel(const LseState* __restrict__ partials,
+                                                           int nparts, double n_total,
+                                                           LseState* __restrict__ out) {
+  // each thread merges a fixed strided subset in index order, then a fixed tree
   LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
-  int nan_any = 0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    LseState p = partials[i];
-    if (isnan(p.m)) nan_any = 1;
-    else acc = lse_merge(acc, p);
-  }
-  if (nan_any) acc.m = CUDART_NAN;
-  part[threadIdx.x] = acc;
-  __syncthreads();
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc = lse_merge(acc, partials[i]);
+  acc = block_lse_reduce(acc);
   if (threadIdx.x == 0) {
-    LseState tot{-CUDART_INF, 0.0, 0.0, 0.0};
-    bool bad = false;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      if (isnan(part[t].m)) bad = true;
-      else tot = lse_merge(tot, part[t]);
-    }
-    tot.n = n_total;
-    if (bad) tot.m = tot.s = tot.s2 = CUDART_NAN;
-    *out = tot;
+    acc.n = n_total;
+    if (isnan(acc.m)) acc.m = acc.s = acc.s2 = CUDART_NAN;
+    *out = acc;
   }
 }
 
@@ -220,7 +208,7 @@ int device_sms() {
 
 cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
                                LseState* state_out, cudaStream_t st) {
-  lse_combine_kernel<<<1, 256, 0, st>>>(partials, nparts, n_total, state_out);
+  lse_combine_kernel<<<1, 1024, 0, st>>>(partials, nparts, n_total, state_out);
   return cudaGetLastError();
 }
 

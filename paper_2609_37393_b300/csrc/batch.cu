@@ -29,22 +29,21 @@ __global__ void fill_empty_kernel(LseState* __restrict__ st, long long n) {
 }
 
 // out[p] = (lnZ, sigma_lnZ, n_eff) from the states of point p's items
-// [first[p], first[p+1]), merged in item order.
+// [first[p], first[p+1]): one warp per point, each lane merging a fixed
+// strided subset in item order, then a fixed shuffle tree.
 __global__ void batch_combine_kernel(const LseState* __restrict__ partials,
                                      const int* __restrict__ first, const double* __restrict__ ndraws,
                                      int P, double* __restrict__ out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+  const int p = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= P) return;  // whole warps leave together
   LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
-  bool bad = false;
-  for (int i = first[p]; i < first[p + 1]; ++i) {
-    const LseState s = partials[i];
-    if (isnan(s.m)) bad = true;
-    else acc = lse_merge(acc, s);
-  }
+  for (int i = first[p] + lane; i < first[p + 1]; i += 32) acc = lse_merge(acc, partials[i]);
+  acc = warp_lse_reduce(acc);
+  if (lane != 0) return;
   const double n = ndraws[p];
   double lnz, sig, neff;
-  if (bad) {
+  if (isnan(acc.m)) {
     lnz = sig = neff = CUDART_NAN;
   } else if (n <= 0.0 || !(acc.m > -CUDART_INF)) {
     lnz = -CUDART_INF;
@@ -159,8 +158,6 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
     nd[p] = (double)d->n;
     maxM = std::max(maxM, pt->host.M);
     maxR = std::max(maxR, pt->host.R);
-    smem = std::max(smem, (size_t)pt->host.ncls * pt->host.R * pt->host.D * sizeof(float4) +
-                              (size_t)pt->host.ncls * pt->host.R * sizeof(float));
     first[p] = (int)items.size();
     for (long long a = 0; a < d->n; a += kTileDraws)
       items.push_back(BatchItem{a, (int)std::min<long long>(kTileDraws, d->n - a), p});
@@ -169,6 +166,9 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
   first[P] = (int)items.size();
   b->dps = hd;
   if (!rc && prec == RIFT_ILE_FP32_MIXED) {
+    for (int p = 0; p < P; ++p)
+      smem = std::max(smem, batch_smem_for(maxM, maxR, pts[p]->host.ncls, pts[p]->host.R,
+                                           pts[p]->host.M));
     b->n_items = (int)items.size();
     b->kernel = batch_kernel_for(maxM, maxR);
     b->smem = smem;
@@ -232,8 +232,8 @@ extern "C" int rift_ile_batch_launch(rift_ile_batch* b, double* out, void* strea
       if ((rc = check_cuda(e, "batch FP64 launch"))) return rc;
     }
   }
-  batch_combine_kernel<<<(b->P + 127) / 128, 128, 0, st>>>(b->d_partials, b->d_first, b->d_ndraws,
-                                                           b->P, out);
+  batch_combine_kernel<<<(b->P + 3) / 4, 128, 0, st>>>(b->d_partials, b->d_first, b->d_ndraws,
+                                                       b->P, out);
   return check_cuda(cudaGetLastError(), "batch combine launch");
 }
 

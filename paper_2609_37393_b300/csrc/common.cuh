@@ -225,13 +225,49 @@ __device__ __forceinline__ void tlse_push_lw(ThreadLse& t, df lnl, float lw) {
   tlse_push(t, df_add_f(lnl, lw));
 }
 
+// Exact merge of two states: the smaller maximum is rescaled to the larger
+// one (one exponential; FP64 is slow on this part, so merges stay few).
 __device__ __forceinline__ LseState lse_merge(LseState a, LseState b) {
   if (isnan(a.m) || isnan(b.m)) return LseState{CUDART_NAN, CUDART_NAN, CUDART_NAN, a.n + b.n};
   if (a.m == -CUDART_INF) return LseState{b.m, b.s, b.s2, a.n + b.n};
   if (b.m == -CUDART_INF) return LseState{a.m, a.s, a.s2, a.n + b.n};
-  double M = fmax(a.m, b.m);
-  double ea = exp(a.m - M), eb = exp(b.m - M);
-  return LseState{M, a.s * ea + b.s * eb, a.s2 * ea * ea + b.s2 * eb * eb, a.n + b.n};
+  if (a.m >= b.m) {
+    const double e = exp(b.m - a.m);
+    return LseState{a.m, fma(b.s, e, a.s), fma(b.s2, e * e, a.s2), a.n + b.n};
+  }
+  const double e = exp(a.m - b.m);
+  return LseState{b.m, fma(a.s, e, b.s), fma(a.s2, e * e, b.s2), a.n + b.n};
+}
+
+__device__ __forceinline__ LseState lse_shfl_down(LseState v, int off) {
+  LseState o;
+  o.m = __shfl_down_sync(0xffffffffu, v.m, off);
+  o.s = __shfl_down_sync(0xffffffffu, v.s, off);
+  o.s2 = __shfl_down_sync(0xffffffffu, v.s2, off);
+  o.n = __shfl_down_sync(0xffffffffu, v.n, off);
+  return o;
+}
+
+// Merge of the 32 lanes' states into lane 0 by a fixed shuffle tree (the
+// same pairing every call, so the result is reproducible bit for bit).
+__device__ __forceinline__ LseState warp_lse_reduce(LseState v) {
+  for (int off = 16; off > 0; off >>= 1) v = lse_merge(v, lse_shfl_down(v, off));
+  return v;
+}
+
+// Merge of one state per thread into thread 0 (blockDim a multiple of 32,
+// at most 1024): shuffle trees within and then across warps.
+__device__ __forceinline__ LseState block_lse_reduce(LseState v) {
+  __shared__ LseState warp_part[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_lse_reduce(v);
+  if (lane == 0) warp_part[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < nw ? warp_part[lane] : LseState{-CUDART_INF, 0.0, 0.0, 0.0};
+    v = warp_lse_reduce(v);
+  }
+  return v;
 }
 
 // Block-level reduction of the per-thread states; thread 0 writes the block
@@ -320,31 +356,9 @@ __device__ __forceinline__ void tlse64_push(ThreadLse64& t, double v) {
 }
 
 __device__ __forceinline__ void block_lse64_write(ThreadLse64 t, LseState* out) {
-  for (int off = 16; off > 0; off >>= 1) {
-    LseState o;
-    o.m = __shfl_down_sync(0xffffffffu, t.st.m, off);
-    o.s = __shfl_down_sync(0xffffffffu, t.st.s, off);
-    o.s2 = __shfl_down_sync(0xffffffffu, t.st.s2, off);
-    o.n = 0.0;
-    t.nan_seen |= __shfl_down_sync(0xffffffffu, t.nan_seen, off);
-    t.st = lse_merge(t.st, o);
-  }
-  __shared__ LseState warp_state64[32];
-  __shared__ int warp_nan64[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    warp_state64[wid] = t.st;
-    warp_nan64[wid] = t.nan_seen;
-  }
-  __syncthreads();
+  const int nan_any = __syncthreads_or(t.nan_seen);
+  LseState acc = block_lse_reduce(t.st);
   if (threadIdx.x == 0) {
-    LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
-    int nan_any = 0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int w = 0; w < nw; ++w) {
-      acc = lse_merge(acc, warp_state64[w]);
-      nan_any |= warp_nan64[w];
-    }
     acc.n = 0.0;
     if (nan_any) acc.m = acc.s = acc.s2 = CUDART_NAN;
     *out = acc;

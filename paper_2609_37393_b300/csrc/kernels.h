@@ -29,6 +29,8 @@ typedef void (*BatchKernelFn)(const PointParams* const*, const DrawsParams*, con
 // The persistent FP32-mixed batch kernel for the largest M and R of a batch
 // (launch with 128 threads and the largest table smem of the batch).
 BatchKernelFn batch_kernel_for(int M, int R);
+// Its dynamic shared memory for one point (ncls classes, width Rp, Mp modes).
+size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp);
 
 // lnL (lnl_out may be NULL) and its gradient, grad_out[7][n].
 cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,

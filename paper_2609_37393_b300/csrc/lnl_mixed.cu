@@ -1,52 +1,42 @@
-// FP32-mixed likelihood kernels.
-//
-// The same lnL as the FP64 path (eq. def:lnL:Decomposed), arranged for a GPU
-// whose FP64 pipe is ~60x narrower than its FP32 pipe.  Per detector, in the
-// whitened coordinates built by point.cu,
-//     lnL_k = 1/2 |e(t_k)|^2 - 1/2 |e(t_k) - w_k|^2,
-//     w_k = x (Re F_k a1 + Im F_k a2),  a1 = A y,  a2 = A J y,  y = (Re Y, Im Y),
-// where a1 and a2 are shared by the detectors of one class.
-//
-// Precision: a rounding of the template w by a relative eps moves lnL by
-// <delta h | d - h> ~ eps rho |d - h|, i.e. ~1e-3 nat at rho = 1000 for
-// FP32's eps = 6e-8 at 50 nat from the peak.  So the template is carried to
-// ~1e-10: the sky angles, psi, iota/2, m phi go through an anchored
-// double-float sine/cosine, x through an anchored double-float exponential,
-// Y_lm, F_k and w in double-float, and a1, a2 through an error-free split
-// product (the head/tail split in lnl_mixed_draw).  The arrival time is also double-float (1 ns
-// is ~1e-3 nat).  1/2|e|^2 comes from the tabulated interval polynomial by
-// double-float Horner; only the residual e - w, which is small where the
-// likelihood matters, is formed in FP32 (its error enters as
-// (e - w) . delta, ~1e-5 nat).
+// Host side of the FP32-mixed path: the anchor tables of the double-float
+// sine/cosine and exponential, and the dispatch of a point's mode count M to
+// the kernels instantiated for MM >= M (one translation unit per MM,
+// lnl_mixed_m*.cu, so that the compiler front end runs on them in parallel).
 #include <cuda_runtime.h>
-#include <math_constants.h>
 
 #include <cmath>
 #include <mutex>
 
-#include "common.cuh"
 #include "kernels.h"
-
-// Tuning knobs (compile-time): the minimum resident blocks per SM given to
-// __launch_bounds__, and whether the large double-float helpers are real
-// calls (smaller code, fewer instruction-cache misses) or inlined.
-#ifndef RIFT_MIXED_MIN_BLOCKS
-#define RIFT_MIXED_MIN_BLOCKS 4
-#endif
-#ifndef RIFT_MIXED_NOINLINE
-#define RIFT_MIXED_NOINLINE 0
-#endif
-#if RIFT_MIXED_NOINLINE
-#define RIFT_HELPER __device__ __noinline__
-#else
-#define RIFT_HELPER __device__ __forceinline__
-#endif
+#include "rift_ile_internal.h"
 
 namespace rift {
 
-__device__ float4 g_anchor[2 * kAnchorHalf + 1];  // (sin hi, sin lo, cos hi, cos lo) of j 2^-7
-__device__ float2 g_exp_anchor[2 * kExpHalf + 1];  // e^(j/128) as (hi, lo)
+template <int MM>
+cudaError_t mixed_lnl(const PointParams&, const PointParams*, const DrawsParams&, double*,
+                      LseState*, unsigned long long*, int*, cudaStream_t);
+template <int MM>
+cudaError_t mixed_lnl_sms(const PointParams&, const PointParams*, const DrawsParams&, double*,
+                          LseState*, unsigned long long*, int, int*, cudaStream_t);
+template <int MM>
+cudaError_t mixed_dist(const PointParams&, const PointParams*, const DrawsParams&,
+                       const DistParams&, double*, LseState*, unsigned long long*, int*,
+                       cudaStream_t);
+template <int MM>
+cudaError_t mixed_grad(const PointParams&, const PointParams*, const DrawsParams&, double*,
+                       double*, cudaStream_t);
+template <int MM>
+cudaError_t mixed_grad_dist(const PointParams&, const PointParams*, const DrawsParams&,
+                            const DistParams&, double*, double*, cudaStream_t);
+template <int MM>
+BatchKernelFn mixed_batch_kernel(int R);
+template <int MM>
+size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp);
+template <int MM>
+int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab);
 
+// Sine/cosine of a_j = j 2^-7 and e^(j/128) as (hi, lo) float pairs, copied
+// into every mode-count unit's tables once per device.
 int ensure_anchor_table() {
   static std::mutex mu;
   static bool done[64] = {false};
@@ -70,987 +60,61 @@ int ensure_anchor_table() {
     float hi = (float)v;
     e[j + kExpHalf] = make_float2(hi, (float)(v - hi));
   }
-  int rc = check_cuda(cudaMemcpyToSymbol(g_anchor, h, sizeof(h)), "anchor table upload");
-  if (!rc) rc = check_cuda(cudaMemcpyToSymbol(g_exp_anchor, e, sizeof(e)), "exp table upload");
+  int rc = mixed_upload_anchors<2>(h, e);
+  if (!rc) rc = mixed_upload_anchors<4>(h, e);
+  if (!rc) rc = mixed_upload_anchors<6>(h, e);
+  if (!rc) rc = mixed_upload_anchors<8>(h, e);
+  if (!rc) rc = mixed_upload_anchors<10>(h, e);
+  if (!rc) rc = mixed_upload_anchors<12>(h, e);
+  if (!rc) rc = mixed_upload_anchors<16>(h, e);
   if (!rc) done[dev] = true;
   return rc;
 }
 
-namespace {
+// Calls F<MM>(args...) for the smallest instantiated MM >= M.
+#define RIFT_DISPATCH_M(M, F, ...)                  \
+  ((M) <= 2    ? F<2>(__VA_ARGS__)                  \
+   : (M) <= 4  ? F<4>(__VA_ARGS__)                  \
+   : (M) <= 6  ? F<6>(__VA_ARGS__)                  \
+   : (M) <= 8  ? F<8>(__VA_ARGS__)                  \
+   : (M) <= 10 ? F<10>(__VA_ARGS__)                 \
+   : (M) <= 12 ? F<12>(__VA_ARGS__)                 \
+               : F<16>(__VA_ARGS__))
 
-// sin and cos of a double-float angle to ~1e-15 absolute: reduce by 2 pi (pair
-// constant), take the nearest anchor a_j = j 2^-7, and add the residual
-// d (|d| <= 2^-8) through sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24.
-RIFT_HELPER void sincos_df(df a, df& s_out, df& c_out) {
-  const float kTwoPiHi = 6.28318548202514648f;
-  const float kTwoPiLo = -1.7484555314695172e-07f;
-  float k = rintf(a.hi * 0.159154943091895336f);
-  df kp = two_prod(k, kTwoPiHi);
-  kp.lo = fmaf(k, kTwoPiLo, kp.lo);
-  df r = df_add(a, df_neg(kp));
-  int j = __float2int_rn(r.hi * kAnchorInvStep);
-  j = max(-kAnchorHalf, min(kAnchorHalf, j));
-  const float dh = __fsub_rn(r.hi, (float)j * kAnchorStep);  // exact
-  const float dl = r.lo;
-  const float d2 = dh * dh;
-  const float sb = fmaf(dh * d2, fmaf(d2, 1.f / 120.f, -1.f / 6.f), dl);  // sin d - dh
-  const float cb = fmaf(d2, fmaf(d2, 1.f / 24.f, -0.5f), -dh * dl);       // cos d - 1
-  const float4 an = g_anchor[j + kAnchorHalf];
-  // sin(a_j + d) = S (1 + cb) + C (dh + sb);  cos(a_j + d) = C (1 + cb) - S (dh + sb)
-  df p = two_prod(an.z, dh);
-  p.lo = fmaf(an.w, dh, p.lo);
-  p.lo = fmaf(an.z, sb, p.lo);
-  p.lo = fmaf(an.x, cb, p.lo);
-  s_out = df_add(df{an.x, an.y}, p);
-  df q = two_prod(an.x, dh);
-  q.lo = fmaf(an.y, dh, q.lo);
-  q.lo = fmaf(an.x, sb, q.lo);
-  q.lo = fmaf(-an.z, cb, q.lo);
-  c_out = df_add(df{an.z, an.w}, df_neg(q));
+cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                             double* lnl_out, LseState* partials, unsigned long long* oob,
+                             int* blocks, cudaStream_t st) {
+  return RIFT_DISPATCH_M(hp.M, mixed_lnl, hp, dP, dp, lnl_out, partials, oob, blocks, st);
 }
 
-// e^a for a double-float a: a = k ln2 + j/128 + d, |d| <= 2^-8, e^d by its
-// Taylor series to d^4, anchors e^(j/128) from the table.
-RIFT_HELPER df exp_df(df a) {
-  const float kLn2Hi = 0.693147182464599609f;
-  const float kLn2Lo = -1.904654323148236e-09f;
-  float k = rintf(a.hi * 1.44269504088896341f);
-  df kp = two_prod(k, kLn2Hi);
-  kp.lo = fmaf(k, kLn2Lo, kp.lo);
-  df r = df_add(a, df_neg(kp));
-  int j = __float2int_rn(r.hi * 128.f);
-  j = max(-kExpHalf, min(kExpHalf, j));
-  const float dh = __fsub_rn(r.hi, (float)j * (1.f / 128.f));
-  const float d = dh + r.lo;
-  // e^d - 1 - dh = r.lo + d^2/2 + d^3/6 + d^4/24
-  const float tail = fmaf(d * d, fmaf(d, fmaf(d, 1.f / 24.f, 1.f / 6.f), 0.5f), r.lo);
-  df ed = fast_two_sum(1.f, dh);
-  ed.lo = __fadd_rn(ed.lo, tail);
-  const float2 an = g_exp_anchor[j + kExpHalf];
-  df v = df_mul(df{an.x, an.y}, ed);
-  const int ki = (int)k;
-  return df{ldexpf(v.hi, ki), ldexpf(v.lo, ki)};
+cudaError_t launch_lnl_mixed_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                                 double* lnl_out, LseState* partials, unsigned long long* oob,
+                                 int sms, int* blocks, cudaStream_t st) {
+  return RIFT_DISPATCH_M(hp.M, mixed_lnl_sms, hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
 }
-
-__device__ __forceinline__ df df_pow(df b, int n) {
-  df r = df{1.f, 0.f};
-  for (int q = 0; q < n; ++q) r = df_mul(r, b);
-  return r;
-}
-
-// |-2Y_lm| part of mode i in double-float from c = cos(iota/2), s = sin(iota/2):
-// sum_r a_r c^(k0+2r) s^(2l-k0-2r) (the Wigner-d polynomial of the point).
-RIFT_HELPER df sylm_amp_df(const PointParams& P, int i, df c, df s) {
-  const int l = P.ell[i], nt = P.ynt[i], k0 = P.yk0[i];
-  df pre = df_mul(df_pow(c, k0), df_pow(s, 2 * l - k0 - 2 * (nt - 1)));
-  df poly = df{P.ycoef_hi[i][nt - 1], P.ycoef_lo[i][nt - 1]};
-  if (nt > 1) {
-    const df X = df_mul(c, c), Ys = df_mul(s, s);
-    df yp = df{1.f, 0.f};
-    for (int r = nt - 2; r >= 0; --r) {
-      yp = df_mul(yp, Ys);
-      poly = df_add(df_mul(poly, X), df_mul(df{P.ycoef_hi[i][r], P.ycoef_lo[i][r]}, yp));
-    }
-  }
-  return df_mul(pre, poly);
-}
-
-// Complex product of pairs.
-__device__ __forceinline__ void cmul_df(df ar, df ai, df br, df bi, df& cr, df& ci) {
-  cr = df_add(df_mul(ar, br), df_neg(df_mul(ai, bi)));
-  ci = df_add(df_mul(ar, bi), df_mul(ai, br));
-}
-
-// Sky functions shared by all detectors: with e1 = (-sl, cl, 0) and
-// e2 = (-sd cl, -sd sl, cd) (sl, cl = sin, cos of ra - gmst; sd, cd of dec),
-//   F_+(0) = e1.D.e1 - e2.D.e2 = Dxx b0 + Dyy b1 + Dxy b2 + Dxz b3 + Dyz b4 + Dzz b5,
-//   F_x(0) = 2 e1.D.e2 = (Dxx - Dyy) g0 + Dxy g1 + Dxz g2 + Dyz g3,
-// b = (sl^2 - sd^2 cl^2, cl^2 - sd^2 sl^2, -2 sl cl (1 + sd^2), 2 sd cd cl,
-//      2 sd cd sl, -cd^2),  g = (2 sd sl cl, 2 sd (sl^2 - cl^2), -2 sl cd, 2 cl cd).
-struct AntennaBasis {
-  df b[6], g[4];
-};
-
-RIFT_HELPER void antenna_basis(df sl, df cl, df sd, df cd, AntennaBasis& B) {
-  const df sl2 = df_mul(sl, sl), cl2 = df_mul(cl, cl), slcl = df_mul(sl, cl);
-  const df sd2 = df_mul(sd, sd), sdcd = df_mul(sd, cd), cd2 = df_mul(cd, cd);
-  B.b[0] = df_sub(sl2, df_mul(sd2, cl2));
-  B.b[1] = df_sub(cl2, df_mul(sd2, sl2));
-  const df t = df_mul(slcl, df_add_f(sd2, 1.f));
-  B.b[2] = df{-2.f * t.hi, -2.f * t.lo};
-  const df u = df_mul(sdcd, cl), v = df_mul(sdcd, sl);
-  B.b[3] = df{2.f * u.hi, 2.f * u.lo};
-  B.b[4] = df{2.f * v.hi, 2.f * v.lo};
-  B.b[5] = df_neg(cd2);
-  const df w = df_mul(sd, slcl);
-  B.g[0] = df{2.f * w.hi, 2.f * w.lo};
-  const df z = df_mul(sd, df_sub(sl2, cl2));
-  B.g[1] = df{2.f * z.hi, 2.f * z.lo};
-  const df a = df_mul(sl, cd), c = df_mul(cl, cd);
-  B.g[2] = df{-2.f * a.hi, -2.f * a.lo};
-  B.g[3] = df{2.f * c.hi, 2.f * c.lo};
-}
-
-// acc += a * b for pairs, the hi*hi product exact.
-__device__ __forceinline__ void dacc_fma_dd(dacc& acc, df a, df b) {
-  const df p = two_prod(a.hi, b.hi);
-  const df t = two_sum(acc.s, p.hi);
-  acc.s = t.hi;
-  float c = __fadd_rn(acc.c, __fadd_rn(t.lo, p.lo));
-  c = fmaf(a.hi, b.lo, c);
-  acc.c = fmaf(a.lo, b.hi, c);
-}
-
-// x F_k = x e^{2 i psi} (F_+(0) - i F_x(0)) of detector k, with xe = x e^{2 i psi}.
-RIFT_HELPER void antenna_df(const PointParams& P, int k, const AntennaBasis& B, df xer, df xei,
-                            df& xFr, df& xFi) {
-  dacc fp = dacc_zero(), fx = dacc_zero();
-#pragma unroll
-  for (int i = 0; i < 6; ++i) dacc_fma_dd(fp, df{P.acoef_hi[k][i], P.acoef_lo[k][i]}, B.b[i]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) dacc_fma_dd(fx, df{P.acoef_hi[k][6 + i], P.acoef_lo[k][6 + i]}, B.g[i]);
-  const df f0r = dacc_result(fp), f0x = dacc_result(fx);
-  // (f0r - i f0x)(xer + i xei)
-  xFr = df_add(df_mul(f0r, xer), df_mul(f0x, xei));
-  xFi = df_sub(df_mul(f0r, xei), df_mul(f0x, xer));
-}
-
-// FP32 amplitude of mode i and its derivative with respect to iota (used by
-// the adjoint, whose terms multiply the small residual and need only FP32):
-// d/d iota [c^p s^q] = (-p c^(p-1) s^(q+1) + q c^(p+1) s^(q-1)) / 2.
-__device__ __forceinline__ void sylm_amp_grad_f(const PointParams& P, int i, float c, float s,
-                                                float& amp, float& damp) {
-  const int l = P.ell[i], nt = P.ynt[i], k0 = P.yk0[i];
-  amp = 0.f;
-  damp = 0.f;
-  for (int r = 0; r < nt; ++r) {
-    const int p = k0 + 2 * r, q = 2 * l - p;
-    float cp = 1.f, sq = 1.f;
-    for (int u = 0; u < p - 1; ++u) cp *= c;  // c^(p-1)
-    for (int u = 0; u < q - 1; ++u) sq *= s;  // s^(q-1)
-    const float a = P.ycoef_hi[i][r];
-    const float cpf = (p > 0) ? cp * c : 1.f, sqf = (q > 0) ? sq * s : 1.f;
-    amp = fmaf(a, cpf * sqf, amp);
-    float d = 0.f;
-    if (p > 0) d -= p * cp * sqf * s;
-    if (q > 0) d += q * cpf * c * sq;
-    damp = fmaf(0.5f * a, d, damp);
-  }
-}
-
-// d(beta_i)/d(ra), d(beta_i)/d(dec) and the same for gamma (FP32; see AntennaBasis).
-struct AntennaBasisGrad {
-  float ba[6], bd[6], ga[4], gd[4];
-};
-
-__device__ __forceinline__ void antenna_basis_grad(float sl, float cl, float sd, float cd,
-                                                   AntennaBasisGrad& G) {
-  const float sd2 = sd * sd, slcl = sl * cl, c2 = cl * cl - sl * sl, dd = cd * cd - sd * sd;
-  G.ba[0] = 2.f * slcl * (1.f + sd2);
-  G.bd[0] = -2.f * sd * cd * cl * cl;
-  G.ba[1] = -2.f * slcl * (1.f + sd2);
-  G.bd[1] = -2.f * sd * cd * sl * sl;
-  G.ba[2] = -2.f * c2 * (1.f + sd2);
-  G.bd[2] = -4.f * slcl * sd * cd;
-  G.ba[3] = -2.f * sd * cd * sl;
-  G.bd[3] = 2.f * dd * cl;
-  G.ba[4] = 2.f * sd * cd * cl;
-  G.bd[4] = 2.f * dd * sl;
-  G.ba[5] = 0.f;
-  G.bd[5] = 2.f * cd * sd;
-  G.ga[0] = 2.f * sd * c2;
-  G.gd[0] = 2.f * cd * slcl;
-  G.ga[1] = 8.f * sd * slcl;
-  G.gd[1] = -2.f * cd * c2;
-  G.ga[2] = -2.f * cl * cd;
-  G.gd[2] = 2.f * sl * sd;
-  G.ga[3] = -2.f * sl * cd;
-  G.gd[3] = -2.f * cl * sd;
-}
-
-// The error-free split of a mode value y (|y| < 2): y1 = y rounded to a
-// multiple of 2^-8 (9 significant bits), y2 = y - y1 exact.
-__device__ __forceinline__ void split_y(float y, float& y1, float& y2) {
-  const float C = 49152.0f;  // 1.5 * 2^15: ulp(C) = 2^-8
-  y1 = __fsub_rn(__fadd_rn(y, C), C);
-  y2 = __fsub_rn(y, y1);
-}
-
-struct MixedDraw {
-  df lnl;      // lnL, or with DIST the data term K at x = 1
-  df R;        // with DIST: the quadratic coefficient R at x = 1 (lnL(x) = K x - R x^2/2)
-  int oob;
-  double grad[kNpar];
-};
-
-// Distance marginal of one draw from K and R (eq. ap:dexp, eq. ap:dlog):
-// K^2/(2R) in double-float plus the node sum of dist_lse, in FP32 offsets
-// from x* = K/R (see dist_lse in common.cuh for the window rule).
-__device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, float* ex = nullptr) {
-  if (!(R.hi > 0.f)) {
-    double peak, exd[2];
-    const double v = dist_lse(dp, df_to_double(K), df_to_double(R), 0.0, &peak, exd);
-    if (ex) {
-      ex[0] = (float)exd[0];
-      ex[1] = (float)exd[1];
-    }
-    return df_from_double(v);
-  }
-  // x* = K / R by one Newton correction of the float quotient
-  const float q0 = K.hi / R.hi;
-  df pr = two_prod(q0, R.hi);
-  pr.lo = fmaf(q0, R.lo, pr.lo);
-  const df rem = df_sub(K, pr);
-  const df xs = fast_two_sum(q0, rem.hi / R.hi);
-  // nearest node by bisection on the hi parts (x decreasing)
-  int lo = 0, hi = dp.n - 1;
-  if (!(xs.hi < dp.xdf[0].x)) {
-    hi = 0;
-  } else if (!(xs.hi > dp.xdf[dp.n - 1].x)) {
-    lo = dp.n - 1;
-  } else {
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (dp.xdf[mid].x > xs.hi) lo = mid;
-      else hi = mid;
-    }
-  }
-  const int j0 = (dp.xdf[lo].x - xs.hi < xs.hi - dp.xdf[hi].x) ? lo : hi;
-  float m = -CUDART_INF_F, s = 0.f, s1 = 0.f, s2 = 0.f;
-  const float halfR = 0.5f * R.hi;
-  const float lnw_max = (float)dp.lnw_max;
-  for (int dir = -1; dir <= 1; dir += 2) {
-    for (int j = (dir < 0 ? j0 : j0 + 1); j >= 0 && j < dp.n; j += dir) {
-      const float2 xj = __ldg(dp.xdf + j);
-      const float d = __fadd_rn(__fsub_rn(xj.x, xs.hi), __fsub_rn(xj.y, xs.lo));
-      const float q = halfR * d * d;
-      if (lnw_max - q < m - 40.f) break;
-      const float t = __ldg(dp.lnwf + j) - q;
-      if (t > m) {
-        const float r = __expf(m - t);
-        s = fmaf(s, r, 1.f);
-        s1 = fmaf(s1, r, xj.x);
-        s2 = fmaf(s2, r, xj.x * xj.x);
-        m = t;
-      } else {
-        const float e = __expf(t - m);
-        s += e;
-        s1 = fmaf(e, xj.x, s1);
-        s2 = fmaf(e * xj.x, xj.x, s2);
-      }
-    }
-  }
-  if (ex) {
-    ex[0] = s1 / s;
-    ex[1] = s2 / s;
-  }
-  const df peak = df_mul(K, xs);
-  return df_add_f(df{0.5f * peak.hi, 0.5f * peak.lo}, m + __logf(s));
-}
-
-// One draw: lnL, and with GRAD its gradient in (ra, dec, psi, incl, phase, lnD, t).
-//
-// Adjoint (Sec. II.B): with r_k = e_k - w_k and rho_k = r_k + gm1 w_k,
-//   d lnL = sum_k [ (P_k'(f)/dt - r_k . edot_k) dt_k + rho_k . dw_k ],
-// the first bracket being w_k . edot_k (computed as the exact polynomial
-// slope minus a small residual term); dw_k follows from w_k = Re(xF_k) a1 +
-// Im(xF_k) a2: rho_k . dw_k = d Re(xF_k) rho_k.a1 + d Im(xF_k) rho_k.a2 for the
-// sky angles, psi and lnD, and (A^T G1 + J^T A^T G2) . dy with
-// G1 = sum_k Re(xF_k) rho_k, G2 = sum_k Im(xF_k) rho_k for iota and phase.
-// With DIST the template is taken at the distance factor xin (1 for the
-// marginal's K and R) instead of D_ref e^{-lnD}.
-template <int MM, int RR, bool GRAD, bool DIST = false>
-__device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const float4* sA,
-                                                    const float* sg, const DrawsParams& dp,
-                                                    long long i, df xin = df{1.f, 0.f}) {
-  const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
-  const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
-  const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
-  const df tc = load_param_df(dp, 6, i);
-  const int M = P.M, D = P.D, R = P.R, n = P.n;
-
-  // distance factor x = D_ref e^{-lnD}
-  df lx = two_sum(P.ln_dref_hi, -lnD);
-  lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
-  // with distance marginalisation the terms are taken at x = 1
-  const df x = DIST ? xin : exp_df(fast_two_sum(lx.hi, lx.lo));
-
-  // sky direction and transverse basis
-  df lam = two_sum(ra, -P.gmst_hi);
-  lam.lo = __fsub_rn(lam.lo, P.gmst_lo);
-  lam = fast_two_sum(lam.hi, lam.lo);
-  df sl, cl, sd, cd;
-  sincos_df(lam, sl, cl);
-  sincos_df(df{dec, 0.f}, sd, cd);
-  const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
-  AntennaBasis AB;
-  antenna_basis(sl, cl, sd, cd, AB);
-  df s2p, c2p;
-  sincos_df(df{2.f * psi, 0.f}, s2p, c2p);
-  const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
-  df sh, ch;
-  sincos_df(df{0.5f * incl, 0.f}, sh, ch);
-
-  dacc T = dacc_zero();
-  dacc Racc = dacc_zero();  // DIST: R = sum_k (|w_k|^2 - sum_r gm1_r w_kr^2)
-  int oob = 0;
-  bool bad = false;
-  // gradient accumulators: time-driven parts of (ra, dec, t) as pairs, the rest in FP32
-  dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
-  float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_incl = 0.f, g_phase = 0.f, g_lnd = 0.f;
-  AntennaBasisGrad ABG;
-  float dsa[3] = {0.f, 0.f, 0.f}, dsd[3] = {0.f, 0.f, 0.f};
-  if (GRAD) {
-    antenna_basis_grad(sl.hi, cl.hi, sd.hi, cd.hi, ABG);
-    // ds/d ra = (-cd sl, cd cl, 0), ds/d dec = (-sd cl, -sd sl, cd)
-    dsa[0] = -cd.hi * sl.hi;
-    dsa[1] = cd.hi * cl.hi;
-    dsd[0] = -sd.hi * cl.hi;
-    dsd[1] = -sd.hi * sl.hi;
-    dsd[2] = cd.hi;
-  }
-  for (int c = 0; c < P.ncls; ++c) {
-    // a1 = A y, a2 = A J y by the split product: the products of the 10-bit
-    // head of A with the 9-bit head of y are exact and their sum stays below
-    // 2^24 quanta, so ex1/ex2 are exact; every other term is ~2^-9 smaller.
-    float ex1[RR], ex2[RR], co1[RR], co2[RR];
-#pragma unroll
-    for (int r = 0; r < RR; ++r) ex1[r] = ex2[r] = co1[r] = co2[r] = 0.f;
-    const float4* Ac = sA + (size_t)c * R * D;
-    int prev_am = -1;
-    df cm = df{1.f, 0.f}, sm = df{0.f, 0.f};
-    for (int a = 0; a < M; ++a) {
-      // e^{i m phi}: reused across the +-m members of a mode pair
-      const int m = P.em[a], am = m < 0 ? -m : m;
-      if (am != prev_am) {
-        sincos_df(two_prod((float)am, phi), sm, cm);
-        prev_am = am;
-      }
-      const df amp = sylm_amp_df(P, a, ch, sh);
-      const df yr = df_mul(amp, cm);
-      const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
-      float yr1, yr2, yi1, yi2;
-      split_y(yr.hi, yr1, yr2);
-      split_y(yi.hi, yi1, yi2);
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        if (r < R) {
-          const float4 at = Ac[r * D + a];      // (head, tail, lo, -) of A[r][a]
-          const float4 ab = Ac[r * D + M + a];  // of A[r][M + a]
-          const float at_hi = at.x + at.y, ab_hi = ab.x + ab.y;
-          // a1_r += A_t yr + A_b yi ;  a2_r += A_b yr - A_t yi
-          ex1[r] = fmaf(at.x, yr1, ex1[r]);
-          ex1[r] = fmaf(ab.x, yi1, ex1[r]);
-          ex2[r] = fmaf(ab.x, yr1, ex2[r]);
-          ex2[r] = fmaf(-at.x, yi1, ex2[r]);
-          float t1 = fmaf(at.x, yr2, co1[r]);
-          t1 = fmaf(at.y, yr.hi, t1);
-          t1 = fmaf(at_hi, yr.lo, t1);
-          t1 = fmaf(at.z, yr.hi, t1);
-          t1 = fmaf(ab.x, yi2, t1);
-          t1 = fmaf(ab.y, yi.hi, t1);
-          t1 = fmaf(ab_hi, yi.lo, t1);
-          co1[r] = fmaf(ab.z, yi.hi, t1);
-          float t2 = fmaf(ab.x, yr2, co2[r]);
-          t2 = fmaf(ab.y, yr.hi, t2);
-          t2 = fmaf(ab_hi, yr.lo, t2);
-          t2 = fmaf(ab.z, yr.hi, t2);
-          t2 = fmaf(-at.x, yi2, t2);
-          t2 = fmaf(-at.y, yi.hi, t2);
-          t2 = fmaf(-at_hi, yi.lo, t2);
-          co2[r] = fmaf(-at.z, yi.hi, t2);
-        }
-      }
-    }
-    df a1[RR], a2[RR];
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      a1[r] = two_sum(ex1[r], co1[r]);
-      a2[r] = two_sum(ex2[r], co2[r]);
-    }
-    const float* gc = sg + c * R;
-    df delay = df{0.f, 0.f};
-    float G1[GRAD ? RR : 1], G2[GRAD ? RR : 1];
-    if (GRAD) {
-#pragma unroll
-      for (int r = 0; r < RR; ++r) G1[r] = G2[r] = 0.f;
-    }
-    for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
-      const int k = P.det_order[q];
-      df xFr, xFi;
-      antenna_df(P, k, AB, xer, xei, xFr, xFi);
-      df w[RR];
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        // w_r = xFr a1_r + xFi a2_r
-        const df p1 = two_prod(xFr.hi, a1[r].hi), p2 = two_prod(xFi.hi, a2[r].hi);
-        const df s = two_sum(p1.hi, p2.hi);
-        float lo = __fadd_rn(__fadd_rn(p1.lo, p2.lo), s.lo);
-        lo = fmaf(xFr.hi, a1[r].lo, lo);
-        lo = fmaf(xFr.lo, a1[r].hi, lo);
-        lo = fmaf(xFi.hi, a2[r].lo, lo);
-        lo = fmaf(xFi.lo, a2[r].hi, lo);
-        w[r] = fast_two_sum(s.hi, lo);
-      }
-      // arrival time (shared by co-located detectors) and table position
-      if (!P.same_pos_prev[q]) {
-        delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
-        delay = df_add(delay, df_mul(df{P.pos_hi[k][1], P.pos_lo[k][1]}, s1));
-        delay = df_add(delay, df_mul(df{P.pos_hi[k][2], P.pos_lo[k][2]}, s2));
-      }
-      const df rel = df_add(df_sub(tc, delay), df{-P.t0_hi[k], -P.t0_lo[k]});
-      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
-      if (!isfinite(u.hi)) {
-        bad = true;
-        oob += 4;
-        continue;
-      }
-      float jf = floorf(u.hi);
-      if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
-      const float f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
-      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the
-      // table) and, for the adjoint, its slope in f (Horner on both)
-      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
-      if (jf >= -2.f && jf <= (float)n) {
-        const float2* pc = P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
-        float2 cf = __ldg(pc + kPolyDeg);
-        df acc = df{cf.x, cf.y};
-        df dacc_p = df{0.f, 0.f};
-#pragma unroll
-        for (int p = kPolyDeg - 1; p >= 0; --p) {
-          if (GRAD) {  // slope: d = d f + acc
-            df pr = two_prod(dacc_p.hi, f);
-            pr.lo = fmaf(dacc_p.lo, f, pr.lo);
-            const df sm3 = two_sum(pr.hi, acc.hi);
-            dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
-          }
-          // acc = acc f + c_p: exact product and sum of the high parts
-          cf = __ldg(pc + p);
-          df pr = two_prod(acc.hi, f);
-          pr.lo = fmaf(acc.lo, f, pr.lo);
-          const df sm2 = two_sum(pr.hi, cf.x);
-          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf.y));
-        }
-        half_e2 = acc;
-        dhalf = dacc_p;
-      }
-      // residual e - w = sum_i wt_i (e_i - w) - sigma (e_j - w) with FP32
-      // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
-      // weights' sum: sum_i wt_i e_i = e + sigma e_j + O(u |e_i - e_j|)
-      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
-      float wt[4];
-      wt[0] = -(f * fc * fd) * (1.f / 6.f);
-      wt[1] = (fa * fc * fd) * 0.5f;
-      wt[2] = -(fa * f * fd) * 0.5f;
-      wt[3] = (fa * f * fc) * (1.f / 6.f);
-      const df ws = df_add(two_sum(wt[0], wt[1]), two_sum(wt[2], wt[3]));
-      const float sigma = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
-      // derivative weights (adjoint only): d wt_i / df
-      float wtd[4] = {0.f, 0.f, 0.f, 0.f};
-      if (GRAD) {
-        wtd[0] = -(fc * fd + f * fd + f * fc) * (1.f / 6.f);
-        wtd[1] = (fc * fd + fa * fd + fa * fc) * 0.5f;
-        wtd[2] = -(f * fd + fa * fd + fa * f) * 0.5f;
-        wtd[3] = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
-      }
-      float res[RR], edr[GRAD ? RR : 1];
-#pragma unroll
-      for (int r = 0; r < RR; ++r) res[r] = 0.f;
-      if (GRAD) {
-#pragma unroll
-        for (int r = 0; r < RR; ++r) edr[r] = 0.f;
-      }
-      const float2* Ek = P.ehat + (size_t)k * n * R;
-#pragma unroll
-      for (int tap = 0; tap < 4; ++tap) {
-        const float jj = jf - 1.f + (float)tap;
-        const bool valid = (jj >= 0.f && jj < (float)n);
-        if (!valid) ++oob;
-        const float2* row = Ek + (size_t)(valid ? (int)jj : 0) * R;
-#pragma unroll
-        for (int r = 0; r < RR; r += 2) {
-          if (r < R) {
-            // rows hold R pairs, R even: two entries per 16-byte load
-            float4 e2 = valid ? __ldg(reinterpret_cast<const float4*>(row + r))
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float d0 = __fadd_rn(__fsub_rn(e2.x, w[r].hi), __fsub_rn(e2.y, w[r].lo));
-            const float d1 = __fadd_rn(__fsub_rn(e2.z, w[r + 1].hi), __fsub_rn(e2.w, w[r + 1].lo));
-            res[r] = fmaf(wt[tap], d0, res[r]);
-            res[r + 1] = fmaf(wt[tap], d1, res[r + 1]);
-            if (tap == 1) {  // sigma is ~1 ulp of wt: applied apart
-              res[r] = fmaf(-sigma, d0, res[r]);
-              res[r + 1] = fmaf(-sigma, d1, res[r + 1]);
-            }
-            if (GRAD) {  // dt edot = sum_i wtd_i (e_i - w)  (the wtd sum to zero)
-              edr[r] = fmaf(wtd[tap], d0, edr[r]);
-              edr[r + 1] = fmaf(wtd[tap], d1, edr[r + 1]);
-            }
-          }
-        }
-      }
-      float q2 = 0.f, nul = 0.f;
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        if (r < R) {
-          q2 = fmaf(res[r], res[r], q2);
-          nul = fmaf(gc[r] * w[r].hi, w[r].hi, nul);
-        }
-      }
-      dacc_add(T, half_e2);
-      dacc_add(T, df{-0.5f * q2, 0.f});
-      if (P.has_null[c] && !DIST) dacc_add(T, df{0.5f * nul, 0.f});
-      if (DIST) {
-        // K_k = e.w = 1/2|e|^2 + 1/2|w|^2 - 1/2|e - w|^2 (the first and last are in T
-        // already); R_k = |w|^2 - sum_r gm1_r w_r^2, with |w|^2 exact in pairs
-        dacc w2 = dacc_zero();
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          if (r < R) {
-            dacc_fma_ff(w2, w[r].hi, w[r].hi);
-            w2.c = fmaf(2.f * w[r].hi, w[r].lo, w2.c);
-          }
-        }
-        const df w2d = dacc_result(w2);
-        dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
-        dacc_add(Racc, w2d);
-        if (P.has_null[c]) dacc_add(Racc, df{-nul, 0.f});
-      }
-      if (GRAD) {
-        // time: d lnL_k / d t_k = (P'(f) - r . edot dt) / dt
-        float red = 0.f, g1 = 0.f, g2 = 0.f;
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          if (r < R) {
-            red = fmaf(res[r], edr[r], red);
-            const float rho = fmaf(gc[r], w[r].hi, res[r]);
-            g1 = fmaf(rho, a1[r].hi, g1);
-            g2 = fmaf(rho, a2[r].hi, g2);
-            G1[r] = fmaf(xFr.hi, rho, G1[r]);
-            G2[r] = fmaf(xFi.hi, rho, G2[r]);
-          }
-        }
-        const df dtk = df_mul(df_add_f(dhalf, -red), df{P.inv_dt_hi, P.inv_dt_lo});
-        const float dka = -(P.pos_hi[k][0] * dsa[0] + P.pos_hi[k][1] * dsa[1]);
-        const float dkd = -(P.pos_hi[k][0] * dsd[0] + P.pos_hi[k][1] * dsd[1] + P.pos_hi[k][2] * dsd[2]);
-        dacc_add(gt_t, dtk);
-        dacc_add(gt_ra, df_mul_f(dtk, dka));
-        dacc_add(gt_dec, df_mul_f(dtk, dkd));
-        // antenna: d(xF) = x e^{2 i psi} (dF+ - i dFx), d/d psi (xF) = 2 i xF
-        float dfpa = 0.f, dfpd = 0.f, dfxa = 0.f, dfxd = 0.f;
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-          dfpa = fmaf(P.acoef_hi[k][u], ABG.ba[u], dfpa);
-          dfpd = fmaf(P.acoef_hi[k][u], ABG.bd[u], dfpd);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          dfxa = fmaf(P.acoef_hi[k][6 + u], ABG.ga[u], dfxa);
-          dfxd = fmaf(P.acoef_hi[k][6 + u], ABG.gd[u], dfxd);
-        }
-        // (dfp - i dfx)(xer + i xei)
-        const float dxra = dfpa * xer.hi + dfxa * xei.hi, dxia = dfpa * xei.hi - dfxa * xer.hi;
-        const float dxrd = dfpd * xer.hi + dfxd * xei.hi, dxid = dfpd * xei.hi - dfxd * xer.hi;
-        g_ra = fmaf(dxra, g1, fmaf(dxia, g2, g_ra));
-        g_dec = fmaf(dxrd, g1, fmaf(dxid, g2, g_dec));
-        g_psi = fmaf(-2.f * xFi.hi, g1, fmaf(2.f * xFr.hi, g2, g_psi));
-        g_lnd = fmaf(-xFr.hi, g1, fmaf(-xFi.hi, g2, g_lnd));
-      }
-    }
-    if (GRAD) {
-      // iota and phase through the modes: H = A^T G1 + J^T A^T G2 (FP32)
-      const float4* Ac2 = sA + (size_t)c * R * D;
-      const float ci = ch.hi, si = sh.hi;
-      float cmf = 1.f, smf = 0.f;
-      int prev = -1;
-      for (int a = 0; a < M; ++a) {
-        float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          if (r < R) {
-            const float4 at = Ac2[r * D + a], ab = Ac2[r * D + M + a];
-            const float ath = at.x + at.y, abh = ab.x + ab.y;
-            h1t = fmaf(G1[r], ath, h1t);
-            h1b = fmaf(G1[r], abh, h1b);
-            h2t = fmaf(G2[r], ath, h2t);
-            h2b = fmaf(G2[r], abh, h2b);
-          }
-        }
-        const float Hre = h1t + h2b, Him = h1b - h2t;
-        const int m = P.em[a], am = m < 0 ? -m : m;
-        if (am != prev) {
-          sincosf((float)am * phi, &smf, &cmf);
-          prev = am;
-        }
-        const float sgn = m < 0 ? -1.f : 1.f;
-        float amp, damp;
-        sylm_amp_grad_f(P, a, ci, si, amp, damp);
-        const float yre = amp * cmf, yim = sgn * amp * smf;
-        g_phase = fmaf((float)m, fmaf(-yim, Hre, yre * Him), g_phase);
-        g_incl = fmaf(damp * cmf, Hre, fmaf(sgn * damp * smf, Him, g_incl));
-      }
-    }
-  }
-  MixedDraw o;
-  o.lnl = dacc_result(T);
-  o.R = dacc_result(Racc);
-  if (bad) o.lnl = df{CUDART_NAN_F, 0.f};
-  o.oob = oob;
-  if (GRAD) {
-    const df a = dacc_result(gt_ra), b = dacc_result(gt_dec), t = dacc_result(gt_t);
-    o.grad[0] = (double)a.hi + (double)a.lo + (double)g_ra;
-    o.grad[1] = (double)b.hi + (double)b.lo + (double)g_dec;
-    o.grad[2] = g_psi;
-    o.grad[3] = g_incl;
-    o.grad[4] = g_phase;
-    o.grad[5] = g_lnd;
-    o.grad[6] = (double)t.hi + (double)t.lo;
-    if (bad)
-      for (int p = 0; p < kNpar; ++p) o.grad[p] = CUDART_NAN;
-  }
-  return o;
-}
-
-// Stages the whitening matrices of all classes into shared memory in split
-// form, (10-bit head, tail, lo part, 0) per entry: the head is A_hi rounded to
-// a multiple of 2^-9 of a power of two >= max_a |A[r][a]| (the error-free
-// product of lnl_mixed_draw relies on it), followed by gm1.  Whole block.
-__device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem4) {
-  const int R = P.R, D = P.D, ncls = P.ncls;
-  float4* sA = smem4;
-  float* sg = reinterpret_cast<float*>(smem4 + (size_t)ncls * R * D);
-  for (int t = threadIdx.x; t < ncls * R; t += blockDim.x) {
-    const float2* row = P.A + (size_t)t * D;
-    float mx = 0.f;
-    for (int a = 0; a < D; ++a) mx = fmaxf(mx, fabsf(__ldg(row + a).x));
-    int e = 0;
-    frexpf(mx, &e);  // mx < 2^e
-    const float C = ldexpf(1.5f, e + 14);  // ulp(C) = 2^(e - 9)
-    for (int a = 0; a < D; ++a) {
-      const float2 v = __ldg(row + a);
-      const float head = __fsub_rn(__fadd_rn(v.x, C), C);
-      sA[(size_t)t * D + a] = make_float4(head, __fsub_rn(v.x, head), v.y, 0.f);
-    }
-    sg[t] = __ldg(P.gm1 + t);
-  }
-}
-
-template <int MM, int RR, bool LSE, bool GRAD = false, bool DIST = false>
-__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(const PointParams* __restrict__ gP,
-                                                        DrawsParams dp, double* __restrict__ lnl_out,
-                                                        LseState* __restrict__ partials,
-                                                        unsigned long long* __restrict__ oob_count,
-                                                        double* __restrict__ grad_out = nullptr,
-                                                        DistParams dist = DistParams{}) {
-  __shared__ PointParams P;
-  extern __shared__ float4 smem4[];
-  stage_point(P, gP);
-  __syncthreads();
-  stage_split_A(P, smem4);
-  __syncthreads();
-  const float4* sA = smem4;
-  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.D);
-  ThreadLse st = tlse_init();
-  int oob = 0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
-    MixedDraw o;
-    if (DIST && GRAD) {
-      // distance-marginal gradient: E[x] dK - E[x^2] dR / 2 equals (a / xbar)
-      // times the gradient at x = xbar = E[x^2]/E[x] (a = E[x]; the lnD slot is 0)
-      MixedDraw k1 = lnl_mixed_draw<MM, RR, false, true>(P, sA, sg, dp, i);
-      float ex[2] = {1.f, 1.f};
-      const df marg = isnan(k1.lnl.hi) ? k1.lnl : dist_marg_df(dist, k1.lnl, k1.R, ex);
-      const float xbar = ex[1] / ex[0], sc = ex[0] / xbar;
-      o = lnl_mixed_draw<MM, RR, true, true>(P, sA, sg, dp, i, df{xbar, 0.f});
-      for (int p = 0; p < kNpar; ++p) o.grad[p] *= sc;
-      o.grad[5] = 0.0;
-      o.lnl = marg;
-      o.oob = k1.oob;
-    } else {
-      o = lnl_mixed_draw<MM, RR, GRAD, DIST>(P, sA, sg, dp, i);
-      if (DIST) o.lnl = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R);
-    }
-    oob += o.oob;
-    if (GRAD) {
-      if (lnl_out) lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
-#pragma unroll
-      for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = o.grad[p];
-    } else if (!LSE) {
-      lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
-    } else {
-      float lw = 0.f;
-      if (dp.logw) lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
-      tlse_push_lw(st, o.lnl, lw);
-    }
-  }
-  if (LSE) block_lse_write(st, partials + blockIdx.x);
-  if (oob_count) {
-    for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
-    if ((threadIdx.x & 31) == 0 && oob) atomicAdd(oob_count, (unsigned long long)oob);
-  }
-}
-
-template <int MM, int RR, bool LSE>
-cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                           double* lnl_out, LseState* partials, unsigned long long* oob,
-                           int* blocks, cudaStream_t st) {
-  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
-                      (size_t)hp.ncls * hp.R * sizeof(float);
-  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  *blocks = grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem);
-  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
-  return cudaGetLastError();
-}
-
-template <int MM, int RR, bool LSE>
-cudaError_t launch_mixed_dist_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                                const DistParams& dist, double* lnl_out, LseState* partials,
-                                unsigned long long* oob, int* blocks, cudaStream_t st) {
-  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
-                      (size_t)hp.ncls * hp.R * sizeof(float);
-  auto kern = lnl_mixed_kernel<MM, RR, LSE, false, true>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  *blocks = grid_for(kern, 128, smem);
-  kern<<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob, nullptr, dist);
-  return cudaGetLastError();
-}
-
-template <int MM>
-cudaError_t launch_mixed_dist_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                                 const DistParams& dist, double* lnl_out, LseState* partials,
-                                 unsigned long long* oob, int* blocks, cudaStream_t st) {
-  const bool wide = hp.R > MM;
-  if (partials)
-    return wide ? launch_mixed_dist_k<MM, 2 * MM, true>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st)
-                : launch_mixed_dist_k<MM, MM, true>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  return wide ? launch_mixed_dist_k<MM, 2 * MM, false>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st)
-              : launch_mixed_dist_k<MM, MM, false>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-}
-
-template <int MM, int RR>
-cudaError_t launch_mixed_mr(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                            double* lnl_out, LseState* partials, unsigned long long* oob,
-                            int* blocks, cudaStream_t st) {
-  if (partials) return launch_mixed_k<MM, RR, true>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  return launch_mixed_k<MM, RR, false>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-}
-
-template <int MM>
-cudaError_t launch_mixed_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                            double* lnl_out, LseState* partials, unsigned long long* oob,
-                            int* blocks, cudaStream_t st) {
-  if (hp.R <= MM) return launch_mixed_mr<MM, MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  return launch_mixed_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-}
-
-template <int MM, int RR>
-cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                                 double* lnl_out, double* grad_out, cudaStream_t st) {
-  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
-                      (size_t)hp.ncls * hp.R * sizeof(float);
-  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, false, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  const int blocks = grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem);
-  lnl_mixed_kernel<MM, RR, false, true><<<blocks, 128, smem, st>>>(dP, dp, lnl_out, nullptr, nullptr,
-                                                                   grad_out);
-  return cudaGetLastError();
-}
-
-template <int MM>
-cudaError_t launch_mixed_grad_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                                 double* lnl_out, double* grad_out, cudaStream_t st) {
-  if (hp.R <= MM) return launch_mixed_grad_mr<MM, MM>(hp, dP, dp, lnl_out, grad_out, st);
-  return launch_mixed_grad_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, grad_out, st);
-}
-
-}  // namespace
 
 cudaError_t launch_lnl_mixed_dist(const PointParams& hp, const PointParams* dP,
                                   const DrawsParams& dp, const DistParams& dist, double* lnl_out,
                                   LseState* partials, unsigned long long* oob, int* blocks,
                                   cudaStream_t st) {
-  const int M = hp.M;
-  if (M <= 2) return launch_mixed_dist_mm<2>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  if (M <= 4) return launch_mixed_dist_mm<4>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  if (M <= 6) return launch_mixed_dist_mm<6>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  if (M <= 8) return launch_mixed_dist_mm<8>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  if (M <= 10) return launch_mixed_dist_mm<10>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  if (M <= 12) return launch_mixed_dist_mm<12>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
-  return launch_mixed_dist_mm<16>(hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
+  return RIFT_DISPATCH_M(hp.M, mixed_dist, hp, dP, dp, dist, lnl_out, partials, oob, blocks, st);
 }
 
-template <int MM, int RR>
-cudaError_t launch_mixed_grad_dist_mr(const PointParams& hp, const PointParams* dP,
-                                      const DrawsParams& dp, const DistParams& dist, double* lnl_out,
-                                      double* grad_out, cudaStream_t st) {
-  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
-                      (size_t)hp.ncls * hp.R * sizeof(float);
-  auto kern = lnl_mixed_kernel<MM, RR, false, true, true>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  const int blocks = grid_for(kern, 128, smem);
-  kern<<<blocks, 128, smem, st>>>(dP, dp, lnl_out, nullptr, nullptr, grad_out, dist);
-  return cudaGetLastError();
-}
-
-template <int MM>
-cudaError_t launch_mixed_grad_dist_mm(const PointParams& hp, const PointParams* dP,
-                                      const DrawsParams& dp, const DistParams& dist, double* lnl_out,
-                                      double* grad_out, cudaStream_t st) {
-  if (hp.R <= MM) return launch_mixed_grad_dist_mr<MM, MM>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  return launch_mixed_grad_dist_mr<MM, 2 * MM>(hp, dP, dp, dist, lnl_out, grad_out, st);
+cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                              double* lnl_out, double* grad_out, cudaStream_t st) {
+  return RIFT_DISPATCH_M(hp.M, mixed_grad, hp, dP, dp, lnl_out, grad_out, st);
 }
 
 cudaError_t launch_grad_mixed_dist(const PointParams& hp, const PointParams* dP,
                                    const DrawsParams& dp, const DistParams& dist, double* lnl_out,
                                    double* grad_out, cudaStream_t st) {
-  const int M = hp.M;
-  if (M <= 2) return launch_mixed_grad_dist_mm<2>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  if (M <= 4) return launch_mixed_grad_dist_mm<4>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  if (M <= 6) return launch_mixed_grad_dist_mm<6>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  if (M <= 8) return launch_mixed_grad_dist_mm<8>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  if (M <= 10) return launch_mixed_grad_dist_mm<10>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  if (M <= 12) return launch_mixed_grad_dist_mm<12>(hp, dP, dp, dist, lnl_out, grad_out, st);
-  return launch_mixed_grad_dist_mm<16>(hp, dP, dp, dist, lnl_out, grad_out, st);
+  return RIFT_DISPATCH_M(hp.M, mixed_grad_dist, hp, dP, dp, dist, lnl_out, grad_out, st);
 }
 
-cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                              double* lnl_out, double* grad_out, cudaStream_t st) {
-  const int M = hp.M;
-  if (M <= 2) return launch_mixed_grad_mm<2>(hp, dP, dp, lnl_out, grad_out, st);
-  if (M <= 4) return launch_mixed_grad_mm<4>(hp, dP, dp, lnl_out, grad_out, st);
-  if (M <= 6) return launch_mixed_grad_mm<6>(hp, dP, dp, lnl_out, grad_out, st);
-  if (M <= 8) return launch_mixed_grad_mm<8>(hp, dP, dp, lnl_out, grad_out, st);
-  if (M <= 10) return launch_mixed_grad_mm<10>(hp, dP, dp, lnl_out, grad_out, st);
-  if (M <= 12) return launch_mixed_grad_mm<12>(hp, dP, dp, lnl_out, grad_out, st);
-  return launch_mixed_grad_mm<16>(hp, dP, dp, lnl_out, grad_out, st);
-}
+BatchKernelFn batch_kernel_for(int M, int R) { return RIFT_DISPATCH_M(M, mixed_batch_kernel, R); }
 
-cudaError_t launch_lnl_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                             double* lnl_out, LseState* partials, unsigned long long* oob,
-                             int* blocks, cudaStream_t st) {
-  const int M = hp.M;
-  if (M <= 2) return launch_mixed_mm<2>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  if (M <= 4) return launch_mixed_mm<4>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  if (M <= 6) return launch_mixed_mm<6>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  if (M <= 8) return launch_mixed_mm<8>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  if (M <= 10) return launch_mixed_mm<10>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  if (M <= 12) return launch_mixed_mm<12>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-  return launch_mixed_mm<16>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
-}
-
-namespace {
-
-template <int MM, int RR, bool LSE>
-cudaError_t launch_mixed_k_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                               double* lnl_out, LseState* partials, unsigned long long* oob,
-                               int sms, int* blocks, cudaStream_t st) {
-  const size_t smem = (size_t)hp.ncls * hp.R * hp.D * sizeof(float4) +
-                      (size_t)hp.ncls * hp.R * sizeof(float);
-  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  *blocks = grid_for_sms(lnl_mixed_kernel<MM, RR, LSE>, 128, smem, sms);
-  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
-  return cudaGetLastError();
-}
-
-template <int MM>
-cudaError_t launch_mixed_mm_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                                double* lnl_out, LseState* partials, unsigned long long* oob,
-                                int sms, int* blocks, cudaStream_t st) {
-  const bool wide = hp.R > MM;
-  if (partials)
-    return wide ? launch_mixed_k_sms<MM, 2 * MM, true>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st)
-                : launch_mixed_k_sms<MM, MM, true>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  return wide ? launch_mixed_k_sms<MM, 2 * MM, false>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st)
-              : launch_mixed_k_sms<MM, MM, false>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-}
-
-}  // namespace
-
-cudaError_t launch_lnl_mixed_sms(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
-                                 double* lnl_out, LseState* partials, unsigned long long* oob,
-                                 int sms, int* blocks, cudaStream_t st) {
-  const int M = hp.M;
-  if (M <= 2) return launch_mixed_mm_sms<2>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  if (M <= 4) return launch_mixed_mm_sms<4>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  if (M <= 6) return launch_mixed_mm_sms<6>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  if (M <= 8) return launch_mixed_mm_sms<8>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  if (M <= 10) return launch_mixed_mm_sms<10>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  if (M <= 12) return launch_mixed_mm_sms<12>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-  return launch_mixed_mm_sms<16>(hp, dP, dp, lnl_out, partials, oob, sms, blocks, st);
-}
-
-
-// ------------------------------------------------------------ batched lnZ
-
-namespace {
-
-// Persistent kernel of rift_ile_batch: resident blocks take (point, tile)
-// items from the queue with an atomic ticket, restage the point's tables when
-// the point changes, and leave one LSE state per item.  No block waits on
-// another: a block stops when the ticket passes the end of the queue.
-template <int MM, int RR>
-__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
-    lnz_batch_kernel(const PointParams* const* __restrict__ pts, const DrawsParams* __restrict__ dps,
-                     const BatchItem* __restrict__ items, int n_items, unsigned int* __restrict__ head,
-                     LseState* __restrict__ partials, unsigned long long* __restrict__ oob_count) {
-  __shared__ PointParams P;
-  __shared__ DrawsParams sdp;
-  __shared__ int s_item;
-  extern __shared__ float4 smem4[];
-  int cur = -1;
-  int oob = 0;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= n_items) break;
-    const BatchItem it = items[item];
-    if (it.point != cur) {
-      stage_point(P, pts[it.point]);
-      if (threadIdx.x == 0) sdp = dps[it.point];
-      __syncthreads();
-      stage_split_A(P, smem4);
-      __syncthreads();
-      cur = it.point;
-    }
-    const float4* sA = smem4;
-    const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.D);
-    ThreadLse st = tlse_init();
-    const long long end = it.begin + it.count;
-    for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
-      MixedDraw o = lnl_mixed_draw<MM, RR, false>(P, sA, sg, sdp, i);
-      oob += o.oob;
-      float lw = 0.f;
-      if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
-      tlse_push_lw(st, o.lnl, lw);
-    }
-    block_lse_write(st, partials + item);  // ends with every thread past its use of s_item
-    __syncthreads();
-  }
-  if (oob_count) {
-    for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
-    if ((threadIdx.x & 31) == 0 && oob) atomicAdd(oob_count, (unsigned long long)oob);
-  }
-}
-
-template <int MM>
-BatchKernelFn pick_batch_kernel(int R) {
-  if (R <= MM) return lnz_batch_kernel<MM, MM>;
-  return lnz_batch_kernel<MM, 2 * MM>;
-}
-
-}  // namespace
-
-BatchKernelFn batch_kernel_for(int M, int R) {
-  if (M <= 2) return pick_batch_kernel<2>(R);
-  if (M <= 4) return pick_batch_kernel<4>(R);
-  if (M <= 6) return pick_batch_kernel<6>(R);
-  if (M <= 8) return pick_batch_kernel<8>(R);
-  if (M <= 10) return pick_batch_kernel<10>(R);
-  if (M <= 12) return pick_batch_kernel<12>(R);
-  return pick_batch_kernel<16>(R);
+size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp) {
+  return RIFT_DISPATCH_M(M, mixed_batch_smem, R, ncls, Rp, Mp);
 }
 
 }  // namespace rift

@@ -1,0 +1,6 @@
+// FP32-mixed kernels instantiated for points with up to 16 modes.
+#include "lnl_mixed_impl.cuh"
+
+namespace rift {
+RIFT_INSTANTIATE_MIXED(16)
+}  // namespace rift

@@ -82,6 +82,30 @@ int harmonic_terms(int l, int mp, int* k0, double* coef) {
   return nt;
 }
 
+// The Goldberg sum of harmonic_terms rewritten in z = cos(iota): every term
+// c^p s^q (p + q = 2l, p of one parity) is ((1+z)/2)^(p/2) ((1-z)/2)^(q/2)
+// for even p, and sin(iota)/2 times ((1+z)/2)^((p-1)/2) ((1-z)/2)^((q-1)/2)
+// for odd p.  Writes the coefficients of z^0..z^l and returns the parity.
+int harmonic_zpoly(int l, int nt, int k0, const double* coef, double* out) {
+  const int par = k0 & 1;
+  for (int j = 0; j <= l; ++j) out[j] = 0.0;
+  for (int r = 0; r < nt; ++r) {
+    const int p = k0 + 2 * r, q = 2 * l - p;
+    const int a = (p - par) / 2, b = (q - par) / 2;
+    double poly[RIFT_ILE_MAX_ELL + 1] = {1.0};
+    int deg = 0;
+    for (int u = 0; u < a + b; ++u) {  // times (1 + z)/2 a times, then (1 - z)/2 b times
+      const double sgn = u < a ? 1.0 : -1.0;
+      for (int j = deg + 1; j >= 1; --j) poly[j] = 0.5 * (poly[j] + sgn * poly[j - 1]);
+      poly[0] *= 0.5;
+      ++deg;
+    }
+    const double w = par ? 0.5 * coef[r] : coef[r];
+    for (int j = 0; j <= deg; ++j) out[j] += w * poly[j];
+  }
+  return par;
+}
+
 // Cyclic Jacobi eigenvalue iteration for a symmetric n x n matrix (row-major,
 // destroyed).  Eigenvalues to lam[], eigenvectors to the columns of V.
 void jacobi_eigen(int n, std::vector<double>& a, std::vector<double>& lam, std::vector<double>& V) {
@@ -393,8 +417,12 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     const double coef[10] = {D[0], D[3], D[1], D[2], D[4], D[5], D[0] - D[3], D[1], D[2], D[4]};
     for (int c = 0; c < 10; ++c) split_df(coef[c], &P.acoef_hi[k][c], &P.acoef_lo[k][c]);
   }
-  for (int i = 0; i < M; ++i)
+  for (int i = 0; i < M; ++i) {
     for (int r = 0; r < P.ynt[i]; ++r) split_df(P.ycoef[i][r], &P.ycoef_hi[i][r], &P.ycoef_lo[i][r]);
+    double yz[RIFT_ILE_MAX_ELL + 1];
+    P.ypar[i] = harmonic_zpoly(P.ell[i], P.ynt[i], P.yk0[i], P.ycoef[i], yz);
+    for (int j = 0; j <= P.ell[i]; ++j) split_df(yz[j], &P.yz_hi[i][j], &P.yz_lo[i][j]);
+  }
 
   // ---- detector classes: detectors with identical U_k and V_k.
   int ncls = 0;
@@ -551,9 +579,14 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
       }
       R = std::max(R, Rc[c]);
     }
-    // rows are padded to an even length (zero directions) so that the kernel
-    // can read two table entries per 16-byte load
-    R = (R + 1) & ~1;
+    // rows are padded with zero directions to the width the FP32-mixed kernels
+    // are compiled for (the mode-count bucket MM >= M, or 2 MM), so that their
+    // per-direction loops need no bounds tests; the width is even, so two
+    // table entries fit one 16-byte load.  Zero rows add exact zeros.
+    {
+      const int mm = M <= 2 ? 2 : M <= 4 ? 4 : M <= 6 ? 6 : M <= 8 ? 8 : M <= 10 ? 10 : M <= 12 ? 12 : 16;
+      R = R <= mm ? mm : 2 * mm;
+    }
     P.R = R;
     std::vector<float2> A((size_t)ncls * R * D, make_float2(0.f, 0.f));
     std::vector<float> gm1((size_t)ncls * R, 0.f);

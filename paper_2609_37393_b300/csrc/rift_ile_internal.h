@@ -13,6 +13,7 @@ constexpr int kMaxDet = RIFT_ILE_MAX_DET;
 constexpr int kMaxModes = RIFT_ILE_MAX_MODES;
 constexpr int kMaxDim = 2 * RIFT_ILE_MAX_MODES;  // real dimension D = 2M
 constexpr int kMaxYTerms = 12;                   // terms of one Goldberg sum, l <= 8
+constexpr int kMaxEll = RIFT_ILE_MAX_ELL;
 constexpr int kNpar = RIFT_ILE_NPAR;
 
 // Anchors of the double-float sine/cosine: a_j = j h, h = 2^-7, |j| <= kAnchorHalf.
@@ -49,6 +50,10 @@ struct PointParams {
   int same_pos_prev[kMaxDet];  // det_order[q] sits where det_order[q - 1] does
   float gmst_hi, gmst_lo, inv_dt_hi, inv_dt_lo, ln_dref_hi, ln_dref_lo;
   float ycoef_hi[kMaxModes][kMaxYTerms], ycoef_lo[kMaxModes][kMaxYTerms];
+  // the same amplitude in z = cos(iota) for the mixed path (c^2 = (1 + z)/2,
+  // s^2 = (1 - z)/2, c s = sin(iota)/2): sin(iota)^ypar sum_{j <= l} yz[j] z^j
+  int ypar[kMaxModes];
+  float yz_hi[kMaxModes][kMaxEll + 1], yz_lo[kMaxModes][kMaxEll + 1];
   // detector classes (identical U_k, V_k share one whitening): the detectors
   // of class c are det_order[cls_begin[c] .. cls_begin[c+1]).
   int R;            // whitened dimension (largest rank over the classes)
