@@ -295,6 +295,8 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     b32 = R.Batch(pts, draws, R.FP32_MIXED)
     out = b32.launch()
+    ms_default = timed_events(torch, lambda: b32.launch(out), 2, stream)
+    tile, blocks, ms_tuned = b32.tune(reps=2)  # the autotuner picks tile and grid
     for _ in range(args.warmup):
         b32.launch(out)
     g = torch.cuda.CUDAGraph()
@@ -315,6 +317,8 @@ def run_batch(args):
         "speedup_vs_fp64_per_point": ms64 / ms32,
         "max_abs_dlnZ_vs_fp64": float(np.nanmax(np.abs(o32[:, 0] - o64[:, 0]))),
         "gpu_launches": 2 * args.steps, "graph": True, "setup_s": setup_s,
+        "autotune": {"tile": tile, "blocks": blocks, "ms_tuned": ms_tuned,
+                     "ms_default_tile_4096": ms_default},
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -465,9 +469,18 @@ def main():
         variants["fp32_mixed_fwd_bwd_draws_per_s"] = N_DRAWS / (ms_grad * 1e-3)
         ms_grad64 = timed(lambda: R.rift_ile_lnL_grad(pt, d_dev, R.FP64, out64, g), 1)
         variants["fp64_fwd_bwd_draws_per_s"] = N_DRAWS / (ms_grad64 * 1e-3)
-        del g
+        # gradient error of the mixed path against the FP64 path, per component,
+        # relative to |g| + the component's RMS, on draws within 50 nat of the best
+        g64 = g.clone()
+        R.rift_ile_lnL_grad(pt, d_dev, R.FP32_MIXED, out32, g)
+        near_g = out64 >= out64.max() - 50.0
+        scale = g64.abs() + g64.pow(2).mean(dim=1, keepdim=True).sqrt()
+        rel = ((g - g64).abs() / scale)[:, near_g]
+        grad_err = {p: float(rel[j].max()) for j, p in enumerate(W.PARAMS)}
+        del g, g64
     except R.RiftError as e:
         variants["fwd_bwd"] = f"unavailable: {e}"
+        grad_err = None
 
     # precision of the measured path against the FP64 GPU path, same draws
     R.rift_ile_lnL(pt, d_dev, R.FP64, out64)
@@ -481,6 +494,7 @@ def main():
         "draws_within_50nat": int(near.sum()),
         "abs_dlnZ_vs_fp64": abs(lnz[0] - z64[0]),
         "lnZ": lnz[0], "sigma_lnZ": lnz[1], "n_eff": lnz[2],
+        "max_rel_grad_err_within_50nat_vs_fp64": grad_err,
     }
     del out64, out32
 

@@ -219,7 +219,8 @@ int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
 /* lnZ of P points in one launch (the ILE stage over many intrinsic points,
  * Sec. II.C): point p uses pts[p] and draws[p] (each point its own Q, U, V,
  * network and draw count).  FP32_MIXED runs one persistent kernel whose
- * resident blocks take (point, 4096-draw tile) items from a queue by an atomic
+ * resident blocks take (point, tile) items (4096 draws unless tuned by
+ * rift_ile_batch_tune) from a queue by an atomic
  * ticket, one LSE state per item, merged per point in item order (the result
  * does not depend on scheduling); FP64 runs the plain fused kernel once per
  * point.  out is DEVICE [P][3] double: lnZ, sigma_lnZ, n_eff per point.
@@ -236,6 +237,21 @@ int rift_ile_batch_create(const rift_ile_point* const* pts, const rift_ile_draws
                           rift_ile_precision prec, rift_ile_batch** out);
 int rift_ile_batch_launch(rift_ile_batch* batch, double* out, void* stream);
 int rift_ile_batch_destroy(rift_ile_batch* batch);
+
+/* Autotuner of an FP32_MIXED batch (measurement support; the paper has no
+ * counterpart).  Times rift_ile_batch_launch on `stream` (one warm-up and
+ * `reps` timed launches, CUDA events) for every draw-tile size in
+ * {512, 1024, 2048, 4096, 8192, 16384} and every grid of {1, 3/4, 1/2} times
+ * the kernel's resident-block limit, then rebuilds the work queue for the
+ * fastest pair, which later launches use.  The result of a launch depends on
+ * the tile size only through the grouping of the per-item merges (lnZ
+ * agrees to rounding).  Synchronous; allocates; do not call while a graph
+ * holding this batch's launch may replay (the queue is reallocated: capture
+ * after tuning).  tile_out, blocks_out (the chosen configuration) and ms_out
+ * (its time per launch, -1 for FP64 batches, which have nothing to tune) may
+ * be NULL.  Errors: INVALID_ARG (NULL batch, reps < 1), CUDA, ALLOC. */
+int rift_ile_batch_tune(rift_ile_batch* batch, int32_t reps, void* stream, int32_t* tile_out,
+                        int32_t* blocks_out, double* ms_out);
 int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* draws, int32_t P,
                        rift_ile_precision prec, double* out, void* stream);
 

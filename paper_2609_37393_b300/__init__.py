@@ -79,6 +79,7 @@ _lib.rift_ile_lnZ_batch.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P, _P
 _lib.rift_ile_batch_create.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P]
 _lib.rift_ile_batch_launch.argtypes = [_P, _P, _P]
 _lib.rift_ile_batch_destroy.argtypes = [_P]
+_lib.rift_ile_batch_tune.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P]
 _lib.rift_ile_lnL_dist.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P]
 _lib.rift_ile_dist_nodes.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int32, _P, _P, _P]
 _lib.rift_ile_last_oob.restype = ctypes.c_int64
@@ -346,6 +347,14 @@ class Batch:
         _check(_lib.rift_ile_batch_launch(self._h, out.data_ptr(), _stream(stream)))
         return out
 
+    def tune(self, reps: int = 3, stream=None):
+        """Autotune the draw-tile size and grid of the persistent launch
+        (rift_ile_batch_tune); returns (tile, blocks, ms per launch)."""
+        tile, blocks, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(_lib.rift_ile_batch_tune(self._h, reps, _stream(stream), ctypes.byref(tile),
+                                        ctypes.byref(blocks), ctypes.byref(ms)))
+        return tile.value, blocks.value, ms.value
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.rift_ile_batch_destroy(self._h)
@@ -402,7 +411,6 @@ def _make_autograd():
                     _, g = rift_ile_lnL_dist(ctx.point, draws, ctx.dist, ctx.precision, grad=True)
                 else:
                     _, g = rift_ile_lnL_grad(ctx.point, draws, ctx.precision)
-            ctx.grad = None
             grads = [None] * 4
             for j in range(7):
                 grads.append((g[j] * grad_out).to(ctx.dtypes[j])

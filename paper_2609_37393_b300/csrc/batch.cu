@@ -19,7 +19,7 @@
 namespace rift {
 namespace {
 
-constexpr int kTileDraws = 4096;
+constexpr int kDefaultTile = 4096;  // draws per queue item unless tuned
 
 // Marks LSE states as empty (m = -inf).
 __global__ void fill_empty_kernel(LseState* __restrict__ st, long long n) {
@@ -92,11 +92,39 @@ struct rift_ile_batch {
   BatchKernelFn kernel = nullptr;
   size_t smem = 0;
   int blocks = 0;
+  int max_blocks = 0;  // resident-block limit of the kernel (SMs x occupancy)
+  int tile = 0;        // draws per queue item
+  std::vector<long long> n_host;  // draw count of each point
   // FP64 per-point form
   std::vector<const rift_ile_point*> pts;
   std::vector<DrawsParams> dps;
   int parts_per_point = 0;
 };
+
+// (Re)builds the FP32-mixed work queue for items of `tile` draws: the items
+// of point p are [first[p], first[p+1]), in draw order, one partial each.
+static int build_queue(rift_ile_batch* b, int tile) {
+  std::vector<BatchItem> items;
+  std::vector<int> first(b->P + 1, 0);
+  for (int p = 0; p < b->P; ++p) {
+    first[p] = (int)items.size();
+    for (long long a = 0; a < b->n_host[p]; a += tile)
+      items.push_back(BatchItem{a, (int)std::min<long long>(tile, b->n_host[p] - a), p});
+  }
+  first[b->P] = (int)items.size();
+  cudaFree(b->d_items);
+  cudaFree(b->d_first);
+  cudaFree(b->d_partials);
+  b->d_items = nullptr;
+  b->d_first = nullptr;
+  b->d_partials = nullptr;
+  int rc = alloc_copy(&b->d_items, items.data(), items.size(), "work queue");
+  if (!rc) rc = alloc_copy(&b->d_first, first.data(), b->P + 1, "item offsets");
+  if (!rc) rc = alloc_copy(&b->d_partials, (LseState*)nullptr, items.size(), "partials");
+  b->n_items = (int)items.size();
+  b->tile = tile;
+  return rc;
+}
 
 extern "C" int rift_ile_batch_destroy(rift_ile_batch* b) {
   if (!b) return RIFT_ILE_OK;
@@ -128,9 +156,7 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
   b->prec = prec;
   std::vector<const PointParams*> hp(P);
   std::vector<DrawsParams> hd(P);
-  std::vector<int> first(P + 1, 0);
   std::vector<double> nd(P);
-  std::vector<BatchItem> items;
   int maxM = 1, maxR = 2;
   size_t smem = 0;
   int rc = RIFT_ILE_OK;
@@ -158,29 +184,24 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
     nd[p] = (double)d->n;
     maxM = std::max(maxM, pt->host.M);
     maxR = std::max(maxR, pt->host.R);
-    first[p] = (int)items.size();
-    for (long long a = 0; a < d->n; a += kTileDraws)
-      items.push_back(BatchItem{a, (int)std::min<long long>(kTileDraws, d->n - a), p});
     b->pts.push_back(pt);
   }
-  first[P] = (int)items.size();
   b->dps = hd;
   if (!rc && prec == RIFT_ILE_FP32_MIXED) {
     for (int p = 0; p < P; ++p)
       smem = std::max(smem, batch_smem_for(maxM, maxR, pts[p]->host.ncls, pts[p]->host.R,
                                            pts[p]->host.M));
-    b->n_items = (int)items.size();
     b->kernel = batch_kernel_for(maxM, maxR);
     b->smem = smem;
     cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    b->blocks = grid_for(b->kernel, 128, smem);
+    b->max_blocks = b->blocks = grid_for(b->kernel, 128, smem);
+    b->n_host.resize(P);
+    for (int p = 0; p < P; ++p) b->n_host[p] = hd[p].n;
     if (!rc) rc = alloc_copy(&b->d_pts, hp.data(), P, "point table");
     if (!rc) rc = alloc_copy(&b->d_dps, hd.data(), P, "draw table");
-    if (!rc) rc = alloc_copy(&b->d_items, items.data(), items.size(), "work queue");
-    if (!rc) rc = alloc_copy(&b->d_first, first.data(), P + 1, "item offsets");
+    if (!rc) rc = build_queue(b, kDefaultTile);
     if (!rc) rc = alloc_copy(&b->d_ndraws, nd.data(), P, "draw counts");
     if (!rc) rc = alloc_copy(&b->d_head, (unsigned int*)nullptr, 1, "queue head");
-    if (!rc) rc = alloc_copy(&b->d_partials, (LseState*)nullptr, items.size(), "partials");
     if (!rc) rc = alloc_copy(&b->d_oob, (unsigned long long*)nullptr, 1, "counter");
   } else if (!rc) {
     // FP64: one fused lnL -> LSE launch per point into its own slice of partials
@@ -235,6 +256,57 @@ extern "C" int rift_ile_batch_launch(rift_ile_batch* b, double* out, void* strea
   batch_combine_kernel<<<(b->P + 3) / 4, 128, 0, st>>>(b->d_partials, b->d_first, b->d_ndraws,
                                                        b->P, out);
   return check_cuda(cudaGetLastError(), "batch combine launch");
+}
+
+extern "C" int rift_ile_batch_tune(rift_ile_batch* b, int32_t reps, void* stream,
+                                   int32_t* tile_out, int32_t* blocks_out, double* ms_out) {
+  if (!b || reps < 1) {
+    rift_ile_set_error("rift_ile_batch_tune: NULL batch or reps < 1");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = RIFT_ILE_OK;
+  double best_ms = -1.0;
+  int best_tile = b->tile, best_blocks = b->blocks;
+  if (b->prec == RIFT_ILE_FP32_MIXED && b->n_items > 0) {
+    double* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc((void**)&out, (size_t)3 * b->P * sizeof(double)) != cudaSuccess) {
+      rift_ile_set_error("rift_ile_batch_tune: allocation failed");
+      return RIFT_ILE_ERR_ALLOC;
+    }
+    rc = check_cuda(cudaEventCreate(&e0), "tune events");
+    if (!rc) rc = check_cuda(cudaEventCreate(&e1), "tune events");
+    static const int kTiles[] = {512, 1024, 2048, 4096, 8192, 16384};
+    static const int kQuarters[] = {4, 3, 2};
+    for (int ti = 0; ti < 6 && !rc; ++ti) {
+      rc = build_queue(b, kTiles[ti]);
+      for (int qi = 0; qi < 3 && !rc; ++qi) {
+        b->blocks = std::max(1, b->max_blocks * kQuarters[qi] / 4);
+        rc = rift_ile_batch_launch(b, out, stream);  // warm-up
+        if (!rc) rc = check_cuda(cudaEventRecord(e0, st), "tune timing");
+        for (int r = 0; r < reps && !rc; ++r) rc = rift_ile_batch_launch(b, out, stream);
+        if (!rc) rc = check_cuda(cudaEventRecord(e1, st), "tune timing");
+        if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "tune timing");
+        float ms = 0.f;
+        if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "tune timing");
+        if (!rc && (best_ms < 0.0 || ms / reps < best_ms)) {
+          best_ms = ms / reps;
+          best_tile = kTiles[ti];
+          best_blocks = b->blocks;
+        }
+      }
+    }
+    if (!rc) rc = build_queue(b, best_tile);
+    b->blocks = best_blocks;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+  }
+  if (tile_out) *tile_out = b->tile;
+  if (blocks_out) *blocks_out = b->blocks;
+  if (ms_out) *ms_out = best_ms;
+  return rc;
 }
 
 extern "C" int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* draws,

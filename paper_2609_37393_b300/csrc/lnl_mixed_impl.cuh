@@ -34,12 +34,15 @@
 // __launch_bounds__, and whether the large double-float helpers are real
 // calls (smaller code, fewer instruction-cache misses) or inlined.
 #ifndef RIFT_MIXED_MIN_BLOCKS
-#define RIFT_MIXED_MIN_BLOCKS 6
+#define RIFT_MIXED_MIN_BLOCKS 7
+#endif
+#ifndef RIFT_MIXED_MIN_BLOCKS_GRAD  // kernels that carry the adjoint
+#define RIFT_MIXED_MIN_BLOCKS_GRAD 4
 #endif
 // RIFT_MIXED_A_SMEM: keep a1, a2 of the current class in a per-thread slice
 // of shared memory instead of registers (for widths RR <= 12).
 #ifndef RIFT_MIXED_A_SMEM
-#define RIFT_MIXED_A_SMEM 0
+#define RIFT_MIXED_A_SMEM 1
 #endif
 #ifndef RIFT_MIXED_NOINLINE
 #define RIFT_MIXED_NOINLINE 0
@@ -204,18 +207,79 @@ __device__ __forceinline__ void dacc_fma_dd(dacc& acc, df a, df b) {
   acc.c = fmaf(a.lo, b.hi, c);
 }
 
+// Head of v on the grid of its own binade: with 2^E <= |v| < 2^(E+1)
+// (m = |v| or a larger value), head = v rounded to a multiple of 2^(E-8),
+// i.e. at most 10 significant bits, by adding and subtracting 1.5 2^(E+15).
+__device__ __forceinline__ float head_constant(float m) {
+  const unsigned e = __float_as_uint(m) & 0x7f800000u;
+  return __uint_as_float(e + (15u << 23) + 0x400000u);
+}
+
+__device__ __forceinline__ float head_of(float v, float C) { return __fsub_rn(__fadd_rn(v, C), C); }
+
+// The sky functions split for the antenna products: (head on the 2^-8 grid,
+// tail = rest + lo part); |beta|, |gamma| < 4.
+struct AntennaSplit {
+  float bh[6], bt[6], gh[4], gt[4];
+};
+
+__device__ __forceinline__ void split_antenna_basis(const AntennaBasis& B, AntennaSplit& S) {
+  const float C = 49152.0f;  // 1.5 * 2^15: ulp 2^-8
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    S.bh[i] = head_of(B.b[i].hi, C);
+    S.bt[i] = __fadd_rn(__fsub_rn(B.b[i].hi, S.bh[i]), B.b[i].lo);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    S.gh[i] = head_of(B.g[i].hi, C);
+    S.gt[i] = __fadd_rn(__fsub_rn(B.g[i].hi, S.gh[i]), B.g[i].lo);
+  }
+}
+
 // x F_k = x e^{2 i psi} (F_+(0) - i F_x(0)) of detector k, with xe = x e^{2 i psi}.
-RIFT_HELPER void antenna_df(const PointParams& P, int k, const AntennaBasis& B, df xer, df xei,
+// F_+(0) and F_x(0) by the split product: the detector's coefficients are
+// stored as a 10-bit head on the grid 2^(E-9) of their largest magnitude and
+// a tail (point.cu); head x head products are exact and their sum of at most
+// six stays below 2^22 quanta, so it is exact in FP32; the cross terms are
+// >= 2^9 smaller and summed in FP32.
+RIFT_HELPER void antenna_df(const PointParams& P, int k, const AntennaSplit& S, df xer, df xei,
                             df& xFr, df& xFi) {
-  dacc fp = dacc_zero(), fx = dacc_zero();
+  float fp = S.bh[0] * P.acoef_h[k][0], fpc = 0.f;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) dacc_fma_dd(fp, df{P.acoef_hi[k][i], P.acoef_lo[k][i]}, B.b[i]);
+  for (int i = 0; i < 6; ++i) {
+    if (i) fp = fmaf(P.acoef_h[k][i], S.bh[i], fp);
+    fpc = fmaf(P.acoef_h[k][i], S.bt[i], fpc);
+    fpc = fmaf(P.acoef_t[k][i], __fadd_rn(S.bh[i], S.bt[i]), fpc);
+  }
+  float fx = S.gh[0] * P.acoef_h[k][6], fxc = 0.f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) dacc_fma_dd(fx, df{P.acoef_hi[k][6 + i], P.acoef_lo[k][6 + i]}, B.g[i]);
-  const df f0r = dacc_result(fp), f0x = dacc_result(fx);
-  // (f0r - i f0x)(xer + i xei)
-  xFr = df_add(df_mul(f0r, xer), df_mul(f0x, xei));
-  xFi = df_sub(df_mul(f0r, xei), df_mul(f0x, xer));
+  for (int i = 0; i < 4; ++i) {
+    if (i) fx = fmaf(P.acoef_h[k][6 + i], S.gh[i], fx);
+    fxc = fmaf(P.acoef_h[k][6 + i], S.gt[i], fxc);
+    fxc = fmaf(P.acoef_t[k][6 + i], __fadd_rn(S.gh[i], S.gt[i]), fxc);
+  }
+  // (fp - i fx)(xer + i xei) with the pairs (fp, fpc), (fx, fxc) unnormalised
+  {
+    const df p1 = two_prod(fp, xer.hi), p2 = two_prod(fx, xei.hi);
+    const df sm = two_sum(p1.hi, p2.hi);
+    float lo = __fadd_rn(__fadd_rn(p1.lo, p2.lo), sm.lo);
+    lo = fmaf(fp, xer.lo, lo);
+    lo = fmaf(fpc, xer.hi, lo);
+    lo = fmaf(fx, xei.lo, lo);
+    lo = fmaf(fxc, xei.hi, lo);
+    xFr = fast_two_sum(sm.hi, lo);
+  }
+  {
+    const df p1 = two_prod(fp, xei.hi), p2 = two_prod(-fx, xer.hi);
+    const df sm = two_sum(p1.hi, p2.hi);
+    float lo = __fadd_rn(__fadd_rn(p1.lo, p2.lo), sm.lo);
+    lo = fmaf(fp, xei.lo, lo);
+    lo = fmaf(fpc, xei.hi, lo);
+    lo = fmaf(-fx, xer.lo, lo);
+    lo = fmaf(-fxc, xer.hi, lo);
+    xFi = fast_two_sum(sm.hi, lo);
+  }
 }
 
 // FP32 amplitude of mode i and its derivative with respect to iota (used by
@@ -384,8 +448,12 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   sincos_df(lam, sl, cl);
   sincos_df(df{dec, 0.f}, sd, cd);
   const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
-  AntennaBasis AB;
-  antenna_basis(sl, cl, sd, cd, AB);
+  AntennaSplit AS;
+  {
+    AntennaBasis AB;
+    antenna_basis(sl, cl, sd, cd, AB);
+    split_antenna_basis(AB, AS);
+  }
   df s2p, c2p;
   sincos_df(df{2.f * psi, 0.f}, s2p, c2p);
   const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
@@ -457,27 +525,28 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         }
       }
     }
+    // a1_r, a2_r as (head, tail) on the grid of the larger of the two: the
+    // template product below takes head x head exactly
     constexpr bool kA12S = A12Smem<RR>::on;
-    df a1[kA12S ? 1 : RR], a2[kA12S ? 1 : RR];
+    float4 a12r[kA12S ? 1 : RR];
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
       const df u = two_sum(ex1[r], co1[r]), v = two_sum(ex2[r], co2[r]);
+      const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
+      const float uh = head_of(u.hi, C), vh = head_of(v.hi, C);
+      const float4 q = make_float4(uh, __fadd_rn(__fsub_rn(u.hi, uh), u.lo), vh,
+                                   __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
       if constexpr (kA12S) {
-        a12s[r * kMixedThreads] = make_float4(u.hi, u.lo, v.hi, v.lo);
+        a12s[r * kMixedThreads] = q;
       } else {
-        a1[r] = u;
-        a2[r] = v;
+        a12r[r] = q;
       }
     }
-    // a1_r, a2_r of this class
-    auto get_a = [&](int r, df& u, df& v) {
+    auto get_a = [&](int r) -> float4 {
       if constexpr (kA12S) {
-        const float4 q = a12s[r * kMixedThreads];
-        u = df{q.x, q.y};
-        v = df{q.z, q.w};
+        return a12s[r * kMixedThreads];
       } else {
-        u = a1[r];
-        v = a2[r];
+        return a12r[r];
       }
     };
     const float* gc = sg + c * R;
@@ -490,21 +559,27 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
       const int k = P.det_order[q];
       df xFr, xFi;
-      antenna_df(P, k, AB, xer, xei, xFr, xFi);
+      antenna_df(P, k, AS, xer, xei, xFr, xFi);
+      // w_r = xFr a1_r + xFi a2_r: heads of xF on the grid of the larger part;
+      // head x head products (10 x 10 bits) and their sum are exact, the
+      // cross terms are >= 2^8 smaller.  w is kept as the unnormalised pair
+      // (exact head sum, FP32 correction); every use takes hi + lo as a sum.
+      const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
+      const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
+      const float xrt = __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo);
+      const float xit = __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo);
       df w[RR];
 #pragma unroll
       for (int r = 0; r < RR; ++r) {
-        // w_r = xFr a1_r + xFi a2_r
-        df ar, br;
-        get_a(r, ar, br);
-        const df p1 = two_prod(xFr.hi, ar.hi), p2 = two_prod(xFi.hi, br.hi);
-        const df s = two_sum(p1.hi, p2.hi);
-        float lo = __fadd_rn(__fadd_rn(p1.lo, p2.lo), s.lo);
-        lo = fmaf(xFr.hi, ar.lo, lo);
-        lo = fmaf(xFr.lo, ar.hi, lo);
-        lo = fmaf(xFi.hi, br.lo, lo);
-        lo = fmaf(xFi.lo, br.hi, lo);
-        w[r] = df{s.hi, lo};  // unnormalised pair: every use takes hi + lo as a sum
+        const float4 q = get_a(r);  // (a1 head, a1 tail, a2 head, a2 tail)
+        const float wh = fmaf(xrh, q.x, xih * q.z);
+        float lo = xrh * q.y;
+        lo = fmaf(xrt, q.x, lo);
+        lo = fmaf(xrt, q.y, lo);
+        lo = fmaf(xih, q.w, lo);
+        lo = fmaf(xit, q.z, lo);
+        lo = fmaf(xit, q.w, lo);
+        w[r] = df{wh, lo};
       }
       // arrival time (shared by co-located detectors) and table position
       if (!P.same_pos_prev[q]) {
@@ -611,7 +686,8 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       for (int r = 0; r < RR; ++r) {
         if (EXACT || r < R) {
           q2 = fmaf(res[r], res[r], q2);
-          nul = fmaf(gc[r] * w[r].hi, w[r].hi, nul);
+          const float wf = __fadd_rn(w[r].hi, w[r].lo);
+          nul = fmaf(gc[r] * wf, wf, nul);
         }
       }
       dacc_add(T, half_e2);
@@ -626,6 +702,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
           if (EXACT || r < R) {
             dacc_fma_ff(w2, w[r].hi, w[r].hi);
             w2.c = fmaf(2.f * w[r].hi, w[r].lo, w2.c);
+            w2.c = fmaf(w[r].lo, w[r].lo, w2.c);
           }
         }
         const df w2d = dacc_result(w2);
@@ -640,11 +717,10 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         for (int r = 0; r < RR; ++r) {
           if (EXACT || r < R) {
             red = fmaf(res[r], edr[r], red);
-            const float rho = fmaf(gc[r], w[r].hi, res[r]);
-            df ar, br;
-            get_a(r, ar, br);
-            g1 = fmaf(rho, ar.hi, g1);
-            g2 = fmaf(rho, br.hi, g2);
+            const float rho = fmaf(gc[r], __fadd_rn(w[r].hi, w[r].lo), res[r]);
+            const float4 q = get_a(r);
+            g1 = fmaf(rho, __fadd_rn(q.x, q.y), g1);
+            g2 = fmaf(rho, __fadd_rn(q.z, q.w), g2);
             G1[r] = fmaf(xFr.hi, rho, G1[r]);
             G2[r] = fmaf(xFi.hi, rho, G2[r]);
           }
@@ -759,7 +835,8 @@ __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem
 }
 
 template <int MM, int RR, bool LSE, bool GRAD = false, bool DIST = false>
-__global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS) lnl_mixed_kernel(const PointParams* __restrict__ gP,
+__global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_MIXED_MIN_BLOCKS)
+    lnl_mixed_kernel(const PointParams* __restrict__ gP,
                                                         DrawsParams dp, double* __restrict__ lnl_out,
                                                         LseState* __restrict__ partials,
                                                         unsigned long long* __restrict__ oob_count,

@@ -416,6 +416,16 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     const double* D = P.resp[k];  // xx, xy, xz, yy, yz, zz
     const double coef[10] = {D[0], D[3], D[1], D[2], D[4], D[5], D[0] - D[3], D[1], D[2], D[4]};
     for (int c = 0; c < 10; ++c) split_df(coef[c], &P.acoef_hi[k][c], &P.acoef_lo[k][c]);
+    double amax = 0.0;
+    for (int c = 0; c < 10; ++c) amax = std::fmax(amax, std::fabs(coef[c]));
+    int e = 0;
+    std::frexp(amax, &e);  // amax < 2^e
+    const double q = std::ldexp(1.0, e - 10);  // head grid 2^(E-9) with E = e - 1
+    for (int c = 0; c < 10; ++c) {
+      const double h = amax > 0.0 ? std::nearbyint(coef[c] / q) * q : 0.0;
+      P.acoef_h[k][c] = (float)h;
+      P.acoef_t[k][c] = (float)(coef[c] - h);
+    }
   }
   for (int i = 0; i < M; ++i) {
     for (int r = 0; r < P.ynt[i]; ++r) split_df(P.ycoef[i][r], &P.ycoef_hi[i][r], &P.ycoef_lo[i][r]);

@@ -47,6 +47,9 @@ struct PointParams {
   // (Dxx, Dyy, Dxy, Dxz, Dyz, Dzz) and F_x(0) = sum_i acoef[6 + i] gamma_i,
   // i < 4 (Dxx - Dyy, Dxy, Dxz, Dyz); see antenna_basis in lnl_mixed.cu.
   float acoef_hi[kMaxDet][10], acoef_lo[kMaxDet][10];
+  // the same split for the mixed path's exact products: acoef_h on the grid
+  // 2^(E-9) of the detector's largest |acoef| (< 2^(E+1)), acoef_t the rest
+  float acoef_h[kMaxDet][10], acoef_t[kMaxDet][10];
   int same_pos_prev[kMaxDet];  // det_order[q] sits where det_order[q - 1] does
   float gmst_hi, gmst_lo, inv_dt_hi, inv_dt_lo, ln_dref_hi, ln_dref_lo;
   float ycoef_hi[kMaxModes][kMaxYTerms], ycoef_lo[kMaxModes][kMaxYTerms];

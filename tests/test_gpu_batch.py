@@ -95,3 +95,41 @@ def test_batch_with_empty_point(R, batch_inputs):
     assert out[0, 0] == -np.inf and out[0, 2] == 0
     single = R.rift_ile_lnZ(points[1], draws[1], R.FP32_MIXED)
     assert abs(out[1, 0] - single[0]) <= 1e-6 * max(1, abs(single[0]))
+
+
+def test_batch_autotune_keeps_results(R, batch_inputs):
+    """The autotuner picks a tile size and grid by timing; the tuned launch
+    gives the same lnZ to rounding, stays deterministic and replays from a
+    graph captured after tuning."""
+    points = [R.Point(p[0]) for p in batch_inputs]
+    draws = [R.Draws(p[3], p[4]) for p in batch_inputs]
+    b = R.Batch(points, draws, R.FP32_MIXED)
+    before = b.launch().cpu().numpy()
+    tile, blocks, ms = b.tune(reps=2)
+    assert tile in (512, 1024, 2048, 4096, 8192, 16384) and blocks >= 1 and ms > 0
+    after = b.launch()
+    a = after.cpu().numpy()
+    assert np.all(np.abs(a[:, 0] - before[:, 0]) <= 1e-9 * np.maximum(1, np.abs(before[:, 0])))
+    assert np.allclose(a[:, 1:], before[:, 1:], rtol=1e-6)
+    assert torch.equal(b.launch(), after)
+    out = torch.empty_like(after)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.launch(out, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.launch(out)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, after)
+
+
+def test_fp64_batch_tune_is_a_no_op(R, batch_inputs):
+    points = [R.Point(p[0]) for p in batch_inputs[:2]]
+    draws = [R.Draws(p[3], p[4]) for p in batch_inputs[:2]]
+    b = R.Batch(points, draws, R.FP64)
+    tile, blocks, ms = b.tune(reps=1)
+    assert ms == -1.0
