@@ -59,15 +59,20 @@ def algorithmic_ops(point: dict, R: int, ncls: int) -> dict:
     em = [int(v) for v in point["em"]]
     sincos, expo, df_mul, df_add = 82, 44, 7, 20
     # distance factor, sky angles, sky direction, antenna basis, 2 psi, iota
-    fixed = (10 + expo) + (10 + 2 * sincos + 2 * df_mul) + 187 + (sincos + 2 * df_mul) + sincos
+    # (the antenna basis is also split into heads and tails once per draw: 40)
+    fixed = (10 + expo) + (10 + 2 * sincos + 2 * df_mul) + 187 + 40 + (sincos + 2 * df_mul) + sincos
     # modes: Horner in cos(iota) (15 per degree), sin(iota) factor for odd m,
     # Y = amp e^{i m phi} and its split, one sine/cosine per change of |m|
     n_phase = sum(1 for a in range(M) if a == 0 or abs(em[a]) != abs(em[a - 1]))
     modes = sum(15 * l for l in ell) + df_mul * sum(1 for m in em if m % 2) + M * (2 * df_mul + 8)
     modes += n_phase * sincos
-    matvec = 12 * R * M + 12 * R  # split product a1, a2 (12 per entry) and their two-sums
-    antenna = 10 * 12 + 2 * 3 + 4 * df_mul + 2 * df_add
-    template = 16 * R
+    # split product a1, a2 (12 per entry); per direction two TwoSums and the
+    # head/tail split of the pair (20)
+    matvec = 12 * R * M + 20 * R
+    # F_+(0), F_x(0) by head x head products and FP32 cross terms (4 per
+    # coefficient), x e^{2 i psi} F as two compensated complex parts (19 each)
+    antenna = 10 * 4 + 2 * 19
+    template = 8 + 8 * R  # split of x F, then 8 per direction
     timing = 2 * df_add + df_mul + 3 + 6 * 14 + 3 + 16 + 32 + 2  # position, 1/2|e|^2 sextic, weights
     residual = 4 * 3 * R + 2 * R + R + 16                  # taps, sigma and low part, |r|^2, T
     per_det = antenna + template + timing + residual

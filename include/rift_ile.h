@@ -218,9 +218,10 @@ int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
 
 /* lnZ of P points in one launch (the ILE stage over many intrinsic points,
  * Sec. II.C): point p uses pts[p] and draws[p] (each point its own Q, U, V,
- * network and draw count).  FP32_MIXED runs one persistent kernel whose
- * resident blocks take (point, tile) items (4096 draws unless tuned by
- * rift_ile_batch_tune) from a queue by an atomic
+ * network and draw count).  FP32_MIXED runs one persistent kernel per group
+ * of points that share a compiled kernel shape (mode-count bucket and
+ * whitened width); its resident blocks take (point, tile) items (4096 draws
+ * unless tuned by rift_ile_batch_tune) from the group's queue by an atomic
  * ticket, one LSE state per item, merged per point in item order (the result
  * does not depend on scheduling); FP64 runs the plain fused kernel once per
  * point.  out is DEVICE [P][3] double: lnZ, sigma_lnZ, n_eff per point.

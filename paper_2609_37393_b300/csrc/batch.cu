@@ -1,11 +1,14 @@
-// lnZ of many intrinsic points in one persistent launch (rift_ile_lnZ_batch,
+// lnZ of many intrinsic points in persistent launches (rift_ile_lnZ_batch,
 // rift_ile_batch_*).  The paper's ILE stage evaluates the marginal likelihood
 // of many intrinsic points (Sec. II.C: each worker handles a set of points);
-// here their draws are cut into tiles, the (point, tile) items form a queue,
-// and resident blocks take items from it with an atomic ticket until it is
-// empty.  Each item leaves one LSE state; a second kernel merges the states of
-// each point in item order, so the result does not depend on which block took
-// which item.  No block waits on another.
+// here their draws are cut into tiles and the (point, tile) items form work
+// queues, one per group of points that share a compiled kernel shape (the
+// mode-count bucket and the padded whitened width), so that every launch runs
+// the exact-width kernel.  Resident blocks take items from their group's queue
+// with an atomic ticket until it is empty; each item leaves one LSE state and
+// a final kernel merges the states of each point in item order, so the
+// result does not depend on which block took which item.  No block waits on
+// another.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -29,7 +32,7 @@ __global__ void fill_empty_kernel(LseState* __restrict__ st, long long n) {
 }
 
 // out[p] = (lnZ, sigma_lnZ, n_eff) from the states of point p's items
-// [first[p], first[p+1]): one warp per point, each lane merging a fixed
+// [first[2p], first[2p+1]): one warp per point, each lane merging a fixed
 // strided subset in item order, then a fixed shuffle tree.
 __global__ void batch_combine_kernel(const LseState* __restrict__ partials,
                                      const int* __restrict__ first, const double* __restrict__ ndraws,
@@ -38,7 +41,7 @@ __global__ void batch_combine_kernel(const LseState* __restrict__ partials,
   const int lane = threadIdx.x & 31;
   if (p >= P) return;  // whole warps leave together
   LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
-  for (int i = first[p] + lane; i < first[p + 1]; i += 32) acc = lse_merge(acc, partials[i]);
+  for (int i = first[2 * p] + lane; i < first[2 * p + 1]; i += 32) acc = lse_merge(acc, partials[i]);
   acc = warp_lse_reduce(acc);
   if (lane != 0) return;
   const double n = ndraws[p];
@@ -86,14 +89,19 @@ struct rift_ile_batch {
   int n_items = 0;
   int* d_first = nullptr;
   double* d_ndraws = nullptr;
-  unsigned int* d_head = nullptr;
+  unsigned int* d_head = nullptr;  // one ticket counter per group
   LseState* d_partials = nullptr;
   unsigned long long* d_oob = nullptr;
-  BatchKernelFn kernel = nullptr;
-  size_t smem = 0;
-  int blocks = 0;
-  int max_blocks = 0;  // resident-block limit of the kernel (SMs x occupancy)
-  int tile = 0;        // draws per queue item
+  struct Group {
+    BatchKernelFn kernel = nullptr;
+    size_t smem = 0;
+    int max_blocks = 0;  // resident-block limit of the kernel (SMs x occupancy)
+    int item0 = 0, n_items = 0;
+    std::vector<int> points;  // in queue order
+  };
+  std::vector<Group> groups;
+  int quarters = 4;  // grid = quarters/4 of each group's resident-block limit
+  int tile = 0;      // draws per queue item
   std::vector<long long> n_host;  // draw count of each point
   // FP64 per-point form
   std::vector<const rift_ile_point*> pts;
@@ -101,17 +109,22 @@ struct rift_ile_batch {
   int parts_per_point = 0;
 };
 
-// (Re)builds the FP32-mixed work queue for items of `tile` draws: the items
-// of point p are [first[p], first[p+1]), in draw order, one partial each.
+// (Re)builds the FP32-mixed work queues for items of `tile` draws: group by
+// group, point by point, in draw order; the items of point p are
+// [ranges[2p], ranges[2p+1]), one partial each.
 static int build_queue(rift_ile_batch* b, int tile) {
   std::vector<BatchItem> items;
-  std::vector<int> first(b->P + 1, 0);
-  for (int p = 0; p < b->P; ++p) {
-    first[p] = (int)items.size();
-    for (long long a = 0; a < b->n_host[p]; a += tile)
-      items.push_back(BatchItem{a, (int)std::min<long long>(tile, b->n_host[p] - a), p});
+  std::vector<int> ranges(2 * b->P, 0);  // [first item, end) of each point
+  for (auto& g : b->groups) {
+    g.item0 = (int)items.size();
+    for (int p : g.points) {
+      ranges[2 * p] = (int)items.size();
+      for (long long a = 0; a < b->n_host[p]; a += tile)
+        items.push_back(BatchItem{a, (int)std::min<long long>(tile, b->n_host[p] - a), p});
+      ranges[2 * p + 1] = (int)items.size();
+    }
+    g.n_items = (int)items.size() - g.item0;
   }
-  first[b->P] = (int)items.size();
   cudaFree(b->d_items);
   cudaFree(b->d_first);
   cudaFree(b->d_partials);
@@ -119,7 +132,7 @@ static int build_queue(rift_ile_batch* b, int tile) {
   b->d_first = nullptr;
   b->d_partials = nullptr;
   int rc = alloc_copy(&b->d_items, items.data(), items.size(), "work queue");
-  if (!rc) rc = alloc_copy(&b->d_first, first.data(), b->P + 1, "item offsets");
+  if (!rc) rc = alloc_copy(&b->d_first, ranges.data(), ranges.size(), "item ranges");
   if (!rc) rc = alloc_copy(&b->d_partials, (LseState*)nullptr, items.size(), "partials");
   b->n_items = (int)items.size();
   b->tile = tile;
@@ -157,8 +170,6 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
   std::vector<const PointParams*> hp(P);
   std::vector<DrawsParams> hd(P);
   std::vector<double> nd(P);
-  int maxM = 1, maxR = 2;
-  size_t smem = 0;
   int rc = RIFT_ILE_OK;
   for (int p = 0; p < P && !rc; ++p) {
     const rift_ile_point* pt = pts[p];
@@ -182,33 +193,51 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
     dp.n = d->n;
     dp.f64 = (d->dtype == RIFT_ILE_F64);
     nd[p] = (double)d->n;
-    maxM = std::max(maxM, pt->host.M);
-    maxR = std::max(maxR, pt->host.R);
     b->pts.push_back(pt);
   }
   b->dps = hd;
   if (!rc && prec == RIFT_ILE_FP32_MIXED) {
-    for (int p = 0; p < P; ++p)
-      smem = std::max(smem, batch_smem_for(maxM, maxR, pts[p]->host.ncls, pts[p]->host.R,
-                                           pts[p]->host.M));
-    b->kernel = batch_kernel_for(maxM, maxR);
-    b->smem = smem;
-    cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    b->max_blocks = b->blocks = grid_for(b->kernel, 128, smem);
+    // one group per compiled kernel shape, in order of first appearance
+    for (int p = 0; p < P && !rc; ++p) {
+      const BatchKernelFn k = batch_kernel_for(pts[p]->host.M, pts[p]->host.R);
+      if (!k) {
+        rift_ile_set_error("rift_ile_batch_create: point %d has no kernel of width %d", p,
+                           pts[p]->host.R);
+        rc = RIFT_ILE_ERR_UNSUPPORTED;
+        break;
+      }
+      size_t gi = 0;
+      while (gi < b->groups.size() && b->groups[gi].kernel != k) ++gi;
+      if (gi == b->groups.size()) {
+        b->groups.emplace_back();
+        b->groups.back().kernel = k;
+      }
+      auto& g = b->groups[gi];
+      g.points.push_back(p);
+      g.smem = std::max(g.smem, batch_smem_for(pts[p]->host.M, pts[p]->host.R, pts[p]->host.ncls,
+                                               pts[p]->host.R, pts[p]->host.M));
+    }
+    for (auto& g : b->groups) {
+      cudaFuncSetAttribute(g.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      g.max_blocks = grid_for(g.kernel, 128, g.smem);
+    }
     b->n_host.resize(P);
     for (int p = 0; p < P; ++p) b->n_host[p] = hd[p].n;
     if (!rc) rc = alloc_copy(&b->d_pts, hp.data(), P, "point table");
     if (!rc) rc = alloc_copy(&b->d_dps, hd.data(), P, "draw table");
     if (!rc) rc = build_queue(b, kDefaultTile);
     if (!rc) rc = alloc_copy(&b->d_ndraws, nd.data(), P, "draw counts");
-    if (!rc) rc = alloc_copy(&b->d_head, (unsigned int*)nullptr, 1, "queue head");
+    if (!rc) rc = alloc_copy(&b->d_head, (unsigned int*)nullptr, b->groups.size(), "queue heads");
     if (!rc) rc = alloc_copy(&b->d_oob, (unsigned long long*)nullptr, 1, "counter");
   } else if (!rc) {
     // FP64: one fused lnL -> LSE launch per point into its own slice of partials
     b->parts_per_point = device_sms() * kMaxPartialsPerSM;
-    std::vector<int> f2(P + 1);
-    for (int p = 0; p <= P; ++p) f2[p] = p * b->parts_per_point;
-    if (!rc) rc = alloc_copy(&b->d_first, f2.data(), P + 1, "item offsets");
+    std::vector<int> f2(2 * P);
+    for (int p = 0; p < P; ++p) {
+      f2[2 * p] = p * b->parts_per_point;
+      f2[2 * p + 1] = (p + 1) * b->parts_per_point;
+    }
+    if (!rc) rc = alloc_copy(&b->d_first, f2.data(), 2 * P, "item ranges");
     if (!rc) rc = alloc_copy(&b->d_ndraws, nd.data(), P, "draw counts");
     if (!rc) rc = alloc_copy(&b->d_partials, (LseState*)nullptr, (size_t)P * b->parts_per_point, "partials");
     if (!rc) rc = alloc_copy(&b->d_oob, (unsigned long long*)nullptr, 1, "counter");
@@ -231,11 +260,15 @@ extern "C" int rift_ile_batch_launch(rift_ile_batch* b, double* out, void* strea
   if ((rc = check_cuda(cudaMemsetAsync(b->d_oob, 0, sizeof(unsigned long long), st), "batch clear")))
     return rc;
   if (b->prec == RIFT_ILE_FP32_MIXED) {
-    if ((rc = check_cuda(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), st), "batch clear")))
+    if ((rc = check_cuda(cudaMemsetAsync(b->d_head, 0, b->groups.size() * sizeof(unsigned int), st),
+                         "batch clear")))
       return rc;
-    if (b->n_items > 0) {
-      b->kernel<<<b->blocks, 128, b->smem, st>>>(b->d_pts, b->d_dps, b->d_items, b->n_items,
-                                                 b->d_head, b->d_partials, b->d_oob);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+      const auto& g = b->groups[gi];
+      if (g.n_items == 0) continue;
+      const int blocks = std::max(1, g.max_blocks * b->quarters / 4);
+      g.kernel<<<blocks, 128, g.smem, st>>>(b->d_pts, b->d_dps, b->d_items + g.item0, g.n_items,
+                                            b->d_head + gi, b->d_partials + g.item0, b->d_oob);
       if ((rc = check_cuda(cudaGetLastError(), "batch kernel launch"))) return rc;
     }
   } else {
@@ -267,7 +300,7 @@ extern "C" int rift_ile_batch_tune(rift_ile_batch* b, int32_t reps, void* stream
   cudaStream_t st = (cudaStream_t)stream;
   int rc = RIFT_ILE_OK;
   double best_ms = -1.0;
-  int best_tile = b->tile, best_blocks = b->blocks;
+  int best_tile = b->tile, best_quarters = b->quarters;
   if (b->prec == RIFT_ILE_FP32_MIXED && b->n_items > 0) {
     double* out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -282,7 +315,7 @@ extern "C" int rift_ile_batch_tune(rift_ile_batch* b, int32_t reps, void* stream
     for (int ti = 0; ti < 6 && !rc; ++ti) {
       rc = build_queue(b, kTiles[ti]);
       for (int qi = 0; qi < 3 && !rc; ++qi) {
-        b->blocks = std::max(1, b->max_blocks * kQuarters[qi] / 4);
+        b->quarters = kQuarters[qi];
         rc = rift_ile_batch_launch(b, out, stream);  // warm-up
         if (!rc) rc = check_cuda(cudaEventRecord(e0, st), "tune timing");
         for (int r = 0; r < reps && !rc; ++r) rc = rift_ile_batch_launch(b, out, stream);
@@ -293,18 +326,27 @@ extern "C" int rift_ile_batch_tune(rift_ile_batch* b, int32_t reps, void* stream
         if (!rc && (best_ms < 0.0 || ms / reps < best_ms)) {
           best_ms = ms / reps;
           best_tile = kTiles[ti];
-          best_blocks = b->blocks;
+          best_quarters = b->quarters;
         }
       }
     }
     if (!rc) rc = build_queue(b, best_tile);
-    b->blocks = best_blocks;
+    b->quarters = best_quarters;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(out);
   }
   if (tile_out) *tile_out = b->tile;
-  if (blocks_out) *blocks_out = b->blocks;
+  if (blocks_out) {  // blocks of the largest group's launch
+    int bl = 0;
+    size_t big = 0;
+    for (const auto& g : b->groups)
+      if ((size_t)g.n_items >= big) {
+        big = g.n_items;
+        bl = std::max(1, g.max_blocks * b->quarters / 4);
+      }
+    *blocks_out = bl;
+  }
   if (ms_out) *ms_out = best_ms;
   return rc;
 }

@@ -26,8 +26,9 @@ struct BatchItem {
 };
 typedef void (*BatchKernelFn)(const PointParams* const*, const DrawsParams*, const BatchItem*, int,
                               unsigned int*, LseState*, unsigned long long*);
-// The persistent FP32-mixed batch kernel for the largest M and R of a batch
-// (launch with 128 threads and the largest table smem of the batch).
+// The persistent FP32-mixed batch kernel for points of M modes and padded
+// whitened width R (nullptr if no kernel has exactly that width); launched
+// with 128 threads.
 BatchKernelFn batch_kernel_for(int M, int R);
 // Its dynamic shared memory for one point (ncls classes, width Rp, Mp modes).
 size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp);

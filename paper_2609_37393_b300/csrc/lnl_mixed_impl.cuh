@@ -432,7 +432,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
   const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
   const df tc = load_param_df(dp, 6, i);
-  const int M = P.M, D = P.D, R = P.R, n = P.n;
+  const int M = P.M, R = P.R, n = P.n;
 
   // distance factor x = D_ref e^{-lnD}
   df lx = two_sum(P.ln_dref_hi, -lnD);
@@ -560,27 +560,6 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const int k = P.det_order[q];
       df xFr, xFi;
       antenna_df(P, k, AS, xer, xei, xFr, xFi);
-      // w_r = xFr a1_r + xFi a2_r: heads of xF on the grid of the larger part;
-      // head x head products (10 x 10 bits) and their sum are exact, the
-      // cross terms are >= 2^8 smaller.  w is kept as the unnormalised pair
-      // (exact head sum, FP32 correction); every use takes hi + lo as a sum.
-      const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
-      const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
-      const float xrt = __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo);
-      const float xit = __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo);
-      df w[RR];
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const float4 q = get_a(r);  // (a1 head, a1 tail, a2 head, a2 tail)
-        const float wh = fmaf(xrh, q.x, xih * q.z);
-        float lo = xrh * q.y;
-        lo = fmaf(xrt, q.x, lo);
-        lo = fmaf(xrt, q.y, lo);
-        lo = fmaf(xih, q.w, lo);
-        lo = fmaf(xit, q.z, lo);
-        lo = fmaf(xit, q.w, lo);
-        w[r] = df{wh, lo};
-      }
       // arrival time (shared by co-located detectors) and table position
       if (!P.same_pos_prev[q]) {
         delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
@@ -642,52 +621,88 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         wtd[2] = -(f * fd + fa * fd + fa * f) * 0.5f;
         wtd[3] = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
       }
-      float res[RR], edr[GRAD ? RR : 1];
-#pragma unroll
-      for (int r = 0; r < RR; ++r) res[r] = 0.f;
-      if (GRAD) {
-#pragma unroll
-        for (int r = 0; r < RR; ++r) edr[r] = 0.f;
-      }
+      // taps j-1 .. j+2: row index (clamped) and whether it is in the table
       const float2* Ek = P.ehat + (size_t)k * n * R;
+      bool vld[4];
+      int rowi[4];
 #pragma unroll
       for (int tap = 0; tap < 4; ++tap) {
         const float jj = jf - 1.f + (float)tap;
-        const bool valid = (jj >= 0.f && jj < (float)n);
-        if (!valid) ++oob;
-        const float2* row = Ek + (size_t)(valid ? (int)jj : 0) * R;
+        vld[tap] = (jj >= 0.f && jj < (float)n);
+        if (!vld[tap]) ++oob;
+        rowi[tap] = vld[tap] ? (int)jj : 0;
+      }
+      // Per pair of directions: the template w_r = xFr a1_r + xFi a2_r (heads
+      // of xF on the grid of its larger part; head x head products of 10 x 10
+      // bits and their sum exact, the cross terms >= 2^8 smaller; w kept as
+      // the unnormalised pair (exact head sum, FP32 correction)), then the
+      // residual r = e - w = sum_i wt_i (e_i - w) - sigma (e_j - w) with FP32
+      // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
+      // weights' sum, the low part of w taken out of the taps and subtracted
+      // once (the weights with sigma removed sum to one).
+      const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
+      const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
+      const float xrt = __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo);
+      const float xit = __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo);
+      float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
+      dacc w2 = dacc_zero();
 #pragma unroll
-        for (int r = 0; r < RR; r += 2) {
-          if (EXACT || r < R) {
+      for (int r = 0; r < RR; r += 2) {
+        if (EXACT || r < R) {
+          df wv[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 q = get_a(r + h);  // (a1 head, a1 tail, a2 head, a2 tail)
+            float lo = xrh * q.y;
+            lo = fmaf(xrt, q.x, lo);
+            lo = fmaf(xrt, q.y, lo);
+            lo = fmaf(xih, q.w, lo);
+            lo = fmaf(xit, q.z, lo);
+            lo = fmaf(xit, q.w, lo);
+            wv[h] = df{fmaf(xrh, q.x, xih * q.z), lo};
+          }
+          float rs0 = 0.f, rs1 = 0.f, ed0 = 0.f, ed1 = 0.f;
+#pragma unroll
+          for (int tap = 0; tap < 4; ++tap) {
             // rows hold R pairs, R even: two entries per 16-byte load
-            float4 e2 = valid ? __ldg(reinterpret_cast<const float4*>(row + r))
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-            // e_i - w with the low part of w taken out: it is added once below
-            // (the weights with sigma removed sum to one)
-            const float d0 = __fadd_rn(__fsub_rn(e2.x, w[r].hi), e2.y);
-            const float d1 = __fadd_rn(__fsub_rn(e2.z, w[r + 1].hi), e2.w);
-            res[r] = fmaf(wt[tap], d0, res[r]);
-            res[r + 1] = fmaf(wt[tap], d1, res[r + 1]);
+            const float4 e2 =
+                vld[tap] ? __ldg(reinterpret_cast<const float4*>(Ek + (size_t)rowi[tap] * R + r))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float d0 = __fadd_rn(__fsub_rn(e2.x, wv[0].hi), e2.y);
+            const float d1 = __fadd_rn(__fsub_rn(e2.z, wv[1].hi), e2.w);
+            rs0 = fmaf(wt[tap], d0, rs0);
+            rs1 = fmaf(wt[tap], d1, rs1);
             if (tap == 1) {  // sigma is ~1 ulp of wt: applied apart
-              res[r] = fmaf(-sigma, d0, res[r]);
-              res[r + 1] = fmaf(-sigma, d1, res[r + 1]);
+              rs0 = fmaf(-sigma, d0, rs0);
+              rs1 = fmaf(-sigma, d1, rs1);
             }
             if (GRAD) {  // dt edot = sum_i wtd_i (e_i - w)  (the wtd sum to zero)
-              edr[r] = fmaf(wtd[tap], d0, edr[r]);
-              edr[r + 1] = fmaf(wtd[tap], d1, edr[r + 1]);
+              ed0 = fmaf(wtd[tap], d0, ed0);
+              ed1 = fmaf(wtd[tap], d1, ed1);
             }
           }
-        }
-      }
+          const float rsv[2] = {__fsub_rn(rs0, wv[0].lo), __fsub_rn(rs1, wv[1].lo)};
+          const float edv[2] = {ed0, ed1};
 #pragma unroll
-      for (int r = 0; r < RR; ++r) res[r] = __fsub_rn(res[r], w[r].lo);
-      float q2 = 0.f, nul = 0.f;
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        if (EXACT || r < R) {
-          q2 = fmaf(res[r], res[r], q2);
-          const float wf = __fadd_rn(w[r].hi, w[r].lo);
-          nul = fmaf(gc[r] * wf, wf, nul);
+          for (int h = 0; h < 2; ++h) {
+            q2 = fmaf(rsv[h], rsv[h], q2);
+            const float wf = __fadd_rn(wv[h].hi, wv[h].lo);
+            nul = fmaf(gc[r + h] * wf, wf, nul);
+            if (DIST) {  // |w|^2 with the head square exact
+              dacc_fma_ff(w2, wv[h].hi, wv[h].hi);
+              w2.c = fmaf(2.f * wv[h].hi, wv[h].lo, w2.c);
+              w2.c = fmaf(wv[h].lo, wv[h].lo, w2.c);
+            }
+            if (GRAD) {
+              red = fmaf(rsv[h], edv[h], red);
+              const float rho = fmaf(gc[r + h], wf, rsv[h]);
+              const float4 q = get_a(r + h);
+              g1 = fmaf(rho, __fadd_rn(q.x, q.y), g1);
+              g2 = fmaf(rho, __fadd_rn(q.z, q.w), g2);
+              G1[r + h] = fmaf(xFr.hi, rho, G1[r + h]);
+              G2[r + h] = fmaf(xFi.hi, rho, G2[r + h]);
+            }
+          }
         }
       }
       dacc_add(T, half_e2);
@@ -695,16 +710,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       if (P.has_null[c] && !DIST) dacc_add(T, df{0.5f * nul, 0.f});
       if (DIST) {
         // K_k = e.w = 1/2|e|^2 + 1/2|w|^2 - 1/2|e - w|^2 (the first and last are in T
-        // already); R_k = |w|^2 - sum_r gm1_r w_r^2, with |w|^2 exact in pairs
-        dacc w2 = dacc_zero();
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          if (EXACT || r < R) {
-            dacc_fma_ff(w2, w[r].hi, w[r].hi);
-            w2.c = fmaf(2.f * w[r].hi, w[r].lo, w2.c);
-            w2.c = fmaf(w[r].lo, w[r].lo, w2.c);
-          }
-        }
+        // already); R_k = |w|^2 - sum_r gm1_r w_r^2
         const df w2d = dacc_result(w2);
         dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
         dacc_add(Racc, w2d);
@@ -712,19 +718,6 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       }
       if (GRAD) {
         // time: d lnL_k / d t_k = (P'(f) - r . edot dt) / dt
-        float red = 0.f, g1 = 0.f, g2 = 0.f;
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          if (EXACT || r < R) {
-            red = fmaf(res[r], edr[r], red);
-            const float rho = fmaf(gc[r], __fadd_rn(w[r].hi, w[r].lo), res[r]);
-            const float4 q = get_a(r);
-            g1 = fmaf(rho, __fadd_rn(q.x, q.y), g1);
-            g2 = fmaf(rho, __fadd_rn(q.z, q.w), g2);
-            G1[r] = fmaf(xFr.hi, rho, G1[r]);
-            G2[r] = fmaf(xFi.hi, rho, G2[r]);
-          }
-        }
         const df dtk = df_mul(df_add_f(dhalf, -red), df{P.inv_dt_hi, P.inv_dt_lo});
         const float dka = -(P.pos_hi[k][0] * dsa[0] + P.pos_hi[k][1] * dsa[1]);
         const float dkd = -(P.pos_hi[k][0] * dsd[0] + P.pos_hi[k][1] * dsd[1] + P.pos_hi[k][2] * dsd[2]);
@@ -836,16 +829,14 @@ __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem
 
 template <int MM, int RR, bool LSE, bool GRAD = false, bool DIST = false>
 __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_MIXED_MIN_BLOCKS)
-    lnl_mixed_kernel(const PointParams* __restrict__ gP,
-                                                        DrawsParams dp, double* __restrict__ lnl_out,
-                                                        LseState* __restrict__ partials,
-                                                        unsigned long long* __restrict__ oob_count,
-                                                        double* __restrict__ grad_out = nullptr,
-                                                        DistParams dist = DistParams{}) {
-  __shared__ PointParams P;
+    lnl_mixed_kernel(const __grid_constant__ PointParams P, DrawsParams dp,
+                     double* __restrict__ lnl_out, LseState* __restrict__ partials,
+                     unsigned long long* __restrict__ oob_count,
+                     double* __restrict__ grad_out = nullptr, DistParams dist = DistParams{}) {
+  // The point's parameters are a kernel parameter (constant bank, read with
+  // warp-uniform addresses; 7.4 KB, within the 32 KB parameter limit), so
+  // they need neither shared memory nor staging.
   extern __shared__ float4 smem4[];
-  stage_point(P, gP);
-  __syncthreads();
   stage_split_A(P, smem4);
   __syncthreads();
   const float4* sA = smem4;
@@ -901,7 +892,7 @@ cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const D
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   *blocks = grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem);
-  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
+  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }
 
@@ -914,7 +905,7 @@ cudaError_t launch_mixed_dist_k(const PointParams& hp, const PointParams* dP, co
   auto kern = lnl_mixed_kernel<MM, RR, LSE, false, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   *blocks = grid_for(kern, 128, smem);
-  kern<<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob, nullptr, dist);
+  kern<<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob, nullptr, dist);
   return cudaGetLastError();
 }
 
@@ -954,7 +945,7 @@ cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, c
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, false, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   const int blocks = grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem);
-  lnl_mixed_kernel<MM, RR, false, true><<<blocks, 128, smem, st>>>(dP, dp, lnl_out, nullptr, nullptr,
+  lnl_mixed_kernel<MM, RR, false, true><<<blocks, 128, smem, st>>>(hp, dp, lnl_out, nullptr, nullptr,
                                                                    grad_out);
   return cudaGetLastError();
 }
@@ -975,7 +966,7 @@ cudaError_t launch_mixed_grad_dist_mr(const PointParams& hp, const PointParams* 
   auto kern = lnl_mixed_kernel<MM, RR, false, true, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   const int blocks = grid_for(kern, 128, smem);
-  kern<<<blocks, 128, smem, st>>>(dP, dp, lnl_out, nullptr, nullptr, grad_out, dist);
+  kern<<<blocks, 128, smem, st>>>(hp, dp, lnl_out, nullptr, nullptr, grad_out, dist);
   return cudaGetLastError();
 }
 
@@ -996,7 +987,7 @@ cudaError_t launch_mixed_k_sms(const PointParams& hp, const PointParams* dP, con
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   *blocks = grid_for_sms(lnl_mixed_kernel<MM, RR, LSE>, 128, smem, sms);
-  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(dP, dp, lnl_out, partials, oob);
+  lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }
 
@@ -1048,7 +1039,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
     ThreadLse st = tlse_init();
     const long long end = it.begin + it.count;
     for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
-      MixedDraw o = lnl_mixed_draw<MM, RR, false>(P, sA, sg, a12s, sdp, i);
+      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, sA, sg, a12s, sdp, i);
       oob += o.oob;
       float lw = 0.f;
       if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
@@ -1065,8 +1056,10 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
 
 template <int MM>
 BatchKernelFn pick_batch_kernel(int R) {
-  if (R <= MM) return lnz_batch_kernel<MM, MM>;
-  return lnz_batch_kernel<MM, 2 * MM>;
+  // every point of a group has exactly the compiled width (tables padded)
+  if (R == MM) return lnz_batch_kernel<MM, MM>;
+  if (R == 2 * MM) return lnz_batch_kernel<MM, 2 * MM>;
+  return nullptr;
 }
 
 
@@ -1118,7 +1111,7 @@ BatchKernelFn mixed_batch_kernel(int R) {
 // point with ncls classes of width Rp and Mp modes.
 template <int MM>
 size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp) {
-  return R <= MM ? mixed_smem_bytes<MM>(ncls, Rp, Mp) : mixed_smem_bytes<2 * MM>(ncls, Rp, Mp);
+  return R == MM ? mixed_smem_bytes<MM>(ncls, Rp, Mp) : mixed_smem_bytes<2 * MM>(ncls, Rp, Mp);
 }
 
 template <int MM>
