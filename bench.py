@@ -109,10 +109,11 @@ def captured_traffic():
         return None
     vals = {}
     for line in text.splitlines():
-        if ":" in line and line.strip().startswith(("kernel_source_sha256", "dram_bytes_per_launch",
-                                                    "draws_per_launch")):
-            k, v = line.strip().strip("`").split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
+        item = line.strip().lstrip("-").strip().strip("`")
+        if ":" in item and item.startswith(("kernel_source_sha256", "dram_bytes_per_launch",
+                                            "draws_per_launch")):
+            k, v = item.split(":", 1)
+            vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256") != kernel_source_hash():
         return None
     try:

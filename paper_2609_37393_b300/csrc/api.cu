@@ -67,15 +67,16 @@ int get_workspace(Workspace** out) {
   return RIFT_ILE_OK;
 }
 
-// Merges the per-block states in a fixed order (one block of 256 threads:
-// thread t folds partials t, t+256, ...; thread 0 folds the 256 results).
-__global__ void __launch_bounds__(1024) lse_combine_kernel(const LseState* __restrict__ partials,
-                                                           int nparts, double n_total,
-                                                           LseState* __restrict__ out) {
-  // each thread merges a fixed strided subset in index order, then a fixed tree
+// Merges the per-block states in a fixed order.  One warp: each lane merges a fixed strided subset in index order, then a
+// fixed shuffle tree.  A single warp is the fastest shape here: every merge
+// costs an FP64 exponential, and a wider block only adds tree levels whose
+// FP64 instructions all queue on the one SM's narrow FP64 pipe.
+__global__ void __launch_bounds__(32) lse_combine_kernel(const LseState* __restrict__ partials,
+                                                         int nparts, double n_total,
+                                                         LseState* __restrict__ out) {
   LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc = lse_merge(acc, partials[i]);
-  acc = block_lse_reduce(acc);
+  acc = warp_lse_reduce(acc);
   if (threadIdx.x == 0) {
     acc.n = n_total;
     if (isnan(acc.m)) acc.m = acc.s = acc.s2 = CUDART_NAN;
@@ -208,7 +209,7 @@ int device_sms() {
 
 cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
                                LseState* state_out, cudaStream_t st) {
-  lse_combine_kernel<<<1, 1024, 0, st>>>(partials, nparts, n_total, state_out);
+  lse_combine_kernel<<<1, 32, 0, st>>>(partials, nparts, n_total, state_out);
   return cudaGetLastError();
 }
 
