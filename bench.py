@@ -43,6 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DRAWS = 1 << 22
+W_PARAMS = ("ra", "dec", "psi", "incl", "phase", "lnD", "t")
 WORKLOAD = "3G ILE: ET triangle + CE40 (K=4), 10 modes, SNR 600, 2^22 float32 draws"
 
 
@@ -210,6 +211,17 @@ def cpu_baseline(point, draws, logw, budget_s: float = 12.0):
             "sample": f"first {n} draws of the 2^22-draw batch, lnL + lnZ in FP64 C, {threads} threads"}
 
 
+def cpu_single_thread(point, draws, n=1 << 14):
+    """The FP64 oracle on one host core (lnL only), draws/s."""
+    import oracle as O
+    opt = O.OraclePoint(point)
+    sub = {p: np.asarray(draws[p][:n]) for p in draws}
+    t0 = time.perf_counter()
+    O.lnL(opt, sub, threads=1)
+    return {"value": n / (time.perf_counter() - t0), "unit": "draws/s", "cores": 1,
+            "sample": f"first {n} draws, lnL in FP64 C"}
+
+
 def run_reference(args, world, rank):
     """--impl reference: the FP64 CPU oracle on the same workload and metric."""
     if rank != 0:
@@ -296,6 +308,17 @@ def run_batch(args):
         pts.append(R.Point(point))
         draws.append(R.Draws(d, lw))
         total += len(d["t"])
+    # the oracle on the first points, whole, until ~5 s of host work
+    import oracle as O
+    t0c, done, k = time.perf_counter(), 0, 0
+    while k < len(gen) and time.perf_counter() - t0c < 5.0:
+        point, d, lw = gen[k]
+        O.lnZ(O.lnL(O.OraclePoint(point), d), np.asarray(lw, dtype=np.float64))
+        done += len(d["t"])
+        k += 1
+    cpu = {"value": done / (time.perf_counter() - t0c), "unit": "draws/s",
+           "cores": O.default_threads(), "kind": "oracle",
+           "sample": f"first {k} points whole ({done} draws), lnL + lnZ in FP64 C"}
     del gen
     setup_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -323,6 +346,7 @@ def run_batch(args):
         "speedup_vs_fp64_per_point": ms64 / ms32,
         "max_abs_dlnZ_vs_fp64": float(np.nanmax(np.abs(o32[:, 0] - o64[:, 0]))),
         "gpu_launches": 2 * args.steps, "graph": True, "setup_s": setup_s,
+        "cpu_baseline": cpu,
         "autotune": {"tile": tile, "blocks": blocks, "ms_tuned": ms_tuned,
                      "ms_default_tile_4096": ms_default},
         "clocks": clocks.summary(),
@@ -342,6 +366,15 @@ def run_event(args):
     rho = math.sqrt(info["rho2"])
     nodes = R.rift_ile_dist_nodes(50.0, 200.0, 100.0, 1e-4, 1000.0)
     dev = [R.Draws(g[2], g[3]) for g in gen]
+    # the oracle's distance-marginalised lnL and gradient on a sample of chunk 0
+    import oracle as O
+    ns = 1 << 15
+    sub = {p: np.asarray(gen[0][2][p][:ns]) for p in W_PARAMS}
+    t0c = time.perf_counter()
+    O.lnL_distmarg(O.OraclePoint(point), sub, nodes[0], nodes[1], grad=True)
+    cpu = {"value": ns / (time.perf_counter() - t0c), "unit": "draws/s",
+           "cores": O.default_threads(), "kind": "oracle",
+           "sample": f"first {ns} draws of chunk 0, distance-marginalised lnL + gradient in FP64 C"}
     del gen
     stream = torch.cuda.current_stream()
     lnl = torch.empty(N_DRAWS, dtype=torch.float64, device="cuda")
@@ -368,6 +401,7 @@ def run_event(args):
         "fwd_bwd_ms": ms_fb32, "fp64_fwd_bwd_draws_per_s": n / (ms_fb64 * 1e-3),
         "lnZ_draws_per_s": n / (ms_z32 * 1e-3), "fp64_lnZ_draws_per_s": n / (ms_z64 * 1e-3),
         "speedup_fwd_bwd_vs_fp64": ms_fb64 / ms_fb32, "lnZ": z32[0], "abs_dlnZ_vs_fp64": abs(z32[0] - z64[0]),
+        "cpu_baseline": cpu,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -539,9 +573,10 @@ def main():
         "plain_formula_flops_per_draw": plain_formula_flops(K, M),
     }
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(point, draws, logw)
+        cpu1 = cpu_single_thread(point, draws)
 
     if rank == 0:
         line = {
@@ -564,6 +599,7 @@ def main():
             "roofline": roofline,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
+            "cpu_oracle_single_thread": cpu1,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

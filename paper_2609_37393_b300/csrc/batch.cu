@@ -215,7 +215,7 @@ extern "C" int rift_ile_batch_create(const rift_ile_point* const* pts, const rif
       auto& g = b->groups[gi];
       g.points.push_back(p);
       g.smem = std::max(g.smem, batch_smem_for(pts[p]->host.M, pts[p]->host.R, pts[p]->host.ncls,
-                                               pts[p]->host.R, pts[p]->host.M));
+                                               pts[p]->host.R, pts[p]->host.M, pts[p]->host.K));
     }
     for (auto& g : b->groups) {
       cudaFuncSetAttribute(g.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -30,8 +30,9 @@ typedef void (*BatchKernelFn)(const PointParams* const*, const DrawsParams*, con
 // whitened width R (nullptr if no kernel has exactly that width); launched
 // with 128 threads.
 BatchKernelFn batch_kernel_for(int M, int R);
-// Its dynamic shared memory for one point (ncls classes, width Rp, Mp modes).
-size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp);
+// Its dynamic shared memory for one point (ncls classes, width Rp, Mp modes,
+// Kp detectors).
+size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp, int Kp);
 
 // lnL (lnl_out may be NULL) and its gradient, grad_out[7][n].
 cudaError_t launch_grad_mixed(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,

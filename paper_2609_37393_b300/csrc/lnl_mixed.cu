@@ -31,7 +31,7 @@ cudaError_t mixed_grad_dist(const PointParams&, const PointParams*, const DrawsP
 template <int MM>
 BatchKernelFn mixed_batch_kernel(int R);
 template <int MM>
-size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp);
+size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp, int Kp);
 template <int MM>
 int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab);
 
@@ -113,8 +113,8 @@ cudaError_t launch_grad_mixed_dist(const PointParams& hp, const PointParams* dP,
 
 BatchKernelFn batch_kernel_for(int M, int R) { return RIFT_DISPATCH_M(M, mixed_batch_kernel, R); }
 
-size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp) {
-  return RIFT_DISPATCH_M(M, mixed_batch_smem, R, ncls, Rp, Mp);
+size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp, int Kp) {
+  return RIFT_DISPATCH_M(M, mixed_batch_smem, R, ncls, Rp, Mp, Kp);
 }
 
 }  // namespace rift

@@ -34,7 +34,7 @@
 // __launch_bounds__, and whether the large double-float helpers are real
 // calls (smaller code, fewer instruction-cache misses) or inlined.
 #ifndef RIFT_MIXED_MIN_BLOCKS
-#define RIFT_MIXED_MIN_BLOCKS 7
+#define RIFT_MIXED_MIN_BLOCKS 6
 #endif
 #ifndef RIFT_MIXED_MIN_BLOCKS_GRAD  // kernels that carry the adjoint
 #define RIFT_MIXED_MIN_BLOCKS_GRAD 4
@@ -70,18 +70,27 @@ struct A12Smem {
 };
 
 // Bytes of dynamic shared memory of a FP32-mixed kernel: the split whitening
-// of every class, gm1, and (A12Smem) the per-thread a1, a2 slices.
+// of every class, gm1, (A12Smem) the per-thread a1, a2 slices, and the
+// per-thread x F_k of the K detectors.
 template <int RR>
-__host__ __device__ inline size_t mixed_smem_bytes(int ncls, int R, int M) {
+__host__ __device__ inline size_t mixed_smem_bytes(int ncls, int R, int M, int K) {
   size_t b = (size_t)ncls * R * M * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
   if (A12Smem<RR>::on) b += (size_t)RR * kMixedThreads * 16;
-  return b;
+  return b + (size_t)K * kMixedThreads * 16;
 }
 
 template <int RR>
 __device__ __forceinline__ float4* a12_slice(float4* smem4, int ncls, int R, int M) {
   if (!A12Smem<RR>::on) return nullptr;
   const size_t off = (size_t)ncls * R * M * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  return reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + off) + threadIdx.x;
+}
+
+// This thread's slots of x F_k (as head/tail pairs), slot k at [k * kMixedThreads].
+template <int RR>
+__device__ __forceinline__ float4* xf_slice(float4* smem4, int ncls, int R, int M) {
+  size_t off = (size_t)ncls * R * M * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  if (A12Smem<RR>::on) off += (size_t)RR * kMixedThreads * 16;
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + off) + threadIdx.x;
 }
 
@@ -425,7 +434,7 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
 // marginal's K and R) instead of D_ref e^{-lnD}.
 template <int MM, int RR, bool GRAD, bool DIST = false, bool EXACT = false>
 __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const float4* sA,
-                                                    const float* sg, float4* a12s,
+                                                    const float* sg, float4* a12s, float4* xfs,
                                                     const DrawsParams& dp, long long i,
                                                     df xin = df{1.f, 0.f}) {
   const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
@@ -457,6 +466,17 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   df s2p, c2p;
   sincos_df(df{2.f * psi, 0.f}, s2p, c2p);
   const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
+  // x F_k of every detector, kept in this thread's shared-memory slots as
+  // (head, tail) pairs on the grid of the larger part (see the template
+  // product below), so the sky functions need not stay in registers
+  for (int k = 0; k < P.K; ++k) {
+    df xFr, xFi;
+    antenna_df(P, k, AS, xer, xei, xFr, xFi);
+    const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
+    const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
+    xfs[k * kMixedThreads] = make_float4(xrh, __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo), xih,
+                                         __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo));
+  }
   df sz, z;  // sin and cos of the inclination
   sincos_df(df{incl, 0.f}, sz, z);
 
@@ -558,8 +578,9 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     }
     for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
       const int k = P.det_order[q];
-      df xFr, xFi;
-      antenna_df(P, k, AS, xer, xei, xFr, xFi);
+      const float4 xfq = xfs[k * kMixedThreads];
+      const float xrh = xfq.x, xrt = xfq.y, xih = xfq.z, xit = xfq.w;
+      const df xFr = df{__fadd_rn(xrh, xrt), 0.f}, xFi = df{__fadd_rn(xih, xit), 0.f};  // FP32 uses
       // arrival time (shared by co-located detectors) and table position
       if (!P.same_pos_prev[q]) {
         delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
@@ -640,10 +661,6 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
       // weights' sum, the low part of w taken out of the taps and subtracted
       // once (the weights with sigma removed sum to one).
-      const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
-      const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
-      const float xrt = __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo);
-      const float xit = __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo);
       float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
       dacc w2 = dacc_zero();
 #pragma unroll
@@ -842,6 +859,7 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   const float4* sA = smem4;
   const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M);
   float4* a12s = a12_slice<RR>(smem4, P.ncls, P.R, P.M);
+  float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
   ThreadLse st = tlse_init();
   int oob = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -850,17 +868,17 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
     if (DIST && GRAD) {
       // distance-marginal gradient: E[x] dK - E[x^2] dR / 2 equals (a / xbar)
       // times the gradient at x = xbar = E[x^2]/E[x] (a = E[x]; the lnD slot is 0)
-      MixedDraw k1 = lnl_mixed_draw<MM, RR, false, true, true>(P, sA, sg, a12s, dp, i);
+      MixedDraw k1 = lnl_mixed_draw<MM, RR, false, true, true>(P, sA, sg, a12s, xfs, dp, i);
       float ex[2] = {1.f, 1.f};
       const df marg = isnan(k1.lnl.hi) ? k1.lnl : dist_marg_df(dist, k1.lnl, k1.R, ex);
       const float xbar = ex[1] / ex[0], sc = ex[0] / xbar;
-      o = lnl_mixed_draw<MM, RR, true, true, true>(P, sA, sg, a12s, dp, i, df{xbar, 0.f});
+      o = lnl_mixed_draw<MM, RR, true, true, true>(P, sA, sg, a12s, xfs, dp, i, df{xbar, 0.f});
       for (int p = 0; p < kNpar; ++p) o.grad[p] *= sc;
       o.grad[5] = 0.0;
       o.lnl = marg;
       o.oob = k1.oob;
     } else {
-      o = lnl_mixed_draw<MM, RR, GRAD, DIST, true>(P, sA, sg, a12s, dp, i);
+      o = lnl_mixed_draw<MM, RR, GRAD, DIST, true>(P, sA, sg, a12s, xfs, dp, i);
       if (DIST) o.lnl = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R);
     }
     oob += o.oob;
@@ -888,7 +906,7 @@ cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const D
                            double* lnl_out, LseState* partials, unsigned long long* oob,
                            int* blocks, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
-  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M);
+  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   *blocks = grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem);
@@ -901,7 +919,7 @@ cudaError_t launch_mixed_dist_k(const PointParams& hp, const PointParams* dP, co
                                 const DistParams& dist, double* lnl_out, LseState* partials,
                                 unsigned long long* oob, int* blocks, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
-  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M);
+  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   auto kern = lnl_mixed_kernel<MM, RR, LSE, false, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   *blocks = grid_for(kern, 128, smem);
@@ -941,7 +959,7 @@ template <int MM, int RR>
 cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                                  double* lnl_out, double* grad_out, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
-  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M);
+  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, false, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   const int blocks = grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem);
@@ -962,7 +980,7 @@ cudaError_t launch_mixed_grad_dist_mr(const PointParams& hp, const PointParams* 
                                       const DrawsParams& dp, const DistParams& dist, double* lnl_out,
                                       double* grad_out, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
-  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M);
+  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   auto kern = lnl_mixed_kernel<MM, RR, false, true, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   const int blocks = grid_for(kern, 128, smem);
@@ -983,7 +1001,7 @@ cudaError_t launch_mixed_k_sms(const PointParams& hp, const PointParams* dP, con
                                double* lnl_out, LseState* partials, unsigned long long* oob,
                                int sms, int* blocks, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
-  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M);
+  const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   *blocks = grid_for_sms(lnl_mixed_kernel<MM, RR, LSE>, 128, smem, sms);
@@ -1036,10 +1054,11 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
     const float4* sA = smem4;
     const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M);
     float4* a12s = a12_slice<RR>(smem4, P.ncls, P.R, P.M);
+    float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
     ThreadLse st = tlse_init();
     const long long end = it.begin + it.count;
     for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
-      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, sA, sg, a12s, sdp, i);
+      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, sA, sg, a12s, xfs, sdp, i);
       oob += o.oob;
       float lw = 0.f;
       if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
@@ -1108,10 +1127,10 @@ BatchKernelFn mixed_batch_kernel(int R) {
 }
 
 // Dynamic shared memory of the batch kernel mixed_batch_kernel<MM>(R) for a
-// point with ncls classes of width Rp and Mp modes.
+// point with ncls classes of width Rp, Mp modes and Kp detectors.
 template <int MM>
-size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp) {
-  return R == MM ? mixed_smem_bytes<MM>(ncls, Rp, Mp) : mixed_smem_bytes<2 * MM>(ncls, Rp, Mp);
+size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp, int Kp) {
+  return R == MM ? mixed_smem_bytes<MM>(ncls, Rp, Mp, Kp) : mixed_smem_bytes<2 * MM>(ncls, Rp, Mp, Kp);
 }
 
 template <int MM>
@@ -1136,7 +1155,7 @@ int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab) {
                                            const DrawsParams&, const DistParams&, double*,        \
                                            double*, cudaStream_t);                                \
   template BatchKernelFn mixed_batch_kernel<MM>(int);                                             \
-  template size_t mixed_batch_smem<MM>(int, int, int, int);                                       \
+  template size_t mixed_batch_smem<MM>(int, int, int, int, int);                                       \
   template int mixed_upload_anchors<MM>(const float4*, const float2*);
 
 }  // namespace rift
