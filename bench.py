@@ -63,10 +63,15 @@ def algorithmic_ops(point: dict, R: int, ncls: int) -> dict:
     # (the antenna basis is also split into heads and tails once per draw: 40)
     fixed = (10 + expo) + (10 + 2 * sincos + 2 * df_mul) + 187 + 40 + (sincos + 2 * df_mul) + sincos
     # modes: Horner in cos(iota) (15 per degree), sin(iota) factor for odd m,
-    # Y = amp e^{i m phi} and its split, one sine/cosine per change of |m|
-    n_phase = sum(1 for a in range(M) if a == 0 or abs(em[a]) != abs(em[a - 1]))
+    # Y = amp e^{i m phi} and its split; the modes are visited by increasing
+    # |m|: e^{i |m| phi} by one pair complex product (68) when |m| grows by
+    # one after |m| = 1 was met, otherwise by an anchored sine/cosine
     modes = sum(15 * l for l in ell) + df_mul * sum(1 for m in em if m % 2) + M * (2 * df_mul + 8)
-    modes += n_phase * sincos
+    prev, have1 = -1, False
+    for am in sorted({abs(m) for m in em}):
+        modes += 68 if (have1 and am == prev + 1) else sincos
+        have1 = have1 or am == 1
+        prev = am
     # split product a1, a2 (12 per entry); per direction two TwoSums and the
     # head/tail split of the pair (20)
     matvec = 12 * R * M + 20 * R

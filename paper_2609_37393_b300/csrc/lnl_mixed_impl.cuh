@@ -34,7 +34,7 @@
 // __launch_bounds__, and whether the large double-float helpers are real
 // calls (smaller code, fewer instruction-cache misses) or inlined.
 #ifndef RIFT_MIXED_MIN_BLOCKS
-#define RIFT_MIXED_MIN_BLOCKS 6
+#define RIFT_MIXED_MIN_BLOCKS 5
 #endif
 #ifndef RIFT_MIXED_MIN_BLOCKS_GRAD  // kernels that carry the adjoint
 #define RIFT_MIXED_MIN_BLOCKS_GRAD 4
@@ -506,13 +506,28 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 #pragma unroll
     for (int r = 0; r < RR; ++r) ex1[r] = ex2[r] = co1[r] = co2[r] = 0.f;
     const float4* Ac = sA + (size_t)c * R * M;
+    // modes in order of increasing |m| (P.morder): e^{i |m| phi} is reused
+    // across modes of equal |m| and stepped by one complex product with
+    // e^{i phi} when |m| grows by one; otherwise an anchored sine/cosine
     int prev_am = -1;
-    df cm = df{1.f, 0.f}, sm = df{0.f, 0.f};
-    for (int a = 0; a < M; ++a) {
-      // e^{i m phi}: reused across the +-m members of a mode pair
+    df cm = df{1.f, 0.f}, sm = df{0.f, 0.f}, c1 = df{1.f, 0.f}, s1p = df{0.f, 0.f};
+    bool have1 = false;
+    for (int j = 0; j < M; ++j) {
+      const int a = P.morder[j];
       const int m = P.em[a], am = m < 0 ? -m : m;
       if (am != prev_am) {
-        sincos_df(two_prod((float)am, phi), sm, cm);
+        if (have1 && am == prev_am + 1) {
+          const df cn = df_sub(df_mul(cm, c1), df_mul(sm, s1p));
+          sm = df_add(df_mul(sm, c1), df_mul(cm, s1p));
+          cm = cn;
+        } else {
+          sincos_df(two_prod((float)am, phi), sm, cm);
+          if (am == 1) {
+            c1 = cm;
+            s1p = sm;
+            have1 = true;
+          }
+        }
         prev_am = am;
       }
       const df amp = sylm_amp_df(P, a, z, sz);
@@ -528,7 +543,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       for (int r = 0; r < RR; ++r) {
         if (EXACT || r < R) {
           // (head, tail) of A[r][a] and of A[r][M + a]
-          const float4 ah = Ac[r * M + a];
+          const float4 ah = Ac[r * M + j];
           // a1_r += A_t yr + A_b yi ;  a2_r += A_b yr - A_t yi
           ex1[r] = fmaf(ah.x, yr1, ex1[r]);
           ex1[r] = fmaf(ah.z, yi1, ex1[r]);
@@ -768,12 +783,13 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const float ci = z.hi, si = sz.hi;
       float cmf = 1.f, smf = 0.f;
       int prev = -1;
-      for (int a = 0; a < M; ++a) {
+      for (int j = 0; j < M; ++j) {
+        const int a = P.morder[j];
         float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
           if (EXACT || r < R) {
-            const float4 ah = Ac2[r * M + a];
+            const float4 ah = Ac2[r * M + j];
             const float ath = ah.x + ah.y, abh = ah.z + ah.w;
             h1t = fmaf(G1[r], ath, h1t);
             h1b = fmaf(G1[r], abh, h1b);
@@ -817,7 +833,8 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 }
 
 // Stages the whitening matrices of all classes into shared memory in split
-// form: entry (r, a < M) holds (head, tail) of A[r][a] and of A[r][M + a],
+// form: entry (r, j < M) holds (head, tail) of A[r][a] and of A[r][M + a] for
+// mode a = morder[j] (modes in the kernels' order of increasing |m|),
 // head = A_hi rounded to a multiple of 2^-9 of a power of two >= max_a
 // |A[r][a]| (10 significant bits; the error-free product of lnl_mixed_draw
 // relies on it), tail = (A_hi - head) + A_lo rounded to FP32; then gm1.
@@ -833,11 +850,12 @@ __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem
     int e = 0;
     frexpf(mx, &e);  // mx < 2^e
     const float C = ldexpf(1.5f, e + 14);  // ulp(C) = 2^(e - 9)
-    for (int a = 0; a < M; ++a) {
+    for (int j = 0; j < M; ++j) {
+      const int a = P.morder[j];
       const float2 v = __ldg(row + a), u = __ldg(row + M + a);
       const float hv = __fsub_rn(__fadd_rn(v.x, C), C);
       const float hu = __fsub_rn(__fadd_rn(u.x, C), C);
-      sA[(size_t)t * M + a] = make_float4(hv, __fadd_rn(__fsub_rn(v.x, hv), v.y), hu,
+      sA[(size_t)t * M + j] = make_float4(hv, __fadd_rn(__fsub_rn(v.x, hv), v.y), hu,
                                           __fadd_rn(__fsub_rn(u.x, hu), u.y));
     }
     sg[t] = __ldg(P.gm1 + t);

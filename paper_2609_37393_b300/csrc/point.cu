@@ -410,6 +410,12 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     for (int r = 0; r < nt; ++r) P.ycoef[i][r] = coef[r];
   }
 
+  {  // the FP32-mixed kernels visit the modes by increasing |m| (stable)
+    int j = 0;
+    for (int am = 0; am <= RIFT_ILE_MAX_ELL; ++am)
+      for (int i = 0; i < M; ++i)
+        if (std::abs(P.em[i]) == am) P.morder[j++] = i;
+  }
   split_df(std::log(d->d_ref), &P.ln_dref_hi, &P.ln_dref_lo);
   for (int k = 0; k < K; ++k) {
     for (int c = 0; c < 6; ++c) split_df(P.resp[k][c], &P.resp_hi[k][c], &P.resp_lo[k][c]);

@@ -56,6 +56,7 @@ struct PointParams {
   // the same amplitude in z = cos(iota) for the mixed path (c^2 = (1 + z)/2,
   // s^2 = (1 - z)/2, c s = sin(iota)/2): sin(iota)^ypar sum_{j <= l} yz[j] z^j
   int ypar[kMaxModes];
+  int morder[kMaxModes];  // mixed path: modes by increasing |m| (stable)
   float yz_hi[kMaxModes][kMaxEll + 1], yz_lo[kMaxModes][kMaxEll + 1];
   // detector classes (identical U_k, V_k share one whitening): the detectors
   // of class c are det_order[cls_begin[c] .. cls_begin[c+1]).
