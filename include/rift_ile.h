@@ -211,6 +211,24 @@ int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws* draws,
 int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_ile_draws* draws,
                                rift_ile_precision prec, rift_ile_lse* state, void* stream);
 
+/* rift_ile_lnZ_state for draws in HOST memory (the end-to-end path; the
+ * paper's sampler produces draws on the host): the seven parameter arrays and
+ * logw of host_draws are HOST pointers (page-locked memory lets the copies
+ * overlap the kernels; pageable memory works but serialises).  The draws are
+ * copied in chunks of `chunk` draws (0: 2^20) into two library-owned device
+ * staging buffers on a library copy stream, double-buffered against the fused
+ * lnL -> LSE kernel on `stream`; the per-chunk block partials are merged once
+ * at the end in a fixed order.  The result agrees with rift_ile_lnZ_state on
+ * the same draws to rounding (the partials group the draws differently).
+ * Synchronous: returns when both streams are idle; not capturable in a graph;
+ * concurrent calls on one process are serialised (they share the buffers).
+ * Allocates the staging buffers and partials on first use (grown on demand,
+ * freed by rift_ile_release).  The host arrays must stay valid until return.
+ * Errors: INVALID_ARG, SHAPE, CUDA, ALLOC. */
+int rift_ile_lnZ_state_host(const rift_ile_point* pt, const rift_ile_draws* host_draws,
+                            rift_ile_precision prec, const rift_ile_dist* dist, int64_t chunk,
+                            rift_ile_lse* state, void* stream);
+
 /* Exact merge of S LSE states (HOST) into out[3] = lnZ, sigma_lnZ, n_eff;
  * merged_state (may be NULL) receives the merged state.  Host only. */
 int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],

@@ -75,6 +75,7 @@ _lib.rift_ile_lnL_grad.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_state.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_merge.argtypes = [_P, ctypes.c_int32, _P, _P]
+_lib.rift_ile_lnZ_state_host.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P, _P]
 _lib.rift_ile_lnZ_batch.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P, _P]
 _lib.rift_ile_batch_create.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P]
 _lib.rift_ile_batch_launch.argtypes = [_P, _P, _P]
@@ -214,6 +215,59 @@ class Draws:
     @property
     def ref(self):
         return ctypes.byref(self.struct)
+
+
+class HostDraws:
+    """Draws in HOST memory for rift_ile_lnZ_state_host: seven arrays (and an
+    optional ln p - ln p_s) as numpy arrays or CPU tensors, float32 or float64
+    (page-locked CPU tensors let the library overlap copies and kernels)."""
+
+    def __init__(self, draws: dict, logw=None):
+        torch = _torch()
+
+        def host(x, dtype=None):
+            t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+            if t.is_cuda:
+                raise ValueError("HostDraws takes host arrays")
+            if dtype is not None and t.dtype != dtype:
+                t = t.to(dtype)
+            return t.contiguous()
+
+        self.t = {p: host(draws[p]) for p in PARAMS}
+        dtype = self.t[PARAMS[0]].dtype
+        if dtype not in (torch.float32, torch.float64):
+            raise ValueError("draws must be float32 or float64")
+        self.t = {p: host(v, dtype) for p, v in self.t.items()}
+        self.logw = None if logw is None else host(logw, dtype)
+        n = self.t[PARAMS[0]].numel()
+        if any(v.numel() != n for v in self.t.values()) or (self.logw is not None and self.logw.numel() != n):
+            raise ValueError("host draw arrays differ in length")
+        self.n = n
+        s = _Draws()
+        for p in PARAMS:
+            setattr(s, p, self.t[p].data_ptr() if n else None)
+        s.logw = self.logw.data_ptr() if (self.logw is not None and n) else None
+        s.n = n
+        s.dtype = 1 if dtype == torch.float64 else 0
+        self.struct = s
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def rift_ile_lnZ_state_host(point: Point, host_draws, precision: int = FP32_MIXED, dist=None,
+                            chunk: int = 0, stream=None):
+    """LSE state of draws held in host memory, copied in double-buffered chunks
+    overlapping the fused kernel (end-to-end path)."""
+    d = host_draws if isinstance(host_draws, HostDraws) else HostDraws(host_draws)
+    st = _Lse()
+    ds, keep = _dist_struct(dist)
+    _check(_lib.rift_ile_lnZ_state_host(point.handle, d.ref, precision,
+                                        ctypes.byref(ds) if ds is not None else None,
+                                        chunk, ctypes.byref(st), _stream(stream)))
+    del keep
+    return (st.m, st.s, st.s2, st.n)
 
 
 def _as_draws(draws, logw=None):

@@ -4,6 +4,7 @@
 #include <math_constants.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -281,6 +282,159 @@ extern "C" int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws
   return RIFT_ILE_OK;
 }
 
+namespace rift {
+namespace {
+
+// Per-device state of the host-streaming lnZ: two staging buffer sets, a copy
+// stream, the events that order copies and kernels, and the partials of all
+// chunks of one call.  Allocated on first use, grown on demand.
+struct HostStream {
+  char* buf[2] = {nullptr, nullptr};
+  size_t buf_bytes = 0;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  LseState* partials = nullptr;
+  size_t cap = 0;
+};
+
+HostStream g_hs[64];
+std::mutex g_hs_mu;
+
+int get_host_stream(size_t bytes_per_buf, size_t nparts, HostStream** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    rift_ile_set_error("no current CUDA device");
+    return RIFT_ILE_ERR_CUDA;
+  }
+  HostStream& h = g_hs[dev];
+  int rc = RIFT_ILE_OK;
+  if (!h.copy) {
+    if ((rc = check_cuda(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking), "copy stream")))
+      return rc;
+    for (int b = 0; b < 2 && !rc; ++b) {
+      rc = check_cuda(cudaEventCreateWithFlags(&h.copied[b], cudaEventDisableTiming), "event");
+      if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&h.consumed[b], cudaEventDisableTiming), "event");
+    }
+    if (rc) return rc;
+  }
+  if (h.buf_bytes < bytes_per_buf) {
+    cudaFree(h.buf[0]);
+    cudaFree(h.buf[1]);
+    h.buf[0] = h.buf[1] = nullptr;
+    h.buf_bytes = 0;
+    if (cudaMalloc((void**)&h.buf[0], bytes_per_buf) != cudaSuccess ||
+        cudaMalloc((void**)&h.buf[1], bytes_per_buf) != cudaSuccess) {
+      rift_ile_set_error("host-stream staging allocation failed");
+      return RIFT_ILE_ERR_ALLOC;
+    }
+    h.buf_bytes = bytes_per_buf;
+  }
+  if (h.cap < nparts) {
+    cudaFree(h.partials);
+    h.partials = nullptr;
+    h.cap = 0;
+    if (cudaMalloc((void**)&h.partials, nparts * sizeof(LseState)) != cudaSuccess) {
+      rift_ile_set_error("host-stream partials allocation failed");
+      return RIFT_ILE_ERR_ALLOC;
+    }
+    h.cap = nparts;
+  }
+  *out = &h;
+  return RIFT_ILE_OK;
+}
+
+}  // namespace
+}  // namespace rift
+
+extern "C" int rift_ile_lnZ_state_host(const rift_ile_point* pt, const rift_ile_draws* host_draws,
+                                       rift_ile_precision prec, const rift_ile_dist* dist,
+                                       int64_t chunk, rift_ile_lse* state, void* stream) {
+  int rc = check_point(pt, prec);
+  if (!rc) rc = check_draws(host_draws);
+  if (rc) return rc;
+  if (!state || chunk < 0) {
+    rift_ile_set_error("rift_ile_lnZ_state_host: state is NULL or chunk < 0");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const long long n = host_draws->n;
+  if (n == 0) {
+    *state = rift_ile_lse{-INFINITY, 0.0, 0.0, 0.0};
+    t_last_oob = 0;
+    return RIFT_ILE_OK;
+  }
+  if (chunk == 0) chunk = 1 << 20;
+  chunk = std::min<long long>(chunk, n);
+  const size_t esz = host_draws->dtype == RIFT_ILE_F64 ? 8 : 4;
+  const int narr = host_draws->logw ? 8 : 7;
+  const long long nchunks = (n + chunk - 1) / chunk;
+  Workspace* ws = nullptr;
+  if ((rc = get_workspace(&ws))) return rc;
+  const size_t per_chunk_parts = (size_t)ws->sms * kMaxPartialsPerSM;
+  HostStream* hs = nullptr;
+  // one call at a time uses the staging buffers (concurrent callers queue here)
+  std::lock_guard<std::mutex> lock(g_hs_mu);
+  if ((rc = get_host_stream((size_t)narr * chunk * esz, per_chunk_parts * nchunks, &hs))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  DistParams dd{};
+  if (dist && (rc = upload_dist(ws, dist, st, &dd))) return rc;
+  if ((rc = check_cuda(cudaMemsetAsync(ws->oob, 0, sizeof(unsigned long long), st), "memset")))
+    return rc;
+  // the copy stream starts after what the caller queued before this call
+  cudaEvent_t start = hs->consumed[1];
+  if ((rc = check_cuda(cudaEventRecord(start, st), "event"))) return rc;
+  if ((rc = check_cuda(cudaStreamWaitEvent(hs->copy, start, 0), "stream wait"))) return rc;
+  const void* src[8] = {host_draws->ra, host_draws->dec, host_draws->psi, host_draws->incl,
+                        host_draws->phase, host_draws->lnD, host_draws->t, host_draws->logw};
+  size_t off_parts = 0;
+  for (long long c = 0; c < nchunks && !rc; ++c) {
+    const int b = (int)(c & 1);
+    const long long a0 = c * chunk, cnt = std::min<long long>(chunk, n - a0);
+    // copies of chunk c into buffer b once the kernel of chunk c - 2 is done with it
+    if (c >= 2) rc = check_cuda(cudaStreamWaitEvent(hs->copy, hs->consumed[b], 0), "stream wait");
+    DrawsParams dp{};
+    for (int q = 0; q < narr && !rc; ++q) {
+      char* dst = hs->buf[b] + (size_t)q * chunk * esz;
+      rc = check_cuda(cudaMemcpyAsync(dst, (const char*)src[q] + (size_t)a0 * esz, (size_t)cnt * esz,
+                                      cudaMemcpyHostToDevice, hs->copy),
+                      "host-to-device copy");
+      if (q < 7) dp.p[q] = dst;
+      else dp.logw = dst;
+    }
+    if (!rc) rc = check_cuda(cudaEventRecord(hs->copied[b], hs->copy), "event");
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(st, hs->copied[b], 0), "stream wait");
+    if (rc) break;
+    dp.n = cnt;
+    dp.f64 = (host_draws->dtype == RIFT_ILE_F64);
+    int blocks = 0;
+    cudaError_t le;
+    if (!dist)
+      le = launch_lnl(pt, dp, prec, nullptr, hs->partials + off_parts, ws->oob, &blocks, st);
+    else if (prec == RIFT_ILE_FP64)
+      le = launch_lnl_fp64_dist(pt->host, pt->dev, dp, dd, nullptr, hs->partials + off_parts, ws->oob,
+                                &blocks, st);
+    else
+      le = launch_lnl_mixed_dist(pt->host, pt->dev, dp, dd, nullptr, hs->partials + off_parts, ws->oob,
+                                 &blocks, st);
+    if ((rc = check_cuda(le, "lnZ kernel launch"))) break;
+    off_parts += blocks;
+    rc = check_cuda(cudaEventRecord(hs->consumed[b], st), "event");
+  }
+  if (!rc)
+    rc = check_cuda(launch_lse_combine(hs->partials, (int)off_parts, (double)n, ws->state, st),
+                    "lnZ combine launch");
+  LseState h{};
+  unsigned long long oob = 0;
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(&h, ws->state, sizeof(h), cudaMemcpyDeviceToHost, st), "copy");
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(&oob, ws->oob, sizeof(oob), cudaMemcpyDeviceToHost, st), "copy");
+  // both streams are idle when this returns (also after an error)
+  cudaError_t e1 = cudaStreamSynchronize(hs->copy), e2 = cudaStreamSynchronize(st);
+  if (!rc) rc = check_cuda(e1 != cudaSuccess ? e1 : e2, "rift_ile_lnZ_state_host");
+  if (rc) return rc;
+  t_last_oob = (long long)oob;
+  *state = rift_ile_lse{h.m, h.s, h.s2, h.n};
+  return RIFT_ILE_OK;
+}
+
 extern "C" int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
                                   rift_ile_lse* merged) {
   if ((!states && S > 0) || S < 0) {
@@ -431,6 +585,23 @@ extern "C" int rift_ile_release(void) {
     cudaFree(w.dist_xdf);
     cudaFree(w.dist_lnwf);
     w = Workspace();
+  }
+  {
+    std::lock_guard<std::mutex> lock2(g_hs_mu);
+    for (int d = 0; d < 64; ++d) {
+      HostStream& h = g_hs[d];
+      if (!h.copy) continue;
+      cudaSetDevice(d);
+      cudaFree(h.buf[0]);
+      cudaFree(h.buf[1]);
+      cudaFree(h.partials);
+      for (int b = 0; b < 2; ++b) {
+        cudaEventDestroy(h.copied[b]);
+        cudaEventDestroy(h.consumed[b]);
+      }
+      cudaStreamDestroy(h.copy);
+      h = HostStream();
+    }
   }
   cudaSetDevice(cur);
   return RIFT_ILE_OK;

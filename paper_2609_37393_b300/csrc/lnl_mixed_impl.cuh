@@ -34,7 +34,7 @@
 // __launch_bounds__, and whether the large double-float helpers are real
 // calls (smaller code, fewer instruction-cache misses) or inlined.
 #ifndef RIFT_MIXED_MIN_BLOCKS
-#define RIFT_MIXED_MIN_BLOCKS 5
+#define RIFT_MIXED_MIN_BLOCKS 4
 #endif
 #ifndef RIFT_MIXED_MIN_BLOCKS_GRAD  // kernels that carry the adjoint
 #define RIFT_MIXED_MIN_BLOCKS_GRAD 4
