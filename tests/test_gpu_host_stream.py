@@ -29,10 +29,13 @@ def cfg():
     return W.config1(n_draws=(1 << 18) + 12345)
 
 
-def close(a, b, rel=1e-12):
+def close(a, b, prec=0):
+    """Same state up to the grouping of the sums: FP64 partials agree to
+    ~1e-15, the FP32-mixed per-thread sums of e^(v - m) to ~1e-7 relative."""
+    tol = 1e-12 if prec == 0 else 1e-6
     lz_a, lz_b = a[0] + math.log(a[1]), b[0] + math.log(b[1])
-    return abs(lz_a - lz_b) <= rel * max(1.0, abs(lz_b)) and a[3] == b[3] and \
-        abs(a[2] / a[1] ** 2 - b[2] / b[1] ** 2) <= 1e-9 * (b[2] / b[1] ** 2)
+    return abs(lz_a - lz_b) <= tol and a[3] == b[3] and \
+        abs(a[2] / a[1] ** 2 - b[2] / b[1] ** 2) <= tol * (b[2] / b[1] ** 2)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -44,7 +47,7 @@ def test_host_stream_matches_resident(R, cfg, prec, chunk):
     pinned = {p: torch.from_numpy(np.ascontiguousarray(draws[p])).pin_memory() for p in W.PARAMS}
     hd = R.HostDraws(pinned, torch.from_numpy(np.ascontiguousarray(logw)).pin_memory())
     got = R.rift_ile_lnZ_state_host(pt, hd, prec, chunk=chunk)
-    assert close(got, ref), (got, ref)
+    assert close(got, ref, prec), (got, ref)
     again = R.rift_ile_lnZ_state_host(pt, hd, prec, chunk=chunk)
     assert again == got  # deterministic
 
@@ -56,7 +59,7 @@ def test_host_stream_pageable_and_dist(R, cfg):
     ref = R.rift_ile_lnZ_state(pt, R.Draws(draws, logw), R.FP32_MIXED, dist=nodes)
     got = R.rift_ile_lnZ_state_host(pt, R.HostDraws(draws, logw), R.FP32_MIXED, dist=nodes,
                                     chunk=50_000)
-    assert close(got, ref), (got, ref)
+    assert close(got, ref, 1), (got, ref)
 
 
 def test_host_stream_empty(R, cfg):
