@@ -15,15 +15,19 @@ path, the ALU roofline of the kernel, sampled clocks and the FP64 CPU oracle
 as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ile|batch|event]
+                  [--workload ile|batch|event|diff|sweep]
 
---workload batch times the 512-point batching workload (2-5 detectors, 2-10
-modes, 8k-65k-sample tables, 1e4-1e6 draws per point): one persistent
-FP32-mixed launch replayed from a CUDA graph against one FP64 launch per
-point.  --workload event times the full 3G event (ET triangle + CE 40 km +
-CE 20 km, SNR 1000, +-50 ms table, 2^26 draws in 2^22 chunks): distance-
-marginalised forward+backward and lnZ, FP32-mixed against FP64.  The default
-(ile) is the headline line.
+The default workload (ile) is the headline line.  The others are extra
+measurements:
+  batch  the 512-point batching workload (2-5 detectors, 2-10 modes,
+         8k-65k-sample tables, 1e4-1e6 draws per point): persistent FP32-mixed
+         launches replayed from a CUDA graph, against one FP64 launch per point;
+  event  the full 3G event (ET triangle + CE 40 km + CE 20 km, SNR 1000,
+         +-50 ms table, 2^26 draws in 2^22 chunks): distance-marginalised
+         forward+backward and lnZ, FP32-mixed against FP64;
+  diff   forward+backward at SNR 1000 (2^20 draws) with the per-component
+         gradient error against the FP64 path;
+  sweep  the FP32-mixed error against the FP64 path at SNR 20 ... 1000.
 """
 from __future__ import annotations
 
@@ -412,6 +416,65 @@ def run_event(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Precision of the FP32-mixed path against network SNR (four-detector,
+    ten-mode network, 2^20 draws each): max |dlnL| near the peak and |dlnZ|
+    against the FP64 GPU path, which the tests pin to the oracle."""
+    import torch
+    import paper_2609_37393_b300 as R
+    import workload as W
+    torch.cuda.set_device(0)
+    rows = []
+    for snr in (20.0, 100.0, 300.0, 600.0, 1000.0):
+        point, exact, info, draws, logw = W.config_3g(1, 4, snr, 0.02, 1 << 20)
+        pt = R.Point(point)
+        d = R.Draws(draws, logw)
+        l64 = R.rift_ile_lnL(pt, d, R.FP64).cpu().numpy()
+        l32 = R.rift_ile_lnL(pt, d, R.FP32_MIXED).cpu().numpy()
+        near = l64 >= l64.max() - 50.0
+        err = np.abs(l32 - l64)
+        z64, z32 = R.rift_ile_lnZ(pt, d, R.FP64), R.rift_ile_lnZ(pt, d, R.FP32_MIXED)
+        rows.append({"snr": snr, "max_abs_dlnL_within_50nat": float(err[near].max()),
+                     "draws_within_50nat": int(near.sum()),
+                     "max_rel_dlnL_all": float(np.max(err / np.maximum(1.0, np.abs(l64)))),
+                     "abs_dlnZ": abs(z32[0] - z64[0]), "lnZ": z64[0]})
+    print(json.dumps({"workload": "sweep", "metric": "FP32-mixed error vs FP64 over SNR",
+                      "rows": rows}), flush=True)
+
+
+def run_diff(args):
+    """The differentiation workload: SNR 1000, 2^20 draws, forward+backward."""
+    import torch
+    import paper_2609_37393_b300 as R
+    import workload as W
+    torch.cuda.set_device(0)
+    n = 1 << 20
+    point, exact, info, draws, logw = W.config2(n_draws=n)
+    pt = R.Point(point)
+    d = R.Draws(draws, logw)
+    stream = torch.cuda.current_stream()
+    l32 = torch.empty(n, dtype=torch.float64, device="cuda")
+    l64 = torch.empty_like(l32)
+    g32 = torch.empty((7, n), dtype=torch.float64, device="cuda")
+    g64 = torch.empty_like(g32)
+    with ClockSampler(0) as clocks:
+        ms32 = timed_events(torch, lambda: R.rift_ile_lnL_grad(pt, d, R.FP32_MIXED, l32, g32),
+                            max(3, args.steps), stream)
+    ms64 = timed_events(torch, lambda: R.rift_ile_lnL_grad(pt, d, R.FP64, l64, g64), 2, stream)
+    R.rift_ile_lnL_grad(pt, d, R.FP32_MIXED, l32, g32)
+    R.rift_ile_lnL_grad(pt, d, R.FP64, l64, g64)
+    near = l64 >= l64.max() - 50.0
+    scale = g64.abs() + g64.pow(2).mean(dim=1, keepdim=True).sqrt()
+    rel = ((g32 - g64).abs() / scale)[:, near]
+    print(json.dumps({
+        "workload": "diff", "metric": "lnL draws/s fwd+bwd (SNR 1000, 2^20 draws)",
+        "value": n / (ms32 * 1e-3), "unit": "draws/s", "fp64_draws_per_s": n / (ms64 * 1e-3),
+        "speedup_vs_fp64": ms64 / ms32,
+        "max_abs_dlnL_within_50nat": float((l32 - l64).abs()[near].max()),
+        "max_rel_grad_err_within_50nat": {p: float(rel[j].max()) for j, p in enumerate(W.PARAMS)},
+        "clocks": clocks.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +482,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ile", choices=["ile", "batch", "event"])
+    ap.add_argument("--workload", default="ile", choices=["ile", "batch", "event", "diff", "sweep"])
     ap.add_argument("--points", type=int, default=512)
     ap.add_argument("--chunks", type=int, default=16)
     args = ap.parse_args()
@@ -434,6 +497,12 @@ def main():
         return
     if args.workload == "event":
         run_event(args)
+        return
+    if args.workload == "diff":
+        run_diff(args)
+        return
+    if args.workload == "sweep":
+        run_sweep(args)
         return
 
     import torch

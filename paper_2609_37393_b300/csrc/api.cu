@@ -68,19 +68,58 @@ int get_workspace(Workspace** out) {
   return RIFT_ILE_OK;
 }
 
-// Merges the per-block states in a fixed order.  One warp: each lane merges a fixed strided subset in index order, then a
-// fixed shuffle tree.  A single warp is the fastest shape here: every merge
-// costs an FP64 exponential, and a wider block only adds tree levels whose
-// FP64 instructions all queue on the one SM's narrow FP64 pipe.
-__global__ void __launch_bounds__(32) lse_combine_kernel(const LseState* __restrict__ partials,
-                                                         int nparts, double n_total,
-                                                         LseState* __restrict__ out) {
-  LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc = lse_merge(acc, partials[i]);
-  acc = warp_lse_reduce(acc);
-  if (threadIdx.x == 0) {
-    acc.n = n_total;
-    if (isnan(acc.m)) acc.m = acc.s = acc.s2 = CUDART_NAN;
+// Merges the per-block states in two passes over them: the largest maximum
+// M (a max is order-free), then the sums of s_i e^(m_i - M) and
+// s2_i e^(2(m_i - M)), each thread over a fixed strided subset and then a
+// fixed tree.  The exponentials are independent of one another, so they
+// pipeline instead of forming a chain of dependent merges (FP64 issues at
+// 2 per clock per SM on this part).  The result is reproducible bit for bit.
+__global__ void __launch_bounds__(256) lse_combine_kernel(const LseState* __restrict__ partials,
+                                                          int nparts, double n_total,
+                                                          LseState* __restrict__ out) {
+  __shared__ double red[256];
+  __shared__ double red2[256];
+  const int t = threadIdx.x;
+  double mx = -CUDART_INF;
+  int bad = 0;
+  for (int i = t; i < nparts; i += blockDim.x) {
+    const double m = partials[i].m;
+    if (isnan(m)) bad = 1;
+    else mx = fmax(mx, m);
+  }
+  bad = __syncthreads_or(bad);
+  red[t] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w) red[t] = fmax(red[t], red[t + w]);
+    __syncthreads();
+  }
+  const double M = red[0];
+  __syncthreads();
+  double s = 0.0, s2 = 0.0;
+  if (M > -CUDART_INF) {
+    for (int i = t; i < nparts; i += blockDim.x) {
+      const LseState p = partials[i];
+      if (!(p.m > -CUDART_INF)) continue;
+      const double e = lse_exp(p.m - M);
+      s = fma(p.s, e, s);
+      s2 = fma(p.s2, e * e, s2);
+    }
+  }
+  red[t] = s;
+  red2[t] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      red[t] += red[t + w];
+      red2[t] += red2[t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    LseState acc{M, red[0], red2[0], n_total};
+    if (!(M > -CUDART_INF)) acc = LseState{-CUDART_INF, 0.0, 0.0, n_total};
+    if (bad) acc.m = acc.s = acc.s2 = CUDART_NAN;
     *out = acc;
   }
 }
@@ -210,7 +249,7 @@ int device_sms() {
 
 cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
                                LseState* state_out, cudaStream_t st) {
-  lse_combine_kernel<<<1, 32, 0, st>>>(partials, nparts, n_total, state_out);
+  lse_combine_kernel<<<1, 256, 0, st>>>(partials, nparts, n_total, state_out);
   return cudaGetLastError();
 }
 

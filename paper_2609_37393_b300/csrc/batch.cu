@@ -32,31 +32,56 @@ __global__ void fill_empty_kernel(LseState* __restrict__ st, long long n) {
 }
 
 // out[p] = (lnZ, sigma_lnZ, n_eff) from the states of point p's items
-// [first[2p], first[2p+1]): one warp per point, each lane merging a fixed
-// strided subset in item order, then a fixed shuffle tree.
+// [first[2p], first[2p+1]): one warp per point, two passes (the largest
+// maximum, then the rescaled sums), each lane over a fixed strided subset and
+// a fixed shuffle tree, so the exponentials pipeline and the result is
+// reproducible.
 __global__ void batch_combine_kernel(const LseState* __restrict__ partials,
                                      const int* __restrict__ first, const double* __restrict__ ndraws,
                                      int P, double* __restrict__ out) {
   const int p = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (p >= P) return;  // whole warps leave together
-  LseState acc{-CUDART_INF, 0.0, 0.0, 0.0};
-  for (int i = first[2 * p] + lane; i < first[2 * p + 1]; i += 32) acc = lse_merge(acc, partials[i]);
-  acc = warp_lse_reduce(acc);
+  const int i0 = first[2 * p], i1 = first[2 * p + 1];
+  double M = -CUDART_INF;
+  int bad = 0;
+  for (int i = i0 + lane; i < i1; i += 32) {
+    const double m = partials[i].m;
+    if (isnan(m)) bad = 1;
+    else M = fmax(M, m);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    M = fmax(M, __shfl_xor_sync(0xffffffffu, M, off));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  double s = 0.0, s2 = 0.0;
+  if (M > -CUDART_INF) {
+    for (int i = i0 + lane; i < i1; i += 32) {
+      const LseState q = partials[i];
+      if (!(q.m > -CUDART_INF)) continue;
+      const double e = lse_exp(q.m - M);
+      s = fma(q.s, e, s);
+      s2 = fma(q.s2, e * e, s2);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, off);
+    s2 += __shfl_down_sync(0xffffffffu, s2, off);
+  }
   if (lane != 0) return;
   const double n = ndraws[p];
   double lnz, sig, neff;
-  if (isnan(acc.m)) {
+  if (bad) {
     lnz = sig = neff = CUDART_NAN;
-  } else if (n <= 0.0 || !(acc.m > -CUDART_INF)) {
+  } else if (n <= 0.0 || !(M > -CUDART_INF)) {
     lnz = -CUDART_INF;
     sig = CUDART_NAN;
     neff = 0.0;
   } else {
-    lnz = acc.m + log(acc.s) - log(n);
-    const double var = acc.s2 / (acc.s * acc.s) - 1.0 / n;
+    lnz = M + log(s) - log(n);
+    const double var = s2 / (s * s) - 1.0 / n;
     sig = sqrt(var > 0.0 ? var : 0.0);
-    neff = acc.s;
+    neff = s;
   }
   out[3 * p] = lnz;
   out[3 * p + 1] = sig;

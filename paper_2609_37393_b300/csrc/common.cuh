@@ -107,6 +107,34 @@ __device__ __forceinline__ int dist_nearest(const DistParams& dp, double x) {
   return (dp.x[lo] - x < x - dp.x[hi]) ? lo : hi;
 }
 
+// e^d for d <= 0 in FP64, for the LSE merges (FP64 issues at 2 per clock per
+// SM on this part, so the merge exponential is kept short): Cody-Waite
+// reduction d = k ln2 + r with ln2 split into a 31-bit head (k * head exact
+// for |k| < 2^21) and the rest, |r| <= ln2/2, then the Taylor polynomial of
+// e^r to degree 13 (remainder below 2^-57 relative) and the exact scaling by
+// 2^k.  Zero below the double range.
+__device__ __forceinline__ double lse_exp(double d) {
+  if (!(d > -745.0)) return 0.0;
+  const double k = rint(d * 1.4426950408889634);
+  double r = fma(-k, 0.6931471803691238, d);
+  r = fma(-k, 1.9082149292705877e-10, r);
+  double p = 1.6059043836821613e-10;  // 1/13!
+  p = fma(p, r, 2.08767569878681e-09);
+  p = fma(p, r, 2.505210838544172e-08);
+  p = fma(p, r, 2.755731922398589e-07);
+  p = fma(p, r, 2.7557319223985893e-06);
+  p = fma(p, r, 2.48015873015873e-05);
+  p = fma(p, r, 0.0001984126984126984);
+  p = fma(p, r, 0.001388888888888889);
+  p = fma(p, r, 0.008333333333333333);
+  p = fma(p, r, 0.041666666666666664);
+  p = fma(p, r, 0.16666666666666666);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  return scalbn(p, (int)k);
+}
+
 // ln sum_j exp(K x_j - R x_j^2 / 2 + ln w_j) (eq. ap:dexp on the node table),
 // written as K^2/(2R) + ln sum_j exp(ln w_j - R (x_j - x*)^2 / 2), x* = K/R,
 // visiting only nodes whose term can exceed the running maximum minus 40:
@@ -127,7 +155,7 @@ __device__ __forceinline__ double dist_lse(const DistParams& dp, double K, doubl
     for (int j = 0; j < dp.n; ++j) m = fmax(m, K * dp.x[j] - 0.5 * R * dp.x[j] * dp.x[j] + dp.lnw[j]);
     double s = 0.0, s1 = 0.0, s2 = 0.0;
     for (int j = 0; j < dp.n; ++j) {
-      const double e = exp(K * dp.x[j] - 0.5 * R * dp.x[j] * dp.x[j] + dp.lnw[j] - m);
+      const double e = lse_exp(K * dp.x[j] - 0.5 * R * dp.x[j] * dp.x[j] + dp.lnw[j] - m);
       s += e;
       s1 += e * dp.x[j];
       s2 += e * dp.x[j] * dp.x[j];
@@ -149,13 +177,13 @@ __device__ __forceinline__ double dist_lse(const DistParams& dp, double K, doubl
       if (dp.lnw_max - q < m - 40.0) break;
       const double t = dp.lnw[j] - q;
       if (t > m) {
-        const double r = exp(m - t);
+        const double r = lse_exp(m - t);
         s = s * r + 1.0;
         s1 = s1 * r + xj;
         s2 = s2 * r + xj * xj;
         m = t;
       } else {
-        const double e = exp(t - m);
+        const double e = lse_exp(t - m);
         s += e;
         s1 += e * xj;
         s2 += e * xj * xj;
@@ -226,16 +254,16 @@ __device__ __forceinline__ void tlse_push_lw(ThreadLse& t, df lnl, float lw) {
 }
 
 // Exact merge of two states: the smaller maximum is rescaled to the larger
-// one (one exponential; FP64 is slow on this part, so merges stay few).
+// one (one exponential).
 __device__ __forceinline__ LseState lse_merge(LseState a, LseState b) {
   if (isnan(a.m) || isnan(b.m)) return LseState{CUDART_NAN, CUDART_NAN, CUDART_NAN, a.n + b.n};
   if (a.m == -CUDART_INF) return LseState{b.m, b.s, b.s2, a.n + b.n};
   if (b.m == -CUDART_INF) return LseState{a.m, a.s, a.s2, a.n + b.n};
   if (a.m >= b.m) {
-    const double e = exp(b.m - a.m);
+    const double e = lse_exp(b.m - a.m);
     return LseState{a.m, fma(b.s, e, a.s), fma(b.s2, e * e, a.s2), a.n + b.n};
   }
-  const double e = exp(a.m - b.m);
+  const double e = lse_exp(a.m - b.m);
   return LseState{b.m, fma(a.s, e, b.s), fma(a.s2, e * e, b.s2), a.n + b.n};
 }
 
@@ -344,12 +372,12 @@ __device__ __forceinline__ void tlse64_push(ThreadLse64& t, double v) {
   }
   if (!(v > -CUDART_INF)) return;
   if (v > t.st.m) {
-    double e = (t.st.m == -CUDART_INF) ? 0.0 : exp(t.st.m - v);
+    double e = (t.st.m == -CUDART_INF) ? 0.0 : lse_exp(t.st.m - v);
     t.st.s = fma(t.st.s, e, 1.0);
     t.st.s2 = fma(t.st.s2, e * e, 1.0);
     t.st.m = v;
   } else {
-    double e = exp(v - t.st.m);
+    double e = lse_exp(v - t.st.m);
     t.st.s += e;
     t.st.s2 = fma(e, e, t.st.s2);
   }
