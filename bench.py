@@ -436,7 +436,7 @@ def run_sweep(args):
         z64, z32 = R.rift_ile_lnZ(pt, d, R.FP64), R.rift_ile_lnZ(pt, d, R.FP32_MIXED)
         rows.append({"snr": snr, "max_abs_dlnL_within_50nat": float(err[near].max()),
                      "draws_within_50nat": int(near.sum()),
-                     "max_rel_dlnL_all": float(np.max(err / np.maximum(1.0, np.abs(l64)))),
+                     "max_abs_dlnL_all_over_rho2": float(err.max() / snr ** 2),
                      "abs_dlnZ": abs(z32[0] - z64[0]), "lnZ": z64[0]})
     print(json.dumps({"workload": "sweep", "metric": "FP32-mixed error vs FP64 over SNR",
                       "rows": rows}), flush=True)
