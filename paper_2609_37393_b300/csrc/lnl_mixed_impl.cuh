@@ -37,7 +37,7 @@
 #define RIFT_MIXED_MIN_BLOCKS 4
 #endif
 #ifndef RIFT_MIXED_MIN_BLOCKS_GRAD  // kernels that carry the adjoint
-#define RIFT_MIXED_MIN_BLOCKS_GRAD 4
+#define RIFT_MIXED_MIN_BLOCKS_GRAD 3
 #endif
 // RIFT_MIXED_A_SMEM: keep a1, a2 of the current class in a per-thread slice
 // of shared memory instead of registers (for widths RR <= 12).
@@ -354,9 +354,13 @@ struct MixedDraw {
   df R;        // with DIST: the quadratic coefficient R at x = 1 (lnL(x) = K x - R x^2/2)
   int oob;
   double grad[kNpar];
+  // with GRAD and DIST (one pass at x = 1): grad = d lnL(1) = dK - dR/2 + ...
+  // split as in lnl_mixed_draw, and gradB = dR/2
+  double gradB[kNpar];
 };
 
-// Distance marginal of one draw from K and R (eq. ap:dexp, eq. ap:dlog):
+// Distance marginal of one draw from K and R (eq. ap:dexp, eq. ap:dlog);
+// ex (if given) receives the node-posterior moments E[x], E[x^2], E[x(1-x)]:
 // K^2/(2R) in double-float plus the node sum of dist_lse, in FP32 offsets
 // from x* = K/R (see dist_lse in common.cuh for the window rule).
 __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, float* ex = nullptr) {
@@ -366,6 +370,7 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
     if (ex) {
       ex[0] = (float)exd[0];
       ex[1] = (float)exd[1];
+      ex[2] = (float)(exd[0] - exd[1]);
     }
     return df_from_double(v);
   }
@@ -389,7 +394,7 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
     }
   }
   const int j0 = (dp.xdf[lo].x - xs.hi < xs.hi - dp.xdf[hi].x) ? lo : hi;
-  float m = -CUDART_INF_F, s = 0.f, s1 = 0.f, s2 = 0.f;
+  float m = -CUDART_INF_F, s = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   const float halfR = 0.5f * R.hi;
   const float lnw_max = (float)dp.lnw_max;
   for (int dir = -1; dir <= 1; dir += 2) {
@@ -399,23 +404,27 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
       const float q = halfR * d * d;
       if (lnw_max - q < m - 40.f) break;
       const float t = __ldg(dp.lnwf + j) - q;
+      const float xq = xj.x * __fsub_rn(1.f, xj.x);  // x (1 - x) without cancellation
       if (t > m) {
         const float r = __expf(m - t);
         s = fmaf(s, r, 1.f);
         s1 = fmaf(s1, r, xj.x);
         s2 = fmaf(s2, r, xj.x * xj.x);
+        s3 = fmaf(s3, r, xq);
         m = t;
       } else {
         const float e = __expf(t - m);
         s += e;
         s1 = fmaf(e, xj.x, s1);
         s2 = fmaf(e * xj.x, xj.x, s2);
+        s3 = fmaf(e, xq, s3);
       }
     }
   }
   if (ex) {
     ex[0] = s1 / s;
     ex[1] = s2 / s;
+    ex[2] = s3 / s;
   }
   const df peak = df_mul(K, xs);
   return df_add_f(df{0.5f * peak.hi, 0.5f * peak.lo}, m + __logf(s));
@@ -487,6 +496,9 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   // gradient accumulators: time-driven parts of (ra, dec, t) as pairs, the rest in FP32
   dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
   float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_incl = 0.f, g_phase = 0.f, g_lnd = 0.f;
+  // with GRAD and DIST: the same template derivatives weighted by (1 - gm1) w
+  constexpr bool TWO = GRAD && DIST;
+  float gB_ra = 0.f, gB_dec = 0.f, gB_psi = 0.f, gB_incl = 0.f, gB_phase = 0.f;
   AntennaBasisGrad ABG;
   float dsa[3] = {0.f, 0.f, 0.f}, dsd[3] = {0.f, 0.f, 0.f};
   if (GRAD) {
@@ -587,9 +599,14 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     const float* gc = sg + c * R;
     df delay = df{0.f, 0.f};
     float G1[GRAD ? RR : 1], G2[GRAD ? RR : 1];
+    float G1B[TWO ? RR : 1], G2B[TWO ? RR : 1];
     if (GRAD) {
 #pragma unroll
       for (int r = 0; r < RR; ++r) G1[r] = G2[r] = 0.f;
+    }
+    if (TWO) {
+#pragma unroll
+      for (int r = 0; r < RR; ++r) G1B[r] = G2B[r] = 0.f;
     }
     for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
       const int k = P.det_order[q];
@@ -676,7 +693,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
       // weights' sum, the low part of w taken out of the taps and subtracted
       // once (the weights with sigma removed sum to one).
-      float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
+      float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f, g1B = 0.f, g2B = 0.f;
       dacc w2 = dacc_zero();
 #pragma unroll
       for (int r = 0; r < RR; r += 2) {
@@ -733,6 +750,13 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
               g2 = fmaf(rho, __fadd_rn(q.z, q.w), g2);
               G1[r + h] = fmaf(xFr.hi, rho, G1[r + h]);
               G2[r + h] = fmaf(xFi.hi, rho, G2[r + h]);
+              if (TWO) {  // dR/2 = sum (1 - gm1) w . dw
+                const float rhoB = __fsub_rn(1.f, gc[r + h]) * wf;
+                g1B = fmaf(rhoB, __fadd_rn(q.x, q.y), g1B);
+                g2B = fmaf(rhoB, __fadd_rn(q.z, q.w), g2B);
+                G1B[r + h] = fmaf(xFr.hi, rhoB, G1B[r + h]);
+                G2B[r + h] = fmaf(xFi.hi, rhoB, G2B[r + h]);
+              }
             }
           }
         }
@@ -775,6 +799,11 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         g_dec = fmaf(dxrd, g1, fmaf(dxid, g2, g_dec));
         g_psi = fmaf(-2.f * xFi.hi, g1, fmaf(2.f * xFr.hi, g2, g_psi));
         g_lnd = fmaf(-xFr.hi, g1, fmaf(-xFi.hi, g2, g_lnd));
+        if (TWO) {
+          gB_ra = fmaf(dxra, g1B, fmaf(dxia, g2B, gB_ra));
+          gB_dec = fmaf(dxrd, g1B, fmaf(dxid, g2B, gB_dec));
+          gB_psi = fmaf(-2.f * xFi.hi, g1B, fmaf(2.f * xFr.hi, g2B, gB_psi));
+        }
       }
     }
     if (GRAD) {
@@ -786,6 +815,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       for (int j = 0; j < M; ++j) {
         const int a = P.morder[j];
         float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
+        float k1t = 0.f, k1b = 0.f, k2t = 0.f, k2b = 0.f;
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
           if (EXACT || r < R) {
@@ -795,9 +825,16 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
             h1b = fmaf(G1[r], abh, h1b);
             h2t = fmaf(G2[r], ath, h2t);
             h2b = fmaf(G2[r], abh, h2b);
+            if (TWO) {
+              k1t = fmaf(G1B[r], ath, k1t);
+              k1b = fmaf(G1B[r], abh, k1b);
+              k2t = fmaf(G2B[r], ath, k2t);
+              k2b = fmaf(G2B[r], abh, k2b);
+            }
           }
         }
         const float Hre = h1t + h2b, Him = h1b - h2t;
+        const float HreB = k1t + k2b, HimB = k1b - k2t;
         const int m = P.em[a], am = m < 0 ? -m : m;
         if (am != prev) {
           sincosf((float)am * phi, &smf, &cmf);
@@ -809,6 +846,10 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         const float yre = amp * cmf, yim = sgn * amp * smf;
         g_phase = fmaf((float)m, fmaf(-yim, Hre, yre * Him), g_phase);
         g_incl = fmaf(damp * cmf, Hre, fmaf(sgn * damp * smf, Him, g_incl));
+        if (TWO) {
+          gB_phase = fmaf((float)m, fmaf(-yim, HreB, yre * HimB), gB_phase);
+          gB_incl = fmaf(damp * cmf, HreB, fmaf(sgn * damp * smf, HimB, gB_incl));
+        }
       }
     }
   }
@@ -828,6 +869,15 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     o.grad[6] = (double)t.hi + (double)t.lo;
     if (bad)
       for (int p = 0; p < kNpar; ++p) o.grad[p] = CUDART_NAN;
+    if (TWO) {
+      o.gradB[0] = gB_ra;
+      o.gradB[1] = gB_dec;
+      o.gradB[2] = gB_psi;
+      o.gradB[3] = gB_incl;
+      o.gradB[4] = gB_phase;
+      o.gradB[5] = 0.0;
+      o.gradB[6] = 0.0;
+    }
   }
   return o;
 }
@@ -884,17 +934,16 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
     MixedDraw o;
     if (DIST && GRAD) {
-      // distance-marginal gradient: E[x] dK - E[x^2] dR / 2 equals (a / xbar)
-      // times the gradient at x = xbar = E[x^2]/E[x] (a = E[x]; the lnD slot is 0)
-      MixedDraw k1 = lnl_mixed_draw<MM, RR, false, true, true>(P, sA, sg, a12s, xfs, dp, i);
-      float ex[2] = {1.f, 1.f};
-      const df marg = isnan(k1.lnl.hi) ? k1.lnl : dist_marg_df(dist, k1.lnl, k1.R, ex);
-      const float xbar = ex[1] / ex[0], sc = ex[0] / xbar;
-      o = lnl_mixed_draw<MM, RR, true, true, true>(P, sA, sg, a12s, xfs, dp, i, df{xbar, 0.f});
-      for (int p = 0; p < kNpar; ++p) o.grad[p] *= sc;
+      // distance-marginal gradient in one pass at x = 1: with lnL(x) = K x -
+      // R x^2/2, the pass gives gA = dK - dR/2 (the adjoint at x = 1) and
+      // gB = dR/2, and E[x] dK - E[x^2] dR/2 = E[x] gA + E[x(1 - x)] gB
+      // (the lnD slot is 0)
+      o = lnl_mixed_draw<MM, RR, true, true, true>(P, sA, sg, a12s, xfs, dp, i);
+      float ex[3] = {1.f, 1.f, 0.f};
+      const df marg = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R, ex);
+      for (int p = 0; p < kNpar; ++p) o.grad[p] = ex[0] * o.grad[p] + ex[2] * o.gradB[p];
       o.grad[5] = 0.0;
       o.lnl = marg;
-      o.oob = k1.oob;
     } else {
       o = lnl_mixed_draw<MM, RR, GRAD, DIST, true>(P, sA, sg, a12s, xfs, dp, i);
       if (DIST) o.lnl = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R);
