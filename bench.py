@@ -15,7 +15,7 @@ path, the ALU roofline of the kernel, sampled clocks and the FP64 CPU oracle
 as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ile|batch|event|diff|sweep]
+                  [--workload ile|batch|event|diff|sweep|sampler]
 
 The default workload (ile) is the headline line.  The others are extra
 measurements:
@@ -27,7 +27,9 @@ measurements:
          forward+backward and lnZ, FP32-mixed against FP64;
   diff   forward+backward at SNR 1000 (2^20 draws) with the per-component
          gradient error against the FP64 path;
-  sweep  the FP32-mixed error against the FP64 path at SNR 20 ... 1000.
+  sweep  the FP32-mixed error against the FP64 path at SNR 20 ... 1000;
+  sampler  forward+backward latency on batches of 128 ... 65536 draws, eager
+         and replayed from a captured CUDA graph.
 """
 from __future__ import annotations
 
@@ -475,6 +477,43 @@ def run_diff(args):
         "clocks": clocks.summary()}), flush=True)
 
 
+def run_sampler(args):
+    """The sampler regime (a NEXT row): one forward+backward call on a small
+    batch of draws, as a gradient-based extrinsic sampler issues them; per-call
+    latency eager and replayed from a captured CUDA graph."""
+    import torch
+    import paper_2609_37393_b300 as R
+    import workload as W
+    torch.cuda.set_device(0)
+    point, exact, info, draws, logw = W.config2(n_draws=1 << 16)
+    pt = R.Point(point)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in (128, 1024, 8192, 65536):
+        d = R.Draws({p: draws[p][:n] for p in W.PARAMS})
+        lnl = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty((7, n), dtype=torch.float64, device="cuda")
+        call = lambda: R.rift_ile_lnL_grad(pt, d, R.FP32_MIXED, lnl, g)
+        eager_us = timed_events(torch, call, 200, stream) * 1e3
+        row = {"draws": n, "eager_us_per_call": eager_us}
+        try:
+            s2 = torch.cuda.Stream()
+            s2.wait_stream(stream)
+            with torch.cuda.stream(s2):
+                call()
+            stream.wait_stream(s2)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                call()
+            row["graph_us_per_call"] = timed_events(torch, graph.replay, 200, stream) * 1e3
+        except Exception as e:  # capture refused: report it
+            row["graph"] = f"unavailable: {e}"
+        row["draws_per_s"] = n / (min(row.get("graph_us_per_call", eager_us), eager_us) * 1e-6)
+        rows.append(row)
+    print(json.dumps({"workload": "sampler", "metric": "fwd+bwd latency per small batch (SNR 1000)",
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,7 +521,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ile", choices=["ile", "batch", "event", "diff", "sweep"])
+    ap.add_argument("--workload", default="ile", choices=["ile", "batch", "event", "diff", "sweep", "sampler"])
     ap.add_argument("--points", type=int, default=512)
     ap.add_argument("--chunks", type=int, default=16)
     args = ap.parse_args()
@@ -503,6 +542,9 @@ def main():
         return
     if args.workload == "sweep":
         run_sweep(args)
+        return
+    if args.workload == "sampler":
+        run_sampler(args)
         return
 
     import torch

@@ -72,6 +72,13 @@ int grid_for(KernelT kernel, int threads, size_t smem) {
   return device_sms() * nb;
 }
 
+// A grid-stride launch needs no more blocks than there are draws to cover
+// (small batches: fewer idle blocks and fewer partials to merge).
+inline int grid_cap(int blocks, long long n, int threads) {
+  const long long need = (n + threads - 1) / threads;
+  return (int)(need < blocks ? (need > 0 ? need : 1) : blocks);
+}
+
 // The same launches with the SM count given by the caller, for code that must
 // not touch the library's workspace (grid = sms x resident blocks per SM, at
 // most kMaxPartialsPerSM per SM).

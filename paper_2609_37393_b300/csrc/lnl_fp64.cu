@@ -207,7 +207,7 @@ cudaError_t launch_fp64_dist_k(const PointParams& hp, const PointParams* dP, con
   const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
   auto kern = lnl_fp64_kernel<MM, LSE, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  *blocks = grid_for(kern, 256, smem);
+  *blocks = grid_cap(grid_for(kern, 256, smem), dp.n, 256);
   kern<<<*blocks, 256, smem, st>>>(dP, dp, lnl_out, partials, oob, dist);
   return cudaGetLastError();
 }
@@ -226,7 +226,7 @@ cudaError_t launch_fp64_k(const PointParams& hp, const PointParams* dP, const Dr
                           int* blocks, cudaStream_t st) {
   const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
   cudaFuncSetAttribute(lnl_fp64_kernel<MM, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  *blocks = grid_for(lnl_fp64_kernel<MM, LSE>, 256, smem);
+  *blocks = grid_cap(grid_for(lnl_fp64_kernel<MM, LSE>, 256, smem), dp.n, 256);
   lnl_fp64_kernel<MM, LSE><<<*blocks, 256, smem, st>>>(dP, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }
@@ -486,7 +486,7 @@ cudaError_t launch_grad_fp64_mm(const PointParams& hp, const PointParams* dP, co
                                 double* lnl_out, double* grad_out, cudaStream_t st) {
   const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
   cudaFuncSetAttribute(grad_fp64_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  const int blocks = grid_for(grad_fp64_kernel<MM>, 256, smem);
+  const int blocks = grid_cap(grid_for(grad_fp64_kernel<MM>, 256, smem), dp.n, 256);
   grad_fp64_kernel<MM><<<blocks, 256, smem, st>>>(dP, dp, lnl_out, grad_out);
   return cudaGetLastError();
 }
@@ -498,7 +498,7 @@ cudaError_t launch_grad_fp64_dist_mm(const PointParams& hp, const PointParams* d
   const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
   auto kern = grad_fp64_kernel<MM, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  const int blocks = grid_for(kern, 256, smem);
+  const int blocks = grid_cap(grid_for(kern, 256, smem), dp.n, 256);
   kern<<<blocks, 256, smem, st>>>(dP, dp, lnl_out, grad_out, dist);
   return cudaGetLastError();
 }
@@ -568,7 +568,7 @@ cudaError_t launch_fp64_k_sms(const PointParams& hp, const PointParams* dP, cons
                               int sms, int* blocks, cudaStream_t st) {
   const size_t smem = (size_t)2 * hp.K * hp.M * hp.M * sizeof(double2);
   cudaFuncSetAttribute(lnl_fp64_kernel<MM, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  *blocks = grid_for_sms(lnl_fp64_kernel<MM, LSE>, 256, smem, sms);
+  *blocks = grid_cap(grid_for_sms(lnl_fp64_kernel<MM, LSE>, 256, smem, sms), dp.n, 256);
   lnl_fp64_kernel<MM, LSE><<<*blocks, 256, smem, st>>>(dP, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }

@@ -976,7 +976,7 @@ cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const D
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
-  *blocks = grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem);
+  *blocks = grid_cap(grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem), dp.n, 128);
   lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }
@@ -989,7 +989,7 @@ cudaError_t launch_mixed_dist_k(const PointParams& hp, const PointParams* dP, co
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   auto kern = lnl_mixed_kernel<MM, RR, LSE, false, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  *blocks = grid_for(kern, 128, smem);
+  *blocks = grid_cap(grid_for(kern, 128, smem), dp.n, 128);
   kern<<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob, nullptr, dist);
   return cudaGetLastError();
 }
@@ -1029,7 +1029,7 @@ cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, c
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, false, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  const int blocks = grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem);
+  const int blocks = grid_cap(grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem), dp.n, 128);
   lnl_mixed_kernel<MM, RR, false, true><<<blocks, 128, smem, st>>>(hp, dp, lnl_out, nullptr, nullptr,
                                                                    grad_out);
   return cudaGetLastError();
@@ -1050,7 +1050,7 @@ cudaError_t launch_mixed_grad_dist_mr(const PointParams& hp, const PointParams* 
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   auto kern = lnl_mixed_kernel<MM, RR, false, true, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  const int blocks = grid_for(kern, 128, smem);
+  const int blocks = grid_cap(grid_for(kern, 128, smem), dp.n, 128);
   kern<<<blocks, 128, smem, st>>>(hp, dp, lnl_out, nullptr, nullptr, grad_out, dist);
   return cudaGetLastError();
 }
@@ -1071,7 +1071,7 @@ cudaError_t launch_mixed_k_sms(const PointParams& hp, const PointParams* dP, con
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
   cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
-  *blocks = grid_for_sms(lnl_mixed_kernel<MM, RR, LSE>, 128, smem, sms);
+  *blocks = grid_cap(grid_for_sms(lnl_mixed_kernel<MM, RR, LSE>, 128, smem, sms), dp.n, 128);
   lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }
