@@ -674,17 +674,17 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         wtd[2] = -(f * fd + fa * fd + fa * f) * 0.5f;
         wtd[3] = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
       }
-      // taps j-1 .. j+2: row index (clamped) and whether it is in the table
-      const float2* Ek = P.ehat + (size_t)k * n * R;
-      bool vld[4];
-      int rowi[4];
+      // taps j-1 .. j+2 read the zero-padded table with j clamped to
+      // [-3, n + 1]: every tap outside the table lands on a zero row, so
+      // the loads need no test (taps outside are only counted)
+      const float2* Ek = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * R;
 #pragma unroll
       for (int tap = 0; tap < 4; ++tap) {
         const float jj = jf - 1.f + (float)tap;
-        vld[tap] = (jj >= 0.f && jj < (float)n);
-        if (!vld[tap]) ++oob;
-        rowi[tap] = vld[tap] ? (int)jj : 0;
+        if (!(jj >= 0.f && jj < (float)n)) ++oob;
       }
+      const int jc = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
+      const float2* Ej = Ek + (ptrdiff_t)(jc - 1) * R;
       // Per pair of directions: the template w_r = xFr a1_r + xFi a2_r (heads
       // of xF on the grid of its larger part; head x head products of 10 x 10
       // bits and their sum exact, the cross terms >= 2^8 smaller; w kept as
@@ -714,9 +714,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 #pragma unroll
           for (int tap = 0; tap < 4; ++tap) {
             // rows hold R pairs, R even: two entries per 16-byte load
-            const float4 e2 =
-                vld[tap] ? __ldg(reinterpret_cast<const float4*>(Ek + (size_t)rowi[tap] * R + r))
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 e2 = __ldg(reinterpret_cast<const float4*>(Ej + tap * R + r));
             const float d0 = __fadd_rn(__fsub_rn(e2.x, wv[0].hi), e2.y);
             const float d1 = __fadd_rn(__fsub_rn(e2.z, wv[1].hi), e2.w);
             rs0 = fmaf(wt[tap], d0, rs0);

@@ -199,16 +199,20 @@ __device__ __forceinline__ float2 split2(double x) {
   return make_float2(hi, __double2float_rn(x - (double)hi));
 }
 
-// ehat[k][j][r] = proj[k][j][perm[k][r]] * inv_s[k][r] as a (hi, lo) pair.
+// ehat[k][kEhatPad + j][r] = proj[k][j][r] * inv_s[k][r] as a (hi, lo) pair.
 __global__ void whiten_kernel(const double* __restrict__ proj, const double* __restrict__ inv_s,
                               int K, int n, int D, int R, float2* __restrict__ ehat) {
+  // rows are stored with kEhatPad zero rows before and after (already zeroed)
   long long total = (long long)K * n * R;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     int r = (int)(idx % R);
     long long kj = idx / R;
     int k = (int)(kj / n);
-    ehat[idx] = split2(proj[kj * D + r] * inv_s[k * R + r]);
+    int j = (int)(kj % n);
+    // directions r >= D exist only as zero padding (inv_s = 0 there)
+    const double v = r < D ? proj[kj * D + r] * inv_s[k * R + r] : 0.0;
+    ehat[((long long)k * (n + 2 * kEhatPad) + kEhatPad + j) * R + r] = split2(v);
   }
 }
 
@@ -239,7 +243,7 @@ __global__ void halfnorm_poly_kernel(const double* __restrict__ proj,
         int jb = j - 1 + b;
         if (jb < 0 || jb >= n) continue;
         double acc = 0.0;
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < R && r < D; ++r) {  // directions r >= D are zero padding
           double ea = proj[((long long)k * n + ja) * D + r] * inv_s[k * R + r];
           double eb = proj[((long long)k * n + jb) * D + r] * inv_s[k * R + r];
           acc = fma(ea, eb, acc);
@@ -623,7 +627,10 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
         inv_s[(size_t)k * R + r] = 1.0 / sc[(size_t)P.cls_of[k] * D + r];
     if ((rc = dev_alloc(&pt->A, A.size()))) break;
     if ((rc = dev_alloc(&pt->gm1, gm1.size()))) break;
-    if ((rc = dev_alloc(&pt->ehat, (size_t)K * n * R))) break;
+    if ((rc = dev_alloc(&pt->ehat, (size_t)K * (n + 2 * kEhatPad) * R))) break;
+    if ((rc = check_cuda(cudaMemsetAsync(pt->ehat, 0, (size_t)K * (n + 2 * kEhatPad) * R * sizeof(float2),
+                                         stream), "table padding")))
+      break;
     if ((rc = dev_alloc(&pt->epoly, (size_t)K * (n + 3) * (kPolyDeg + 1)))) break;
     if ((rc = dev_alloc(&dinv_s, inv_s.size()))) break;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->A, A.data(), A.size() * sizeof(float2),

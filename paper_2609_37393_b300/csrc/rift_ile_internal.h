@@ -23,6 +23,9 @@ constexpr float kAnchorInvStep = 128.0f;
 // Anchors of the double-float exponential: e^(j/128), |j| <= kExpHalf.
 constexpr int kExpHalf = 46;
 constexpr int kPolyDeg = 6;  // 1/2 |e(f)|^2 on one table interval is a sextic in f
+// Zero rows stored before and after each detector's whitened table, so that
+// any tap window whose first tap lies in [-kEhatPad, n] reads rows in memory.
+constexpr int kEhatPad = 4;
 
 // Everything a kernel needs about one intrinsic point.  Lives in device
 // memory (one record per point) and is staged into shared memory by each
@@ -73,7 +76,7 @@ struct PointParams {
   // FP32-mixed path tables (whitened real form, see point.cu), (hi, lo) pairs
   const float2* A;      // [ncls][R][D]  w = A z
   const float* gm1;     // [ncls][R]     1 - lam_r/s_r^2 (0 except kept null directions)
-  const float2* ehat;   // [K][n][R]     whitened Q table
+  const float2* ehat;   // [K][n + 2 kEhatPad][R] whitened Q table, zero rows around it
   const float2* epoly;  // [K][n+3][7]   1/2|e(f)|^2 on interval j (index j+2), coefficients of f^0..f^6
 };
 

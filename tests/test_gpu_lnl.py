@@ -208,3 +208,31 @@ def test_invalid_arguments_are_rejected(R, cfg0):
     pt = R.Point(point)
     with pytest.raises(R.RiftError):
         R.rift_ile_lnZ(pt, cfg0[3], 7)
+
+
+@pytest.mark.parametrize("n_modes", [1, 3, 5])
+def test_odd_mode_counts(R, n_modes):
+    """Odd mode counts run the kernels compiled for the next even count with
+    the whitened width padded past 2M; parity with the oracle holds."""
+    rng = np.random.default_rng(W.seed_for(5, n_modes))
+    truth = W.default_truth(rng, W.D_REF)
+    point, exact, info = W.make_point(
+        dets=W.random_l_detectors(rng, 3), modes=W.MODES10[:n_modes], f_low=5.0, f_max=2048.0,
+        df=0.25, rate=32768.0, half_window=0.03, snr=300.0, truth=truth,
+        gmst=float(rng.uniform(0, 2 * math.pi)), d_ref=W.D_REF, rng=rng, noise=False,
+        q_dtype=np.complex64)
+    sig = W.proposal_sigma(info, exact)
+    draws, logw = W.mixture_draws(rng, W.Prior(0.5 * W.D_REF, 2.0 * W.D_REF, 0.01), truth, sig,
+                                  20000)
+    draws = W.as_float(draws, np.float32)
+    pt = R.Point(point)
+    assert pt.info()["M"] == n_modes
+    ref = O.lnL(O.OraclePoint(point), draws)
+    got64 = R.rift_ile_lnL(pt, draws, R.FP64).cpu().numpy()
+    assert np.all(np.abs(got64 - ref) <= fp64_tol(ref))
+    got32 = R.rift_ile_lnL(pt, draws, R.FP32_MIXED).cpu().numpy()
+    near = ref >= ref.max() - 50
+    assert np.max(np.abs(got32 - ref)[near]) <= 1e-3
+    rz = O.lnZ(ref, np.asarray(logw, dtype=np.float64))
+    z = R.rift_ile_lnZ(pt, R.Draws(draws, logw.astype(np.float32)), R.FP32_MIXED)
+    assert abs(z[0] - rz[0]) <= 1e-4
