@@ -97,7 +97,15 @@ __device__ __forceinline__ float4* xf_slice(float4* smem4, int ncls, int R, int 
 // sin and cos of a double-float angle to ~1e-15 absolute: reduce by 2 pi (pair
 // constant), take the nearest anchor a_j = j 2^-7, and add the residual
 // d (|d| <= 2^-8) through sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24.
-RIFT_HELPER void sincos_df(df a, df& s_out, df& c_out) {
+#ifndef RIFT_MIXED_SINCOS_CALL  // 1: the anchored sine/cosine is a real call (less code)
+#define RIFT_MIXED_SINCOS_CALL 0
+#endif
+#if RIFT_MIXED_SINCOS_CALL
+__device__ __noinline__
+#else
+RIFT_HELPER
+#endif
+void sincos_df(df a, df& s_out, df& c_out) {
   const float kTwoPiHi = 6.28318548202514648f;
   const float kTwoPiLo = -1.7484555314695172e-07f;
   float k = rintf(a.hi * 0.159154943091895336f);
@@ -154,20 +162,56 @@ __device__ __forceinline__ df df_pow(df b, int n) {
   return r;
 }
 
-// The real amplitude of -2Y_lm(iota, 0) of mode i in double-float from
-// z = cos(iota) and sz = sin(iota): sz^ypar sum_j yz[j] z^j by Horner, each
+// Per-detector and per-mode values the draw loop reads, copied from the
+// point parameters into shared memory once per block (and once per point in
+// the batch kernel): whole 16-byte vectors indexed by the loop variables
+// instead of scalar constant-bank loads with register-indexed addresses.
+struct MixedTables {
+  float4 ah[kMaxDet][3];  // acoef_h[0..9] (head of the antenna coefficients)
+  float4 at[kMaxDet][3];  // acoef_t[0..9] (their tails)
+  float4 pos_hi[kMaxDet];  // (pos_hi[0..2], t0_hi)
+  float4 pos_lo[kMaxDet];  // (pos_lo[0..2], t0_lo)
+  int4 mode[kMaxModes];    // visiting order j: (mode index, m, l, ypar)
+  float2 yz[kMaxModes][kMaxEll + 1];  // visiting order j: (hi, lo) of yz
+};
+
+__device__ __forceinline__ void stage_tables(const PointParams& P, MixedTables& T) {
+  for (int t = threadIdx.x; t < P.K; t += blockDim.x) {
+    float h[12] = {}, tl[12] = {};
+    for (int c = 0; c < 10; ++c) {
+      h[c] = P.acoef_h[t][c];
+      tl[c] = P.acoef_t[t][c];
+    }
+    for (int v = 0; v < 3; ++v) {
+      T.ah[t][v] = make_float4(h[4 * v], h[4 * v + 1], h[4 * v + 2], h[4 * v + 3]);
+      T.at[t][v] = make_float4(tl[4 * v], tl[4 * v + 1], tl[4 * v + 2], tl[4 * v + 3]);
+    }
+    T.pos_hi[t] = make_float4(P.pos_hi[t][0], P.pos_hi[t][1], P.pos_hi[t][2], P.t0_hi[t]);
+    T.pos_lo[t] = make_float4(P.pos_lo[t][0], P.pos_lo[t][1], P.pos_lo[t][2], P.t0_lo[t]);
+  }
+  for (int j = threadIdx.x; j < P.M; j += blockDim.x) {
+    const int a = P.morder[j];
+    T.mode[j] = make_int4(a, P.em[a], P.ell[a], P.ypar[a]);
+    for (int q = 0; q <= P.ell[a]; ++q) T.yz[j][q] = make_float2(P.yz_hi[a][q], P.yz_lo[a][q]);
+  }
+}
+
+// The real amplitude of -2Y_lm(iota, 0) of the mode visited j-th (degree l,
+// parity par) in double-float from z = cos(iota) and sz = sin(iota):
+// sz^par sum_q yz[q] z^q by Horner, each
 // step an exact product of the high parts and an exact sum with the
 // coefficient's high part.
-RIFT_HELPER df sylm_amp_df(const PointParams& P, int i, df z, df sz) {
-  const int l = P.ell[i];
-  df acc = df{P.yz_hi[i][l], P.yz_lo[i][l]};
-  for (int j = l - 1; j >= 0; --j) {
+RIFT_HELPER df sylm_amp_df(const MixedTables& T, int j, int l, int par, df z, df sz) {
+  float2 c = T.yz[j][l];
+  df acc = df{c.x, c.y};
+  for (int q = l - 1; q >= 0; --q) {
+    c = T.yz[j][q];
     df pr = two_prod(acc.hi, z.hi);
     pr.lo = fmaf(acc.hi, z.lo, fmaf(acc.lo, z.hi, pr.lo));
-    const df sm = two_sum(pr.hi, P.yz_hi[i][j]);
-    acc = fast_two_sum(sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), P.yz_lo[i][j]));
+    const df sm = two_sum(pr.hi, c.x);
+    acc = fast_two_sum(sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), c.y));
   }
-  return P.ypar[i] ? df_mul(acc, sz) : acc;
+  return par ? df_mul(acc, sz) : acc;
 }
 
 // Complex product of pairs.
@@ -252,21 +296,28 @@ __device__ __forceinline__ void split_antenna_basis(const AntennaBasis& B, Anten
 // a tail (point.cu); head x head products are exact and their sum of at most
 // six stays below 2^22 quanta, so it is exact in FP32; the cross terms are
 // >= 2^9 smaller and summed in FP32.
-RIFT_HELPER void antenna_df(const PointParams& P, int k, const AntennaSplit& S, df xer, df xei,
+RIFT_HELPER void antenna_df(const MixedTables& T, int k, const AntennaSplit& S, df xer, df xei,
                             df& xFr, df& xFi) {
-  float fp = S.bh[0] * P.acoef_h[k][0], fpc = 0.f;
+  float h[12], t[12];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const float4 a = T.ah[k][v], b = T.at[k][v];
+    h[4 * v] = a.x; h[4 * v + 1] = a.y; h[4 * v + 2] = a.z; h[4 * v + 3] = a.w;
+    t[4 * v] = b.x; t[4 * v + 1] = b.y; t[4 * v + 2] = b.z; t[4 * v + 3] = b.w;
+  }
+  float fp = S.bh[0] * h[0], fpc = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    if (i) fp = fmaf(P.acoef_h[k][i], S.bh[i], fp);
-    fpc = fmaf(P.acoef_h[k][i], S.bt[i], fpc);
-    fpc = fmaf(P.acoef_t[k][i], __fadd_rn(S.bh[i], S.bt[i]), fpc);
+    if (i) fp = fmaf(h[i], S.bh[i], fp);
+    fpc = fmaf(h[i], S.bt[i], fpc);
+    fpc = fmaf(t[i], __fadd_rn(S.bh[i], S.bt[i]), fpc);
   }
-  float fx = S.gh[0] * P.acoef_h[k][6], fxc = 0.f;
+  float fx = S.gh[0] * h[6], fxc = 0.f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (i) fx = fmaf(P.acoef_h[k][6 + i], S.gh[i], fx);
-    fxc = fmaf(P.acoef_h[k][6 + i], S.gt[i], fxc);
-    fxc = fmaf(P.acoef_t[k][6 + i], __fadd_rn(S.gh[i], S.gt[i]), fxc);
+    if (i) fx = fmaf(h[6 + i], S.gh[i], fx);
+    fxc = fmaf(h[6 + i], S.gt[i], fxc);
+    fxc = fmaf(t[6 + i], __fadd_rn(S.gh[i], S.gt[i]), fxc);
   }
   // (fp - i fx)(xer + i xei) with the pairs (fp, fpc), (fx, fxc) unnormalised
   {
@@ -294,15 +345,14 @@ RIFT_HELPER void antenna_df(const PointParams& P, int k, const AntennaSplit& S, 
 // FP32 amplitude of mode i and its derivative with respect to iota (used by
 // the adjoint, whose terms multiply the small residual and need only FP32):
 // amp = sz^par p(z), d amp/d iota = par z p(z) - sz^(par+1) p'(z) (dz = -sz d iota).
-__device__ __forceinline__ void sylm_amp_grad_f(const PointParams& P, int i, float z, float sz,
-                                                float& amp, float& damp) {
-  const int l = P.ell[i];
-  float pz = P.yz_hi[i][l], dp = 0.f;
-  for (int j = l - 1; j >= 0; --j) {
+__device__ __forceinline__ void sylm_amp_grad_f(const MixedTables& T, int j, int l, int par,
+                                                float z, float sz, float& amp, float& damp) {
+  float pz = T.yz[j][l].x, dp = 0.f;
+  for (int q = l - 1; q >= 0; --q) {
     dp = fmaf(dp, z, pz);
-    pz = fmaf(pz, z, P.yz_hi[i][j]);
+    pz = fmaf(pz, z, T.yz[j][q].x);
   }
-  if (P.ypar[i]) {
+  if (par) {
     amp = sz * pz;
     damp = fmaf(z, pz, -sz * sz * dp);
   } else {
@@ -442,7 +492,8 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
 // With DIST the template is taken at the distance factor xin (1 for the
 // marginal's K and R) instead of D_ref e^{-lnD}.
 template <int MM, int RR, bool GRAD, bool DIST = false, bool EXACT = false>
-__device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const float4* sA,
+__device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const MixedTables& TB,
+                                                    const float4* sA,
                                                     const float* sg, float4* a12s, float4* xfs,
                                                     const DrawsParams& dp, long long i,
                                                     df xin = df{1.f, 0.f}) {
@@ -480,7 +531,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
   // product below), so the sky functions need not stay in registers
   for (int k = 0; k < P.K; ++k) {
     df xFr, xFi;
-    antenna_df(P, k, AS, xer, xei, xFr, xFi);
+    antenna_df(TB, k, AS, xer, xei, xFr, xFi);
     const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
     const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
     xfs[k * kMixedThreads] = make_float4(xrh, __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo), xih,
@@ -525,8 +576,8 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     df cm = df{1.f, 0.f}, sm = df{0.f, 0.f}, c1 = df{1.f, 0.f}, s1p = df{0.f, 0.f};
     bool have1 = false;
     for (int j = 0; j < M; ++j) {
-      const int a = P.morder[j];
-      const int m = P.em[a], am = m < 0 ? -m : m;
+      const int4 md = TB.mode[j];  // (mode index, m, l, ypar)
+      const int m = md.y, am = m < 0 ? -m : m;
       if (am != prev_am) {
         if (have1 && am == prev_am + 1) {
           const df cn = df_sub(df_mul(cm, c1), df_mul(sm, s1p));
@@ -542,7 +593,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         }
         prev_am = am;
       }
-      const df amp = sylm_amp_df(P, a, z, sz);
+      const df amp = sylm_amp_df(TB, j, md.z, md.w, z, sz);
       const df yr = df_mul(amp, cm);
       const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
       // y = y1 + y2 with y1 the 9-bit head and y2 = (y.hi - y1) + y.lo
@@ -614,12 +665,13 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const float xrh = xfq.x, xrt = xfq.y, xih = xfq.z, xit = xfq.w;
       const df xFr = df{__fadd_rn(xrh, xrt), 0.f}, xFi = df{__fadd_rn(xih, xit), 0.f};  // FP32 uses
       // arrival time (shared by co-located detectors) and table position
+      const float4 ph = TB.pos_hi[k], pl = TB.pos_lo[k];  // (position, t0) pairs
       if (!P.same_pos_prev[q]) {
-        delay = df_mul(df{P.pos_hi[k][0], P.pos_lo[k][0]}, s0);
-        delay = df_add(delay, df_mul(df{P.pos_hi[k][1], P.pos_lo[k][1]}, s1));
-        delay = df_add(delay, df_mul(df{P.pos_hi[k][2], P.pos_lo[k][2]}, s2));
+        delay = df_mul(df{ph.x, pl.x}, s0);
+        delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
+        delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
       }
-      const df rel = df_add(df_sub(tc, delay), df{-P.t0_hi[k], -P.t0_lo[k]});
+      const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
       const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
       if (!isfinite(u.hi)) {
         bad = true;
@@ -773,22 +825,31 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       if (GRAD) {
         // time: d lnL_k / d t_k = (P'(f) - r . edot dt) / dt
         const df dtk = df_mul(df_add_f(dhalf, -red), df{P.inv_dt_hi, P.inv_dt_lo});
-        const float dka = -(P.pos_hi[k][0] * dsa[0] + P.pos_hi[k][1] * dsa[1]);
-        const float dkd = -(P.pos_hi[k][0] * dsd[0] + P.pos_hi[k][1] * dsd[1] + P.pos_hi[k][2] * dsd[2]);
+        const float dka = -(ph.x * dsa[0] + ph.y * dsa[1]);
+        const float dkd = -(ph.x * dsd[0] + ph.y * dsd[1] + ph.z * dsd[2]);
         dacc_add(gt_t, dtk);
         dacc_add(gt_ra, df_mul_f(dtk, dka));
         dacc_add(gt_dec, df_mul_f(dtk, dkd));
         // antenna: d(xF) = x e^{2 i psi} (dF+ - i dFx), d/d psi (xF) = 2 i xF
         float dfpa = 0.f, dfpd = 0.f, dfxa = 0.f, dfxd = 0.f;
+        float ac[12];  // the antenna coefficients in FP32 (head + tail)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const float4 a4 = TB.ah[k][v], b4 = TB.at[k][v];
+          ac[4 * v] = a4.x + b4.x;
+          ac[4 * v + 1] = a4.y + b4.y;
+          ac[4 * v + 2] = a4.z + b4.z;
+          ac[4 * v + 3] = a4.w + b4.w;
+        }
 #pragma unroll
         for (int u = 0; u < 6; ++u) {
-          dfpa = fmaf(P.acoef_hi[k][u], ABG.ba[u], dfpa);
-          dfpd = fmaf(P.acoef_hi[k][u], ABG.bd[u], dfpd);
+          dfpa = fmaf(ac[u], ABG.ba[u], dfpa);
+          dfpd = fmaf(ac[u], ABG.bd[u], dfpd);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          dfxa = fmaf(P.acoef_hi[k][6 + u], ABG.ga[u], dfxa);
-          dfxd = fmaf(P.acoef_hi[k][6 + u], ABG.gd[u], dfxd);
+          dfxa = fmaf(ac[6 + u], ABG.ga[u], dfxa);
+          dfxd = fmaf(ac[6 + u], ABG.gd[u], dfxd);
         }
         // (dfp - i dfx)(xer + i xei)
         const float dxra = dfpa * xer.hi + dfxa * xei.hi, dxia = dfpa * xei.hi - dfxa * xer.hi;
@@ -811,7 +872,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       float cmf = 1.f, smf = 0.f;
       int prev = -1;
       for (int j = 0; j < M; ++j) {
-        const int a = P.morder[j];
+        const int4 md = TB.mode[j];  // (mode index, m, l, ypar)
         float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
         float k1t = 0.f, k1b = 0.f, k2t = 0.f, k2b = 0.f;
 #pragma unroll
@@ -833,14 +894,14 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         }
         const float Hre = h1t + h2b, Him = h1b - h2t;
         const float HreB = k1t + k2b, HimB = k1b - k2t;
-        const int m = P.em[a], am = m < 0 ? -m : m;
+        const int m = md.y, am = m < 0 ? -m : m;
         if (am != prev) {
           sincosf((float)am * phi, &smf, &cmf);
           prev = am;
         }
         const float sgn = m < 0 ? -1.f : 1.f;
         float amp, damp;
-        sylm_amp_grad_f(P, a, ci, si, amp, damp);
+        sylm_amp_grad_f(TB, j, md.z, md.w, ci, si, amp, damp);
         const float yre = amp * cmf, yim = sgn * amp * smf;
         g_phase = fmaf((float)m, fmaf(-yim, Hre, yre * Him), g_phase);
         g_incl = fmaf(damp * cmf, Hre, fmaf(sgn * damp * smf, Him, g_incl));
@@ -920,7 +981,9 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   // warp-uniform addresses; 7.4 KB, within the 32 KB parameter limit), so
   // they need neither shared memory nor staging.
   extern __shared__ float4 smem4[];
+  __shared__ MixedTables T;
   stage_split_A(P, smem4);
+  stage_tables(P, T);
   __syncthreads();
   const float4* sA = smem4;
   const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M);
@@ -936,14 +999,14 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
       // R x^2/2, the pass gives gA = dK - dR/2 (the adjoint at x = 1) and
       // gB = dR/2, and E[x] dK - E[x^2] dR/2 = E[x] gA + E[x(1 - x)] gB
       // (the lnD slot is 0)
-      o = lnl_mixed_draw<MM, RR, true, true, true>(P, sA, sg, a12s, xfs, dp, i);
+      o = lnl_mixed_draw<MM, RR, true, true, true>(P, T, sA, sg, a12s, xfs, dp, i);
       float ex[3] = {1.f, 1.f, 0.f};
       const df marg = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R, ex);
       for (int p = 0; p < kNpar; ++p) o.grad[p] = ex[0] * o.grad[p] + ex[2] * o.gradB[p];
       o.grad[5] = 0.0;
       o.lnl = marg;
     } else {
-      o = lnl_mixed_draw<MM, RR, GRAD, DIST, true>(P, sA, sg, a12s, xfs, dp, i);
+      o = lnl_mixed_draw<MM, RR, GRAD, DIST, true>(P, T, sA, sg, a12s, xfs, dp, i);
       if (DIST) o.lnl = isnan(o.lnl.hi) ? o.lnl : dist_marg_df(dist, o.lnl, o.R);
     }
     oob += o.oob;
@@ -1097,6 +1160,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
                      const BatchItem* __restrict__ items, int n_items, unsigned int* __restrict__ head,
                      LseState* __restrict__ partials, unsigned long long* __restrict__ oob_count) {
   __shared__ PointParams P;
+  __shared__ MixedTables T;
   __shared__ DrawsParams sdp;
   __shared__ int s_item;
   extern __shared__ float4 smem4[];
@@ -1113,6 +1177,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
       if (threadIdx.x == 0) sdp = dps[it.point];
       __syncthreads();
       stage_split_A(P, smem4);
+      stage_tables(P, T);
       __syncthreads();
       cur = it.point;
     }
@@ -1123,7 +1188,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
     ThreadLse st = tlse_init();
     const long long end = it.begin + it.count;
     for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
-      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, sA, sg, a12s, xfs, sdp, i);
+      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, T, sA, sg, a12s, xfs, sdp, i);
       oob += o.oob;
       float lw = 0.f;
       if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
