@@ -1,6 +1,7 @@
 """Benchmark of the extrinsic-likelihood hot path on B300.
 
-Workload (one step): the FP32-mixed fused lnL -> lnZ pass (rift_ile_lnZ_state)
+Workload (one step): the FP32-mixed fused lnL -> lnZ pass (rift_ile_lnZ_state_async:
+the fused kernel and the merge of its partials, state left on the device)
 over one batch of 2^22 float32 extrinsic draws of the 3G precision
 workload: an ET-like triangle plus a CE-like 40 km L (K = 4), ten modes
 (2,+-1),(2,+-2),(3,+-2),(3,+-3),(4,+-4), zero-noise injection at network SNR
@@ -571,8 +572,13 @@ def main():
     # ALU peak of this GPU (roofline denominator), measured before the timing
     fp32_ops, probe_mhz = R.rift_ile_probe_alu(0, 0.2)
 
+    # one step: the fused lnL -> LSE kernel and the merge of its partials,
+    # the LSE state left on the device (steps are chained on the stream; the
+    # host reads the last state once)
+    state_dev = torch.empty(4, dtype=torch.float64, device="cuda")
+
     def step():
-        return R.rift_ile_lnZ_state(pt, d_dev, R.FP32_MIXED)
+        R.rift_ile_lnZ_state_async(pt, d_dev, R.FP32_MIXED, out=state_dev)
 
     for _ in range(args.warmup):
         step()
@@ -583,10 +589,11 @@ def main():
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            state = step()
+            step()
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
+    state = tuple(state_dev.cpu().tolist())
     ms = e0.elapsed_time(e1) / args.steps
     ms_t = torch.tensor([ms], device="cuda")
     if dist is not None:
@@ -613,8 +620,10 @@ def main():
     out32 = torch.empty(N_DRAWS, dtype=torch.float64, device="cuda")
     ms_fp64 = timed(lambda: R.rift_ile_lnZ_state(pt, d_dev, R.FP64), 2)
     ms_lnl = timed(lambda: R.rift_ile_lnL(pt, d_dev, R.FP32_MIXED, out32), 5)
+    ms_sync = timed(lambda: R.rift_ile_lnZ_state(pt, d_dev, R.FP32_MIXED), 10)
     variants = {
         "fp32_mixed_lnZ_draws_per_s": N_DRAWS / (ms * 1e-3),
+        "fp32_mixed_lnZ_with_host_sync_draws_per_s": N_DRAWS / (ms_sync * 1e-3),
         "fp32_mixed_lnL_out_draws_per_s": N_DRAWS / (ms_lnl * 1e-3),
         "fp64_lnZ_draws_per_s": N_DRAWS / (ms_fp64 * 1e-3),
         "speedup_mixed_vs_fp64": ms_fp64 / ms,

@@ -194,6 +194,21 @@ int rift_ile_lnZ_state(const rift_ile_point* pt, const rift_ile_draws* draws,
                        rift_ile_precision prec, const rift_ile_dist* dist, rift_ile_lse* state,
                        void* stream);
 
+/* rift_ile_lnZ_state without a host round trip: enqueues the fused kernel and
+ * the merge of its block partials on `stream` and writes the LSE state
+ * (one rift_ile_lse, 32 bytes) to DEVICE memory state_out when they complete;
+ * nothing is synchronised (except the copy of a distance table, which is
+ * uploaded first as in rift_ile_lnZ_state), so many evaluations can be
+ * chained on a stream and their states read once.  Uses the library's per-device workspace
+ * (allocated on the first call of any lnZ entry point on the device; make
+ * that first call before capturing a stream).  Calls on one device share the
+ * workspace: calls that overlap on the GPU (different streams) race; calls
+ * on one stream are ordered.  The out-of-table count of rift_ile_last_oob is
+ * not updated.  Errors: INVALID_ARG, SHAPE, CUDA, ALLOC. */
+int rift_ile_lnZ_state_async(const rift_ile_point* pt, const rift_ile_draws* draws,
+                             rift_ile_precision prec, const rift_ile_dist* dist,
+                             rift_ile_lse* state_out, void* stream);
+
 /* rift_ile_lnZ_state without any allocation (the paper has no counterpart:
  * this is a deployment variant).  For callers that may not allocate device
  * memory while they run: a framework that owns the device heap through its

@@ -75,6 +75,7 @@ _lib.rift_ile_lnL_grad.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_state.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_merge.argtypes = [_P, ctypes.c_int32, _P, _P]
+_lib.rift_ile_lnZ_state_async.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P]
 _lib.rift_ile_lnZ_state_host.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P, _P]
 _lib.rift_ile_lnZ_batch.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P, _P]
 _lib.rift_ile_batch_create.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int, _P]
@@ -338,6 +339,22 @@ def rift_ile_lnZ_state(point: Point, draws, precision: int = FP32_MIXED, dist=No
                                    ctypes.byref(st), _stream(stream)))
     del keep
     return (st.m, st.s, st.s2, st.n)
+
+
+def rift_ile_lnZ_state_async(point: Point, draws, precision: int = FP32_MIXED, dist=None,
+                             out=None, stream=None):
+    """LSE state (m, s, s2, n) written to a float64 CUDA tensor of 4 without a
+    host synchronisation (chain many on a stream, read once)."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=point.device)
+    ds, keep = _dist_struct(dist)
+    _check(_lib.rift_ile_lnZ_state_async(point.handle, d.ref, precision,
+                                         ctypes.byref(ds) if ds is not None else None,
+                                         out.data_ptr(), _stream(stream)))
+    del keep
+    return out
 
 
 def rift_ile_lnZ(point: Point, draws, precision: int = FP32_MIXED, dist=None, stream=None):

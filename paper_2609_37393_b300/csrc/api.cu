@@ -474,6 +474,38 @@ extern "C" int rift_ile_lnZ_state_host(const rift_ile_point* pt, const rift_ile_
   return RIFT_ILE_OK;
 }
 
+extern "C" int rift_ile_lnZ_state_async(const rift_ile_point* pt, const rift_ile_draws* draws,
+                                        rift_ile_precision prec, const rift_ile_dist* dist,
+                                        rift_ile_lse* state_out, void* stream) {
+  int rc = check_point(pt, prec);
+  if (!rc) rc = check_draws(draws);
+  if (rc) return rc;
+  if (!state_out) {
+    rift_ile_set_error("rift_ile_lnZ_state_async: state_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  static_assert(sizeof(rift_ile_lse) == sizeof(LseState), "state layouts differ");
+  LseState* out = reinterpret_cast<LseState*>(state_out);
+  Workspace* ws = nullptr;
+  if ((rc = get_workspace(&ws))) return rc;
+  if (draws->n == 0)  // the merge of no partials is the empty state
+    return check_cuda(launch_lse_combine(ws->partials, 0, 0.0, out, st), "lnZ combine launch");
+  DistParams dd{};
+  if (dist && (rc = upload_dist(ws, dist, st, &dd))) return rc;
+  int blocks = 0;
+  cudaError_t le;
+  if (!dist)
+    le = launch_lnl(pt, to_params(draws), prec, nullptr, ws->partials, nullptr, &blocks, st);
+  else if (prec == RIFT_ILE_FP64)
+    le = launch_lnl_fp64_dist(pt->host, pt->dev, to_params(draws), dd, nullptr, ws->partials, nullptr, &blocks, st);
+  else
+    le = launch_lnl_mixed_dist(pt->host, pt->dev, to_params(draws), dd, nullptr, ws->partials, nullptr, &blocks, st);
+  if ((rc = check_cuda(le, "lnZ kernel launch"))) return rc;
+  return check_cuda(launch_lse_combine(ws->partials, blocks, (double)draws->n, out, st),
+                    "lnZ combine launch");
+}
+
 extern "C" int rift_ile_lnZ_merge(const rift_ile_lse* states, int32_t S, double out[3],
                                   rift_ile_lse* merged) {
   if ((!states && S > 0) || S < 0) {

@@ -97,6 +97,16 @@ __device__ __forceinline__ float4* xf_slice(float4* smem4, int ncls, int R, int 
 // sin and cos of a double-float angle to ~1e-15 absolute: reduce by 2 pi (pair
 // constant), take the nearest anchor a_j = j 2^-7, and add the residual
 // d (|d| <= 2^-8) through sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24.
+// Unroll factors of the mode loop and of the detector loop (0: the
+// compiler's choice).
+#ifndef RIFT_MIXED_MODE_UNROLL
+#define RIFT_MIXED_MODE_UNROLL 0
+#endif
+#ifndef RIFT_MIXED_DET_UNROLL
+#define RIFT_MIXED_DET_UNROLL 0
+#endif
+constexpr int kModeUnroll = RIFT_MIXED_MODE_UNROLL;
+constexpr int kDetUnroll = RIFT_MIXED_DET_UNROLL;
 #ifndef RIFT_MIXED_SINCOS_CALL  // 1: the anchored sine/cosine is a real call (less code)
 #define RIFT_MIXED_SINCOS_CALL 0
 #endif
@@ -575,6 +585,9 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     int prev_am = -1;
     df cm = df{1.f, 0.f}, sm = df{0.f, 0.f}, c1 = df{1.f, 0.f}, s1p = df{0.f, 0.f};
     bool have1 = false;
+#if RIFT_MIXED_MODE_UNROLL
+#pragma unroll kModeUnroll
+#endif
     for (int j = 0; j < M; ++j) {
       const int4 md = TB.mode[j];  // (mode index, m, l, ypar)
       const int m = md.y, am = m < 0 ? -m : m;
@@ -659,6 +672,9 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 #pragma unroll
       for (int r = 0; r < RR; ++r) G1B[r] = G2B[r] = 0.f;
     }
+#if RIFT_MIXED_DET_UNROLL
+#pragma unroll kDetUnroll
+#endif
     for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
       const int k = P.det_order[q];
       const float4 xfq = xfs[k * kMixedThreads];

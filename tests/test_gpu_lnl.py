@@ -236,3 +236,23 @@ def test_odd_mode_counts(R, n_modes):
     rz = O.lnZ(ref, np.asarray(logw, dtype=np.float64))
     z = R.rift_ile_lnZ(pt, R.Draws(draws, logw.astype(np.float32)), R.FP32_MIXED)
     assert abs(z[0] - rz[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_async_state_equals_sync_state(R, cfg1_small, prec):
+    """rift_ile_lnZ_state_async runs the same kernels as rift_ile_lnZ_state
+    and leaves the same state in device memory, bit for bit; chained calls on
+    one stream stay ordered; zero draws give the empty state."""
+    point, exact, info, draws, logw = cfg1_small
+    pt = R.Point(point)
+    d = R.Draws(draws, logw)
+    ref = R.rift_ile_lnZ_state(pt, d, prec)
+    outs = [R.rift_ile_lnZ_state_async(pt, d, prec) for _ in range(3)]
+    for o in outs:
+        assert tuple(o.cpu().tolist()) == ref
+    nodes = R.rift_ile_dist_nodes(50.0, 200.0, 100.0, 1e-4, 1000.0)
+    ref_d = R.rift_ile_lnZ_state(pt, d, prec, dist=nodes)
+    assert tuple(R.rift_ile_lnZ_state_async(pt, d, prec, dist=nodes).cpu().tolist()) == ref_d
+    empty = {p: np.zeros(0, dtype=np.float32) for p in W.PARAMS}
+    e = R.rift_ile_lnZ_state_async(pt, empty, prec).cpu().tolist()
+    assert e[0] == -math.inf and e[1] == 0.0 and e[3] == 0.0
