@@ -240,17 +240,26 @@ __device__ __forceinline__ void tlse_push(ThreadLse& t, df v) {
 
 // Pushes lnL + ln w with a float ln w that may be infinite: a zero weight
 // (ln w = -inf) is skipped unless lnL is NaN, +inf dominates; the pair sum
-// of a finite lnL and an infinite ln w would otherwise be NaN.
+// of a finite lnL and an infinite ln w would otherwise be NaN.  Written with
+// selects instead of branches (the same arithmetic as tlse_push), so that
+// the update does not split the draw loop into divergent blocks.
 __device__ __forceinline__ void tlse_push_lw(ThreadLse& t, df lnl, float lw) {
-  if (isnan(lw) || isnan(lnl.hi)) {
-    t.nan_seen = 1;
-    return;
-  }
-  if (isinf(lw)) {
-    if (lw > 0.f) tlse_push(t, df{CUDART_INF_F, 0.f});
-    return;
-  }
-  tlse_push(t, df_add_f(lnl, lw));
+  const bool nan_in = isnan(lw) || isnan(lnl.hi);
+  const bool lw_inf = isinf(lw);
+  df v = df_add_f(lnl, lw_inf ? 0.f : lw);
+  if (lw_inf) v = df{lw, 0.f};
+  const bool skip = nan_in || !(v.hi > -CUDART_INF_F);
+  const bool bigger = (v.hi > t.m.hi) || (v.hi == t.m.hi && v.lo > t.m.lo);
+  const float d = __fadd_rn(__fsub_rn(v.hi, t.m.hi), __fsub_rn(v.lo, t.m.lo));
+  const float e = __expf(bigger ? -d : d);  // 0 when t is empty (d = +inf)
+  const float s_new = bigger ? fmaf(t.s, e, 1.f) : t.s + e;
+  const float s2_new = bigger ? fmaf(t.s2, e * e, 1.f) : fmaf(e, e, t.s2);
+  t.nan_seen |= nan_in ? 1 : 0;
+  t.s = skip ? t.s : s_new;
+  t.s2 = skip ? t.s2 : s2_new;
+  const bool take = !skip && bigger;
+  t.m.hi = take ? v.hi : t.m.hi;
+  t.m.lo = take ? v.lo : t.m.lo;
 }
 
 // Exact merge of two states: the smaller maximum is rescaled to the larger

@@ -1008,7 +1008,17 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   ThreadLse st = tlse_init();
   int oob = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  // the LSE update of a draw is applied during the next draw (its loads in
+  // flight), so that its dependent chain does not stall the warp at the end
+  // of every iteration
+  bool pend = false;
+  df pend_l = df{0.f, 0.f};
+  float pend_w = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
+    float lw = 0.f;
+    if (LSE && dp.logw)
+      lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
+    if (LSE && pend) tlse_push_lw(st, pend_l, pend_w);
     MixedDraw o;
     if (DIST && GRAD) {
       // distance-marginal gradient in one pass at x = 1: with lnL(x) = K x -
@@ -1033,11 +1043,12 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
     } else if (!LSE) {
       lnl_out[i] = (double)o.lnl.hi + (double)o.lnl.lo;
     } else {
-      float lw = 0.f;
-      if (dp.logw) lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
-      tlse_push_lw(st, o.lnl, lw);
+      pend = true;
+      pend_l = o.lnl;
+      pend_w = lw;
     }
   }
+  if (LSE && pend) tlse_push_lw(st, pend_l, pend_w);
   if (LSE) block_lse_write(st, partials + blockIdx.x);
   if (oob_count) {
     for (int off = 16; off > 0; off >>= 1) oob += __shfl_down_sync(0xffffffffu, oob, off);
@@ -1203,13 +1214,20 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
     float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
     ThreadLse st = tlse_init();
     const long long end = it.begin + it.count;
+    bool pend = false;  // deferred LSE update, as in lnl_mixed_kernel
+    df pend_l = df{0.f, 0.f};
+    float pend_w = 0.f;
     for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
-      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, T, sA, sg, a12s, xfs, sdp, i);
-      oob += o.oob;
       float lw = 0.f;
       if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
-      tlse_push_lw(st, o.lnl, lw);
+      if (pend) tlse_push_lw(st, pend_l, pend_w);
+      MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, T, sA, sg, a12s, xfs, sdp, i);
+      oob += o.oob;
+      pend = true;
+      pend_l = o.lnl;
+      pend_w = lw;
     }
+    if (pend) tlse_push_lw(st, pend_l, pend_w);
     block_lse_write(st, partials + item);  // ends with every thread past its use of s_item
     __syncthreads();
   }
