@@ -675,6 +675,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 #if RIFT_MIXED_DET_UNROLL
 #pragma unroll kDetUnroll
 #endif
+    const bool hn = P.has_null[c] != 0;  // uniform over the block
     for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
       const int k = P.det_order[q];
       const float4 xfq = xfs[k * kMixedThreads];
@@ -746,10 +747,10 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       // [-3, n + 1]: every tap outside the table lands on a zero row, so
       // the loads need no test (taps outside are only counted)
       const float2* Ek = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * R;
-#pragma unroll
-      for (int tap = 0; tap < 4; ++tap) {
-        const float jj = jf - 1.f + (float)tap;
-        if (!(jj >= 0.f && jj < (float)n)) ++oob;
+      {  // taps outside the table: 1 - j below it, j + 3 - n above it (each in [0, 4])
+        const float nb = fminf(fmaxf(1.f - jf, 0.f), 4.f);
+        const float na = fminf(fmaxf(jf + 3.f - (float)n, 0.f), 4.f);
+        oob += (int)fminf(nb + na, 4.f);
       }
       const int jc = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
       const float2* Ej = Ek + (ptrdiff_t)(jc - 1) * R;
@@ -802,7 +803,10 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
           for (int h = 0; h < 2; ++h) {
             q2 = fmaf(rsv[h], rsv[h], q2);
             const float wf = __fadd_rn(wv[h].hi, wv[h].lo);
-            nul = fmaf(gc[r + h] * wf, wf, nul);
+            // gm1 is zero unless the class keeps near-null directions: the
+            // forward pass skips it then (the adjoint keeps the load, faster there)
+            const float gmr = (GRAD || hn) ? gc[r + h] : 0.f;
+            if (GRAD || hn) nul = fmaf(gmr * wf, wf, nul);
             if (DIST) {  // |w|^2 with the head square exact
               dacc_fma_ff(w2, wv[h].hi, wv[h].hi);
               w2.c = fmaf(2.f * wv[h].hi, wv[h].lo, w2.c);
@@ -810,14 +814,14 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
             }
             if (GRAD) {
               red = fmaf(rsv[h], edv[h], red);
-              const float rho = fmaf(gc[r + h], wf, rsv[h]);
+              const float rho = fmaf(gmr, wf, rsv[h]);
               const float4 q = get_a(r + h);
               g1 = fmaf(rho, __fadd_rn(q.x, q.y), g1);
               g2 = fmaf(rho, __fadd_rn(q.z, q.w), g2);
               G1[r + h] = fmaf(xFr.hi, rho, G1[r + h]);
               G2[r + h] = fmaf(xFi.hi, rho, G2[r + h]);
               if (TWO) {  // dR/2 = sum (1 - gm1) w . dw
-                const float rhoB = __fsub_rn(1.f, gc[r + h]) * wf;
+                const float rhoB = __fsub_rn(1.f, gmr) * wf;
                 g1B = fmaf(rhoB, __fadd_rn(q.x, q.y), g1B);
                 g2B = fmaf(rhoB, __fadd_rn(q.z, q.w), g2B);
                 G1B[r + h] = fmaf(xFr.hi, rhoB, G1B[r + h]);
