@@ -16,7 +16,7 @@ path, the ALU roofline of the kernel, sampled clocks and the FP64 CPU oracle
 as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ile|batch|event|diff|sweep|sampler]
+                  [--workload ile|batch|event|diff|sweep|sampler|response]
 
 The default workload (ile) is the headline line.  The others are extra
 measurements:
@@ -30,7 +30,9 @@ measurements:
          gradient error against the FP64 path;
   sweep  the FP32-mixed error against the FP64 path at SNR 20 ... 1000;
   sampler  forward+backward latency on batches of 128 ... 65536 draws, eager
-         and replayed from a captured CUDA graph.
+         and replayed from a captured CUDA graph;
+  response  the composite-index response (Earth rotation Paths A and B,
+         finite arms Path D) on the 3G network: fused FP64 lnZ steps.
 """
 from __future__ import annotations
 
@@ -515,6 +517,62 @@ def run_sampler(args):
                       "rows": rows}), flush=True)
 
 
+def comp_fp64_fmas(K: int, A: int) -> int:
+    """Declared FP64 FMAs per draw of the composite-index likelihood: per
+    detector the quadratic form of eq. slowrot:lnL:Decomposed in the 2A real
+    coordinates (z^T G z over the upper triangle, 2A^2 + A) and the four-tap
+    data contraction Re sum conj(c) Q (2 FMAs per complex term, 8A)."""
+    return K * (2 * A * A + A + 8 * A)
+
+
+def run_response(args):
+    """The composite-index response (Sec. III) on the 3G network, ten modes,
+    SNR 600: fused FP64 lnL -> LSE steps for Path A (Earth rotation, p_max 0),
+    Path B (p_max 1) and Path D (40 km / 10 km arms, p_max 3)."""
+    import torch
+    import paper_2609_37393_b300 as R
+    import workload.composite as WC
+    torch.cuda.set_device(0)
+    n = args.draws
+    stream = torch.cuda.current_stream()
+    fp64_fma, probe_mhz = R.rift_ile_probe_alu(1, 0.2)
+    rows = []
+    head = None
+    with ClockSampler(0) as clocks:
+        for name, kind, p_max in (("path_a", WC.ROTATION, 0), ("path_b_p1", WC.ROTATION, 1),
+                                  ("path_d_p3", WC.FINITE_ARM, 3)):
+            point, exact, info, draws, logw = WC.comp_3g(kind, p_max, n_draws=n)
+            cp = R.CompPoint(point)
+            d = R.Draws(draws, logw)
+            state = torch.empty(4, dtype=torch.float64, device="cuda")
+            step = lambda: R.rift_ile_comp_lnZ_state_async(cp, d, out=state)
+            for _ in range(args.warmup):
+                step()
+            ms = timed_events(torch, step, max(3, min(args.steps, 10)), stream)
+            z = R.rift_ile_lnZ_merge([tuple(state.cpu().tolist())])[0]
+            row = {"response": name, "kind": kind, "p_max": p_max, "composite_dim": cp.A,
+                   "draws_per_s": n / (ms * 1e-3), "ms_per_step": ms, "lnZ": z[0],
+                   "fp64_fma_per_draw": comp_fp64_fmas(cp.K, cp.A)}
+            rows.append(row)
+            if head is None:
+                head = row
+            cp.close()
+    achieved = head["draws_per_s"] * head["fp64_fma_per_draw"]
+    line = {
+        "metric": "composite-response lnZ draws/s (FP64), 3G network, Path A",
+        "workload": "response", "value": head["draws_per_s"], "unit": "draws/s", "n_gpus": 1,
+        "draws": n, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3G network K=4 (ET triangle + CE 40 km), M=10, SNR 600, "
+                   "Earth rotation Path A (5 sidereal harmonics, A=50)", "draws": n},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_fma / 1e12,
+                     "unit": "TFMA/s (FP64 pipe)", "frac": achieved / fp64_fma,
+                     "fma_per_draw": head["fp64_fma_per_draw"],
+                     "peak_source": f"measured FP64 FMA rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu)"},
+        "rows": rows, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,7 +580,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ile", choices=["ile", "batch", "event", "diff", "sweep", "sampler"])
+    ap.add_argument("--workload", default="ile",
+                    choices=["ile", "batch", "event", "diff", "sweep", "sampler", "response"])
+    ap.add_argument("--draws", type=int, default=1 << 22, help="draws of --workload response")
     ap.add_argument("--points", type=int, default=512)
     ap.add_argument("--chunks", type=int, default=16)
     args = ap.parse_args()
@@ -546,6 +606,9 @@ def main():
         return
     if args.workload == "sampler":
         run_sampler(args)
+        return
+    if args.workload == "response":
+        run_response(args)
         return
 
     import torch

@@ -559,3 +559,151 @@ def lnZ_from_state(state):
     if n <= 0:
         return -math.inf, math.nan, 0.0
     return (m + math.log(s) - math.log(n), math.sqrt(max(0.0, s2 / (s * s) - 1.0 / n)), s)
+
+
+# ------------------------------------------------ composite-index response
+
+RESP_ROTATION = 1
+RESP_FINITE_ARM = 2
+
+
+class _CompDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_det", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+        ("ell", ctypes.c_void_p), ("em", ctypes.c_void_p),
+        ("kind", ctypes.c_int32), ("p_max", ctypes.c_int32), ("omega", ctypes.c_double),
+        ("arm_x", ctypes.c_void_p), ("arm_y", ctypes.c_void_p),
+        ("Q", ctypes.c_void_p), ("q_len", ctypes.c_int32),
+        ("q_t0", ctypes.c_void_p), ("q_dt", ctypes.c_double),
+        ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
+        ("det_pos", ctypes.c_void_p), ("det_resp", ctypes.c_void_p),
+        ("gmst", ctypes.c_double), ("d_ref", ctypes.c_double),
+    ]
+
+
+_lib.rift_ile_comp_n_index.argtypes = [ctypes.c_int32, ctypes.c_int32]
+_lib.rift_ile_comp_create.argtypes = [_P, _P, _P]
+_lib.rift_ile_comp_destroy.argtypes = [_P]
+_lib.rift_ile_comp_coeffs.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_lnL.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_lnZ_state.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_lnZ_state_async.argtypes = [_P, _P, _P, _P]
+
+
+def rift_ile_comp_n_index(kind: int, p_max: int) -> int:
+    """Number of response indices a of the composite response (kind, p_max)."""
+    na = _lib.rift_ile_comp_n_index(kind, p_max)
+    if na < 0:
+        _check(na)
+    return na
+
+
+class CompPoint:
+    """An intrinsic point with a composite response (rift_ile_comp_create).
+
+    point: dict with K, M, ell, em, kind (RESP_ROTATION or RESP_FINITE_ARM),
+    p_max, omega (rad/s), arm_x[K, 3], arm_y[K, 3] (finite arms), Q[K, n, A]
+    complex128 with A = n_index * M (composite index a * M + i), q_t0[K], q_dt,
+    U[K, A, A], V[K, A, A], det_pos[K, 3], det_resp[K, 6], gmst, d_ref.
+    """
+
+    def __init__(self, point: dict, device=None, stream=None):
+        torch = _torch()
+        device = torch.device(device or "cuda")
+        Q = _dev_tensor(point["Q"], torch.complex128, device)
+        K, n, A = Q.shape
+        kind, p_max = int(point["kind"]), int(point["p_max"])
+        self.na = rift_ile_comp_n_index(kind, p_max)
+        M = int(point["M"])
+        if A != self.na * M:
+            raise ValueError(f"Q has {A} composite columns, expected {self.na} x {M}")
+        arms = kind == RESP_FINITE_ARM
+        self._host = {
+            "ell": np.ascontiguousarray(point["ell"], dtype=np.int32),
+            "em": np.ascontiguousarray(point["em"], dtype=np.int32),
+            "t0": np.ascontiguousarray(point["q_t0"], dtype=np.float64),
+            "U": np.ascontiguousarray(np.asarray(point["U"], dtype=np.complex128)).view(np.float64),
+            "V": np.ascontiguousarray(np.asarray(point["V"], dtype=np.complex128)).view(np.float64),
+            "pos": np.ascontiguousarray(point["det_pos"], dtype=np.float64),
+            "resp": np.ascontiguousarray(point["det_resp"], dtype=np.float64),
+            "ax": np.ascontiguousarray(point["arm_x"], dtype=np.float64) if arms else None,
+            "ay": np.ascontiguousarray(point["arm_y"], dtype=np.float64) if arms else None,
+        }
+        h = self._host
+        d = _CompDesc()
+        d.n_det, d.n_modes = K, M
+        d.ell, d.em = h["ell"].ctypes.data, h["em"].ctypes.data
+        d.kind, d.p_max, d.omega = kind, p_max, float(point.get("omega", 0.0))
+        d.arm_x = h["ax"].ctypes.data if arms else None
+        d.arm_y = h["ay"].ctypes.data if arms else None
+        d.Q, d.q_len = Q.data_ptr(), n
+        d.q_t0, d.q_dt = h["t0"].ctypes.data, float(point["q_dt"])
+        d.U, d.V = h["U"].ctypes.data, h["V"].ctypes.data
+        d.det_pos, d.det_resp = h["pos"].ctypes.data, h["resp"].ctypes.data
+        d.gmst, d.d_ref = float(point["gmst"]), float(point["d_ref"])
+        hd = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            _check(_lib.rift_ile_comp_create(ctypes.byref(d), ctypes.byref(hd), _stream(stream)))
+        self._h = hd
+        self.K, self.M, self.n, self.A = K, M, n, A
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.rift_ile_comp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rift_ile_comp_coeffs(cp: CompPoint, draws, out=None, stream=None):
+    """C~^k_a of every draw: complex128 CUDA tensor [n, K, n_index]."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty((d.n, cp.K, cp.na), dtype=torch.complex128, device=cp.device)
+    _check(_lib.rift_ile_comp_coeffs(cp.handle, d.ref, out.data_ptr() if d.n else None,
+                                     _stream(stream)))
+    return out
+
+
+def rift_ile_comp_lnL(cp: CompPoint, draws, out=None, stream=None):
+    """lnL per draw of the composite response (float64 CUDA tensor), FP64."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(d.n, dtype=torch.float64, device=cp.device)
+    _check(_lib.rift_ile_comp_lnL(cp.handle, d.ref, out.data_ptr() if d.n else None,
+                                  _stream(stream)))
+    return out
+
+
+def rift_ile_comp_lnZ_state(cp: CompPoint, draws, stream=None):
+    """LSE state (m, s, s2, n) of the draws under the composite response."""
+    d = _as_draws(draws)
+    st = _Lse()
+    _check(_lib.rift_ile_comp_lnZ_state(cp.handle, d.ref, ctypes.byref(st), _stream(stream)))
+    return (st.m, st.s, st.s2, st.n)
+
+
+def rift_ile_comp_lnZ_state_async(cp: CompPoint, draws, out=None, stream=None):
+    """The LSE state into a float64 CUDA tensor of 4, no host synchronisation."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=cp.device)
+    _check(_lib.rift_ile_comp_lnZ_state_async(cp.handle, d.ref, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def rift_ile_comp_lnZ(cp: CompPoint, draws, stream=None):
+    """(lnZ, sigma_lnZ, n_eff) under the composite response."""
+    return rift_ile_lnZ_merge([rift_ile_comp_lnZ_state(cp, draws, stream)])[0]

@@ -253,6 +253,22 @@ cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_to
   return cudaGetLastError();
 }
 
+int lse_workspace(LseState** partials, LseState** state, unsigned long long** oob) {
+  Workspace* ws = nullptr;
+  int rc = get_workspace(&ws);
+  if (rc) return rc;
+  *partials = ws->partials;
+  *state = ws->state;
+  *oob = ws->oob;
+  return RIFT_ILE_OK;
+}
+
+int validate_draws(const rift_ile_draws* d) { return check_draws(d); }
+
+DrawsParams draws_params(const rift_ile_draws* d) { return to_params(d); }
+
+void set_last_oob(long long v) { t_last_oob = v; }
+
 }  // namespace rift
 
 using namespace rift;

@@ -60,6 +60,14 @@ cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_to
 // SM count of the current device (cached).
 int device_sms();
 
+// The library's per-device scratch (LSE partials, combined state, tap
+// counter), allocated on first use; draw validation and marshalling; the
+// thread-local out-of-table tap count reported by rift_ile_last_oob.
+int lse_workspace(LseState** partials, LseState** state, unsigned long long** oob);
+int validate_draws(const rift_ile_draws* d);
+DrawsParams draws_params(const rift_ile_draws* d);
+void set_last_oob(long long v);
+
 // Grid of a per-draw kernel: SMs x resident blocks per SM, capped so that the
 // per-block partials fit the workspace.  Fixed for a given device and build,
 // so results do not depend on the launch history.

@@ -332,6 +332,11 @@ int validate(const rift_ile_point_desc* d) {
 }
 
 }  // namespace
+
+int harmonic_coefficients(int l, int m, int* k0, double* coef) {
+  return harmonic_terms(l, m, k0, coef);
+}
+
 }  // namespace rift
 
 using namespace rift;

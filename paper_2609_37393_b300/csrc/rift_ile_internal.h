@@ -105,6 +105,9 @@ struct LseState {
 
 // Host helpers ---------------------------------------------------------------
 int check_cuda(cudaError_t e, const char* what);
+// -2Y_lm(iota, phi) = e^{i m phi} sum_r coef[r] c^(k0 + 2r) s^(2l - k0 - 2r),
+// c = cos(iota/2), s = sin(iota/2): fills k0 and coef, returns the term count.
+int harmonic_coefficients(int l, int m, int* k0, double* coef);
 int ensure_anchor_table();  // once per device (sine/cosine and exponential anchors)
 
 }  // namespace rift

@@ -1,5 +1,5 @@
 """The C-ABI library loads without a GPU and exports every symbol that
-include/rift_ile.h declares; the product package fails loudly without it and
+the headers in include/ declare; the product package fails loudly without it and
 never touches the oracle."""
 import ctypes
 import os
@@ -9,12 +9,12 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "rift_ile.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("rift_ile.h", "rift_ile_response.h")]
 PKG = os.path.join(ROOT, "paper_2609_37393_b300")
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(rift_ile_\w+)\s*\(", text)))
 
@@ -29,7 +29,8 @@ def library():
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for n in ("rift_ile_lnL", "rift_ile_lnL_grad", "rift_ile_lnZ", "rift_ile_lnZ_batch",
-              "rift_ile_point_create", "rift_ile_point_destroy", "rift_ile_lnZ_merge"):
+              "rift_ile_point_create", "rift_ile_point_destroy", "rift_ile_lnZ_merge",
+              "rift_ile_comp_create", "rift_ile_comp_lnL", "rift_ile_comp_lnZ_state"):
         assert n in names
 
 
