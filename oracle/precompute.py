@@ -1,0 +1,58 @@
+"""Plain FP64 CPU oracle of the per-point products of eq. QUV.
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.
+
+On a two-sided uniform frequency grid f_q = (q - (nf - 1)/2) df with inner
+product weights w_k(f) = 2 df / S_k(|f|) inside the band (eq. QUV, as a
+Riemann sum), the products are the plain sums
+
+    Q_{k,lm}(t)     = sum_q w_k(f_q) e^{2 pi i f_q t} conj(h_lm(f_q)) d_k(f_q)
+    U_{k,lm,l'm'}   = sum_q w_k(f_q) conj(h_lm(f_q)) h_l'm'(f_q)
+    V_{k,lm,l'm'}   = sum_q w_k(f_q) h_lm(-f_q) h_l'm'(f_q)
+
+evaluated here term by term (the exponential per (t, f) pair, no FFT).  The
+tests pin them against the FFT-based table builder of the workloads (a
+different algorithm), the symmetries U = U^+ and V = V^T, and the physical
+normalisation: with noise-free data the factored likelihood built from these
+products equals rho^2/2 at the injection.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def q_direct(freq, wgt_k, hlm, dk_k, times, chunk: int = 64):
+    """Q_{k,lm}(t) for every t in `times`: [len(times)][M] complex128."""
+    freq = np.asarray(freq, dtype=np.float64)
+    X = np.asarray(wgt_k)[None, :] * np.conj(np.asarray(hlm)) * np.asarray(dk_k)[None, :]
+    times = np.asarray(times, dtype=np.float64)
+    out = np.empty((times.shape[0], X.shape[0]), dtype=np.complex128)
+    for a in range(0, times.shape[0], chunk):
+        t = times[a:a + chunk]
+        E = np.exp(2j * np.pi * np.outer(t, freq))          # [chunk][nf]
+        out[a:a + chunk] = E @ X.T
+    return out
+
+
+def q_table_direct(freq, wgt, hlm, dk, t0, dt, n):
+    """Q_{k,lm}(t0_k + j dt), j < n: [K][n][M]."""
+    K = np.asarray(dk).shape[0]
+    return np.stack([q_direct(freq, wgt[k], hlm, dk[k], t0[k] + dt * np.arange(n))
+                     for k in range(K)])
+
+
+def uv_direct(wgt, hlm):
+    """(U, V): [K][M][M] each; h(-f_q) is the grid's mirror entry nf - 1 - q."""
+    wgt = np.asarray(wgt)
+    hlm = np.asarray(hlm)
+    K, M = wgt.shape[0], hlm.shape[0]
+    U = np.empty((K, M, M), dtype=np.complex128)
+    V = np.empty((K, M, M), dtype=np.complex128)
+    hm = hlm[:, ::-1]
+    for k in range(K):
+        for i in range(M):
+            for j in range(M):
+                U[k, i, j] = np.sum(wgt[k] * np.conj(hlm[i]) * hlm[j])
+                V[k, i, j] = np.sum(wgt[k] * hm[i] * hlm[j])
+    return U, V
