@@ -16,7 +16,7 @@ path, the ALU roofline of the kernel, sampled clocks and the FP64 CPU oracle
 as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ile|batch|event|diff|sweep|sampler|response]
+                  [--workload ile|batch|event|diff|sweep|sampler|response|precompute]
 
 The default workload (ile) is the headline line.  The others are extra
 measurements:
@@ -32,7 +32,8 @@ measurements:
   sampler  forward+backward latency on batches of 128 ... 65536 draws, eager
          and replayed from a captured CUDA graph;
   response  the composite-index response (Earth rotation Paths A and B,
-         finite arms Path D) on the 3G network: fused FP64 lnZ steps.
+         finite arms Path D) on the 3G network: fused FP64 lnZ steps;
+  precompute  the GPU precompute of Q, U, V for the 3G point (cuFFT).
 """
 from __future__ import annotations
 
@@ -573,6 +574,70 @@ def run_response(args):
     print(json.dumps(line), flush=True)
 
 
+def precompute_flops(K: int, M: int, nf: int, nfft: int) -> int:
+    """Declared FP64 flops of one GPU precompute: K M inverse FFTs of length
+    nfft at the customary 5 N log2 N, plus 8 flops per (k, i, j, f) for the
+    U and V sums; the scatter and gather are a few flops per element."""
+    return int(K * M * 5 * nfft * math.log2(nfft)) + K * M * M * nf * 8
+
+
+def run_precompute(args):
+    """GPU precompute of Q, U, V (eq. QUV) for the 3G point: scatter into
+    zero-padded frames, one batched inverse FFT (cuFFT), gather; U and V by
+    block reductions.  Against the fixture's numpy FFT builder and the oracle's
+    direct sums on a sample of table rows."""
+    import torch
+    import paper_2609_37393_b300 as R
+    import workload as W
+    import oracle.precompute as OP
+    torch.cuda.set_device(0)
+    point, exact, info, draws, logw = W.config1(n_draws=1 << 10)
+    df = float(exact["freq"][1] - exact["freq"][0])
+    K, n, M = np.asarray(point["Q"]).shape
+    nf = exact["freq"].shape[0]
+    nfft = int(round(1.0 / (df * point["q_dt"])))
+    hlm = torch.as_tensor(exact["hlm"], device="cuda")
+    dk = torch.as_tensor(exact["dk"], device="cuda")
+    wgt = torch.as_tensor(exact["wgt"], device="cuda")
+    stream = torch.cuda.current_stream()
+    call = lambda: R.rift_ile_precompute(hlm, dk, wgt, df, point["q_t0"], point["q_dt"], n)
+    with ClockSampler(0) as clocks:
+        for _ in range(args.warmup):
+            call()
+        ms = timed_events(torch, call, max(10, min(args.steps, 50)), stream)
+    Qg = call()[0].cpu().numpy()
+    t0 = time.perf_counter()
+    Qf = W.q_table(exact["wgt"], exact["hlm"], exact["dk"], exact["freq"], df, point["q_t0"],
+                   point["q_dt"], n)
+    W.uv_matrices(exact["wgt"], exact["hlm"])
+    numpy_s = time.perf_counter() - t0
+    rows = np.arange(0, n, n // 16)
+    t0 = time.perf_counter()
+    Qd = OP.q_direct(exact["freq"], exact["wgt"][0], exact["hlm"], exact["dk"][0],
+                     point["q_t0"][0] + point["q_dt"] * rows)
+    oracle_s = (time.perf_counter() - t0) * (K * n / len(rows))
+    err = float(np.max(np.abs(Qg[0, rows] - Qd)) / np.max(np.abs(Qd)))
+    flops = precompute_flops(K, M, nf, nfft)
+    fp64_fma, probe_mhz = R.rift_ile_probe_alu(1, 0.2)
+    achieved = flops / (ms * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "GPU precompute of Q, U, V per intrinsic point (ms)", "workload": "precompute",
+        "value": ms, "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "3G network K=4, M=10, 16385 frequencies (5-2048 Hz, df 0.25 Hz), "
+                   "table 1311 samples at 32768 Hz (nfft 131072), complex64 Q"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": 2 * fp64_fma / 1e12,
+                     "unit": "TFLOP/s (FP64 pipe, one FMA = 2 flops)",
+                     "frac": achieved / (2 * fp64_fma / 1e12), "flops_per_call": flops,
+                     "peak_source": f"measured FP64 FMA rate at {probe_mhz:.0f} MHz "
+                                    "(rift_ile_probe_alu)"},
+        "numpy_fft_builder_ms": numpy_s * 1e3, "speedup_vs_numpy_fft": numpy_s * 1e3 / ms,
+        "cpu_baseline": {"value": oracle_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"direct sums of eq. QUV for {len(rows)} table rows of "
+                                   "detector 0, scaled to the whole table"},
+        "max_rel_err_vs_direct_sum": err, "clocks": clocks.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -581,7 +646,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="ile",
-                    choices=["ile", "batch", "event", "diff", "sweep", "sampler", "response"])
+                    choices=["ile", "batch", "event", "diff", "sweep", "sampler", "response",
+                             "precompute"])
     ap.add_argument("--draws", type=int, default=1 << 22, help="draws of --workload response")
     ap.add_argument("--points", type=int, default=512)
     ap.add_argument("--chunks", type=int, default=16)
@@ -609,6 +675,9 @@ def main():
         return
     if args.workload == "response":
         run_response(args)
+        return
+    if args.workload == "precompute":
+        run_precompute(args)
         return
 
     import torch

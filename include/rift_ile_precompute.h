@@ -1,0 +1,64 @@
+/* rift_ile_precompute.h -- GPU precompute of the per-point products of
+ * eq. QUV ("Scaling RIFT 1", arXiv 2609.37393, Sec. II.A; the fine-table
+ * pregrid of eq. q-time-pregrid), C ABI, FP64.
+ *
+ * On a two-sided uniform frequency grid f_q = (q - (nf - 1)/2) df, q < nf
+ * (nf odd, so that -f_q is the grid entry nf - 1 - q), with inner-product
+ * weights w_k(f_q) (2 df / S_k(|f|) inside the band, 0 outside):
+ *
+ *   Q_{k,lm}(t) = sum_q w_k(f_q) e^{2 pi i f_q t} conj(h_lm(f_q)) d_k(f_q)
+ *   U_{k,ij}    = sum_q w_k(f_q) conj(h_i(f_q)) h_j(f_q)
+ *   V_{k,ij}    = sum_q w_k(f_q) h_i(-f_q) h_j(f_q)
+ *
+ * Q is produced on the table t = q_t0[k] + j q_dt, j < q_len, by one
+ * zero-padded inverse FFT of length nfft = 1 / (df q_dt) per (detector, mode)
+ * (cuFFT, double complex, batched): the frequency series times
+ * e^{2 pi i f t0} is scattered to the FFT bins f / df mod nfft, which makes
+ * sample j of the transform exactly the sum above at t0 + j dt.  U and V are
+ * per-(k, i, j) block reductions in a fixed order (bitwise reproducible).
+ *
+ * Requirements: 1 / (df q_dt) within 1e-9 of an integer nfft >= max(nf,
+ * q_len); nf odd; K <= RIFT_ILE_MAX_DET, M <= RIFT_ILE_MAX_MODES.
+ * Ownership: the caller owns every buffer; the call allocates its FFT work
+ * buffer (K M nfft complex doubles) stream-ordered and frees it before
+ * returning, and keeps one cuFFT plan per (device, nfft, batch) until
+ * rift_ile_release.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA (cuFFT failures included),
+ * ALLOC.
+ */
+#ifndef RIFT_ILE_PRECOMPUTE_H
+#define RIFT_ILE_PRECOMPUTE_H
+#include "rift_ile.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*   hlm   DEVICE [M][nf] complex128 (re, im interleaved): the mode spectra
+ *   dk    DEVICE [K][nf] complex128: the data of each detector
+ *   wgt   DEVICE [K][nf] double: inner-product weights
+ *   q_t0  HOST [K] time of table sample 0, seconds
+ *   q_dtype  RIFT_ILE_C64 or RIFT_ILE_C128: element type of Q_out */
+typedef struct {
+  int32_t n_det;
+  int32_t n_modes;
+  int32_t nf;
+  double df;
+  const double* hlm;
+  const double* dk;
+  const double* wgt;
+  const double* q_t0;
+  double q_dt;
+  int32_t q_len;
+  int32_t q_dtype;
+} rift_ile_precompute_desc;
+
+/* Q_out: DEVICE [K][q_len][M] complex (q_dtype); U_out, V_out: DEVICE
+ * [K][M][M] complex128.  Any of the three may be NULL to skip it. */
+int rift_ile_precompute(const rift_ile_precompute_desc* desc, void* Q_out, double* U_out,
+                        double* V_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

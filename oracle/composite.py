@@ -171,3 +171,76 @@ def lnL(pt: CompPoint, draws, terms: bool = False):
     if terms:
         return out, tds, tqs, oob
     return out
+
+
+def _coeff_derivs(pt: CompPoint, k, ra, dec, psi, tc, h=1e-4):
+    """d C~^k / d(ra, dec, psi, t_c) by fourth-order central differences of
+    the coefficient functions (smooth trigonometric polynomials of the angles
+    and of the arrival time; no table is involved)."""
+    base = np.array([ra, dec, psi, tc], dtype=np.float64)
+    steps = np.array([h, h, h, h * 1e-2])
+    out = []
+    for j in range(4):
+        def f(v):
+            a = base.copy()
+            a[j] += v
+            return pt.coeffs(k, a[0], a[1], a[2], a[3])
+        s = steps[j]
+        out.append((-f(2 * s) + 8 * f(s) - 8 * f(-s) + f(-2 * s)) / (12 * s))
+    return out
+
+
+def lnL_grad(pt: CompPoint, draws):
+    """(lnL, grad[N, 7]) of the composite likelihood by the chain rule:
+    d T_d = Re sum conj(dc) Q + Re sum conj(c) Q' dt_k and
+    d T_q = 2 Re(dc^+ U c) + 2 Re(dc^T V c) (U Hermitian, V symmetric), with
+    the template derivative dc = dC~ (x) Y + C~ (x) dY: dY/d phase = i m Y,
+    dY/d incl analytic, Q' the slope of the same cubic, dt_k from the delay,
+    and dC~ by central differences of the coefficient functions.  Parameter
+    order (ra, dec, psi, incl, phase, lnD, t)."""
+    th = {p: np.asarray(draws[p], dtype=np.float64) for p in
+          ("ra", "dec", "psi", "incl", "phase", "lnD", "t")}
+    N = th["ra"].shape[0]
+    out = np.empty(N)
+    g = np.zeros((N, 7))
+    for i in range(N):
+        ra, dec, psi, tc = th["ra"][i], th["dec"][i], th["psi"][i], th["t"][i]
+        incl, phase = th["incl"][i], th["phase"][i]
+        Y = np.array([sylm(-2, l, m, incl, phase) for l, m in zip(pt.ell, pt.em)])
+        dYi = np.array([sylm(-2, l, m, incl, phase, dtheta=True) for l, m in zip(pt.ell, pt.em)])
+        dYp = 1j * np.array(pt.em) * Y
+        x = pt.d_ref * math.exp(-th["lnD"][i])
+        td = tq = 0.0
+        dtd = np.zeros(7)
+        dtq = np.zeros(7)
+        for k in range(pt.K):
+            C = pt.coeffs(k, ra, dec, psi, tc)
+            dC = _coeff_derivs(pt, k, ra, dec, psi, tc)
+            c = np.kron(C, Y)
+            tk = delay(pt.pos[k], ra, dec, pt.gmst, tc)
+            hh = 1e-6
+            dtk = [(delay(pt.pos[k], ra + hh, dec, pt.gmst, tc)
+                    - delay(pt.pos[k], ra - hh, dec, pt.gmst, tc)) / (2 * hh),
+                   (delay(pt.pos[k], ra, dec + hh, pt.gmst, tc)
+                    - delay(pt.pos[k], ra, dec - hh, pt.gmst, tc)) / (2 * hh)]
+            out_q = np.empty(2 * pt.A)
+            dout_q = np.empty(2 * pt.A)
+            lib().ora_qinterp(_ptr(pt.Qv[k]), pt.n, pt.A, float(pt.t0[k]), pt.dt, float(tk),
+                              _ptr(out_q), _ptr(dout_q))
+            q, dq = out_q.view(np.complex128), dout_q.view(np.complex128)
+            Uc, Vc = pt.U[k] @ c, pt.V[k] @ c
+            td += float(np.real(np.vdot(c, q)))
+            tq += float(np.real(np.conj(c) @ Uc) + np.real(c @ Vc))
+            dcs = {0: np.kron(dC[0], Y), 1: np.kron(dC[1], Y), 2: np.kron(dC[2], Y),
+                   3: np.kron(C, dYi), 4: np.kron(C, dYp), 6: np.kron(dC[3], Y)}
+            dts = {0: dtk[0], 1: dtk[1], 6: 1.0}
+            for j, dc in dcs.items():
+                v = float(np.real(np.vdot(dc, q)))
+                if j in dts:
+                    v += dts[j] * float(np.real(np.vdot(c, dq)))
+                dtd[j] += v
+                dtq[j] += 2.0 * float(np.real(np.conj(dc) @ Uc)) + 2.0 * float(np.real(dc @ Vc))
+        out[i] = x * td - 0.25 * x * x * tq
+        g[i] = x * dtd - 0.25 * x * x * dtq
+        g[i, 5] = -x * td + 0.5 * x * x * tq
+    return out, g

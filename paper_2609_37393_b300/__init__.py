@@ -707,3 +707,46 @@ def rift_ile_comp_lnZ_state_async(cp: CompPoint, draws, out=None, stream=None):
 def rift_ile_comp_lnZ(cp: CompPoint, draws, stream=None):
     """(lnZ, sigma_lnZ, n_eff) under the composite response."""
     return rift_ile_lnZ_merge([rift_ile_comp_lnZ_state(cp, draws, stream)])[0]
+
+
+# ------------------------------------------------------- Q, U, V precompute
+
+class _PrecompDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_det", ctypes.c_int32), ("n_modes", ctypes.c_int32), ("nf", ctypes.c_int32),
+        ("df", ctypes.c_double), ("hlm", ctypes.c_void_p), ("dk", ctypes.c_void_p),
+        ("wgt", ctypes.c_void_p), ("q_t0", ctypes.c_void_p), ("q_dt", ctypes.c_double),
+        ("q_len", ctypes.c_int32), ("q_dtype", ctypes.c_int32),
+    ]
+
+
+_lib.rift_ile_precompute.argtypes = [_P, _P, _P, _P, _P]
+
+
+def rift_ile_precompute(hlm, dk, wgt, df, q_t0, q_dt, q_len, q_dtype="complex64", device=None,
+                        stream=None):
+    """Q[K, q_len, M] (complex64 or complex128), U[K, M, M], V[K, M, M]
+    (complex128) of eq. QUV on the GPU from the mode spectra hlm[M, nf], the
+    data dk[K, nf] and the weights wgt[K, nf] on the two-sided grid of
+    spacing df (nf odd); all CUDA tensors are returned."""
+    torch = _torch()
+    device = torch.device(device or "cuda")
+    h = _dev_tensor(hlm, torch.complex128, device)
+    d = _dev_tensor(dk, torch.complex128, device)
+    w = _dev_tensor(wgt, torch.float64, device)
+    M, nf = h.shape
+    K = d.shape[0]
+    t0 = np.ascontiguousarray(q_t0, dtype=np.float64)
+    qt = {"complex64": torch.complex64, "complex128": torch.complex128}[q_dtype]
+    Q = torch.empty((K, int(q_len), M), dtype=qt, device=device)
+    U = torch.empty((K, M, M), dtype=torch.complex128, device=device)
+    V = torch.empty_like(U)
+    s = _PrecompDesc()
+    s.n_det, s.n_modes, s.nf, s.df = K, M, nf, float(df)
+    s.hlm, s.dk, s.wgt = h.data_ptr(), d.data_ptr(), w.data_ptr()
+    s.q_t0, s.q_dt, s.q_len = t0.ctypes.data, float(q_dt), int(q_len)
+    s.q_dtype = 1 if qt == torch.complex128 else 0
+    with torch.cuda.device(device):
+        _check(_lib.rift_ile_precompute(ctypes.byref(s), Q.data_ptr(), U.data_ptr(), V.data_ptr(),
+                                        _stream(stream)))
+    return Q, U, V

@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if (not os.path.exists(OUT) or force
             or os.path.getmtime(OUT) < max(os.path.getmtime(o) for o in objs)):
         tmp = OUT + f".tmp{os.getpid()}"
-        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -657,6 +657,7 @@ extern "C" int rift_ile_dist_nodes(double d_min, double d_max, double d_ref, dou
 }
 
 extern "C" int rift_ile_release(void) {
+  release_fft_plans();
   std::lock_guard<std::mutex> lock(g_ws_mu);
   int cur = 0;
   cudaGetDevice(&cur);

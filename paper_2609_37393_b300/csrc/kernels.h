@@ -67,6 +67,8 @@ int lse_workspace(LseState** partials, LseState** state, unsigned long long** oo
 int validate_draws(const rift_ile_draws* d);
 DrawsParams draws_params(const rift_ile_draws* d);
 void set_last_oob(long long v);
+// Destroys the cuFFT plans the precompute keeps (rift_ile_release).
+void release_fft_plans();
 
 // Grid of a per-draw kernel: SMs x resident blocks per SM, capped so that the
 // per-block partials fit the workspace.  Fixed for a given device and build,

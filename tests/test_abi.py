@@ -9,7 +9,8 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("rift_ile.h", "rift_ile_response.h")]
+HEADERS = [os.path.join(ROOT, "include", h)
+           for h in ("rift_ile.h", "rift_ile_response.h", "rift_ile_precompute.h")]
 PKG = os.path.join(ROOT, "paper_2609_37393_b300")
 
 
@@ -30,7 +31,8 @@ def test_header_declares_the_entry_points():
     names = declared_functions()
     for n in ("rift_ile_lnL", "rift_ile_lnL_grad", "rift_ile_lnZ", "rift_ile_lnZ_batch",
               "rift_ile_point_create", "rift_ile_point_destroy", "rift_ile_lnZ_merge",
-              "rift_ile_comp_create", "rift_ile_comp_lnL", "rift_ile_comp_lnZ_state"):
+              "rift_ile_comp_create", "rift_ile_comp_lnL", "rift_ile_comp_lnZ_state",
+              "rift_ile_precompute"):
         assert n in names
 
 
