@@ -245,3 +245,33 @@ def test_planted_mistake_is_caught(name):
     assert text.count(old) == 1, name
     fails = _battery(_load_variant(text.replace(old, new), name))
     assert fails, f"mutation {name} passed every pin"
+
+
+@pytest.mark.parametrize("kind,p_max", [(WC.ROTATION, 0), (WC.ROTATION, 2), (WC.FINITE_ARM, 3)])
+def test_oracle_gradient_against_central_differences(kind, p_max):
+    """The chain-rule gradient against central differences of lnL itself, on
+    draws whose arrival times stay inside one table interval over the steps
+    (the cubic's slope is only continuous inside an interval)."""
+    point, exact, info, draws, logw = WC.comp_small(kind, p_max, n_draws=48)
+    pt = OC.CompPoint(point)
+    lnl, g = OC.lnL_grad(pt, draws)
+    assert np.allclose(lnl, OC.lnL(pt, draws), rtol=0, atol=1e-9 * np.max(np.abs(lnl)))
+    steps = [1e-5, 1e-5, 1e-5, 1e-5, 1e-5, 1e-6, 1e-7]
+    keep = np.ones(len(lnl), dtype=bool)
+    for i in range(len(lnl)):
+        for k in range(pt.K):
+            tk = O.delay(pt.pos[k], draws["ra"][i], draws["dec"][i], pt.gmst, draws["t"][i])
+            u = (tk - pt.t0[k]) / pt.dt
+            fr = u - math.floor(u)
+            if min(fr, 1 - fr) < 3e-3 or u < 2 or u > pt.n - 3:
+                keep[i] = False
+    assert keep.sum() >= 24
+    scale = np.abs(g) + np.sqrt(np.mean(g ** 2, axis=0))
+    for j, p in enumerate(W.PARAMS):
+        up = {q: np.array(draws[q], dtype=float) for q in W.PARAMS}
+        dn = {q: np.array(draws[q], dtype=float) for q in W.PARAMS}
+        up[p] += steps[j]
+        dn[p] -= steps[j]
+        fd = (OC.lnL(pt, up) - OC.lnL(pt, dn)) / (2 * steps[j])
+        err = (np.abs(fd - g[:, j]) / scale[:, j])[keep]
+        assert err.max() <= 2e-6, (p, err.max())
