@@ -551,8 +551,13 @@ def run_response(args):
                 step()
             ms = timed_events(torch, step, max(3, min(args.steps, 10)), stream)
             z = R.rift_ile_lnZ_merge([tuple(state.cpu().tolist())])[0]
+            lnl = torch.empty(n, dtype=torch.float64, device="cuda")
+            grad = torch.empty((7, n), dtype=torch.float64, device="cuda")
+            ms_g = timed_events(torch, lambda: R.rift_ile_comp_lnL_grad(cp, d, lnl, grad), 2,
+                                stream)
             row = {"response": name, "kind": kind, "p_max": p_max, "composite_dim": cp.A,
                    "draws_per_s": n / (ms * 1e-3), "ms_per_step": ms, "lnZ": z[0],
+                   "fwd_bwd_draws_per_s": n / (ms_g * 1e-3),
                    "fp64_fma_per_draw": comp_fp64_fmas(cp.K, cp.A)}
             rows.append(row)
             if head is None:

@@ -118,6 +118,15 @@ int rift_ile_comp_coeffs(const rift_ile_comp* cp, const rift_ile_draws* draws, d
 int rift_ile_comp_lnL(const rift_ile_comp* cp, const rift_ile_draws* draws, double* lnL_out,
                       void* stream);
 
+/* lnL (DEVICE [n], may be NULL) and d lnL / d theta into DEVICE grad_out
+ * [7][n] (double; parameter-major: ra, dec, psi, incl, phase, lnD, t), FP64,
+ * on `stream`: the chain rule of Sec. II.B through the coefficients C~^k_a
+ * (their angle and arrival-time derivatives in closed form), the harmonics
+ * and the slope of the table cubic.  A draw whose arrival time is not finite
+ * gets NaN throughout.  Errors: INVALID_ARG, CUDA. */
+int rift_ile_comp_lnL_grad(const rift_ile_comp* cp, const rift_ile_draws* draws, double* lnL_out,
+                           double* grad_out, void* stream);
+
 /* LSE state of the draws (fused lnL -> LSE, FP64), to HOST *state; synchronises.
  * Taps outside the table read zero and are counted (rift_ile_last_oob). */
 int rift_ile_comp_lnZ_state(const rift_ile_comp* cp, const rift_ile_draws* draws,

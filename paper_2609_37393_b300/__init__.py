@@ -750,3 +750,19 @@ def rift_ile_precompute(hlm, dk, wgt, df, q_t0, q_dt, q_len, q_dtype="complex64"
         _check(_lib.rift_ile_precompute(ctypes.byref(s), Q.data_ptr(), U.data_ptr(), V.data_ptr(),
                                         _stream(stream)))
     return Q, U, V
+
+
+_lib.rift_ile_comp_lnL_grad.argtypes = [_P, _P, _P, _P, _P]
+
+
+def rift_ile_comp_lnL_grad(cp: CompPoint, draws, lnl_out=None, grad_out=None, stream=None):
+    """(lnL[n], grad[7, n]) of the composite response as float64 CUDA tensors, FP64."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if lnl_out is None:
+        lnl_out = torch.empty(d.n, dtype=torch.float64, device=cp.device)
+    if grad_out is None:
+        grad_out = torch.empty((7, d.n), dtype=torch.float64, device=cp.device)
+    _check(_lib.rift_ile_comp_lnL_grad(cp.handle, d.ref, lnl_out.data_ptr() if d.n else None,
+                                       grad_out.data_ptr() if d.n else None, _stream(stream)))
+    return lnl_out, grad_out

@@ -70,6 +70,25 @@ __device__ __forceinline__ void sylm_eval(const PointParams& P, int i, T c, T s,
   yim = amp * ei;
 }
 
+// d/d iota of the real amplitude of -2Y_lm (mode i): the Goldberg sum
+// sum_r a_r c^p s^q, p = k0 + 2r, q = 2l - p, c = cos(iota/2), s = sin(iota/2),
+// differentiated term by term (dc/d iota = -s/2, ds/d iota = c/2).
+__device__ __forceinline__ double sylm_damp_dincl(const PointParams& P, int i, double c, double s) {
+  const int l = P.ell[i], nt = P.ynt[i], k0 = P.yk0[i];
+  double damp = 0.0;
+  for (int r = 0; r < nt; ++r) {
+    const int pp = k0 + 2 * r, qq = 2 * l - pp;
+    double cpm = 1.0, sqm = 1.0;
+    for (int u = 0; u < pp - 1; ++u) cpm *= c;
+    for (int u = 0; u < qq - 1; ++u) sqm *= s;
+    double t = 0.0;
+    if (pp > 0) t -= pp * cpm * (qq > 0 ? sqm * s : 1.0) * s;
+    if (qq > 0) t += qq * (pp > 0 ? cpm * c : 1.0) * c * sqm;
+    damp += 0.5 * P.ycoef[i][r] * t;
+  }
+  return damp;
+}
+
 // a^T D b with D stored as xx, xy, xz, yy, yz, zz.
 template <typename T>
 __device__ __forceinline__ T quad3(const T* D, const T a[3], const T b[3]) {

@@ -32,31 +32,13 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/rift_ile_response.h"
+#include "comp.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
 namespace rift {
 
-constexpr int kMaxRespIdx = 32;  // response indices a (rotation p_max <= 3)
-constexpr int kCompThreads = 128;
-
-struct CompParams {
-  int K, M, kind, p_max, na, A, n, nblk;
-  double omega, gmst, d_ref, dt, inv_dt;
-  double t0[kMaxDet];
-  double pos[kMaxDet][3];
-  double resp[kMaxDet][6];
-  double armx[kMaxDet][3], army[kMaxDet][3];
-  const double2* Q;  // [K][n][A]
-  const double* G;   // [K][nblk][4][M][M]: sub-blocks (Re,Re), (Re,Im), (Im,Re), (Im,Im)
-};
-
 namespace {
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 
 // C~^k_a of one detector (composite order), out[na].
 __device__ void comp_coeffs(const CompParams& C, int k, double sd, double cd, double sg,
@@ -152,32 +134,6 @@ __device__ void comp_coeffs(const CompParams& C, int k, double sd, double cd, do
     }
     off += width;
   }
-}
-
-struct CompDraw {
-  double sd, cd, sg, cg, s2p, c2p;
-  double s[3], e1[3], e2[3];
-};
-
-__device__ __forceinline__ CompDraw comp_geometry(const CompParams& C, double ra, double dec,
-                                                  double psi) {
-  CompDraw g;
-  double sl, cl;
-  sincos(ra - C.gmst, &sl, &cl);
-  sincos(dec, &g.sd, &g.cd);
-  g.sg = -sl;  // g = gmst - ra = -lam
-  g.cg = cl;
-  g.s[0] = g.cd * cl;
-  g.s[1] = g.cd * sl;
-  g.s[2] = g.sd;
-  g.e1[0] = -sl;
-  g.e1[1] = cl;
-  g.e1[2] = 0.0;
-  g.e2[0] = -g.sd * cl;
-  g.e2[1] = -g.sd * sl;
-  g.e2[2] = g.cd;
-  sincos(2.0 * psi, &g.s2p, &g.c2p);
-  return g;
 }
 
 struct CompOut {
@@ -442,13 +398,6 @@ int validate_comp(const rift_ile_comp_desc* d, int* na_out) {
 }  // namespace
 }  // namespace rift
 
-struct rift_ile_comp {
-  rift::CompParams host;
-  rift::PointParams* dev_base;  // harmonics of the modes (device)
-  double2* q;                   // owned copy of Q
-  double* G;                    // owned quadratic-form blocks
-  int device;
-};
 
 using namespace rift;
 

@@ -286,19 +286,8 @@ __device__ __forceinline__ double lnl_fp64_grad_draw(const PointParams& P, const
       yr[m] = yi[m] = dyr[m] = dyi[m] = 0.0;
       if (m < M) {
         sylm_eval<double>(P, m, ch, sh, cp, sp, P.ycoef[m], yr[m], yi[m]);
-        // d/d iota of sum_r a_r c^p s^q, p = k0 + 2r, q = 2l - p
-        const int l = P.ell[m], nt = P.ynt[m], k0 = P.yk0[m], em = P.em[m];
-        double damp = 0.0;
-        for (int r = 0; r < nt; ++r) {
-          const int pp = k0 + 2 * r, qq = 2 * l - pp;
-          double cpm = 1.0, sqm = 1.0;
-          for (int u = 0; u < pp - 1; ++u) cpm *= ch;
-          for (int u = 0; u < qq - 1; ++u) sqm *= sh;
-          double t = 0.0;
-          if (pp > 0) t -= pp * cpm * (qq > 0 ? sqm * sh : 1.0) * sh;
-          if (qq > 0) t += qq * (pp > 0 ? cpm * ch : 1.0) * ch * sqm;
-          damp += 0.5 * P.ycoef[m][r] * t;
-        }
+        const int em = P.em[m];
+        const double damp = sylm_damp_dincl(P, m, ch, sh);
         double er = 1.0, ei = 0.0;
         const int am = em < 0 ? -em : em;
         for (int u = 0; u < am; ++u) {
