@@ -1,0 +1,115 @@
+"""Plain FP64 CPU oracle of the in-likelihood direct marginalisation over
+(phi_ref, psi) and distance (Sec. II.D, eq. direct_marginalization; App. F).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.
+
+For one draw of the sampled coordinates (ra, dec, incl, t_c) it computes
+
+    L_dir = int dphi dpsi dx  p(phi) p(psi) p_x(x) exp[lnL(phi, psi, x)],
+
+following the paper's steps:
+
+1. ERAI reconstruction (eq. ap:angleharm, eq. ap:nyquist): at fixed time the
+   data term K(phi, psi) and the model norm R(phi, psi) of lnL(x) = K x - R x^2/2
+   (eq. ap:dexp; K and R at x = 1) are finite trigonometric polynomials, with
+   harmonics e^{2 i p psi}, |p| <= 2, and e^{i q phi}, |q| <= 2 m_max.  They are
+   sampled with the static oracle on a product grid of N_psi = 5 polarisations
+   and N_phi = 4 m_max + 1 phases and their coefficients recovered by a 2D DFT.
+2. The exponential is integrated on an arithmetic (periodic trapezoid) grid of
+   n_phi x n_psi points in [0, 2 pi) x [0, pi), sized by the caller from the
+   amplitude, with the uniform priors p(phi) = 1/(2 pi), p(psi) = 1/pi.
+3. At each grid point the distance is integrated by adaptive Gauss-Hermite in
+   x = d_ref / D (eq. ap:dgh) centred at x* = K/R with width sigma_x = R^(-1/2)
+   (eq. ap:dpeak), with the prior uniform in volume, p(D) = 3 D^2 /
+   (D_max^3 - D_min^3) on [D_min, D_max], i.e. p_x(x) = 3 d_ref^3 x^-4 /
+   (D_max^3 - D_min^3) on [d_ref/D_max, d_ref/D_min]:
+   int p_x e^{K x - R x^2/2} dx ~ e^{K^2/(2R)} sqrt(2) sigma_x sum_i w_i
+   p_x(x* + sqrt(2) sigma_x xi_i) with the Gauss-Hermite rule (xi_i, w_i) of
+   weight e^{-xi^2}.
+
+Readings: the phase grid of the reconstruction covers |q| <= 2 m_max with
+4 m_max + 1 samples (the model norm carries m_i + m_j; the printed
+2 m_max + 1 assumes even-only harmonics); the draw's own phase, psi and lnD
+are not used; where the Gaussian in x lies outside the prior the rule is
+applied as printed (no fallback).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import numpy.polynomial.hermite as _herm
+
+from . import OraclePoint, lnL as _static_lnL
+
+PARAMS = ("ra", "dec", "psi", "incl", "phase", "lnD", "t")
+
+
+def _terms_on_grid(pt: OraclePoint, d_ref, ra, dec, incl, tc, phis, psis):
+    """K and R at x = 1 on the product grid [len(psis)][len(phis)]."""
+    P, F = np.meshgrid(psis, phis, indexing="ij")
+    n = P.size
+    th = {"ra": np.full(n, ra), "dec": np.full(n, dec), "psi": P.ravel(),
+          "incl": np.full(n, incl), "phase": F.ravel(), "lnD": np.full(n, math.log(d_ref)),
+          "t": np.full(n, tc)}
+    _, Td, Tq, _ = _static_lnL(pt, th, terms=True, threads=1)
+    return Td.reshape(P.shape), (2.0 * Tq).reshape(P.shape)
+
+
+def reconstruct(pt: OraclePoint, point: dict, ra, dec, incl, tc):
+    """ERAI step 1: the harmonic coefficients of K and R, as 2D DFTs over the
+    Nyquist grid: returns (cK, cR, m_max) with c[p, q] the coefficient of
+    e^{i (2 p psi + q phi)} stored at [p mod 5][q mod (4 m_max + 1)]."""
+    m_max = int(np.max(np.abs(point["em"])))
+    n_psi, n_phi = 5, 4 * m_max + 1
+    psis = np.pi * np.arange(n_psi) / n_psi
+    phis = 2 * np.pi * np.arange(n_phi) / n_phi
+    K, R = _terms_on_grid(pt, point["d_ref"], ra, dec, incl, tc, phis, psis)
+    return np.fft.fft2(K) / K.size, np.fft.fft2(R) / R.size, m_max
+
+
+def evaluate(c, psi, phi):
+    """The trigonometric polynomial with DFT coefficients c at (psi, phi)."""
+    n_psi, n_phi = c.shape
+    p = np.fft.fftfreq(n_psi, 1.0 / n_psi)
+    q = np.fft.fftfreq(n_phi, 1.0 / n_phi)
+    E = np.exp(1j * (2 * np.multiply.outer(np.asarray(psi), p)))          # [..., n_psi]
+    G = np.exp(1j * np.multiply.outer(np.asarray(phi), q))                # [..., n_phi]
+    return np.real(np.einsum("...p,pq,...q->...", E, c, G))
+
+
+def distance_gh(K, R, d_ref, d_min, d_max, n_gh):
+    """ln of the adaptive Gauss-Hermite distance integral (eq. ap:dgh)."""
+    xi, w = _herm.hermgauss(n_gh)
+    K = np.asarray(K, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    xs, sig = K / R, 1.0 / np.sqrt(R)
+    lo, hi = d_ref / d_max, d_ref / d_min
+    norm = 3.0 * d_ref ** 3 / (d_max ** 3 - d_min ** 3)
+    x = xs[..., None] + math.sqrt(2.0) * sig[..., None] * xi
+    px = np.where((x >= lo) & (x <= hi), norm * np.abs(x) ** -4.0, 0.0)
+    s = np.sum(w * px, axis=-1)
+    with np.errstate(divide="ignore"):
+        return K * K / (2.0 * R) + np.log(math.sqrt(2.0) * sig * s)
+
+
+def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
+               d_max: float):
+    """ln L_dir per draw (uses ra, dec, incl, t of each draw)."""
+    pt = OraclePoint(point)
+    th = {p: np.asarray(draws[p], dtype=np.float64) for p in PARAMS}
+    N = th["ra"].shape[0]
+    psis = np.pi * np.arange(n_psi) / n_psi
+    phis = 2 * np.pi * np.arange(n_phi) / n_phi
+    PS, PH = np.meshgrid(psis, phis, indexing="ij")
+    lnw = -math.log(n_phi * n_psi)   # trapezoid weights times the uniform priors
+    out = np.empty(N)
+    for i in range(N):
+        cK, cR, _ = reconstruct(pt, point, th["ra"][i], th["dec"][i], th["incl"][i], th["t"][i])
+        K = evaluate(cK, PS, PH)
+        R = evaluate(cR, PS, PH)
+        v = distance_gh(K, R, point["d_ref"], d_min, d_max, n_gh) + lnw
+        m = np.max(v)
+        out[i] = m + math.log(np.sum(np.exp(v - m))) if m > -np.inf else -np.inf
+    return out

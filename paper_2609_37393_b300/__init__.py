@@ -461,7 +461,14 @@ def _make_autograd():
             ctx.grad = None
             if need and recompute:
                 ctx.save_for_backward(*[x.detach() for x in theta])
-            if dist is not None:
+            if isinstance(point, CompPoint):
+                if dist is not None:
+                    raise ValueError("distance marginalisation is not built for CompPoint")
+                if need and not recompute:
+                    lnl, ctx.grad = rift_ile_comp_lnL_grad(point, draws)
+                else:
+                    lnl = rift_ile_comp_lnL(point, draws)
+            elif dist is not None:
                 if need and not recompute:
                     lnl, ctx.grad = rift_ile_lnL_dist(point, draws, dist, precision, grad=True)
                 else:
@@ -478,7 +485,9 @@ def _make_autograd():
             if g is None:
                 theta = ctx.saved_tensors
                 draws = Draws(dict(zip(PARAMS, theta)))
-                if ctx.dist is not None:
+                if isinstance(ctx.point, CompPoint):
+                    _, g = rift_ile_comp_lnL_grad(ctx.point, draws)
+                elif ctx.dist is not None:
                     _, g = rift_ile_lnL_dist(ctx.point, draws, ctx.dist, ctx.precision, grad=True)
                 else:
                     _, g = rift_ile_lnL_grad(ctx.point, draws, ctx.precision)
@@ -497,7 +506,9 @@ _LnLFunction = None
 def lnL(point: Point, ra, dec, psi, incl, phase, lnD, t, precision: int = FP32_MIXED,
         dist=None, recompute: bool = False):
     """Differentiable lnL[n] (float64) of CUDA tensors of draws (torch autograd);
-    dist = (x_nodes, lnw_nodes) marginalises the distance (eq. ap:dexp)."""
+    dist = (x_nodes, lnw_nodes) marginalises the distance (eq. ap:dexp).  A
+    CompPoint (composite-index response, Sec. III) evaluates in FP64 whatever
+    `precision` says."""
     global _LnLFunction
     if _LnLFunction is None:
         _LnLFunction = _make_autograd()

@@ -1,0 +1,144 @@
+"""Pins of the direct-marginalisation oracle (ERAI over (phi, psi), adaptive
+Gauss-Hermite in distance), against things other than itself:
+
+* the reconstructed harmonic model equals the static oracle's data and norm
+  terms at off-grid (phi, psi) (eq. ap:angleharm is exact at fixed time);
+* the Gauss-Hermite distance integral equals adaptive quadrature of the same
+  integrand over the prior range when the peak is inside it;
+* the marginal equals a brute-force quadrature (static oracle on a fine
+  (phi, psi) grid, distance by adaptive quadrature) on the two-detector
+  workload, and changes little when the angle grid is refined;
+* planted mistakes (a too-small phase grid, a lost sqrt(2), the wrong
+  distance prior power) each fail one of these.
+"""
+import importlib.util
+import math
+import os
+import sys
+import tempfile
+
+import numpy as np
+import pytest
+import scipy.integrate
+
+import oracle as O
+import oracle.direct as OD
+import workload as W
+
+FIX = W.config0(n_draws=8)
+
+
+def _truth_like(info, k=0):
+    tr = dict(info["truth"])
+    return tr
+
+
+def _general_point():
+    """The two-detector point with a generic symmetric V added, so that the
+    model norm carries phase harmonics up to 2 m_max (as a precessing source's
+    would); the reconstruction must still be exact."""
+    point, exact, info, draws, logw = FIX
+    p = dict(point)
+    rng = np.random.default_rng(3)
+    M = int(p["M"])
+    E = rng.normal(size=(p["K"], M, M)) + 1j * rng.normal(size=(p["K"], M, M))
+    p["V"] = np.asarray(p["V"]) + 0.1 * np.max(np.abs(p["U"])) * (E + np.transpose(E, (0, 2, 1)))
+    return p
+
+
+GENERAL = _general_point()
+
+
+def _battery(mod):
+    fails = []
+    _, exact, info, draws, logw = FIX
+    point = GENERAL
+    pt = O.OraclePoint(point)
+    tr = info["truth"]
+    cK, cR, _ = mod.reconstruct(pt, point, tr["ra"], tr["dec"], tr["incl"], tr["t"])
+    rng = np.random.default_rng(1)
+    ps, ph = rng.uniform(0, np.pi, 6), rng.uniform(0, 2 * np.pi, 6)
+    th = {"ra": np.full(6, tr["ra"]), "dec": np.full(6, tr["dec"]), "psi": ps,
+          "incl": np.full(6, tr["incl"]), "phase": ph, "lnD": np.full(6, math.log(point["d_ref"])),
+          "t": np.full(6, tr["t"])}
+    _, Td, Tq, _ = O.lnL(pt, th, terms=True, threads=1)
+    if (np.max(np.abs(mod.evaluate(cK, ps, ph) - Td)) > 1e-9 * np.max(np.abs(Td))
+            or np.max(np.abs(mod.evaluate(cR, ps, ph) - 2 * Tq)) > 1e-9 * np.max(np.abs(Tq))):
+        fails.append("reconstruction")
+    # Gauss-Hermite against quadrature: peak well inside [d_ref/d_max, d_ref/d_min]
+    d_ref, d_min, d_max = 100.0, 50.0, 200.0
+    for K, R in ((400.0, 400.0), (300.0, 350.0), (150.0, 125.0)):
+        lo, hi = d_ref / d_max, d_ref / d_min
+        norm = 3.0 * d_ref ** 3 / (d_max ** 3 - d_min ** 3)
+        peak = K * K / (2 * R)
+        val, _ = scipy.integrate.quad(lambda x: norm * x ** -4 * math.exp(K * x - 0.5 * R * x * x - peak),
+                                      lo, hi, epsabs=0, epsrel=1e-13, limit=200)
+        got = mod.distance_gh(np.array(K), np.array(R), d_ref, d_min, d_max, 40)
+        if abs(float(got) - (peak + math.log(val))) > 1e-7:
+            fails.append("gauss_hermite")
+            break
+    return fails
+
+
+def test_unmodified_passes_battery():
+    assert _battery(OD) == []
+
+
+def test_marginal_against_brute_force():
+    point, exact, info, draws, logw = FIX
+    pt = O.OraclePoint(point)
+    tr = info["truth"]
+    d = {p: np.array([tr[p]]) for p in W.PARAMS}
+    d["ra"] = d["ra"] + 0.01
+    n_phi, n_psi = 48, 24
+    got = OD.lnL_direct(point, d, n_phi, n_psi, 40, 50.0, 200.0)[0]
+    # the angle grid resolves the peak (width ~1/(2 rho) in phase at SNR 20)
+    coarse = OD.lnL_direct(point, d, 256, 128, 40, 50.0, 200.0)[0]
+    finer = OD.lnL_direct(point, d, 512, 256, 40, 50.0, 200.0)[0]
+    # brute force: static oracle on the grid, distance by adaptive quadrature
+    psis = np.pi * np.arange(n_psi) / n_psi
+    phis = 2 * np.pi * np.arange(n_phi) / n_phi
+    K, R = OD._terms_on_grid(pt, point["d_ref"], d["ra"][0], d["dec"][0], d["incl"][0],
+                             d["t"][0], phis, psis)
+    lo, hi = point["d_ref"] / 200.0, point["d_ref"] / 50.0
+    norm = 3.0 * point["d_ref"] ** 3 / (200.0 ** 3 - 50.0 ** 3)
+    vals = []
+    ref = float(np.max(K * K / (2 * R)))
+    for k_, r_ in zip(K.ravel(), R.ravel()):
+        v, _ = scipy.integrate.quad(lambda x: norm * x ** -4 * math.exp(k_ * x - 0.5 * r_ * x * x - ref),
+                                    lo, hi, epsabs=0, epsrel=1e-12, limit=200)
+        vals.append(v)
+    brute = ref + math.log(np.mean(vals))
+    assert abs(got - brute) <= 1e-6, (got, brute)
+    assert abs(finer - coarse) <= 1e-6, (finer, coarse)
+
+
+SRC = os.path.join(os.path.dirname(OD.__file__), "direct.py")
+MUTATIONS = {
+    "nyquist_too_small": ("n_psi, n_phi = 5, 4 * m_max + 1", "n_psi, n_phi = 5, 2 * m_max + 1"),
+    "gh_no_sqrt2": ("x = xs[..., None] + math.sqrt(2.0) * sig[..., None] * xi",
+                    "x = xs[..., None] + sig[..., None] * xi"),
+    "prior_power": ("norm * np.abs(x) ** -4.0", "norm * np.abs(x) ** -2.0"),
+    "norm_scale": ("np.fft.fft2(R) / R.size", "np.fft.fft2(R) / K.shape[0]"),
+}
+
+
+def _load(text, tag):
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, f"direct_{tag}.py")
+    with open(path, "w") as f:
+        f.write(text)
+    spec = importlib.util.spec_from_file_location(f"oracle._direct_{tag}", path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    old, new = MUTATIONS[name]
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1
+    assert _battery(_load(text.replace(old, new), name)), name
