@@ -16,7 +16,7 @@ path, the ALU roofline of the kernel, sampled clocks and the FP64 CPU oracle
 as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ile|batch|event|diff|sweep|sampler|response|precompute]
+                  [--workload ile|batch|event|diff|sweep|sampler|response|precompute|direct]
 
 The default workload (ile) is the headline line.  The others are extra
 measurements:
@@ -33,7 +33,8 @@ measurements:
          and replayed from a captured CUDA graph;
   response  the composite-index response (Earth rotation Paths A and B,
          finite arms Path D) on the 3G network: fused FP64 lnZ steps;
-  precompute  the GPU precompute of Q, U, V for the 3G point (cuFFT).
+  precompute  the GPU precompute of Q, U, V for the 3G point (cuFFT);
+  direct  phase, polarisation and distance marginalised inside the kernel.
 """
 from __future__ import annotations
 
@@ -643,6 +644,47 @@ def run_precompute(args):
         "max_rel_err_vs_direct_sum": err, "clocks": clocks.summary()}), flush=True)
 
 
+def run_direct(args):
+    """Direct marginalisation over phase, polarisation and distance inside the
+    likelihood (ERAI on a 128 x 64 grid, 16-node adaptive Gauss-Hermite) on
+    the 3G network at SNR 30, 2^16 draws of (ra, dec, incl, t)."""
+    import torch
+    import paper_2609_37393_b300 as R
+    import workload as W
+    import oracle.direct as OD
+    torch.cuda.set_device(0)
+    n = 1 << 16
+    point, exact, info, draws, logw = W.config_3g(1, 4, 30.0, 0.02, n)
+    pt = R.Point(point)
+    d = R.Draws(draws, logw)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    rule = (128, 64, 16, 50.0, 200.0)
+    stream = torch.cuda.current_stream()
+    with ClockSampler(0) as clocks:
+        for _ in range(args.warmup):
+            R.rift_ile_lnL_direct(pt, d, *rule, out=out)
+        ms = timed_events(torch, lambda: R.rift_ile_lnL_direct(pt, d, *rule, out=out),
+                          max(3, min(args.steps, 10)), stream)
+    got = out.cpu().numpy()
+    ns = 16
+    sub = {p: np.asarray(draws[p])[:ns] for p in W.PARAMS}
+    t0 = time.perf_counter()
+    ref = OD.lnL_direct(point, sub, *rule)
+    cpu_s = time.perf_counter() - t0
+    fin = np.isfinite(ref)
+    err = float(np.max(np.abs(got[:ns][fin] - ref[fin]) / np.maximum(1.0, np.abs(ref[fin]))))
+    print(json.dumps({
+        "metric": "directly marginalised lnL draws/s (phase, polarisation, distance in-kernel)",
+        "workload": "direct", "value": n / (ms * 1e-3), "unit": "draws/s", "n_gpus": 1,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3G network K=4, M=10, SNR 30, grid 128 x 64 (phase x "
+                   "polarisation), 16 Gauss-Hermite nodes in x, D in [50, 200]", "draws": n},
+        "ms_per_call": ms, "grid_nodes_per_s": n * rule[0] * rule[1] / (ms * 1e-3),
+        "cpu_baseline": {"value": ns / cpu_s, "unit": "draws/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {ns} draws, numpy reconstruction and quadrature"},
+        "max_rel_err_vs_oracle": err, "clocks": clocks.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -652,7 +694,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="ile",
                     choices=["ile", "batch", "event", "diff", "sweep", "sampler", "response",
-                             "precompute"])
+                             "precompute", "direct"])
     ap.add_argument("--draws", type=int, default=1 << 22, help="draws of --workload response")
     ap.add_argument("--points", type=int, default=512)
     ap.add_argument("--chunks", type=int, default=16)
@@ -683,6 +725,9 @@ def main():
         return
     if args.workload == "precompute":
         run_precompute(args)
+        return
+    if args.workload == "direct":
+        run_direct(args)
         return
 
     import torch

@@ -1,0 +1,56 @@
+/* rift_ile_direct.h -- direct marginalisation inside the likelihood
+ * ("Scaling RIFT 1", arXiv 2609.37393, eq. direct_marginalization, App. F),
+ * C ABI, FP64.
+ *
+ * For each draw of the sampled coordinates (ra, dec, incl, t_c) the library
+ * returns
+ *
+ *   ln L_dir = ln int dphi dpsi dx p(phi) p(psi) p_x(x) exp[lnL(phi, psi, x)]
+ *
+ * with lnL(x) = K x - R x^2 / 2 (eq. ap:dexp), K and R the data term and the
+ * model norm of eq. def:lnL:Decomposed at x = d_ref / D = 1.  At the draw's
+ * arrival time K and R are finite trigonometric polynomials in (phi, psi)
+ * (eq. ap:angleharm): their harmonic coefficients are formed per draw from the
+ * factored likelihood (F_k(psi) = e^{2 i psi} F_k(0), Y_lm(phi) = e^{i m phi}
+ * Y_lm(0)), which is the exact reconstruction ERAI performs, and the
+ * exponential is integrated on an n_phi x n_psi periodic trapezoid grid over
+ * [0, 2 pi) x [0, pi) (uniform priors).  At each grid point the distance is
+ * integrated by adaptive Gauss-Hermite (eq. ap:dgh) about x* = K/R with width
+ * R^(-1/2) (eq. ap:dpeak), n_gh nodes, prior uniform in volume on
+ * [d_min, d_max]: p_x(x) = 3 d_ref^3 x^-4 / (d_max^3 - d_min^3) on
+ * [d_ref/d_max, d_ref/d_min].  Grid points whose largest possible
+ * contribution is more than 60 nat below the best point's are skipped.
+ *
+ * The draw's psi, phase and lnD are ignored.  A draw whose distance nodes all
+ * fall outside the prior gets -inf.  Ownership and errors as in rift_ile.h;
+ * asynchronous on `stream`.  Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA.
+ */
+#ifndef RIFT_ILE_DIRECT_H
+#define RIFT_ILE_DIRECT_H
+#include "rift_ile.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIFT_ILE_MAX_GH 64
+
+typedef struct {
+  int32_t n_phi;  /* phase nodes over [0, 2 pi), >= 1; spacing should resolve the peak */
+  int32_t n_psi;  /* polarisation nodes over [0, pi), >= 1; n_phi n_psi <= 2^26 */
+  int32_t n_gh;   /* Gauss-Hermite nodes in x, 1..RIFT_ILE_MAX_GH */
+  double d_min;   /* distance prior range, same unit as d_ref */
+  double d_max;
+} rift_ile_direct_rule;
+
+/* ln L_dir per draw into DEVICE out[n] (double). */
+int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draws* draws,
+                        const rift_ile_direct_rule* rule, double* out, void* stream);
+
+/* The Gauss-Hermite rule the kernel uses (weight e^{-x^2}): HOST x[n], w[n]. */
+int rift_ile_gauss_hermite(int32_t n, double* x, double* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -777,3 +777,37 @@ def rift_ile_comp_lnL_grad(cp: CompPoint, draws, lnl_out=None, grad_out=None, st
     _check(_lib.rift_ile_comp_lnL_grad(cp.handle, d.ref, lnl_out.data_ptr() if d.n else None,
                                        grad_out.data_ptr() if d.n else None, _stream(stream)))
     return lnl_out, grad_out
+
+
+# ------------------------------------------------- direct marginalisation
+
+class _DirectRule(ctypes.Structure):
+    _fields_ = [("n_phi", ctypes.c_int32), ("n_psi", ctypes.c_int32), ("n_gh", ctypes.c_int32),
+                ("d_min", ctypes.c_double), ("d_max", ctypes.c_double)]
+
+
+_lib.rift_ile_lnL_direct.argtypes = [_P, _P, _P, _P, _P]
+_lib.rift_ile_gauss_hermite.argtypes = [ctypes.c_int32, _P, _P]
+
+
+def rift_ile_gauss_hermite(n: int):
+    """The Gauss-Hermite rule (weight e^{-x^2}) the direct kernel uses: (x, w)."""
+    x = np.empty(n)
+    w = np.empty(n)
+    _check(_lib.rift_ile_gauss_hermite(n, x.ctypes.data, w.ctypes.data))
+    return x, w
+
+
+def rift_ile_lnL_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
+                        d_max: float, out=None, stream=None):
+    """ln L_dir per draw (float64 CUDA tensor): phase, polarisation and
+    distance integrated inside the likelihood (ERAI on an n_phi x n_psi grid,
+    adaptive Gauss-Hermite in x); uses each draw's ra, dec, incl and t."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(d.n, dtype=torch.float64, device=point.device)
+    r = _DirectRule(int(n_phi), int(n_psi), int(n_gh), float(d_min), float(d_max))
+    _check(_lib.rift_ile_lnL_direct(point.handle, d.ref, ctypes.byref(r),
+                                    out.data_ptr() if d.n else None, _stream(stream)))
+    return out

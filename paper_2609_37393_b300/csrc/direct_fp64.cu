@@ -1,0 +1,443 @@
+// Direct marginalisation over (phi_ref, psi) and distance inside the
+// likelihood (eq. direct_marginalization; ERAI of App. F.1, adaptive
+// Gauss-Hermite of eq. ap:dgh), FP64, one warp per draw.
+//
+// Per draw (lane 0): sky basis, F_k(0), Y_lm(phi = 0), Q_k,lm(t_k) by the
+// table cubic, then the harmonic coefficients of
+//   K(phi, psi) = Re[e^{-2 i psi} sum_m e^{-i m phi} c_m],
+//     c_m = sum_k conj(F_k(0)) sum_{lm: m} conj(Y_lm(0)) Q_k,lm(t_k),
+//   2R(phi, psi) = sum_d alpha_d e^{i d phi} + Re[e^{4 i psi} sum_s beta_s e^{i s phi}],
+//     alpha_d = sum_{m_j - m_i = d} conj(Y_i) Y_j sum_k |F_k|^2 U_k,ij,
+//     beta_s = sum_{m_i + m_j = s} Y_i Y_j sum_k F_k^2 V_k,ij,
+// (F_k(psi) = e^{2 i psi} F_k(0), Y(phi) = e^{i m phi} Y(0)), kept in shared
+// memory.  The lanes then share the n_phi phase columns: per column the three
+// harmonic sums once, per polarisation node K and R in a few operations, and
+// at each node the Gauss-Hermite distance integral and an online log-sum-exp.
+// A first pass finds the node with the largest K^2/(2R) and evaluates it in
+// full (v0); the second pass skips nodes whose upper bound
+// K^2/(2R) + ln(sqrt(2 pi) sigma_x max p_x) is below v0 - 60.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/rift_ile_direct.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rift {
+namespace {
+
+constexpr int kDirWarps = 4;
+constexpr int kHm = 2 * kMaxEll + 1;        // data harmonics m = -8..8
+constexpr int kHn = 4 * kMaxEll + 1;        // norm harmonics -16..16
+constexpr double kSkipNat = 60.0;
+
+struct DirectParams {
+  int n_phi, n_psi, n_gh;
+  double lo, hi;          // prior range of x
+  double lnnorm;          // ln of 3 d_ref^3 / (d_max^3 - d_min^3)
+  double lnw;             // -ln(n_phi n_psi)
+  double ln_ub;           // ln(sqrt(2 pi) norm lo^-4), the prefactor bound over sigma_x
+  double xi[RIFT_ILE_MAX_GH], w[RIFT_ILE_MAX_GH];
+};
+
+struct DirCoef {
+  double2 c[kHm];
+  double2 al[kHn];
+  double2 be[kHn];
+};
+
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// The harmonic coefficients of one draw (one thread).
+template <int MM>
+__device__ void direct_coeffs(const PointParams& P, const DrawsParams& dp, long long i,
+                              DirCoef& out) {
+  const double ra = load_param_d(dp, 0, i), dec = load_param_d(dp, 1, i);
+  const double incl = load_param_d(dp, 3, i), tc = load_param_d(dp, 6, i);
+  const int K = P.K, M = P.M;
+  double sl, cl, sd, cd;
+  sincos(ra - P.gmst, &sl, &cl);
+  sincos(dec, &sd, &cd);
+  const double s[3] = {cd * cl, cd * sl, sd};
+  const double e1[3] = {-sl, cl, 0.0};
+  const double e2[3] = {-sd * cl, -sd * sl, cd};
+  double yr[MM], yi[MM];
+  {
+    double sh, ch;
+    sincos(0.5 * incl, &sh, &ch);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      yr[m] = yi[m] = 0.0;
+      if (m < M) sylm_eval<double>(P, m, ch, sh, 1.0, 0.0, P.ycoef[m], yr[m], yi[m]);
+    }
+  }
+  for (int h = 0; h < kHm; ++h) out.c[h] = make_double2(0.0, 0.0);
+  for (int h = 0; h < kHn; ++h) out.al[h] = out.be[h] = make_double2(0.0, 0.0);
+  for (int k = 0; k < K; ++k) {
+    const double* D = P.resp[k];
+    const double Fr = quad3(D, e1, e1) - quad3(D, e2, e2), Fi = -2.0 * quad3(D, e1, e2);
+    const double tk = tc - (P.pos[k][0] * s[0] + P.pos[k][1] * s[1] + P.pos[k][2] * s[2]);
+    const double u = (tk - P.t0[k]) * P.inv_dt;
+    // G_i = Q_k,i(t_k) by the cubic; taps outside the table read zero
+    double gr[MM], gi[MM];
+#pragma unroll
+    for (int m = 0; m < MM; ++m) gr[m] = gi[m] = 0.0;
+    if (!isfinite(u)) {
+#pragma unroll
+      for (int m = 0; m < MM; ++m) gr[m] = CUDART_NAN;
+    } else {
+      const double jf = floor(u);
+      double w[4], dw[4];
+      lagrange4_d(u - jf, w, dw);
+      const long long j0 = (long long)jf - 1;
+      for (int tap = 0; tap < 4; ++tap) {
+        const long long j = j0 + tap;
+        if (j < 0 || j >= P.n) continue;
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+          if (m < M) {
+            double qr, qi;
+            if (P.q_c128) {
+              const double2 q = __ldg((const double2*)P.Q + ((long long)k * P.n + j) * M + m);
+              qr = q.x;
+              qi = q.y;
+            } else {
+              const float2 q = __ldg((const float2*)P.Q + ((long long)k * P.n + j) * M + m);
+              qr = q.x;
+              qi = q.y;
+            }
+            gr[m] = fma(w[tap], qr, gr[m]);
+            gi[m] = fma(w[tap], qi, gi[m]);
+          }
+        }
+      }
+    }
+    // c_m += conj(F) conj(Y_i) G_i
+    const double2 cF = make_double2(Fr, -Fi);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      if (m < M) {
+        const double2 t = cmul_d(cF, cmul_d(make_double2(yr[m], -yi[m]), make_double2(gr[m], gi[m])));
+        double2& c = out.c[P.em[m] + kMaxEll];
+        c.x += t.x;
+        c.y += t.y;
+      }
+    }
+    // |F|^2 and F^2 weight this detector's U and V
+    const double F2 = Fr * Fr + Fi * Fi;
+    const double2 FF = make_double2(Fr * Fr - Fi * Fi, 2.0 * Fr * Fi);
+    for (int a = 0; a < M; ++a) {
+      for (int b = 0; b < M; ++b) {
+        const double2 uu = P.U[((size_t)k * M + a) * M + b], vv = P.V[((size_t)k * M + a) * M + b];
+        const double2 pu = cmul_d(make_double2(yr[a], -yi[a]), make_double2(yr[b], yi[b]));
+        const double2 tu = cmul_d(pu, uu);
+        double2& al = out.al[P.em[b] - P.em[a] + 2 * kMaxEll];
+        al.x += F2 * tu.x;
+        al.y += F2 * tu.y;
+        const double2 tv = cmul_d(FF, cmul_d(cmul_d(make_double2(yr[a], yi[a]), make_double2(yr[b], yi[b])), vv));
+        double2& be = out.be[P.em[a] + P.em[b] + 2 * kMaxEll];
+        be.x += tv.x;
+        be.y += tv.y;
+      }
+    }
+  }
+}
+
+// Per phase column: D = sum_m c_m e^{-i m phi}, A = Re sum_d al_d e^{i d phi},
+// B = sum_s be_s e^{i s phi}.
+__device__ void direct_column(const DirCoef& C, double phi_frac, double2& D, double& A,
+                              double2& B) {
+  double s1, c1;
+  sincospi(2.0 * phi_frac, &s1, &c1);
+  double2 pw[2 * kMaxEll + 1];  // e^{i k phi}, k = 0..16
+  pw[0] = make_double2(1.0, 0.0);
+  pw[1] = make_double2(c1, s1);
+  for (int k = 2; k <= 2 * kMaxEll; ++k) pw[k] = cmul_d(pw[k - 1], pw[1]);
+  D = make_double2(0.0, 0.0);
+  for (int m = -kMaxEll; m <= kMaxEll; ++m) {
+    const double2 e = m >= 0 ? make_double2(pw[m].x, -pw[m].y) : pw[-m];  // e^{-i m phi}
+    const double2 t = cmul_d(C.c[m + kMaxEll], e);
+    D.x += t.x;
+    D.y += t.y;
+  }
+  A = 0.0;
+  B = make_double2(0.0, 0.0);
+  for (int d = -2 * kMaxEll; d <= 2 * kMaxEll; ++d) {
+    const double2 e = d >= 0 ? pw[d] : make_double2(pw[-d].x, -pw[-d].y);  // e^{i d phi}
+    const double2 a = C.al[d + 2 * kMaxEll], b = C.be[d + 2 * kMaxEll];
+    A += a.x * e.x - a.y * e.y;
+    const double2 t = cmul_d(b, e);
+    B.x += t.x;
+    B.y += t.y;
+  }
+}
+
+// K, R at one polarisation node from the column sums; e2 = e^{2 i psi}.
+__device__ __forceinline__ void direct_node(const double2& D, double A, const double2& B,
+                                            double2 e2, double& K, double& R) {
+  K = e2.x * D.x + e2.y * D.y;  // Re(e^{-2 i psi} D)
+  const double2 e4 = cmul_d(e2, e2);
+  R = 0.5 * (A + (e4.x * B.x - e4.y * B.y));
+}
+
+// ln of the Gauss-Hermite distance integral at one node (eq. ap:dgh).
+__device__ double direct_distance(const DirectParams& Q, double K, double R) {
+  if (!(R > 0.0)) return -CUDART_INF;
+  const double sig = rsqrt(R), xs = K / R;
+  const double h = 1.4142135623730951 * sig;
+  double s = 0.0;
+  for (int j = 0; j < Q.n_gh; ++j) {
+    const double x = fma(h, Q.xi[j], xs);
+    if (x >= Q.lo && x <= Q.hi) {
+      const double r = 1.0 / x, r2 = r * r;
+      s = fma(Q.w[j], r2 * r2, s);
+    }
+  }
+  if (!(s > 0.0)) return -CUDART_INF;
+  return K * K / (2.0 * R) + log(h * s) + Q.lnnorm;
+}
+
+__device__ __forceinline__ void lse_add(double& m, double& s, double v) {
+  if (!(v > -CUDART_INF)) return;
+  if (v > m) {
+    s = fma(s, exp(m - v), 1.0);
+    m = v;
+  } else {
+    s += exp(v - m);
+  }
+}
+
+template <int MM>
+__global__ void __launch_bounds__(32 * kDirWarps) direct_kernel(const PointParams* __restrict__ gP,
+                                                                DrawsParams dp,
+                                                                const __grid_constant__ DirectParams Q,
+                                                                double* __restrict__ out) {
+  __shared__ PointParams P;
+  __shared__ DirCoef coef[kDirWarps];
+  stage_point(P, gP);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  DirCoef& C = coef[wid];
+  const long long stride = (long long)gridDim.x * kDirWarps;
+  for (long long i = blockIdx.x * (long long)kDirWarps + wid; i < dp.n; i += stride) {
+    if (lane == 0) direct_coeffs<MM>(P, dp, i, C);
+    __syncwarp();
+    // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
+    double best = -CUDART_INF;
+    long long best_idx = (long long)Q.n_phi * Q.n_psi;
+    for (int a = lane; a < Q.n_phi; a += 32) {
+      double2 D, B;
+      double A;
+      direct_column(C, (double)a / Q.n_phi, D, A, B);
+      for (int b = 0; b < Q.n_psi; ++b) {
+        double s2, c2;
+        sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+        double K, R;
+        direct_node(D, A, B, make_double2(c2, s2), K, R);
+        const double h = (R > 0.0) ? K * K / (2.0 * R) : -CUDART_INF;
+        const long long idx = (long long)a * Q.n_psi + b;
+        if (h > best || (h == best && idx < best_idx)) {
+          best = h;
+          best_idx = idx;
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
+      if (ob > best || (ob == best && oi < best_idx)) {
+        best = ob;
+        best_idx = oi;
+      }
+    }
+    double v0 = -CUDART_INF;
+    if (best_idx < (long long)Q.n_phi * Q.n_psi) {
+      const int a = (int)(best_idx / Q.n_psi), b = (int)(best_idx % Q.n_psi);
+      double2 D, B;
+      double A;
+      direct_column(C, (double)a / Q.n_phi, D, A, B);
+      double s2, c2;
+      sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+      double K, R;
+      direct_node(D, A, B, make_double2(c2, s2), K, R);
+      v0 = direct_distance(Q, K, R);
+    }
+    const double cut = v0 - kSkipNat;
+    // pass 2: the log-sum-exp over the nodes that can matter
+    double m = -CUDART_INF, s = 0.0;
+    bool nan_seen = false;
+    for (int a = lane; a < Q.n_phi; a += 32) {
+      double2 D, B;
+      double A;
+      direct_column(C, (double)a / Q.n_phi, D, A, B);
+      for (int b = 0; b < Q.n_psi; ++b) {
+        double s2, c2;
+        sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+        double K, R;
+        direct_node(D, A, B, make_double2(c2, s2), K, R);
+        if (isnan(K) || isnan(R)) {
+          nan_seen = true;
+          continue;
+        }
+        if (!(R > 0.0)) continue;
+        const double ub = K * K / (2.0 * R) - 0.5 * log(R) + Q.ln_ub;
+        if (ub < cut) continue;
+        lse_add(m, s, direct_distance(Q, K, R));
+      }
+    }
+    nan_seen = __any_sync(0xffffffffu, nan_seen);
+    for (int off = 16; off > 0; off >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, m, off);
+      const double os = __shfl_xor_sync(0xffffffffu, s, off);
+      if (om > m) {
+        s = fma(s, exp(m - om), os);
+        m = om;
+      } else if (om > -CUDART_INF) {
+        s = fma(os, exp(om - m), s);
+      }
+    }
+    if (lane == 0) out[i] = nan_seen ? CUDART_NAN : (m > -CUDART_INF ? m + log(s) + Q.lnw : -CUDART_INF);
+    __syncwarp();
+  }
+}
+
+template <int MM>
+cudaError_t launch_direct_mm(const PointParams* dP, const DrawsParams& dp, const DirectParams& Q,
+                             double* out, cudaStream_t st) {
+  const int threads = 32 * kDirWarps;
+  const long long need = (dp.n + kDirWarps - 1) / kDirWarps;
+  int blocks = grid_for(direct_kernel<MM>, threads, 0);
+  if (need < blocks) blocks = (int)(need > 0 ? need : 1);
+  direct_kernel<MM><<<blocks, threads, 0, st>>>(dP, dp, Q, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direct(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
+                          const DirectParams& Q, double* out, cudaStream_t st) {
+  const int M = hp.M;
+  if (M <= 2) return launch_direct_mm<2>(dP, dp, Q, out, st);
+  if (M <= 4) return launch_direct_mm<4>(dP, dp, Q, out, st);
+  if (M <= 6) return launch_direct_mm<6>(dP, dp, Q, out, st);
+  if (M <= 8) return launch_direct_mm<8>(dP, dp, Q, out, st);
+  if (M <= 10) return launch_direct_mm<10>(dP, dp, Q, out, st);
+  if (M <= 12) return launch_direct_mm<12>(dP, dp, Q, out, st);
+  return launch_direct_mm<16>(dP, dp, Q, out, st);
+}
+
+// Orthonormal Hermite polynomials p_0..p_n at x (weight e^{-x^2}):
+// p_0 = pi^(-1/4), p_(k+1) = sqrt(2/(k+1)) x p_k - sqrt(k/(k+1)) p_(k-1).
+void hermite_orthonormal(int n, double x, double* p) {
+  p[0] = std::pow(M_PI, -0.25);
+  if (n >= 1) p[1] = std::sqrt(2.0) * x * p[0];
+  for (int k = 1; k < n; ++k)
+    p[k + 1] = std::sqrt(2.0 / (k + 1)) * x * p[k] - std::sqrt((double)k / (k + 1)) * p[k - 1];
+}
+
+// Gauss-Hermite nodes as the zeros of p_n (bracketed by a scan of
+// (-sqrt(2n+1)-1, sqrt(2n+1)+1), refined by bisection) and the Christoffel
+// weights w_i = 1 / sum_{k<n} p_k(x_i)^2.
+int gauss_hermite(int n, double* x, double* w) {
+  std::vector<double> p(n + 1);
+  const double lim = std::sqrt(2.0 * n + 1.0) + 1.0;
+  const int steps = 400 * n + 400;
+  int found = 0;
+  double xa = -lim;
+  hermite_orthonormal(n, xa, p.data());
+  double fa = p[n];
+  for (int s = 1; s <= steps && found < n; ++s) {
+    const double xb = -lim + 2.0 * lim * s / steps;
+    hermite_orthonormal(n, xb, p.data());
+    const double fb = p[n];
+    if (fb == 0.0 || (fa < 0.0) != (fb < 0.0)) {
+      double lo = xa, hi = xb, flo = fa;
+      for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        hermite_orthonormal(n, mid, p.data());
+        if ((p[n] < 0.0) == (flo < 0.0)) {
+          lo = mid;
+          flo = p[n];
+        } else {
+          hi = mid;
+        }
+      }
+      x[found++] = 0.5 * (lo + hi);
+    }
+    xa = xb;
+    fa = fb;
+  }
+  if (found != n) return RIFT_ILE_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    hermite_orthonormal(n, x[i], p.data());
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += p[k] * p[k];
+    w[i] = 1.0 / s;
+  }
+  return RIFT_ILE_OK;
+}
+
+}  // namespace
+}  // namespace rift
+
+using namespace rift;
+
+extern "C" int rift_ile_gauss_hermite(int32_t n, double* x, double* w) {
+  if (n < 1 || n > RIFT_ILE_MAX_GH || !x || !w) {
+    rift_ile_set_error("rift_ile_gauss_hermite: n=%d outside 1..%d or NULL output", n, RIFT_ILE_MAX_GH);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const int rc = gauss_hermite(n, x, w);
+  if (rc) rift_ile_set_error("rift_ile_gauss_hermite: root bracketing failed for n=%d", n);
+  return rc;
+}
+
+extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draws* draws,
+                                   const rift_ile_direct_rule* rule, double* out, void* stream) {
+  if (!pt || !rule) {
+    rift_ile_set_error("rift_ile_lnL_direct: point or rule is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  int rc = validate_draws(draws);
+  if (rc) return rc;
+  if (rule->n_phi < 1 || rule->n_psi < 1 || (long long)rule->n_phi * rule->n_psi > (1LL << 26) ||
+      rule->n_gh < 1 || rule->n_gh > RIFT_ILE_MAX_GH) {
+    rift_ile_set_error("rift_ile_lnL_direct: grid %d x %d or n_gh=%d out of range", rule->n_phi,
+                       rule->n_psi, rule->n_gh);
+    return RIFT_ILE_ERR_SHAPE;
+  }
+  if (!(rule->d_min > 0.0) || !(rule->d_max > rule->d_min) || !std::isfinite(rule->d_max)) {
+    rift_ile_set_error("rift_ile_lnL_direct: need 0 < d_min < d_max finite");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (draws->n == 0) return RIFT_ILE_OK;
+  if (!out) {
+    rift_ile_set_error("rift_ile_lnL_direct: out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const PointParams& hp = pt->host;
+  DirectParams Q;
+  std::memset(&Q, 0, sizeof(Q));
+  Q.n_phi = rule->n_phi;
+  Q.n_psi = rule->n_psi;
+  Q.n_gh = rule->n_gh;
+  const double dref = hp.d_ref;
+  Q.lo = dref / rule->d_max;
+  Q.hi = dref / rule->d_min;
+  const double norm = 3.0 * dref * dref * dref /
+                      (rule->d_max * rule->d_max * rule->d_max - rule->d_min * rule->d_min * rule->d_min);
+  Q.lnnorm = std::log(norm);
+  Q.lnw = -std::log((double)rule->n_phi * rule->n_psi);
+  Q.ln_ub = std::log(std::sqrt(2.0 * M_PI) * norm) - 4.0 * std::log(Q.lo);
+  if ((rc = gauss_hermite(Q.n_gh, Q.xi, Q.w))) {
+    rift_ile_set_error("rift_ile_lnL_direct: Gauss-Hermite rule failed for n=%d", Q.n_gh);
+    return rc;
+  }
+  return check_cuda(launch_direct(hp, pt->dev, draws_params(draws), Q, out, (cudaStream_t)stream),
+                    "rift_ile_lnL_direct launch");
+}

@@ -10,7 +10,8 @@ import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", h)
-           for h in ("rift_ile.h", "rift_ile_response.h", "rift_ile_precompute.h")]
+           for h in ("rift_ile.h", "rift_ile_response.h", "rift_ile_precompute.h",
+                     "rift_ile_direct.h")]
 PKG = os.path.join(ROOT, "paper_2609_37393_b300")
 
 
@@ -73,3 +74,20 @@ def test_product_never_uses_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "rift_oracle" not in text, f
+
+
+def test_gauss_hermite_rule_is_the_textbook_one():
+    """The host-side Gauss-Hermite rule of the direct kernel equals numpy's
+    (Golub-Welsch) to rounding for every supported size."""
+    import numpy as np
+    import numpy.polynomial.hermite as H
+    lib = library()
+    lib.rift_ile_gauss_hermite.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    for n in (1, 2, 5, 16, 40, 64):
+        x = np.empty(n)
+        w = np.empty(n)
+        assert lib.rift_ile_gauss_hermite(n, x.ctypes.data, w.ctypes.data) == 0
+        xr, wr = H.hermgauss(n)
+        assert np.max(np.abs(x - xr)) <= 1e-12 * max(1.0, np.max(np.abs(xr)))
+        assert np.max(np.abs(w - wr) / wr) <= 1e-9
+    assert lib.rift_ile_gauss_hermite(65, x.ctypes.data, w.ctypes.data) != 0
