@@ -519,12 +519,23 @@ def run_sampler(args):
                       "rows": rows}), flush=True)
 
 
-def comp_fp64_fmas(K: int, A: int) -> int:
+def comp_fp64_fmas(point: dict, na: int) -> int:
     """Declared FP64 FMAs per draw of the composite-index likelihood: per
-    detector the quadratic form of eq. slowrot:lnL:Decomposed in the 2A real
-    coordinates (z^T G z over the upper triangle, 2A^2 + A) and the four-tap
-    data contraction Re sum conj(c) Q (2 FMAs per complex term, 8A)."""
-    return K * (2 * A * A + A + 8 * A)
+    detector class (detectors with identical U, V) and block pair a <= b of
+    response indices the four quadratic forms of y = (Re Y, Im Y) and Jy with
+    the folded real form of eq. slowrot:lnL:Decomposed (two 2M x 2M
+    matrix-vector products, 8 M^2); per detector 4 FMAs per block pair to
+    weight them with the coefficients and the four-tap data contraction
+    Re sum conj(c) Q (2 FMAs per complex term and tap, 8A)."""
+    K, M = int(point["K"]), int(point["M"])
+    A = na * M
+    nblk = na * (na + 1) // 2
+    U, V = np.asarray(point["U"]), np.asarray(point["V"])
+    reps = []
+    for k in range(K):
+        if not any(np.array_equal(U[k], U[r]) and np.array_equal(V[k], V[r]) for r in reps):
+            reps.append(k)
+    return len(reps) * nblk * 8 * M * M + K * (4 * nblk + 8 * A)
 
 
 def run_response(args):
@@ -559,7 +570,7 @@ def run_response(args):
             row = {"response": name, "kind": kind, "p_max": p_max, "composite_dim": cp.A,
                    "draws_per_s": n / (ms * 1e-3), "ms_per_step": ms, "lnZ": z[0],
                    "fwd_bwd_draws_per_s": n / (ms_g * 1e-3),
-                   "fp64_fma_per_draw": comp_fp64_fmas(cp.K, cp.A)}
+                   "fp64_fma_per_draw": comp_fp64_fmas(point, cp.na)}
             rows.append(row)
             if head is None:
                 head = row

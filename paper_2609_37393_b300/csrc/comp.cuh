@@ -14,13 +14,15 @@ constexpr int kCompThreads = 128;
 
 struct CompParams {
   int K, M, kind, p_max, na, A, n, nblk;
+  int ncls;                 // detector classes: identical (U_k, V_k) share one G
+  int cls_of[kMaxDet];
   double omega, gmst, d_ref, dt, inv_dt;
   double t0[kMaxDet];
   double pos[kMaxDet][3];
   double resp[kMaxDet][6];
   double armx[kMaxDet][3], army[kMaxDet][3];
   const double2* Q;  // [K][n][A]
-  const double* G;   // [K][nblk][4][M][M]: sub-blocks (Re,Re), (Re,Im), (Im,Re), (Im,Im)
+  const double* G;   // [ncls][nblk][4][M][M]: sub-blocks (Re,Re), (Re,Im), (Im,Re), (Im,Im)
 };
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {

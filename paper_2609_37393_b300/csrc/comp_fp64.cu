@@ -40,6 +40,8 @@ namespace rift {
 
 namespace {
 
+constexpr int kClassCoef = 64;  // detectors x response indices kept for the class pass
+
 // C~^k_a of one detector (composite order), out[na].
 __device__ void comp_coeffs(const CompParams& C, int k, double sd, double cd, double sg,
                             double cg, double s2p, double c2p, double tk, const double s[3],
@@ -166,6 +168,10 @@ __device__ CompOut comp_lnl_draw(const CompParams& C, const PointParams& P, cons
 
   double td = 0.0, tq = 0.0;
   int oob = 0;
+  // the coefficients of all detectors fit a small local array: then the
+  // quadratic forms are formed once per detector class (below)
+  const bool by_class = C.K * na <= kClassCoef;
+  double2 cfs[kClassCoef];
   for (int k = 0; k < C.K; ++k) {
     const double tk = tc - (C.pos[k][0] * g.s[0] + C.pos[k][1] * g.s[1] + C.pos[k][2] * g.s[2]);
     double2 cf[kMaxRespIdx];
@@ -206,8 +212,12 @@ __device__ CompOut comp_lnl_draw(const CompParams& C, const PointParams& P, cons
       }
     }
 
-    // quadratic term: sum over block pairs a <= b of z_a^T G_ab z_b
-    const double* Gk = C.G + (size_t)k * C.nblk * 4 * M * M;
+    if (by_class) {
+      for (int a = 0; a < na; ++a) cfs[k * na + a] = cf[a];
+      continue;
+    }
+    // quadratic term, this detector: sum over block pairs a <= b of z_a^T G_ab z_b
+    const double* Gk = C.G + (size_t)C.cls_of[k] * C.nblk * 4 * M * M;
     int blk = 0;
     for (int a = 0; a < na; ++a) {
       double ar[MM], ai[MM];
@@ -243,6 +253,48 @@ __device__ CompOut comp_lnl_draw(const CompParams& C, const PointParams& P, cons
           }
         }
         tq += acc;
+      }
+    }
+  }
+  if (by_class) {
+    // z_a = Re C_a y + Im C_a Jy with y = (Re Y, Im Y), Jy = (-Im Y, Re Y), so
+    // z_a^T G_ab z_b needs only the four forms y^T G y, y^T G Jy, (Jy)^T G y,
+    // (Jy)^T G Jy of each block, shared by the detectors of a class
+    for (int cc = 0; cc < C.ncls; ++cc) {
+      const double* Gc = C.G + (size_t)cc * C.nblk * 4 * M * M;
+      int blk = 0;
+      for (int a = 0; a < na; ++a) {
+        for (int b = a; b < na; ++b, ++blk) {
+          const double* Gb = Gc + (size_t)blk * 4 * M * M;
+          double s00 = 0.0, s01 = 0.0, s10 = 0.0, s11 = 0.0;
+#pragma unroll
+          for (int r = 0; r < MM; ++r) {
+            if (r < M) {
+              double g1r = 0.0, g1i = 0.0, g2r = 0.0, g2i = 0.0;  // rows of G y and G Jy
+#pragma unroll
+              for (int c = 0; c < MM; ++c) {
+                if (c < M) {
+                  const double g00 = __ldg(Gb + r * M + c), g01 = __ldg(Gb + M * M + r * M + c);
+                  const double g10 = __ldg(Gb + 2 * M * M + r * M + c);
+                  const double g11 = __ldg(Gb + 3 * M * M + r * M + c);
+                  g1r = fma(g00, yr[c], fma(g01, yi[c], g1r));
+                  g1i = fma(g10, yr[c], fma(g11, yi[c], g1i));
+                  g2r = fma(g01, yr[c], fma(-g00, yi[c], g2r));
+                  g2i = fma(g11, yr[c], fma(-g10, yi[c], g2i));
+                }
+              }
+              s00 = fma(yr[r], g1r, fma(yi[r], g1i, s00));
+              s10 = fma(yr[r], g1i, fma(-yi[r], g1r, s10));
+              s01 = fma(yr[r], g2r, fma(yi[r], g2i, s01));
+              s11 = fma(yr[r], g2i, fma(-yi[r], g2r, s11));
+            }
+          }
+          for (int k = 0; k < C.K; ++k) {
+            if (C.cls_of[k] != cc) continue;
+            const double2 ca = cfs[k * na + a], cb = cfs[k * na + b];
+            tq += ca.x * (cb.x * s00 + cb.y * s01) + ca.y * (cb.x * s10 + cb.y * s11);
+          }
+        }
       }
     }
   }
@@ -462,8 +514,24 @@ extern "C" int rift_ile_comp_create(const rift_ile_comp_desc* d, rift_ile_comp**
 
   // real form of c^+ U c + Re(c^T V c) in z = (Re c, Im c): diagonal blocks
   // sym(Ur + Vr), sym(Ur - Vr); off-diagonal 1/2 (Ui^T - Ui - Vi - Vi^T)
+  // detectors with identical U and V (the same noise curve and bank) share one form
+  const size_t uv_len = 2 * (size_t)A * A;
+  int rep[kMaxDet];
+  C.ncls = 0;
+  for (int k = 0; k < K; ++k) {
+    int c = -1;
+    for (int q = 0; q < C.ncls && c < 0; ++q)
+      if (std::memcmp(d->U + rep[q] * uv_len, d->U + k * uv_len, uv_len * sizeof(double)) == 0 &&
+          std::memcmp(d->V + rep[q] * uv_len, d->V + k * uv_len, uv_len * sizeof(double)) == 0)
+        c = q;
+    if (c < 0) {
+      c = C.ncls++;
+      rep[c] = k;
+    }
+    C.cls_of[k] = c;
+  }
   const size_t blk_sz = 4 * (size_t)M * M;
-  std::vector<double> G((size_t)K * C.nblk * blk_sz);
+  std::vector<double> G((size_t)C.ncls * C.nblk * blk_sz);
   auto U = [&](int k, int r, int c, int part) { return d->U[(((size_t)k * A + r) * A + c) * 2 + part]; };
   auto V = [&](int k, int r, int c, int part) { return d->V[(((size_t)k * A + r) * A + c) * 2 + part]; };
   auto Gfull = [&](int k, int pr, int r, int pc, int c) {
@@ -473,12 +541,13 @@ extern "C" int rift_ile_comp_create(const rift_ile_comp_desc* d, rift_ile_comp**
       return 0.5 * (U(k, c, r, 1) - U(k, r, c, 1) - V(k, r, c, 1) - V(k, c, r, 1));
     return 0.5 * (U(k, r, c, 1) - U(k, c, r, 1) - V(k, c, r, 1) - V(k, r, c, 1));
   };
-  for (int k = 0; k < K; ++k) {
+  for (int cc = 0; cc < C.ncls; ++cc) {
+    const int k = rep[cc];
     int blk = 0;
     for (int a = 0; a < na; ++a)
       for (int b = a; b < na; ++b, ++blk) {
         const double f = (a == b) ? 1.0 : 2.0;
-        double* Gb = G.data() + ((size_t)k * C.nblk + blk) * blk_sz;
+        double* Gb = G.data() + ((size_t)cc * C.nblk + blk) * blk_sz;
         for (int sub = 0; sub < 4; ++sub) {
           const int pr = sub >> 1, pc = sub & 1;
           for (int r = 0; r < M; ++r)

@@ -290,7 +290,7 @@ __device__ double comp_grad_draw(const CompParams& C, const PointParams& P, cons
     }
 
     // quadratic term over the block pairs a <= b
-    const double* Gk = C.G + (size_t)k * C.nblk * 4 * M * M;
+    const double* Gk = C.G + (size_t)C.cls_of[k] * C.nblk * 4 * M * M;
     int blk = 0;
     for (int a = 0; a < na; ++a) {
       double ar[MM], ai[MM];
