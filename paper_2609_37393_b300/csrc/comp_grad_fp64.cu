@@ -35,6 +35,7 @@ namespace rift {
 namespace {
 
 constexpr int kPsi = 2, kRa = 0, kDec = 1, kTc = 3;  // slots of dC: ra, dec, psi, t_c
+constexpr int kClassCoefGrad = 40;  // detectors x response indices kept for the class pass
 
 // C~^k_a and dC~^k_a / d(ra, dec, psi, t_c) of one detector.
 __device__ void comp_coeffs_grad(const CompParams& C, int k, const CompDraw& g, double tk,
@@ -235,6 +236,10 @@ __device__ double comp_grad_draw(const CompParams& C, const PointParams& P, cons
   }
 
   double td = 0.0, tq = 0.0, gd[kNpar], gq[kNpar];
+  // coefficients of all detectors kept locally: the quadratic forms are then
+  // formed once per detector class (below)
+  const bool by_class = C.K * na <= kClassCoefGrad;
+  double2 cfs[kClassCoefGrad], dcfs[kClassCoefGrad][4];
   bool bad = false;  // an arrival time that is not finite
 #pragma unroll
   for (int p = 0; p < kNpar; ++p) gd[p] = gq[p] = 0.0;
@@ -289,6 +294,13 @@ __device__ double comp_grad_draw(const CompParams& C, const PointParams& P, cons
       }
     }
 
+    if (by_class) {
+      for (int a = 0; a < na; ++a) {
+        cfs[k * na + a] = cf[a];
+        for (int v = 0; v < 4; ++v) dcfs[k * na + a][v] = dcf[a][v];
+      }
+      continue;
+    }
     // quadratic term over the block pairs a <= b
     const double* Gk = C.G + (size_t)C.cls_of[k] * C.nblk * 4 * M * M;
     int blk = 0;
@@ -374,6 +386,96 @@ __device__ double comp_grad_draw(const CompParams& C, const PointParams& P, cons
       gq[6] += dcf[a][kTc].x * gy.x + dcf[a][kTc].y * gy.y;
       gq[3] += cf[a].x * gyi.x + cf[a].y * gyi.y;
       gq[4] += cf[a].x * gyp.x + cf[a].y * gyp.y;
+    }
+  }
+  if (by_class) {
+    // With v_0 = y = (Re Y, Im Y), v_1 = Jy = (-Im Y, Re Y), z_a = sum_p c^p_a v_p
+    // (c^0 = Re C_a, c^1 = Im C_a), so per block and class the forms
+    // S^pq = v_p^T G v_q and, for incl and phase, v_p'^T G v_q + v_p^T G v_q'
+    // carry the whole quadratic term and its derivatives.
+    for (int cc = 0; cc < C.ncls; ++cc) {
+      const double* Gc = C.G + (size_t)cc * C.nblk * 4 * M * M;
+      int blk = 0;
+      for (int a = 0; a < na; ++a) {
+        for (int b = a; b < na; ++b, ++blk) {
+          const double* Gb = Gc + (size_t)blk * 4 * M * M;
+          // rows of G v_q (g) and of G^T v_p (h), q, p in {0, 1}
+          double S[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, Ti[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+          double Tp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+          for (int r = 0; r < MM; ++r) {
+            if (r < M) {
+              double g[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // [q][Re row, Im row]
+              double hh[2][2] = {{0.0, 0.0}, {0.0, 0.0}}; // [p][Re col, Im col] of G^T v_p at r
+#pragma unroll
+              for (int c = 0; c < MM; ++c) {
+                if (c < M) {
+                  const double g00 = __ldg(Gb + r * M + c), g01 = __ldg(Gb + M * M + r * M + c);
+                  const double g10 = __ldg(Gb + 2 * M * M + r * M + c);
+                  const double g11 = __ldg(Gb + 3 * M * M + r * M + c);
+                  // G v_0, G v_1 at rows (Re r, Im r)
+                  g[0][0] = fma(g00, yr[c], fma(g01, yi[c], g[0][0]));
+                  g[0][1] = fma(g10, yr[c], fma(g11, yi[c], g[0][1]));
+                  g[1][0] = fma(g01, yr[c], fma(-g00, yi[c], g[1][0]));
+                  g[1][1] = fma(g11, yr[c], fma(-g10, yi[c], g[1][1]));
+                  // G^T v_0, G^T v_1 at columns (Re r, Im r): sum over rows c
+                  const double t00 = __ldg(Gb + c * M + r), t01 = __ldg(Gb + M * M + c * M + r);
+                  const double t10 = __ldg(Gb + 2 * M * M + c * M + r);
+                  const double t11 = __ldg(Gb + 3 * M * M + c * M + r);
+                  hh[0][0] = fma(t00, yr[c], fma(t10, yi[c], hh[0][0]));
+                  hh[0][1] = fma(t01, yr[c], fma(t11, yi[c], hh[0][1]));
+                  hh[1][0] = fma(t10, yr[c], fma(-t00, yi[c], hh[1][0]));
+                  hh[1][1] = fma(t11, yr[c], fma(-t01, yi[c], hh[1][1]));
+                }
+              }
+              // v_p (and its incl, phase derivatives) at rows (Re r, Im r)
+              const double vr[2][2] = {{yr[r], yi[r]}, {-yi[r], yr[r]}};
+              const double vi[2][2] = {{ir[r], ii[r]}, {-ii[r], ir[r]}};
+              const double vp[2][2] = {{pr[r], pi[r]}, {-pi[r], pr[r]}};
+#pragma unroll
+              for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                  S[pp][qq] = fma(vr[pp][0], g[qq][0], fma(vr[pp][1], g[qq][1], S[pp][qq]));
+                  // v_p'^T G v_q + v_p^T G v_q' = v_p' . g_q + v_q' . h_p
+                  Ti[pp][qq] = fma(vi[pp][0], g[qq][0], fma(vi[pp][1], g[qq][1], Ti[pp][qq]));
+                  Ti[pp][qq] = fma(vi[qq][0], hh[pp][0], fma(vi[qq][1], hh[pp][1], Ti[pp][qq]));
+                  Tp[pp][qq] = fma(vp[pp][0], g[qq][0], fma(vp[pp][1], g[qq][1], Tp[pp][qq]));
+                  Tp[pp][qq] = fma(vp[qq][0], hh[pp][0], fma(vp[qq][1], hh[pp][1], Tp[pp][qq]));
+                }
+            }
+          }
+          for (int k = 0; k < C.K; ++k) {
+            if (C.cls_of[k] != cc) continue;
+            const double2 ca = cfs[k * na + a], cb = cfs[k * na + b];
+            const double pa[2] = {ca.x, ca.y}, pb[2] = {cb.x, cb.y};
+            double val = 0.0, vi_ = 0.0, vp_ = 0.0;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+              for (int qq = 0; qq < 2; ++qq) {
+                val = fma(pa[pp] * pb[qq], S[pp][qq], val);
+                vi_ = fma(pa[pp] * pb[qq], Ti[pp][qq], vi_);
+                vp_ = fma(pa[pp] * pb[qq], Tp[pp][qq], vp_);
+              }
+            tq += val;
+            gq[3] += vi_;
+            gq[4] += vp_;
+            const int slot[4] = {0, 1, 2, 6};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const double2 da = dcfs[k * na + a][v], db = dcfs[k * na + b][v];
+              const double qa[2] = {da.x, da.y}, qb[2] = {db.x, db.y};
+              double d = 0.0;
+#pragma unroll
+              for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) d = fma(qa[pp] * pb[qq] + pa[pp] * qb[qq], S[pp][qq], d);
+              gq[slot[v]] += d;
+            }
+          }
+        }
+      }
     }
   }
   const double q4 = 0.25 * x * x;
