@@ -684,6 +684,14 @@ def run_direct(args):
     cpu_s = time.perf_counter() - t0
     fin = np.isfinite(ref)
     err = float(np.max(np.abs(got[:ns][fin] - ref[fin]) / np.maximum(1.0, np.abs(ref[fin]))))
+    # with geocentric time integrated too: 32 midpoints over +-0.5 ms about the injection
+    tr = info["truth"]
+    rule_t = rule + (32, tr["t"] - 5e-4, tr["t"] + 5e-4)
+    nt_draws = 1 << 12
+    dt_ = R.Draws({p: np.asarray(draws[p])[:nt_draws] for p in W.PARAMS})
+    out_t = torch.empty(nt_draws, dtype=torch.float64, device="cuda")
+    ms_t = timed_events(torch, lambda: R.rift_ile_lnL_direct(pt, dt_, *rule_t, out=out_t), 3,
+                        stream)
     print(json.dumps({
         "metric": "directly marginalised lnL draws/s (phase, polarisation, distance in-kernel)",
         "workload": "direct", "value": n / (ms * 1e-3), "unit": "draws/s", "n_gpus": 1,
@@ -691,6 +699,8 @@ def run_direct(args):
         "config": {"workload": "3G network K=4, M=10, SNR 30, grid 128 x 64 (phase x "
                    "polarisation), 16 Gauss-Hermite nodes in x, D in [50, 200]", "draws": n},
         "ms_per_call": ms, "grid_nodes_per_s": n * rule[0] * rule[1] / (ms * 1e-3),
+        "with_time_rule": {"draws_per_s": nt_draws / (ms_t * 1e-3), "time_nodes": 32,
+                           "window_s": 1e-3},
         "cpu_baseline": {"value": ns / cpu_s, "unit": "draws/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {ns} draws, numpy reconstruction and quadrature"},
         "max_rel_err_vs_oracle": err, "clocks": clocks.summary()}), flush=True)

@@ -21,6 +21,11 @@
  * [d_ref/d_max, d_ref/d_min].  Grid points whose largest possible
  * contribution is more than 60 nat below the best point's are skipped.
  *
+ * With n_t > 0 the geocentric time is integrated as well, by the
+ * fixed-spacing rule of eq. ap:tfixed on the window [t_lo, t_hi] (the draw's
+ * t is then ignored); the harmonic model is rebuilt at every time node
+ * before any integration, as App. F.1 requires.
+ *
  * The draw's psi, phase and lnD are ignored.  A draw whose distance nodes all
  * fall outside the prior gets -inf.  Ownership and errors as in rift_ile.h;
  * asynchronous on `stream`.  Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA.
@@ -41,6 +46,9 @@ typedef struct {
   int32_t n_gh;   /* Gauss-Hermite nodes in x, 1..RIFT_ILE_MAX_GH */
   double d_min;   /* distance prior range, same unit as d_ref */
   double d_max;
+  int32_t n_t;    /* 0: use each draw's t; else time nodes of the fixed-spacing rule */
+  double t_lo;    /* time window (seconds, n_t > 0): midpoints t_lo + (j + 1/2) h, */
+  double t_hi;    /* h = (t_hi - t_lo) / n_t, uniform prior on the window */
 } rift_ile_direct_rule;
 
 /* ln L_dir per draw into DEVICE out[n] (double). */

@@ -8,6 +8,8 @@ For one draw of the sampled coordinates (ra, dec, incl, t_c) it computes
 
     L_dir = int dphi dpsi dx  p(phi) p(psi) p_x(x) exp[lnL(phi, psi, x)],
 
+and optionally integrates t_c as well (fixed-spacing rule, eq. ap:tfixed).
+
 following the paper's steps:
 
 1. ERAI reconstruction (eq. ap:angleharm, eq. ap:nyquist): at fixed time the
@@ -95,8 +97,13 @@ def distance_gh(K, R, d_ref, d_min, d_max, n_gh):
 
 
 def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
-               d_max: float):
-    """ln L_dir per draw (uses ra, dec, incl, t of each draw)."""
+               d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0):
+    """ln L_dir per draw.  With n_t = 0 the draw's t is used; otherwise t is
+    integrated too, by the fixed-spacing rule of eq. ap:tfixed on n_t
+    midpoints t_j = t_lo + (j + 1/2) h, h = (t_hi - t_lo)/n_t, with the
+    uniform prior on [t_lo, t_hi] (weight 1/n_t per node); the harmonic model
+    is reconstructed at every time node before any integration, as the
+    fixed-time qualification of App. F.1 requires."""
     pt = OraclePoint(point)
     th = {p: np.asarray(draws[p], dtype=np.float64) for p in PARAMS}
     N = th["ra"].shape[0]
@@ -106,10 +113,19 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
     lnw = -math.log(n_phi * n_psi)   # trapezoid weights times the uniform priors
     out = np.empty(N)
     for i in range(N):
-        cK, cR, _ = reconstruct(pt, point, th["ra"][i], th["dec"][i], th["incl"][i], th["t"][i])
-        K = evaluate(cK, PS, PH)
-        R = evaluate(cR, PS, PH)
-        v = distance_gh(K, R, point["d_ref"], d_min, d_max, n_gh) + lnw
+        if n_t > 0:
+            h = (t_hi - t_lo) / n_t
+            times = t_lo + (np.arange(n_t) + 0.5) * h
+            lnwt = -math.log(n_t)
+        else:
+            times, lnwt = [th["t"][i]], 0.0
+        vals = []
+        for t in times:
+            cK, cR, _ = reconstruct(pt, point, th["ra"][i], th["dec"][i], th["incl"][i], t)
+            K = evaluate(cK, PS, PH)
+            R = evaluate(cR, PS, PH)
+            vals.append(distance_gh(K, R, point["d_ref"], d_min, d_max, n_gh) + lnw + lnwt)
+        v = np.concatenate([x.ravel() for x in vals])
         m = np.max(v)
         out[i] = m + math.log(np.sum(np.exp(v - m))) if m > -np.inf else -np.inf
     return out

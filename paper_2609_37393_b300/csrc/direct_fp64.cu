@@ -36,10 +36,11 @@ constexpr int kHn = 4 * kMaxEll + 1;        // norm harmonics -16..16
 constexpr double kSkipNat = 60.0;
 
 struct DirectParams {
-  int n_phi, n_psi, n_gh;
+  int n_phi, n_psi, n_gh, n_t;  // n_t = 0: the draw's own t
+  double t_lo, t_h;             // time midpoints t_lo + (j + 1/2) t_h
   double lo, hi;          // prior range of x
   double lnnorm;          // ln of 3 d_ref^3 / (d_max^3 - d_min^3)
-  double lnw;             // -ln(n_phi n_psi)
+  double lnw;             // -ln(n_phi n_psi max(n_t, 1))
   double ln_ub;           // ln(sqrt(2 pi) norm lo^-4), the prefactor bound over sigma_x
   double xi[RIFT_ILE_MAX_GH], w[RIFT_ILE_MAX_GH];
 };
@@ -56,10 +57,10 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 
 // The harmonic coefficients of one draw (one thread).
 template <int MM>
-__device__ void direct_coeffs(const PointParams& P, const DrawsParams& dp, long long i,
+__device__ void direct_coeffs(const PointParams& P, const DrawsParams& dp, long long i, double tc,
                               DirCoef& out) {
   const double ra = load_param_d(dp, 0, i), dec = load_param_d(dp, 1, i);
-  const double incl = load_param_d(dp, 3, i), tc = load_param_d(dp, 6, i);
+  const double incl = load_param_d(dp, 3, i);
   const int K = P.K, M = P.M;
   double sl, cl, sd, cd;
   sincos(ra - P.gmst, &sl, &cl);
@@ -226,70 +227,75 @@ __global__ void __launch_bounds__(32 * kDirWarps) direct_kernel(const PointParam
   DirCoef& C = coef[wid];
   const long long stride = (long long)gridDim.x * kDirWarps;
   for (long long i = blockIdx.x * (long long)kDirWarps + wid; i < dp.n; i += stride) {
-    if (lane == 0) direct_coeffs<MM>(P, dp, i, C);
-    __syncwarp();
-    // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
-    double best = -CUDART_INF;
-    long long best_idx = (long long)Q.n_phi * Q.n_psi;
-    for (int a = lane; a < Q.n_phi; a += 32) {
-      double2 D, B;
-      double A;
-      direct_column(C, (double)a / Q.n_phi, D, A, B);
-      for (int b = 0; b < Q.n_psi; ++b) {
-        double s2, c2;
-        sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
-        double K, R;
-        direct_node(D, A, B, make_double2(c2, s2), K, R);
-        const double h = (R > 0.0) ? K * K / (2.0 * R) : -CUDART_INF;
-        const long long idx = (long long)a * Q.n_psi + b;
-        if (h > best || (h == best && idx < best_idx)) {
-          best = h;
-          best_idx = idx;
-        }
-      }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
-      if (ob > best || (ob == best && oi < best_idx)) {
-        best = ob;
-        best_idx = oi;
-      }
-    }
-    double v0 = -CUDART_INF;
-    if (best_idx < (long long)Q.n_phi * Q.n_psi) {
-      const int a = (int)(best_idx / Q.n_psi), b = (int)(best_idx % Q.n_psi);
-      double2 D, B;
-      double A;
-      direct_column(C, (double)a / Q.n_phi, D, A, B);
-      double s2, c2;
-      sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
-      double K, R;
-      direct_node(D, A, B, make_double2(c2, s2), K, R);
-      v0 = direct_distance(Q, K, R);
-    }
-    const double cut = v0 - kSkipNat;
-    // pass 2: the log-sum-exp over the nodes that can matter
     double m = -CUDART_INF, s = 0.0;
     bool nan_seen = false;
-    for (int a = lane; a < Q.n_phi; a += 32) {
-      double2 D, B;
-      double A;
-      direct_column(C, (double)a / Q.n_phi, D, A, B);
-      for (int b = 0; b < Q.n_psi; ++b) {
+    const int nt = Q.n_t > 0 ? Q.n_t : 1;
+    for (int jt = 0; jt < nt; ++jt) {
+      const double tc = Q.n_t > 0 ? Q.t_lo + (jt + 0.5) * Q.t_h : load_param_d(dp, 6, i);
+      if (lane == 0) direct_coeffs<MM>(P, dp, i, tc, C);
+      __syncwarp();
+      // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
+      double best = -CUDART_INF;
+      long long best_idx = (long long)Q.n_phi * Q.n_psi;
+      for (int a = lane; a < Q.n_phi; a += 32) {
+        double2 D, B;
+        double A;
+        direct_column(C, (double)a / Q.n_phi, D, A, B);
+        for (int b = 0; b < Q.n_psi; ++b) {
+          double s2, c2;
+          sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+          double K, R;
+          direct_node(D, A, B, make_double2(c2, s2), K, R);
+          const double h = (R > 0.0) ? K * K / (2.0 * R) : -CUDART_INF;
+          const long long idx = (long long)a * Q.n_psi + b;
+          if (h > best || (h == best && idx < best_idx)) {
+            best = h;
+            best_idx = idx;
+          }
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
+        if (ob > best || (ob == best && oi < best_idx)) {
+          best = ob;
+          best_idx = oi;
+        }
+      }
+      double v0 = -CUDART_INF;
+      if (best_idx < (long long)Q.n_phi * Q.n_psi) {
+        const int a = (int)(best_idx / Q.n_psi), b = (int)(best_idx % Q.n_psi);
+        double2 D, B;
+        double A;
+        direct_column(C, (double)a / Q.n_phi, D, A, B);
         double s2, c2;
         sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
         double K, R;
         direct_node(D, A, B, make_double2(c2, s2), K, R);
-        if (isnan(K) || isnan(R)) {
-          nan_seen = true;
-          continue;
-        }
-        if (!(R > 0.0)) continue;
-        const double ub = K * K / (2.0 * R) - 0.5 * log(R) + Q.ln_ub;
-        if (ub < cut) continue;
-        lse_add(m, s, direct_distance(Q, K, R));
+        v0 = direct_distance(Q, K, R);
       }
+      const double cut = v0 - kSkipNat;
+      // pass 2: the log-sum-exp over the nodes that can matter
+      for (int a = lane; a < Q.n_phi; a += 32) {
+        double2 D, B;
+        double A;
+        direct_column(C, (double)a / Q.n_phi, D, A, B);
+        for (int b = 0; b < Q.n_psi; ++b) {
+          double s2, c2;
+          sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+          double K, R;
+          direct_node(D, A, B, make_double2(c2, s2), K, R);
+          if (isnan(K) || isnan(R)) {
+            nan_seen = true;
+            continue;
+          }
+          if (!(R > 0.0)) continue;
+          const double ub = K * K / (2.0 * R) - 0.5 * log(R) + Q.ln_ub;
+          if (ub < cut) continue;
+          lse_add(m, s, direct_distance(Q, K, R));
+        }
+      }
+      __syncwarp();  // C is rewritten for the next time node
     }
     nan_seen = __any_sync(0xffffffffu, nan_seen);
     for (int off = 16; off > 0; off >>= 1) {
@@ -411,6 +417,13 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
                        rule->n_psi, rule->n_gh);
     return RIFT_ILE_ERR_SHAPE;
   }
+  if (rule->n_t < 0 || rule->n_t > (1 << 20) ||
+      (rule->n_t > 0 && !(rule->t_hi > rule->t_lo && std::isfinite(rule->t_lo) &&
+                          std::isfinite(rule->t_hi)))) {
+    rift_ile_set_error("rift_ile_lnL_direct: n_t=%d needs 0 <= n_t <= 2^20 and t_lo < t_hi finite",
+                       rule->n_t);
+    return RIFT_ILE_ERR_SHAPE;
+  }
   if (!(rule->d_min > 0.0) || !(rule->d_max > rule->d_min) || !std::isfinite(rule->d_max)) {
     rift_ile_set_error("rift_ile_lnL_direct: need 0 < d_min < d_max finite");
     return RIFT_ILE_ERR_INVALID_ARG;
@@ -432,7 +445,10 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   const double norm = 3.0 * dref * dref * dref /
                       (rule->d_max * rule->d_max * rule->d_max - rule->d_min * rule->d_min * rule->d_min);
   Q.lnnorm = std::log(norm);
-  Q.lnw = -std::log((double)rule->n_phi * rule->n_psi);
+  Q.n_t = rule->n_t;
+  Q.t_lo = rule->t_lo;
+  Q.t_h = rule->n_t > 0 ? (rule->t_hi - rule->t_lo) / rule->n_t : 0.0;
+  Q.lnw = -std::log((double)rule->n_phi * rule->n_psi * (rule->n_t > 0 ? rule->n_t : 1));
   Q.ln_ub = std::log(std::sqrt(2.0 * M_PI) * norm) - 4.0 * std::log(Q.lo);
   if ((rc = gauss_hermite(Q.n_gh, Q.xi, Q.w))) {
     rift_ile_set_error("rift_ile_lnL_direct: Gauss-Hermite rule failed for n=%d", Q.n_gh);

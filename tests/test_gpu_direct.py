@@ -52,10 +52,24 @@ def test_3g_network_moderate_snr(R):
     _cmp(got, ref)
 
 
+def test_time_rule(R):
+    """t integrated on a +-1 ms window (fixed-spacing rule), against the oracle."""
+    point, exact, info, draws, logw = W.config0(n_draws=12)
+    tr = info["truth"]
+    d = {p: np.concatenate([[tr[p]], np.asarray(draws[p])]) for p in W.PARAMS}
+    pt = R.Point(point)
+    args = (64, 32, 16, 50.0, 200.0, 24, tr["t"] - 1e-3, tr["t"] + 1e-3)
+    got = R.rift_ile_lnL_direct(pt, R.Draws(d), *args).cpu().numpy()
+    ref = OD.lnL_direct(point, d, *args)
+    _cmp(got, ref)
+    assert np.isfinite(got[0])
+
+
 def test_invalid_rules(R):
     point, exact, info, draws, logw = W.config0(n_draws=4)
     pt = R.Point(point)
     d = R.Draws(draws)
-    for args in ((0, 8, 16, 50.0, 200.0), (8, 8, 65, 50.0, 200.0), (8, 8, 16, 200.0, 50.0)):
+    for args in ((0, 8, 16, 50.0, 200.0), (8, 8, 65, 50.0, 200.0), (8, 8, 16, 200.0, 50.0),
+                 (8, 8, 16, 50.0, 200.0, 4, 0.01, -0.01)):
         with pytest.raises(R.RiftError):
             R.rift_ile_lnL_direct(pt, d, *args)
