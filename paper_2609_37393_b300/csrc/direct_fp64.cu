@@ -2,8 +2,9 @@
 // likelihood (eq. direct_marginalization; ERAI of App. F.1, adaptive
 // Gauss-Hermite of eq. ap:dgh), FP64, one warp per draw.
 //
-// Per draw (lane 0): sky basis, F_k(0), Y_lm(phi = 0), Q_k,lm(t_k) by the
-// table cubic, then the harmonic coefficients of
+// Per draw (all lanes): sky basis, F_k(0), Y_lm(phi = 0); the lanes share the
+// mode pairs and the (detector, mode) pairs (Q_k,lm(t_k) by the table cubic)
+// and bin them by harmonic in a fixed order into the coefficients of
 //   K(phi, psi) = Re[e^{-2 i psi} sum_m e^{-i m phi} c_m],
 //     c_m = sum_k conj(F_k(0)) sum_{lm: m} conj(Y_lm(0)) Q_k,lm(t_k),
 //   2R(phi, psi) = sum_d alpha_d e^{i d phi} + Re[e^{4 i psi} sum_s beta_s e^{i s phi}],
@@ -55,43 +56,124 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// The harmonic coefficients of one draw (one thread).
+// Per-draw values every lane keeps: Y_lm(phi = 0), F_k(psi = 0), the source direction.
 template <int MM>
-__device__ void direct_coeffs(const PointParams& P, const DrawsParams& dp, long long i, double tc,
-                              DirCoef& out) {
+struct DirDraw {
+  double yr[MM], yi[MM];
+  double Fr[kMaxDet], Fi[kMaxDet];
+  double s[3];
+};
+
+template <int MM>
+__device__ void direct_setup(const PointParams& P, const DrawsParams& dp, long long i,
+                             DirDraw<MM>& g) {
   const double ra = load_param_d(dp, 0, i), dec = load_param_d(dp, 1, i);
   const double incl = load_param_d(dp, 3, i);
-  const int K = P.K, M = P.M;
   double sl, cl, sd, cd;
   sincos(ra - P.gmst, &sl, &cl);
   sincos(dec, &sd, &cd);
-  const double s[3] = {cd * cl, cd * sl, sd};
+  g.s[0] = cd * cl;
+  g.s[1] = cd * sl;
+  g.s[2] = sd;
   const double e1[3] = {-sl, cl, 0.0};
   const double e2[3] = {-sd * cl, -sd * sl, cd};
-  double yr[MM], yi[MM];
-  {
-    double sh, ch;
-    sincos(0.5 * incl, &sh, &ch);
+  double sh, ch;
+  sincos(0.5 * incl, &sh, &ch);
 #pragma unroll
-    for (int m = 0; m < MM; ++m) {
-      yr[m] = yi[m] = 0.0;
-      if (m < M) sylm_eval<double>(P, m, ch, sh, 1.0, 0.0, P.ycoef[m], yr[m], yi[m]);
+  for (int m = 0; m < MM; ++m) {
+    g.yr[m] = g.yi[m] = 0.0;
+    if (m < P.M) sylm_eval<double>(P, m, ch, sh, 1.0, 0.0, P.ycoef[m], g.yr[m], g.yi[m]);
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxDet; ++k) {
+    g.Fr[k] = g.Fi[k] = 0.0;
+    if (k < P.K) {
+      const double* D = P.resp[k];
+      g.Fr[k] = quad3(D, e1, e1) - quad3(D, e2, e2);
+      g.Fi[k] = -2.0 * quad3(D, e1, e2);
     }
   }
-  for (int h = 0; h < kHm; ++h) out.c[h] = make_double2(0.0, 0.0);
-  for (int h = 0; h < kHn; ++h) out.al[h] = out.be[h] = make_double2(0.0, 0.0);
-  for (int k = 0; k < K; ++k) {
-    const double* D = P.resp[k];
-    const double Fr = quad3(D, e1, e1) - quad3(D, e2, e2), Fi = -2.0 * quad3(D, e1, e2);
-    const double tk = tc - (P.pos[k][0] * s[0] + P.pos[k][1] * s[1] + P.pos[k][2] * s[2]);
+}
+
+template <int MM>
+__device__ __forceinline__ double2 y_of(const DirDraw<MM>& g, int m) {
+  double2 y = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int q = 0; q < MM; ++q)
+    if (q == m) y = make_double2(g.yr[q], g.yi[q]);
+  return y;
+}
+
+// Norm coefficients (time independent), the lanes sharing the mode pairs:
+// buf_u[p] = conj(Y_a) Y_b sum_k |F_k|^2 U_k,ab and buf_v[p] = Y_a Y_b sum_k F_k^2
+// V_k,ab for p = a M + b, then lane h bins the pairs by harmonic in pair order.
+template <int MM>
+__device__ void direct_norm_warp(const PointParams& P, const DirDraw<MM>& g, int lane,
+                                 DirCoef& C, double2* buf_u, double2* buf_v) {
+  const int K = P.K, M = P.M;
+  for (int p = lane; p < M * M; p += 32) {
+    const int a = p / M, b = p % M;
+    double ur = 0.0, ui = 0.0, vr = 0.0, vi = 0.0;
+    for (int k = 0; k < K; ++k) {
+      double Fr = 0.0, Fi = 0.0;
+#pragma unroll
+      for (int q = 0; q < kMaxDet; ++q)
+        if (q == k) {
+          Fr = g.Fr[q];
+          Fi = g.Fi[q];
+        }
+      const double F2 = Fr * Fr + Fi * Fi, FFr = Fr * Fr - Fi * Fi, FFi = 2.0 * Fr * Fi;
+      const double2 uu = P.U[((size_t)k * M + a) * M + b], vv = P.V[((size_t)k * M + a) * M + b];
+      ur = fma(F2, uu.x, ur);
+      ui = fma(F2, uu.y, ui);
+      vr += FFr * vv.x - FFi * vv.y;
+      vi += FFr * vv.y + FFi * vv.x;
+    }
+    const double2 ya = y_of(g, a), yb = y_of(g, b);
+    const double2 pu = cmul_d(make_double2(ya.x, -ya.y), yb), pv = cmul_d(ya, yb);
+    buf_u[p] = cmul_d(pu, make_double2(ur, ui));
+    buf_v[p] = cmul_d(pv, make_double2(vr, vi));
+  }
+  __syncwarp();
+  for (int h = lane; h < kHn; h += 32) {
+    double2 al = make_double2(0.0, 0.0), be = al;
+    for (int p = 0; p < M * M; ++p) {
+      const int a = p / M, b = p % M;
+      if (P.em[b] - P.em[a] + 2 * kMaxEll == h) {
+        al.x += buf_u[p].x;
+        al.y += buf_u[p].y;
+      }
+      if (P.em[a] + P.em[b] + 2 * kMaxEll == h) {
+        be.x += buf_v[p].x;
+        be.y += buf_v[p].y;
+      }
+    }
+    C.al[h] = al;
+    C.be[h] = be;
+  }
+  __syncwarp();
+}
+
+// Data coefficients at geocentric time tc, the lanes sharing the (detector,
+// mode) pairs: buf[p] = conj(F_k) conj(Y_m) Q_k,m(t_k), p = k M + m, binned by m.
+template <int MM>
+__device__ void direct_data_warp(const PointParams& P, const DirDraw<MM>& g, double tc, int lane,
+                                 DirCoef& C, double2* buf) {
+  const int K = P.K, M = P.M;
+  for (int p = lane; p < K * M; p += 32) {
+    const int k = p / M, m = p % M;
+    double Fr = 0.0, Fi = 0.0;
+#pragma unroll
+    for (int q = 0; q < kMaxDet; ++q)
+      if (q == k) {
+        Fr = g.Fr[q];
+        Fi = g.Fi[q];
+      }
+    const double tk = tc - (P.pos[k][0] * g.s[0] + P.pos[k][1] * g.s[1] + P.pos[k][2] * g.s[2]);
     const double u = (tk - P.t0[k]) * P.inv_dt;
-    // G_i = Q_k,i(t_k) by the cubic; taps outside the table read zero
-    double gr[MM], gi[MM];
-#pragma unroll
-    for (int m = 0; m < MM; ++m) gr[m] = gi[m] = 0.0;
+    double gr = 0.0, gi = 0.0;
     if (!isfinite(u)) {
-#pragma unroll
-      for (int m = 0; m < MM; ++m) gr[m] = CUDART_NAN;
+      gr = CUDART_NAN;
     } else {
       const double jf = floor(u);
       double w[4], dw[4];
@@ -100,54 +182,34 @@ __device__ void direct_coeffs(const PointParams& P, const DrawsParams& dp, long 
       for (int tap = 0; tap < 4; ++tap) {
         const long long j = j0 + tap;
         if (j < 0 || j >= P.n) continue;
-#pragma unroll
-        for (int m = 0; m < MM; ++m) {
-          if (m < M) {
-            double qr, qi;
-            if (P.q_c128) {
-              const double2 q = __ldg((const double2*)P.Q + ((long long)k * P.n + j) * M + m);
-              qr = q.x;
-              qi = q.y;
-            } else {
-              const float2 q = __ldg((const float2*)P.Q + ((long long)k * P.n + j) * M + m);
-              qr = q.x;
-              qi = q.y;
-            }
-            gr[m] = fma(w[tap], qr, gr[m]);
-            gi[m] = fma(w[tap], qi, gi[m]);
-          }
+        double qr, qi;
+        if (P.q_c128) {
+          const double2 q = __ldg((const double2*)P.Q + ((long long)k * P.n + j) * M + m);
+          qr = q.x;
+          qi = q.y;
+        } else {
+          const float2 q = __ldg((const float2*)P.Q + ((long long)k * P.n + j) * M + m);
+          qr = q.x;
+          qi = q.y;
         }
+        gr = fma(w[tap], qr, gr);
+        gi = fma(w[tap], qi, gi);
       }
     }
-    // c_m += conj(F) conj(Y_i) G_i
-    const double2 cF = make_double2(Fr, -Fi);
-#pragma unroll
-    for (int m = 0; m < MM; ++m) {
-      if (m < M) {
-        const double2 t = cmul_d(cF, cmul_d(make_double2(yr[m], -yi[m]), make_double2(gr[m], gi[m])));
-        double2& c = out.c[P.em[m] + kMaxEll];
-        c.x += t.x;
-        c.y += t.y;
-      }
-    }
-    // |F|^2 and F^2 weight this detector's U and V
-    const double F2 = Fr * Fr + Fi * Fi;
-    const double2 FF = make_double2(Fr * Fr - Fi * Fi, 2.0 * Fr * Fi);
-    for (int a = 0; a < M; ++a) {
-      for (int b = 0; b < M; ++b) {
-        const double2 uu = P.U[((size_t)k * M + a) * M + b], vv = P.V[((size_t)k * M + a) * M + b];
-        const double2 pu = cmul_d(make_double2(yr[a], -yi[a]), make_double2(yr[b], yi[b]));
-        const double2 tu = cmul_d(pu, uu);
-        double2& al = out.al[P.em[b] - P.em[a] + 2 * kMaxEll];
-        al.x += F2 * tu.x;
-        al.y += F2 * tu.y;
-        const double2 tv = cmul_d(FF, cmul_d(cmul_d(make_double2(yr[a], yi[a]), make_double2(yr[b], yi[b])), vv));
-        double2& be = out.be[P.em[a] + P.em[b] + 2 * kMaxEll];
-        be.x += tv.x;
-        be.y += tv.y;
-      }
-    }
+    const double2 ym = y_of(g, m);
+    buf[p] = cmul_d(make_double2(Fr, -Fi), cmul_d(make_double2(ym.x, -ym.y), make_double2(gr, gi)));
   }
+  __syncwarp();
+  for (int h = lane; h < kHm; h += 32) {
+    double2 c = make_double2(0.0, 0.0);
+    for (int p = 0; p < K * M; ++p)
+      if (P.em[p % M] + kMaxEll == h) {
+        c.x += buf[p].x;
+        c.y += buf[p].y;
+      }
+    C.c[h] = c;
+  }
+  __syncwarp();
 }
 
 // Per phase column: D = sum_m c_m e^{-i m phi}, A = Re sum_d al_d e^{i d phi},
@@ -221,19 +283,22 @@ __global__ void __launch_bounds__(32 * kDirWarps) direct_kernel(const PointParam
                                                                 double* __restrict__ out) {
   __shared__ PointParams P;
   __shared__ DirCoef coef[kDirWarps];
+  __shared__ double2 pairbuf[kDirWarps][2][kMaxModes * kMaxModes];
   stage_point(P, gP);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   DirCoef& C = coef[wid];
   const long long stride = (long long)gridDim.x * kDirWarps;
   for (long long i = blockIdx.x * (long long)kDirWarps + wid; i < dp.n; i += stride) {
+    DirDraw<MM> g;
+    direct_setup<MM>(P, dp, i, g);
+    direct_norm_warp<MM>(P, g, lane, C, pairbuf[wid][0], pairbuf[wid][1]);
     double m = -CUDART_INF, s = 0.0;
     bool nan_seen = false;
     const int nt = Q.n_t > 0 ? Q.n_t : 1;
     for (int jt = 0; jt < nt; ++jt) {
       const double tc = Q.n_t > 0 ? Q.t_lo + (jt + 0.5) * Q.t_h : load_param_d(dp, 6, i);
-      if (lane == 0) direct_coeffs<MM>(P, dp, i, tc, C);
-      __syncwarp();
+      direct_data_warp<MM>(P, g, tc, lane, C, pairbuf[wid][0]);
       // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
       double best = -CUDART_INF;
       long long best_idx = (long long)Q.n_phi * Q.n_psi;
