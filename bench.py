@@ -575,6 +575,17 @@ def run_response(args):
             if head is None:
                 head = row
             cp.close()
+    # the composite oracle on a sample of the Path A draws (one core)
+    import oracle.composite as OC
+    point, exact, info, draws, logw = WC.comp_3g(WC.ROTATION, 0, n_draws=n)
+    ns = 64
+    sub = {p: np.asarray(draws[p])[:ns] for p in W_PARAMS}
+    t0 = time.perf_counter()
+    ref = OC.lnL(OC.CompPoint(point), sub)
+    cpu_s = time.perf_counter() - t0
+    cp = R.CompPoint(point)
+    got = R.rift_ile_comp_lnL(cp, R.Draws(sub)).cpu().numpy()
+    err = float(np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))))
     achieved = head["draws_per_s"] * head["fp64_fma_per_draw"]
     line = {
         "metric": "composite-response lnZ draws/s (FP64), 3G network, Path A",
@@ -587,6 +598,9 @@ def run_response(args):
                      "fma_per_draw": head["fp64_fma_per_draw"],
                      "peak_source": f"measured FP64 FMA rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu)"},
         "rows": rows, "clocks": clocks.summary(),
+        "cpu_baseline": {"value": ns / cpu_s, "unit": "draws/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {ns} Path A draws, numpy/C composite oracle"},
+        "max_rel_err_vs_oracle": err,
     }
     print(json.dumps(line), flush=True)
 
