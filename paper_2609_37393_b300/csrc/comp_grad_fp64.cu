@@ -35,7 +35,7 @@ namespace rift {
 namespace {
 
 constexpr int kPsi = 2, kRa = 0, kDec = 1, kTc = 3;  // slots of dC: ra, dec, psi, t_c
-constexpr int kClassCoefGrad = 40;  // detectors x response indices kept for the class pass
+constexpr int kClassCoefGrad = 64;  // detectors x response indices kept for the class pass
 
 // C~^k_a and dC~^k_a / d(ra, dec, psi, t_c) of one detector.
 __device__ void comp_coeffs_grad(const CompParams& C, int k, const CompDraw& g, double tk,

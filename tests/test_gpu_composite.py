@@ -205,3 +205,23 @@ def test_autograd_on_composite_point(R):
 
     small = small[:6] + (small[6].detach().mul(1e4).requires_grad_(),)
     assert torch.autograd.gradcheck(f, small, eps=1e-6, atol=1e-3, rtol=1e-4, nondet_tol=0.0)
+
+
+def test_sharded_lnz_merges_to_the_whole(R):
+    """Draws split into shards (as ranks would hold them) give LSE states whose
+    host merge equals the state of all draws at once (the one exchange of the
+    sharded path)."""
+    point, exact, info, draws, logw = fixture(WC.ROTATION, 1)
+    cp = R.CompPoint(point)
+    whole = R.rift_ile_comp_lnZ_state(cp, R.Draws(draws, logw))
+    n = len(draws["ra"])
+    states = []
+    for r in range(3):
+        lo, hi = R.shard_bounds(n, r, 3)
+        sub = {p: np.asarray(draws[p])[lo:hi] for p in W.PARAMS}
+        states.append(R.rift_ile_comp_lnZ_state(cp, R.Draws(sub, np.asarray(logw)[lo:hi])))
+    merged, mstate = R.rift_ile_lnZ_merge(states)
+    ref = R.rift_ile_lnZ_merge([whole])[0]
+    assert abs(merged[0] - ref[0]) <= 1e-12 * abs(ref[0])
+    assert abs(merged[2] - ref[2]) <= 1e-10 * ref[2]
+    assert mstate[3] == n
