@@ -225,3 +225,38 @@ def test_sharded_lnz_merges_to_the_whole(R):
     assert abs(merged[0] - ref[0]) <= 1e-12 * abs(ref[0])
     assert abs(merged[2] - ref[2]) <= 1e-10 * ref[2]
     assert mstate[3] == n
+
+
+def _three_detector_point(kind, p_max, lengths):
+    import math as _m
+    rng = np.random.default_rng(WC.seed_for(30 + kind, 0))
+    gmst = rng.uniform(0, 2 * _m.pi)
+    truth = WC._truth(rng)
+    dets = [WC.random_detectors_arms(rng, 1, L)[0] for L in lengths]
+    point, exact, info = WC.make_comp_point(
+        kind=kind, p_max=p_max, dets=dets, modes=WC.MODES4, f_low=20.0,
+        f_max=1024.0 if kind == WC.ROTATION else 2048.0, df=0.25, rate=8192.0,
+        half_window=0.025, snr=20.0, truth=truth, gmst=gmst, d_ref=W.D_REF, rng=rng, omega=2.0)
+    sig = W.proposal_sigma(info, exact)
+    draws, logw = W.mixture_draws(np.random.default_rng(WC.seed_for(30 + kind, 1)),
+                                  W.Prior(0.5 * W.D_REF, 2.0 * W.D_REF, 0.01), truth, sig, 96)
+    return point, W.as_float(draws, np.float64)
+
+
+@pytest.mark.parametrize("kind,p_max,lengths", [
+    (WC.ROTATION, 3, (4e3, 4e3, 4e3)),           # 3 x 32 response indices: per-detector forms
+    (WC.FINITE_ARM, 3, (1e4, 1e4, 4e4)),         # two detector classes share forms
+])
+def test_detector_classes_and_per_detector_path(R, kind, p_max, lengths):
+    point, draws = _three_detector_point(kind, p_max, lengths)
+    cp = R.CompPoint(point)
+    l, g = R.rift_ile_comp_lnL_grad(cp, R.Draws(draws))
+    fwd = R.rift_ile_comp_lnL(cp, R.Draws(draws)).cpu().numpy()
+    ref_l, ref_g = OC.lnL_grad(OC.CompPoint(point), draws)
+    tol = 1e-8 if p_max >= 2 and kind == WC.ROTATION else 1e-9
+    assert np.max(np.abs(fwd - ref_l) / np.maximum(1.0, np.abs(ref_l))) <= tol
+    assert np.max(np.abs(l.cpu().numpy() - ref_l) / np.maximum(1.0, np.abs(ref_l))) <= tol
+    g = g.cpu().numpy()
+    for j, p in enumerate(W.PARAMS):
+        s = np.abs(ref_g[:, j]) + np.sqrt(np.mean(ref_g[:, j] ** 2))
+        assert np.max(np.abs(g[j] - ref_g[:, j]) / s) <= 1e-7, p
