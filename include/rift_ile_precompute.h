@@ -58,6 +58,22 @@ typedef struct {
 int rift_ile_precompute(const rift_ile_precompute_desc* desc, void* Q_out, double* U_out,
                         double* V_out, void* stream);
 
+/* The widened bank of Earth-rotation templates of Sec. III.A,
+ * chi^(p,n)_lm = M_n h_lm^(p) (eq. slowrot:master), built as Appendix B
+ * describes: the p-th time derivative as the weight (2 pi i f)^p on the
+ * frequency grid, then the sidereal modulation e^{i n Omega t} applied as a
+ * linear phase in the time domain through one DFT round trip over the grid's
+ * period 1/df (times centred on the reference time, t_j = j' / (nf df),
+ * j' in [-(nf-1)/2, (nf-1)/2]).  Composite order as in rift_ile_response.h:
+ * row a * M + i with a = (p, n), p = 0..p_max, n = -(2+p)..(2+p).
+ *   hlm       DEVICE [M][nf] complex128 on the two-sided grid (nf odd)
+ *   bank_out  DEVICE [n_index * M][nf] complex128
+ * Allocates its work buffers stream-ordered and frees them before returning;
+ * asynchronous on `stream`.  Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA,
+ * ALLOC. */
+int rift_ile_rotation_bank(const double* hlm, int32_t n_modes, int32_t nf, double df,
+                           double omega, int32_t p_max, double* bank_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,3 +56,32 @@ def uv_direct(wgt, hlm):
                 U[k, i, j] = np.sum(wgt[k] * np.conj(hlm[i]) * hlm[j])
                 V[k, i, j] = np.sum(wgt[k] * hm[i] * hlm[j])
     return U, V
+
+
+def rotation_bank_fft(hlm, df, omega, p_max):
+    """The widened bank of Earth-rotation templates chi^(p,n)_lm =
+    M_n h_lm^(p) (eq. slowrot:master) built as Appendix B does: the p-th time
+    derivative as the weight (2 pi i f)^p, then the sidereal modulation
+    e^{i n Omega t} applied as a linear phase in the time domain through one
+    DFT round trip on the grid's period 1/df, times centred on the reference
+    time.  Composite order (p, n) then mode: [n_index * M][nf]."""
+    hlm = np.asarray(hlm, dtype=np.complex128)
+    M, nf = hlm.shape
+    nh = (nf - 1) // 2
+    q = np.arange(nf) - nh                       # f_q / df
+    f = q * df
+    # unshifted order: index (q mod nf)
+    perm = np.mod(q, nf)
+    j = np.arange(nf)
+    t = np.where(j <= nh, j, j - nf) / (nf * df)  # centred times of the period
+    rows = []
+    for p in range(p_max + 1):
+        X = hlm * (2j * np.pi * f) ** p
+        Xs = np.zeros_like(X)
+        Xs[:, perm] = X
+        x = np.fft.ifft(Xs, axis=1) * nf          # sum_q X_q e^{+2 pi i q j / nf}
+        for n in range(-(2 + p), 3 + p):
+            y = x * np.exp(1j * n * omega * t)[None, :]
+            Ys = np.fft.fft(y, axis=1) / nf
+            rows.append(Ys[:, perm])
+    return np.concatenate(rows)

@@ -815,3 +815,23 @@ def rift_ile_lnL_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, 
     _check(_lib.rift_ile_lnL_direct(point.handle, d.ref, ctypes.byref(r),
                                     out.data_ptr() if d.n else None, _stream(stream)))
     return out
+
+
+_lib.rift_ile_rotation_bank.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int32, _P, _P]
+
+
+def rift_ile_rotation_bank(hlm, df: float, omega: float, p_max: int, device=None, stream=None):
+    """The widened Earth-rotation bank chi^(p,n)_lm [n_index * M, nf]
+    (complex128 CUDA tensor) from mode spectra hlm[M, nf] on the two-sided
+    grid of spacing df, by the DFT round trip of Appendix B."""
+    torch = _torch()
+    device = torch.device(device or "cuda")
+    h = _dev_tensor(hlm, torch.complex128, device)
+    M, nf = h.shape
+    na = rift_ile_comp_n_index(RESP_ROTATION, p_max)
+    out = torch.empty((na * M, nf), dtype=torch.complex128, device=device)
+    with torch.cuda.device(device):
+        _check(_lib.rift_ile_rotation_bank(h.data_ptr(), M, nf, float(df), float(omega), int(p_max),
+                                           out.data_ptr(), _stream(stream)))
+    return out

@@ -11,6 +11,7 @@
 // frequencies, a fixed shared-memory tree: reproducible bit for bit.
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <math_constants.h>
 
 #include <cmath>
 #include <mutex>
@@ -266,4 +267,147 @@ extern "C" int rift_ile_precompute(const rift_ile_precompute_desc* d, void* Q_ou
   cudaFreeAsync(Y, st);
   if (rc) return rc;
   return check_cuda(e, "rift_ile_precompute");
+}
+
+// ----------------------------------------------- widened rotation bank
+
+namespace rift {
+namespace {
+
+// X[(p M + i)][(q - nh) mod nf] = h_i(f_q) (2 pi i f_q)^p
+__global__ void bank_weight_kernel(const double2* __restrict__ hlm, int M, int nf, double df,
+                                   int np, double2* __restrict__ X) {
+  const long long total = (long long)np * M * nf;
+  const int nh = (nf - 1) / 2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % nf);
+    const long long row = idx / nf;
+    const int i = (int)(row % M), p = (int)(row / M);
+    const double w = 2.0 * CUDART_PI * (double)(q - nh) * df;  // 2 pi f
+    double2 v = hlm[(long long)i * nf + q];
+    for (int k = 0; k < p; ++k) v = make_double2(-w * v.y, w * v.x);  // times i 2 pi f
+    const int qs = ((q - nh) % nf + nf) % nf;
+    X[row * nf + qs] = v;
+  }
+}
+
+// Z[(a M + i)][j] = x[(p(a) M + i)][j] e^{i n(a) Omega t_j}, t_j centred
+__global__ void bank_modulate_kernel(const double2* __restrict__ x, int M, int nf, double df,
+                                     double omega, int p_max, double2* __restrict__ Z) {
+  const int na = (p_max + 1) * (p_max + 5);
+  const long long total = (long long)na * M * nf;
+  const int nh = (nf - 1) / 2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % nf);
+    const long long row = idx / nf;
+    const int i = (int)(row % M), a = (int)(row / M);
+    int p = 0, off = 0;
+    while (off + 5 + 2 * p <= a) {
+      off += 5 + 2 * p;
+      ++p;
+    }
+    const int n = a - off - (2 + p);
+    const double t = (double)(j <= nh ? j : j - nf) / ((double)nf * df);
+    double s, c;
+    sincos((double)n * omega * t, &s, &c);
+    const double2 v = x[((long long)p * M + i) * nf + j];
+    Z[idx] = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+  }
+}
+
+// bank[(row)][q] = Z[row][(q - nh) mod nf] / nf
+__global__ void bank_gather_kernel(const double2* __restrict__ Z, long long rows, int nf,
+                                   double2* __restrict__ bank) {
+  const long long total = rows * nf;
+  const int nh = (nf - 1) / 2;
+  const double inv = 1.0 / (double)nf;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % nf);
+    const long long row = idx / nf;
+    const int qs = ((q - nh) % nf + nf) % nf;
+    const double2 v = Z[row * nf + qs];
+    bank[idx] = make_double2(v.x * inv, v.y * inv);
+  }
+}
+
+}  // namespace
+}  // namespace rift
+
+extern "C" int rift_ile_rotation_bank(const double* hlm, int32_t n_modes, int32_t nf, double df,
+                                      double omega, int32_t p_max, double* bank_out,
+                                      void* stream) {
+  using namespace rift;
+  if (!hlm || !bank_out) {
+    rift_ile_set_error("rift_ile_rotation_bank: hlm or bank_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (n_modes < 1 || n_modes > RIFT_ILE_MAX_MODES || p_max < 0 || p_max > 3) {
+    rift_ile_set_error("rift_ile_rotation_bank: n_modes=%d or p_max=%d unsupported", n_modes, p_max);
+    return RIFT_ILE_ERR_UNSUPPORTED;
+  }
+  if (nf < 1 || nf % 2 == 0 || nf > (1 << 26)) {
+    rift_ile_set_error("rift_ile_rotation_bank: nf=%d must be odd and positive", nf);
+    return RIFT_ILE_ERR_SHAPE;
+  }
+  if (!(df > 0.0) || !std::isfinite(df) || !std::isfinite(omega)) {
+    rift_ile_set_error("rift_ile_rotation_bank: df must be positive and omega finite");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  const int M = n_modes, np = p_max + 1, na = (p_max + 1) * (p_max + 5);
+  cudaStream_t st = (cudaStream_t)stream;
+  double2 *X = nullptr, *Z = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&X, (size_t)np * M * nf * sizeof(double2), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&Z, (size_t)na * M * nf * sizeof(double2), st);
+  if (e != cudaSuccess) {
+    if (X) cudaFreeAsync(X, st);
+    rift_ile_set_error("rift_ile_rotation_bank work buffers: %s", cudaGetErrorString(e));
+    return RIFT_ILE_ERR_ALLOC;
+  }
+  int rc = RIFT_ILE_OK;
+  bank_weight_kernel<<<blocks_for((long long)np * M * nf), 256, 0, st>>>((const double2*)hlm, M, nf,
+                                                                         df, np, X);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    cufftHandle plan;
+    rc = get_plan(nf, np * M, &plan);
+    cufftResult r = CUFFT_SUCCESS;
+    if (!rc) r = cufftSetStream(plan, st);
+    if (!rc && r == CUFFT_SUCCESS)
+      r = cufftExecZ2Z(plan, (cufftDoubleComplex*)X, (cufftDoubleComplex*)X, CUFFT_INVERSE);
+    if (!rc && r != CUFFT_SUCCESS) {
+      rift_ile_set_error("cuFFT inverse transform failed: cufftResult %d", (int)r);
+      rc = RIFT_ILE_ERR_CUDA;
+    }
+  }
+  if (e == cudaSuccess && !rc) {
+    bank_modulate_kernel<<<blocks_for((long long)na * M * nf), 256, 0, st>>>(X, M, nf, df, omega,
+                                                                             p_max, Z);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && !rc) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    cufftHandle plan;
+    rc = get_plan(nf, na * M, &plan);
+    cufftResult r = CUFFT_SUCCESS;
+    if (!rc) r = cufftSetStream(plan, st);
+    if (!rc && r == CUFFT_SUCCESS)
+      r = cufftExecZ2Z(plan, (cufftDoubleComplex*)Z, (cufftDoubleComplex*)Z, CUFFT_FORWARD);
+    if (!rc && r != CUFFT_SUCCESS) {
+      rift_ile_set_error("cuFFT forward transform failed: cufftResult %d", (int)r);
+      rc = RIFT_ILE_ERR_CUDA;
+    }
+  }
+  if (e == cudaSuccess && !rc) {
+    bank_gather_kernel<<<blocks_for((long long)na * M * nf), 256, 0, st>>>(Z, (long long)na * M, nf,
+                                                                           (double2*)bank_out);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(X, st);
+  cudaFreeAsync(Z, st);
+  if (rc) return rc;
+  return check_cuda(e, "rift_ile_rotation_bank");
 }

@@ -107,3 +107,20 @@ def test_invalid_grids(R):
     with pytest.raises(R.RiftError):   # 1/(df dt) not an integer
         R.rift_ile_precompute(exact["hlm"], exact["dk"], exact["wgt"], df, point["q_t0"],
                               point["q_dt"] * 1.1, n)
+
+
+@pytest.mark.parametrize("p_max", [0, 1, 3])
+def test_rotation_bank_matches_oracle(R, p_max):
+    """The widened Earth-rotation bank (derivative weights, DFT round trip
+    with the sidereal phase) against the oracle's numpy round trip."""
+    import workload.composite as WC
+    rng = np.random.default_rng(11)
+    model = WC.ModeModel(rng, WC.MODES4, 20.0, 1024.0)
+    freq = W.freq_grid(1024.0, 0.25)
+    h = model(freq)
+    got = R.rift_ile_rotation_bank(h, 0.25, 2.0, p_max).cpu().numpy()
+    ref = OP.rotation_bank_fft(h, 0.25, 2.0, p_max)
+    assert got.shape == ref.shape
+    # rows of one derivative order share a scale: compare each row to its own maximum
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.max(np.abs(got - ref) / scale) <= 1e-12

@@ -133,3 +133,27 @@ def test_planted_mistake_is_caught(name):
         text = f.read()
     assert text.count(old) == 1
     assert _battery(_load(text.replace(old, new), name)), name
+
+
+def test_rotation_bank_round_trip_is_exact_for_a_compact_pulse():
+    """For a Gaussian pulse well inside the grid's period the DFT round trip
+    of the bank construction reproduces the analytic spectra of
+    e^{i n Omega t} d^p h/dt^p: (2 pi i f')^p h(f'), f' = f - n Omega / 2 pi."""
+    df, fmax, sig, om = 0.25, 64.0, 0.05, 3.0
+    freq = W.freq_grid(fmax, df)
+    def pulse(f, t0=0.2, phase=0.7):
+        return np.exp(-0.5 * (2 * np.pi * f * sig) ** 2 - 2j * np.pi * f * t0 + 1j * phase)
+    h = np.stack([pulse(freq), pulse(freq, -0.3, 1.9)])
+    bank = OP.rotation_bank_fft(h, df, om, 2)
+    rows = []
+    for p in range(3):
+        for n in range(-(2 + p), 3 + p):
+            fs = freq - n * om / (2 * np.pi)
+            rows.append(np.stack([(2j * np.pi * fs) ** p * pulse(fs),
+                                  (2j * np.pi * fs) ** p * pulse(fs, -0.3, 1.9)]))
+    ref = np.concatenate(rows)
+    assert bank.shape == ref.shape
+    assert np.max(np.abs(bank - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # no modulation: the identity (up to the derivative weights)
+    b0 = OP.rotation_bank_fft(h, df, 0.0, 0)
+    assert np.max(np.abs(b0[4:6] - h)) <= 1e-14
