@@ -74,6 +74,16 @@ int rift_ile_precompute(const rift_ile_precompute_desc* desc, void* Q_out, doubl
 int rift_ile_rotation_bank(const double* hlm, int32_t n_modes, int32_t nf, double df,
                            double omega, int32_t p_max, double* bank_out, void* stream);
 
+/* The finite-arm bank of Sec. III.B (Path D): chi^(p)_lm(f) =
+ * e^{-2 pi i f T} W_p(pi f T) h_lm(f), p = 0..p_max (eq. fsize:factorization),
+ * with W_p the Taylor coefficients in u of the residual arm transfer D^(u, x)
+ * (eq. fsize:Wp), taken by a 64-point Cauchy integral over |u| = 1 (D^ is
+ * entire in u) for each frequency; T is the detector's one-way light time
+ * L / c, seconds.  Rows p * M + i of bank_out DEVICE [(p_max + 1) M][nf]
+ * complex128.  Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA. */
+int rift_ile_arm_bank(const double* hlm, int32_t n_modes, int32_t nf, double df, double T,
+                      int32_t p_max, double* bank_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,8 @@ products equals rho^2/2 at the injection.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 
@@ -85,3 +87,44 @@ def rotation_bank_fft(hlm, df, omega, p_max):
             Ys = np.fft.fft(y, axis=1) / nf
             rows.append(Ys[:, perm])
     return np.concatenate(rows)
+
+
+def _sinc_derivs(y, kmax):
+    """d^k sinc / dy^k at y for k <= kmax, from sinc(y) = int_0^1 cos(y s) ds:
+    the k-th derivative is int_0^1 s^k cos(y s + k pi/2) ds (Gauss-Legendre)."""
+    s, w = np.polynomial.legendre.leggauss(64)
+    s = 0.5 * (s + 1.0)
+    w = 0.5 * w
+    y = np.asarray(y, dtype=np.float64)
+    return np.stack([np.sum(w * s ** k * np.cos(np.multiply.outer(y, s) + k * np.pi / 2), axis=-1)
+                     for k in range(kmax + 1)])
+
+
+def arm_weights_series(x, p_max):
+    """W_p(x), p <= p_max, of eq. fsize:Wp: the Taylor coefficients in u of
+    D^(u, x) = 1/2 [e^{i x (1-u)} sinc(x(1+u)) + e^{-i x (1+u)} sinc(x(1-u))]
+    (eq. slowrot:armtransfer without its common delay) as the Cauchy products
+    of the series of e^{-i x u} and of sinc(x (1 +- u))."""
+    x = np.asarray(x, dtype=np.float64)
+    sd = _sinc_derivs(x, p_max)                      # [p_max + 1][...]
+    fact = np.array([math.factorial(k) for k in range(p_max + 1)], dtype=np.float64)
+    e = np.stack([(-1j * x) ** k / fact[k] for k in range(p_max + 1)])
+    sp = np.stack([sd[k] * x ** k / fact[k] for k in range(p_max + 1)])
+    sm = np.stack([sd[k] * (-x) ** k / fact[k] for k in range(p_max + 1)])
+    out = []
+    for p in range(p_max + 1):
+        a = sum(e[p - j] * sp[j] for j in range(p + 1))
+        b = sum(e[p - j] * sm[j] for j in range(p + 1))
+        out.append(0.5 * (np.exp(1j * x) * a + np.exp(-1j * x) * b))
+    return np.stack(out)
+
+
+def arm_bank(hlm, df, T, p_max):
+    """The finite-arm bank chi^(p)_lm(f) = e^{-2 pi i f T} W_p(pi f T) h_lm(f)
+    (eq. fsize:factorization) on the two-sided grid: [(p_max + 1) M][nf]."""
+    hlm = np.asarray(hlm, dtype=np.complex128)
+    M, nf = hlm.shape
+    f = (np.arange(nf) - (nf - 1) // 2) * df
+    W = arm_weights_series(np.pi * f * T, p_max)
+    shift = np.exp(-2j * np.pi * f * T)
+    return np.concatenate([W[p][None, :] * shift[None, :] * hlm for p in range(p_max + 1)])

@@ -835,3 +835,21 @@ def rift_ile_rotation_bank(hlm, df: float, omega: float, p_max: int, device=None
         _check(_lib.rift_ile_rotation_bank(h.data_ptr(), M, nf, float(df), float(omega), int(p_max),
                                            out.data_ptr(), _stream(stream)))
     return out
+
+
+_lib.rift_ile_arm_bank.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int32, _P, _P]
+
+
+def rift_ile_arm_bank(hlm, df: float, T: float, p_max: int, device=None, stream=None):
+    """The finite-arm bank chi^(p)_lm = e^{-2 pi i f T} W_p(pi f T) h_lm
+    [(p_max + 1) M, nf] (complex128 CUDA tensor), T the one-way light time."""
+    torch = _torch()
+    device = torch.device(device or "cuda")
+    h = _dev_tensor(hlm, torch.complex128, device)
+    M, nf = h.shape
+    out = torch.empty(((p_max + 1) * M, nf), dtype=torch.complex128, device=device)
+    with torch.cuda.device(device):
+        _check(_lib.rift_ile_arm_bank(h.data_ptr(), M, nf, float(df), float(T), int(p_max),
+                                      out.data_ptr(), _stream(stream)))
+    return out

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/rift_ile_precompute.h"
+#include "../../include/rift_ile_response.h"
 #include "kernels.h"
 #include "rift_ile_internal.h"
 
@@ -25,6 +26,10 @@ namespace rift {
 namespace {
 
 constexpr int kUvThreads = 256;
+
+__device__ __forceinline__ double2 cmul_pc(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
 
 struct Times {
   double t0[kMaxDet];
@@ -410,4 +415,99 @@ extern "C" int rift_ile_rotation_bank(const double* hlm, int32_t n_modes, int32_
   cudaFreeAsync(Z, st);
   if (rc) return rc;
   return check_cuda(e, "rift_ile_rotation_bank");
+}
+
+// ------------------------------------------------------- finite-arm bank
+
+namespace rift {
+namespace {
+
+constexpr int kCauchyNodes = 64;
+
+__device__ __forceinline__ double2 csin_d(double2 z) {  // sin(a + i b)
+  double sa, ca;
+  sincos(z.x, &sa, &ca);
+  return make_double2(sa * cosh(z.y), ca * sinh(z.y));
+}
+
+__device__ __forceinline__ double2 cdiv_d(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__device__ __forceinline__ double2 csinc_d(double2 z) {
+  if (z.x * z.x + z.y * z.y < 1e-16) {  // 1 - z^2/6, error ~ |z|^4/120
+    return make_double2(1.0 - (z.x * z.x - z.y * z.y) / 6.0, -(2.0 * z.x * z.y) / 6.0);
+  }
+  return cdiv_d(csin_d(z), z);
+}
+
+// e^{a + i b}
+__device__ __forceinline__ double2 cexp_d(double a, double b) {
+  double s, c;
+  sincos(b, &s, &c);
+  const double e = exp(a);
+  return make_double2(e * c, e * s);
+}
+
+__global__ void arm_bank_kernel(const double2* __restrict__ hlm, int M, int nf, double df, double T,
+                                int p_max, double2* __restrict__ bank) {
+  const int nh = (nf - 1) / 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += gridDim.x * blockDim.x) {
+    const double f = (double)(q - nh) * df;
+    const double x = CUDART_PI * f * T;
+    double2 W[RIFT_ILE_MAX_ARM_PMAX + 1];
+    for (int p = 0; p <= p_max; ++p) W[p] = make_double2(0.0, 0.0);
+    for (int j = 0; j < kCauchyNodes; ++j) {
+      double s, c;
+      sincospi(2.0 * j / kCauchyNodes, &s, &c);  // u = c + i s on the unit circle
+      // D^ = 1/2 [e^{i x (1-u)} sinc(x (1+u)) + e^{-i x (1+u)} sinc(x (1-u))]
+      const double2 t1 = cmul_pc(cexp_d(x * s, x * (1.0 - c)), csinc_d(make_double2(x * (1.0 + c), x * s)));
+      const double2 t2 = cmul_pc(cexp_d(x * s, -x * (1.0 + c)), csinc_d(make_double2(x * (1.0 - c), -x * s)));
+      const double2 D = make_double2(0.5 * (t1.x + t2.x), 0.5 * (t1.y + t2.y));
+      // W_p += D e^{-i p phi_j} / N
+      double2 e = make_double2(1.0, 0.0);
+      for (int p = 0; p <= p_max; ++p) {
+        const double2 t = cmul_pc(D, e);
+        W[p].x += t.x / kCauchyNodes;
+        W[p].y += t.y / kCauchyNodes;
+        e = cmul_pc(e, make_double2(c, -s));
+      }
+    }
+    double sd, cd;
+    sincospi(-2.0 * f * T, &sd, &cd);
+    const double2 delay = make_double2(cd, sd);
+    for (int p = 0; p <= p_max; ++p) {
+      const double2 wp = cmul_pc(W[p], delay);
+      for (int i = 0; i < M; ++i)
+        bank[((long long)p * M + i) * nf + q] = cmul_pc(wp, hlm[(long long)i * nf + q]);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace rift
+
+extern "C" int rift_ile_arm_bank(const double* hlm, int32_t n_modes, int32_t nf, double df, double T,
+                                 int32_t p_max, double* bank_out, void* stream) {
+  using namespace rift;
+  if (!hlm || !bank_out) {
+    rift_ile_set_error("rift_ile_arm_bank: hlm or bank_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (n_modes < 1 || n_modes > RIFT_ILE_MAX_MODES || p_max < 0 || p_max > RIFT_ILE_MAX_ARM_PMAX) {
+    rift_ile_set_error("rift_ile_arm_bank: n_modes=%d or p_max=%d unsupported", n_modes, p_max);
+    return RIFT_ILE_ERR_UNSUPPORTED;
+  }
+  if (nf < 1 || nf % 2 == 0) {
+    rift_ile_set_error("rift_ile_arm_bank: nf=%d must be odd and positive", nf);
+    return RIFT_ILE_ERR_SHAPE;
+  }
+  if (!(df > 0.0) || !std::isfinite(df) || !(T >= 0.0) || !std::isfinite(T)) {
+    rift_ile_set_error("rift_ile_arm_bank: df must be positive and T finite, non-negative");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  arm_bank_kernel<<<blocks_for(nf), 256, 0, (cudaStream_t)stream>>>((const double2*)hlm, n_modes, nf, df,
+                                                                    T, p_max, (double2*)bank_out);
+  return check_cuda(cudaGetLastError(), "rift_ile_arm_bank launch");
 }

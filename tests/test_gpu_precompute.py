@@ -124,3 +124,19 @@ def test_rotation_bank_matches_oracle(R, p_max):
     # rows of one derivative order share a scale: compare each row to its own maximum
     scale = np.max(np.abs(ref), axis=1, keepdims=True)
     assert np.max(np.abs(got - ref) / scale) <= 1e-12
+
+
+@pytest.mark.parametrize("p_max", [0, 3, 6])
+def test_arm_bank_matches_oracle(R, p_max):
+    """The finite-arm bank (Cauchy-integral W_p on the GPU) against the
+    oracle's series construction, on 40 km arms up to 2048 Hz."""
+    import workload.composite as WC
+    rng = np.random.default_rng(12)
+    model = WC.ModeModel(rng, WC.MODES4, 20.0, 2048.0)
+    freq = W.freq_grid(2048.0, 0.25)
+    h = model(freq)
+    T = 4.0e4 / W.C_LIGHT
+    got = R.rift_ile_arm_bank(h, 0.25, T, p_max).cpu().numpy()
+    ref = OP.arm_bank(h, 0.25, T, p_max)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))

@@ -157,3 +157,23 @@ def test_rotation_bank_round_trip_is_exact_for_a_compact_pulse():
     # no modulation: the identity (up to the derivative weights)
     b0 = OP.rotation_bank_fft(h, df, 0.0, 0)
     assert np.max(np.abs(b0[4:6] - h)) <= 1e-14
+
+
+def test_arm_weights_series():
+    """W_0 = sinc(x) cos x; the series in u sums back to the two-leg transfer
+    function for |u| <= 1; the arm bank at p_max = 0 is the tapered,
+    delayed mode."""
+    x = np.linspace(-1.2, 1.2, 25)
+    W = OP.arm_weights_series(x, 30)
+    assert np.max(np.abs(W[0] - np.sinc(x / np.pi) * np.cos(x))) <= 1e-14
+    for u in (-1.0, -0.4, 0.3, 0.9):
+        def sinc(z):
+            return np.where(np.abs(z) < 1e-12, 1.0 + 0j, np.sin(z + 0j) / np.where(z == 0, 1, z))
+        full = 0.5 * (np.exp(1j * x * (1 - u)) * sinc(x * (1 + u))
+                      + np.exp(-1j * x * (1 + u)) * sinc(x * (1 - u)))
+        assert np.max(np.abs(np.tensordot(u ** np.arange(31), W, axes=1) - full)) <= 1e-13
+    freq = np.arange(-8, 9) * 0.5
+    h = np.exp(1j * freq)[None, :]
+    b = OP.arm_bank(h, 0.5, 1e-4, 0)
+    xx = np.pi * freq * 1e-4
+    assert np.max(np.abs(b[0] - np.sinc(xx / np.pi) * np.cos(xx) * np.exp(-2j * np.pi * freq * 1e-4) * h[0])) <= 1e-15
