@@ -636,6 +636,11 @@ def run_precompute(args):
         for _ in range(args.warmup):
             call()
         ms = timed_events(torch, call, max(10, min(args.steps, 50)), stream)
+    # the widened banks of Sec. III on the same modes (rotation p_max 1, 40 km arms p_max 3)
+    ms_rot = timed_events(torch, lambda: R.rift_ile_rotation_bank(hlm, df, 7.2921159e-5, 1), 10,
+                          stream)
+    ms_arm = timed_events(torch, lambda: R.rift_ile_arm_bank(hlm, df, 4.0e4 / 299792458.0, 3), 10,
+                          stream)
     Qg = call()[0].cpu().numpy()
     t0 = time.perf_counter()
     Qf = W.q_table(exact["wgt"], exact["hlm"], exact["dk"], exact["freq"], df, point["q_t0"],
@@ -663,6 +668,7 @@ def run_precompute(args):
                      "peak_source": f"measured FP64 FMA rate at {probe_mhz:.0f} MHz "
                                     "(rift_ile_probe_alu)"},
         "numpy_fft_builder_ms": numpy_s * 1e3, "speedup_vs_numpy_fft": numpy_s * 1e3 / ms,
+        "rotation_bank_p1_ms": ms_rot, "arm_bank_p3_ms": ms_arm,
         "cpu_baseline": {"value": oracle_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
                          "sample": f"direct sums of eq. QUV for {len(rows)} table rows of "
                                    "detector 0, scaled to the whole table"},
