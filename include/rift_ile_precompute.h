@@ -15,7 +15,9 @@
  * (cuFFT, double complex, batched): the frequency series times
  * e^{2 pi i f t0} is scattered to the FFT bins f / df mod nfft, which makes
  * sample j of the transform exactly the sum above at t0 + j dt.  U and V are
- * per-(k, i, j) block reductions in a fixed order (bitwise reproducible).
+ * block reductions in a fixed order (bitwise reproducible) over the pairs
+ * i <= j, the rest filled by U_ji = conj(U_ij) and V_ji = V_ij: the weights
+ * must be even in f (w_k(-f) = w_k(f), as for a one-sided noise curve).
  *
  * Requirements: 1 / (df q_dt) within 1e-9 of an integer nfft >= max(nf,
  * q_len); nf odd; K <= RIFT_ILE_MAX_DET, M <= RIFT_ILE_MAX_MODES.

@@ -7,8 +7,9 @@
 // unnormalised, e^{+2 pi i b j / nfft}) turns bin b = f/df into
 // e^{2 pi i f j dt}, so output j is Q_{k,i}(t0_k + j dt) exactly as the sum of
 // eq. QUV; a gather kernel transposes the first q_len samples to [K][n][M].
-// U, V: one block per (k, i, j), each thread a fixed strided subset of the
-// frequencies, a fixed shared-memory tree: reproducible bit for bit.
+// U, V: one block per (k, i <= j) (U Hermitian, V symmetric), each thread a
+// fixed strided subset of the frequencies, a fixed shared-memory tree:
+// reproducible bit for bit.
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <math_constants.h>
@@ -85,9 +86,15 @@ __global__ void __launch_bounds__(kUvThreads) uv_kernel(const double2* __restric
                                                         const double* __restrict__ wgt, int M,
                                                         int nf, double2* __restrict__ U,
                                                         double2* __restrict__ V) {
-  const int j = blockIdx.x % M;
-  const int i = (blockIdx.x / M) % M;
-  const int k = blockIdx.x / (M * M);
+  // one block per (k, i <= j): U is Hermitian and V symmetric by construction
+  const int npair = M * (M + 1) / 2;
+  const int k = blockIdx.x / npair;
+  int r = blockIdx.x % npair, i = 0;
+  while (r >= M - i) {
+    r -= M - i;
+    ++i;
+  }
+  const int j = i + r;
   const double2* hi = hlm + (long long)i * nf;
   const double2* hj = hlm + (long long)j * nf;
   const double* w = wgt + (long long)k * nf;
@@ -113,9 +120,15 @@ __global__ void __launch_bounds__(kUvThreads) uv_kernel(const double2* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const long long o = ((long long)k * M + i) * M + j;
-    if (U) U[o] = make_double2(red[0][0], red[1][0]);
-    if (V) V[o] = make_double2(red[2][0], red[3][0]);
+    const long long o = ((long long)k * M + i) * M + j, ot = ((long long)k * M + j) * M + i;
+    if (U) {
+      U[o] = make_double2(red[0][0], red[1][0]);
+      U[ot] = make_double2(red[0][0], -red[1][0]);
+    }
+    if (V) {
+      V[o] = make_double2(red[2][0], red[3][0]);
+      V[ot] = V[o];
+    }
   }
 }
 
@@ -224,7 +237,7 @@ extern "C" int rift_ile_precompute(const rift_ile_precompute_desc* d, void* Q_ou
   cudaStream_t st = (cudaStream_t)stream;
   const int K = d->n_det, M = d->n_modes, nf = d->nf;
   if (U_out || V_out) {
-    uv_kernel<<<K * M * M, kUvThreads, 0, st>>>((const double2*)d->hlm, d->wgt, M, nf,
+    uv_kernel<<<K * M * (M + 1) / 2, kUvThreads, 0, st>>>((const double2*)d->hlm, d->wgt, M, nf,
                                                  (double2*)U_out, (double2*)V_out);
     if ((rc = check_cuda(cudaGetLastError(), "uv_kernel launch"))) return rc;
   }
