@@ -260,3 +260,26 @@ def test_detector_classes_and_per_detector_path(R, kind, p_max, lengths):
     for j, p in enumerate(W.PARAMS):
         s = np.abs(ref_g[:, j]) + np.sqrt(np.mean(ref_g[:, j] ** 2))
         assert np.max(np.abs(g[j] - ref_g[:, j]) / s) <= 1e-7, p
+
+
+def test_graph_capture_of_the_fused_step(R):
+    """The asynchronous composite lnZ step (fused kernel + merge, no host
+    synchronisation) can be captured in a CUDA graph and replayed, with the
+    result equal bit for bit to the eager step."""
+    point, exact, info, draws, logw = fixture(WC.ROTATION, 0)
+    cp = R.CompPoint(point)
+    d = R.Draws(draws, logw)
+    eager = R.rift_ile_comp_lnZ_state_async(cp, d).clone()
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s2):
+        R.rift_ile_comp_lnZ_state_async(cp, d, out=out)
+    torch.cuda.current_stream().wait_stream(s2)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        R.rift_ile_comp_lnZ_state_async(cp, d, out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
