@@ -31,6 +31,9 @@
 namespace rift {
 namespace {
 
+#ifndef RIFT_DIRECT_MIN_BLOCKS
+#define RIFT_DIRECT_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
+#endif
 constexpr int kDirWarps = 4;
 constexpr int kHm = 2 * kMaxEll + 1;        // data harmonics m = -8..8
 constexpr int kHn = 4 * kMaxEll + 1;        // norm harmonics -16..16
@@ -277,7 +280,7 @@ __device__ __forceinline__ void lse_add(double& m, double& s, double v) {
 }
 
 template <int MM>
-__global__ void __launch_bounds__(32 * kDirWarps) direct_kernel(const PointParams* __restrict__ gP,
+__global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct_kernel(const PointParams* __restrict__ gP,
                                                                 DrawsParams dp,
                                                                 const __grid_constant__ DirectParams Q,
                                                                 double* __restrict__ out) {
