@@ -73,7 +73,8 @@ typedef enum {
  *                 Q_{k,A}(q_t0[k] + j q_dt), n_comp = n_index * M
  *   U, V          HOST [K][n_comp][n_comp][2] double: <chi_A|chi_B>_k and
  *                 <chi_A^*|chi_B>_k
- *   the other fields as in rift_ile_point_desc (det_resp is used by ROTATION). */
+ *   the other fields as in rift_ile_point_desc; det_resp is required for
+ *   ROTATION and may be NULL for FINITE_ARM (the arms define the response). */
 typedef struct {
   int32_t n_det;
   int32_t n_modes;

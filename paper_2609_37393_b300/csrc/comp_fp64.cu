@@ -416,7 +416,8 @@ int validate_comp(const rift_ile_comp_desc* d, int* na_out) {
                        d->n_modes, na * d->n_modes);
     return RIFT_ILE_ERR_UNSUPPORTED;
   }
-  if (!d->ell || !d->em || !d->Q || !d->q_t0 || !d->U || !d->V || !d->det_pos || !d->det_resp ||
+  if (!d->ell || !d->em || !d->Q || !d->q_t0 || !d->U || !d->V || !d->det_pos ||
+      (d->kind == RIFT_ILE_RESP_ROTATION && !d->det_resp) ||
       (d->kind == RIFT_ILE_RESP_FINITE_ARM && (!d->arm_x || !d->arm_y))) {
     rift_ile_set_error("a required array of the composite description is NULL");
     return RIFT_ILE_ERR_INVALID_ARG;
@@ -436,7 +437,8 @@ int validate_comp(const rift_ile_comp_desc* d, int* na_out) {
       return RIFT_ILE_ERR_UNSUPPORTED;
     }
   const size_t K = d->n_det, Ac = (size_t)na * d->n_modes;
-  if (!finite_all(d->q_t0, K) || !finite_all(d->det_pos, 3 * K) || !finite_all(d->det_resp, 6 * K) ||
+  if (!finite_all(d->q_t0, K) || !finite_all(d->det_pos, 3 * K) ||
+      (d->det_resp && !finite_all(d->det_resp, 6 * K)) ||
       !finite_all(d->U, 2 * K * Ac * Ac) || !finite_all(d->V, 2 * K * Ac * Ac) ||
       (d->kind == RIFT_ILE_RESP_FINITE_ARM &&
        (!finite_all(d->arm_x, 3 * K) || !finite_all(d->arm_y, 3 * K)))) {
@@ -495,7 +497,7 @@ extern "C" int rift_ile_comp_create(const rift_ile_comp_desc* d, rift_ile_comp**
         C.army[k][c] = d->arm_y[3 * k + c];
       }
     }
-    for (int c = 0; c < 6; ++c) C.resp[k][c] = d->det_resp[6 * k + c];
+    for (int c = 0; c < 6; ++c) C.resp[k][c] = d->det_resp ? d->det_resp[6 * k + c] : 0.0;
   }
 
   PointParams B;
