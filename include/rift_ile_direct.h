@@ -55,6 +55,16 @@ typedef struct {
 int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draws* draws,
                         const rift_ile_direct_rule* rule, double* out, void* stream);
 
+/* The Monte Carlo evidence over the sampled coordinates with the direct
+ * marginal as the integrand: the LSE state (see rift_ile_lse) of
+ * ln L_dir_i + ln w_i over the draws (eq. lnL:MonteCarlo), written to DEVICE
+ * state_out without a host synchronisation; `scratch` is DEVICE [n] doubles
+ * for the per-draw values (may alias nothing else).  Errors as
+ * rift_ile_lnL_direct. */
+int rift_ile_lnZ_direct_state(const rift_ile_point* pt, const rift_ile_draws* draws,
+                              const rift_ile_direct_rule* rule, double* scratch,
+                              rift_ile_lse* state_out, void* stream);
+
 /* The Gauss-Hermite rule the kernel uses (weight e^{-x^2}): HOST x[n], w[n]. */
 int rift_ile_gauss_hermite(int32_t n, double* x, double* w);
 

@@ -853,3 +853,22 @@ def rift_ile_arm_bank(hlm, df: float, T: float, p_max: int, device=None, stream=
         _check(_lib.rift_ile_arm_bank(h.data_ptr(), M, nf, float(df), float(T), int(p_max),
                                       out.data_ptr(), _stream(stream)))
     return out
+
+
+_lib.rift_ile_lnZ_direct_state.argtypes = [_P, _P, _P, _P, _P, _P]
+
+
+def rift_ile_lnZ_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
+                        d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
+                        stream=None):
+    """(lnZ, sigma_lnZ, n_eff) of the draws with the direct marginal as the
+    integrand (the LSE state formed on the device, merged on the host)."""
+    torch = _torch()
+    d = _as_draws(draws)
+    scratch = torch.empty(max(d.n, 1), dtype=torch.float64, device=point.device)
+    state = torch.empty(4, dtype=torch.float64, device=point.device)
+    r = _DirectRule(int(n_phi), int(n_psi), int(n_gh), float(d_min), float(d_max), int(n_t),
+                    float(t_lo), float(t_hi))
+    _check(_lib.rift_ile_lnZ_direct_state(point.handle, d.ref, ctypes.byref(r), scratch.data_ptr(),
+                                          state.data_ptr(), _stream(stream)))
+    return rift_ile_lnZ_merge([tuple(state.cpu().tolist())])[0]

@@ -525,3 +525,43 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   return check_cuda(launch_direct(hp, pt->dev, draws_params(draws), Q, out, (cudaStream_t)stream),
                     "rift_ile_lnL_direct launch");
 }
+
+namespace rift {
+namespace {
+
+// LSE partials of values[i] + logw[i], one per block (fixed reduction order).
+__global__ void __launch_bounds__(256) lse_array_kernel(const double* __restrict__ v, DrawsParams dp,
+                                                        LseState* __restrict__ partials) {
+  ThreadLse64 st = tlse64_init();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride)
+    tlse64_push(st, v[i] + load_logw_d(dp, i));
+  block_lse64_write(st, partials + blockIdx.x);
+}
+
+}  // namespace
+}  // namespace rift
+
+extern "C" int rift_ile_lnZ_direct_state(const rift_ile_point* pt, const rift_ile_draws* draws,
+                                         const rift_ile_direct_rule* rule, double* scratch,
+                                         rift_ile_lse* state_out, void* stream) {
+  using namespace rift;
+  if (!state_out || (!scratch && draws && draws->n > 0)) {
+    rift_ile_set_error("rift_ile_lnZ_direct_state: state_out or scratch is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  int rc = rift_ile_lnL_direct(pt, draws, rule, scratch, stream);
+  if (rc) return rc;
+  LseState *partials = nullptr, *state = nullptr;
+  unsigned long long* oob = nullptr;
+  if ((rc = lse_workspace(&partials, &state, &oob))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  LseState* out = reinterpret_cast<LseState*>(state_out);
+  if (draws->n == 0)
+    return check_cuda(launch_lse_combine(partials, 0, 0.0, out, st), "lnZ combine launch");
+  const int blocks = grid_cap(device_sms() * 4, draws->n, 256);
+  lse_array_kernel<<<blocks, 256, 0, st>>>(scratch, draws_params(draws), partials);
+  if ((rc = check_cuda(cudaGetLastError(), "lse_array_kernel launch"))) return rc;
+  return check_cuda(launch_lse_combine(partials, blocks, (double)draws->n, out, st),
+                    "lnZ combine launch");
+}

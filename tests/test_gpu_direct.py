@@ -73,3 +73,17 @@ def test_invalid_rules(R):
                  (8, 8, 16, 50.0, 200.0, 4, 0.01, -0.01)):
         with pytest.raises(R.RiftError):
             R.rift_ile_lnL_direct(pt, d, *args)
+
+
+def test_lnz_with_the_direct_marginal(R):
+    """The evidence over (ra, dec, incl, t) draws with the direct marginal as
+    integrand equals the oracle's LSE of the oracle's per-draw values."""
+    import oracle as O
+    point, exact, info, draws, logw = W.config0(n_draws=48)
+    pt = R.Point(point)
+    args = (64, 32, 16, 50.0, 200.0)
+    z = R.rift_ile_lnZ_direct(pt, R.Draws(draws), *args)
+    ref = OD.lnL_direct(point, draws, *args)
+    zr = O.lnZ(ref, np.zeros(len(ref)))
+    assert abs(z[0] - zr[0]) <= 1e-9 * max(1.0, abs(zr[0]))
+    assert abs(z[2] - zr[2]) <= 1e-7 * zr[2]
