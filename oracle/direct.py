@@ -8,7 +8,8 @@ For one draw of the sampled coordinates (ra, dec, incl, t_c) it computes
 
     L_dir = int dphi dpsi dx  p(phi) p(psi) p_x(x) exp[lnL(phi, psi, x)],
 
-and optionally integrates t_c as well (fixed-spacing rule, eq. ap:tfixed).
+and optionally integrates t_c as well (fixed-spacing rule, eq. ap:tfixed, or
+the band-limited full-window rule, eq. ap:tband).
 
 following the paper's steps:
 
@@ -96,14 +97,38 @@ def distance_gh(K, R, d_ref, d_min, d_max, n_gh):
         return K * K / (2.0 * R) + np.log(math.sqrt(2.0) * sig * s)
 
 
+def sinc_upsample(coarse, t_up: int):
+    """The band-limited reconstruction of eq. ap:tband: samples taken at
+    spacing h on the midpoints (j + 1/2) h, j < n, are carried to the t_up
+    fine midpoints of each interval, (f + 1/2) h / t_up, f < n t_up, by
+    sum_j value_j sinc((t_f - t_j) / h), sinc(x) = sin(pi x)/(pi x) (eq.
+    ap:sinc), the sum running over the n samples of the window.  `coarse` is
+    [n, ...]; returns [n t_up, ...]."""
+    coarse = np.asarray(coarse)
+    n = coarse.shape[0]
+    tf = (np.arange(n * t_up) + 0.5) / t_up          # fine times in units of h
+    tj = np.arange(n) + 0.5
+    S = np.sinc(np.subtract.outer(tf, tj))            # numpy's sinc is sin(pi x)/(pi x)
+    return np.tensordot(S, coarse, axes=1)
+
+
 def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
-               d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0):
+               d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
+               t_up: int = 1):
     """ln L_dir per draw.  With n_t = 0 the draw's t is used; otherwise t is
     integrated too, by the fixed-spacing rule of eq. ap:tfixed on n_t
     midpoints t_j = t_lo + (j + 1/2) h, h = (t_hi - t_lo)/n_t, with the
     uniform prior on [t_lo, t_hi] (weight 1/n_t per node); the harmonic model
     is reconstructed at every time node before any integration, as the
-    fixed-time qualification of App. F.1 requires."""
+    fixed-time qualification of App. F.1 requires.
+
+    With t_up > 1 the band-limited full-window rule of eq. ap:tband: the data
+    term's harmonic coefficients (linear in Q, hence band limited) are
+    reconstructed at the n_t coarse midpoints, carried to t_up fine midpoints
+    per interval by ``sinc_upsample``, and the angular and distance integrals
+    run at each of the n_t t_up fine nodes (weight 1/(n_t t_up)).  The model
+    norm does not depend on t at a fixed sky position; it is taken from the
+    first coarse node."""
     pt = OraclePoint(point)
     th = {p: np.asarray(draws[p], dtype=np.float64) for p in PARAMS}
     N = th["ra"].shape[0]
@@ -119,9 +144,14 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
             lnwt = -math.log(n_t)
         else:
             times, lnwt = [th["t"][i]], 0.0
+        coefs = [reconstruct(pt, point, th["ra"][i], th["dec"][i], th["incl"][i], t)[:2]
+                 for t in times]
+        if n_t > 0 and t_up > 1:
+            cR = coefs[0][1]
+            coefs = [(cK, cR) for cK in sinc_upsample(np.stack([c[0] for c in coefs]), t_up)]
+            lnwt = -math.log(n_t * t_up)
         vals = []
-        for t in times:
-            cK, cR, _ = reconstruct(pt, point, th["ra"][i], th["dec"][i], th["incl"][i], t)
+        for cK, cR in coefs:
             K = evaluate(cK, PS, PH)
             R = evaluate(cR, PS, PH)
             vals.append(distance_gh(K, R, point["d_ref"], d_min, d_max, n_gh) + lnw + lnwt)

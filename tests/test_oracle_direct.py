@@ -9,7 +9,12 @@ Gauss-Hermite in distance), against things other than itself:
   (phi, psi) grid, distance by adaptive quadrature) on the two-detector
   workload, and changes little when the angle grid is refined;
 * planted mistakes (a too-small phase grid, a lost sqrt(2), the wrong
-  distance prior power) each fail one of these.
+  distance prior power) each fail one of these;
+* the band-limited time rule (eq. ap:tband): its sinc reconstruction of the
+  data coefficients converges to the coefficients evaluated at the fine
+  times as the window widens, the rule agrees with the fixed-spacing rule
+  evaluated directly on the same fine nodes, and fine nodes misplaced by half
+  an interval are caught.
 """
 import importlib.util
 import math
@@ -160,3 +165,82 @@ def test_time_rule_converges_and_reduces():
     # algebraically: each doubling cuts the change by more than 4
     d1, d2 = abs(vals[1] - vals[0]), abs(vals[2] - vals[1])
     assert d2 <= 0.25 * d1 and d2 <= 5e-4, vals
+
+
+def _fine_table_point():
+    """Noise-free two-detector point whose Q table is sampled at 16 384 Hz
+    (band limit 512 Hz), so that the table cubic is exact to ~1e-5 and the
+    data coefficients reconstructed at any time stand in for the band-limited
+    correlation itself."""
+    rng = np.random.default_rng(41)
+    dets = W.random_l_detectors(rng, 2)
+    truth = W.default_truth(rng, 100.0)
+    point, exact, info = W.make_point(
+        dets=dets, modes=W.MODES10[:4], f_low=20.0, f_max=512.0, df=0.5, rate=16384.0,
+        half_window=0.03, snr=20.0, truth=truth, gmst=0.4, d_ref=100.0, rng=rng, noise=False,
+        q_dtype=np.complex128)
+    return point, info
+
+
+def _tband_error(mod, half):
+    """Largest error, relative to the largest coefficient, of the sinc
+    reconstruction (coarse spacing h = 1/2048 s, 4 fine nodes per interval)
+    against the directly reconstructed data coefficients at the fine nodes of
+    the two central coarse intervals, for a window of `half` coarse samples on
+    each side of the peak."""
+    point, info = _fine_table_point()
+    pt = O.OraclePoint(point)
+    tr = info["truth"]
+    h, M = 1.0 / 2048, 4
+    t_lo = tr["t"] - half * h
+    times = t_lo + (np.arange(2 * half) + 0.5) * h
+    cK = np.stack([mod.reconstruct(pt, point, tr["ra"], tr["dec"], tr["incl"], t)[0]
+                   for t in times])
+    up = mod.sinc_upsample(cK, M)
+    mid = np.arange(half * M - 2 * M, half * M + 2 * M)
+    direct = np.stack([mod.reconstruct(pt, point, tr["ra"], tr["dec"], tr["incl"],
+                                       t_lo + (f + 0.5) * h / M)[0] for f in mid])
+    return np.max(np.abs(up[mid] - direct)) / np.max(np.abs(direct))
+
+
+def test_band_limited_reconstruction_converges_to_the_correlation():
+    """eq. ap:tband: the sinc-interpolated data coefficients approach the
+    correlation evaluated at the fine times as the window widens (the
+    truncated stencil is the only error: the coefficients are linear in the
+    band-limited Q); at t_up = 1 the upsampling is the identity."""
+    errs = [_tband_error(OD, half) for half in (8, 16, 32)]
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] <= 1e-4, errs
+    x = np.random.default_rng(2).normal(size=(7, 3))
+    assert np.max(np.abs(OD.sinc_upsample(x, 1) - x)) <= 1e-15
+
+
+def test_band_limited_rule_matches_the_fine_fixed_rule():
+    """With the peak well inside the window, the band-limited rule on n_t
+    coarse nodes x t_up equals the fixed-spacing rule evaluated directly at
+    the same n_t t_up fine nodes (same weights), up to the reconstruction
+    error; t_up = 1 is the fixed-spacing rule itself."""
+    point, info = _fine_table_point()
+    tr = info["truth"]
+    d = {p: np.array([tr[p]]) for p in W.PARAMS}
+    h, half = 1.0 / 2048, 32
+    lo, hi = tr["t"] - half * h, tr["t"] + half * h
+    band = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4)[0]
+    fine = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 8 * half, lo, hi)[0]
+    coarse = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi)[0]
+    same = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 1)[0]
+    # the truncated stencil leaves ~4e-6 of K at the peak (K ~ 370 at x = 1)
+    assert abs(band - fine) <= 2.5e-3, (band, fine)
+    assert abs(same - coarse) == 0.0
+    assert abs(band - coarse) > 10 * abs(band - fine)  # the coarse rule alone is not enough
+
+
+def test_band_limited_offset_mistake_is_caught():
+    """Planted: fine nodes placed at the interval starts instead of their
+    midpoints."""
+    with open(SRC) as f:
+        text = f.read()
+    old = "tf = (np.arange(n * t_up) + 0.5) / t_up"
+    assert text.count(old) == 1
+    mod = _load(text.replace(old, "tf = np.arange(n * t_up) / t_up"), "tband_offset")
+    assert _tband_error(mod, 32) > 1e-2
