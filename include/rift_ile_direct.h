@@ -49,6 +49,19 @@ typedef struct {
   int32_t n_t;    /* 0: use each draw's t; else time nodes of the fixed-spacing rule */
   double t_lo;    /* time window (seconds, n_t > 0): midpoints t_lo + (j + 1/2) h, */
   double t_hi;    /* h = (t_hi - t_lo) / n_t, uniform prior on the window */
+  int32_t t_up;   /* 0 or 1: the fixed-spacing rule (eq. ap:tfixed) on the n_t
+                   * midpoints.  > 1 (needs n_t in 1..1024, n_t t_up <= 2^20):
+                   * the band-limited full-window rule of eq. ap:tband -- the
+                   * data coefficients (linear in Q) are formed at the n_t
+                   * midpoints, carried to t_up fine midpoints per interval,
+                   * t_lo + (f + 1/2) h / t_up, by sum_j c(t_j) sinc((t_f -
+                   * t_j) / h) over the window, sinc(x) = sin(pi x)/(pi x),
+                   * and the angles and distance are integrated at every fine
+                   * node (weight 1 / (n_t t_up)).  The call then allocates a
+                   * stream-ordered scratch of n_t * 17 complex doubles per
+                   * resident warp and frees it before returning.  The stencil
+                   * is truncated at the window: place the window so that the
+                   * correlation has decayed at its ends. */
 } rift_ile_direct_rule;
 
 /* ln L_dir per draw into DEVICE out[n] (double). */

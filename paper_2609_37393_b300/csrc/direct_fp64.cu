@@ -17,6 +17,10 @@
 // A first pass finds the node with the largest K^2/(2R) and evaluates it in
 // full (v0); the second pass skips nodes whose upper bound
 // K^2/(2R) + ln(sqrt(2 pi) sigma_x max p_x) is below v0 - 60.
+// Geocentric time is the draw's own, or integrated over a window: by the
+// fixed-spacing rule (eq. ap:tfixed, the data coefficients formed at every
+// node) or by the band-limited rule (eq. ap:tband, the coefficients formed
+// at coarse nodes and sinc-reconstructed at the fine ones).
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -41,10 +45,12 @@ constexpr double kSkipNat = 60.0;
 
 struct DirectParams {
   int n_phi, n_psi, n_gh, n_t;  // n_t = 0: the draw's own t
+  int t_up;                     // > 1: fine nodes per interval (band-limited rule)
+  double2* slab;                // band-limited rule: n_t * kHm coefficients per warp
   double t_lo, t_h;             // time midpoints t_lo + (j + 1/2) t_h
   double lo, hi;          // prior range of x
   double lnnorm;          // ln of 3 d_ref^3 / (d_max^3 - d_min^3)
-  double lnw;             // -ln(n_phi n_psi max(n_t, 1))
+  double lnw;             // -ln(n_phi n_psi max(n_t, 1) max(t_up, 1))
   double ln_ub;           // ln(sqrt(2 pi) norm lo^-4), the prefactor bound over sigma_x
   double xi[RIFT_ILE_MAX_GH], w[RIFT_ILE_MAX_GH];
 };
@@ -279,6 +285,73 @@ __device__ __forceinline__ void lse_add(double& m, double& s, double v) {
   }
 }
 
+// The angular and distance integral at one time node (coefficients in C),
+// accumulated into the lane's log-sum-exp (m, s).
+__device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectParams& Q, int lane, double& m,
+                                 double& s, bool& nan_seen) {
+  // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
+  double best = -CUDART_INF;
+  long long best_idx = (long long)Q.n_phi * Q.n_psi;
+  for (int a = lane; a < Q.n_phi; a += 32) {
+    double2 D, B;
+    double A;
+    direct_column(C, (double)a / Q.n_phi, D, A, B);
+    for (int b = 0; b < Q.n_psi; ++b) {
+      double s2, c2;
+      sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+      double K, R;
+      direct_node(D, A, B, make_double2(c2, s2), K, R);
+      const double h = (R > 0.0) ? K * K / (2.0 * R) : -CUDART_INF;
+      const long long idx = (long long)a * Q.n_psi + b;
+      if (h > best || (h == best && idx < best_idx)) {
+        best = h;
+        best_idx = idx;
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
+    if (ob > best || (ob == best && oi < best_idx)) {
+      best = ob;
+      best_idx = oi;
+    }
+  }
+  double v0 = -CUDART_INF;
+  if (best_idx < (long long)Q.n_phi * Q.n_psi) {
+    const int a = (int)(best_idx / Q.n_psi), b = (int)(best_idx % Q.n_psi);
+    double2 D, B;
+    double A;
+    direct_column(C, (double)a / Q.n_phi, D, A, B);
+    double s2, c2;
+    sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+    double K, R;
+    direct_node(D, A, B, make_double2(c2, s2), K, R);
+    v0 = direct_distance(Q, K, R);
+  }
+  const double cut = v0 - kSkipNat;
+  // pass 2: the log-sum-exp over the nodes that can matter
+  for (int a = lane; a < Q.n_phi; a += 32) {
+    double2 D, B;
+    double A;
+    direct_column(C, (double)a / Q.n_phi, D, A, B);
+    for (int b = 0; b < Q.n_psi; ++b) {
+      double s2, c2;
+      sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+      double K, R;
+      direct_node(D, A, B, make_double2(c2, s2), K, R);
+      if (isnan(K) || isnan(R)) {
+        nan_seen = true;
+        continue;
+      }
+      if (!(R > 0.0)) continue;
+      const double ub = K * K / (2.0 * R) - 0.5 * log(R) + Q.ln_ub;
+      if (ub < cut) continue;
+      lse_add(m, s, direct_distance(Q, K, R));
+    }
+  }
+}
+
 template <int MM>
 __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct_kernel(const PointParams* __restrict__ gP,
                                                                 DrawsParams dp,
@@ -298,72 +371,46 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
     direct_norm_warp<MM>(P, g, lane, C, pairbuf[wid][0], pairbuf[wid][1]);
     double m = -CUDART_INF, s = 0.0;
     bool nan_seen = false;
-    const int nt = Q.n_t > 0 ? Q.n_t : 1;
-    for (int jt = 0; jt < nt; ++jt) {
-      const double tc = Q.n_t > 0 ? Q.t_lo + (jt + 0.5) * Q.t_h : load_param_d(dp, 6, i);
-      direct_data_warp<MM>(P, g, tc, lane, C, pairbuf[wid][0]);
-      // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
-      double best = -CUDART_INF;
-      long long best_idx = (long long)Q.n_phi * Q.n_psi;
-      for (int a = lane; a < Q.n_phi; a += 32) {
-        double2 D, B;
-        double A;
-        direct_column(C, (double)a / Q.n_phi, D, A, B);
-        for (int b = 0; b < Q.n_psi; ++b) {
-          double s2, c2;
-          sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
-          double K, R;
-          direct_node(D, A, B, make_double2(c2, s2), K, R);
-          const double h = (R > 0.0) ? K * K / (2.0 * R) : -CUDART_INF;
-          const long long idx = (long long)a * Q.n_psi + b;
-          if (h > best || (h == best && idx < best_idx)) {
-            best = h;
-            best_idx = idx;
+    if (Q.t_up > 1) {
+      // band-limited rule: the data coefficients at the coarse midpoints
+      // (lane h keeps harmonic h), then their sinc sum at each fine midpoint,
+      // (t_f - t_j) / h = (2 f + 1 - t_up (2 j + 1)) / (2 t_up)
+      double2* my = Q.slab + (long long)(blockIdx.x * kDirWarps + wid) * Q.n_t * kHm;
+      for (int jt = 0; jt < Q.n_t; ++jt) {
+        direct_data_warp<MM>(P, g, Q.t_lo + (jt + 0.5) * Q.t_h, lane, C, pairbuf[wid][0]);
+        if (lane < kHm) my[jt * kHm + lane] = C.c[lane];
+        __syncwarp();
+      }
+      const int nf = Q.n_t * Q.t_up;
+      const double inv2u = 1.0 / (2.0 * Q.t_up);
+      for (int f = 0; f < nf; ++f) {
+        if (lane < kHm) {
+          double2 c = make_double2(0.0, 0.0);
+          for (int j = 0; j < Q.n_t; ++j) {
+            const long long num = 2LL * f + 1 - (long long)Q.t_up * (2 * j + 1);
+            double w = 1.0;
+            if (num != 0) {
+              const double z = (double)num * inv2u;
+              w = sinpi(z) / (CUDART_PI * z);
+            }
+            const double2 v = my[j * kHm + lane];
+            c.x = fma(w, v.x, c.x);
+            c.y = fma(w, v.y, c.y);
           }
+          C.c[lane] = c;
         }
+        __syncwarp();
+        direct_time_node(C, Q, lane, m, s, nan_seen);
+        __syncwarp();  // C is rewritten for the next fine node
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
-        if (ob > best || (ob == best && oi < best_idx)) {
-          best = ob;
-          best_idx = oi;
-        }
+    } else {
+      const int nt = Q.n_t > 0 ? Q.n_t : 1;
+      for (int jt = 0; jt < nt; ++jt) {
+        const double tc = Q.n_t > 0 ? Q.t_lo + (jt + 0.5) * Q.t_h : load_param_d(dp, 6, i);
+        direct_data_warp<MM>(P, g, tc, lane, C, pairbuf[wid][0]);
+        direct_time_node(C, Q, lane, m, s, nan_seen);
+        __syncwarp();  // C is rewritten for the next time node
       }
-      double v0 = -CUDART_INF;
-      if (best_idx < (long long)Q.n_phi * Q.n_psi) {
-        const int a = (int)(best_idx / Q.n_psi), b = (int)(best_idx % Q.n_psi);
-        double2 D, B;
-        double A;
-        direct_column(C, (double)a / Q.n_phi, D, A, B);
-        double s2, c2;
-        sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
-        double K, R;
-        direct_node(D, A, B, make_double2(c2, s2), K, R);
-        v0 = direct_distance(Q, K, R);
-      }
-      const double cut = v0 - kSkipNat;
-      // pass 2: the log-sum-exp over the nodes that can matter
-      for (int a = lane; a < Q.n_phi; a += 32) {
-        double2 D, B;
-        double A;
-        direct_column(C, (double)a / Q.n_phi, D, A, B);
-        for (int b = 0; b < Q.n_psi; ++b) {
-          double s2, c2;
-          sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
-          double K, R;
-          direct_node(D, A, B, make_double2(c2, s2), K, R);
-          if (isnan(K) || isnan(R)) {
-            nan_seen = true;
-            continue;
-          }
-          if (!(R > 0.0)) continue;
-          const double ub = K * K / (2.0 * R) - 0.5 * log(R) + Q.ln_ub;
-          if (ub < cut) continue;
-          lse_add(m, s, direct_distance(Q, K, R));
-        }
-      }
-      __syncwarp();  // C is rewritten for the next time node
     }
     nan_seen = __any_sync(0xffffffffu, nan_seen);
     for (int off = 16; off > 0; off >>= 1) {
@@ -388,8 +435,18 @@ cudaError_t launch_direct_mm(const PointParams* dP, const DrawsParams& dp, const
   const long long need = (dp.n + kDirWarps - 1) / kDirWarps;
   int blocks = grid_for(direct_kernel<MM>, threads, 0);
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
-  direct_kernel<MM><<<blocks, threads, 0, st>>>(dP, dp, Q, out);
-  return cudaGetLastError();
+  if (Q.t_up <= 1) {
+    direct_kernel<MM><<<blocks, threads, 0, st>>>(dP, dp, Q, out);
+    return cudaGetLastError();
+  }
+  DirectParams Qb = Q;
+  const size_t bytes = (size_t)blocks * kDirWarps * Q.n_t * kHm * sizeof(double2);
+  cudaError_t e = cudaMallocAsync((void**)&Qb.slab, bytes, st);
+  if (e != cudaSuccess) return e;
+  direct_kernel<MM><<<blocks, threads, 0, st>>>(dP, dp, Qb, out);
+  e = cudaGetLastError();
+  const cudaError_t f = cudaFreeAsync(Qb.slab, st);
+  return e != cudaSuccess ? e : f;
 }
 
 cudaError_t launch_direct(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
@@ -492,6 +549,13 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
                        rule->n_t);
     return RIFT_ILE_ERR_SHAPE;
   }
+  if (rule->t_up < 0 ||
+      (rule->t_up > 1 && (rule->n_t < 1 || rule->n_t > 1024 ||
+                          (long long)rule->n_t * rule->t_up > (1LL << 20)))) {
+    rift_ile_set_error("rift_ile_lnL_direct: t_up=%d needs n_t in 1..1024 and n_t t_up <= 2^20",
+                       rule->t_up);
+    return RIFT_ILE_ERR_SHAPE;
+  }
   if (!(rule->d_min > 0.0) || !(rule->d_max > rule->d_min) || !std::isfinite(rule->d_max)) {
     rift_ile_set_error("rift_ile_lnL_direct: need 0 < d_min < d_max finite");
     return RIFT_ILE_ERR_INVALID_ARG;
@@ -516,7 +580,9 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   Q.n_t = rule->n_t;
   Q.t_lo = rule->t_lo;
   Q.t_h = rule->n_t > 0 ? (rule->t_hi - rule->t_lo) / rule->n_t : 0.0;
-  Q.lnw = -std::log((double)rule->n_phi * rule->n_psi * (rule->n_t > 0 ? rule->n_t : 1));
+  Q.t_up = rule->t_up > 1 ? rule->t_up : 1;
+  Q.slab = nullptr;
+  Q.lnw = -std::log((double)rule->n_phi * rule->n_psi * (rule->n_t > 0 ? rule->n_t : 1) * Q.t_up);
   Q.ln_ub = std::log(std::sqrt(2.0 * M_PI) * norm) - 4.0 * std::log(Q.lo);
   if ((rc = gauss_hermite(Q.n_gh, Q.xi, Q.w))) {
     rift_ile_set_error("rift_ile_lnL_direct: Gauss-Hermite rule failed for n=%d", Q.n_gh);

@@ -70,7 +70,9 @@ def test_invalid_rules(R):
     pt = R.Point(point)
     d = R.Draws(draws)
     for args in ((0, 8, 16, 50.0, 200.0), (8, 8, 65, 50.0, 200.0), (8, 8, 16, 200.0, 50.0),
-                 (8, 8, 16, 50.0, 200.0, 4, 0.01, -0.01)):
+                 (8, 8, 16, 50.0, 200.0, 4, 0.01, -0.01), (8, 8, 16, 50.0, 200.0, 0, 0.0, 0.0, 2),
+                 (8, 8, 16, 50.0, 200.0, 4, -0.01, 0.01, -1),
+                 (8, 8, 16, 50.0, 200.0, 2000, -0.01, 0.01, 2)):
         with pytest.raises(R.RiftError):
             R.rift_ile_lnL_direct(pt, d, *args)
 
@@ -87,3 +89,22 @@ def test_lnz_with_the_direct_marginal(R):
     zr = O.lnZ(ref, np.zeros(len(ref)))
     assert abs(z[0] - zr[0]) <= 1e-9 * max(1.0, abs(zr[0]))
     assert abs(z[2] - zr[2]) <= 1e-7 * zr[2]
+
+
+@pytest.mark.parametrize("n_t,t_up", [(8, 3), (5, 4)])
+def test_band_limited_time_rule(R, n_t, t_up):
+    """eq. ap:tband: coarse data coefficients sinc-reconstructed at t_up fine
+    nodes per interval, against the oracle's rule on the same draws."""
+    point, exact, info, draws, logw = W.config0(n_draws=10)
+    tr = info["truth"]
+    d = {p: np.concatenate([[tr[p]], np.asarray(draws[p])]) for p in W.PARAMS}
+    pt = R.Point(point)
+    args = (64, 32, 16, 50.0, 200.0, n_t, tr["t"] - 1e-3, tr["t"] + 1e-3, t_up)
+    got = R.rift_ile_lnL_direct(pt, R.Draws(d), *args).cpu().numpy()
+    ref = OD.lnL_direct(point, d, *args)
+    _cmp(got, ref)
+    assert np.isfinite(got[0])
+    # t_up = 1 is the fixed-spacing rule
+    one = R.rift_ile_lnL_direct(pt, R.Draws(d), *args[:-1], 1).cpu().numpy()
+    fixed = R.rift_ile_lnL_direct(pt, R.Draws(d), *args[:-1]).cpu().numpy()
+    assert np.array_equal(one, fixed)
