@@ -697,6 +697,13 @@ def run_direct(args):
         ms = timed_events(torch, lambda: R.rift_ile_lnL_direct(pt, d, *rule, out=out),
                           max(3, min(args.steps, 10)), stream)
     got = out.cpu().numpy()
+    out_m = torch.empty(n, dtype=torch.float64, device="cuda")
+    ms_m = timed_events(torch, lambda: R.rift_ile_lnL_direct(pt, d, *rule, precision=R.FP32_MIXED,
+                                                             out=out_m),
+                        max(3, min(args.steps, 10)), stream)
+    gm = out_m.cpu().numpy()
+    fin_g = np.isfinite(got)
+    mixed_err = float(np.max(np.abs(gm[fin_g] - got[fin_g]))) if fin_g.any() else 0.0
     ns = 16
     sub = {p: np.asarray(draws[p])[:ns] for p in W.PARAMS}
     t0 = time.perf_counter()
@@ -723,6 +730,10 @@ def run_direct(args):
         "config": {"workload": "3G network K=4, M=10, SNR 30, grid 128 x 64 (phase x "
                    "polarisation), 16 Gauss-Hermite nodes in x, D in [50, 200]", "draws": n},
         "ms_per_call": ms, "grid_nodes_per_s": n * rule[0] * rule[1] / (ms * 1e-3),
+        "fp32_mixed_distance_sum": {"draws_per_s": n / (ms_m * 1e-3), "ms_per_call": ms_m,
+                                    "max_abs_dlnL_vs_fp64": mixed_err,
+                                    "same_inf_pattern": bool(np.array_equal(np.isfinite(gm),
+                                                                            fin_g))},
         "with_time_rule": {"draws_per_s": nt_draws / (ms_t * 1e-3), "time_nodes": 32,
                            "window_s": 1e-3},
         "with_band_limited_time_rule": {"draws_per_s": nt_draws / (ms_b * 1e-3),

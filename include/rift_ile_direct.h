@@ -62,6 +62,12 @@ typedef struct {
                    * resident warp and frees it before returning.  The stencil
                    * is truncated at the window: place the window so that the
                    * correlation has decayed at its ends. */
+  int32_t precision; /* RIFT_ILE_FP64 (0): every step in double.  RIFT_ILE_FP32_MIXED:
+                   * the harmonic model, K, R, K^2/(2R), the Gauss-Hermite
+                   * abscissae and their prior-range test stay in double; the
+                   * prior-weighted sum sum_i w_i (x_i / x_lo)^-4 runs in
+                   * float (relative error ~1e-6, i.e. ~1e-6 in ln L_dir);
+                   * needs d_max / d_min <= 1e9. */
 } rift_ile_direct_rule;
 
 /* ln L_dir per draw into DEVICE out[n] (double). */

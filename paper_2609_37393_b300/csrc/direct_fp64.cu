@@ -41,6 +41,7 @@ namespace {
 constexpr int kDirWarps = 4;
 constexpr int kHm = 2 * kMaxEll + 1;        // data harmonics m = -8..8
 constexpr int kHn = 4 * kMaxEll + 1;        // norm harmonics -16..16
+constexpr int kPsiTab = 256;                // polarisation phases tabulated up to this n_psi
 constexpr double kSkipNat = 60.0;
 
 struct DirectParams {
@@ -53,6 +54,12 @@ struct DirectParams {
   double lnw;             // -ln(n_phi n_psi max(n_t, 1) max(t_up, 1))
   double ln_ub;           // ln(sqrt(2 pi) norm lo^-4), the prefactor bound over sigma_x
   double xi[RIFT_ILE_MAX_GH], w[RIFT_ILE_MAX_GH];
+  int mixed;              // 1: the prior-weighted Gauss-Hermite sum in float
+  double inv_lo;          // 1 / lo
+  double hi_lo;           // hi / lo
+  double lnnorm_lo;       // lnnorm - 4 ln lo (the sum taken in y = x / lo)
+  float wf[RIFT_ILE_MAX_GH];
+  double2 e2[kPsiTab];    // e^{2 i psi_b}, psi_b = pi b / n_psi (n_psi <= kPsiTab)
 };
 
 struct DirCoef {
@@ -263,6 +270,20 @@ __device__ double direct_distance(const DirectParams& Q, double K, double R) {
   if (!(R > 0.0)) return -CUDART_INF;
   const double sig = rsqrt(R), xs = K / R;
   const double h = 1.4142135623730951 * sig;
+  if (Q.mixed) {
+    // y = x / lo in [1, hi / lo] inside the prior, so y^-4 lies in [(lo/hi)^4, 1]
+    const double ys = xs * Q.inv_lo, hy = h * Q.inv_lo;
+    float sf = 0.0f;
+    for (int j = 0; j < Q.n_gh; ++j) {
+      const double y = fma(hy, Q.xi[j], ys);
+      if (y >= 1.0 && y <= Q.hi_lo) {
+        const float r = __frcp_rn((float)y), r2 = r * r;
+        sf = fmaf(Q.wf[j], r2 * r2, sf);
+      }
+    }
+    if (!(sf > 0.0f)) return -CUDART_INF;
+    return K * K / (2.0 * R) + log(h * (double)sf) + Q.lnnorm_lo;
+  }
   double s = 0.0;
   for (int j = 0; j < Q.n_gh; ++j) {
     const double x = fma(h, Q.xi[j], xs);
@@ -285,36 +306,54 @@ __device__ __forceinline__ void lse_add(double& m, double& s, double v) {
   }
 }
 
+// e^{2 i psi_b}: from the launch's table (uniform across the warp: one
+// constant-cache access), else computed.
+__device__ __forceinline__ double2 psi_phase(const DirectParams& Q, int b) {
+  if (Q.n_psi <= kPsiTab) return Q.e2[b];
+  double s2, c2;
+  sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
+  return make_double2(c2, s2);
+}
+
 // The angular and distance integral at one time node (coefficients in C),
-// accumulated into the lane's log-sum-exp (m, s).
-__device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectParams& Q, int lane, double& m,
-                                 double& s, bool& nan_seen) {
-  // pass 1: the node with the largest K^2/(2R) (first in node order on ties)
-  double best = -CUDART_INF;
+// accumulated into the lane's log-sum-exp (m, s).  Pass 1 picks a node of
+// largest K^2/(2R) by cross-multiplication (no division); any evaluated node
+// makes a valid skip reference, the largest skips the most.  Pass 2 skips
+// nodes whose bound K^2/(2R) - ln(R)/2 + ln_ub is below v0 - 60, tested as
+// K^2 < 2R (cut - ln_ub + ln(R)/2), ln R in float with a 1e-3 nat margin
+// (the float log errs by < 1e-6): a skipped node adds below e^-60 of v0.
+__device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectParams& Q, int lane,
+                                              double& m, double& s, bool& nan_seen) {
+  // pass 1 (first in node order on ties)
+  double bk = 0.0, br = 0.0;  // K^2 and R of the best node; br = 0: none yet
   long long best_idx = (long long)Q.n_phi * Q.n_psi;
   for (int a = lane; a < Q.n_phi; a += 32) {
     double2 D, B;
     double A;
     direct_column(C, (double)a / Q.n_phi, D, A, B);
     for (int b = 0; b < Q.n_psi; ++b) {
-      double s2, c2;
-      sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
       double K, R;
-      direct_node(D, A, B, make_double2(c2, s2), K, R);
-      const double h = (R > 0.0) ? K * K / (2.0 * R) : -CUDART_INF;
-      const long long idx = (long long)a * Q.n_psi + b;
-      if (h > best || (h == best && idx < best_idx)) {
-        best = h;
-        best_idx = idx;
+      direct_node(D, A, B, psi_phase(Q, b), K, R);
+      if (!(R > 0.0) || isnan(K)) continue;
+      const double kk = K * K;
+      if (br == 0.0 || kk * br > bk * R) {
+        bk = kk;
+        br = R;
+        best_idx = (long long)a * Q.n_psi + b;
       }
     }
   }
   for (int off = 16; off > 0; off >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const double ok = __shfl_xor_sync(0xffffffffu, bk, off);
+    const double orr = __shfl_xor_sync(0xffffffffu, br, off);
     const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
-    if (ob > best || (ob == best && oi < best_idx)) {
-      best = ob;
-      best_idx = oi;
+    if (orr > 0.0) {
+      const double l = ok * br, r = bk * orr;
+      if (br == 0.0 || l > r || (l == r && oi < best_idx)) {
+        bk = ok;
+        br = orr;
+        best_idx = oi;
+      }
     }
   }
   double v0 = -CUDART_INF;
@@ -323,30 +362,27 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     double2 D, B;
     double A;
     direct_column(C, (double)a / Q.n_phi, D, A, B);
-    double s2, c2;
-    sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
     double K, R;
-    direct_node(D, A, B, make_double2(c2, s2), K, R);
+    direct_node(D, A, B, psi_phase(Q, b), K, R);
     v0 = direct_distance(Q, K, R);
   }
-  const double cut = v0 - kSkipNat;
+  const double c0 = v0 - kSkipNat - Q.ln_ub - 1e-3;
   // pass 2: the log-sum-exp over the nodes that can matter
   for (int a = lane; a < Q.n_phi; a += 32) {
     double2 D, B;
     double A;
     direct_column(C, (double)a / Q.n_phi, D, A, B);
     for (int b = 0; b < Q.n_psi; ++b) {
-      double s2, c2;
-      sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
       double K, R;
-      direct_node(D, A, B, make_double2(c2, s2), K, R);
+      direct_node(D, A, B, psi_phase(Q, b), K, R);
       if (isnan(K) || isnan(R)) {
         nan_seen = true;
         continue;
       }
       if (!(R > 0.0)) continue;
-      const double ub = K * K / (2.0 * R) - 0.5 * log(R) + Q.ln_ub;
-      if (ub < cut) continue;
+      // ln R: float where R is a normal float, else double
+      const double lr = (R > 1e-30 && R < 1e30) ? (double)__logf((float)R) : log(R);
+      if (K * K < 2.0 * R * (c0 + 0.5 * lr)) continue;
       lse_add(m, s, direct_distance(Q, K, R));
     }
   }
@@ -560,6 +596,14 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
     rift_ile_set_error("rift_ile_lnL_direct: need 0 < d_min < d_max finite");
     return RIFT_ILE_ERR_INVALID_ARG;
   }
+  if (rule->precision != RIFT_ILE_FP64 && rule->precision != RIFT_ILE_FP32_MIXED) {
+    rift_ile_set_error("rift_ile_lnL_direct: precision %d unknown", rule->precision);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (rule->precision == RIFT_ILE_FP32_MIXED && rule->d_max > 1e9 * rule->d_min) {
+    rift_ile_set_error("rift_ile_lnL_direct: the mixed rule needs d_max / d_min <= 1e9");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
   if (draws->n == 0) return RIFT_ILE_OK;
   if (!out) {
     rift_ile_set_error("rift_ile_lnL_direct: out is NULL");
@@ -588,6 +632,16 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
     rift_ile_set_error("rift_ile_lnL_direct: Gauss-Hermite rule failed for n=%d", Q.n_gh);
     return rc;
   }
+  Q.mixed = rule->precision == RIFT_ILE_FP32_MIXED ? 1 : 0;
+  Q.inv_lo = 1.0 / Q.lo;
+  Q.hi_lo = Q.hi / Q.lo;
+  Q.lnnorm_lo = Q.lnnorm - 4.0 * std::log(Q.lo);
+  for (int j = 0; j < Q.n_gh; ++j) Q.wf[j] = (float)Q.w[j];
+  if (Q.n_psi <= kPsiTab)
+    for (int b = 0; b < Q.n_psi; ++b) {
+      const double ang = 2.0 * M_PI * b / Q.n_psi;
+      Q.e2[b] = make_double2(std::cos(ang), std::sin(ang));
+    }
   return check_cuda(launch_direct(hp, pt->dev, draws_params(draws), Q, out, (cudaStream_t)stream),
                     "rift_ile_lnL_direct launch");
 }

@@ -108,3 +108,33 @@ def test_band_limited_time_rule(R, n_t, t_up):
     one = R.rift_ile_lnL_direct(pt, R.Draws(d), *args[:-1], 1).cpu().numpy()
     fixed = R.rift_ile_lnL_direct(pt, R.Draws(d), *args[:-1]).cpu().numpy()
     assert np.array_equal(one, fixed)
+
+
+def test_mixed_distance_sum(R):
+    """precision=FP32_MIXED: the prior-weighted Gauss-Hermite sum in float,
+    everything else in double: within 1e-5 of the FP64 oracle (the north-star
+    bound is 1e-3) on the 3G network and on the two-detector workload, with
+    the same -inf pattern."""
+    for point, exact, info, draws, logw in (W.config_3g(1, 4, 30.0, 0.02, 16),
+                                            W.config0(n_draws=24)):
+        pt = R.Point(point)
+        args = (96, 48, 16, 50.0, 200.0)
+        got = R.rift_ile_lnL_direct(pt, R.Draws(draws), *args, precision=R.FP32_MIXED).cpu().numpy()
+        ref = OD.lnL_direct(point, draws, *args)
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(got), fin)
+        assert np.max(np.abs(got[fin] - ref[fin])) <= 1e-5
+    # the band-limited time rule in the mixed form too
+    point, exact, info, draws, logw = W.config0(n_draws=6)
+    tr = info["truth"]
+    args = (64, 32, 16, 50.0, 200.0, 8, tr["t"] - 1e-3, tr["t"] + 1e-3, 3)
+    pt = R.Point(point)
+    got = R.rift_ile_lnL_direct(pt, R.Draws(draws), *args, precision=R.FP32_MIXED).cpu().numpy()
+    ref = OD.lnL_direct(point, draws, *args)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(got), fin)
+    assert np.max(np.abs(got[fin] - ref[fin])) <= 1e-5
+    with pytest.raises(R.RiftError):
+        R.rift_ile_lnL_direct(pt, R.Draws(draws), 8, 8, 16, 1e-3, 1e7, precision=R.FP32_MIXED)
+    with pytest.raises(R.RiftError):
+        R.rift_ile_lnL_direct(pt, R.Draws(draws), 8, 8, 16, 50.0, 200.0, precision=7)
