@@ -60,6 +60,7 @@ struct DirectParams {
   double lnnorm_lo;       // lnnorm - 4 ln lo (the sum taken in y = x / lo)
   float wf[RIFT_ILE_MAX_GH];
   double2 e2[kPsiTab];    // e^{2 i psi_b}, psi_b = pi b / n_psi (n_psi <= kPsiTab)
+  double2 e4[kPsiTab];    // e^{4 i psi_b}
 };
 
 struct DirCoef {
@@ -257,11 +258,10 @@ __device__ void direct_column(const DirCoef& C, double phi_frac, double2& D, dou
   }
 }
 
-// K, R at one polarisation node from the column sums; e2 = e^{2 i psi}.
+// K, R at one polarisation node from the column sums; e2 = e^{2 i psi}, e4 = e2^2.
 __device__ __forceinline__ void direct_node(const double2& D, double A, const double2& B,
-                                            double2 e2, double& K, double& R) {
+                                            double2 e2, double2 e4, double& K, double& R) {
   K = e2.x * D.x + e2.y * D.y;  // Re(e^{-2 i psi} D)
-  const double2 e4 = cmul_d(e2, e2);
   R = 0.5 * (A + (e4.x * B.x - e4.y * B.y));
 }
 
@@ -306,22 +306,28 @@ __device__ __forceinline__ void lse_add(double& m, double& s, double v) {
   }
 }
 
-// e^{2 i psi_b}: from the launch's table (uniform across the warp: one
-// constant-cache access), else computed.
-__device__ __forceinline__ double2 psi_phase(const DirectParams& Q, int b) {
-  if (Q.n_psi <= kPsiTab) return Q.e2[b];
+// K, R at polarisation node b: e^{2 i psi_b}, e^{4 i psi_b} from the launch's
+// tables (uniform across the warp: one constant-cache access), else computed.
+__device__ __forceinline__ void direct_node_b(const DirectParams& Q, int b, const double2& D,
+                                              double A, const double2& B, double& K, double& R) {
+  if (Q.n_psi <= kPsiTab) {
+    direct_node(D, A, B, Q.e2[b], Q.e4[b], K, R);
+    return;
+  }
   double s2, c2;
   sincospi(2.0 * (double)b / Q.n_psi, &s2, &c2);
-  return make_double2(c2, s2);
+  const double2 e2 = make_double2(c2, s2);
+  direct_node(D, A, B, e2, cmul_d(e2, e2), K, R);
 }
 
 // The angular and distance integral at one time node (coefficients in C),
 // accumulated into the lane's log-sum-exp (m, s).  Pass 1 picks a node of
 // largest K^2/(2R) by cross-multiplication (no division); any evaluated node
 // makes a valid skip reference, the largest skips the most.  Pass 2 skips
-// nodes whose bound K^2/(2R) - ln(R)/2 + ln_ub is below v0 - 60, tested as
-// K^2 < 2R (cut - ln_ub + ln(R)/2), ln R in float with a 1e-3 nat margin
-// (the float log errs by < 1e-6): a skipped node adds below e^-60 of v0.
+// nodes whose bound K^2/(2R) - ln(R)/2 + ln_ub is below v0 - 60, tested in
+// float with a margin of 1e-3 nat + 2e-6 of the magnitudes (above the float
+// error), or in double where R is outside the normal float range: a skipped
+// node adds below e^-60 of v0.
 __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectParams& Q, int lane,
                                               double& m, double& s, bool& nan_seen) {
   // pass 1 (first in node order on ties)
@@ -333,7 +339,7 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     direct_column(C, (double)a / Q.n_phi, D, A, B);
     for (int b = 0; b < Q.n_psi; ++b) {
       double K, R;
-      direct_node(D, A, B, psi_phase(Q, b), K, R);
+      direct_node_b(Q, b, D, A, B, K, R);
       if (!(R > 0.0) || isnan(K)) continue;
       const double kk = K * K;
       if (br == 0.0 || kk * br > bk * R) {
@@ -363,10 +369,11 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     double A;
     direct_column(C, (double)a / Q.n_phi, D, A, B);
     double K, R;
-    direct_node(D, A, B, psi_phase(Q, b), K, R);
+    direct_node_b(Q, b, D, A, B, K, R);
     v0 = direct_distance(Q, K, R);
   }
   const double c0 = v0 - kSkipNat - Q.ln_ub - 1e-3;
+  const float c0f = (float)c0;
   // pass 2: the log-sum-exp over the nodes that can matter
   for (int a = lane; a < Q.n_phi; a += 32) {
     double2 D, B;
@@ -374,15 +381,22 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     direct_column(C, (double)a / Q.n_phi, D, A, B);
     for (int b = 0; b < Q.n_psi; ++b) {
       double K, R;
-      direct_node(D, A, B, psi_phase(Q, b), K, R);
-      if (isnan(K) || isnan(R)) {
+      direct_node_b(Q, b, D, A, B, K, R);
+      if (isnan(K + R)) {  // either is NaN (or they are opposite infinities)
         nan_seen = true;
         continue;
       }
       if (!(R > 0.0)) continue;
-      // ln R: float where R is a normal float, else double
-      const double lr = (R > 1e-30 && R < 1e30) ? (double)__logf((float)R) : log(R);
-      if (K * K < 2.0 * R * (c0 + 0.5 * lr)) continue;
+      const float rf = (float)R;
+      if (rf > 1e-30f && rf < 1e30f) {
+        // in float: K^2/(2R) - ln(R)/2 errs by < 1e-6 (|K^2/(2R)| + 1)
+        const float kf = (float)K;
+        const float hf = __fdividef(kf * kf, 2.0f * rf);
+        const float lhs = hf - 0.5f * __logf(rf);
+        if (lhs < c0f - (1e-3f + 2e-6f * (hf + fabsf(c0f)))) continue;
+      } else if (K * K < 2.0 * R * (c0 + 0.5 * log(R))) {
+        continue;
+      }
       lse_add(m, s, direct_distance(Q, K, R));
     }
   }
@@ -641,6 +655,7 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
     for (int b = 0; b < Q.n_psi; ++b) {
       const double ang = 2.0 * M_PI * b / Q.n_psi;
       Q.e2[b] = make_double2(std::cos(ang), std::sin(ang));
+      Q.e4[b] = make_double2(std::cos(2.0 * ang), std::sin(2.0 * ang));
     }
   return check_cuda(launch_direct(hp, pt->dev, draws_params(draws), Q, out, (cudaStream_t)stream),
                     "rift_ile_lnL_direct launch");
