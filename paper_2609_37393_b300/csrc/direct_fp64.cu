@@ -42,6 +42,10 @@ constexpr int kDirWarps = 4;
 constexpr int kHm = 2 * kMaxEll + 1;        // data harmonics m = -8..8
 constexpr int kHn = 4 * kMaxEll + 1;        // norm harmonics -16..16
 constexpr int kPsiTab = 256;                // polarisation phases tabulated up to this n_psi
+// Column sums (D, A, B: 5 doubles) kept between the passes in the warp's
+// pair buffers (idle during the angular sweep) up to this n_phi.
+constexpr int kColCache = (2 * kMaxModes * kMaxModes * 2) / 5;
+static_assert(5 * kColCache <= 2 * kMaxModes * kMaxModes * 2, "column cache exceeds the pair buffers");
 constexpr double kSkipNat = 60.0;
 
 struct DirectParams {
@@ -328,8 +332,25 @@ __device__ __forceinline__ void direct_node_b(const DirectParams& Q, int b, cons
 // float with a margin of 1e-3 nat + 2e-6 of the magnitudes (above the float
 // error), or in double where R is outside the normal float range: a skipped
 // node adds below e^-60 of v0.
+__device__ __forceinline__ void column_store(double* col, int a, const double2& D, double A,
+                                             const double2& B) {
+  col[a] = D.x;
+  col[kColCache + a] = D.y;
+  col[2 * kColCache + a] = A;
+  col[3 * kColCache + a] = B.x;
+  col[4 * kColCache + a] = B.y;
+}
+
+__device__ __forceinline__ void column_load(const double* col, int a, double2& D, double& A,
+                                            double2& B) {
+  D = make_double2(col[a], col[kColCache + a]);
+  A = col[2 * kColCache + a];
+  B = make_double2(col[3 * kColCache + a], col[4 * kColCache + a]);
+}
+
 __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectParams& Q, int lane,
-                                              double& m, double& s, bool& nan_seen) {
+                                              double& m, double& s, bool& nan_seen, double* col) {
+  const bool cached = Q.n_phi <= kColCache;
   // pass 1 (first in node order on ties)
   double bk = 0.0, br = 0.0;  // K^2 and R of the best node; br = 0: none yet
   long long best_idx = (long long)Q.n_phi * Q.n_psi;
@@ -337,6 +358,7 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     double2 D, B;
     double A;
     direct_column(C, (double)a / Q.n_phi, D, A, B);
+    if (cached) column_store(col, a, D, A, B);
     for (int b = 0; b < Q.n_psi; ++b) {
       double K, R;
       direct_node_b(Q, b, D, A, B, K, R);
@@ -349,6 +371,7 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
       }
     }
   }
+  __syncwarp();  // the cached columns are read by other lanes below
   for (int off = 16; off > 0; off >>= 1) {
     const double ok = __shfl_xor_sync(0xffffffffu, bk, off);
     const double orr = __shfl_xor_sync(0xffffffffu, br, off);
@@ -367,7 +390,10 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     const int a = (int)(best_idx / Q.n_psi), b = (int)(best_idx % Q.n_psi);
     double2 D, B;
     double A;
-    direct_column(C, (double)a / Q.n_phi, D, A, B);
+    if (cached)
+      column_load(col, a, D, A, B);
+    else
+      direct_column(C, (double)a / Q.n_phi, D, A, B);
     double K, R;
     direct_node_b(Q, b, D, A, B, K, R);
     v0 = direct_distance(Q, K, R);
@@ -378,7 +404,10 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
   for (int a = lane; a < Q.n_phi; a += 32) {
     double2 D, B;
     double A;
-    direct_column(C, (double)a / Q.n_phi, D, A, B);
+    if (cached)
+      column_load(col, a, D, A, B);
+    else
+      direct_column(C, (double)a / Q.n_phi, D, A, B);
     for (int b = 0; b < Q.n_psi; ++b) {
       double K, R;
       direct_node_b(Q, b, D, A, B, K, R);
@@ -450,7 +479,7 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
           C.c[lane] = c;
         }
         __syncwarp();
-        direct_time_node(C, Q, lane, m, s, nan_seen);
+        direct_time_node(C, Q, lane, m, s, nan_seen, reinterpret_cast<double*>(pairbuf[wid]));
         __syncwarp();  // C is rewritten for the next fine node
       }
     } else {
@@ -458,7 +487,7 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
       for (int jt = 0; jt < nt; ++jt) {
         const double tc = Q.n_t > 0 ? Q.t_lo + (jt + 0.5) * Q.t_h : load_param_d(dp, 6, i);
         direct_data_warp<MM>(P, g, tc, lane, C, pairbuf[wid][0]);
-        direct_time_node(C, Q, lane, m, s, nan_seen);
+        direct_time_node(C, Q, lane, m, s, nan_seen, reinterpret_cast<double*>(pairbuf[wid]));
         __syncwarp();  // C is rewritten for the next time node
       }
     }

@@ -138,3 +138,19 @@ def test_mixed_distance_sum(R):
         R.rift_ile_lnL_direct(pt, R.Draws(draws), 8, 8, 16, 1e-3, 1e7, precision=R.FP32_MIXED)
     with pytest.raises(R.RiftError):
         R.rift_ile_lnL_direct(pt, R.Draws(draws), 8, 8, 16, 50.0, 200.0, precision=7)
+
+
+@pytest.mark.parametrize("n_phi,n_psi", [(256, 8), (12, 300), (205, 257)])
+def test_grids_beyond_the_kernel_tables(R, n_phi, n_psi):
+    """Phase grids beyond the column cache (n_phi > 204) and polarisation
+    grids beyond the phase table (n_psi > 256) take the computed paths; both
+    must agree with the oracle like the tabulated ones."""
+    point, exact, info, draws, logw = W.config0(n_draws=6)
+    tr = info["truth"]
+    d = {p: np.concatenate([[tr[p]], np.asarray(draws[p])]) for p in W.PARAMS}
+    pt = R.Point(point)
+    args = (n_phi, n_psi, 16, 50.0, 200.0)
+    got = R.rift_ile_lnL_direct(pt, R.Draws(d), *args).cpu().numpy()
+    ref = OD.lnL_direct(point, d, *args)
+    _cmp(got, ref)
+    assert np.isfinite(got[0])
