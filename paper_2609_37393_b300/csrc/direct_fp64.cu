@@ -65,6 +65,8 @@ struct DirectParams {
   float wf[RIFT_ILE_MAX_GH];
   double2 e2[kPsiTab];    // e^{2 i psi_b}, psi_b = pi b / n_psi (n_psi <= kPsiTab)
   double2 e4[kPsiTab];    // e^{4 i psi_b}
+  float2 e2f[kPsiTab];    // the same in float, for the first pass
+  float2 e4f[kPsiTab];
 };
 
 struct DirCoef {
@@ -326,8 +328,9 @@ __device__ __forceinline__ void direct_node_b(const DirectParams& Q, int b, cons
 
 // The angular and distance integral at one time node (coefficients in C),
 // accumulated into the lane's log-sum-exp (m, s).  Pass 1 picks a node of
-// largest K^2/(2R) by cross-multiplication (no division); any evaluated node
-// makes a valid skip reference, the largest skips the most.  Pass 2 skips
+// largest K^2/(2R), in float and by cross-multiplication; any evaluated node
+// makes a valid skip reference (its value v0 is then taken in double), the
+// largest skips the most.  Pass 2 skips
 // nodes whose bound K^2/(2R) - ln(R)/2 + ln_ub is below v0 - 60, tested in
 // float with a margin of 1e-3 nat + 2e-6 of the magnitudes (above the float
 // error), or in double where R is outside the normal float range: a skipped
@@ -351,20 +354,31 @@ __device__ __forceinline__ void column_load(const double* col, int a, double2& D
 __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectParams& Q, int lane,
                                               double& m, double& s, bool& nan_seen, double* col) {
   const bool cached = Q.n_phi <= kColCache;
-  // pass 1 (first in node order on ties)
-  double bk = 0.0, br = 0.0;  // K^2 and R of the best node; br = 0: none yet
+  // pass 1 in float (first in node order on ties): it only chooses the
+  // reference node, and any node is a valid one
+  float bk = 0.0f, br = 0.0f;  // K^2 and R of the best node; br = 0: none yet
   long long best_idx = (long long)Q.n_phi * Q.n_psi;
   for (int a = lane; a < Q.n_phi; a += 32) {
     double2 D, B;
     double A;
     direct_column(C, (double)a / Q.n_phi, D, A, B);
     if (cached) column_store(col, a, D, A, B);
+    const float dx = (float)D.x, dy = (float)D.y, af = (float)A, bx = (float)B.x,
+                by = (float)B.y;
     for (int b = 0; b < Q.n_psi; ++b) {
-      double K, R;
-      direct_node_b(Q, b, D, A, B, K, R);
-      if (!(R > 0.0) || isnan(K)) continue;
-      const double kk = K * K;
-      if (br == 0.0 || kk * br > bk * R) {
+      float2 e2, e4;
+      if (Q.n_psi <= kPsiTab) {
+        e2 = Q.e2f[b];
+        e4 = Q.e4f[b];
+      } else {
+        sincospif(2.0f * (float)b / (float)Q.n_psi, &e2.y, &e2.x);
+        e4 = make_float2(e2.x * e2.x - e2.y * e2.y, 2.0f * e2.x * e2.y);
+      }
+      const float K = e2.x * dx + e2.y * dy;
+      const float R = 0.5f * (af + (e4.x * bx - e4.y * by));
+      if (!(R > 0.0f) || isnan(K)) continue;
+      const float kk = K * K;
+      if (br == 0.0f || kk * br > bk * R) {
         bk = kk;
         br = R;
         best_idx = (long long)a * Q.n_psi + b;
@@ -373,12 +387,12 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
   }
   __syncwarp();  // the cached columns are read by other lanes below
   for (int off = 16; off > 0; off >>= 1) {
-    const double ok = __shfl_xor_sync(0xffffffffu, bk, off);
-    const double orr = __shfl_xor_sync(0xffffffffu, br, off);
+    const float ok = __shfl_xor_sync(0xffffffffu, bk, off);
+    const float orr = __shfl_xor_sync(0xffffffffu, br, off);
     const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, off);
-    if (orr > 0.0) {
-      const double l = ok * br, r = bk * orr;
-      if (br == 0.0 || l > r || (l == r && oi < best_idx)) {
+    if (orr > 0.0f) {
+      const float l = ok * br, r = bk * orr;
+      if (br == 0.0f || l > r || (l == r && oi < best_idx)) {
         bk = ok;
         br = orr;
         best_idx = oi;
@@ -685,6 +699,8 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
       const double ang = 2.0 * M_PI * b / Q.n_psi;
       Q.e2[b] = make_double2(std::cos(ang), std::sin(ang));
       Q.e4[b] = make_double2(std::cos(2.0 * ang), std::sin(2.0 * ang));
+      Q.e2f[b] = make_float2((float)Q.e2[b].x, (float)Q.e2[b].y);
+      Q.e4f[b] = make_float2((float)Q.e4[b].x, (float)Q.e4[b].y);
     }
   return check_cuda(launch_direct(hp, pt->dev, draws_params(draws), Q, out, (cudaStream_t)stream),
                     "rift_ile_lnL_direct launch");
