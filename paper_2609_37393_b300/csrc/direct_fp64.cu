@@ -414,7 +414,11 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
   }
   const double c0 = v0 - kSkipNat - Q.ln_ub - 1e-3;
   const float c0f = (float)c0;
-  // pass 2: the log-sum-exp over the nodes that can matter
+  // pass 2: the log-sum-exp over the nodes that can matter.  A float screen
+  // first: |K| <= |K_f| + eK and R >= R_f - eR bound the double values (eK,
+  // eR cover the conversions and the float products, 8 units of 2^-24 of the
+  // summed magnitudes), so the bound K^2/(2R) - ln(R)/2 taken at those ends
+  // is an upper bound; only nodes it cannot exclude are formed in double.
   for (int a = lane; a < Q.n_phi; a += 32) {
     double2 D, B;
     double A;
@@ -422,7 +426,21 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
       column_load(col, a, D, A, B);
     else
       direct_column(C, (double)a / Q.n_phi, D, A, B);
+    const float dx = (float)D.x, dy = (float)D.y, af = (float)A, bx = (float)B.x,
+                by = (float)B.y;
+    const float eK = 4.8e-7f * (fabsf(dx) + fabsf(dy));
+    const float eR = 2.4e-7f * (fabsf(af) + fabsf(bx) + fabsf(by));
     for (int b = 0; b < Q.n_psi; ++b) {
+      if (Q.n_psi <= kPsiTab) {
+        const float2 e2 = Q.e2f[b], e4 = Q.e4f[b];
+        const float Ka = fabsf(e2.x * dx + e2.y * dy) + eK;
+        const float Rl = 0.5f * (af + (e4.x * bx - e4.y * by)) - eR;
+        if (Rl > 1e-30f && Rl < 1e30f && Ka < 1e18f) {
+          const float hu = __fdividef(Ka * Ka, 2.0f * Rl);
+          const float lg = __logf(Rl);
+          if (hu - 0.5f * lg < c0f - (1e-3f + 2e-6f * (hu + fabsf(lg) + fabsf(c0f)))) continue;
+        }
+      }
       double K, R;
       direct_node_b(Q, b, D, A, B, K, R);
       if (isnan(K + R)) {  // either is NaN (or they are opposite infinities)
