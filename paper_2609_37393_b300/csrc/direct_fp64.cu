@@ -16,7 +16,8 @@
 // at each node the Gauss-Hermite distance integral and an online log-sum-exp.
 // A first pass finds the node with the largest K^2/(2R) and evaluates it in
 // full (v0); the second pass skips nodes whose upper bound
-// K^2/(2R) + ln(sqrt(2 pi) sigma_x max p_x) is below v0 - 60.
+// K^2/(2R) + ln(sqrt(2 pi) sigma_x max p_x) is below v0 - T, T = 36 + ln(n_phi
+// n_psi): the skipped nodes together weigh below e^-36 of v0's node.
 // Geocentric time is the draw's own, or integrated over a window: by the
 // fixed-spacing rule (eq. ap:tfixed, the data coefficients formed at every
 // node) or by the band-limited rule (eq. ap:tband, the coefficients formed
@@ -46,7 +47,7 @@ constexpr int kPsiTab = 256;                // polarisation phases tabulated up 
 // pair buffers (idle during the angular sweep) up to this n_phi.
 constexpr int kColCache = (2 * kMaxModes * kMaxModes * 2) / 5;
 static_assert(5 * kColCache <= 2 * kMaxModes * kMaxModes * 2, "column cache exceeds the pair buffers");
-constexpr double kSkipNat = 60.0;
+constexpr double kSkipNat = 36.0;  // plus ln(n_phi n_psi): the skipped mass stays below e^-36
 
 struct DirectParams {
   int n_phi, n_psi, n_gh, n_t;  // n_t = 0: the draw's own t
@@ -57,6 +58,7 @@ struct DirectParams {
   double lnnorm;          // ln of 3 d_ref^3 / (d_max^3 - d_min^3)
   double lnw;             // -ln(n_phi n_psi max(n_t, 1) max(t_up, 1))
   double ln_ub;           // ln(sqrt(2 pi) norm lo^-4), the prefactor bound over sigma_x
+  double skip_nat;        // kSkipNat + ln(n_phi n_psi)
   double xi[RIFT_ILE_MAX_GH], w[RIFT_ILE_MAX_GH];
   int mixed;              // 1: the prior-weighted Gauss-Hermite sum in float
   double inv_lo;          // 1 / lo
@@ -331,10 +333,10 @@ __device__ __forceinline__ void direct_node_b(const DirectParams& Q, int b, cons
 // largest K^2/(2R), in float and by cross-multiplication; any evaluated node
 // makes a valid skip reference (its value v0 is then taken in double), the
 // largest skips the most.  Pass 2 skips
-// nodes whose bound K^2/(2R) - ln(R)/2 + ln_ub is below v0 - 60, tested in
+// nodes whose bound K^2/(2R) - ln(R)/2 + ln_ub is below v0 - T, tested in
 // float with a margin of 1e-3 nat + 2e-6 of the magnitudes (above the float
 // error), or in double where R is outside the normal float range: a skipped
-// node adds below e^-60 of v0.
+// node adds below e^-T of v0, all of them below e^-36 (T = skip_nat).
 __device__ __forceinline__ void column_store(double* col, int a, const double2& D, double A,
                                              const double2& B) {
   col[a] = D.x;
@@ -412,7 +414,7 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
     direct_node_b(Q, b, D, A, B, K, R);
     v0 = direct_distance(Q, K, R);
   }
-  const double c0 = v0 - kSkipNat - Q.ln_ub - 1e-3;
+  const double c0 = v0 - Q.skip_nat - Q.ln_ub - 1e-3;
   const float c0f = (float)c0;
   // pass 2: the log-sum-exp over the nodes that can matter.  A float screen
   // first: |K| <= |K_f| + eK and R >= R_f - eR bound the double values (eK,
@@ -703,6 +705,7 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   Q.slab = nullptr;
   Q.lnw = -std::log((double)rule->n_phi * rule->n_psi * (rule->n_t > 0 ? rule->n_t : 1) * Q.t_up);
   Q.ln_ub = std::log(std::sqrt(2.0 * M_PI) * norm) - 4.0 * std::log(Q.lo);
+  Q.skip_nat = kSkipNat + std::log((double)rule->n_phi * rule->n_psi);
   if ((rc = gauss_hermite(Q.n_gh, Q.xi, Q.w))) {
     rift_ile_set_error("rift_ile_lnL_direct: Gauss-Hermite rule failed for n=%d", Q.n_gh);
     return rc;
