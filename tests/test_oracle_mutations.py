@@ -39,6 +39,11 @@ MUTATIONS = {
                       "lnw_nodes[j] = log(wtrap) + lnZp + 2.0 * lnd;"),
     "time_slope_scale": ("dout[2 * i] += dw[tap] * row[2 * i] / dt;",
                          "dout[2 * i] += dw[tap] * row[2 * i];"),
+    # distance-marginalised gradient E[x] dK - E[x^2] dR/2 (dR/2 = dT_q at x = 1)
+    "dist_grad_half_dropped": ("g[p] = ex * dtd[p] - ex2 * dtq[p];",
+                               "g[p] = ex * dtd[p] - 2.0 * ex2 * dtq[p];"),
+    "dist_grad_mean_squared": ("g[p] = ex * dtd[p] - ex2 * dtq[p];",
+                               "g[p] = ex * dtd[p] - ex * ex * dtq[p];"),
 }
 
 
@@ -115,7 +120,24 @@ def battery():
     val, _ = scipy.integrate.quad(f, 50.0, 200.0, epsrel=1e-12, limit=400, points=[100.0 * R / K])
     if not abs(marg - (math.log(val) + K * K / (2 * R))) < 1e-5:
         failed.append("dist")
-    # 7. harmonic closed form
+    # 7. distance-marginalised gradient against central differences of the
+    # distance-marginalised lnL (eq. ap:dexp summed on the node table)
+    rng8 = np.random.default_rng(33)
+    dn = {p: truth[p] + s * rng8.standard_normal(8) for p, s in
+          (("ra", 0.02), ("dec", 0.02), ("psi", 0.1), ("incl", 0.1), ("phase", 0.1),
+           ("lnD", 0.3), ("t", 3e-4))}
+    thn = np.stack([dn[p] for p in W.PARAMS], axis=1)
+    _, gd = O.lnL_distmarg(pt, thn, x, lnw, grad=True)
+    for j in (0, 1, 2, 3, 4, 6):
+        step = 1e-6 * (1e-3 if j == 6 else 1.0)
+        tp, tm = thn.copy(), thn.copy()
+        tp[:, j] += step
+        tm[:, j] -= step
+        fd = (O.lnL_distmarg(pt, tp, x, lnw) - O.lnL_distmarg(pt, tm, x, lnw)) / (2 * step)
+        if not np.median(np.abs(gd[:, j] - fd) / np.maximum(1, np.abs(gd[:, j]))) < 1e-5:
+            failed.append("dist_grad")
+            break
+    # 8. harmonic closed form
     if not abs(O.sylm(-2, 2, 1, 1.0, 0.0) - math.sqrt(5 / (16 * math.pi)) * math.sin(1.0) *
                (1 + math.cos(1.0))) < 1e-14:
         failed.append("sylm")

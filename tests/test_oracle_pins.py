@@ -357,6 +357,51 @@ def test_distance_marginal_against_adaptive_quadrature():
     assert worst[240.0] <= worst[60.0]
 
 
+def dist_marginal_fd_errors(pt, d, x, lnw):
+    """Per component, |analytic - central difference| / max(1, |analytic|) of
+    the distance-marginalised gradient.  The node sum is a smooth function of
+    K and R whatever the table, so its derivative is E[x] dK - E[x^2] dR/2
+    over the node posterior exactly (eq. ap:dexp, eq. ap:dlog)."""
+    _, g = O.lnL_distmarg(pt, d, x, lnw, grad=True)
+    th = np.stack([d[p] for p in W.PARAMS], axis=1)
+    errs = {}
+    for j in range(7):
+        step = 1e-6 * (1e-3 if j == 6 else 1.0)  # t in seconds
+        tp, tm = th.copy(), th.copy()
+        tp[:, j] += step
+        tm[:, j] -= step
+        fd = (O.lnL_distmarg(pt, tp, x, lnw) - O.lnL_distmarg(pt, tm, x, lnw)) / (2 * step)
+        errs[j] = np.abs(g[:, j] - fd) / np.maximum(1.0, np.abs(g[:, j]))
+    return g, errs
+
+
+def test_distance_marginal_gradient_matches_central_differences():
+    """The distance-marginalised gradient against central differences of the
+    distance-marginalised lnL in ra, dec, psi, iota, phi_ref and t_c, on draws
+    near the peak where the node posterior is narrow and E[x^2] - E[x]^2 is
+    small but not negligible; the draw's own lnD is ignored, so its slot and its
+    central difference are both zero.  A dropped 1/2 on dR or E[x]^2 in place
+    of E[x^2] moves every component by ~T_q-sized amounts."""
+    point, exact, info, pt = small_point(modes=W.MODES10[:6], noise=True, snr=30.0,
+                                         rate=16384.0)
+    rng = np.random.default_rng(21)
+    truth = info["truth"]
+    spread = {"ra": 0.02, "dec": 0.02, "psi": 0.1, "incl": 0.1, "phase": 0.1, "lnD": 0.3,
+              "t": 3e-4}
+    d = rand_draws(rng, 64, truth, spread)
+    x, lnw = O.dist_nodes(50.0, 200.0, 100.0, 1e-4, 60.0)
+    g, errs = dist_marginal_fd_errors(pt, d, x, lnw)
+    assert np.all(g[:, 5] == 0.0)
+    for j in (0, 1, 2, 3, 4, 6):
+        # the cubic's slope is only C0 at knots (t, and ra/dec through t_k)
+        assert np.median(errs[j]) < 1e-5, (j, np.median(errs[j]))
+        assert np.mean(errs[j] < 1e-4) > 0.9, j
+    assert np.max(errs[5]) < 1e-12
+    # the node posterior really is spread: E[x^2] differs from E[x]^2, so the
+    # check separates the two moments
+    assert np.max(np.abs(g[:, :5])) > 10.0
+
+
 # ------------------------------------------------------------ interpolation
 
 def test_cubic_interpolant_exact_for_cubics():
