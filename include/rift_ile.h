@@ -222,7 +222,10 @@ int rift_ile_lnZ_state_async(const rift_ile_point* pt, const rift_ile_draws* dra
  * up that array's device address (cudaGetSymbolAddress) with the device
  * current, so make it before any stream capture.  All calls on a device
  * share the array: calls whose work overlaps on the GPU race and must be
- * serialised.  Synchronises `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+ * serialised.  rift_ile_release forgets the looked-up addresses (call it
+ * after a device reset; the next call looks them up again).  Sets the count
+ * of rift_ile_last_oob like rift_ile_lnZ_state.  Synchronises `stream`.
+ * Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA. */
 int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_ile_draws* draws,
                                rift_ile_precision prec, rift_ile_lse* state, void* stream);
 
@@ -299,12 +302,14 @@ int rift_ile_release(void);
 const char* rift_ile_last_error(void);
 
 /* ALU issue-rate probes used as roofline denominators (measurement support;
- * the paper has no counterpart).  ops_per_second counts one FMA as one op. */
+ * the paper has no counterpart).  ops_per_second counts one FMA as one op;
+ * FP32X2_FMA issues packed pair FMAs (two ops per instruction). */
 enum {
   RIFT_ILE_PROBE_FP32_FMA = 0,
   RIFT_ILE_PROBE_FP64_FMA = 1,
   RIFT_ILE_PROBE_MUFU_EX2 = 2,
-  RIFT_ILE_PROBE_MUFU_SIN = 3
+  RIFT_ILE_PROBE_MUFU_SIN = 3,
+  RIFT_ILE_PROBE_FP32X2_FMA = 4
 };
 int rift_ile_probe_alu(int which, double target_seconds, double* ops_per_second, double* sm_mhz);
 

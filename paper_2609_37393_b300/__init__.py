@@ -531,7 +531,7 @@ def rift_ile_last_oob() -> int:
 
 def rift_ile_probe_alu(which: int, target_seconds: float = 0.2):
     """(ops per second, SM MHz seen by the probe) of FP32 FMA (0), FP64 FMA (1),
-    MUFU ex2 (2) or MUFU sin (3)."""
+    MUFU ex2 (2), MUFU sin (3) or packed FP32 pair FMA (4, two ops each)."""
     ops = ctypes.c_double()
     mhz = ctypes.c_double()
     _check(_lib.rift_ile_probe_alu(which, target_seconds, ctypes.byref(ops), ctypes.byref(mhz)))

@@ -43,6 +43,30 @@ __global__ void probe_fma(T* sink, long long* clk, T b, T c, int iters) {
   }
 }
 
+// Packed pairs: each __ffma2_rn is one instruction carrying two FP32 FMAs
+// (sm_100 and later); counted as two operations.
+__global__ void probe_fma2(float* sink, long long* clk, float b, float c, int iters) {
+  float2 a[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i)
+    a[i] = make_float2(threadIdx.x * 1e-3f + (float)i, threadIdx.x * 2e-3f - (float)i);
+  const float2 b2 = make_float2(b, b), c2 = make_float2(c, c);
+  long long c0 = clock64();
+  uint64_t t0 = global_ns();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = __ffma2_rn(a[i], b2, c2);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += a[i].x + a[i].y;
+  if (s == 12345.678f) sink[0] = s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    clk[0] = clock64() - c0;
+    clk[1] = (long long)(global_ns() - t0);
+  }
+}
+
 __global__ void probe_ex2(float* sink, long long* clk, float b, int iters) {
   float a[kChains];
 #pragma unroll
@@ -108,8 +132,13 @@ int run_probe(int which, int blocks, int threads, int iters, void* sink,
     case RIFT_ILE_PROBE_MUFU_EX2:
       probe_ex2<<<blocks, threads>>>((float*)sink, d_clk, 0.5f, iters);
       break;
-    default:
+    case RIFT_ILE_PROBE_FP32X2_FMA:
+      probe_fma2<<<blocks, threads>>>((float*)sink, d_clk, 0.9999999f, 1e-7f, iters);
+      break;
+    case RIFT_ILE_PROBE_MUFU_SIN:
       probe_sin<<<blocks, threads>>>((float*)sink, d_clk, 0.25f, iters);
+      break;
+    default:
       break;
   }
   cudaEventRecord(e1, 0);
@@ -127,7 +156,7 @@ int run_probe(int which, int blocks, int threads, int iters, void* sink,
 
 extern "C" int rift_ile_probe_alu(int which, double target_seconds, double* ops_per_second,
                                   double* sm_mhz) {
-  if (!ops_per_second || which < 0 || which > RIFT_ILE_PROBE_MUFU_SIN || !(target_seconds > 0)) {
+  if (!ops_per_second || which < 0 || which > RIFT_ILE_PROBE_FP32X2_FMA || !(target_seconds > 0)) {
     rift_ile_set_error("rift_ile_probe_alu: invalid argument");
     return RIFT_ILE_ERR_INVALID_ARG;
   }
@@ -169,7 +198,8 @@ extern "C" int rift_ile_probe_alu(int which, double target_seconds, double* ops_
     rift_ile_set_error("rift_ile_probe_alu: probe launch failed");
     return RIFT_ILE_ERR_CUDA;
   }
-  const double ops = (double)blocks * threads * (double)iters * kChains;
+  const double ops = (double)blocks * threads * (double)iters * kChains *
+                     (which == RIFT_ILE_PROBE_FP32X2_FMA ? 2.0 : 1.0);
   *ops_per_second = ops / (1e-3 * ms);
   if (sm_mhz) *sm_mhz = (h_clk[1] > 0) ? (double)h_clk[0] / (double)h_clk[1] * 1e3 : 0.0;
   return RIFT_ILE_OK;

@@ -658,6 +658,7 @@ extern "C" int rift_ile_dist_nodes(double d_min, double d_max, double d_ref, dou
 
 extern "C" int rift_ile_release(void) {
   release_fft_plans();
+  forget_noalloc_scratch();
   std::lock_guard<std::mutex> lock(g_ws_mu);
   int cur = 0;
   cudaGetDevice(&cur);

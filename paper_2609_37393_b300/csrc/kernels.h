@@ -67,6 +67,8 @@ int lse_workspace(LseState** partials, LseState** state, unsigned long long** oo
 int validate_draws(const rift_ile_draws* d);
 DrawsParams draws_params(const rift_ile_draws* d);
 void set_last_oob(long long v);
+// Drops the cached device addresses of the allocation-free entry point's scratch (rift_ile_release).
+void forget_noalloc_scratch();
 // Destroys the cuFFT plans the precompute keeps (rift_ile_release).
 void release_fft_plans();
 

@@ -28,6 +28,7 @@
 #include <math_constants.h>
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.h"
@@ -66,6 +67,15 @@ int scratch_address(void** out) {
 }
 
 }  // namespace
+
+// Forgets the cached device addresses (rift_ile_release): after a device
+// reset the module is loaded again and the array may sit elsewhere, so the
+// next call looks the address up afresh (cudaGetSymbolAddress allocates nothing).
+void forget_noalloc_scratch() {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  for (auto& a : g_scratch_addr) a = nullptr;
+}
+
 }  // namespace rift
 
 using namespace rift;
@@ -73,7 +83,7 @@ using namespace rift;
 extern "C" int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_ile_draws* draws,
                                           rift_ile_precision prec, rift_ile_lse* state,
                                           void* stream) {
-  if (!pt || !draws || !state) {
+  if (!pt || !state) {
     rift_ile_set_error("rift_ile_lnZ_state_noalloc: NULL argument");
     return RIFT_ILE_ERR_INVALID_ARG;
   }
@@ -82,15 +92,9 @@ extern "C" int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_i
                        "RIFT_ILE_FP32_MIXED", (int)prec);
     return RIFT_ILE_ERR_INVALID_ARG;
   }
-  if (draws->n < 0 || (draws->dtype != RIFT_ILE_F32 && draws->dtype != RIFT_ILE_F64)) {
-    rift_ile_set_error("rift_ile_lnZ_state_noalloc: bad draw count or dtype");
-    return RIFT_ILE_ERR_INVALID_ARG;
-  }
-  if (draws->n > 0 && (!draws->ra || !draws->dec || !draws->psi || !draws->incl ||
-                       !draws->phase || !draws->lnD || !draws->t)) {
-    rift_ile_set_error("rift_ile_lnZ_state_noalloc: a draw parameter array is NULL");
-    return RIFT_ILE_ERR_INVALID_ARG;
-  }
+  // the same draw rules (and error codes) as every other entry point
+  int rc = validate_draws(draws);
+  if (rc) return rc;
   if (draws->n == 0) {
     *state = rift_ile_lse{-INFINITY, 0.0, 0.0, 0.0};
     return RIFT_ILE_OK;
@@ -108,24 +112,13 @@ extern "C" int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_i
     return RIFT_ILE_ERR_UNSUPPORTED;
   }
   void* base = nullptr;
-  int rc = scratch_address(&base);
-  if (rc) return rc;
+  if ((rc = scratch_address(&base))) return rc;
   LseState* partials = static_cast<LseState*>(base);
   LseState* combined = partials + kScratchPartials;
   unsigned long long* oob = reinterpret_cast<unsigned long long*>(partials + kScratchPartials + 1);
   cudaStream_t st = (cudaStream_t)stream;
 
-  DrawsParams dp;
-  dp.p[0] = draws->ra;
-  dp.p[1] = draws->dec;
-  dp.p[2] = draws->psi;
-  dp.p[3] = draws->incl;
-  dp.p[4] = draws->phase;
-  dp.p[5] = draws->lnD;
-  dp.p[6] = draws->t;
-  dp.logw = draws->logw;
-  dp.n = draws->n;
-  dp.f64 = (draws->dtype == RIFT_ILE_F64);
+  const DrawsParams dp = draws_params(draws);
 
   if ((rc = check_cuda(cudaMemsetAsync(oob, 0, sizeof(unsigned long long), st),
                        "rift_ile_lnZ_state_noalloc: clear")))
@@ -138,11 +131,15 @@ extern "C" int rift_ile_lnZ_state_noalloc(const rift_ile_point* pt, const rift_i
   if ((rc = check_cuda(launch_lse_combine(partials, blocks, (double)draws->n, combined, st),
                        "rift_ile_lnZ_state_noalloc: combine launch")))
     return rc;
-  LseState h;
-  if ((rc = check_cuda(cudaMemcpyAsync(&h, combined, sizeof(h), cudaMemcpyDeviceToHost, st),
+  // the combined state and the tap counter are adjacent: one copy brings both
+  LseState h[2];
+  if ((rc = check_cuda(cudaMemcpyAsync(h, combined, sizeof(h), cudaMemcpyDeviceToHost, st),
                        "rift_ile_lnZ_state_noalloc: copy")))
     return rc;
   if ((rc = check_cuda(cudaStreamSynchronize(st), "rift_ile_lnZ_state_noalloc"))) return rc;
-  *state = rift_ile_lse{h.m, h.s, h.s2, h.n};
+  unsigned long long taps = 0;
+  memcpy(&taps, &h[1], sizeof(taps));
+  set_last_oob((long long)taps);
+  *state = rift_ile_lse{h[0].m, h[0].s, h[0].s2, h[0].n};
   return RIFT_ILE_OK;
 }
