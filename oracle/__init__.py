@@ -16,23 +16,55 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rift_oracle.c")
-_LIB = os.path.join(_HERE, "librift_oracle.so")
+
+
+def _host_key() -> str:
+    """Short key of this host's CPU (model and instruction-set flags): the
+    oracle is compiled for the host it runs on (-march=native), so each kind
+    of host gets its own build."""
+    import hashlib
+    import platform
+    info = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith(("model name", "flags", "Features", "CPU part")):
+                    info += line
+                if line.strip() == "":
+                    break
+    except OSError:
+        pass
+    return hashlib.sha1(info.encode()).hexdigest()[:10]
+
+
+_LIB = os.path.join(_HERE, f"librift_oracle-{_host_key()}.so")
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "libopcount.so")
 
 NPAR = 7
 PARAMS = ("ra", "dec", "psi", "incl", "phase", "lnD", "t")
 
 
+def _stale(lib: str, *srcs: str) -> bool:
+    return not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(s) for s in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable -O3, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "rift_oracle.h"))
-    ):
+    """Compile the oracle with gcc (-O3 -march=native for the host it runs
+    on, no fast-math), and the op counter (opcount.cpp) beside it."""
+    hdr = os.path.join(_HERE, "rift_oracle.h")
+    if force or _stale(_LIB, _SRC, hdr):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O3", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC,
-             "-lm", "-lpthread"]
+            ["gcc", "-O3", "-march=native", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+             "-o", tmp, _SRC, "-lm", "-lpthread"]
         )
         os.replace(tmp, _LIB)
+    if force or _stale(_OPC_LIB, _OPC_SRC, hdr):
+        tmp = _OPC_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp,
+                               _OPC_SRC])
+        os.replace(tmp, _OPC_LIB)
     return _LIB
 
 
@@ -266,3 +298,43 @@ def qinterp(q: np.ndarray, t0: float, dt: float, t: float):
     dout = np.empty(2 * M)
     oob = lib().ora_qinterp(_ptr(qq), n, M, t0, dt, t, _ptr(out), _ptr(dout))
     return out.view(np.complex128), dout.view(np.complex128), int(oob)
+
+
+_opc = None
+
+
+def op_counts(pt: OraclePoint, draws, which: str, logw=None, x_nodes=None, lnw_nodes=None):
+    """Counted plain evaluation (opcount.cpp) over the draws, one thread.
+
+    which: "lnZ" (lnL and the online log-sum-exp), "grad" (lnL and its
+    gradient), "dist" (distance-marginalised lnL over the node table) or
+    "dist_grad".  Returns a dict with the per-draw values, the gradient
+    [N, 7] (gradient modes), the online LSE (max, sum e, sum e^2) ("lnZ") and
+    the totals add, mul, div, special (sin, cos, exp, log) over the N draws;
+    flops = add + mul + div."""
+    global _opc
+    if _opc is None:
+        build()
+        _opc = ctypes.CDLL(_OPC_LIB)
+        P = ctypes.c_void_p
+        _opc.ora_count_ops.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_int,
+                                       P, P, P, P]
+        _opc.ora_count_ops.restype = ctypes.c_int
+    code = {"lnZ": 0, "grad": 1, "dist": 2, "dist_grad": 3}[which]
+    th = _theta(draws)
+    N = th.shape[0]
+    vals = np.empty(N)
+    g = np.zeros((N, NPAR))
+    lse = np.zeros(3)
+    cnt = np.zeros(4, dtype=np.int64)
+    lw = None if logw is None else np.ascontiguousarray(logw, dtype=np.float64)
+    xn = None if x_nodes is None else np.ascontiguousarray(x_nodes, dtype=np.float64)
+    wn = None if lnw_nodes is None else np.ascontiguousarray(lnw_nodes, dtype=np.float64)
+    rc = _opc.ora_count_ops(pt.ref, _ptr(th), N, _ptr(lw), _ptr(xn), _ptr(wn),
+                            0 if xn is None else xn.shape[0], code, _ptr(vals), _ptr(g),
+                            _ptr(lse), _ptr(cnt))
+    if rc != 0:
+        raise ValueError(which)
+    add, mul, div, special = (int(v) for v in cnt)
+    return {"values": vals, "grad": g, "lse": lse, "add": add, "mul": mul, "div": div,
+            "special": special, "flops": add + mul + div, "n": N}
