@@ -58,14 +58,16 @@ W_PARAMS = ("ra", "dec", "psi", "incl", "phase", "lnD", "t")
 WORKLOAD = "3G ILE: ET triangle + CE40 (K=4), 10 modes, SNR 600, 2^22 float32 draws"
 
 
-def algorithmic_ops(point: dict, R: int, ncls: int) -> dict:
-    """Declared FP32-pipe operation count of one draw of the FP32-mixed lnL ->
-    LSE pass for this point: every FP32 add, multiply and fused multiply-add
-    the method's arithmetic takes at the stated precision (one op each), with
-    the double-float steps at their operation counts (TwoSum 6, FastTwoSum 3,
-    TwoProduct 2, pair product 7, pair sum 20, compensated multiply-add 12,
-    anchored sine/cosine 82, anchored exponential 44).  Addressing, loads,
-    comparisons and control are not counted."""
+def kernel_fp32_ops(point: dict, R: int, ncls: int) -> dict:
+    """FP32-pipe operations the FP32-mixed kernel issues per draw of the lnL ->
+    LSE pass for this point, built from its own arithmetic: every FP32 add,
+    multiply and fused multiply-add (one op each), the double-float steps at
+    their operation counts (TwoSum 6, FastTwoSum 3, TwoProduct 2, pair product
+    7, pair sum 20, compensated multiply-add 12, anchored sine/cosine 82,
+    anchored exponential 44); addressing, loads, comparisons and control not
+    counted.  This measures how busy the FP32 pipe is (fp32_issue_frac), not
+    the method's work: the roofline's numerator is the algorithmic count of
+    oracle/flops.json."""
     K, M = int(point["K"]), int(point["M"])
     ell = [int(v) for v in point["ell"]]
     em = [int(v) for v in point["em"]]
@@ -139,10 +141,30 @@ def captured_traffic():
         return None
 
 
-def plain_formula_flops(K: int, M: int) -> int:
-    """FLOPs of a plain single-precision evaluation of eq. def:lnL:Decomposed
-    per draw (the survey's count F(K, M))."""
-    return 40 + 66 * K + 20 * M + K * (12 + 16 * M) + K * (8 * M + 6) + (K + 1) * 6 * M * (M + 1) + 10 * K + 4
+FLOPS_FILE = os.path.join(ROOT, "oracle", "flops.json")
+
+
+def frozen_flops(key: str) -> dict:
+    """Algorithmic operations per draw of one workload, as frozen in
+    oracle/flops.json by oracle/freeze_flops.py from the counted plain FP64
+    evaluation (add, subtract, multiply, divide one flop each; a multiply-add
+    two; sin, cos, exp, log counted apart).  Read as data."""
+    with open(FLOPS_FILE) as f:
+        return json.load(f)["workloads"][key]
+
+
+def roofline_block(flops_per_draw: float, draws_per_s: float, peak_flops: float,
+                   peak_source: str, **extra) -> dict:
+    """achieved = frozen algorithmic flops per draw x draws/s; frac against the
+    measured peak in flop/s (two per FMA)."""
+    achieved = flops_per_draw * draws_per_s
+    out = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
+           "unit": "TFLOP/s", "frac": achieved / peak_flops,
+           "flops_per_draw": flops_per_draw,
+           "flops_source": "oracle/flops.json (counted plain FP64 evaluation, oracle/opcount.cpp)",
+           "peak_source": peak_source}
+    out.update(extra)
+    return out
 
 
 class ClockSampler:
@@ -208,7 +230,8 @@ def dist_env():
 
 def cpu_baseline(point, draws, logw, budget_s: float = 12.0):
     """The FP64 oracle on a bounded sample of the workload's draws, all host
-    cores; scaled to draws/s."""
+    cores; scaled to draws/s.  Returns (the baseline record, the oracle's lnL on
+    the sample, the sample size)."""
     import oracle as O
     opt = O.OraclePoint(point)
     threads = O.default_threads()
@@ -223,8 +246,15 @@ def cpu_baseline(point, draws, logw, budget_s: float = 12.0):
         if dt > budget_s / 4 or n >= len(draws["t"]):
             break
         n = min(len(draws["t"]), int(n * max(2.0, min(8.0, budget_s / 4 / max(dt, 1e-3)))))
-    return {"value": n / dt, "unit": "draws/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {n} draws of the 2^22-draw batch, lnL + lnZ in FP64 C, {threads} threads"}
+    return ({"value": n / dt, "unit": "draws/s", "cores": threads, "kind": "oracle",
+             "sample": f"first {n} draws of the 2^22-draw batch, lnL + lnZ in FP64 C, {threads} threads"},
+            lnl, n)
+
+
+def O_lnZ(lnl, logw):
+    """lnZ of the oracle's values (its FP64 two-pass log-sum-exp)."""
+    import oracle as O
+    return O.lnZ(np.asarray(lnl, dtype=np.float64), np.asarray(logw, dtype=np.float64))
 
 
 def cpu_single_thread(point, draws, n=1 << 14):
@@ -810,8 +840,11 @@ def main():
     K, M = point["K"], point["M"]
     stream = torch.cuda.current_stream()
 
-    # ALU peak of this GPU (roofline denominator), measured before the timing
-    fp32_ops, probe_mhz = R.rift_ile_probe_alu(0, 0.2)
+    # ALU peaks of this GPU (roofline denominators), measured before the timing
+    fp32_ops, probe_mhz = R.rift_ile_probe_alu(R.PROBE_FP32_FMA, 0.2)
+    fp32x2_ops, _ = R.rift_ile_probe_alu(R.PROBE_FP32X2_FMA, 0.2)
+    fp64_ops, _ = R.rift_ile_probe_alu(R.PROBE_FP64_FMA, 0.2)
+    fma32 = max(fp32_ops, fp32x2_ops)  # FP32 FMA rate, scalar or packed pairs
 
     # one step: the fused lnL -> LSE kernel and the merge of its partials,
     # the LSE state left on the device (steps are chained on the stream; the
@@ -821,12 +854,29 @@ def main():
     def step():
         R.rift_ile_lnZ_state_async(pt, d_dev, R.FP32_MIXED, out=state_dev)
 
+    def event_ms(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    ms_est = event_ms(3)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
+        # sustained load before the timed steps (further warm-up, not timed
+        # into the value): >= 1 s of the same step in 8 event-timed groups, so
+        # the clock record spans a second or more of this load and the spread
+        # of the step time is on the line
+        group = max(1, int(math.ceil(1.0 / 8 / (ms_est * 1e-3))))
+        soak = [event_ms(group) for _ in range(8)]
+        barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
@@ -841,7 +891,8 @@ def main():
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms = float(ms_t.item())
     value = world * N_DRAWS / (ms * 1e-3)
-    lnz = R.lnZ_from_state(state)
+    # lnZ, sigma, n_eff from the LSE state through the library's merge
+    lnz = R.rift_ile_lnZ_merge([state])[0]
     # the path's one exchange step: every rank's 32-byte LSE state, merged
     merged = R.lnZ_merge_ranks(state)[0] if dist is not None else lnz
 
@@ -869,6 +920,7 @@ def main():
         "fp64_lnZ_draws_per_s": N_DRAWS / (ms_fp64 * 1e-3),
         "speedup_mixed_vs_fp64": ms_fp64 / ms,
     }
+    ms_grad = ms_grad64 = None
     try:
         g = torch.empty((7, N_DRAWS), dtype=torch.float64, device="cuda")
         ms_grad = timed(lambda: R.rift_ile_lnL_grad(pt, d_dev, R.FP32_MIXED, out32, g), 3)
@@ -925,26 +977,50 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) / max(3, args.steps // 4) * 1e3
 
-    # ---- roofline of the dominant kernel (the fused lnL -> LSE kernel)
+    # ---- roofline of the dominant kernel (the fused lnL -> LSE kernel): the
+    # algorithmic flops of oracle/flops.json over the measured FP32 peak
+    # (2 flops per FMA); the step time includes the ~1% LSE combine
     pinfo = pt.info()
-    ops = algorithmic_ops(point, pinfo["R"], pinfo["ncls"])
-    achieved = ops["ops_per_draw"] * N_DRAWS / (ms * 1e-3)
+    fl = frozen_flops("3g_ile_k4_m10")
+    assert fl["K"] == K and fl["M"] == M
+    kops = kernel_fp32_ops(point, pinfo["R"], pinfo["ncls"])
     tr = captured_traffic()
     # bytes per launch of this step's size (traffic grows with the draws)
     traffic = None if tr is None else tr[0] * N_DRAWS / tr[1]
-    roofline = {
-        "bound": "alu", "achieved": achieved / 1e12, "peak": fp32_ops / 1e12,
-        "unit": "Tops/s (FP32-pipe ops, one FMA = one op)", "frac": achieved / fp32_ops,
-        "traffic": traffic,
-        "ops_per_draw": ops["ops_per_draw"],
-        "peak_source": f"measured FP32 FMA issue rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu)",
-        "plain_formula_flops_per_draw": plain_formula_flops(K, M),
-    }
+    peak_src = (f"2 x measured FP32 FMA rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu: scalar "
+                f"{fp32_ops:.3e}/s, packed pairs {fp32x2_ops:.3e}/s; the larger)")
+    roofline = roofline_block(
+        fl["lnZ_forward"]["flops"], N_DRAWS / (ms * 1e-3), 2 * fma32, peak_src, traffic=traffic,
+        fp32_issue_frac=kops["ops_per_draw"] * N_DRAWS / (ms * 1e-3) / fma32,
+        kernel_fp32_ops_per_draw=kops["ops_per_draw"])
+    rooflines = {}
+    if ms_grad is not None:
+        rooflines["fp32_mixed_fwd_bwd"] = roofline_block(
+            fl["fwd_bwd"]["flops"], N_DRAWS / (ms_grad * 1e-3), 2 * fma32, peak_src)
+    rooflines["fp64_lnZ"] = roofline_block(
+        fl["lnZ_forward"]["flops"], N_DRAWS / (ms_fp64 * 1e-3), 2 * fp64_ops,
+        "2 x measured FP64 FMA rate (rift_ile_probe_alu)")
+    if ms_grad64 is not None:
+        rooflines["fp64_fwd_bwd"] = roofline_block(
+            fl["fwd_bwd"]["flops"], N_DRAWS / (ms_grad64 * 1e-3), 2 * fp64_ops,
+            "2 x measured FP64 FMA rate (rift_ile_probe_alu)")
 
     cpu = cpu1 = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(point, draws, logw)
+        cpu, ora_lnl, n_ora = cpu_baseline(point, draws, logw)
         cpu1 = cpu_single_thread(point, draws)
+        # the measured path against the FP64 oracle on the oracle's sample
+        near_o = ora_lnl >= ora_lnl.max() - 50.0
+        sub = R.Draws({p: draws[p][:n_ora] for p in W.PARAMS}, logw[:n_ora])
+        z_sub = R.rift_ile_lnZ(pt, sub, R.FP32_MIXED)
+        z_ora = O_lnZ(ora_lnl, logw[:n_ora])
+        precision.update({
+            "max_abs_dlnL_within_50nat_vs_oracle": float(np.max(np.abs(got[:n_ora] - ora_lnl)[near_o])),
+            "max_rel_dlnL_all_vs_oracle": float(np.max(np.abs(got[:n_ora] - ora_lnl) /
+                                                       np.maximum(1.0, np.abs(ora_lnl)))),
+            "abs_dlnZ_vs_oracle": abs(z_sub[0] - z_ora[0]),
+            "oracle_sample_draws": int(n_ora),
+        })
 
     if rank == 0:
         line = {
@@ -960,11 +1036,15 @@ def main():
             "e2e": {"value": world * N_DRAWS / (e2e_ms * 1e-3), "unit": "draws/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 32 + 8},
             "gpu_launches": 2 * args.steps,
+            "ms_per_step_soak": {"median": statistics.median(soak), "min": min(soak),
+                                 "max": max(soak), "groups": len(soak), "steps_per_group": group,
+                                 "seconds": sum(soak) * group * 1e-3},
             "variants": variants,
             "precision": precision,
             "lnZ_all_ranks": {"lnZ": merged[0], "sigma_lnZ": merged[1], "n_eff": merged[2],
                               "draws": world * N_DRAWS},
             "roofline": roofline,
+            "rooflines_other": rooflines,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
             "cpu_oracle_single_thread": cpu1,

@@ -9,7 +9,6 @@ fails if the library has not been built.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -529,6 +528,9 @@ def rift_ile_last_oob() -> int:
     return int(_lib.rift_ile_last_oob())
 
 
+PROBE_FP32_FMA, PROBE_FP64_FMA, PROBE_MUFU_EX2, PROBE_MUFU_SIN, PROBE_FP32X2_FMA = range(5)
+
+
 def rift_ile_probe_alu(which: int, target_seconds: float = 0.2):
     """(ops per second, SM MHz seen by the probe) of FP32 FMA (0), FP64 FMA (1),
     MUFU ex2 (2), MUFU sin (3) or packed FP32 pair FMA (4, two ops each)."""
@@ -563,13 +565,6 @@ def lnZ_merge_ranks(state, group=None):
     states = [None] * world
     dist.all_gather_object(states, tuple(float(v) for v in state), group=group)
     return rift_ile_lnZ_merge(states)
-
-
-def lnZ_from_state(state):
-    m, s, s2, n = state
-    if n <= 0:
-        return -math.inf, math.nan, 0.0
-    return (m + math.log(s) - math.log(n), math.sqrt(max(0.0, s2 / (s * s) - 1.0 / n)), s)
 
 
 # ------------------------------------------------ composite-index response
