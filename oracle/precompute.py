@@ -44,6 +44,29 @@ def q_table_direct(freq, wgt, hlm, dk, t0, dt, n):
                      for k in range(K)])
 
 
+def q_pregrid(q_native, r: int):
+    """The fine table of eq. q-time-pregrid from a native-rate table, in the
+    four steps the paper states: reflect each (detector, mode) series
+    q_0 .. q_{n-1} into q_0 .. q_{n-1}, q_{n-1} .. q_0 (its periodic extension
+    is then continuous), take its DFT, zero-pad the coefficients from length
+    2n to 2rn (the Z_r of eq. q-time-pregrid: positive frequencies at the
+    start, negative at the end, zeros between), and invert with the 1/(2n) of
+    the shorter series; sample m is the trigonometric interpolant at
+    t0 + m h / r.  The reflected series has no Nyquist component (its
+    (-1)^j sum cancels between the halves), so no bin needs splitting.
+    q_native [K][n][M] -> [K][r (n - 1) + 1][M] complex128 (the native window)."""
+    q = np.asarray(q_native, dtype=np.complex128)
+    K, n, M = q.shape
+    refl = np.concatenate([q, q[:, ::-1, :]], axis=1)        # [K][2n][M]
+    X = np.fft.fft(refl, axis=1)                              # sum_j x_j e^{-2 pi i k j / 2n}
+    N, L = 2 * n, 2 * n * r
+    Y = np.zeros((K, L, M), dtype=np.complex128)
+    Y[:, :n, :] = X[:, :n, :]                                 # frequencies 0 .. n-1
+    Y[:, L - n + 1:, :] = X[:, n + 1:, :]                     # -(n-1) .. -1
+    y = np.fft.ifft(Y, axis=1) * (L / N)                      # (1/N) sum_k Y_k e^{+2 pi i k m / L}
+    return y[:, :r * (n - 1) + 1, :]
+
+
 def uv_direct(wgt, hlm):
     """(U, V): [K][M][M] each; h(-f_q) is the grid's mirror entry nf - 1 - q."""
     wgt = np.asarray(wgt)
