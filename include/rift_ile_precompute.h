@@ -86,6 +86,33 @@ int rift_ile_rotation_bank(const double* hlm, int32_t n_modes, int32_t nf, doubl
 int rift_ile_arm_bank(const double* hlm, int32_t n_modes, int32_t nf, double df, double T,
                       int32_t p_max, double* bank_out, void* stream);
 
+/* The fine table of eq. q-time-pregrid from a native-rate one: per
+ * (detector, mode) series q_j = Q(t0 + j h), j < n, the reflected series
+ * q_0 .. q_{n-1}, q_{n-1} .. q_0 of length 2n (its periodic extension is
+ * continuous), its DFT, the coefficients zero-padded to length 2 r n (the
+ * Z_r of eq. q-time-pregrid: frequencies 0 .. n-1 first, -(n-1) .. -1 last,
+ * zeros between; the reflected series has no Nyquist component), and the
+ * inverse DFT scaled by 1/(2n): sample m is the trigonometric interpolant
+ * of the reflected series at t0 + m h / r, and the fine table passes
+ * through every native sample (m = r j).  The first r (n - 1) + 1 samples,
+ * the native window, are written.  The four-point cubic of the likelihood
+ * kernels then reads the fine table (eq. ap:q-pregrid-rate: h = 1/4096 s,
+ * r = 8 gives 32 768 Hz).  Two batched cuFFT transforms (lengths 2n and
+ * 2rn, K M series each) in FP64.
+ *   Q_native  DEVICE [K][n][M] complex, q_dtype_in RIFT_ILE_C64 or RIFT_ILE_C128
+ *   Q_fine    DEVICE [K][r (n - 1) + 1][M] complex, q_dtype_out likewise
+ * Requirements: K, M >= 1, K M <= 4096, n >= 1, 1 <= r <= 64,
+ * 2 r n <= 2^27.  Ownership: the caller owns both tables (they must not
+ * overlap); the call allocates its two FFT work buffers (K M 2n and
+ * K M 2rn complex doubles) stream-ordered and frees them before returning,
+ * and keeps one cuFFT plan per (device, length, batch) until
+ * rift_ile_release.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, SHAPE, UNSUPPORTED, CUDA (cuFFT failures included),
+ * ALLOC. */
+int rift_ile_pregrid(const void* Q_native, int32_t n_det, int32_t n_modes, int32_t n,
+                     int32_t q_dtype_in, int32_t r, void* Q_fine, int32_t q_dtype_out,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

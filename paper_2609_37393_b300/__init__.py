@@ -758,6 +758,34 @@ def rift_ile_precompute(hlm, dk, wgt, df, q_t0, q_dt, q_len, q_dtype="complex64"
     return Q, U, V
 
 
+_lib.rift_ile_pregrid.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]
+
+
+def rift_ile_pregrid(q_native, r: int, q_dtype="complex64", out=None, stream=None):
+    """The fine table Q_fine[K, r (n - 1) + 1, M] of eq. q-time-pregrid from a
+    native-rate table q_native[K, n, M] (complex64 or complex128 CUDA tensor,
+    or array-like copied to the current device): reflected series, DFT,
+    zero-padding x r, inverse DFT, on the GPU (cuFFT).  The fine spacing is
+    the native spacing / r, from the same t0."""
+    torch = _torch()
+    q = q_native
+    if not (torch.is_tensor(q) and q.is_cuda):
+        q = torch.as_tensor(np.asarray(q)).to("cuda")
+    if q.dtype not in (torch.complex64, torch.complex128):
+        q = q.to(torch.complex128)
+    q = q.contiguous()
+    K, n, M = q.shape
+    qt = {"complex64": torch.complex64, "complex128": torch.complex128}[q_dtype]
+    if out is None:
+        out = torch.empty((K, int(r) * (n - 1) + 1, M), dtype=qt, device=q.device)
+    with torch.cuda.device(q.device):
+        _check(_lib.rift_ile_pregrid(q.data_ptr(), K, M, n, 1 if q.dtype == torch.complex128 else 0,
+                                     int(r), out.data_ptr(), 1 if out.dtype == torch.complex128 else 0,
+                                     _stream(stream)))
+    return out
+
+
 _lib.rift_ile_comp_lnL_grad.argtypes = [_P, _P, _P, _P, _P]
 
 

@@ -69,6 +69,10 @@ DrawsParams draws_params(const rift_ile_draws* d);
 void set_last_oob(long long v);
 // Drops the cached device addresses of the allocation-free entry point's scratch (rift_ile_release).
 void forget_noalloc_scratch();
+// One batched in-place double-complex transform with the cached cuFFT plan of
+// (device, nfft, batch): direction < 0 forward (e^{-2 pi i}), else inverse
+// (e^{+2 pi i}, unnormalised).  Thread-safe; asynchronous on st.
+int fft_z2z_inplace(double2* data, long long nfft, int batch, int direction, cudaStream_t st);
 // Destroys the cuFFT plans the precompute keeps (rift_ile_release).
 void release_fft_plans();
 

@@ -213,6 +213,23 @@ int blocks_for(long long total) {
 
 }  // namespace
 
+int fft_z2z_inplace(double2* data, long long nfft, int batch, int direction, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  cufftHandle plan;
+  int rc = get_plan(nfft, batch, &plan);
+  if (rc) return rc;
+  cufftResult r = cufftSetStream(plan, st);
+  if (r == CUFFT_SUCCESS)
+    r = cufftExecZ2Z(plan, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data,
+                     direction < 0 ? CUFFT_FORWARD : CUFFT_INVERSE);
+  if (r != CUFFT_SUCCESS) {
+    rift_ile_set_error("cuFFT transform of length %lld (batch %d) failed: cufftResult %d", nfft,
+                       batch, (int)r);
+    return RIFT_ILE_ERR_CUDA;
+  }
+  return RIFT_ILE_OK;
+}
+
 void release_fft_plans() {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   int cur = 0;
