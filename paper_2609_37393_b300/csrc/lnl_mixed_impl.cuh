@@ -74,7 +74,7 @@ struct A12Smem {
 // per-thread x F_k of the K detectors.
 template <int RR>
 __host__ __device__ inline size_t mixed_smem_bytes(int ncls, int R, int M, int K) {
-  size_t b = (size_t)ncls * R * M * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  size_t b = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
   if (A12Smem<RR>::on) b += (size_t)RR * kMixedThreads * 16;
   return b + (size_t)K * kMixedThreads * 16;
 }
@@ -82,14 +82,14 @@ __host__ __device__ inline size_t mixed_smem_bytes(int ncls, int R, int M, int K
 template <int RR>
 __device__ __forceinline__ float4* a12_slice(float4* smem4, int ncls, int R, int M) {
   if (!A12Smem<RR>::on) return nullptr;
-  const size_t off = (size_t)ncls * R * M * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  const size_t off = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + off) + threadIdx.x;
 }
 
 // This thread's slots of x F_k (as head/tail pairs), slot k at [k * kMixedThreads].
 template <int RR>
 __device__ __forceinline__ float4* xf_slice(float4* smem4, int ncls, int R, int M) {
-  size_t off = (size_t)ncls * R * M * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  size_t off = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
   if (A12Smem<RR>::on) off += (size_t)RR * kMixedThreads * 16;
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + off) + threadIdx.x;
 }
@@ -575,10 +575,12 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     // a1 = A y, a2 = A J y by the split product: the products of the 10-bit
     // head of A with the 9-bit head of y are exact and their sum stays below
     // 2^24 quanta, so ex1/ex2 are exact; every other term is ~2^-9 smaller.
-    float ex1[RR], ex2[RR], co1[RR], co2[RR];
+    // (ex1, ex2) and (co1, co2) of each direction advance together as packed
+    // pairs (one FFMA2 issues both FMAs)
+    float2 ex[RR], co[RR];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) ex1[r] = ex2[r] = co1[r] = co2[r] = 0.f;
-    const float4* Ac = sA + (size_t)c * R * M;
+    for (int r = 0; r < RR; ++r) ex[r] = co[r] = make_float2(0.f, 0.f);
+    const float4* Ac = sA + (size_t)c * R * M * 2;
     // modes in order of increasing |m| (P.morder): e^{i |m| phi} is reused
     // across modes of equal |m| and stepped by one complex product with
     // e^{i phi} when |m| grows by one; otherwise an anchored sine/cosine
@@ -615,42 +617,52 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       split_y(yi.hi, yi1, yi2);
       yr2 = __fadd_rn(yr2, yr.lo);
       yi2 = __fadd_rn(yi2, yi.lo);
+      const float2 pr1 = make_float2(yr1, yr1), pi1 = make_float2(yi1, yi1);
+      const float2 pr2 = make_float2(yr2, yr2), pi2 = make_float2(yi2, yi2);
+      const float2 prh = make_float2(yr.hi, yr.hi), pih = make_float2(yi.hi, yi.hi);
 #pragma unroll
       for (int r = 0; r < RR; ++r) {
         if (EXACT || r < R) {
-          // (head, tail) of A[r][a] and of A[r][M + a]
-          const float4 ah = Ac[r * M + j];
-          // a1_r += A_t yr + A_b yi ;  a2_r += A_b yr - A_t yi
-          ex1[r] = fmaf(ah.x, yr1, ex1[r]);
-          ex1[r] = fmaf(ah.z, yi1, ex1[r]);
-          ex2[r] = fmaf(ah.z, yr1, ex2[r]);
-          ex2[r] = fmaf(-ah.x, yi1, ex2[r]);
-          float t1 = fmaf(ah.x, yr2, co1[r]);
-          t1 = fmaf(ah.y, yr.hi, t1);
-          t1 = fmaf(ah.z, yi2, t1);
-          co1[r] = fmaf(ah.w, yi.hi, t1);
-          float t2 = fmaf(ah.z, yr2, co2[r]);
-          t2 = fmaf(ah.w, yr.hi, t2);
-          t2 = fmaf(-ah.x, yi2, t2);
-          co2[r] = fmaf(-ah.y, yi.hi, t2);
+          // with t = A[r][a], b = A[r][M + a] as (head, tail):
+          // ap = (t_h, b_h, t_t, b_t), an = (b_h, -t_h, b_t, -t_t);
+          // a1_r += t yr + b yi ;  a2_r += b yr - t yi
+          const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
+          ex[r] = __ffma2_rn(make_float2(ap.x, ap.y), pr1, ex[r]);
+          ex[r] = __ffma2_rn(make_float2(an.x, an.y), pi1, ex[r]);
+          co[r] = __ffma2_rn(make_float2(ap.x, ap.y), pr2, co[r]);
+          co[r] = __ffma2_rn(make_float2(ap.z, ap.w), prh, co[r]);
+          co[r] = __ffma2_rn(make_float2(an.x, an.y), pi2, co[r]);
+          co[r] = __ffma2_rn(make_float2(an.z, an.w), pih, co[r]);
         }
       }
     }
     // a1_r, a2_r as (head, tail) on the grid of the larger of the two: the
-    // template product below takes head x head exactly
+    // template product below takes head x head exactly.  Stored by direction
+    // pairs (r, r + 1), r even: slot r = (a1 heads, a1 tails) and slot r + 1 =
+    // (a2 heads, a2 tails), each component pair (r, r + 1) adjacent for the
+    // packed instructions of the residual loop
     constexpr bool kA12S = A12Smem<RR>::on;
     float4 a12r[kA12S ? 1 : RR];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      const df u = two_sum(ex1[r], co1[r]), v = two_sum(ex2[r], co2[r]);
-      const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
-      const float uh = head_of(u.hi, C), vh = head_of(v.hi, C);
-      const float4 q = make_float4(uh, __fadd_rn(__fsub_rn(u.hi, uh), u.lo), vh,
-                                   __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
+    for (int r = 0; r < RR; r += 2) {
+      float uh[2], ut[2], vh[2], vt[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const df u = two_sum(ex[r + h].x, co[r + h].x), v = two_sum(ex[r + h].y, co[r + h].y);
+        const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
+        uh[h] = head_of(u.hi, C);
+        vh[h] = head_of(v.hi, C);
+        ut[h] = __fadd_rn(__fsub_rn(u.hi, uh[h]), u.lo);
+        vt[h] = __fadd_rn(__fsub_rn(v.hi, vh[h]), v.lo);
+      }
+      const float4 qa = make_float4(uh[0], uh[1], ut[0], ut[1]);
+      const float4 qb = make_float4(vh[0], vh[1], vt[0], vt[1]);
       if constexpr (kA12S) {
-        a12s[r * kMixedThreads] = q;
+        a12s[r * kMixedThreads] = qa;
+        a12s[(r + 1) * kMixedThreads] = qb;
       } else {
-        a12r[r] = q;
+        a12r[r] = qa;
+        a12r[r + 1] = qb;
       }
     }
     auto get_a = [&](int r) -> float4 {
@@ -662,15 +674,16 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     };
     const float* gc = sg + c * R;
     df delay = df{0.f, 0.f};
-    float G1[GRAD ? RR : 1], G2[GRAD ? RR : 1];
-    float G1B[TWO ? RR : 1], G2B[TWO ? RR : 1];
+    // G1, G2 (and G1B, G2B) by direction pairs: .x direction r, .y r + 1
+    float2 G1[GRAD ? RR / 2 : 1], G2[GRAD ? RR / 2 : 1];
+    float2 G1B[TWO ? RR / 2 : 1], G2B[TWO ? RR / 2 : 1];
     if (GRAD) {
 #pragma unroll
-      for (int r = 0; r < RR; ++r) G1[r] = G2[r] = 0.f;
+      for (int r = 0; r < RR / 2; ++r) G1[r] = G2[r] = make_float2(0.f, 0.f);
     }
     if (TWO) {
 #pragma unroll
-      for (int r = 0; r < RR; ++r) G1B[r] = G2B[r] = 0.f;
+      for (int r = 0; r < RR / 2; ++r) G1B[r] = G2B[r] = make_float2(0.f, 0.f);
     }
 #if RIFT_MIXED_DET_UNROLL
 #pragma unroll kDetUnroll
@@ -762,75 +775,91 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
       // weights' sum, the low part of w taken out of the taps and subtracted
       // once (the weights with sigma removed sum to one).
-      float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f, g1B = 0.f, g2B = 0.f;
+      // Both directions of a pair advance together in packed FP32 pairs
+      // (FFMA2 / FADD2 / FMUL2 issue two operations each).  The template is
+      // formed negated, nw = -w (negation is exact, so every rounding is the
+      // one of the unnegated form), which turns e - w into a packed add.
+      const float2 nxrh = make_float2(-xrh, -xrh), nxrt = make_float2(-xrt, -xrt);
+      const float2 nxih = make_float2(-xih, -xih), nxit = make_float2(-xit, -xit);
+      const float2 xFr2 = make_float2(xFr.hi, xFr.hi), xFi2 = make_float2(xFi.hi, xFi.hi);
+      float2 wt2[4], wtd2[4];
+#pragma unroll
+      for (int tap = 0; tap < 4; ++tap) {
+        wt2[tap] = make_float2(wt[tap], wt[tap]);
+        wtd2[tap] = make_float2(wtd[tap], wtd[tap]);
+      }
+      const float2 nsig = make_float2(-sigma, -sigma);
+      const float2 zero2 = make_float2(0.f, 0.f);
+      float2 q2p = zero2, nulp = zero2, redp = zero2, g1p = zero2, g2p = zero2, g1Bp = zero2,
+             g2Bp = zero2;
       dacc w2 = dacc_zero();
 #pragma unroll
       for (int r = 0; r < RR; r += 2) {
         if (EXACT || r < R) {
-          df wv[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float4 q = get_a(r + h);  // (a1 head, a1 tail, a2 head, a2 tail)
-            float lo = xrh * q.y;
-            lo = fmaf(xrt, q.x, lo);
-            lo = fmaf(xrt, q.y, lo);
-            lo = fmaf(xih, q.w, lo);
-            lo = fmaf(xit, q.z, lo);
-            lo = fmaf(xit, q.w, lo);
-            wv[h] = df{fmaf(xrh, q.x, xih * q.z), lo};
-          }
-          float rs0 = 0.f, rs1 = 0.f, ed0 = 0.f, ed1 = 0.f;
+          const float4 qa = get_a(r), qb = get_a(r + 1);  // (a1 | a2) heads, tails of r, r + 1
+          const float2 a1h = make_float2(qa.x, qa.y), a1t = make_float2(qa.z, qa.w);
+          const float2 a2h = make_float2(qb.x, qb.y), a2t = make_float2(qb.z, qb.w);
+          float2 nlo = __fmul2_rn(nxrh, a1t);
+          nlo = __ffma2_rn(nxrt, a1h, nlo);
+          nlo = __ffma2_rn(nxrt, a1t, nlo);
+          nlo = __ffma2_rn(nxih, a2t, nlo);
+          nlo = __ffma2_rn(nxit, a2h, nlo);
+          nlo = __ffma2_rn(nxit, a2t, nlo);
+          const float2 nhi = __ffma2_rn(nxrh, a1h, __fmul2_rn(nxih, a2h));
+          float2 rs = zero2, ed = zero2;
 #pragma unroll
           for (int tap = 0; tap < 4; ++tap) {
-            // rows hold R pairs, R even: two entries per 16-byte load
-            const float4 e2 = __ldg(reinterpret_cast<const float4*>(Ej + tap * R + r));
-            const float d0 = __fadd_rn(__fsub_rn(e2.x, wv[0].hi), e2.y);
-            const float d1 = __fadd_rn(__fsub_rn(e2.z, wv[1].hi), e2.w);
-            rs0 = fmaf(wt[tap], d0, rs0);
-            rs1 = fmaf(wt[tap], d1, rs1);
-            if (tap == 1) {  // sigma is ~1 ulp of wt: applied apart
-              rs0 = fmaf(-sigma, d0, rs0);
-              rs1 = fmaf(-sigma, d1, rs1);
-            }
-            if (GRAD) {  // dt edot = sum_i wtd_i (e_i - w)  (the wtd sum to zero)
-              ed0 = fmaf(wtd[tap], d0, ed0);
-              ed1 = fmaf(wtd[tap], d1, ed1);
+            // rows hold R directions in pairs: (hi_r, hi_r+1, lo_r, lo_r+1)
+            const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + tap * R + r));
+            const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
+                                        make_float2(e4.z, e4.w));
+            rs = __ffma2_rn(wt2[tap], d, rs);
+            if (tap == 1) rs = __ffma2_rn(nsig, d, rs);  // sigma is ~1 ulp of wt: applied apart
+            if (GRAD) ed = __ffma2_rn(wtd2[tap], d, ed);  // dt edot = sum_i wtd_i (e_i - w)
+          }
+          const float2 rsv = __fadd2_rn(rs, nlo);
+          q2p = __ffma2_rn(rsv, rsv, q2p);
+          const float2 nwf = __fadd2_rn(nhi, nlo);  // -w rounded to FP32
+          // gm1 is zero unless the class keeps near-null directions: the
+          // forward pass skips it then (the adjoint keeps the load, faster there)
+          float2 gm = zero2;
+          if (GRAD || hn) {
+            gm = make_float2(gc[r], gc[r + 1]);
+            nulp = __ffma2_rn(__fmul2_rn(gm, nwf), nwf, nulp);
+          }
+          if (DIST) {  // |w|^2 with the head square exact
+            const float hi2[2] = {nhi.x, nhi.y}, lo2[2] = {nlo.x, nlo.y};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              dacc_fma_ff(w2, hi2[h], hi2[h]);
+              w2.c = fmaf(2.f * hi2[h], lo2[h], w2.c);
+              w2.c = fmaf(lo2[h], lo2[h], w2.c);
             }
           }
-          const float rsv[2] = {__fsub_rn(rs0, wv[0].lo), __fsub_rn(rs1, wv[1].lo)};
-          const float edv[2] = {ed0, ed1};
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            q2 = fmaf(rsv[h], rsv[h], q2);
-            const float wf = __fadd_rn(wv[h].hi, wv[h].lo);
-            // gm1 is zero unless the class keeps near-null directions: the
-            // forward pass skips it then (the adjoint keeps the load, faster there)
-            const float gmr = (GRAD || hn) ? gc[r + h] : 0.f;
-            if (GRAD || hn) nul = fmaf(gmr * wf, wf, nul);
-            if (DIST) {  // |w|^2 with the head square exact
-              dacc_fma_ff(w2, wv[h].hi, wv[h].hi);
-              w2.c = fmaf(2.f * wv[h].hi, wv[h].lo, w2.c);
-              w2.c = fmaf(wv[h].lo, wv[h].lo, w2.c);
-            }
-            if (GRAD) {
-              red = fmaf(rsv[h], edv[h], red);
-              const float rho = fmaf(gmr, wf, rsv[h]);
-              const float4 q = get_a(r + h);
-              g1 = fmaf(rho, __fadd_rn(q.x, q.y), g1);
-              g2 = fmaf(rho, __fadd_rn(q.z, q.w), g2);
-              G1[r + h] = fmaf(xFr.hi, rho, G1[r + h]);
-              G2[r + h] = fmaf(xFi.hi, rho, G2[r + h]);
-              if (TWO) {  // dR/2 = sum (1 - gm1) w . dw
-                const float rhoB = __fsub_rn(1.f, gmr) * wf;
-                g1B = fmaf(rhoB, __fadd_rn(q.x, q.y), g1B);
-                g2B = fmaf(rhoB, __fadd_rn(q.z, q.w), g2B);
-                G1B[r + h] = fmaf(xFr.hi, rhoB, G1B[r + h]);
-                G2B[r + h] = fmaf(xFi.hi, rhoB, G2B[r + h]);
-              }
+          if (GRAD) {
+            redp = __ffma2_rn(rsv, ed, redp);
+            // rho = r + gm1 w = r - gm1 nw
+            const float2 rho = __ffma2_rn(make_float2(-gm.x, -gm.y), nwf, rsv);
+            const float2 a1 = __fadd2_rn(a1h, a1t), a2 = __fadd2_rn(a2h, a2t);
+            g1p = __ffma2_rn(rho, a1, g1p);
+            g2p = __ffma2_rn(rho, a2, g2p);
+            G1[r / 2] = __ffma2_rn(xFr2, rho, G1[r / 2]);
+            G2[r / 2] = __ffma2_rn(xFi2, rho, G2[r / 2]);
+            if (TWO) {  // dR/2 = sum (1 - gm1) w . dw = sum (gm1 - 1) nw . dw
+              const float2 rhoB = __fmul2_rn(make_float2(__fsub_rn(gm.x, 1.f), __fsub_rn(gm.y, 1.f)),
+                                             nwf);
+              g1Bp = __ffma2_rn(rhoB, a1, g1Bp);
+              g2Bp = __ffma2_rn(rhoB, a2, g2Bp);
+              G1B[r / 2] = __ffma2_rn(xFr2, rhoB, G1B[r / 2]);
+              G2B[r / 2] = __ffma2_rn(xFi2, rhoB, G2B[r / 2]);
             }
           }
         }
       }
+      const float q2 = __fadd_rn(q2p.x, q2p.y), nul = __fadd_rn(nulp.x, nulp.y);
+      const float red = __fadd_rn(redp.x, redp.y);
+      const float g1 = __fadd_rn(g1p.x, g1p.y), g2 = __fadd_rn(g2p.x, g2p.y);
+      const float g1B = __fadd_rn(g1Bp.x, g1Bp.y), g2B = __fadd_rn(g2Bp.x, g2Bp.y);
       dacc_add(T, half_e2);
       dacc_add(T, df{-0.5f * q2, 0.f});
       if (P.has_null[c] && !DIST) dacc_add(T, df{0.5f * nul, 0.f});
@@ -887,7 +916,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     }
     if (GRAD) {
       // iota and phase through the modes: H = A^T G1 + J^T A^T G2 (FP32)
-      const float4* Ac2 = sA + (size_t)c * R * M;
+      const float4* Ac2 = sA + (size_t)c * R * M * 2;
       const float ci = z.hi, si = sz.hi;
       float cmf = 1.f, smf = 0.f;
       int prev = -1;
@@ -898,17 +927,21 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
           if (EXACT || r < R) {
-            const float4 ah = Ac2[r * M + j];
-            const float ath = ah.x + ah.y, abh = ah.z + ah.w;
-            h1t = fmaf(G1[r], ath, h1t);
-            h1b = fmaf(G1[r], abh, h1b);
-            h2t = fmaf(G2[r], ath, h2t);
-            h2b = fmaf(G2[r], abh, h2b);
+            const float4 ah = Ac2[2 * (r * M + j)];  // (t_h, b_h, t_t, b_t)
+            const float ath = ah.x + ah.z, abh = ah.y + ah.w;
+            const float g1r = (r & 1) ? G1[r / 2].y : G1[r / 2].x;
+            const float g2r = (r & 1) ? G2[r / 2].y : G2[r / 2].x;
+            h1t = fmaf(g1r, ath, h1t);
+            h1b = fmaf(g1r, abh, h1b);
+            h2t = fmaf(g2r, ath, h2t);
+            h2b = fmaf(g2r, abh, h2b);
             if (TWO) {
-              k1t = fmaf(G1B[r], ath, k1t);
-              k1b = fmaf(G1B[r], abh, k1b);
-              k2t = fmaf(G2B[r], ath, k2t);
-              k2b = fmaf(G2B[r], abh, k2b);
+              const float g1Br = (r & 1) ? G1B[r / 2].y : G1B[r / 2].x;
+              const float g2Br = (r & 1) ? G2B[r / 2].y : G2B[r / 2].x;
+              k1t = fmaf(g1Br, ath, k1t);
+              k1b = fmaf(g1Br, abh, k1b);
+              k2t = fmaf(g2Br, ath, k2t);
+              k2b = fmaf(g2Br, abh, k2b);
             }
           }
         }
@@ -962,8 +995,10 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 }
 
 // Stages the whitening matrices of all classes into shared memory in split
-// form: entry (r, j < M) holds (head, tail) of A[r][a] and of A[r][M + a] for
-// mode a = morder[j] (modes in the kernels' order of increasing |m|),
+// form: entry (r, j < M) is two float4, (t_h, b_h, t_t, b_t) and
+// (b_h, -t_h, b_t, -t_t), with (t_h, t_t) the (head, tail) of A[r][a] and
+// (b_h, b_t) of A[r][M + a], for mode a = morder[j] (modes in the kernels'
+// order of increasing |m|; the pairs feed the packed FMAs of the mat-vec),
 // head = A_hi rounded to a multiple of 2^-9 of a power of two >= max_a
 // |A[r][a]| (10 significant bits; the error-free product of lnl_mixed_draw
 // relies on it), tail = (A_hi - head) + A_lo rounded to FP32; then gm1.
@@ -971,7 +1006,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem4) {
   const int R = P.R, D = P.D, M = P.M, ncls = P.ncls;
   float4* sA = smem4;
-  float* sg = reinterpret_cast<float*>(smem4 + (size_t)ncls * R * M);
+  float* sg = reinterpret_cast<float*>(smem4 + (size_t)ncls * R * M * 2);
   for (int t = threadIdx.x; t < ncls * R; t += blockDim.x) {
     const float2* row = P.A + (size_t)t * D;
     float mx = 0.f;
@@ -984,8 +1019,9 @@ __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem
       const float2 v = __ldg(row + a), u = __ldg(row + M + a);
       const float hv = __fsub_rn(__fadd_rn(v.x, C), C);
       const float hu = __fsub_rn(__fadd_rn(u.x, C), C);
-      sA[(size_t)t * M + j] = make_float4(hv, __fadd_rn(__fsub_rn(v.x, hv), v.y), hu,
-                                          __fadd_rn(__fsub_rn(u.x, hu), u.y));
+      const float tv = __fadd_rn(__fsub_rn(v.x, hv), v.y), tu = __fadd_rn(__fsub_rn(u.x, hu), u.y);
+      sA[2 * ((size_t)t * M + j)] = make_float4(hv, hu, tv, tu);
+      sA[2 * ((size_t)t * M + j) + 1] = make_float4(hu, -hv, tu, -tv);
     }
     sg[t] = __ldg(P.gm1 + t);
   }
@@ -1006,7 +1042,7 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   stage_tables(P, T);
   __syncthreads();
   const float4* sA = smem4;
-  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M);
+  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
   float4* a12s = a12_slice<RR>(smem4, P.ncls, P.R, P.M);
   float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
   ThreadLse st = tlse_init();
@@ -1213,7 +1249,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
       cur = it.point;
     }
     const float4* sA = smem4;
-    const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M);
+    const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
     float4* a12s = a12_slice<RR>(smem4, P.ncls, P.R, P.M);
     float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
     ThreadLse st = tlse_init();

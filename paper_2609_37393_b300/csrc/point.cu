@@ -199,7 +199,9 @@ __device__ __forceinline__ float2 split2(double x) {
   return make_float2(hi, __double2float_rn(x - (double)hi));
 }
 
-// ehat[k][kEhatPad + j][r] = proj[k][j][r] * inv_s[k][r] as a (hi, lo) pair.
+// ehat[k][kEhatPad + j] = proj[k][j][r] * inv_s[k][r], r < R, as (hi, lo)
+// pairs laid out by direction pairs: floats (hi_r, hi_r+1, lo_r, lo_r+1) for
+// even r, so that one 16-byte load gives the packed operands of two directions.
 __global__ void whiten_kernel(const double* __restrict__ proj, const double* __restrict__ inv_s,
                               int K, int n, int D, int R, float2* __restrict__ ehat) {
   // rows are stored with kEhatPad zero rows before and after (already zeroed)
@@ -212,7 +214,10 @@ __global__ void whiten_kernel(const double* __restrict__ proj, const double* __r
     int j = (int)(kj % n);
     // directions r >= D exist only as zero padding (inv_s = 0 there)
     const double v = r < D ? proj[kj * D + r] * inv_s[k * R + r] : 0.0;
-    ehat[((long long)k * (n + 2 * kEhatPad) + kEhatPad + j) * R + r] = split2(v);
+    const float2 hl = split2(v);
+    float* row = reinterpret_cast<float*>(ehat + ((long long)k * (n + 2 * kEhatPad) + kEhatPad + j) * R);
+    row[4 * (r / 2) + (r & 1)] = hl.x;
+    row[4 * (r / 2) + 2 + (r & 1)] = hl.y;
   }
 }
 
