@@ -513,40 +513,72 @@ def run_diff(args):
 
 
 def run_sampler(args):
-    """The sampler regime (a NEXT row): one forward+backward call on a small
-    batch of draws, as a gradient-based extrinsic sampler issues them; per-call
-    latency eager and replayed from a captured CUDA graph."""
+    """The sampler regime (NEXT-4): one forward+backward call on a small batch
+    of draws, as a gradient-based extrinsic sampler issues them; per-call
+    latency through the Python API (eager), replayed from a captured CUDA graph
+    (one call per replay), and as 32 calls chained in one graph (the device
+    time per call of a sampler loop captured whole), for the warp-per-draw
+    kernel (the default up to 4096 draws) and the one-thread-per-draw kernel."""
     import torch
     import paper_2609_37393_b300 as R
     import workload as W
+    import oracle as O
     torch.cuda.set_device(0)
     point, exact, info, draws, logw = W.config2(n_draws=1 << 16)
     pt = R.Point(point)
     stream = torch.cuda.current_stream()
+    opt = O.OraclePoint(point)
+
+    def graph_of(fn, calls):
+        s2 = torch.cuda.Stream()
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            fn()
+        stream.wait_stream(s2)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(calls):
+                fn()
+        return graph
+
     rows = []
-    for n in (128, 1024, 8192, 65536):
-        d = R.Draws({p: draws[p][:n] for p in W.PARAMS})
-        lnl = torch.empty(n, dtype=torch.float64, device="cuda")
-        g = torch.empty((7, n), dtype=torch.float64, device="cuda")
-        call = lambda: R.rift_ile_lnL_grad(pt, d, R.FP32_MIXED, lnl, g)
-        eager_us = timed_events(torch, call, 200, stream) * 1e3
-        row = {"draws": n, "eager_us_per_call": eager_us}
-        try:
-            s2 = torch.cuda.Stream()
-            s2.wait_stream(stream)
-            with torch.cuda.stream(s2):
-                call()
-            stream.wait_stream(s2)
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph):
-                call()
-            row["graph_us_per_call"] = timed_events(torch, graph.replay, 200, stream) * 1e3
-        except Exception as e:  # capture refused: report it
-            row["graph"] = f"unavailable: {e}"
-        row["draws_per_s"] = n / (min(row.get("graph_us_per_call", eager_us), eager_us) * 1e-6)
-        rows.append(row)
+    default = R.rift_ile_set_small_batch(4096)
+    with ClockSampler(0) as clocks:
+        for n in (1, 32, 128, 1024, 4096, 8192, 65536):
+            d = R.Draws({p: draws[p][:n] for p in W.PARAMS})
+            lnl = torch.empty(n, dtype=torch.float64, device="cuda")
+            g = torch.empty((7, n), dtype=torch.float64, device="cuda")
+            call = lambda: R.rift_ile_lnL_grad(pt, d, R.FP32_MIXED, lnl, g)
+            row = {"draws": n}
+            for name, limit in (("warp", 1 << 20), ("thread", 0)):
+                R.rift_ile_set_small_batch(limit)
+                r = {"eager_us_per_call": timed_events(torch, call, 200, stream) * 1e3}
+                try:
+                    g1 = graph_of(call, 1)
+                    r["graph_us_per_call"] = timed_events(torch, g1.replay, 200, stream) * 1e3
+                    g32 = graph_of(call, 32)
+                    r["graph32_us_per_call"] = timed_events(torch, g32.replay, 20, stream) * 1e3 / 32
+                except Exception as e:  # capture refused: report it
+                    r["graph"] = f"unavailable: {e}"
+                row[name] = r
+            R.rift_ile_set_small_batch(default)
+            call()
+            if n <= 8192:  # the default dispatch against the oracle
+                rl, rg = O.lnL_grad(opt, {p: draws[p][:n] for p in W.PARAMS})
+                near = rl >= rl.max() - 50
+                sc = np.abs(rg) + np.sqrt(np.mean(rg ** 2, axis=0))[None, :]
+                row["max_abs_dlnL_within_50nat_vs_oracle"] = float(
+                    np.max(np.abs(lnl.cpu().numpy() - rl)[near]))
+                row["max_rel_grad_err_within_50nat_vs_oracle"] = float(
+                    np.max((np.abs(g.cpu().numpy().T - rg) / sc)[near]))
+            best = min(v for k in ("warp", "thread") for v in row[k].values()
+                       if isinstance(v, float))
+            row["draws_per_s_best"] = n / (best * 1e-6)
+            rows.append(row)
+    R.rift_ile_set_small_batch(default)
     print(json.dumps({"workload": "sampler", "metric": "fwd+bwd latency per small batch (SNR 1000)",
-                      "rows": rows}), flush=True)
+                      "unit": "us per call", "default_small_batch": default, "rows": rows,
+                      "clocks": clocks.summary()}), flush=True)
 
 
 def comp_fp64_fmas(point: dict, na: int) -> int:

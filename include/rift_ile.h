@@ -292,6 +292,17 @@ int rift_ile_batch_tune(rift_ile_batch* batch, int32_t reps, void* stream, int32
 int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* draws, int32_t P,
                        rift_ile_precision prec, double* out, void* stream);
 
+/* Draw count up to which rift_ile_lnL and rift_ile_lnL_grad with
+ * RIFT_ILE_FP32_MIXED run the warp-per-draw kernel: the 32 lanes of a warp
+ * share one draw (its angles, harmonics, mat-vec rows, detectors and
+ * whitened directions), which cuts the latency of a small batch, the regime
+ * of a gradient-based extrinsic sampler (App. H of the paper: tens to
+ * thousands of draws per call).  Larger batches use the one-thread-per-draw
+ * kernels, whose throughput is higher.  The two agree to rounding.  Default
+ * 4096; 0 disables the warp kernel.  Process-wide; returns the previous
+ * value.  Host only, no GPU call. */
+int64_t rift_ile_set_small_batch(int64_t max_draws);
+
 /* Number of Q taps that fell outside their tables in the last completed
  * lnZ call of this thread (host read; the draws get zero Q there). */
 int64_t rift_ile_last_oob(void);

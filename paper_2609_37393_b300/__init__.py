@@ -85,6 +85,8 @@ _lib.rift_ile_lnL_dist.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P]
 _lib.rift_ile_dist_nodes.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int32, _P, _P, _P]
 _lib.rift_ile_last_oob.restype = ctypes.c_int64
 _lib.rift_ile_probe_alu.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]
+_lib.rift_ile_set_small_batch.argtypes = [ctypes.c_int64]
+_lib.rift_ile_set_small_batch.restype = ctypes.c_int64
 
 
 def _check(rc: int):
@@ -526,6 +528,12 @@ def rift_ile_dist_nodes(d_min, d_max, d_ref, tol, rho_max, max_nodes=1 << 16):
 
 def rift_ile_last_oob() -> int:
     return int(_lib.rift_ile_last_oob())
+
+
+def rift_ile_set_small_batch(max_draws: int) -> int:
+    """Draw count up to which FP32-mixed lnL and lnL + gradient calls use the
+    warp-per-draw kernel (0 disables it); returns the previous value."""
+    return int(_lib.rift_ile_set_small_batch(int(max_draws)))
 
 
 PROBE_FP32_FMA, PROBE_FP64_FMA, PROBE_MUFU_EX2, PROBE_MUFU_SIN, PROBE_FP32X2_FMA = range(5)

@@ -59,6 +59,9 @@ cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_to
 
 // SM count of the current device (cached).
 int device_sms();
+// Draw count up to which FP32-mixed lnL and lnL + gradient calls (no
+// distance table) run the warp-per-draw kernel (rift_ile_set_small_batch).
+long long small_batch_max();
 
 // The library's per-device scratch (LSE partials, combined state, tap
 // counter), allocated on first use; draw validation and marshalling; the

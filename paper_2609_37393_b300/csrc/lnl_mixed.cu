@@ -4,6 +4,7 @@
 // lnl_mixed_m*.cu, so that the compiler front end runs on them in parallel).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -34,6 +35,12 @@ template <int MM>
 size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp, int Kp);
 template <int MM>
 int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab);
+
+namespace {
+std::atomic<long long> g_small_batch_max{4096};
+}
+
+long long small_batch_max() { return g_small_batch_max.load(std::memory_order_relaxed); }
 
 // Sine/cosine of a_j = j 2^-7 and e^(j/128) as (hi, lo) float pairs, copied
 // into every mode-count unit's tables once per device.
@@ -118,3 +125,8 @@ size_t batch_smem_for(int M, int R, int ncls, int Rp, int Mp, int Kp) {
 }
 
 }  // namespace rift
+
+extern "C" int64_t rift_ile_set_small_batch(int64_t max_draws) {
+  if (max_draws < 0) max_draws = 0;
+  return (int64_t)rift::g_small_batch_max.exchange((long long)max_draws);
+}

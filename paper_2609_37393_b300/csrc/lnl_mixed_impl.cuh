@@ -1096,15 +1096,72 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   }
 }
 
+// Resident blocks per SM of `kern` at `smem` bytes of dynamic shared memory on
+// the current device, with the shared-memory attribute set once per device:
+// both are cached per kernel instantiation, so a launch costs no attribute or
+// occupancy call once a point's shape has been seen.
+template <typename KernelT>
+int cached_blocks_per_sm(KernelT kern, int threads, size_t smem) {
+  static std::mutex mu;
+  static bool attr_set[64] = {false};
+  static size_t last_smem[64] = {0};
+  static int last_nb[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!attr_set[dev]) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[dev] = true;
+  }
+  if (last_nb[dev] == 0 || last_smem[dev] != smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess || nb < 1)
+      nb = 1;
+    last_nb[dev] = nb < kMaxPartialsPerSM ? nb : kMaxPartialsPerSM;
+    last_smem[dev] = smem;
+  }
+  return last_nb[dev];
+}
+
+#include "lnl_warp.cuh"
+
+template <int MM, int RR, bool GRAD>
+cudaError_t launch_warp_k(const PointParams& hp, const DrawsParams& dp, double* lnl_out,
+                          double* grad_out, cudaStream_t st) {
+  if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
+  const size_t smem = warp_smem_bytes<MM, RR>(hp.ncls, hp.R, hp.M);
+  auto kern = lnl_warp_kernel<MM, RR, GRAD>;
+  const long long need = (dp.n + kWarpDrawWarps - 1) / kWarpDrawWarps;
+  const long long cap = (long long)device_sms() * cached_blocks_per_sm(kern, 32 * kWarpDrawWarps, smem);
+  const int blocks = (int)(need < cap ? need : cap);
+  kern<<<blocks, 32 * kWarpDrawWarps, smem, st>>>(hp, dp, lnl_out, grad_out);
+  return cudaGetLastError();
+}
+
+// Serves lnL (GRAD false) or lnL and its gradient with one warp per draw when
+// the batch is small (at most small_batch_max() draws) and the point's
+// scratch fits; returns false to leave the call to the per-thread kernels.
+template <int MM, bool GRAD>
+bool try_warp(const PointParams& hp, const DrawsParams& dp, double* lnl_out, double* grad_out,
+              cudaStream_t st, cudaError_t* e) {
+  if (dp.n > small_batch_max() || hp.K > kMaxDet || (hp.R != MM && hp.R != 2 * MM)) return false;
+  const bool wide = hp.R > MM;
+  const size_t smem = wide ? warp_smem_bytes<MM, 2 * MM>(hp.ncls, hp.R, hp.M)
+                           : warp_smem_bytes<MM, MM>(hp.ncls, hp.R, hp.M);
+  if (smem > 200 * 1024) return false;
+  *e = wide ? launch_warp_k<MM, 2 * MM, GRAD>(hp, dp, lnl_out, grad_out, st)
+            : launch_warp_k<MM, MM, GRAD>(hp, dp, lnl_out, grad_out, st);
+  return true;
+}
+
 template <int MM, int RR, bool LSE>
 cudaError_t launch_mixed_k(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                            double* lnl_out, LseState* partials, unsigned long long* oob,
                            int* blocks, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
-  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, LSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  *blocks = grid_cap(grid_for(lnl_mixed_kernel<MM, RR, LSE>, 128, smem), dp.n, 128);
+  *blocks = grid_cap(device_sms() * cached_blocks_per_sm(lnl_mixed_kernel<MM, RR, LSE>, 128, smem),
+                     dp.n, 128);
   lnl_mixed_kernel<MM, RR, LSE><<<*blocks, 128, smem, st>>>(hp, dp, lnl_out, partials, oob);
   return cudaGetLastError();
 }
@@ -1146,6 +1203,11 @@ template <int MM>
 cudaError_t launch_mixed_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                             double* lnl_out, LseState* partials, unsigned long long* oob,
                             int* blocks, cudaStream_t st) {
+  cudaError_t e;
+  if (!partials && !oob && try_warp<MM, false>(hp, dp, lnl_out, nullptr, st, &e)) {
+    *blocks = 0;
+    return e;
+  }
   if (hp.R <= MM) return launch_mixed_mr<MM, MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
   return launch_mixed_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, partials, oob, blocks, st);
 }
@@ -1155,9 +1217,8 @@ cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, c
                                  double* lnl_out, double* grad_out, cudaStream_t st) {
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
   const size_t smem = mixed_smem_bytes<RR>(hp.ncls, hp.R, hp.M, hp.K);
-  cudaFuncSetAttribute(lnl_mixed_kernel<MM, RR, false, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  const int blocks = grid_cap(grid_for(lnl_mixed_kernel<MM, RR, false, true>, 128, smem), dp.n, 128);
+  const int blocks = grid_cap(
+      device_sms() * cached_blocks_per_sm(lnl_mixed_kernel<MM, RR, false, true>, 128, smem), dp.n, 128);
   lnl_mixed_kernel<MM, RR, false, true><<<blocks, 128, smem, st>>>(hp, dp, lnl_out, nullptr, nullptr,
                                                                    grad_out);
   return cudaGetLastError();
@@ -1166,6 +1227,8 @@ cudaError_t launch_mixed_grad_mr(const PointParams& hp, const PointParams* dP, c
 template <int MM>
 cudaError_t launch_mixed_grad_mm(const PointParams& hp, const PointParams* dP, const DrawsParams& dp,
                                  double* lnl_out, double* grad_out, cudaStream_t st) {
+  cudaError_t e;
+  if (try_warp<MM, true>(hp, dp, lnl_out, grad_out, st, &e)) return e;
   if (hp.R <= MM) return launch_mixed_grad_mr<MM, MM>(hp, dP, dp, lnl_out, grad_out, st);
   return launch_mixed_grad_mr<MM, 2 * MM>(hp, dP, dp, lnl_out, grad_out, st);
 }

@@ -1,0 +1,453 @@
+// FP32-mixed lnL and gradient with one warp per draw, for the small batches a
+// gradient-based extrinsic sampler issues (the paper's warm-likelihood regime,
+// App. H): included by lnl_mixed_impl.cuh inside its anonymous namespace, so
+// it shares that file's double-float helpers and anchor tables.
+//
+// The arithmetic is the one of lnl_mixed_draw (whitened residual, double-float
+// template, packed pairs), rearranged so that the 32 lanes of a warp share one
+// draw.  Every phase runs the same code on all its active lanes (lanes of a
+// warp that take different branches run one after the other), and hands its
+// results to the next phase through the warp's slice of shared memory:
+//   1  lanes 0..3: anchored sine/cosine of ra - gmst, dec, 2 psi, iota;
+//      lanes 4..: of |m| phi for |m| = 1 .. max |m|; one lane the distance factor
+//   2  every lane: the sky direction, the antenna basis and its split, x e^{2 i psi}
+//   3  lane j < M: the harmonic of mode j, split for the exact products;
+//      lane (c, r): row r of the class-c mat-vec a1 = A y, a2 = A J y
+//   4  lane k < K: x F_k, the arrival time and table position, 1/2 |e|^2 and
+//      its slope, the cubic's weights, the detector's antenna derivatives
+//   5  lane (k, direction pair): the template, the residual over the four
+//      taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
+//   6  lane k: the detector's terms; lane (c, r): G1_r, G2_r of the class
+//   7  lane (c, j): the iota and phi_ref derivatives through mode j
+//   8  lane 0: the sums in a fixed order, the outputs
+// Reductions run in fixed orders, so results are reproducible; they differ
+// from the one-thread-per-draw kernel's by rounding only (e^{i |m| phi} is
+// taken by the anchored sine/cosine for every |m| rather than by recurrence,
+// and the direction sums are grouped differently).
+#pragma once
+
+constexpr int kWarpDrawWarps = 4;  // warps (draws in flight) per block
+
+template <int MM, int RR>
+struct WarpScratch {
+  float4 ang[16];                  // (sin hi, sin lo, cos hi, cos lo): lam, dec, 2 psi, iota, |m| phi
+  float2 x;                        // distance factor (hi, lo)
+  float4 ys[MM];                   // (yr1, yr2, yi1, yi2) of visited mode j
+  float2 yh[MM];                   // (yr.hi, yi.hi)
+  float4 a12[kMaxDet][RR];         // class c, direction r: (a1 head, a1 tail, a2 head, a2 tail)
+  float4 xf[kMaxDet];              // x F_k: (re head, re tail, im head, im tail)
+  float4 wt[kMaxDet], wtd[kMaxDet];
+  float sigma[kMaxDet];
+  int jc[kMaxDet];
+  int bad[kMaxDet];
+  float2 he2[kMaxDet], dhe2[kMaxDet];  // 1/2 |e|^2 and its slope in f (hi, lo)
+  float4 dx[kMaxDet];              // d(x F_k)/d ra (re, im), d(x F_k)/d dec (re, im)
+  float2 dk[kMaxDet];              // d t_k / d ra, d t_k / d dec
+  float part[kMaxDet][RR / 2][5];  // per (k, pair): |r|^2, null term, r.edot, rho.a1, rho.a2
+  float2 gp[kMaxDet][RR];          // per (k, r): (Re xF_k rho_r, Im xF_k rho_r)
+  float2 G[kMaxDet][RR];           // per class c, direction r: (G1, G2)
+  float2 gm[kMaxDet][MM];          // per (c, j): (d/d phi, d/d iota) shares
+};
+
+template <int MM, int RR>
+__host__ __device__ inline size_t warp_smem_bytes(int ncls, int R, int M) {
+  // the split whitening and gm1 of every class (as the per-thread kernel),
+  // then one scratch slice per warp
+  const size_t a = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  return a + (size_t)kWarpDrawWarps * sizeof(WarpScratch<MM, RR>);
+}
+
+template <int MM, int RR, bool GRAD>
+__global__ void __launch_bounds__(32 * kWarpDrawWarps)
+    lnl_warp_kernel(const __grid_constant__ PointParams P, DrawsParams dp,
+                    double* __restrict__ lnl_out, double* __restrict__ grad_out) {
+  extern __shared__ float4 smem4[];
+  __shared__ MixedTables T;
+  stage_split_A(P, smem4);
+  stage_tables(P, T);
+  __syncthreads();
+  const float4* sA = smem4;
+  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
+  const size_t aoff = (size_t)P.ncls * P.R * P.M * 32 + (((size_t)P.ncls * P.R * 4 + 15) & ~(size_t)15);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpScratch<MM, RR>& W =
+      reinterpret_cast<WarpScratch<MM, RR>*>(reinterpret_cast<char*>(smem4) + aoff)[warp];
+  const int K = P.K, M = P.M, n = P.n, ncls = P.ncls;
+  constexpr int NP = RR / 2;  // direction pairs
+  int mmax = 0;
+  for (int j = 0; j < M; ++j) mmax = max(mmax, abs(T.mode[j].y));
+
+  for (long long i = blockIdx.x * (long long)kWarpDrawWarps + warp; i < dp.n;
+       i += (long long)gridDim.x * kWarpDrawWarps) {
+    const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
+    const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
+    const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
+    const df tc = load_param_df(dp, 6, i);
+
+    // ---- 1: the anchored sines and cosines, and the distance factor
+    if (lane < 4 + mmax) {
+      df a;
+      if (lane == 0) {
+        a = two_sum(ra, -P.gmst_hi);
+        a.lo = __fsub_rn(a.lo, P.gmst_lo);
+        a = fast_two_sum(a.hi, a.lo);
+      } else if (lane == 1) {
+        a = df{dec, 0.f};
+      } else if (lane == 2) {
+        a = df{2.f * psi, 0.f};
+      } else if (lane == 3) {
+        a = df{incl, 0.f};
+      } else {
+        a = two_prod((float)(lane - 3), phi);
+      }
+      df s, c;
+      sincos_df(a, s, c);
+      W.ang[lane] = make_float4(s.hi, s.lo, c.hi, c.lo);
+    } else if (lane == 31) {
+      df lx = two_sum(P.ln_dref_hi, -lnD);
+      lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
+      const df x = exp_df(fast_two_sum(lx.hi, lx.lo));
+      W.x = make_float2(x.hi, x.lo);
+    }
+    __syncwarp();
+
+    // ---- 2: sky direction, antenna basis (every lane), x e^{2 i psi}
+    const float4 a0 = W.ang[0], a1v = W.ang[1], a2v = W.ang[2], a3v = W.ang[3];
+    const df sl{a0.x, a0.y}, cl{a0.z, a0.w}, sd{a1v.x, a1v.y}, cd{a1v.z, a1v.w};
+    const df s2p{a2v.x, a2v.y}, c2p{a2v.z, a2v.w}, sz{a3v.x, a3v.y}, z{a3v.z, a3v.w};
+    const df x{W.x.x, W.x.y};
+    const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
+    const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
+
+    // ---- 3a: lane j < M: the harmonic of mode j (visiting order), split
+    if (lane < M) {
+      const int4 md = T.mode[lane];  // (mode index, m, l, ypar)
+      const int m = md.y, am = m < 0 ? -m : m;
+      df cm{1.f, 0.f}, sm{0.f, 0.f};
+      if (am > 0) {
+        const float4 e = W.ang[3 + am];
+        sm = df{e.x, e.y};
+        cm = df{e.z, e.w};
+      }
+      const df amp = sylm_amp_df(T, lane, md.z, md.w, z, sz);
+      const df yr = df_mul(amp, cm);
+      const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
+      float yr1, yr2, yi1, yi2;
+      split_y(yr.hi, yr1, yr2);
+      split_y(yi.hi, yi1, yi2);
+      W.ys[lane] = make_float4(yr1, __fadd_rn(yr2, yr.lo), yi1, __fadd_rn(yi2, yi.lo));
+      W.yh[lane] = make_float2(yr.hi, yi.hi);
+    }
+    __syncwarp();
+    // ---- 3b: lane (c, r): row r of class c's mat-vec, packed as in the per-thread kernel
+    for (int it = lane; it < ncls * RR; it += 32) {
+      const int c = it / RR, r = it - c * RR;
+      const float4* Ac = sA + (size_t)c * RR * M * 2;
+      float2 ex = make_float2(0.f, 0.f), co = make_float2(0.f, 0.f);
+      for (int j = 0; j < M; ++j) {
+        const float4 y = W.ys[j];
+        const float2 yh = W.yh[j];
+        const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
+        ex = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.x, y.x), ex);
+        ex = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.z, y.z), ex);
+        co = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.y, y.y), co);
+        co = __ffma2_rn(make_float2(ap.z, ap.w), make_float2(yh.x, yh.x), co);
+        co = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.w, y.w), co);
+        co = __ffma2_rn(make_float2(an.z, an.w), make_float2(yh.y, yh.y), co);
+      }
+      const df u = two_sum(ex.x, co.x), v = two_sum(ex.y, co.y);
+      const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
+      const float uh = head_of(u.hi, C), vh = head_of(v.hi, C);
+      W.a12[c][r] = make_float4(uh, __fadd_rn(__fsub_rn(u.hi, uh), u.lo), vh,
+                                __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
+    }
+
+    // ---- 4: lane k < K: antenna factor, arrival time, table position, 1/2|e|^2
+    if (lane < K) {
+      const int k = lane;
+      AntennaSplit AS;
+      {
+        AntennaBasis AB;
+        antenna_basis(sl, cl, sd, cd, AB);
+        split_antenna_basis(AB, AS);
+      }
+      df xFr, xFi;
+      antenna_df(T, k, AS, xer, xei, xFr, xFi);
+      const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
+      const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
+      W.xf[k] = make_float4(xrh, __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo), xih,
+                            __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo));
+      const float4 ph = T.pos_hi[k], pl = T.pos_lo[k];
+      df delay = df_mul(df{ph.x, pl.x}, s0);
+      delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
+      delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
+      const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
+      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
+      int bad = 0;
+      float f = 0.f, jf = 0.f;
+      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
+      if (!isfinite(u.hi)) {
+        bad = 1;
+      } else {
+        jf = floorf(u.hi);
+        if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
+        f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
+        if (jf >= -2.f && jf <= (float)n) {
+          const float2* pc =
+              P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
+          float2 cf = __ldg(pc + kPolyDeg);
+          df acc = df{cf.x, cf.y};
+          df dacc_p = df{0.f, 0.f};
+#pragma unroll
+          for (int p = kPolyDeg - 1; p >= 0; --p) {
+            if (GRAD) {
+              df pr = two_prod(dacc_p.hi, f);
+              pr.lo = fmaf(dacc_p.lo, f, pr.lo);
+              const df sm3 = two_sum(pr.hi, acc.hi);
+              dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
+            }
+            cf = __ldg(pc + p);
+            df pr = two_prod(acc.hi, f);
+            pr.lo = fmaf(acc.lo, f, pr.lo);
+            const df sm2 = two_sum(pr.hi, cf.x);
+            acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf.y));
+          }
+          half_e2 = acc;
+          dhalf = dacc_p;
+        }
+      }
+      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
+      const float w0 = -(f * fc * fd) * (1.f / 6.f), w1 = (fa * fc * fd) * 0.5f;
+      const float w2 = -(fa * f * fd) * 0.5f, w3 = (fa * f * fc) * (1.f / 6.f);
+      const df ws = df_add(two_sum(w0, w1), two_sum(w2, w3));
+      W.sigma[k] = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
+      W.wt[k] = make_float4(w0, w1, w2, w3);
+      if (GRAD) {
+        W.wtd[k] = make_float4(-(fc * fd + f * fd + f * fc) * (1.f / 6.f),
+                               (fc * fd + fa * fd + fa * fc) * 0.5f,
+                               -(f * fd + fa * fd + fa * f) * 0.5f,
+                               (f * fc + fa * fc + fa * f) * (1.f / 6.f));
+      }
+      W.jc[k] = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
+      W.bad[k] = bad;
+      W.he2[k] = make_float2(half_e2.hi, half_e2.lo);
+      W.dhe2[k] = make_float2(dhalf.hi, dhalf.lo);
+      if (GRAD) {
+        AntennaBasisGrad ABG;
+        antenna_basis_grad(sl.hi, cl.hi, sd.hi, cd.hi, ABG);
+        float dfpa = 0.f, dfpd = 0.f, dfxa = 0.f, dfxd = 0.f;
+        float ac[12];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const float4 a4 = T.ah[k][v], b4 = T.at[k][v];
+          ac[4 * v] = a4.x + b4.x;
+          ac[4 * v + 1] = a4.y + b4.y;
+          ac[4 * v + 2] = a4.z + b4.z;
+          ac[4 * v + 3] = a4.w + b4.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          dfpa = fmaf(ac[q], ABG.ba[q], dfpa);
+          dfpd = fmaf(ac[q], ABG.bd[q], dfpd);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          dfxa = fmaf(ac[6 + q], ABG.ga[q], dfxa);
+          dfxd = fmaf(ac[6 + q], ABG.gd[q], dfxd);
+        }
+        W.dx[k] = make_float4(dfpa * xer.hi + dfxa * xei.hi, dfpa * xei.hi - dfxa * xer.hi,
+                              dfpd * xer.hi + dfxd * xei.hi, dfpd * xei.hi - dfxd * xer.hi);
+        // ds/d ra = (-cd sl, cd cl, 0), ds/d dec = (-sd cl, -sd sl, cd)
+        W.dk[k] = make_float2(-(ph.x * (-cd.hi * sl.hi) + ph.y * (cd.hi * cl.hi)),
+                              -(ph.x * (-sd.hi * cl.hi) + ph.y * (-sd.hi * sl.hi) + ph.z * cd.hi));
+      }
+    }
+    __syncwarp();
+
+    // ---- 5: lane (k, pair): the residual of two directions (packed, as in
+    // the per-thread kernel's loop body)
+    for (int it = lane; it < K * NP; it += 32) {
+      const int k = it / NP, pr = it - k * NP, r = 2 * pr;
+      if (W.bad[k]) continue;
+      const int c = P.cls_of[k];
+      const float4 xfq = W.xf[k];
+      const float2 nxrh = make_float2(-xfq.x, -xfq.x), nxrt = make_float2(-xfq.y, -xfq.y);
+      const float2 nxih = make_float2(-xfq.z, -xfq.z), nxit = make_float2(-xfq.w, -xfq.w);
+      const float4 qa0 = W.a12[c][r], qa1 = W.a12[c][r + 1];
+      const float2 a1h = make_float2(qa0.x, qa1.x), a1t = make_float2(qa0.y, qa1.y);
+      const float2 a2h = make_float2(qa0.z, qa1.z), a2t = make_float2(qa0.w, qa1.w);
+      float2 nlo = __fmul2_rn(nxrh, a1t);
+      nlo = __ffma2_rn(nxrt, a1h, nlo);
+      nlo = __ffma2_rn(nxrt, a1t, nlo);
+      nlo = __ffma2_rn(nxih, a2t, nlo);
+      nlo = __ffma2_rn(nxit, a2h, nlo);
+      nlo = __ffma2_rn(nxit, a2t, nlo);
+      const float2 nhi = __ffma2_rn(nxrh, a1h, __fmul2_rn(nxih, a2h));
+      const float4 w4 = W.wt[k];
+      const float wtv[4] = {w4.x, w4.y, w4.z, w4.w};
+      float wdv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (GRAD) {
+        const float4 d4 = W.wtd[k];
+        wdv[0] = d4.x;
+        wdv[1] = d4.y;
+        wdv[2] = d4.z;
+        wdv[3] = d4.w;
+      }
+      const float nsg = -W.sigma[k];
+      const float2* Ej = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * RR +
+                         (ptrdiff_t)(W.jc[k] - 1) * RR;
+      float2 rs = make_float2(0.f, 0.f), ed = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int tap = 0; tap < 4; ++tap) {
+        const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + tap * RR + r));
+        const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
+                                    make_float2(e4.z, e4.w));
+        rs = __ffma2_rn(make_float2(wtv[tap], wtv[tap]), d, rs);
+        if (tap == 1) rs = __ffma2_rn(make_float2(nsg, nsg), d, rs);
+        if (GRAD) ed = __ffma2_rn(make_float2(wdv[tap], wdv[tap]), d, ed);
+      }
+      const float2 rsv = __fadd2_rn(rs, nlo);
+      const float2 q2 = __fmul2_rn(rsv, rsv);
+      const float2 nwf = __fadd2_rn(nhi, nlo);
+      float2 gm = make_float2(0.f, 0.f), nul = make_float2(0.f, 0.f);
+      const float* gc = sg + c * RR;
+      if (GRAD || P.has_null[c]) {
+        gm = make_float2(gc[r], gc[r + 1]);
+        nul = __fmul2_rn(__fmul2_rn(gm, nwf), nwf);
+      }
+      float* pt = W.part[k][pr];
+      pt[0] = __fadd_rn(q2.x, q2.y);
+      pt[1] = __fadd_rn(nul.x, nul.y);
+      if (GRAD) {
+        const float2 red = __fmul2_rn(rsv, ed);
+        const float2 rho = __ffma2_rn(make_float2(-gm.x, -gm.y), nwf, rsv);
+        const float2 g1 = __fmul2_rn(rho, __fadd2_rn(a1h, a1t));
+        const float2 g2 = __fmul2_rn(rho, __fadd2_rn(a2h, a2t));
+        pt[2] = __fadd_rn(red.x, red.y);
+        pt[3] = __fadd_rn(g1.x, g1.y);
+        pt[4] = __fadd_rn(g2.x, g2.y);
+        const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
+        W.gp[k][r] = make_float2(xFr * rho.x, xFi * rho.x);
+        W.gp[k][r + 1] = make_float2(xFr * rho.y, xFi * rho.y);
+      }
+    }
+    __syncwarp();
+
+    // ---- 6a: lane (c, r): G1_r, G2_r of class c over its detectors in order
+    if (GRAD) {
+      for (int it = lane; it < ncls * RR; it += 32) {
+        const int c = it / RR, r = it - c * RR;
+        float g1 = 0.f, g2 = 0.f;
+        for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
+          const int k = P.det_order[q];
+          if (W.bad[k]) continue;
+          const float2 v = W.gp[k][r];
+          g1 += v.x;
+          g2 += v.y;
+        }
+        W.G[c][r] = make_float2(g1, g2);
+      }
+      __syncwarp();
+      // ---- 7: lane (c, j): iota and phi_ref through mode j of class c
+      for (int it = lane; it < ncls * M; it += 32) {
+        const int c = it / M, j = it - c * M;
+        const float4* Ac2 = sA + (size_t)c * RR * M * 2;
+        float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
+        for (int r = 0; r < RR; ++r) {
+          const float4 ah = Ac2[2 * (r * M + j)];  // (t_h, b_h, t_t, b_t)
+          const float ath = ah.x + ah.z, abh = ah.y + ah.w;
+          const float2 g = W.G[c][r];
+          h1t = fmaf(g.x, ath, h1t);
+          h1b = fmaf(g.x, abh, h1b);
+          h2t = fmaf(g.y, ath, h2t);
+          h2b = fmaf(g.y, abh, h2b);
+        }
+        const float Hre = h1t + h2b, Him = h1b - h2t;
+        const int4 md = T.mode[j];
+        const int m = md.y, am = m < 0 ? -m : m;
+        float cmf = 1.f, smf = 0.f;
+        if (am > 0) {
+          const float4 e = W.ang[3 + am];
+          smf = e.x;
+          cmf = e.z;
+        }
+        const float sgn = m < 0 ? -1.f : 1.f;
+        float amp, damp;
+        sylm_amp_grad_f(T, j, md.z, md.w, z.hi, sz.hi, amp, damp);
+        const float yre = amp * cmf, yim = sgn * amp * smf;
+        W.gm[c][j] = make_float2((float)m * fmaf(-yim, Hre, yre * Him),
+                                 fmaf(damp * cmf, Hre, sgn * damp * smf * Him));
+      }
+      __syncwarp();
+    }
+
+    // ---- 8: lane 0: the sums over detectors (classes, then the class's
+    // detectors in order, as the per-thread kernel), the outputs
+    if (lane == 0) {
+      dacc Tl = dacc_zero();
+      dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
+      float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_incl = 0.f, g_phase = 0.f, g_lnd = 0.f;
+      bool bad = false;
+      for (int c = 0; c < ncls; ++c) {
+        for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
+          const int k = P.det_order[q];
+          if (W.bad[k]) {
+            bad = true;
+            continue;
+          }
+          float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
+          for (int pr = 0; pr < NP; ++pr) {
+            q2 += W.part[k][pr][0];
+            nul += W.part[k][pr][1];
+            if (GRAD) {
+              red += W.part[k][pr][2];
+              g1 += W.part[k][pr][3];
+              g2 += W.part[k][pr][4];
+            }
+          }
+          const float2 he = W.he2[k];
+          dacc_add(Tl, df{he.x, he.y});
+          dacc_add(Tl, df{-0.5f * q2, 0.f});
+          if (P.has_null[c]) dacc_add(Tl, df{0.5f * nul, 0.f});
+          if (GRAD) {
+            const float2 dh = W.dhe2[k];
+            const df dtk = df_mul(df_add_f(df{dh.x, dh.y}, -red), df{P.inv_dt_hi, P.inv_dt_lo});
+            const float2 dkk = W.dk[k];
+            dacc_add(gt_t, dtk);
+            dacc_add(gt_ra, df_mul_f(dtk, dkk.x));
+            dacc_add(gt_dec, df_mul_f(dtk, dkk.y));
+            const float4 d = W.dx[k];
+            const float4 xfq = W.xf[k];
+            const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
+            g_ra = fmaf(d.x, g1, fmaf(d.y, g2, g_ra));
+            g_dec = fmaf(d.z, g1, fmaf(d.w, g2, g_dec));
+            g_psi = fmaf(-2.f * xFi, g1, fmaf(2.f * xFr, g2, g_psi));
+            g_lnd = fmaf(-xFr, g1, fmaf(-xFi, g2, g_lnd));
+          }
+        }
+        if (GRAD)
+          for (int j = 0; j < M; ++j) {
+            g_phase += W.gm[c][j].x;
+            g_incl += W.gm[c][j].y;
+          }
+      }
+      const df lnl = dacc_result(Tl);
+      const double lv = bad ? CUDART_NAN : (double)lnl.hi + (double)lnl.lo;
+      if (lnl_out) lnl_out[i] = lv;
+      if (GRAD) {
+        const df a = dacc_result(gt_ra), b = dacc_result(gt_dec), t = dacc_result(gt_t);
+        double g[kNpar];
+        g[0] = (double)a.hi + (double)a.lo + (double)g_ra;
+        g[1] = (double)b.hi + (double)b.lo + (double)g_dec;
+        g[2] = g_psi;
+        g[3] = g_incl;
+        g[4] = g_phase;
+        g[5] = g_lnd;
+        g[6] = (double)t.hi + (double)t.lo;
+#pragma unroll
+        for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = bad ? CUDART_NAN : g[p];
+      }
+    }
+    __syncwarp();  // the scratch is reused by this warp's next draw
+  }
+}
