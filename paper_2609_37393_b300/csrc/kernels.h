@@ -57,6 +57,9 @@ cudaError_t launch_grad_mixed_dist(const PointParams& hp, const PointParams* dP,
 cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_total,
                                LseState* state_out, cudaStream_t st);
 
+// Builds the shared-memory image of the FP32-mixed tables of a point (hp
+// complete apart from img); *img is a new device buffer of *nf4 float4.
+int build_mixed_image(const PointParams& hp, float4** img, int* nf4, cudaStream_t st);
 // SM count of the current device (cached).
 int device_sms();
 // Draw count up to which FP32-mixed lnL and lnL + gradient calls (no

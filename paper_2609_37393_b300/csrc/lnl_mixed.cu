@@ -35,6 +35,8 @@ template <int MM>
 size_t mixed_batch_smem(int R, int ncls, int Rp, int Mp, int Kp);
 template <int MM>
 int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab);
+template <int MM>
+int mixed_image(const PointParams& hp, float4** img, int* nf4, cudaStream_t st);
 
 namespace {
 std::atomic<long long> g_small_batch_max{4096};
@@ -116,6 +118,10 @@ cudaError_t launch_grad_mixed_dist(const PointParams& hp, const PointParams* dP,
                                    const DrawsParams& dp, const DistParams& dist, double* lnl_out,
                                    double* grad_out, cudaStream_t st) {
   return RIFT_DISPATCH_M(hp.M, mixed_grad_dist, hp, dP, dp, dist, lnl_out, grad_out, st);
+}
+
+int build_mixed_image(const PointParams& hp, float4** img, int* nf4, cudaStream_t st) {
+  return RIFT_DISPATCH_M(hp.M, mixed_image, hp, img, nf4, st);
 }
 
 BatchKernelFn batch_kernel_for(int M, int R) { return RIFT_DISPATCH_M(M, mixed_batch_kernel, R); }

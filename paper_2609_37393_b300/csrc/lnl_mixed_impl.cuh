@@ -1096,6 +1096,31 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   }
 }
 
+// Bytes of the split whitening and gm1 at the start of the shared memory of
+// the FP32-mixed kernels, and of the per-point image (those plus the staged
+// tables) that the warp-per-draw kernel copies flat.
+__host__ __device__ inline size_t split_a_bytes(int ncls, int R, int M) {
+  return (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+}
+__host__ __device__ inline size_t image_bytes(int ncls, int R, int M) {
+  return split_a_bytes(ncls, R, M) + ((sizeof(MixedTables) + 15) & ~(size_t)15);
+}
+
+// Builds the image once per point: the block stages the tables into shared
+// memory exactly as the kernels do, then writes that memory out.
+__global__ void __launch_bounds__(128) image_kernel(const __grid_constant__ PointParams P,
+                                                    float4* __restrict__ img, int nf4) {
+  extern __shared__ float4 smem4[];
+  for (int t = threadIdx.x; t < nf4; t += blockDim.x) smem4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  stage_split_A(P, smem4);
+  MixedTables& T = *reinterpret_cast<MixedTables*>(reinterpret_cast<char*>(smem4) +
+                                                    split_a_bytes(P.ncls, P.R, P.M));
+  stage_tables(P, T);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nf4; t += blockDim.x) img[t] = smem4[t];
+}
+
 // Resident blocks per SM of `kern` at `smem` bytes of dynamic shared memory on
 // the current device, with the shared-memory attribute set once per device:
 // both are cached per kernel instantiation, so a launch costs no attribute or
@@ -1144,7 +1169,8 @@ cudaError_t launch_warp_k(const PointParams& hp, const DrawsParams& dp, double* 
 template <int MM, bool GRAD>
 bool try_warp(const PointParams& hp, const DrawsParams& dp, double* lnl_out, double* grad_out,
               cudaStream_t st, cudaError_t* e) {
-  if (dp.n > small_batch_max() || hp.K > kMaxDet || (hp.R != MM && hp.R != 2 * MM)) return false;
+  if (dp.n > small_batch_max() || hp.K > kMaxDet || (hp.R != MM && hp.R != 2 * MM) || !hp.img)
+    return false;
   const bool wide = hp.R > MM;
   const size_t smem = wide ? warp_smem_bytes<MM, 2 * MM>(hp.ncls, hp.R, hp.M)
                            : warp_smem_bytes<MM, MM>(hp.ncls, hp.R, hp.M);
@@ -1407,6 +1433,19 @@ int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab) {
   return rc;
 }
 
+template <int MM>
+int mixed_image(const PointParams& hp, float4** img, int* nf4, cudaStream_t st) {
+  const size_t bytes = image_bytes(hp.ncls, hp.R, hp.M);
+  *nf4 = (int)(bytes / 16);
+  *img = nullptr;
+  if (bytes > 200 * 1024) return RIFT_ILE_OK;  // no image: the warp kernel is not used then
+  int rc = check_cuda(cudaMalloc((void**)img, bytes), "point image allocation");
+  if (rc) return rc;
+  cudaFuncSetAttribute(image_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  image_kernel<<<1, 128, bytes, st>>>(hp, *img, *nf4);
+  return check_cuda(cudaGetLastError(), "point image kernel");
+}
+
 #define RIFT_INSTANTIATE_MIXED(MM)                                                              \
   template cudaError_t mixed_lnl<MM>(const PointParams&, const PointParams*, const DrawsParams&, \
                                      double*, LseState*, unsigned long long*, int*, cudaStream_t); \
@@ -1423,6 +1462,7 @@ int mixed_upload_anchors(const float4* sincos_tab, const float2* exp_tab) {
                                            double*, cudaStream_t);                                \
   template BatchKernelFn mixed_batch_kernel<MM>(int);                                             \
   template size_t mixed_batch_smem<MM>(int, int, int, int, int);                                       \
-  template int mixed_upload_anchors<MM>(const float4*, const float2*);
+  template int mixed_upload_anchors<MM>(const float4*, const float2*);                         \
+  template int mixed_image<MM>(const PointParams&, float4**, int*, cudaStream_t);
 
 }  // namespace rift

@@ -10,16 +10,23 @@
 // results to the next phase through the warp's slice of shared memory:
 //   1  lanes 0..3: anchored sine/cosine of ra - gmst, dec, 2 psi, iota;
 //      lanes 4..: of |m| phi for |m| = 1 .. max |m|; one lane the distance factor
-//   2  every lane: the sky direction, the antenna basis and its split, x e^{2 i psi}
+//   2  every lane: the sky direction and x e^{2 i psi}; lanes 0..5 the six
+//      products of the sky sines and cosines, lanes 0..9 the ten antenna-basis
+//      terms from them, split for the exact products
 //   3  lane j < M: the harmonic of mode j, split for the exact products;
 //      lane (c, r): row r of the class-c mat-vec a1 = A y, a2 = A J y
-//   4  lane k < K: x F_k, the arrival time and table position, 1/2 |e|^2 and
-//      its slope, the cubic's weights, the detector's antenna derivatives
+//   4  lane k < K: x F_k, the arrival time and table position (the table rows
+//      of the four taps are prefetched into L1), 1/2 |e|^2 and its slope, the
+//      cubic's weights, the detector's antenna derivatives
 //   5  lane (k, direction pair): the template, the residual over the four
 //      taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
-//   6  lane k: the detector's terms; lane (c, r): G1_r, G2_r of the class
-//   7  lane (c, j): the iota and phi_ref derivatives through mode j
-//   8  lane 0: the sums in a fixed order, the outputs
+//   6  lane (c, r): G1_r, G2_r of the class; lane k: the detector's terms of
+//      lnL and of the gradient
+//   7  lane (c, j): the iota and phi_ref derivatives through mode j, summed
+//      over the lanes by a fixed shuffle tree
+//   8  lane 0: the sums over detectors in a fixed order, the outputs
+// The per-point tables (split whitening, gm1, detector and mode tables) are
+// copied flat from the point's image at block start.
 // Reductions run in fixed orders, so results are reproducible; they differ
 // from the one-thread-per-draw kernel's by rounding only (e^{i |m| phi} is
 // taken by the anchored sine/cosine for every |m| rather than by recurrence,
@@ -32,6 +39,8 @@ template <int MM, int RR>
 struct WarpScratch {
   float4 ang[16];                  // (sin hi, sin lo, cos hi, cos lo): lam, dec, 2 psi, iota, |m| phi
   float2 x;                        // distance factor (hi, lo)
+  float2 base[12];                 // sl, cl, sd, cd, sl^2, cl^2, sl cl, sd^2, sd cd, cd^2, 1, 0
+  float2 bs[10];                   // antenna basis beta_0..5, gamma_0..3 as (head, tail)
   float4 ys[MM];                   // (yr1, yr2, yi1, yi2) of visited mode j
   float2 yh[MM];                   // (yr.hi, yi.hi)
   float4 a12[kMaxDet][RR];         // class c, direction r: (a1 head, a1 tail, a2 head, a2 tail)
@@ -43,18 +52,47 @@ struct WarpScratch {
   float2 he2[kMaxDet], dhe2[kMaxDet];  // 1/2 |e|^2 and its slope in f (hi, lo)
   float4 dx[kMaxDet];              // d(x F_k)/d ra (re, im), d(x F_k)/d dec (re, im)
   float2 dk[kMaxDet];              // d t_k / d ra, d t_k / d dec
-  float part[kMaxDet][RR / 2][5];  // per (k, pair): |r|^2, null term, r.edot, rho.a1, rho.a2
+  float4 part[kMaxDet][RR / 2];    // per (k, pair): |r|^2, null term, r.edot, rho.a1
+  float part5[kMaxDet][RR / 2];    // per (k, pair): rho.a2
   float2 gp[kMaxDet][RR];          // per (k, r): (Re xF_k rho_r, Im xF_k rho_r)
   float2 G[kMaxDet][RR];           // per class c, direction r: (G1, G2)
-  float2 gm[kMaxDet][MM];          // per (c, j): (d/d phi, d/d iota) shares
+  float4 fin[kMaxDet][3];          // per k: T_k, dt_k (hi, lo); gt_ra_k, gt_dec_k; g_ra, g_dec, g_psi, g_lnd
+  float2 gmode;                    // d lnL/d phi_ref, d lnL/d iota
+  float4 out[8];                   // lnL and the gradient as (hi, lo, extra, bad flag)
 };
+
+// Antenna-basis term i (beta_0..5, gamma_0..3, see antenna_basis) as
+// kappa (X Y + sigma Z W) over the values of WarpScratch::base:
+// (X, Y, Z, W, sigma + 1, kappa + 2) packed as bytes.
+__device__ __forceinline__ void basis_ops(int i, int& X, int& Y, int& Z, int& Wd, float& sig,
+                                          float& kap) {
+  // 0 sl, 1 cl, 2 sd, 3 cd, 4 sl^2, 5 cl^2, 6 sl cl, 7 sd^2, 8 sd cd, 9 cd^2, 10 one, 11 zero
+  constexpr unsigned long long code[10] = {
+      // X | Y<<4 | Z<<8 | W<<12 | (sigma+1)<<16 | (kappa+2)<<20
+      4ull | 10ull << 4 | 7ull << 8 | 5ull << 12 | 0ull << 16 | 3ull << 20,    // sl^2 - sd^2 cl^2
+      5ull | 10ull << 4 | 7ull << 8 | 4ull << 12 | 0ull << 16 | 3ull << 20,    // cl^2 - sd^2 sl^2
+      6ull | 10ull << 4 | 6ull << 8 | 7ull << 12 | 2ull << 16 | 0ull << 20,    // -2 (sl cl + sl cl sd^2)
+      8ull | 1ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20,   // 2 sd cd cl
+      8ull | 0ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20,   // 2 sd cd sl
+      9ull | 10ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 1ull << 20,  // -cd^2
+      2ull | 6ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20,   // 2 sd sl cl
+      2ull | 4ull << 4 | 2ull << 8 | 5ull << 12 | 0ull << 16 | 4ull << 20,     // 2 (sd sl^2 - sd cl^2)
+      0ull | 3ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 0ull << 20,   // -2 sl cd
+      1ull | 3ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20};  // 2 cl cd
+  const unsigned long long c = code[i];
+  X = (int)(c & 15);
+  Y = (int)((c >> 4) & 15);
+  Z = (int)((c >> 8) & 15);
+  Wd = (int)((c >> 12) & 15);
+  sig = (float)((int)((c >> 16) & 15) - 1);
+  kap = (float)((int)((c >> 20) & 15) - 2);
+}
 
 template <int MM, int RR>
 __host__ __device__ inline size_t warp_smem_bytes(int ncls, int R, int M) {
-  // the split whitening and gm1 of every class (as the per-thread kernel),
-  // then one scratch slice per warp
-  const size_t a = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
-  return a + (size_t)kWarpDrawWarps * sizeof(WarpScratch<MM, RR>);
+  // the point's image (split whitening, gm1, staged tables), then one
+  // scratch slice per warp
+  return image_bytes(ncls, R, M) + (size_t)kWarpDrawWarps * sizeof(WarpScratch<MM, RR>);
 }
 
 template <int MM, int RR, bool GRAD>
@@ -62,29 +100,37 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     lnl_warp_kernel(const __grid_constant__ PointParams P, DrawsParams dp,
                     double* __restrict__ lnl_out, double* __restrict__ grad_out) {
   extern __shared__ float4 smem4[];
-  __shared__ MixedTables T;
-  stage_split_A(P, smem4);
-  stage_tables(P, T);
-  __syncthreads();
+  // the point's image into shared memory by asynchronous copies, waited for
+  // once the first draw's angles (which need neither) are under way
+  {
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem4);
+    for (int t = threadIdx.x; t < P.img_f4; t += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * (unsigned)t),
+                   "l"(P.img + t)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   const float4* sA = smem4;
   const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
-  const size_t aoff = (size_t)P.ncls * P.R * P.M * 32 + (((size_t)P.ncls * P.R * 4 + 15) & ~(size_t)15);
+  const MixedTables& T = *reinterpret_cast<const MixedTables*>(
+      reinterpret_cast<const char*>(smem4) + split_a_bytes(P.ncls, P.R, P.M));
+  const size_t aoff = (size_t)P.img_f4 * 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpScratch<MM, RR>& W =
       reinterpret_cast<WarpScratch<MM, RR>*>(reinterpret_cast<char*>(smem4) + aoff)[warp];
   const int K = P.K, M = P.M, n = P.n, ncls = P.ncls;
   constexpr int NP = RR / 2;  // direction pairs
   int mmax = 0;
-  for (int j = 0; j < M; ++j) mmax = max(mmax, abs(T.mode[j].y));
+  for (int j = 0; j < M; ++j) mmax = max(mmax, abs(P.em[j]));
 
-  for (long long i = blockIdx.x * (long long)kWarpDrawWarps + warp; i < dp.n;
-       i += (long long)gridDim.x * kWarpDrawWarps) {
+  // ---- 1 (a function of the draw): the anchored sines and cosines, and the
+  // distance factor; leaves the draw's t_c in tc
+  df tc;
+  auto angles = [&](long long i) {
     const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
     const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
     const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
-    const df tc = load_param_df(dp, 6, i);
-
-    // ---- 1: the anchored sines and cosines, and the distance factor
+    tc = load_param_df(dp, 6, i);
     if (lane < 4 + mmax) {
       df a;
       if (lane == 0) {
@@ -110,6 +156,16 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       W.x = make_float2(x.hi, x.lo);
     }
     __syncwarp();
+  };
+
+  const long long i0 = blockIdx.x * (long long)kWarpDrawWarps + warp;
+  const long long stride = (long long)gridDim.x * kWarpDrawWarps;
+  if (i0 < dp.n) angles(i0);  // uniform over the warp
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+
+  for (long long i = i0; i < dp.n; i += stride) {
+    if (i != i0) angles(i);
 
     // ---- 2: sky direction, antenna basis (every lane), x e^{2 i psi}
     const float4 a0 = W.ang[0], a1v = W.ang[1], a2v = W.ang[2], a3v = W.ang[3];
@@ -118,6 +174,35 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     const df x{W.x.x, W.x.y};
     const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
     const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
+    // the antenna basis: six products on lanes 0..5, ten terms on lanes 0..9
+    if (lane < 6) {
+      // (sl, sl), (cl, cl), (sl, cl), (sd, sd), (sd, cd), (cd, cd)
+      const df u = lane < 2 ? (lane == 0 ? sl : cl) : lane == 2 ? sl : lane == 5 ? cd : sd;
+      const df v = lane == 0 ? sl : lane < 3 ? cl : lane == 3 ? sd : cd;
+      const df pr = df_mul(u, v);
+      W.base[4 + lane] = make_float2(pr.hi, pr.lo);
+    } else if (lane < 10) {
+      const df b = lane == 6 ? sl : lane == 7 ? cl : lane == 8 ? sd : cd;
+      W.base[lane - 6] = make_float2(b.hi, b.lo);
+    } else if (lane == 10) {
+      W.base[10] = make_float2(1.f, 0.f);
+      W.base[11] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    if (lane < 10) {
+      int X, Y, Z, Wd;
+      float sig, kap;
+      basis_ops(lane, X, Y, Z, Wd, sig, kap);
+      const float2 bx = W.base[X], by = W.base[Y], bz = W.base[Z], bw = W.base[Wd];
+      const df p1 = df_mul(df{bx.x, bx.y}, df{by.x, by.y});
+      const df p2 = df_mul(df{bz.x, bz.y}, df{bw.x, bw.y});
+      const df q = df_add(p1, df{sig * p2.hi, sig * p2.lo});
+      // kappa is 0, +-1 or +-2: the scaling is exact; then the split of
+      // split_antenna_basis (head on the 2^-8 grid, tail = rest + low part)
+      const float qh = kap * q.hi, ql = kap * q.lo;
+      const float h = head_of(qh, 49152.0f);
+      W.bs[lane] = make_float2(h, __fadd_rn(__fsub_rn(qh, h), ql));
+    }
 
     // ---- 3a: lane j < M: the harmonic of mode j (visiting order), split
     if (lane < M) {
@@ -162,14 +247,49 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
                                 __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
     }
 
-    // ---- 4: lane k < K: antenna factor, arrival time, table position, 1/2|e|^2
+    // ---- 4: lane k < K: arrival time and table position first, so that the
+    // interval polynomial's coefficients and the tap rows are in flight while
+    // the antenna factor is formed; then 1/2|e|^2, the weights, the derivatives
     if (lane < K) {
       const int k = lane;
+      const float4 ph = T.pos_hi[k], pl = T.pos_lo[k];
+      df delay = df_mul(df{ph.x, pl.x}, s0);
+      delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
+      delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
+      const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
+      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
+      const int bad = isfinite(u.hi) ? 0 : 1;
+      float f = 0.f, jf = 0.f;
+      if (!bad) {
+        jf = floorf(u.hi);
+        if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
+        f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
+      }
+      const bool inpoly = !bad && jf >= -2.f && jf <= (float)n;
+      float2 cf[kPolyDeg + 1];
+      if (inpoly) {
+        const float2* pc =
+            P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
+#pragma unroll
+        for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
+      }
+      const int jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
+      {  // the four tap rows (contiguous) into L1 for the residual phase
+        const char* row = reinterpret_cast<const char*>(
+            P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (jck - 1)) * RR);
+        for (int off = 0; off < 4 * RR * 8; off += 128)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(row + off));
+      }
       AntennaSplit AS;
-      {
-        AntennaBasis AB;
-        antenna_basis(sl, cl, sd, cd, AB);
-        split_antenna_basis(AB, AS);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        AS.bh[q] = W.bs[q].x;
+        AS.bt[q] = W.bs[q].y;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        AS.gh[q] = W.bs[6 + q].x;
+        AS.gt[q] = W.bs[6 + q].y;
       }
       df xFr, xFi;
       antenna_df(T, k, AS, xer, xei, xFr, xFi);
@@ -177,61 +297,6 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
       W.xf[k] = make_float4(xrh, __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo), xih,
                             __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo));
-      const float4 ph = T.pos_hi[k], pl = T.pos_lo[k];
-      df delay = df_mul(df{ph.x, pl.x}, s0);
-      delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
-      delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
-      const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
-      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
-      int bad = 0;
-      float f = 0.f, jf = 0.f;
-      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
-      if (!isfinite(u.hi)) {
-        bad = 1;
-      } else {
-        jf = floorf(u.hi);
-        if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
-        f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
-        if (jf >= -2.f && jf <= (float)n) {
-          const float2* pc =
-              P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
-          float2 cf = __ldg(pc + kPolyDeg);
-          df acc = df{cf.x, cf.y};
-          df dacc_p = df{0.f, 0.f};
-#pragma unroll
-          for (int p = kPolyDeg - 1; p >= 0; --p) {
-            if (GRAD) {
-              df pr = two_prod(dacc_p.hi, f);
-              pr.lo = fmaf(dacc_p.lo, f, pr.lo);
-              const df sm3 = two_sum(pr.hi, acc.hi);
-              dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
-            }
-            cf = __ldg(pc + p);
-            df pr = two_prod(acc.hi, f);
-            pr.lo = fmaf(acc.lo, f, pr.lo);
-            const df sm2 = two_sum(pr.hi, cf.x);
-            acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf.y));
-          }
-          half_e2 = acc;
-          dhalf = dacc_p;
-        }
-      }
-      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
-      const float w0 = -(f * fc * fd) * (1.f / 6.f), w1 = (fa * fc * fd) * 0.5f;
-      const float w2 = -(fa * f * fd) * 0.5f, w3 = (fa * f * fc) * (1.f / 6.f);
-      const df ws = df_add(two_sum(w0, w1), two_sum(w2, w3));
-      W.sigma[k] = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
-      W.wt[k] = make_float4(w0, w1, w2, w3);
-      if (GRAD) {
-        W.wtd[k] = make_float4(-(fc * fd + f * fd + f * fc) * (1.f / 6.f),
-                               (fc * fd + fa * fd + fa * fc) * 0.5f,
-                               -(f * fd + fa * fd + fa * f) * 0.5f,
-                               (f * fc + fa * fc + fa * f) * (1.f / 6.f));
-      }
-      W.jc[k] = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-      W.bad[k] = bad;
-      W.he2[k] = make_float2(half_e2.hi, half_e2.lo);
-      W.dhe2[k] = make_float2(dhalf.hi, dhalf.lo);
       if (GRAD) {
         AntennaBasisGrad ABG;
         antenna_basis_grad(sl.hi, cl.hi, sd.hi, cd.hi, ABG);
@@ -261,6 +326,44 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         W.dk[k] = make_float2(-(ph.x * (-cd.hi * sl.hi) + ph.y * (cd.hi * cl.hi)),
                               -(ph.x * (-sd.hi * cl.hi) + ph.y * (-sd.hi * sl.hi) + ph.z * cd.hi));
       }
+      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the
+      // table) and its slope in f, Horner on both as in the per-thread kernel
+      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
+      if (inpoly) {
+        df acc = df{cf[kPolyDeg].x, cf[kPolyDeg].y};
+        df dacc_p = df{0.f, 0.f};
+#pragma unroll
+        for (int p = kPolyDeg - 1; p >= 0; --p) {
+          if (GRAD) {
+            df pr = two_prod(dacc_p.hi, f);
+            pr.lo = fmaf(dacc_p.lo, f, pr.lo);
+            const df sm3 = two_sum(pr.hi, acc.hi);
+            dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
+          }
+          df pr = two_prod(acc.hi, f);
+          pr.lo = fmaf(acc.lo, f, pr.lo);
+          const df sm2 = two_sum(pr.hi, cf[p].x);
+          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf[p].y));
+        }
+        half_e2 = acc;
+        dhalf = dacc_p;
+      }
+      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
+      const float w0 = -(f * fc * fd) * (1.f / 6.f), w1 = (fa * fc * fd) * 0.5f;
+      const float w2 = -(fa * f * fd) * 0.5f, w3 = (fa * f * fc) * (1.f / 6.f);
+      const df ws = df_add(two_sum(w0, w1), two_sum(w2, w3));
+      W.sigma[k] = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
+      W.wt[k] = make_float4(w0, w1, w2, w3);
+      if (GRAD) {
+        W.wtd[k] = make_float4(-(fc * fd + f * fd + f * fc) * (1.f / 6.f),
+                               (fc * fd + fa * fd + fa * fc) * 0.5f,
+                               -(f * fd + fa * fd + fa * f) * 0.5f,
+                               (f * fc + fa * fc + fa * f) * (1.f / 6.f));
+      }
+      W.jc[k] = jck;
+      W.bad[k] = bad;
+      W.he2[k] = make_float2(half_e2.hi, half_e2.lo);
+      W.dhe2[k] = make_float2(dhalf.hi, dhalf.lo);
     }
     __syncwarp();
 
@@ -315,25 +418,25 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         gm = make_float2(gc[r], gc[r + 1]);
         nul = __fmul2_rn(__fmul2_rn(gm, nwf), nwf);
       }
-      float* pt = W.part[k][pr];
-      pt[0] = __fadd_rn(q2.x, q2.y);
-      pt[1] = __fadd_rn(nul.x, nul.y);
+      float4 pt = make_float4(__fadd_rn(q2.x, q2.y), __fadd_rn(nul.x, nul.y), 0.f, 0.f);
       if (GRAD) {
         const float2 red = __fmul2_rn(rsv, ed);
         const float2 rho = __ffma2_rn(make_float2(-gm.x, -gm.y), nwf, rsv);
         const float2 g1 = __fmul2_rn(rho, __fadd2_rn(a1h, a1t));
         const float2 g2 = __fmul2_rn(rho, __fadd2_rn(a2h, a2t));
-        pt[2] = __fadd_rn(red.x, red.y);
-        pt[3] = __fadd_rn(g1.x, g1.y);
-        pt[4] = __fadd_rn(g2.x, g2.y);
+        pt.z = __fadd_rn(red.x, red.y);
+        pt.w = __fadd_rn(g1.x, g1.y);
+        W.part5[k][pr] = __fadd_rn(g2.x, g2.y);
         const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
         W.gp[k][r] = make_float2(xFr * rho.x, xFi * rho.x);
         W.gp[k][r + 1] = make_float2(xFr * rho.y, xFi * rho.y);
       }
+      W.part[k][pr] = pt;
     }
     __syncwarp();
 
-    // ---- 6a: lane (c, r): G1_r, G2_r of class c over its detectors in order
+    // ---- 6: lane (c, r): G1_r, G2_r of class c over its detectors in order;
+    // lane k: the detector's terms
     if (GRAD) {
       for (int it = lane; it < ncls * RR; it += 32) {
         const int c = it / RR, r = it - c * RR;
@@ -347,8 +450,46 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         }
         W.G[c][r] = make_float2(g1, g2);
       }
-      __syncwarp();
+    }
+    if (lane < K && !W.bad[lane]) {
+      const int k = lane, c = P.cls_of[k];
+      float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
+      for (int pr = 0; pr < NP; ++pr) {
+        const float4 v = W.part[k][pr];
+        q2 += v.x;
+        nul += v.y;
+        if (GRAD) {
+          red += v.z;
+          g1 += v.w;
+          g2 += W.part5[k][pr];
+        }
+      }
+      const float2 he = W.he2[k];
+      dacc tk = dacc_zero();
+      dacc_add(tk, df{he.x, he.y});
+      dacc_add(tk, df{-0.5f * q2, 0.f});
+      if (P.has_null[c]) dacc_add(tk, df{0.5f * nul, 0.f});
+      const df tv = dacc_result(tk);
+      if (GRAD) {
+        const float2 dh = W.dhe2[k];
+        const df dtk = df_mul(df_add_f(df{dh.x, dh.y}, -red), df{P.inv_dt_hi, P.inv_dt_lo});
+        const float2 dkk = W.dk[k];
+        const df dra = df_mul_f(dtk, dkk.x), ddec = df_mul_f(dtk, dkk.y);
+        const float4 d = W.dx[k];
+        const float4 xfq = W.xf[k];
+        const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
+        W.fin[k][0] = make_float4(tv.hi, tv.lo, dtk.hi, dtk.lo);
+        W.fin[k][1] = make_float4(dra.hi, dra.lo, ddec.hi, ddec.lo);
+        W.fin[k][2] = make_float4(fmaf(d.x, g1, d.y * g2), fmaf(d.z, g1, d.w * g2),
+                                  fmaf(-2.f * xFi, g1, 2.f * xFr * g2), fmaf(-xFr, g1, -xFi * g2));
+      } else {
+        W.fin[k][0] = make_float4(tv.hi, tv.lo, 0.f, 0.f);
+      }
+    }
+    __syncwarp();
+    if (GRAD) {
       // ---- 7: lane (c, j): iota and phi_ref through mode j of class c
+      float gph = 0.f, gin = 0.f;
       for (int it = lane; it < ncls * M; it += 32) {
         const int c = it / M, j = it - c * M;
         const float4* Ac2 = sA + (size_t)c * RR * M * 2;
@@ -375,77 +516,68 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         float amp, damp;
         sylm_amp_grad_f(T, j, md.z, md.w, z.hi, sz.hi, amp, damp);
         const float yre = amp * cmf, yim = sgn * amp * smf;
-        W.gm[c][j] = make_float2((float)m * fmaf(-yim, Hre, yre * Him),
-                                 fmaf(damp * cmf, Hre, sgn * damp * smf * Him));
+        gph = fmaf((float)m, fmaf(-yim, Hre, yre * Him), gph);
+        gin = fmaf(damp * cmf, Hre, fmaf(sgn * damp * smf, Him, gin));
       }
+      // a fixed shuffle tree over the 32 lanes
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        gph += __shfl_down_sync(0xffffffffu, gph, off);
+        gin += __shfl_down_sync(0xffffffffu, gin, off);
+      }
+      if (lane == 0) W.gmode = make_float2(gph, gin);
       __syncwarp();
     }
 
-    // ---- 8: lane 0: the sums over detectors (classes, then the class's
-    // detectors in order, as the per-thread kernel), the outputs
+    // ---- 8: lane 0 sums over detectors in a fixed order (pairs and floats
+    // only); lanes 0..7 then form one output each in FP64 (a warp-wide FP64
+    // instruction costs the same for one lane or eight)
     if (lane == 0) {
       dacc Tl = dacc_zero();
       dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
-      float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_incl = 0.f, g_phase = 0.f, g_lnd = 0.f;
-      bool bad = false;
-      for (int c = 0; c < ncls; ++c) {
-        for (int q = P.cls_begin[c]; q < P.cls_begin[c + 1]; ++q) {
-          const int k = P.det_order[q];
-          if (W.bad[k]) {
-            bad = true;
-            continue;
-          }
-          float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
-          for (int pr = 0; pr < NP; ++pr) {
-            q2 += W.part[k][pr][0];
-            nul += W.part[k][pr][1];
-            if (GRAD) {
-              red += W.part[k][pr][2];
-              g1 += W.part[k][pr][3];
-              g2 += W.part[k][pr][4];
-            }
-          }
-          const float2 he = W.he2[k];
-          dacc_add(Tl, df{he.x, he.y});
-          dacc_add(Tl, df{-0.5f * q2, 0.f});
-          if (P.has_null[c]) dacc_add(Tl, df{0.5f * nul, 0.f});
-          if (GRAD) {
-            const float2 dh = W.dhe2[k];
-            const df dtk = df_mul(df_add_f(df{dh.x, dh.y}, -red), df{P.inv_dt_hi, P.inv_dt_lo});
-            const float2 dkk = W.dk[k];
-            dacc_add(gt_t, dtk);
-            dacc_add(gt_ra, df_mul_f(dtk, dkk.x));
-            dacc_add(gt_dec, df_mul_f(dtk, dkk.y));
-            const float4 d = W.dx[k];
-            const float4 xfq = W.xf[k];
-            const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
-            g_ra = fmaf(d.x, g1, fmaf(d.y, g2, g_ra));
-            g_dec = fmaf(d.z, g1, fmaf(d.w, g2, g_dec));
-            g_psi = fmaf(-2.f * xFi, g1, fmaf(2.f * xFr, g2, g_psi));
-            g_lnd = fmaf(-xFr, g1, fmaf(-xFi, g2, g_lnd));
-          }
+      float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_lnd = 0.f;
+      int bad = 0;
+      for (int q = 0; q < K; ++q) {
+        const int k = P.det_order[q];
+        if (W.bad[k]) {
+          bad = 1;
+          continue;
         }
-        if (GRAD)
-          for (int j = 0; j < M; ++j) {
-            g_phase += W.gm[c][j].x;
-            g_incl += W.gm[c][j].y;
-          }
+        const float4 f0 = W.fin[k][0];
+        dacc_add(Tl, df{f0.x, f0.y});
+        if (GRAD) {
+          const float4 f1 = W.fin[k][1], f2 = W.fin[k][2];
+          dacc_add(gt_t, df{f0.z, f0.w});
+          dacc_add(gt_ra, df{f1.x, f1.y});
+          dacc_add(gt_dec, df{f1.z, f1.w});
+          g_ra += f2.x;
+          g_dec += f2.y;
+          g_psi += f2.z;
+          g_lnd += f2.w;
+        }
       }
       const df lnl = dacc_result(Tl);
-      const double lv = bad ? CUDART_NAN : (double)lnl.hi + (double)lnl.lo;
-      if (lnl_out) lnl_out[i] = lv;
+      W.out[0] = make_float4(lnl.hi, lnl.lo, 0.f, __int_as_float(bad));
       if (GRAD) {
         const df a = dacc_result(gt_ra), b = dacc_result(gt_dec), t = dacc_result(gt_t);
-        double g[kNpar];
-        g[0] = (double)a.hi + (double)a.lo + (double)g_ra;
-        g[1] = (double)b.hi + (double)b.lo + (double)g_dec;
-        g[2] = g_psi;
-        g[3] = g_incl;
-        g[4] = g_phase;
-        g[5] = g_lnd;
-        g[6] = (double)t.hi + (double)t.lo;
-#pragma unroll
-        for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = bad ? CUDART_NAN : g[p];
+        W.out[1] = make_float4(a.hi, a.lo, g_ra, 0.f);
+        W.out[2] = make_float4(b.hi, b.lo, g_dec, 0.f);
+        W.out[3] = make_float4(g_psi, 0.f, 0.f, 0.f);
+        W.out[4] = make_float4(W.gmode.y, 0.f, 0.f, 0.f);
+        W.out[5] = make_float4(W.gmode.x, 0.f, 0.f, 0.f);
+        W.out[6] = make_float4(g_lnd, 0.f, 0.f, 0.f);
+        W.out[7] = make_float4(t.hi, t.lo, 0.f, 0.f);
+      }
+    }
+    __syncwarp();
+    if (lane < (GRAD ? 8 : 1)) {
+      const float4 o = W.out[lane];
+      const bool bad = __float_as_int(W.out[0].w) != 0;
+      const double v = bad ? CUDART_NAN : (double)o.x + (double)o.y + (double)o.z;
+      if (lane == 0) {
+        if (lnl_out) lnl_out[i] = v;
+      } else {
+        grad_out[(size_t)(lane - 1) * dp.n + i] = v;
       }
     }
     __syncwarp();  // the scratch is reused by this warp's next draw

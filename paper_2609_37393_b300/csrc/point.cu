@@ -31,6 +31,7 @@
 #include <cstring>
 #include <vector>
 
+#include "kernels.h"
 #include "rift_ile_internal.h"
 
 namespace rift {
@@ -355,6 +356,7 @@ extern "C" int rift_ile_point_destroy(rift_ile_point* pt) {
   cudaFree(pt->gm1);
   cudaFree(pt->ehat);
   cudaFree(pt->epoly);
+  cudaFree(pt->img);
   delete pt;
   return RIFT_ILE_OK;
 }
@@ -666,6 +668,8 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     P.gm1 = pt->gm1;
     P.ehat = pt->ehat;
     P.epoly = pt->epoly;
+    if ((rc = build_mixed_image(P, &pt->img, &P.img_f4, stream))) break;
+    P.img = pt->img;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->dev, &P, sizeof(PointParams), cudaMemcpyHostToDevice,
                                          stream), "copy of point parameters")))
       break;

@@ -78,6 +78,12 @@ struct PointParams {
   const float* gm1;     // [ncls][R]     1 - lam_r/s_r^2 (0 except kept null directions)
   const float2* ehat;   // [K][n + 2 kEhatPad][R] whitened Q table, zero rows around it
   const float2* epoly;  // [K][n+3][7]   1/2|e(f)|^2 on interval j (index j+2), coefficients of f^0..f^6
+  // The shared-memory image of the FP32-mixed kernels' per-point tables (the
+  // split whitening, gm1 and the staged detector and mode tables, built once
+  // at point creation): the warp-per-draw kernel copies it flat.
+  const float4* img;
+  int img_f4;           // its length in float4
+  int pad1;
 };
 
 // Per-launch description of the draws.
@@ -121,5 +127,6 @@ struct rift_ile_point {
   float* gm1;                    // owned
   float2* ehat;                  // owned
   float2* epoly;                 // owned
+  float4* img;                   // owned
   int device;
 };

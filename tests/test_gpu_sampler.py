@@ -90,10 +90,17 @@ def test_warp_kernel_forward_only(R, cfg2):
 
 
 def test_warp_kernel_event_network_two_classes(R):
-    """K = 5 (ET triangle + CE 40 km + CE 20 km): two detector classes."""
+    """K = 5 (ET triangle + CE 40 km + CE 20 km) with the two CE detectors'
+    noise scaled (their Q, U and V by 1.7, a consistent point): two detector
+    classes, so the per-class mat-vec, sums and iota/phi_ref terms run twice."""
     point, exact, info, draws, logw = W.config4(n_draws=512)
+    point = dict(point)
+    for key in ("Q", "U", "V"):
+        a = np.array(point[key])
+        a[3:] = (a[3:] * 1.7).astype(a.dtype)
+        point[key] = a
     pt = R.Point(point)
-    assert pt.info()["ncls"] >= 2
+    assert pt.info()["ncls"] == 2
     lw, gw = run(R, pt, draws, warp=True)
     rl, rg = O.lnL_grad(O.OraclePoint(point), draws)
     near = rl >= rl.max() - 50
