@@ -21,10 +21,11 @@
 //   5  lane (k, direction pair): the template, the residual over the four
 //      taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
 //   6  lane (c, r): G1_r, G2_r of the class; lane k: the detector's terms of
-//      lnL and of the gradient
+//      lnL and of the gradient, summed over the detectors by a fixed shuffle
+//      tree (compensated pairs merged exactly)
 //   7  lane (c, j): the iota and phi_ref derivatives through mode j, summed
 //      over the lanes by a fixed shuffle tree
-//   8  lane 0: the sums over detectors in a fixed order, the outputs
+//   8  lanes 0..7: the outputs
 // The per-point tables (split whitening, gm1, detector and mode tables) are
 // copied flat from the point's image at block start.
 // Reductions run in fixed orders, so results are reproducible; they differ
@@ -56,7 +57,6 @@ struct WarpScratch {
   float part5[kMaxDet][RR / 2];    // per (k, pair): rho.a2
   float2 gp[kMaxDet][RR];          // per (k, r): (Re xF_k rho_r, Im xF_k rho_r)
   float2 G[kMaxDet][RR];           // per class c, direction r: (G1, G2)
-  float4 fin[kMaxDet][3];          // per k: T_k, dt_k (hi, lo); gt_ra_k, gt_dec_k; g_ra, g_dec, g_psi, g_lnd
   float2 gmode;                    // d lnL/d phi_ref, d lnL/d iota
   float4 out[8];                   // lnL and the gradient as (hi, lo, extra, bad flag)
 };
@@ -64,28 +64,54 @@ struct WarpScratch {
 // Antenna-basis term i (beta_0..5, gamma_0..3, see antenna_basis) as
 // kappa (X Y + sigma Z W) over the values of WarpScratch::base:
 // (X, Y, Z, W, sigma + 1, kappa + 2) packed as bytes.
-__device__ __forceinline__ void basis_ops(int i, int& X, int& Y, int& Z, int& Wd, float& sig,
-                                          float& kap) {
-  // 0 sl, 1 cl, 2 sd, 3 cd, 4 sl^2, 5 cl^2, 6 sl cl, 7 sd^2, 8 sd cd, 9 cd^2, 10 one, 11 zero
-  constexpr unsigned long long code[10] = {
-      // X | Y<<4 | Z<<8 | W<<12 | (sigma+1)<<16 | (kappa+2)<<20
-      4ull | 10ull << 4 | 7ull << 8 | 5ull << 12 | 0ull << 16 | 3ull << 20,    // sl^2 - sd^2 cl^2
-      5ull | 10ull << 4 | 7ull << 8 | 4ull << 12 | 0ull << 16 | 3ull << 20,    // cl^2 - sd^2 sl^2
-      6ull | 10ull << 4 | 6ull << 8 | 7ull << 12 | 2ull << 16 | 0ull << 20,    // -2 (sl cl + sl cl sd^2)
-      8ull | 1ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20,   // 2 sd cd cl
-      8ull | 0ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20,   // 2 sd cd sl
-      9ull | 10ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 1ull << 20,  // -cd^2
-      2ull | 6ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20,   // 2 sd sl cl
-      2ull | 4ull << 4 | 2ull << 8 | 5ull << 12 | 0ull << 16 | 4ull << 20,     // 2 (sd sl^2 - sd cl^2)
-      0ull | 3ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 0ull << 20,   // -2 sl cd
-      1ull | 3ull << 4 | 11ull << 8 | 11ull << 12 | 1ull << 16 | 4ull << 20};  // 2 cl cd
-  const unsigned long long c = code[i];
-  X = (int)(c & 15);
-  Y = (int)((c >> 4) & 15);
-  Z = (int)((c >> 8) & 15);
-  Wd = (int)((c >> 12) & 15);
-  sig = (float)((int)((c >> 16) & 15) - 1);
-  kap = (float)((int)((c >> 20) & 15) - 2);
+// Operand codes of the ten antenna-basis terms over WarpScratch::base
+// (0 sl, 1 cl, 2 sd, 3 cd, 4 sl^2, 5 cl^2, 6 sl cl, 7 sd^2, 8 sd cd, 9 cd^2,
+// 10 one, 11 zero): X | Y<<4 | Z<<8 | W<<12 | (sigma+1)<<16 | (kappa+2)<<20
+// for the term kappa (X Y + sigma Z W).  Copied into shared memory at block
+// start, so that each lane reads its own code without a branch.
+__host__ __device__ constexpr unsigned basis_code(int i) {
+  return i == 0 ? (4u | 10u << 4 | 7u << 8 | 5u << 12 | 0u << 16 | 3u << 20)      // sl^2 - sd^2 cl^2
+         : i == 1 ? (5u | 10u << 4 | 7u << 8 | 4u << 12 | 0u << 16 | 3u << 20)    // cl^2 - sd^2 sl^2
+         : i == 2 ? (6u | 10u << 4 | 6u << 8 | 7u << 12 | 2u << 16 | 0u << 20)    // -2 (sl cl + sl cl sd^2)
+         : i == 3 ? (8u | 1u << 4 | 11u << 8 | 11u << 12 | 1u << 16 | 4u << 20)   // 2 sd cd cl
+         : i == 4 ? (8u | 0u << 4 | 11u << 8 | 11u << 12 | 1u << 16 | 4u << 20)   // 2 sd cd sl
+         : i == 5 ? (9u | 10u << 4 | 11u << 8 | 11u << 12 | 1u << 16 | 1u << 20)  // -cd^2
+         : i == 6 ? (2u | 6u << 4 | 11u << 8 | 11u << 12 | 1u << 16 | 4u << 20)   // 2 sd sl cl
+         : i == 7 ? (2u | 4u << 4 | 2u << 8 | 5u << 12 | 0u << 16 | 4u << 20)     // 2 (sd sl^2 - sd cl^2)
+         : i == 8 ? (0u | 3u << 4 | 11u << 8 | 11u << 12 | 1u << 16 | 0u << 20)   // -2 sl cd
+                  : (1u | 3u << 4 | 11u << 8 | 11u << 12 | 1u << 16 | 4u << 20);  // 2 cl cd
+}
+
+// sylm_amp_df with the Horner loop unrolled to the largest degree (steps
+// beyond the mode's degree are skipped), so its coefficient reads issue
+// together.
+__device__ __forceinline__ df sylm_amp_df_unrolled(const MixedTables& T, int j, int l, int par, df z,
+                                                   df sz) {
+  float2 cq[kMaxEll + 1];
+#pragma unroll
+  for (int q = 0; q <= kMaxEll; ++q) cq[q] = T.yz[j][q];
+  df acc = df{0.f, 0.f};
+  bool started = false;
+#pragma unroll
+  for (int q = kMaxEll; q >= 0; --q) {
+    if (q > l) continue;
+    if (!started) {
+      acc = df{cq[q].x, cq[q].y};
+      started = true;
+      continue;
+    }
+    df pr = two_prod(acc.hi, z.hi);
+    pr.lo = fmaf(acc.hi, z.lo, fmaf(acc.lo, z.hi, pr.lo));
+    const df sm = two_sum(pr.hi, cq[q].x);
+    acc = fast_two_sum(sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), cq[q].y));
+  }
+  return par ? df_mul(acc, sz) : acc;
+}
+
+// Merge of two compensated accumulators (the sum of their values).
+__device__ __forceinline__ dacc dacc_merge(dacc a, dacc b) {
+  const df t = two_sum(a.s, b.s);
+  return dacc{t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo)};
 }
 
 template <int MM, int RR>
@@ -100,6 +126,8 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     lnl_warp_kernel(const __grid_constant__ PointParams P, DrawsParams dp,
                     double* __restrict__ lnl_out, double* __restrict__ grad_out) {
   extern __shared__ float4 smem4[];
+  __shared__ unsigned s_basis[10];
+  if (threadIdx.x < 10) s_basis[threadIdx.x] = basis_code(threadIdx.x);
   // the point's image into shared memory by asynchronous copies, waited for
   // once the first draw's angles (which need neither) are under way
   {
@@ -131,7 +159,12 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
     const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
     tc = load_param_df(dp, 6, i);
-    if (lane < 4 + mmax) {
+    // every lane takes the exponential in the same instruction stream as its
+    // sine and cosine, so the two anchor-table reads are in flight together
+    df lx = two_sum(P.ln_dref_hi, -lnD);
+    lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
+    const df x = exp_df(fast_two_sum(lx.hi, lx.lo));
+    {
       df a;
       if (lane == 0) {
         a = two_sum(ra, -P.gmst_hi);
@@ -147,13 +180,9 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         a = two_prod((float)(lane - 3), phi);
       }
       df s, c;
-      sincos_df(a, s, c);
-      W.ang[lane] = make_float4(s.hi, s.lo, c.hi, c.lo);
-    } else if (lane == 31) {
-      df lx = two_sum(P.ln_dref_hi, -lnD);
-      lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
-      const df x = exp_df(fast_two_sum(lx.hi, lx.lo));
-      W.x = make_float2(x.hi, x.lo);
+      sincos_df(a, s, c);  // lanes beyond 3 + max|m| take a harmless spare angle
+      if (lane < 4 + mmax) W.ang[lane] = make_float4(s.hi, s.lo, c.hi, c.lo);
+      if (lane == 31) W.x = make_float2(x.hi, x.lo);
     }
     __syncwarp();
   };
@@ -190,9 +219,11 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     }
     __syncwarp();
     if (lane < 10) {
-      int X, Y, Z, Wd;
-      float sig, kap;
-      basis_ops(lane, X, Y, Z, Wd, sig, kap);
+      const unsigned code = s_basis[lane];
+      const int X = (int)(code & 15u), Y = (int)((code >> 4) & 15u);
+      const int Z = (int)((code >> 8) & 15u), Wd = (int)((code >> 12) & 15u);
+      const float sig = (float)((int)((code >> 16) & 15u) - 1);
+      const float kap = (float)((int)((code >> 20) & 15u) - 2);
       const float2 bx = W.base[X], by = W.base[Y], bz = W.base[Z], bw = W.base[Wd];
       const df p1 = df_mul(df{bx.x, bx.y}, df{by.x, by.y});
       const df p2 = df_mul(df{bz.x, bz.y}, df{bw.x, bw.y});
@@ -214,7 +245,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         sm = df{e.x, e.y};
         cm = df{e.z, e.w};
       }
-      const df amp = sylm_amp_df(T, lane, md.z, md.w, z, sz);
+      const df amp = sylm_amp_df_unrolled(T, lane, md.z, md.w, z, sz);
       const df yr = df_mul(amp, cm);
       const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
       float yr1, yr2, yi1, yi2;
@@ -229,7 +260,9 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       const int c = it / RR, r = it - c * RR;
       const float4* Ac = sA + (size_t)c * RR * M * 2;
       float2 ex = make_float2(0.f, 0.f), co = make_float2(0.f, 0.f);
-      for (int j = 0; j < M; ++j) {
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        if (j >= M) break;
         const float4 y = W.ys[j];
         const float2 yh = W.yh[j];
         const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
@@ -451,9 +484,15 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         W.G[c][r] = make_float2(g1, g2);
       }
     }
-    if (lane < K && !W.bad[lane]) {
+    // lane k's terms (zero on lanes without a detector or with a bad one)
+    dacc tk = dacc_zero(), gk_t = dacc_zero(), gk_ra = dacc_zero(), gk_dec = dacc_zero();
+    float gk[4] = {0.f, 0.f, 0.f, 0.f};  // ra, dec, psi, lnD through the antenna factor
+    int badk = 0;
+    if (lane < K) badk = W.bad[lane];
+    if (lane < K && !badk) {
       const int k = lane, c = P.cls_of[k];
       float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
       for (int pr = 0; pr < NP; ++pr) {
         const float4 v = W.part[k][pr];
         q2 += v.x;
@@ -465,25 +504,46 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         }
       }
       const float2 he = W.he2[k];
-      dacc tk = dacc_zero();
       dacc_add(tk, df{he.x, he.y});
       dacc_add(tk, df{-0.5f * q2, 0.f});
       if (P.has_null[c]) dacc_add(tk, df{0.5f * nul, 0.f});
-      const df tv = dacc_result(tk);
       if (GRAD) {
         const float2 dh = W.dhe2[k];
         const df dtk = df_mul(df_add_f(df{dh.x, dh.y}, -red), df{P.inv_dt_hi, P.inv_dt_lo});
         const float2 dkk = W.dk[k];
         const df dra = df_mul_f(dtk, dkk.x), ddec = df_mul_f(dtk, dkk.y);
+        gk_t = dacc{dtk.hi, dtk.lo};
+        gk_ra = dacc{dra.hi, dra.lo};
+        gk_dec = dacc{ddec.hi, ddec.lo};
         const float4 d = W.dx[k];
         const float4 xfq = W.xf[k];
         const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
-        W.fin[k][0] = make_float4(tv.hi, tv.lo, dtk.hi, dtk.lo);
-        W.fin[k][1] = make_float4(dra.hi, dra.lo, ddec.hi, ddec.lo);
-        W.fin[k][2] = make_float4(fmaf(d.x, g1, d.y * g2), fmaf(d.z, g1, d.w * g2),
-                                  fmaf(-2.f * xFi, g1, 2.f * xFr * g2), fmaf(-xFr, g1, -xFi * g2));
-      } else {
-        W.fin[k][0] = make_float4(tv.hi, tv.lo, 0.f, 0.f);
+        gk[0] = fmaf(d.x, g1, d.y * g2);
+        gk[1] = fmaf(d.z, g1, d.w * g2);
+        gk[2] = fmaf(-2.f * xFi, g1, 2.f * xFr * g2);
+        gk[3] = fmaf(-xFr, g1, -xFi * g2);
+      }
+    }
+    // the sums over detectors: a fixed shuffle tree over lanes 0..7
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      dacc o;
+      o.s = __shfl_down_sync(0xffffffffu, tk.s, off, 8);
+      o.c = __shfl_down_sync(0xffffffffu, tk.c, off, 8);
+      tk = dacc_merge(tk, o);
+      badk |= __shfl_down_sync(0xffffffffu, badk, off, 8);
+      if (GRAD) {
+        o.s = __shfl_down_sync(0xffffffffu, gk_t.s, off, 8);
+        o.c = __shfl_down_sync(0xffffffffu, gk_t.c, off, 8);
+        gk_t = dacc_merge(gk_t, o);
+        o.s = __shfl_down_sync(0xffffffffu, gk_ra.s, off, 8);
+        o.c = __shfl_down_sync(0xffffffffu, gk_ra.c, off, 8);
+        gk_ra = dacc_merge(gk_ra, o);
+        o.s = __shfl_down_sync(0xffffffffu, gk_dec.s, off, 8);
+        o.c = __shfl_down_sync(0xffffffffu, gk_dec.c, off, 8);
+        gk_dec = dacc_merge(gk_dec, o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gk[q] += __shfl_down_sync(0xffffffffu, gk[q], off, 8);
       }
     }
     __syncwarp();
@@ -494,6 +554,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         const int c = it / M, j = it - c * M;
         const float4* Ac2 = sA + (size_t)c * RR * M * 2;
         float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
+#pragma unroll
         for (int r = 0; r < RR; ++r) {
           const float4 ah = Ac2[2 * (r * M + j)];  // (t_h, b_h, t_t, b_t)
           const float ath = ah.x + ah.z, abh = ah.y + ah.w;
@@ -529,43 +590,19 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       __syncwarp();
     }
 
-    // ---- 8: lane 0 sums over detectors in a fixed order (pairs and floats
-    // only); lanes 0..7 then form one output each in FP64 (a warp-wide FP64
-    // instruction costs the same for one lane or eight)
+    // ---- 8: lane 0 holds the sums; lanes 0..7 then form one output each in
+    // FP64 (a warp-wide FP64 instruction costs the same for one lane or eight)
     if (lane == 0) {
-      dacc Tl = dacc_zero();
-      dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
-      float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_lnd = 0.f;
-      int bad = 0;
-      for (int q = 0; q < K; ++q) {
-        const int k = P.det_order[q];
-        if (W.bad[k]) {
-          bad = 1;
-          continue;
-        }
-        const float4 f0 = W.fin[k][0];
-        dacc_add(Tl, df{f0.x, f0.y});
-        if (GRAD) {
-          const float4 f1 = W.fin[k][1], f2 = W.fin[k][2];
-          dacc_add(gt_t, df{f0.z, f0.w});
-          dacc_add(gt_ra, df{f1.x, f1.y});
-          dacc_add(gt_dec, df{f1.z, f1.w});
-          g_ra += f2.x;
-          g_dec += f2.y;
-          g_psi += f2.z;
-          g_lnd += f2.w;
-        }
-      }
-      const df lnl = dacc_result(Tl);
-      W.out[0] = make_float4(lnl.hi, lnl.lo, 0.f, __int_as_float(bad));
+      const df lnl = dacc_result(tk);
+      W.out[0] = make_float4(lnl.hi, lnl.lo, 0.f, __int_as_float(badk));
       if (GRAD) {
-        const df a = dacc_result(gt_ra), b = dacc_result(gt_dec), t = dacc_result(gt_t);
-        W.out[1] = make_float4(a.hi, a.lo, g_ra, 0.f);
-        W.out[2] = make_float4(b.hi, b.lo, g_dec, 0.f);
-        W.out[3] = make_float4(g_psi, 0.f, 0.f, 0.f);
+        const df a = dacc_result(gk_ra), b = dacc_result(gk_dec), t = dacc_result(gk_t);
+        W.out[1] = make_float4(a.hi, a.lo, gk[0], 0.f);
+        W.out[2] = make_float4(b.hi, b.lo, gk[1], 0.f);
+        W.out[3] = make_float4(gk[2], 0.f, 0.f, 0.f);
         W.out[4] = make_float4(W.gmode.y, 0.f, 0.f, 0.f);
         W.out[5] = make_float4(W.gmode.x, 0.f, 0.f, 0.f);
-        W.out[6] = make_float4(g_lnd, 0.f, 0.f, 0.f);
+        W.out[6] = make_float4(gk[3], 0.f, 0.f, 0.f);
         W.out[7] = make_float4(t.hi, t.lo, 0.f, 0.f);
       }
     }
