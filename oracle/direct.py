@@ -8,8 +8,9 @@ For one draw of the sampled coordinates (ra, dec, incl, t_c) it computes
 
     L_dir = int dphi dpsi dx  p(phi) p(psi) p_x(x) exp[lnL(phi, psi, x)],
 
-and optionally integrates t_c as well (fixed-spacing rule, eq. ap:tfixed, or
-the band-limited full-window rule, eq. ap:tband).
+and optionally integrates t_c as well (fixed-spacing rule, eq. ap:tfixed,
+the band-limited full-window rule, eq. ap:tband, or the peak-local rule,
+eq. ap:tlocal, on the band-limited rule's fine nodes).
 
 following the paper's steps:
 
@@ -112,9 +113,88 @@ def sinc_upsample(coarse, t_up: int):
     return np.tensordot(S, coarse, axes=1)
 
 
+class ProjectionBound:
+    """The envelope of the peak-local rule: an upper bound of ln of the
+    angular-and-distance integrand at one time node.  Per detector k the
+    template is a x F_k Y with a amplitude vector a in C^M; writing y =
+    (Re a, Im a), the data term is y.q_k with q_k = (Re Q_k(t_k), Im Q_k(t_k))
+    and the quadratic term is (1/2) y^T G_k y with G_k the Hessian of
+    (1/4)(a^dag U_k a + Re a^T V_k a).  Every (phi, psi, x) template is one
+    such y per detector, so by Cauchy-Schwarz over the detectors
+    K^2/(2R) <= (1/2) sum_k q_k^T G_k^+ q_k, and since the distance prior
+    integrates to one, int p_x e^{K x - R x^2/2} dx <= e^{K^2/(2R)}: the bound
+    U(t) = (1/2) sum_k q_k^T G_k^+ q_k at the detectors' arrival times.  It is
+    attained at a noise-free injection (the data lie in the template span)."""
+
+    def __init__(self, point: dict):
+        self.point = point
+        K, M = int(point["K"]), int(point["M"])
+        self.Ginv = []
+        for k in range(K):
+            U = np.asarray(point["U"][k], dtype=np.complex128)
+            V = np.asarray(point["V"][k], dtype=np.complex128)
+
+            def quad(y):
+                a = y[:M] + 1j * y[M:]
+                return 0.25 * float(np.real(np.conj(a) @ U @ a + a @ V @ a))
+
+            E = np.eye(2 * M)
+            G = np.empty((2 * M, 2 * M))
+            for i in range(2 * M):
+                G[i, i] = 2.0 * quad(E[i])
+                for j in range(i):
+                    G[i, j] = G[j, i] = quad(E[i] + E[j]) - quad(E[i]) - quad(E[j])
+            self.Ginv.append(np.linalg.pinv(G, rcond=1e-12))
+
+    def __call__(self, ra, dec, tc):
+        P = self.point
+        total = 0.0
+        for k in range(int(P["K"])):
+            from . import delay as _delay, qinterp as _qinterp
+            tk = _delay(P["det_pos"][k], ra, dec, P["gmst"], tc)
+            qv, _, _ = _qinterp(np.asarray(P["Q"][k]), float(P["q_t0"][k]), float(P["q_dt"]), tk)
+            q = np.concatenate([qv.real, qv.imag])
+            total += 0.5 * float(q @ self.Ginv[k] @ q)
+        return total
+
+
+def peak_local_nodes(U, h, c, depth):
+    """The nodes eq. ap:tlocal keeps: every local maximum f of the envelope
+    U (U_f >= U_{f-1} and U_f > U_{f+1}; beyond the ends the neighbour is
+    mirrored) that lies within `depth` nat of the largest (a lower one
+    contributes less than e^-depth of the peak even whole, and its nodes are
+    covered by the remainder bound), its width sigma_t from the three-point
+    curvature, sigma_t^2 = h^2 / (2 U_f - U_{f-1} - U_{f+1}) (U ~ U_f -
+    (t - t_f)^2 / (2 sigma_t^2) near the maximum), and the nodes within
+    c sigma_t of any such maximum (overlapping neighbourhoods merge).
+    Returns (mask, maxima, widths), or None where a maximum is flat (no
+    justified width)."""
+    U = np.asarray(U, dtype=np.float64)
+    n = U.shape[0]
+    if n == 1:
+        return np.ones(1, bool), [0], [np.inf]
+    ext = np.concatenate([[U[1]], U, [U[n - 2]]])
+    tf = np.arange(n) * h
+    keep = np.zeros(n, bool)
+    peaks, widths = [], []
+    top = np.max(U)
+    for f in range(n):
+        l, m, r = ext[f], ext[f + 1], ext[f + 2]
+        if m >= l and m > r and m >= top - depth:
+            curv = 2.0 * m - l - r
+            if not curv > 0.0:
+                return None
+            sig = h / math.sqrt(curv)
+            keep |= np.abs(tf - tf[f]) <= c * sig
+            peaks.append(f)
+            widths.append(sig)
+    return keep, peaks, widths
+
+
 def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
                d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
-               t_up: int = 1):
+               t_up: int = 1, t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10,
+               diag: list | None = None):
     """ln L_dir per draw.  With n_t = 0 the draw's t is used; otherwise t is
     integrated too, by the fixed-spacing rule of eq. ap:tfixed on n_t
     midpoints t_j = t_lo + (j + 1/2) h, h = (t_hi - t_lo)/n_t, with the
@@ -128,7 +208,18 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
     per interval by ``sinc_upsample``, and the angular and distance integrals
     run at each of the n_t t_up fine nodes (weight 1/(n_t t_up)).  The model
     norm does not depend on t at a fixed sky position; it is taken from the
-    first coarse node."""
+    first coarse node.
+
+    With t_local (needs t_up > 1) the peak-local rule of eq. ap:tlocal on the
+    same fine nodes: the envelope bound U_f of every fine node
+    (``ProjectionBound``), the nodes within t_c sigma_t of its maxima
+    (``peak_local_nodes``) integrated as above, and the others bounded:
+    together they add at most ln R = LSE_skipped(U_f) - ln(n_t t_up).  If
+    that bound exceeds t_tol of the kept value, or no justified width or
+    bound exists, every fine node is integrated (the band-limited rule).
+    `diag`, if a list, receives per draw a dict: kept (node mask or None),
+    maxima (node indices), widths (their sigma_t), gap (ln R - kept value),
+    fallback (bool)."""
     pt = OraclePoint(point)
     th = {p: np.asarray(draws[p], dtype=np.float64) for p in PARAMS}
     N = th["ra"].shape[0]
@@ -137,6 +228,7 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
     PS, PH = np.meshgrid(psis, phis, indexing="ij")
     lnw = -math.log(n_phi * n_psi)   # trapezoid weights times the uniform priors
     out = np.empty(N)
+    bound_fn = None
     for i in range(N):
         if n_t > 0:
             h = (t_hi - t_lo) / n_t
@@ -150,12 +242,46 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
             cR = coefs[0][1]
             coefs = [(cK, cR) for cK in sinc_upsample(np.stack([c[0] for c in coefs]), t_up)]
             lnwt = -math.log(n_t * t_up)
-        vals = []
-        for cK, cR in coefs:
+
+        def node_values(cK, cR):
             K = evaluate(cK, PS, PH)
             R = evaluate(cR, PS, PH)
-            vals.append(distance_gh(K, R, point["d_ref"], d_min, d_max, n_gh) + lnw + lnwt)
-        v = np.concatenate([x.ravel() for x in vals])
-        m = np.max(v)
-        out[i] = m + math.log(np.sum(np.exp(v - m))) if m > -np.inf else -np.inf
+            return (distance_gh(K, R, point["d_ref"], d_min, d_max, n_gh) + lnw + lnwt).ravel()
+
+        def lse(v):
+            m = np.max(v) if v.size else -np.inf
+            return m + math.log(np.sum(np.exp(v - m))) if m > -np.inf else -np.inf
+
+        keep, maxima, widths = None, [], []
+        if t_local and n_t > 0 and t_up > 1:
+            if bound_fn is None:
+                bound_fn = ProjectionBound(point)
+            hf = (t_hi - t_lo) / (n_t * t_up)
+            U = [bound_fn(th["ra"][i], th["dec"][i], t_lo + (f + 0.5) * hf)
+                 for f in range(n_t * t_up)]
+            # maxima lower than the largest by more than ln(1/t_tol) + ln(n_f)
+            # cannot matter at the tolerance
+            sel = peak_local_nodes(U, hf, t_c, -math.log(t_tol) + math.log(n_t * t_up))
+            if sel is not None:
+                keep, maxima, widths = sel
+        if keep is None or keep.all():
+            out[i] = lse(np.concatenate([node_values(cK, cR) for cK, cR in coefs]))
+            if diag is not None:
+                diag.append({"kept": keep, "maxima": maxima, "widths": widths, "gap": -np.inf,
+                             "fallback": keep is None})
+            continue
+        kept = lse(np.concatenate([node_values(*coefs[f]) for f in np.flatnonzero(keep)]))
+        bound = lse(np.asarray([U[f] for f in np.flatnonzero(~keep)])) + lnwt
+        if bound - kept > math.log(t_tol):  # the remainder may matter: the full rule
+            rest = lse(np.concatenate([node_values(*coefs[f]) for f in np.flatnonzero(~keep)]))
+            m = max(kept, rest)
+            out[i] = m + math.log(math.exp(kept - m) + math.exp(rest - m))
+            if diag is not None:
+                diag.append({"kept": keep, "maxima": maxima, "widths": widths, "gap": bound - kept,
+                             "fallback": True})
+        else:
+            out[i] = kept
+            if diag is not None:
+                diag.append({"kept": keep, "maxima": maxima, "widths": widths, "gap": bound - kept,
+                             "fallback": False})
     return out

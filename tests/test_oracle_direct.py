@@ -244,3 +244,154 @@ def test_band_limited_offset_mistake_is_caught():
     assert text.count(old) == 1
     mod = _load(text.replace(old, "tf = np.arange(n * t_up) / t_up"), "tband_offset")
     assert _tband_error(mod, 32) > 1e-2
+
+
+# ------------------------------------------------------------- peak-local rule
+
+def _two_injection_point(shift):
+    """The noise-free fine-table point, and the same point whose correlation
+    tables also hold a second, identical signal `shift` table samples later
+    (the tables add as the data do; U and V do not depend on the data)."""
+    point, info = _fine_table_point()
+    Q = np.asarray(point["Q"])
+    Q2 = np.zeros_like(Q)
+    Q2[:, shift:, :] = Q[:, :-shift, :]
+    both = dict(point)
+    both["Q"] = Q + Q2
+    return point, both, info
+
+
+def test_projection_bound_is_attained_at_the_injection_and_bounds_every_template():
+    """The peak-local rule's envelope: U(t) = (1/2) sum_k q_k^T G_k^+ q_k is
+    rho^2/2 at a noise-free injection (the data lie in the template span), and
+    lies above lnL at any (phi, psi, x) and above the angular-and-distance
+    marginal at that time."""
+    point, info = _fine_table_point()
+    tr = info["truth"]
+    B = OD.ProjectionBound(point)
+    assert abs(B(tr["ra"], tr["dec"], tr["t"]) - info["rho2"] / 2) <= 1e-5 * info["rho2"]
+    pt = O.OraclePoint(point)
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        t = tr["t"] + rng.uniform(-2e-3, 2e-3)
+        U = B(tr["ra"], tr["dec"], t)
+        th = {p: np.full(300, tr[p]) for p in W.PARAMS}
+        th["t"][:] = t
+        th["phase"] = rng.uniform(0, 2 * np.pi, 300)
+        th["psi"] = rng.uniform(0, np.pi, 300)
+        th["lnD"] = np.log(100.0) + rng.normal(0, 0.2, 300)
+        assert np.max(O.lnL(pt, th)) <= U + 1e-6 * abs(U)
+        d1 = {p: np.array([tr[p]]) for p in W.PARAMS}
+        one = OD.lnL_direct(point, d1, 32, 16, 16, 50.0, 200.0, 1, t - 1e-7, t + 1e-7)[0]
+        assert one <= U
+
+
+def test_peak_local_rule_matches_the_band_limited_rule():
+    """eq. ap:tlocal on the fine nodes of eq. ap:tband: with the peak well
+    inside a +-32 coarse-sample window, the neighbourhood of +-16 sigma_t keeps
+    under a third of the nodes, the remainder bound is below the tolerance,
+    and the value equals the full band-limited rule within that bound."""
+    point, info = _fine_table_point()
+    tr = info["truth"]
+    d = {p: np.array([tr[p]]) for p in W.PARAMS}
+    h, half = 1.0 / 2048, 32
+    lo, hi = tr["t"] - half * h, tr["t"] + half * h
+    full = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4)[0]
+    diag = []
+    loc = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4, t_local=True,
+                        diag=diag)[0]
+    g = diag[0]
+    assert not g["fallback"] and g["gap"] < math.log(1e-10)
+    assert 0.05 < g["kept"].mean() < 0.33
+    # the width against a least-squares parabola through the envelope's seven
+    # nodes about the maximum (U ~ U0 - (t - t0)^2 / (2 sigma_t^2))
+    B = OD.ProjectionBound(point)
+    hf = h / 4
+    f0 = g["maxima"][int(np.argmax([B(tr["ra"], tr["dec"], lo + (f + 0.5) * hf)
+                                    for f in g["maxima"]]))]
+    fs = np.arange(f0 - 3, f0 + 4)
+    Us = [B(tr["ra"], tr["dec"], lo + (f + 0.5) * hf) for f in fs]
+    a = np.polyfit((fs - f0) * hf, Us, 2)[0]
+    sig_fit = 1.0 / math.sqrt(-2.0 * a)
+    sig_rule = g["widths"][g["maxima"].index(f0)]
+    assert abs(sig_rule / sig_fit - 1.0) < 0.1, (sig_rule, sig_fit)
+    assert abs(loc - full) <= 2 * math.exp(g["gap"]) + 1e-13 * abs(full)
+    # the neighbourhood holds the injection's node
+    tf = lo + (np.arange(8 * half) + 0.5) * h / 4
+    assert g["kept"][np.argmin(np.abs(tf - tr["t"]))]
+    # a tolerance no bound can meet falls back to the band-limited rule itself
+    diag = []
+    fb = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4, t_local=True,
+                       t_tol=1e-300, diag=diag)[0]
+    assert diag[0]["fallback"] and fb == full
+
+
+def test_peak_local_rule_keeps_both_peaks_of_two_injections():
+    """Two identical signals 300 table samples (18.3 ms) apart: the envelope
+    has two maxima of equal height, both neighbourhoods are kept and the
+    stretch between them is not, and (at a tolerance of 1e-8) the value equals
+    the band-limited rule within the remainder bound."""
+    shift = 300
+    dts = shift * float(np.asarray(_fine_table_point()[0]["q_dt"]))
+    point, both, info = _two_injection_point(shift)
+    tr = info["truth"]
+    d = {p: np.array([tr[p]]) for p in W.PARAMS}
+    h, half = 1.0 / 2048, 48
+    lo, hi = tr["t"] - half * h + dts / 2, tr["t"] + half * h + dts / 2
+    full = OD.lnL_direct(both, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4)[0]
+    diag = []
+    loc = OD.lnL_direct(both, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4, t_local=True,
+                        t_tol=1e-8, diag=diag)[0]
+    g = diag[0]
+    tf = lo + (np.arange(8 * half) + 0.5) * h / 4
+    for t_inj in (tr["t"], tr["t"] + dts):
+        assert g["kept"][np.argmin(np.abs(tf - t_inj))]
+    assert len(g["maxima"]) >= 2
+    assert not g["kept"][np.argmin(np.abs(tf - (tr["t"] + dts / 2)))]
+    assert not g["fallback"] and g["kept"].mean() < 0.35
+    assert abs(loc - full) <= 2 * math.exp(g["gap"]) + 1e-13 * abs(full)
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("bound_half_dropped", "total += 0.5 * float(q @ self.Ginv[k] @ q)",
+     "total += float(q @ self.Ginv[k] @ q)"),
+    ("width_without_root", "sig = h / math.sqrt(curv)", "sig = h / curv"),
+    ("neighbourhood_one_sided", "keep |= np.abs(tf - tf[f]) <= c * sig",
+     "keep |= (tf - tf[f] >= 0) & (tf - tf[f] <= c * sig)"),
+])
+def test_peak_local_planted_mistakes_are_caught(name, old, new):
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, name
+    mod = _load(text.replace(old, new), "tlocal_" + name)
+    failed = False
+    try:
+        point, info = _fine_table_point()
+        tr = info["truth"]
+        B = mod.ProjectionBound(point)
+        if abs(B(tr["ra"], tr["dec"], tr["t"]) - info["rho2"] / 2) > 1e-5 * info["rho2"]:
+            failed = True
+        d = {p: np.array([tr[p]]) for p in W.PARAMS}
+        h, half = 1.0 / 2048, 32
+        lo, hi = tr["t"] - half * h, tr["t"] + half * h
+        diag = []
+        mod.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4, t_local=True,
+                       diag=diag)
+        g = diag[0]
+        tf = lo + (np.arange(8 * half) + 0.5) * h / 4
+        if g["fallback"] or not (0.05 < g["kept"].mean() < 0.33):
+            failed = True
+        else:  # the width against a parabola fit of the correct envelope
+            Bc = OD.ProjectionBound(point)
+            f0 = g["maxima"][0]
+            fs = np.arange(f0 - 3, f0 + 4)
+            Us = [Bc(tr["ra"], tr["dec"], lo + (f + 0.5) * h / 4) for f in fs]
+            sig_fit = 1.0 / math.sqrt(-2.0 * np.polyfit((fs - f0) * h / 4, Us, 2)[0])
+            if abs(g["widths"][0] / sig_fit - 1.0) >= 0.1:
+                failed = True
+            # the neighbourhood must reach 4 coarse samples before the peak
+            if not g["kept"][np.argmin(np.abs(tf - (tr["t"] - 4 * h)))]:
+                failed = True
+    except Exception:
+        failed = True
+    assert failed, f"planted mistake {name} passed every pin"
