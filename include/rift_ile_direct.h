@@ -24,7 +24,8 @@
  * With n_t > 0 the geocentric time is integrated as well, by the
  * fixed-spacing rule of eq. ap:tfixed on the window [t_lo, t_hi] (the draw's
  * t is then ignored); the harmonic model is rebuilt at every time node
- * before any integration, as App. F.1 requires.
+ * before any integration, as App. F.1 requires; or by the band-limited rule
+ * (t_up) or the peak-local rule (t_local) below.
  *
  * The draw's psi, phase and lnD are ignored.  A draw whose distance nodes all
  * fall outside the prior gets -inf.  Ownership and errors as in rift_ile.h;
@@ -68,6 +69,26 @@ typedef struct {
                    * prior-weighted sum sum_i w_i (x_i / x_lo)^-4 runs in
                    * float (relative error ~1e-6, i.e. ~1e-6 in ln L_dir);
                    * needs d_max / d_min <= 1e9. */
+  int32_t t_local; /* 0: off.  1 (needs t_up >= 2, n_t t_up <= 65536): the
+                   * peak-local rule of eq. ap:tlocal on the band-limited
+                   * rule's fine nodes.  Per draw the envelope
+                   * U(t) = 1/2 sum_k |e_k(t_k)|^2 (the data of each detector
+                   * projected on its template span, from the point's whitened
+                   * tables; U bounds the angular-and-distance integrand at t
+                   * by Cauchy-Schwarz and is attained at a noise-free
+                   * injection) is taken at every fine node; its maxima within
+                   * ln(1/t_tol) + ln(n_t t_up) of the largest get a width
+                   * sigma_t^2 = h_f^2 / (2 U_m - U_{m-1} - U_{m+1}) (h_f the
+                   * fine spacing; the end nodes mirror their neighbour); the
+                   * fine nodes within t_c sigma_t of a maximum are integrated,
+                   * the others bounded together by ln R = LSE(U) -
+                   * ln(n_t t_up).  If ln R exceeds ln(t_tol) plus the kept
+                   * value, or a maximum is flat or there are more than 64, every
+                   * fine node is integrated (the band-limited rule).  The
+                   * scratch grows by 12 bytes per fine node and 1 KB per
+                   * resident warp. */
+  double t_c;     /* neighbourhood half-width in units of sigma_t (e.g. 16) */
+  double t_tol;   /* relative tolerance of the skipped remainder, in (0, 1) */
 } rift_ile_direct_rule;
 
 /* ln L_dir per draw into DEVICE out[n] (double). */

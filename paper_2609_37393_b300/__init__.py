@@ -816,7 +816,8 @@ class _DirectRule(ctypes.Structure):
     _fields_ = [("n_phi", ctypes.c_int32), ("n_psi", ctypes.c_int32), ("n_gh", ctypes.c_int32),
                 ("d_min", ctypes.c_double), ("d_max", ctypes.c_double), ("n_t", ctypes.c_int32),
                 ("t_lo", ctypes.c_double), ("t_hi", ctypes.c_double), ("t_up", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("t_local", ctypes.c_int32),
+                ("t_c", ctypes.c_double), ("t_tol", ctypes.c_double)]
 
 
 _lib.rift_ile_lnL_direct.argtypes = [_P, _P, _P, _P, _P]
@@ -833,19 +834,24 @@ def rift_ile_gauss_hermite(n: int):
 
 def rift_ile_lnL_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
                         d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
-                        t_up: int = 0, precision: int = FP64, out=None, stream=None):
+                        t_up: int = 0, precision: int = FP64, out=None, stream=None,
+                        t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10):
     """ln L_dir per draw (float64 CUDA tensor): phase, polarisation and
     distance integrated inside the likelihood (ERAI on an n_phi x n_psi grid,
     adaptive Gauss-Hermite in x); uses each draw's ra, dec, incl and t, or
     with n_t > 0 integrates t over [t_lo, t_hi] on n_t midpoints, or with
-    t_up > 1 on t_up sinc-reconstructed fine nodes per interval (eq. ap:tband).
+    t_up > 1 on t_up sinc-reconstructed fine nodes per interval (eq. ap:tband),
+    with t_local on those nodes by the peak-local rule (eq. ap:tlocal: the
+    neighbourhoods of t_c sigma_t about the envelope's maxima, the rest
+    bounded, the full rule when the bound exceeds t_tol).
     precision=FP32_MIXED takes the prior-weighted distance sum in float."""
     torch = _torch()
     d = _as_draws(draws)
     if out is None:
         out = torch.empty(d.n, dtype=torch.float64, device=point.device)
     r = _DirectRule(int(n_phi), int(n_psi), int(n_gh), float(d_min), float(d_max), int(n_t),
-                    float(t_lo), float(t_hi), int(t_up), int(precision))
+                    float(t_lo), float(t_hi), int(t_up), int(precision), int(bool(t_local)),
+                    float(t_c), float(t_tol))
     _check(_lib.rift_ile_lnL_direct(point.handle, d.ref, ctypes.byref(r),
                                     out.data_ptr() if d.n else None, _stream(stream)))
     return out
@@ -894,7 +900,8 @@ _lib.rift_ile_lnZ_direct_state.argtypes = [_P, _P, _P, _P, _P, _P]
 
 def rift_ile_lnZ_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
                         d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
-                        t_up: int = 0, precision: int = FP64, stream=None):
+                        t_up: int = 0, precision: int = FP64, stream=None,
+                        t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10):
     """(lnZ, sigma_lnZ, n_eff) of the draws with the direct marginal as the
     integrand (the LSE state formed on the device, merged on the host)."""
     torch = _torch()
@@ -902,7 +909,8 @@ def rift_ile_lnZ_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, 
     scratch = torch.empty(max(d.n, 1), dtype=torch.float64, device=point.device)
     state = torch.empty(4, dtype=torch.float64, device=point.device)
     r = _DirectRule(int(n_phi), int(n_psi), int(n_gh), float(d_min), float(d_max), int(n_t),
-                    float(t_lo), float(t_hi), int(t_up), int(precision))
+                    float(t_lo), float(t_hi), int(t_up), int(precision), int(bool(t_local)),
+                    float(t_c), float(t_tol))
     _check(_lib.rift_ile_lnZ_direct_state(point.handle, d.ref, ctypes.byref(r), scratch.data_ptr(),
                                           state.data_ptr(), _stream(stream)))
     return rift_ile_lnZ_merge([tuple(state.cpu().tolist())])[0]

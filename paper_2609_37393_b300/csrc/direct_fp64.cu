@@ -20,8 +20,15 @@
 // n_psi): the skipped nodes together weigh below e^-36 of v0's node.
 // Geocentric time is the draw's own, or integrated over a window: by the
 // fixed-spacing rule (eq. ap:tfixed, the data coefficients formed at every
-// node) or by the band-limited rule (eq. ap:tband, the coefficients formed
-// at coarse nodes and sinc-reconstructed at the fine ones).
+// node), by the band-limited rule (eq. ap:tband, the coefficients formed at
+// coarse nodes and sinc-reconstructed at the fine ones), or by the peak-local
+// rule (eq. ap:tlocal) on those fine nodes: the envelope
+// U(t) = 1/2 sum_k |e_k(t_k)|^2 (the network's data projected on each
+// detector's template span, from the point's interval polynomials; it bounds
+// the angular-and-distance integrand at t by Cauchy-Schwarz), its maxima
+// within ln(1/tol) + ln(n_f) of the largest, widths from the three-point
+// curvature, the fine nodes within c sigma_t of a maximum integrated and the
+// others bounded by LSE(U); above the tolerance every fine node is integrated.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -48,11 +55,17 @@ constexpr int kPsiTab = 256;                // polarisation phases tabulated up 
 constexpr int kColCache = (2 * kMaxModes * kMaxModes * 2) / 5;
 static_assert(5 * kColCache <= 2 * kMaxModes * kMaxModes * 2, "column cache exceeds the pair buffers");
 constexpr double kSkipNat = 36.0;  // plus ln(n_phi n_psi): the skipped mass stays below e^-36
+constexpr int kMaxPeaks = 64;      // maxima the peak-local rule keeps per draw (more: the full rule)
+constexpr int kMaxLocalFine = 1 << 16;  // fine nodes the peak-local rule handles
 
 struct DirectParams {
   int n_phi, n_psi, n_gh, n_t;  // n_t = 0: the draw's own t
   int t_up;                     // > 1: fine nodes per interval (band-limited rule)
   double2* slab;                // band-limited rule: n_t * kHm coefficients per warp
+  // peak-local rule (t_local): per warp, after the coefficients, U[n_f], the
+  // kept flags[n_f] and the maxima (fine index, c sigma_t)[kMaxPeaks]
+  int t_local;
+  double t_c, ln_tol, depth;    // c, ln(tol), ln(1/tol) + ln(n_f)
   double t_lo, t_h;             // time midpoints t_lo + (j + 1/2) t_h
   double lo, hi;          // prior range of x
   double lnnorm;          // ln of 3 d_ref^3 / (d_max^3 - d_min^3)
@@ -70,6 +83,19 @@ struct DirectParams {
   float2 e2f[kPsiTab];    // the same in float, for the first pass
   float2 e4f[kPsiTab];
 };
+
+// Bytes of the band-limited (and peak-local) scratch per warp: the coarse
+// coefficients, then U (padded to an even count), the kept flags (padded to a
+// multiple of four) and the maxima; every part starts on 16 bytes.
+__host__ __device__ inline size_t direct_slab_per_warp(const DirectParams& Q) {
+  size_t b = (size_t)Q.n_t * kHm * sizeof(double2);
+  if (Q.t_local) {
+    const size_t nf = (size_t)Q.n_t * Q.t_up;
+    b += ((nf + 1) & ~(size_t)1) * sizeof(double) + ((nf + 3) & ~(size_t)3) * sizeof(int) +
+         kMaxPeaks * sizeof(double2);
+  }
+  return b;
+}
 
 struct DirCoef {
   double2 c[kHm];
@@ -304,6 +330,29 @@ __device__ double direct_distance(const DirectParams& Q, double K, double R) {
   return K * K / (2.0 * R) + log(h * s) + Q.lnnorm;
 }
 
+// The peak-local rule's envelope at geocentric time t: 1/2 sum_k |e_k(t_k)|^2
+// from the interval polynomials of the point (zero where no tap is in a
+// detector's table).
+template <int MM>
+__device__ double envelope_at(const PointParams& P, const DirDraw<MM>& g, double t) {
+  double u_sum = 0.0;
+  for (int k = 0; k < P.K; ++k) {
+    const double tk = t - (P.pos[k][0] * g.s[0] + P.pos[k][1] * g.s[1] + P.pos[k][2] * g.s[2]);
+    const double u = (tk - P.t0[k]) * P.inv_dt;
+    const double jf = floor(u);
+    if (!(jf >= -2.0 && jf <= (double)P.n)) continue;
+    const double f = u - jf;
+    const float2* pc = P.epoly + ((size_t)k * (P.n + 3) + (size_t)((long long)jf + 2)) * (kPolyDeg + 1);
+    double acc = 0.0;
+    for (int p = kPolyDeg; p >= 0; --p) {
+      const float2 c = __ldg(pc + p);
+      acc = fma(acc, f, (double)c.x + (double)c.y);
+    }
+    u_sum += acc;
+  }
+  return u_sum;
+}
+
 __device__ __forceinline__ void lse_add(double& m, double& s, double v) {
   if (!(v > -CUDART_INF)) return;
   if (v > m) {
@@ -488,7 +537,9 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
       // band-limited rule: the data coefficients at the coarse midpoints
       // (lane h keeps harmonic h), then their sinc sum at each fine midpoint,
       // (t_f - t_j) / h = (2 f + 1 - t_up (2 j + 1)) / (2 t_up)
-      double2* my = Q.slab + (long long)(blockIdx.x * kDirWarps + wid) * Q.n_t * kHm;
+      double2* my = reinterpret_cast<double2*>(reinterpret_cast<char*>(Q.slab) +
+                                               (size_t)(blockIdx.x * kDirWarps + wid) *
+                                                   direct_slab_per_warp(Q));
       for (int jt = 0; jt < Q.n_t; ++jt) {
         direct_data_warp<MM>(P, g, Q.t_lo + (jt + 0.5) * Q.t_h, lane, C, pairbuf[wid][0]);
         if (lane < kHm) my[jt * kHm + lane] = C.c[lane];
@@ -496,7 +547,9 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
       }
       const int nf = Q.n_t * Q.t_up;
       const double inv2u = 1.0 / (2.0 * Q.t_up);
-      for (int f = 0; f < nf; ++f) {
+      // the data coefficients at fine node f by the sinc sum, then the angular
+      // and distance integral there into (m, s)
+      auto fine_node = [&](int f) {
         if (lane < kHm) {
           double2 c = make_double2(0.0, 0.0);
           for (int j = 0; j < Q.n_t; ++j) {
@@ -515,6 +568,93 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
         __syncwarp();
         direct_time_node(C, Q, lane, m, s, nan_seen, reinterpret_cast<double*>(pairbuf[wid]));
         __syncwarp();  // C is rewritten for the next fine node
+      };
+      bool local = Q.t_local != 0;
+      double* U = reinterpret_cast<double*>(my + Q.n_t * kHm);
+      int* kept = reinterpret_cast<int*>(U + ((nf + 1) & ~1));
+      double2* peaks = reinterpret_cast<double2*>(kept + ((nf + 3) & ~3));
+      const double hf = Q.t_h / Q.t_up;
+      if (local) {
+        // eq. ap:tlocal: the envelope, its maxima and their neighbourhoods
+        double top = -CUDART_INF;
+        for (int f = lane; f < nf; f += 32) {
+          const double u = envelope_at<MM>(P, g, Q.t_lo + (f + 0.5) * hf);
+          U[f] = u;
+          top = fmax(top, u);
+        }
+        for (int off = 16; off > 0; off >>= 1) top = fmax(top, __shfl_xor_sync(0xffffffffu, top, off));
+        __syncwarp();
+        int npk = 0;
+        bool flat = false;
+        for (int base = 0; base < nf; base += 32) {
+          const int f = base + lane;
+          bool is_max = false;
+          double csig = 0.0;
+          if (f < nf && nf > 1) {
+            const double um = U[f];
+            const double ul = f > 0 ? U[f - 1] : U[1];
+            const double ur = f < nf - 1 ? U[f + 1] : U[nf - 2];
+            if (um >= ul && um > ur && um >= top - Q.depth) {
+              is_max = true;
+              const double curv = 2.0 * um - ul - ur;
+              if (curv > 0.0) csig = Q.t_c * hf / sqrt(curv);
+              else flat = true;
+            }
+          } else if (f < nf) {  // a single node
+            is_max = true;
+            csig = CUDART_INF;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, is_max);
+          const int rank = __popc(bal & ((1u << lane) - 1u));
+          if (is_max && npk + rank < kMaxPeaks) peaks[npk + rank] = make_double2((double)f, csig);
+          npk += __popc(bal);
+        }
+        flat = __any_sync(0xffffffffu, flat);
+        if (flat || npk > kMaxPeaks) local = false;  // no justified width, or too many maxima
+        __syncwarp();
+        if (local) {
+          int nkept = 0;
+          for (int f = lane; f < nf; f += 32) {
+            int k = 0;
+            for (int q = 0; q < npk && !k; ++q) {
+              const double2 pk = peaks[q];
+              k = fabs(((double)f - pk.x) * hf) <= pk.y;
+            }
+            kept[f] = k;
+            nkept += k;
+          }
+          for (int off = 16; off > 0; off >>= 1) nkept += __shfl_xor_sync(0xffffffffu, nkept, off);
+          if (nkept == nf) local = false;  // nothing to skip: the full rule
+          __syncwarp();
+        }
+      }
+      if (!local) {
+        for (int f = 0; f < nf; ++f) fine_node(f);
+      } else {
+        // the kept neighbourhoods, and the bound of the rest (lane-uniform)
+        double mb = -CUDART_INF, sb = 0.0;
+        for (int f = 0; f < nf; ++f) {
+          if (kept[f]) fine_node(f);
+          else lse_add(mb, sb, U[f]);
+        }
+        // the kept value (a merged copy of the lanes' sums) against the bound
+        double mk = m, sk = s;
+        for (int off = 16; off > 0; off >>= 1) {
+          const double om = __shfl_xor_sync(0xffffffffu, mk, off);
+          const double os = __shfl_xor_sync(0xffffffffu, sk, off);
+          if (om > mk) {
+            sk = fma(sk, exp(mk - om), os);
+            mk = om;
+          } else if (om > -CUDART_INF) {
+            sk = fma(os, exp(om - mk), sk);
+          }
+        }
+        const double vk = mk > -CUDART_INF ? mk + log(sk) + Q.lnw : -CUDART_INF;
+        const double vb = mb + log(sb) - log((double)nf);
+        if (!(vb - vk <= Q.ln_tol)) {  // the remainder may matter: every fine node
+          for (int f = 0; f < nf; ++f)
+            if (!kept[f]) fine_node(f);
+        }
       }
     } else {
       const int nt = Q.n_t > 0 ? Q.n_t : 1;
@@ -553,7 +693,7 @@ cudaError_t launch_direct_mm(const PointParams* dP, const DrawsParams& dp, const
     return cudaGetLastError();
   }
   DirectParams Qb = Q;
-  const size_t bytes = (size_t)blocks * kDirWarps * Q.n_t * kHm * sizeof(double2);
+  const size_t bytes = (size_t)blocks * kDirWarps * direct_slab_per_warp(Q);
   cudaError_t e = cudaMallocAsync((void**)&Qb.slab, bytes, st);
   if (e != cudaSuccess) return e;
   direct_kernel<MM><<<blocks, threads, 0, st>>>(dP, dp, Qb, out);
@@ -673,6 +813,14 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
     rift_ile_set_error("rift_ile_lnL_direct: need 0 < d_min < d_max finite");
     return RIFT_ILE_ERR_INVALID_ARG;
   }
+  if (rule->t_local &&
+      (rule->t_up < 2 || (long long)rule->n_t * rule->t_up > kMaxLocalFine ||
+       !(rule->t_c > 0.0) || !std::isfinite(rule->t_c) || !(rule->t_tol > 0.0) ||
+       !(rule->t_tol < 1.0))) {
+    rift_ile_set_error("rift_ile_lnL_direct: the peak-local rule needs t_up >= 2, n_t t_up <= "
+                       "%d, t_c > 0 finite and 0 < t_tol < 1", kMaxLocalFine);
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
   if (rule->precision != RIFT_ILE_FP64 && rule->precision != RIFT_ILE_FP32_MIXED) {
     rift_ile_set_error("rift_ile_lnL_direct: precision %d unknown", rule->precision);
     return RIFT_ILE_ERR_INVALID_ARG;
@@ -703,6 +851,12 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   Q.t_h = rule->n_t > 0 ? (rule->t_hi - rule->t_lo) / rule->n_t : 0.0;
   Q.t_up = rule->t_up > 1 ? rule->t_up : 1;
   Q.slab = nullptr;
+  Q.t_local = rule->t_local ? 1 : 0;
+  if (Q.t_local) {
+    Q.t_c = rule->t_c;
+    Q.ln_tol = std::log(rule->t_tol);
+    Q.depth = -std::log(rule->t_tol) + std::log((double)Q.n_t * Q.t_up);
+  }
   Q.lnw = -std::log((double)rule->n_phi * rule->n_psi * (rule->n_t > 0 ? rule->n_t : 1) * Q.t_up);
   Q.ln_ub = std::log(std::sqrt(2.0 * M_PI) * norm) - 4.0 * std::log(Q.lo);
   Q.skip_nat = kSkipNat + std::log((double)rule->n_phi * rule->n_psi);

@@ -154,3 +154,84 @@ def test_grids_beyond_the_kernel_tables(R, n_phi, n_psi):
     ref = OD.lnL_direct(point, d, *args)
     _cmp(got, ref)
     assert np.isfinite(got[0])
+
+
+def _fine_point():
+    """Noise-free two-detector point with its table at 16 384 Hz (band to
+    512 Hz), as in the oracle's time-rule pins."""
+    rng = np.random.default_rng(41)
+    dets = W.random_l_detectors(rng, 2)
+    truth = W.default_truth(rng, 100.0)
+    point, exact, info = W.make_point(
+        dets=dets, modes=W.MODES10[:4], f_low=20.0, f_max=512.0, df=0.5, rate=16384.0,
+        half_window=0.03, snr=20.0, truth=truth, gmst=0.4, d_ref=100.0, rng=rng, noise=False,
+        q_dtype=np.complex128)
+    return point, info
+
+
+def _near_truth(info, n, rng):
+    tr = info["truth"]
+    d = {p: np.full(n, tr[p]) for p in W.PARAMS}
+    d["ra"] = d["ra"] + rng.normal(0, 0.01, n)
+    d["dec"] = d["dec"] + rng.normal(0, 0.01, n)
+    d["incl"] = d["incl"] + rng.normal(0, 0.05, n)
+    return d
+
+
+def test_peak_local_time_rule_against_oracle(R):
+    """eq. ap:tlocal on the band-limited fine nodes: GPU against the oracle,
+    every draw within 1e-9 relative; the same value as the band-limited rule
+    within the remainder bound the oracle reports; a tolerance no bound meets
+    gives the band-limited rule itself."""
+    point, info = _fine_point()
+    tr = info["truth"]
+    d = _near_truth(info, 6, np.random.default_rng(4))
+    h, half = 1.0 / 2048, 32
+    lo, hi = tr["t"] - half * h, tr["t"] + half * h
+    pt = R.Point(point)
+    args = (48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4)
+    got = R.rift_ile_lnL_direct(pt, R.Draws(d), *args, t_local=True).cpu().numpy()
+    diag = []
+    ref = OD.lnL_direct(point, d, *args, t_local=True, diag=diag)
+    _cmp(got, ref)
+    assert not any(g["fallback"] for g in diag)
+    band = R.rift_ile_lnL_direct(pt, R.Draws(d), *args).cpu().numpy()
+    for i, g in enumerate(diag):
+        assert abs(got[i] - band[i]) <= 2 * math.exp(g["gap"]) + 1e-12 * abs(band[i])
+    fb = R.rift_ile_lnL_direct(pt, R.Draws(d), *args, t_local=True, t_tol=1e-300).cpu().numpy()
+    assert np.max(np.abs(fb - band) / np.abs(band)) <= 1e-13
+
+
+def test_peak_local_time_rule_two_signals(R):
+    """Two identical signals 300 table samples apart, tolerance 1e-8: both
+    neighbourhoods kept, GPU against the oracle within 1e-9 relative."""
+    point, info = _fine_point()
+    Q = np.asarray(point["Q"])
+    Q2 = np.zeros_like(Q)
+    Q2[:, 300:, :] = Q[:, :-300, :]
+    both = dict(point)
+    both["Q"] = Q + Q2
+    tr = info["truth"]
+    dts = 300 * float(point["q_dt"])
+    d = _near_truth(info, 4, np.random.default_rng(5))
+    h, half = 1.0 / 2048, 48
+    lo, hi = tr["t"] - half * h + dts / 2, tr["t"] + half * h + dts / 2
+    args = (48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4)
+    got = R.rift_ile_lnL_direct(R.Point(both), R.Draws(d), *args, t_local=True,
+                                t_tol=1e-8).cpu().numpy()
+    diag = []
+    ref = OD.lnL_direct(both, d, *args, t_local=True, t_tol=1e-8, diag=diag)
+    _cmp(got, ref)
+    assert all(len(g["maxima"]) >= 2 for g in diag)
+
+
+def test_peak_local_rule_refuses_bad_arguments(R):
+    point, info = _fine_point()
+    pt = R.Point(point)
+    d = _near_truth(info, 1, np.random.default_rng(6))
+    tr = info["truth"]
+    for kw in ({"t_local": True}, {"t_local": True, "t_c": 0.0, "t_up": 4},
+               {"t_local": True, "t_tol": 2.0, "t_up": 4}):
+        args = dict(n_t=16, t_lo=tr["t"] - 1e-3, t_hi=tr["t"] + 1e-3, t_up=kw.pop("t_up", 0))
+        with pytest.raises(R.RiftError):
+            R.rift_ile_lnL_direct(pt, R.Draws(d), 32, 16, 8, 50.0, 200.0, **args, **kw)
