@@ -98,6 +98,36 @@ def distance_gh(K, R, d_ref, d_min, d_max, n_gh):
         return K * K / (2.0 * R) + np.log(math.sqrt(2.0) * sig * s)
 
 
+def mirrored_kernel(z, n):
+    """The reconstruction kernel of the mirrored series: the trigonometric
+    interpolant, of period 2n samples and harmonics |k| <= n - 1,
+    D(z) = (1/2n) sum_{|k|<n} e^{i pi k z / n} = sin((2n-1) pi z/(2n)) /
+    (2n sin(pi z/(2n))), z in units of the coarse spacing."""
+    z = np.asarray(z, dtype=np.float64)
+    den = 2 * n * np.sin(np.pi * z / (2 * n))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v = np.sin((2 * n - 1) * np.pi * z / (2 * n)) / den
+    return np.where(np.abs(den) < 1e-300, (2 * n - 1) / (2 * n), v)
+
+
+def mirrored_upsample(coarse, t_up: int):
+    """The mirrored band-limited reconstruction (the "terminal band-limited,
+    mirrored" option beside eq. ap:tband): the n window samples at the
+    midpoints (j + 1/2) h are extended by their reflection about the window's
+    ends (sample j mirrored to -(j + 1/2) h; the extension of period 2n h is
+    continuous, as the pregrid's reflected series), and the trigonometric
+    interpolant of that series is taken at the t_up fine midpoints of each
+    interval: sum_j value_j [D(t_f - t_j) + D(t_f + t_j)] in units of h.  The
+    reflected series has no Nyquist component, so the kernel omits it.
+    `coarse` is [n, ...]; returns [n t_up, ...]."""
+    coarse = np.asarray(coarse)
+    n = coarse.shape[0]
+    tf = (0.5 + np.arange(n * t_up)) / t_up
+    tj = np.arange(n) + 0.5
+    S = mirrored_kernel(np.subtract.outer(tf, tj), n) + mirrored_kernel(np.add.outer(tf, tj), n)
+    return np.tensordot(S, coarse, axes=1)
+
+
 def sinc_upsample(coarse, t_up: int):
     """The band-limited reconstruction of eq. ap:tband: samples taken at
     spacing h on the midpoints (j + 1/2) h, j < n, are carried to the t_up
@@ -194,7 +224,7 @@ def peak_local_nodes(U, h, c, depth):
 def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
                d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
                t_up: int = 1, t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10,
-               diag: list | None = None):
+               diag: list | None = None, t_mirror: bool = False):
     """ln L_dir per draw.  With n_t = 0 the draw's t is used; otherwise t is
     integrated too, by the fixed-spacing rule of eq. ap:tfixed on n_t
     midpoints t_j = t_lo + (j + 1/2) h, h = (t_hi - t_lo)/n_t, with the
@@ -209,6 +239,9 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
     run at each of the n_t t_up fine nodes (weight 1/(n_t t_up)).  The model
     norm does not depend on t at a fixed sky position; it is taken from the
     first coarse node.
+
+    With t_mirror the fine coefficients come from the mirrored series
+    (``mirrored_upsample``) instead of the truncated sinc sum.
 
     With t_local (needs t_up > 1) the peak-local rule of eq. ap:tlocal on the
     same fine nodes: the envelope bound U_f of every fine node
@@ -240,7 +273,8 @@ def lnL_direct(point: dict, draws, n_phi: int, n_psi: int, n_gh: int, d_min: flo
                  for t in times]
         if n_t > 0 and t_up > 1:
             cR = coefs[0][1]
-            coefs = [(cK, cR) for cK in sinc_upsample(np.stack([c[0] for c in coefs]), t_up)]
+            up = mirrored_upsample if t_mirror else sinc_upsample
+            coefs = [(cK, cR) for cK in up(np.stack([c[0] for c in coefs]), t_up)]
             lnwt = -math.log(n_t * t_up)
 
         def node_values(cK, cR):

@@ -395,3 +395,55 @@ def test_peak_local_planted_mistakes_are_caught(name, old, new):
     except Exception:
         failed = True
     assert failed, f"planted mistake {name} passed every pin"
+
+
+# ------------------------------------------- mirrored band-limited reconstruction
+
+def test_mirrored_reconstruction_is_exact_on_the_reflection_basis_and_equals_the_pregrid():
+    """The mirrored series' trigonometric interpolant reproduces, at every
+    fine midpoint, the series the reflection continues smoothly (sums of
+    cos(pi k (x + 1/2)/n) sampled at the coarse midpoints, k < n), where the
+    truncated sinc sum errs at the window's ends; and it equals the pregrid's
+    FFT route (reflect, zero-pad, invert) at the common points."""
+    import oracle.precompute as OP
+    rng = np.random.default_rng(1)
+    for n, tu in ((12, 4), (33, 2), (7, 8)):
+        a = rng.normal(size=n) + 1j * rng.normal(size=n)
+        ks = np.arange(n)
+        coarse = np.cos(np.pi * np.outer(np.arange(n) + 0.5, ks) / n) @ a
+        tf = (np.arange(n * tu) + 0.5) / tu
+        exact = np.cos(np.pi * np.outer(tf, ks) / n) @ a
+        m = OD.mirrored_upsample(coarse, tu)
+        assert np.max(np.abs(m - exact)) <= 1e-12 * np.sum(np.abs(a))
+        assert np.max(np.abs(OD.sinc_upsample(coarse, tu) - exact)) > 1e-3
+        pg = OP.q_pregrid(coarse[None, :, None], 2 * tu)[0, :, 0]
+        idx = 2 * np.arange(n * tu) + 1 - tu   # offsets from the first sample in h / (2 tu)
+        ok = (idx >= 0) & (idx < pg.shape[0])
+        assert np.max(np.abs(m[ok] - pg[idx[ok]])) <= 1e-12 * np.sum(np.abs(a))
+
+
+def test_mirrored_rule_matches_the_fine_fixed_rule():
+    """With the peak well inside the window, the mirrored band-limited rule
+    agrees with the fixed-spacing rule evaluated directly on its fine nodes,
+    as the truncated one does."""
+    point, info = _fine_table_point()
+    tr = info["truth"]
+    d = {p: np.array([tr[p]]) for p in W.PARAMS}
+    h, half = 1.0 / 2048, 32
+    lo, hi = tr["t"] - half * h, tr["t"] + half * h
+    mir = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4, t_mirror=True)[0]
+    fine = OD.lnL_direct(point, d, 48, 24, 16, 50.0, 200.0, 8 * half, lo, hi)[0]
+    assert abs(mir - fine) <= 2.5e-3, (mir, fine)
+
+
+def test_mirrored_reconstruction_misplaced_mirror_is_caught():
+    with open(SRC) as f:
+        text = f.read()
+    old = "mirrored_kernel(np.add.outer(tf, tj), n)"
+    assert text.count(old) == 1
+    mod = _load(text.replace(old, "mirrored_kernel(np.add.outer(tf, tj - 0.5), n)"), "mirror_shift")
+    n, tu = 12, 4
+    a = np.random.default_rng(2).normal(size=n)
+    coarse = np.cos(np.pi * np.outer(np.arange(n) + 0.5, np.arange(n)) / n) @ a
+    exact = np.cos(np.pi * np.outer((np.arange(n * tu) + 0.5) / tu, np.arange(n)) / n) @ a
+    assert np.max(np.abs(mod.mirrored_upsample(coarse, tu) - exact)) > 1e-3
