@@ -89,6 +89,16 @@ typedef struct {
                    * resident warp. */
   double t_c;     /* neighbourhood half-width in units of sigma_t (e.g. 16) */
   double t_tol;   /* relative tolerance of the skipped remainder, in (0, 1) */
+  int32_t t_mirror; /* 0: the fine coefficients by the truncated sinc sum of
+                   * eq. ap:tband.  1 (needs t_up >= 2): by the mirrored series
+                   * -- the n_t window samples reflected about the window's ends
+                   * (period 2 n_t h, continuous), its trigonometric interpolant
+                   * with harmonics |k| < n_t at the fine midpoints:
+                   * sum_j c(t_j) [D(t_f - t_j) + D(t_f + t_j - 2 t_lo)],
+                   * D(z h) = sin((2 n_t - 1) pi z / (2 n_t)) /
+                   * (2 n_t sin(pi z / (2 n_t))); exact for series the reflection
+                   * continues smoothly, equal to the pregrid construction of
+                   * eq. q-time-pregrid applied to the window. */
 } rift_ile_direct_rule;
 
 /* ln L_dir per draw into DEVICE out[n] (double). */

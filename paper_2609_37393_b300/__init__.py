@@ -817,7 +817,8 @@ class _DirectRule(ctypes.Structure):
                 ("d_min", ctypes.c_double), ("d_max", ctypes.c_double), ("n_t", ctypes.c_int32),
                 ("t_lo", ctypes.c_double), ("t_hi", ctypes.c_double), ("t_up", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("t_local", ctypes.c_int32),
-                ("t_c", ctypes.c_double), ("t_tol", ctypes.c_double)]
+                ("t_c", ctypes.c_double), ("t_tol", ctypes.c_double),
+                ("t_mirror", ctypes.c_int32)]
 
 
 _lib.rift_ile_lnL_direct.argtypes = [_P, _P, _P, _P, _P]
@@ -835,7 +836,8 @@ def rift_ile_gauss_hermite(n: int):
 def rift_ile_lnL_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
                         d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
                         t_up: int = 0, precision: int = FP64, out=None, stream=None,
-                        t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10):
+                        t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10,
+                        t_mirror: bool = False):
     """ln L_dir per draw (float64 CUDA tensor): phase, polarisation and
     distance integrated inside the likelihood (ERAI on an n_phi x n_psi grid,
     adaptive Gauss-Hermite in x); uses each draw's ra, dec, incl and t, or
@@ -843,7 +845,9 @@ def rift_ile_lnL_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, 
     t_up > 1 on t_up sinc-reconstructed fine nodes per interval (eq. ap:tband),
     with t_local on those nodes by the peak-local rule (eq. ap:tlocal: the
     neighbourhoods of t_c sigma_t about the envelope's maxima, the rest
-    bounded, the full rule when the bound exceeds t_tol).
+    bounded, the full rule when the bound exceeds t_tol); t_mirror takes the
+    fine coefficients from the window's mirrored series instead of the
+    truncated sinc sum.
     precision=FP32_MIXED takes the prior-weighted distance sum in float."""
     torch = _torch()
     d = _as_draws(draws)
@@ -851,7 +855,7 @@ def rift_ile_lnL_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, 
         out = torch.empty(d.n, dtype=torch.float64, device=point.device)
     r = _DirectRule(int(n_phi), int(n_psi), int(n_gh), float(d_min), float(d_max), int(n_t),
                     float(t_lo), float(t_hi), int(t_up), int(precision), int(bool(t_local)),
-                    float(t_c), float(t_tol))
+                    float(t_c), float(t_tol), int(bool(t_mirror)))
     _check(_lib.rift_ile_lnL_direct(point.handle, d.ref, ctypes.byref(r),
                                     out.data_ptr() if d.n else None, _stream(stream)))
     return out
@@ -901,7 +905,8 @@ _lib.rift_ile_lnZ_direct_state.argtypes = [_P, _P, _P, _P, _P, _P]
 def rift_ile_lnZ_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, d_min: float,
                         d_max: float, n_t: int = 0, t_lo: float = 0.0, t_hi: float = 0.0,
                         t_up: int = 0, precision: int = FP64, stream=None,
-                        t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10):
+                        t_local: bool = False, t_c: float = 16.0, t_tol: float = 1e-10,
+                        t_mirror: bool = False):
     """(lnZ, sigma_lnZ, n_eff) of the draws with the direct marginal as the
     integrand (the LSE state formed on the device, merged on the host)."""
     torch = _torch()
@@ -910,7 +915,7 @@ def rift_ile_lnZ_direct(point: Point, draws, n_phi: int, n_psi: int, n_gh: int, 
     state = torch.empty(4, dtype=torch.float64, device=point.device)
     r = _DirectRule(int(n_phi), int(n_psi), int(n_gh), float(d_min), float(d_max), int(n_t),
                     float(t_lo), float(t_hi), int(t_up), int(precision), int(bool(t_local)),
-                    float(t_c), float(t_tol))
+                    float(t_c), float(t_tol), int(bool(t_mirror)))
     _check(_lib.rift_ile_lnZ_direct_state(point.handle, d.ref, ctypes.byref(r), scratch.data_ptr(),
                                           state.data_ptr(), _stream(stream)))
     return rift_ile_lnZ_merge([tuple(state.cpu().tolist())])[0]

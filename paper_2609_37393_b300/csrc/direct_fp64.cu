@@ -66,6 +66,7 @@ struct DirectParams {
   // kept flags[n_f] and the maxima (fine index, c sigma_t)[kMaxPeaks]
   int t_local;
   double t_c, ln_tol, depth;    // c, ln(tol), ln(1/tol) + ln(n_f)
+  int t_mirror;                 // fine coefficients from the mirrored series
   double t_lo, t_h;             // time midpoints t_lo + (j + 1/2) t_h
   double lo, hi;          // prior range of x
   double lnnorm;          // ln of 3 d_ref^3 / (d_max^3 - d_min^3)
@@ -554,10 +555,26 @@ __global__ void __launch_bounds__(32 * kDirWarps, RIFT_DIRECT_MIN_BLOCKS) direct
           double2 c = make_double2(0.0, 0.0);
           for (int j = 0; j < Q.n_t; ++j) {
             const long long num = 2LL * f + 1 - (long long)Q.t_up * (2 * j + 1);
-            double w = 1.0;
-            if (num != 0) {
-              const double z = (double)num * inv2u;
-              w = sinpi(z) / (CUDART_PI * z);
+            double w;
+            if (Q.t_mirror) {
+              // the mirrored series: D(t_f - t_j) + D(t_f + t_j) in units of
+              // h, D the interpolant kernel of period 2 n_t with |k| < n_t
+              const long long nump = 2LL * f + 1 + (long long)Q.t_up * (2 * j + 1);
+              const double inv2n = 1.0 / (2.0 * Q.n_t), k2n = 2.0 * Q.n_t - 1.0;
+              double d1 = k2n * inv2n;
+              if (num != 0) {
+                const double z = (double)num * inv2u;
+                d1 = sinpi(k2n * z * inv2n) / (2.0 * Q.n_t * sinpi(z * inv2n));
+              }
+              const double zp = (double)nump * inv2u;
+              const double d2 = sinpi(k2n * zp * inv2n) / (2.0 * Q.n_t * sinpi(zp * inv2n));
+              w = d1 + d2;
+            } else {
+              w = 1.0;
+              if (num != 0) {
+                const double z = (double)num * inv2u;
+                w = sinpi(z) / (CUDART_PI * z);
+              }
             }
             const double2 v = my[j * kHm + lane];
             c.x = fma(w, v.x, c.x);
@@ -813,6 +830,10 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
     rift_ile_set_error("rift_ile_lnL_direct: need 0 < d_min < d_max finite");
     return RIFT_ILE_ERR_INVALID_ARG;
   }
+  if (rule->t_mirror && rule->t_up < 2) {
+    rift_ile_set_error("rift_ile_lnL_direct: the mirrored reconstruction needs t_up >= 2");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
   if (rule->t_local &&
       (rule->t_up < 2 || (long long)rule->n_t * rule->t_up > kMaxLocalFine ||
        !(rule->t_c > 0.0) || !std::isfinite(rule->t_c) || !(rule->t_tol > 0.0) ||
@@ -852,6 +873,7 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   Q.t_up = rule->t_up > 1 ? rule->t_up : 1;
   Q.slab = nullptr;
   Q.t_local = rule->t_local ? 1 : 0;
+  Q.t_mirror = rule->t_mirror ? 1 : 0;
   if (Q.t_local) {
     Q.t_c = rule->t_c;
     Q.ln_tol = std::log(rule->t_tol);

@@ -235,3 +235,24 @@ def test_peak_local_rule_refuses_bad_arguments(R):
         args = dict(n_t=16, t_lo=tr["t"] - 1e-3, t_hi=tr["t"] + 1e-3, t_up=kw.pop("t_up", 0))
         with pytest.raises(R.RiftError):
             R.rift_ile_lnL_direct(pt, R.Draws(d), 32, 16, 8, 50.0, 200.0, **args, **kw)
+
+
+def test_mirrored_band_limited_rule_against_oracle(R):
+    """The mirrored reconstruction of the fine coefficients (alone and under
+    the peak-local rule): GPU against the oracle within 1e-9 relative; with
+    the peak near the window's end the mirrored and truncated values differ."""
+    point, info = _fine_point()
+    tr = info["truth"]
+    d = _near_truth(info, 5, np.random.default_rng(7))
+    h, half = 1.0 / 2048, 16
+    pt = R.Point(point)
+    for shift in (0.0, 12 * h):  # peak centred, and 4 coarse samples from the end
+        lo, hi = tr["t"] - half * h + shift, tr["t"] + half * h + shift
+        args = (48, 24, 16, 50.0, 200.0, 2 * half, lo, hi, 4)
+        got = R.rift_ile_lnL_direct(pt, R.Draws(d), *args, t_mirror=True).cpu().numpy()
+        _cmp(got, OD.lnL_direct(point, d, *args, t_mirror=True))
+        loc = R.rift_ile_lnL_direct(pt, R.Draws(d), *args, t_mirror=True, t_local=True,
+                                    t_tol=1e-8).cpu().numpy()
+        _cmp(loc, OD.lnL_direct(point, d, *args, t_mirror=True, t_local=True, t_tol=1e-8))
+    trunc = R.rift_ile_lnL_direct(pt, R.Draws(d), *args).cpu().numpy()
+    assert np.max(np.abs(trunc - got)) > 1e-6
