@@ -600,10 +600,22 @@ def comp_fp64_fmas(point: dict, na: int) -> int:
     return len(reps) * nblk * 8 * M * M + K * (4 * nblk + 8 * A)
 
 
+def comp_mixed_fp32_ops(K: int, M: int, na: int, R: int, ncls: int) -> int:
+    """FP32 lane operations per draw of the mixed composite kernel's r loop
+    (the bulk of its work): per class, response index, direction and mode
+    pair the a1/a2 sums (12 packed FMAs, 24 lane ops, on the kernel's mode
+    bucket); per class, index and direction the split (6 packed ops); per
+    detector, index and direction the template products (3 packed FMAs); per
+    detector and direction pair the residual over four taps (14 packed ops)."""
+    jp = (4 if M <= 4 else 10 if M <= 10 else 16) // 2
+    return (ncls * na * R * (jp * 24 + 12) + K * na * R * 6 + K * (R // 2) * 28)
+
+
 def run_response(args):
     """The composite-index response (Sec. III) on the 3G network, ten modes,
-    SNR 600: fused FP64 lnL -> LSE steps for Path A (Earth rotation, p_max 0),
-    Path B (p_max 1) and Path D (40 km / 10 km arms, p_max 3)."""
+    SNR 600: fused lnL -> LSE steps for Path A (Earth rotation, p_max 0),
+    Path B (p_max 1) and Path D (40 km / 10 km arms, p_max 3), FP32-mixed
+    (whitened form, rift_ile_comp_mixed_build) and FP64."""
     import torch
     import paper_2609_37393_b300 as R
     import workload.composite as WC
@@ -611,6 +623,7 @@ def run_response(args):
     n = args.draws
     stream = torch.cuda.current_stream()
     fp64_fma, probe_mhz = R.rift_ile_probe_alu(1, 0.2)
+    fp32_fma, _ = R.rift_ile_probe_alu(R.PROBE_FP32_FMA, 0.2)
     rows = []
     head = None
     with ClockSampler(0) as clocks:
@@ -629,10 +642,34 @@ def run_response(args):
             grad = torch.empty((7, n), dtype=torch.float64, device="cuda")
             ms_g = timed_events(torch, lambda: R.rift_ile_comp_lnL_grad(cp, d, lnl, grad), 2,
                                 stream)
+            # the FP32-mixed form: whitening built once per point, then the same steps
+            t0 = time.perf_counter()
+            info_m = R.rift_ile_comp_mixed_build(cp, 1e-14)
+            build_s = time.perf_counter() - t0
+            state_m = torch.empty(4, dtype=torch.float64, device="cuda")
+            step_m = lambda: R.rift_ile_comp_lnZ_state_mixed_async(cp, d, out=state_m)
+            for _ in range(args.warmup):
+                step_m()
+            ms_m = timed_events(torch, step_m, max(3, min(args.steps, 20)), stream)
+            zm = R.rift_ile_lnZ_merge([tuple(state_m.cpu().tolist())])[0]
+            lf = R.rift_ile_comp_lnL(cp, d)
+            lm = R.rift_ile_comp_lnL_mixed(cp, d)
+            near = lf > lf.max() - 50.0
+            ops = comp_mixed_fp32_ops(cp.K, cp.M, cp.na, info_m[0], info_m[2])
             row = {"response": name, "kind": kind, "p_max": p_max, "composite_dim": cp.A,
                    "draws_per_s": n / (ms * 1e-3), "ms_per_step": ms, "lnZ": z[0],
                    "fwd_bwd_draws_per_s": n / (ms_g * 1e-3),
-                   "fp64_fma_per_draw": comp_fp64_fmas(point, cp.na)}
+                   "fp64_fma_per_draw": comp_fp64_fmas(point, cp.na),
+                   "mixed": {"draws_per_s": n / (ms_m * 1e-3), "ms_per_step": ms_m,
+                             "speedup_vs_fp64": ms / ms_m, "lnZ": zm[0],
+                             "abs_dlnZ_vs_fp64": abs(zm[0] - z[0]),
+                             "max_abs_dlnL_within_50nat_vs_fp64":
+                                 float((lm - lf).abs()[near].max()),
+                             "whitened_width": info_m[0], "kept_directions": info_m[1],
+                             "classes": info_m[2], "threads_per_block": info_m[3],
+                             "eig_tol": 1e-14, "build_s": build_s,
+                             "loop_fp32_lane_ops_per_draw": ops,
+                             "fp32_issue_frac": ops * n / (ms_m * 1e-3) / fp32_fma}}
             rows.append(row)
             if head is None:
                 head = row
@@ -650,15 +687,25 @@ def run_response(args):
     err = float(np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))))
     achieved = head["draws_per_s"] * head["fp64_fma_per_draw"]
     line = {
-        "metric": "composite-response lnZ draws/s (FP64), 3G network, Path A",
-        "workload": "response", "value": head["draws_per_s"], "unit": "draws/s", "n_gpus": 1,
-        "draws": n, "dtype": "f64", "data": "synthetic",
+        "metric": "composite-response lnZ draws/s (FP32-mixed), 3G network, Path A",
+        "workload": "response", "value": head["mixed"]["draws_per_s"], "unit": "draws/s",
+        "n_gpus": 1, "draws": n, "dtype": "f32+df (whitened form)", "data": "synthetic",
+        "fp64_draws_per_s": head["draws_per_s"],
+        "speedup_mixed_vs_fp64": head["mixed"]["speedup_vs_fp64"],
         "config": {"workload": "3G network K=4 (ET triangle + CE 40 km), M=10, SNR 600, "
                    "Earth rotation Path A (5 sidereal harmonics, A=50)", "draws": n},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_fma / 1e12,
-                     "unit": "TFMA/s (FP64 pipe)", "frac": achieved / fp64_fma,
-                     "fma_per_draw": head["fp64_fma_per_draw"],
-                     "peak_source": f"measured FP64 FMA rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu)"},
+        "roofline": {"bound": "alu", "kernel": "comp_mixed_kernel (FP32 pipe)",
+                     "achieved": head["mixed"]["loop_fp32_lane_ops_per_draw"]
+                                 * head["mixed"]["draws_per_s"] / 1e12,
+                     "peak": fp32_fma / 1e12, "unit": "T lane-op/s (FP32 pipe)",
+                     "frac": head["mixed"]["fp32_issue_frac"],
+                     "ops_per_draw": head["mixed"]["loop_fp32_lane_ops_per_draw"],
+                     "ops_source": "bench.comp_mixed_fp32_ops (the kernel's r loop, declared)",
+                     "peak_source": "measured FP32 FMA rate (rift_ile_probe_alu)"},
+        "roofline_fp64": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_fma / 1e12,
+                          "unit": "TFMA/s (FP64 pipe)", "frac": achieved / fp64_fma,
+                          "fma_per_draw": head["fp64_fma_per_draw"],
+                          "peak_source": f"measured FP64 FMA rate at {probe_mhz:.0f} MHz (rift_ile_probe_alu)"},
         "rows": rows, "clocks": clocks.summary(),
         "cpu_baseline": {"value": ns / cpu_s, "unit": "draws/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {ns} Path A draws, numpy/C composite oracle"},

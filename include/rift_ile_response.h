@@ -138,6 +138,50 @@ int rift_ile_comp_lnZ_state(const rift_ile_comp* cp, const rift_ile_draws* draws
 int rift_ile_comp_lnZ_state_async(const rift_ile_comp* cp, const rift_ile_draws* draws,
                                   rift_ile_lse* state_out, void* stream);
 
+/* ---- FP32-mixed form (eq. slowrot:lnL:Decomposed in whitened coordinates).
+ *
+ * rift_ile_comp_mixed_build prepares it: for each class of detectors with
+ * identical U, V the real quadratic form G of the term above (over
+ * z = (Re c, Im c), 2 n_comp dimensions) is diagonalised on the host (cyclic
+ * Jacobi), and the eigen-directions with eigenvalue > tol * (the largest) are
+ * kept.  In those coordinates (whitened data e_k(t) = V^T b(t) / s, template
+ * w_k = s V^T z) each detector contributes 1/2 |e_k|^2 - 1/2 |e_k - w_k|^2, the
+ * form of the static FP32-mixed path (rift_ile.h), with
+ *   w_k = sum_a (Re C~^k_a a1_a + Im C~^k_a a2_a), a1_a + i a2_a = B_a conj(Y)
+ * (B_a the whitening's columns of response index a, shared by a class).  The
+ * coefficients, harmonics, arrival times and 1/2|e|^2 are double-float; a1,
+ * a2 and w use error-free split products; the residual e - w is FP32.  The
+ * dropped directions' share of lnL, sum_r (b_r zeta_r - lam_r zeta_r^2 / 2)
+ * over them (zeta_r = x v_r . z, b_r = v_r . b), is left out: it is the part
+ * of the interpolated data outside the bank's numerical span (about 1e-5 nat
+ * within 50 nat of the peak for tol = 1e-14 on a 3G-network SNR-600 point).
+ * The build copies nothing from the caller; it runs on `stream` and
+ * synchronises it; a second call rebuilds with the new tol.
+ * Errors: INVALID_ARG (tol outside (0, 1)), UNSUPPORTED (a form that is not
+ * positive, or has an eigenvalue below -max(tol, 1e-10) * the largest; more
+ * detectors x response indices than shared memory holds), ALLOC, CUDA. */
+int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* stream);
+
+/* out[0] = the whitened width R the kernels use (kept directions padded to
+ * even), out[1] = the largest kept count of a class, out[2] = classes,
+ * out[3] = threads per block; all zero before rift_ile_comp_mixed_build. */
+int rift_ile_comp_mixed_info(const rift_ile_comp* cp, int32_t out[4]);
+
+/* lnL per draw into DEVICE lnL_out[n] (double), FP32-mixed, on `stream`;
+ * draws float32 or float64.  A draw whose arrival time is not finite gets NaN.
+ * Errors: INVALID_ARG (also: the mixed form is not built), SHAPE, CUDA. */
+int rift_ile_comp_lnL_mixed(const rift_ile_comp* cp, const rift_ile_draws* draws, double* lnL_out,
+                            void* stream);
+
+/* LSE state of the draws (fused lnL -> LSE, FP32-mixed lnL, FP64 combine) to
+ * HOST *state; synchronises; out-of-table taps as rift_ile_comp_lnZ_state. */
+int rift_ile_comp_lnZ_state_mixed(const rift_ile_comp* cp, const rift_ile_draws* draws,
+                                  rift_ile_lse* state, void* stream);
+
+/* The same state written to DEVICE state_out without a host synchronisation. */
+int rift_ile_comp_lnZ_state_mixed_async(const rift_ile_comp* cp, const rift_ile_draws* draws,
+                                        rift_ile_lse* state_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -602,6 +602,11 @@ _lib.rift_ile_comp_coeffs.argtypes = [_P, _P, _P, _P]
 _lib.rift_ile_comp_lnL.argtypes = [_P, _P, _P, _P]
 _lib.rift_ile_comp_lnZ_state.argtypes = [_P, _P, _P, _P]
 _lib.rift_ile_comp_lnZ_state_async.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_mixed_build.argtypes = [_P, ctypes.c_double, _P]
+_lib.rift_ile_comp_mixed_info.argtypes = [_P, _P]
+_lib.rift_ile_comp_lnL_mixed.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_lnZ_state_mixed.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_lnZ_state_mixed_async.argtypes = [_P, _P, _P, _P]
 
 
 def rift_ile_comp_n_index(kind: int, p_max: int) -> int:
@@ -721,6 +726,60 @@ def rift_ile_comp_lnZ_state_async(cp: CompPoint, draws, out=None, stream=None):
 def rift_ile_comp_lnZ(cp: CompPoint, draws, stream=None):
     """(lnZ, sigma_lnZ, n_eff) under the composite response."""
     return rift_ile_lnZ_merge([rift_ile_comp_lnZ_state(cp, draws, stream)])[0]
+
+
+def rift_ile_comp_mixed_build(cp: CompPoint, tol: float = 1e-14, stream=None):
+    """Builds the FP32-mixed (whitened) form of a composite point, keeping the
+    eigen-directions of each class's quadratic form above tol x the largest
+    eigenvalue; returns rift_ile_comp_mixed_info."""
+    torch = _torch()
+    with torch.cuda.device(cp.device):
+        _check(_lib.rift_ile_comp_mixed_build(cp.handle, float(tol), _stream(stream)))
+    return rift_ile_comp_mixed_info(cp)
+
+
+def rift_ile_comp_mixed_info(cp: CompPoint):
+    """(R, largest kept count of a class, classes, threads per block) of the
+    mixed form; zeros before it is built."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(_lib.rift_ile_comp_mixed_info(cp.handle, out.ctypes.data))
+    return tuple(int(v) for v in out)
+
+
+def rift_ile_comp_lnL_mixed(cp: CompPoint, draws, out=None, stream=None):
+    """lnL per draw of the composite response (float64 CUDA tensor), FP32-mixed."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(d.n, dtype=torch.float64, device=cp.device)
+    _check(_lib.rift_ile_comp_lnL_mixed(cp.handle, d.ref, out.data_ptr() if d.n else None,
+                                        _stream(stream)))
+    return out
+
+
+def rift_ile_comp_lnZ_state_mixed(cp: CompPoint, draws, stream=None):
+    """LSE state (m, s, s2, n) of the draws, FP32-mixed composite likelihood."""
+    d = _as_draws(draws)
+    st = _Lse()
+    _check(_lib.rift_ile_comp_lnZ_state_mixed(cp.handle, d.ref, ctypes.byref(st),
+                                              _stream(stream)))
+    return (st.m, st.s, st.s2, st.n)
+
+
+def rift_ile_comp_lnZ_state_mixed_async(cp: CompPoint, draws, out=None, stream=None):
+    """The mixed LSE state into a float64 CUDA tensor of 4, no host synchronisation."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=cp.device)
+    _check(_lib.rift_ile_comp_lnZ_state_mixed_async(cp.handle, d.ref, out.data_ptr(),
+                                                    _stream(stream)))
+    return out
+
+
+def rift_ile_comp_lnZ_mixed(cp: CompPoint, draws, stream=None):
+    """(lnZ, sigma_lnZ, n_eff) under the composite response, FP32-mixed."""
+    return rift_ile_lnZ_merge([rift_ile_comp_lnZ_state_mixed(cp, draws, stream)])[0]
 
 
 # ------------------------------------------------------- Q, U, V precompute

@@ -564,6 +564,23 @@ extern "C" int rift_ile_comp_create(const rift_ile_comp_desc* d, rift_ile_comp**
   cp->q = nullptr;
   cp->G = nullptr;
   cudaGetDevice(&cp->device);
+  for (int i = 0; i < M; ++i) {
+    cp->host_ell[i] = d->ell[i];
+    cp->host_em[i] = d->em[i];
+  }
+  // the full real form of each class, kept for the FP32-mixed form's whitening
+  {
+    const size_t D = 2 * (size_t)A;
+    cp->Gfull.assign((size_t)C.ncls * D * D, 0.0);
+    for (int cc = 0; cc < C.ncls; ++cc) {
+      double* Gc = cp->Gfull.data() + (size_t)cc * D * D;
+      for (int pr = 0; pr < 2; ++pr)
+        for (int r = 0; r < A; ++r)
+          for (int pc = 0; pc < 2; ++pc)
+            for (int c = 0; c < A; ++c)
+              Gc[((size_t)pr * A + r) * D + (size_t)pc * A + c] = Gfull(rep[cc], pr, r, pc, c);
+    }
+  }
   const size_t qbytes = (size_t)K * n * A * sizeof(double2);
   cudaError_t e = cudaMalloc((void**)&cp->q, qbytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&cp->G, G.size() * sizeof(double));
@@ -597,6 +614,11 @@ extern "C" int rift_ile_comp_destroy(rift_ile_comp* cp) {
   cudaFree(cp->q);
   cudaFree(cp->G);
   cudaFree(cp->dev_base);
+  cudaFree(cp->mixed_dev);
+  cudaFree(cp->Bs);
+  cudaFree(cp->agrid);
+  cudaFree(cp->ehat);
+  cudaFree(cp->epoly);
   delete cp;
   return RIFT_ILE_OK;
 }

@@ -128,4 +128,64 @@ __device__ __forceinline__ void dacc_add(dacc& acc, df x) {
 
 __device__ __forceinline__ df dacc_result(dacc acc) { return fast_two_sum(acc.s, acc.c); }
 
+// ---- two pairs at once: the packed FP32 instructions of sm_100 and later
+// (FADD2 / FMUL2 / FFMA2, each two operations in one issue slot).  Every
+// component goes through exactly the operations of the scalar functions
+// above, so the results are the same bit for bit.
+struct df2 {
+  float2 hi, lo;  // component 0 is (hi.x, lo.x), component 1 (hi.y, lo.y)
+};
+
+__device__ __forceinline__ df2 df2_make(df a, df b) {
+  return df2{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)};
+}
+__device__ __forceinline__ df df2_x(const df2& a) { return df{a.hi.x, a.lo.x}; }
+__device__ __forceinline__ df df2_y(const df2& a) { return df{a.hi.y, a.lo.y}; }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// a - b rounded once, as a single packed instruction (b (-1) + a)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bb = sub2(s, a);
+  const float2 e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+  return df2{s, e};
+}
+
+__device__ __forceinline__ df2 fast_two_sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return df2{s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ df2 two_prod2(float2 a, float2 b) {
+  const float2 p = __fmul2_rn(a, b);
+  return df2{p, __ffma2_rn(a, b, neg2(p))};
+}
+
+__device__ __forceinline__ df2 df2_neg(const df2& a) { return df2{neg2(a.hi), neg2(a.lo)}; }
+
+__device__ __forceinline__ df2 df_add2(const df2& a, const df2& b) {
+  df2 s = two_sum2(a.hi, b.hi);
+  const df2 t = two_sum2(a.lo, b.lo);
+  s.lo = __fadd2_rn(s.lo, t.hi);
+  s = fast_two_sum2(s.hi, s.lo);
+  s.lo = __fadd2_rn(s.lo, t.lo);
+  return fast_two_sum2(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df2 df_mul2(const df2& a, const df2& b) {
+  df2 p = two_prod2(a.hi, b.hi);
+  p.lo = __ffma2_rn(a.hi, b.lo, p.lo);
+  p.lo = __ffma2_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum2(p.hi, p.lo);
+}
+
+__device__ __forceinline__ df2 df_add_f2(const df2& a, float2 b) {
+  df2 s = two_sum2(a.hi, b);
+  s.lo = __fadd2_rn(s.lo, a.lo);
+  return fast_two_sum2(s.hi, s.lo);
+}
+
 }  // namespace rift

@@ -6,6 +6,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "rift_ile_internal.h"
 
 namespace rift {
@@ -60,6 +62,22 @@ cudaError_t launch_lse_combine(const LseState* partials, int nparts, double n_to
 // Builds the shared-memory image of the FP32-mixed tables of a point (hp
 // complete apart from img); *img is a new device buffer of *nf4 float4.
 int build_mixed_image(const PointParams& hp, float4** img, int* nf4, cudaStream_t st);
+// Host helpers of point.cu shared with the composite response: the cyclic
+// Jacobi eigen-decomposition of a symmetric n x n matrix (row-major, destroyed;
+// eigenvectors in the columns of V), the harmonic's polynomial in cos(iota)
+// (returns its parity), and the (hi, lo) float split of a double.
+void jacobi_eigen(int n, std::vector<double>& a, std::vector<double>& lam, std::vector<double>& V);
+int harmonic_zpoly(int l, int nt, int k0, const double* coef, double* out);
+void split_df(double x, float* hi, float* lo);
+// The whitened tables of K detectors from a complex table Q [K][n][Mq]
+// (complex128 if q_c128, else complex64; device): with the eigenvectors Vt
+// [ncls][2 Mq][2 Mq] (rows, host) and the scales inv_s [K][R] (host; zero for
+// dropped or padding directions), writes ehat [K][n + 2 kEhatPad][R] and the
+// interval polynomials epoly [K][n + 3][7] (device, caller-allocated) and
+// synchronises st.
+int whitened_tables(const void* Q, int q_c128, int K, int n, int Mq, int ncls, const int* cls_of,
+                    const double* Vt, const double* inv_s, int R, float2* ehat, float2* epoly,
+                    cudaStream_t st);
 // SM count of the current device (cached).
 int device_sms();
 // Draw count up to which FP32-mixed lnL and lnL + gradient calls (no

@@ -83,6 +83,8 @@ int harmonic_terms(int l, int mp, int* k0, double* coef) {
   return nt;
 }
 
+}  // namespace
+
 // The Goldberg sum of harmonic_terms rewritten in z = cos(iota): every term
 // c^p s^q (p + q = 2l, p of one parity) is ((1+z)/2)^(p/2) ((1-z)/2)^(q/2)
 // for even p, and sin(iota)/2 times ((1+z)/2)^((p-1)/2) ((1-z)/2)^((q-1)/2)
@@ -153,6 +155,8 @@ void split_df(double x, float* hi, float* lo) {
   *hi = h;
   *lo = (float)(x - (double)h);
 }
+
+namespace {
 
 // proj[k][j][r] = v_r . b_k[j] for every eigen-direction r of detector k's
 // class (FP64), with b = (Re Q[k][j][:], Im Q[k][j][:]).
@@ -341,6 +345,52 @@ int validate(const rift_ile_point_desc* d) {
 
 int harmonic_coefficients(int l, int m, int* k0, double* coef) {
   return harmonic_terms(l, m, k0, coef);
+}
+
+int whitened_tables(const void* Q, int q_c128, int K, int n, int Mq, int ncls, const int* cls_of,
+                    const double* Vt, const double* inv_s, int R, float2* ehat, float2* epoly,
+                    cudaStream_t st) {
+  const int D = 2 * Mq;
+  double *dVt = nullptr, *dproj = nullptr, *dinv_s = nullptr;
+  int* dcls = nullptr;
+  int rc = RIFT_ILE_OK;
+  do {
+    if ((rc = dev_alloc(&dVt, (size_t)ncls * D * D))) break;
+    if ((rc = dev_alloc(&dproj, (size_t)K * n * D))) break;
+    if ((rc = dev_alloc(&dinv_s, (size_t)K * R))) break;
+    if ((rc = dev_alloc(&dcls, (size_t)K))) break;
+    if ((rc = check_cuda(cudaMemcpyAsync(dVt, Vt, (size_t)ncls * D * D * sizeof(double),
+                                         cudaMemcpyHostToDevice, st), "copy of eigenvectors")))
+      break;
+    if ((rc = check_cuda(cudaMemcpyAsync(dinv_s, inv_s, (size_t)K * R * sizeof(double),
+                                         cudaMemcpyHostToDevice, st), "copy of scales")))
+      break;
+    if ((rc = check_cuda(cudaMemcpyAsync(dcls, cls_of, K * sizeof(int), cudaMemcpyHostToDevice, st),
+                         "copy of classes")))
+      break;
+    if ((rc = check_cuda(cudaMemsetAsync(ehat, 0, (size_t)K * (n + 2 * kEhatPad) * R * sizeof(float2),
+                                         st), "table padding")))
+      break;
+    const long long total = (long long)K * n * D;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
+    if (q_c128)
+      project_kernel<double2><<<blocks, 256, 0, st>>>((const double2*)Q, dVt, dcls, K, n, Mq, dproj);
+    else
+      project_kernel<float2><<<blocks, 256, 0, st>>>((const float2*)Q, dVt, dcls, K, n, Mq, dproj);
+    const long long tw = (long long)K * n * R;
+    whiten_kernel<<<(int)std::min<long long>((tw + 255) / 256, 148LL * 16), 256, 0, st>>>(
+        dproj, dinv_s, K, n, D, R, ehat);
+    const long long tp = (long long)K * (n + 3);
+    halfnorm_poly_kernel<<<(int)std::min<long long>((tp + 127) / 128, 148LL * 16), 128, 0, st>>>(
+        dproj, dinv_s, K, n, D, R, epoly);
+    if ((rc = check_cuda(cudaGetLastError(), "whitened table kernels"))) break;
+    rc = check_cuda(cudaStreamSynchronize(st), "whitened tables");
+  } while (0);
+  cudaFree(dVt);
+  cudaFree(dproj);
+  cudaFree(dinv_s);
+  cudaFree(dcls);
+  return rc;
 }
 
 }  // namespace rift
