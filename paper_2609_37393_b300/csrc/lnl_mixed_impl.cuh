@@ -26,6 +26,8 @@
 
 #include <cmath>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -1122,30 +1124,39 @@ __global__ void __launch_bounds__(128) image_kernel(const __grid_constant__ Poin
 }
 
 // Resident blocks per SM of `kern` at `smem` bytes of dynamic shared memory on
-// the current device, with the shared-memory attribute set once per device:
-// both are cached per kernel instantiation, so a launch costs no attribute or
-// occupancy call once a point's shape has been seen.
+// the current device, with the kernel's shared-memory attribute set on first
+// use: both are cached per (kernel, device, block size, shared memory), keyed
+// by the kernel's address (every instantiation of a kernel template has the
+// same function type), so a launch costs no attribute or occupancy call once
+// a point's shape has been seen.
 template <typename KernelT>
 int cached_blocks_per_sm(KernelT kern, int threads, size_t smem) {
+  struct Entry {
+    const void* fn;
+    int dev, threads, nb;
+    size_t smem;
+  };
   static std::mutex mu;
-  static bool attr_set[64] = {false};
-  static size_t last_smem[64] = {0};
-  static int last_nb[64] = {0};
+  static std::vector<Entry> cache;
+  static std::vector<std::pair<const void*, int>> attr_set;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const void* fn = reinterpret_cast<const void*>(kern);
   std::lock_guard<std::mutex> lock(mu);
-  if (!attr_set[dev]) {
+  for (const Entry& e : cache)
+    if (e.fn == fn && e.dev == dev && e.threads == threads && e.smem == smem) return e.nb;
+  bool have_attr = false;
+  for (const auto& a : attr_set) have_attr |= (a.first == fn && a.second == dev);
+  if (!have_attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[dev] = true;
+    attr_set.emplace_back(fn, dev);
   }
-  if (last_nb[dev] == 0 || last_smem[dev] != smem) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess || nb < 1)
-      nb = 1;
-    last_nb[dev] = nb < kMaxPartialsPerSM ? nb : kMaxPartialsPerSM;
-    last_smem[dev] = smem;
-  }
-  return last_nb[dev];
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess || nb < 1)
+    nb = 1;
+  nb = nb < kMaxPartialsPerSM ? nb : kMaxPartialsPerSM;
+  cache.push_back(Entry{fn, dev, threads, nb, smem});
+  return nb;
 }
 
 #include "lnl_warp.cuh"
