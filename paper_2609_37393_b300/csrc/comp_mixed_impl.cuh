@@ -51,6 +51,11 @@ __device__ __forceinline__ cdf cdf_add(const cdf& a, const cdf& b) {
 __device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
 __device__ __forceinline__ df df_half(df a) { return df{0.5f * a.hi, 0.5f * a.lo}; }
 
+// The anchored sine/cosine as a real call: the kernel takes it at up to a
+// dozen sites per draw, and one body keeps its code within the instruction
+// cache.
+__device__ __noinline__ void sincos_df_call(df a, df& s, df& c) { sincos_df(a, s, c); }
+
 // Slot s of this thread (stride: the block size): c / sigma_a (a power of
 // two, so the scaling is exact), and the running largest component.
 __device__ __forceinline__ void slot_put(float4* base, int s, int bd, float isg, const cdf& c,
@@ -75,8 +80,9 @@ struct CompSky {
 // A_-1 = al cos(dec) (r3 - i r4), A_1 = -be cos(dec) (r3 + i r4),
 // A_0 = 2 al be r5 - cos(dec)^2 r6 (r = Dyy - Dxx, 2 Dxy, 2 Dxz, 2 Dyz,
 // Dxx + Dyy, Dzz), and C_(0,n) = e^{2 i psi} A_n e^{i n g}, g = gmst - ra.
-__device__ float rot_coeffs(const CompMixed& C, int k, const CompSky& S, const cdf* G, df f0a,
-                            df f0b, df tk, float4* slot, int bd) {
+__device__ __noinline__ float rot_coeffs(const CompMixed& C, int k, const CompSky& S,
+                                         const cdf* G, df f0a, df f0b, df tk, float4* slot,
+                                         int bd) {
   const float2* rc = C.rc[k];
   const df r1 = df_of(rc[0]), r2 = df_of(rc[1]), r3 = df_of(rc[2]), r4 = df_of(rc[3]);
   const df r5 = df_of(rc[4]), r6 = df_of(rc[5]);
@@ -91,8 +97,20 @@ __device__ float rot_coeffs(const CompMixed& C, int k, const CompSky& S, const c
   C0[2] = cdf_scale(S.xe2p, df_sub(df_mul(f0a, r5), df_mul(f0b, r6)));
   // post-phase step e^{i Omega t_k}
   cdf ep;
-  sincos_df(df_mul(df{C.omega_hi, C.omega_lo}, tk), ep.im, ep.re);
+  sincos_df_call(df_mul(df{C.omega_hi, C.omega_lo}, tk), ep.im, ep.re);
   const cdf epc = cdf_conj(ep);
+  float mx = 0.f;
+  if (C.p_max == 0) {  // Path A: C~_(0,n) = C_(0,n) e^{i n Omega t_k}, n = -2..2
+    const cdf e2 = cdf_mul(ep, ep);
+    const float* isg = C.inv_sigma;
+    const int off = k * C.na;
+    slot_put(slot, off, bd, isg[0], cdf_mul(C0[0], cdf_conj(e2)), mx);
+    slot_put(slot, off + 1, bd, isg[1], cdf_mul(C0[1], epc), mx);
+    slot_put(slot, off + 2, bd, isg[2], C0[2], mx);
+    slot_put(slot, off + 3, bd, isg[3], cdf_mul(C0[3], ep), mx);
+    slot_put(slot, off + 4, bd, isg[4], cdf_mul(C0[4], e2), mx);
+    return mx;
+  }
   // drift harmonics of -(t_k(t) - t_k(0)): with w = (x + i y) e^{i g},
   // E_-1 = cos(dec) conj(w)/2, E_0 = -cos(dec) Re w, E_1 = cos(dec) w/2
   cdf E[3];
@@ -107,7 +125,6 @@ __device__ float rot_coeffs(const CompMixed& C, int k, const CompSky& S, const c
   }
   cdf P[2 * RIFT_ILE_MAX_ROT_PMAX + 1];  // harmonics of (-dt)^p, index m + p
   P[0] = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
-  float mx = 0.f;
   int off = k * C.na;
   for (int p = 0; p <= C.p_max; ++p) {
     if (p > 0) {
@@ -145,7 +162,8 @@ __device__ float rot_coeffs(const CompMixed& C, int k, const CompSky& S, const c
 
 // x b^k_p = x/2 [(X.s)^p (m.X)^2 - (Y.s)^p (m.Y)^2] (eq. fsize:bp), p = 0..p_max,
 // with (m.X)^2 = e^{2 i psi} (e1.X - i e2.X)^2, into slots k na + p.
-__device__ float arm_coeffs(const CompMixed& C, int k, const CompSky& S, float4* slot, int bd) {
+__device__ __noinline__ float arm_coeffs(const CompMixed& C, int k, const CompSky& S,
+                                         float4* slot, int bd) {
   const float2* rc = C.rc[k];
   cdf q[2];
   df u[2];
@@ -195,13 +213,13 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
     df lam = two_sum(ra, -C.gmst_hi);
     lam.lo = __fsub_rn(lam.lo, C.gmst_lo);
     lam = fast_two_sum(lam.hi, lam.lo);
-    sincos_df(lam, S.sl, S.cl);
-    sincos_df(df{dec, 0.f}, S.sd, S.cd);
+    sincos_df_call(lam, S.sl, S.cl);
+    sincos_df_call(df{dec, 0.f}, S.sd, S.cd);
     S.s[0] = df_mul(S.cd, S.cl);
     S.s[1] = df_mul(S.cd, S.sl);
     S.s[2] = S.sd;
     df s2p, c2p;
-    sincos_df(df{2.f * psi, 0.f}, s2p, c2p);
+    sincos_df_call(df{2.f * psi, 0.f}, s2p, c2p);
     S.xe2p = cdf{df_mul(x, c2p), df_mul(x, s2p)};
   }
 
@@ -298,7 +316,7 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
     Yr1[q] = Yi1[q] = Yr2[q] = Yi2[q] = Yrh[q] = Yih[q] = make_float2(0.f, 0.f);
   {
     df sz, z;
-    sincos_df(df{incl, 0.f}, sz, z);
+    sincos_df_call(df{incl, 0.f}, sz, z);
     int prev_am = -1;
     df cm = df{1.f, 0.f}, sm = df{0.f, 0.f}, c1 = df{1.f, 0.f}, s1p = df{0.f, 0.f};
     bool have1 = false;
@@ -313,7 +331,7 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
             sm = df_add(df_mul(sm, c1), df_mul(cm, s1p));
             cm = cn;
           } else {
-            sincos_df(two_prod((float)am, phi), sm, cm);
+            sincos_df_call(two_prod((float)am, phi), sm, cm);
             if (am == 1) {
               c1 = cm;
               s1p = sm;
