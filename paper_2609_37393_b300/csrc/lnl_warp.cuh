@@ -108,6 +108,73 @@ __device__ __forceinline__ df sylm_amp_df_unrolled(const MixedTables& T, int j, 
   return par ? df_mul(acc, sz) : acc;
 }
 
+// Sine and cosine of a double-float angle without a table, for the
+// latency-bound warp kernel (the anchored form waits on a dependent table
+// load): a = 2 pi k + q pi/2 + d with |d| <= pi/4 (the 2 pi and pi/2 products
+// exact or double-float), then sin d = d S(d^2), cos d = C(d^2) by their
+// Taylor series to d^15 and d^16 (truncation < 1e-16 on |d| <= pi/4), the
+// terms of order u^4 and up (u = d^2, each < 3e-6) by FP32 Horner, the four
+// lowest by double-float Horner; absolute error ~1e-14, far below the
+// template's 1e-10 budget.  The quadrant q then swaps and negates.
+__device__ __forceinline__ df horner_df_step(df acc, df u, float ch, float cl) {
+  // acc u + c with the high-part product exact
+  df pr = two_prod(acc.hi, u.hi);
+  pr.lo = fmaf(acc.hi, u.lo, fmaf(acc.lo, u.hi, pr.lo));
+  const df sm = two_sum(pr.hi, ch);
+  return fast_two_sum(sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), cl));
+}
+
+__device__ __forceinline__ void sincos_df_notable(df a, df& s_out, df& c_out) {
+  const float kTwoPiHi = 6.28318548202514648f;
+  const float kTwoPiLo = -1.7484555314695172e-07f;
+  const float kHalfPiHi = 1.57079637050628662f;
+  const float kHalfPiLo = -4.37113900018624283e-08f;
+  const float k = rintf(a.hi * 0.159154943091895336f);
+  df kp = two_prod(k, kTwoPiHi);
+  kp.lo = fmaf(k, kTwoPiLo, kp.lo);
+  const df r = df_add(a, df_neg(kp));
+  const float q = rintf(r.hi * 0.636619772367581343f);  // -2..2
+  const df d = df_add(r, df{-q * kHalfPiHi, -q * kHalfPiLo});  // q pi/2 exact in the pair
+  df u = two_prod(d.hi, d.hi);
+  u.lo = fmaf(2.f * d.hi, d.lo, u.lo);
+  u = fast_two_sum(u.hi, u.lo);
+  // 1/(2j+1)! and 1/(2j)! with alternating signs, as (hi, lo) pairs
+  constexpr double s1 = -1.0 / 6, s2 = 1.0 / 120, s3 = -1.0 / 5040, s4 = 1.0 / 362880,
+                   s5 = -1.0 / 39916800, s6 = 1.0 / 6227020800.0, s7 = -1.0 / 1307674368000.0;
+  constexpr double c1 = -0.5, c2 = 1.0 / 24, c3 = -1.0 / 720, c4 = 1.0 / 40320,
+                   c5 = -1.0 / 3628800, c6 = 1.0 / 479001600, c7 = -1.0 / 87178291200.0,
+                   c8 = 1.0 / 20922789888000.0;
+  const float uh = u.hi;
+  float ts = fmaf(fmaf(fmaf((float)s7, uh, (float)s6), uh, (float)s5), uh, (float)s4);
+  float tc = fmaf(fmaf(fmaf(fmaf((float)c8, uh, (float)c7), uh, (float)c6), uh, (float)c5), uh,
+                  (float)c4);
+  df S = df{ts, 0.f}, Cc = df{tc, 0.f};
+  S = horner_df_step(S, u, (float)s3, (float)(s3 - (double)(float)s3));
+  S = horner_df_step(S, u, (float)s2, (float)(s2 - (double)(float)s2));
+  S = horner_df_step(S, u, (float)s1, (float)(s1 - (double)(float)s1));
+  S = horner_df_step(S, u, 1.f, 0.f);
+  Cc = horner_df_step(Cc, u, (float)c3, (float)(c3 - (double)(float)c3));
+  Cc = horner_df_step(Cc, u, (float)c2, (float)(c2 - (double)(float)c2));
+  Cc = horner_df_step(Cc, u, (float)c1, 0.f);
+  Cc = horner_df_step(Cc, u, 1.f, 0.f);
+  const df sd = df_mul(d, S);
+  // quadrant: (sin, cos) of d + q pi/2
+  const int qi = (int)q & 3;
+  df so = sd, co = Cc;
+  if (qi == 1) {
+    so = Cc;
+    co = df_neg(sd);
+  } else if (qi == 2) {
+    so = df_neg(sd);
+    co = df_neg(Cc);
+  } else if (qi == 3) {
+    so = df_neg(Cc);
+    co = sd;
+  }
+  s_out = so;
+  c_out = co;
+}
+
 // Merge of two compensated accumulators (the sum of their values).
 __device__ __forceinline__ dacc dacc_merge(dacc a, dacc b) {
   const df t = two_sum(a.s, b.s);
@@ -148,8 +215,6 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       reinterpret_cast<WarpScratch<MM, RR>*>(reinterpret_cast<char*>(smem4) + aoff)[warp];
   const int K = P.K, M = P.M, n = P.n, ncls = P.ncls;
   constexpr int NP = RR / 2;  // direction pairs
-  int mmax = 0;
-  for (int j = 0; j < M; ++j) mmax = max(mmax, abs(P.em[j]));
 
   // ---- 1 (a function of the draw): the anchored sines and cosines, and the
   // distance factor; leaves the draw's t_c in tc
@@ -180,8 +245,10 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         a = two_prod((float)(lane - 3), phi);
       }
       df s, c;
-      sincos_df(a, s, c);  // lanes beyond 3 + max|m| take a harmless spare angle
-      if (lane < 4 + mmax) W.ang[lane] = make_float4(s.hi, s.lo, c.hi, c.lo);
+      // lanes 4.. take |m| phi for |m| = lane - 3 (beyond the point's largest
+      // |m| a spare angle; no loop over the modes' constants on this path)
+      sincos_df_notable(a, s, c);
+      if (lane < 16) W.ang[lane] = make_float4(s.hi, s.lo, c.hi, c.lo);
       if (lane == 31) W.x = make_float2(x.hi, x.lo);
     }
     __syncwarp();
