@@ -518,7 +518,8 @@ def run_sampler(args):
     latency through the Python API (eager), replayed from a captured CUDA graph
     (one call per replay), and as 32 calls chained in one graph (the device
     time per call of a sampler loop captured whole), for the warp-per-draw
-    kernel (the default up to 4096 draws) and the one-thread-per-draw kernel."""
+    kernel (two warps per draw; the default up to 2048 draws) and the
+    one-thread-per-draw kernel."""
     import torch
     import paper_2609_37393_b300 as R
     import workload as W
@@ -542,7 +543,8 @@ def run_sampler(args):
         return graph
 
     rows = []
-    default = R.rift_ile_set_small_batch(4096)
+    default = R.rift_ile_set_small_batch(0)  # the library's default, restored below
+    R.rift_ile_set_small_batch(default)
     with ClockSampler(0) as clocks:
         for n in (1, 32, 128, 1024, 4096, 8192, 65536):
             d = R.Draws({p: draws[p][:n] for p in W.PARAMS})

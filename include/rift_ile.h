@@ -293,14 +293,15 @@ int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* d
                        rift_ile_precision prec, double* out, void* stream);
 
 /* Draw count up to which rift_ile_lnL and rift_ile_lnL_grad with
- * RIFT_ILE_FP32_MIXED run the warp-per-draw kernel: the 32 lanes of a warp
- * share one draw (its angles, harmonics, mat-vec rows, detectors and
- * whitened directions), which cuts the latency of a small batch, the regime
- * of a gradient-based extrinsic sampler (App. H of the paper: tens to
- * thousands of draws per call).  Larger batches use the one-thread-per-draw
- * kernels, whose throughput is higher.  The two agree to rounding.  Default
- * 4096; 0 disables the warp kernel.  Process-wide; returns the previous
- * value.  Host only, no GPU call. */
+ * RIFT_ILE_FP32_MIXED run the warp-pair kernel: two warps share one draw
+ * (one takes the sky, the detectors and the sums, the other the harmonics,
+ * the mat-vec and the adjoint's mode terms, each phase across its lanes),
+ * which cuts the latency of a small batch, the regime of a gradient-based
+ * extrinsic sampler (App. H of the paper: tens to thousands of draws per
+ * call).  Larger batches use the one-thread-per-draw kernels, whose
+ * throughput is higher.  The two agree to rounding.  Default 2048; 0
+ * disables the warp kernel.  Process-wide; returns the previous value.  Host
+ * only, no GPU call. */
 int64_t rift_ile_set_small_batch(int64_t max_draws);
 
 /* Number of Q taps that fell outside their tables in the last completed

@@ -39,7 +39,7 @@ template <int MM>
 int mixed_image(const PointParams& hp, float4** img, int* nf4, cudaStream_t st);
 
 namespace {
-std::atomic<long long> g_small_batch_max{4096};
+std::atomic<long long> g_small_batch_max{2048};
 }
 
 long long small_batch_max() { return g_small_batch_max.load(std::memory_order_relaxed); }

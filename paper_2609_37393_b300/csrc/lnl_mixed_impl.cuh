@@ -1167,7 +1167,7 @@ cudaError_t launch_warp_k(const PointParams& hp, const DrawsParams& dp, double* 
   if (hp.R != RR) return cudaErrorInvalidValue;  // tables are padded to RR
   const size_t smem = warp_smem_bytes<MM, RR>(hp.ncls, hp.R, hp.M);
   auto kern = lnl_warp_kernel<MM, RR, GRAD>;
-  const long long need = (dp.n + kWarpDrawWarps - 1) / kWarpDrawWarps;
+  const long long need = (dp.n + kWarpDrawsPerBlock - 1) / kWarpDrawsPerBlock;
   const long long cap = (long long)device_sms() * cached_blocks_per_sm(kern, 32 * kWarpDrawWarps, smem);
   const int blocks = (int)(need < cap ? need : cap);
   kern<<<blocks, 32 * kWarpDrawWarps, smem, st>>>(hp, dp, lnl_out, grad_out);

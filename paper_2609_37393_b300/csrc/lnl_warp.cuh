@@ -1,40 +1,47 @@
-// FP32-mixed lnL and gradient with one warp per draw, for the small batches a
-// gradient-based extrinsic sampler issues (the paper's warm-likelihood regime,
-// App. H): included by lnl_mixed_impl.cuh inside its anonymous namespace, so
-// it shares that file's double-float helpers and anchor tables.
+// FP32-mixed lnL and gradient with two warps per draw, for the small batches
+// a gradient-based extrinsic sampler issues (the paper's warm-likelihood
+// regime, App. H): included by lnl_mixed_impl.cuh inside its anonymous
+// namespace, so it shares that file's double-float helpers.
 //
 // The arithmetic is the one of lnl_mixed_draw (whitened residual, double-float
-// template, packed pairs), rearranged so that the 32 lanes of a warp share one
-// draw.  Every phase runs the same code on all its active lanes (lanes of a
-// warp that take different branches run one after the other), and hands its
-// results to the next phase through the warp's slice of shared memory:
-//   1  lanes 0..3: anchored sine/cosine of ra - gmst, dec, 2 psi, iota;
-//      lanes 4..: of |m| phi for |m| = 1 .. max |m|; one lane the distance factor
-//   2  every lane: the sky direction and x e^{2 i psi}; lanes 0..5 the six
+// template, packed pairs), rearranged so that a pair of warps shares one draw:
+// role 0 takes the sky, the detectors and the sums, role 1 the harmonics, the
+// mat-vec and the adjoint's mode terms, so that the two independent branches
+// after the angles run at once; within a warp each phase runs on its active
+// lanes, and the phases hand their results on through the pair's slice of
+// shared memory, the two warps meeting at named barriers:
+//   1  role 0, lanes 0..3: sine/cosine of ra - gmst, dec, 2 psi, iota (no
+//      table: quadrant reduction and Taylor series in double-float); lanes
+//      4..15: of |m| phi for |m| = 1..12; every lane the distance factor
+//      (the exponential, also without a table)
+//   2  role 0: the sky direction and x e^{2 i psi}; lanes 0..5 the six
 //      products of the sky sines and cosines, lanes 0..9 the ten antenna-basis
 //      terms from them, split for the exact products
-//   3  lane j < M: the harmonic of mode j, split for the exact products;
-//      lane (c, r): row r of the class-c mat-vec a1 = A y, a2 = A J y
-//   4  lane k < K: x F_k, the arrival time and table position (the table rows
-//      of the four taps are prefetched into L1), 1/2 |e|^2 and its slope, the
-//      cubic's weights, the detector's antenna derivatives
-//   5  lane (k, direction pair): the template, the residual over the four
-//      taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
-//   6  lane (c, r): G1_r, G2_r of the class; lane k: the detector's terms of
-//      lnL and of the gradient, summed over the detectors by a fixed shuffle
-//      tree (compensated pairs merged exactly)
-//   7  lane (c, j): the iota and phi_ref derivatives through mode j, summed
-//      over the lanes by a fixed shuffle tree
-//   8  lanes 0..7: the outputs
+//   3  role 1, lane j < M: the harmonic of mode j, split for the exact
+//      products; lane (c, r): row r of the class-c mat-vec a1 = A y, a2 = A J y
+//   4  role 0, lane k < K: x F_k, the arrival time and table position (the
+//      table rows of the four taps are prefetched into L1), 1/2 |e|^2 and its
+//      slope, the cubic's weights, the detector's antenna derivatives
+//      (phases 2 and 4 run while role 1 runs phase 3)
+//   5  role 0, lane (k, direction pair): the template, the residual over the
+//      four taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
+//   6  role 1, lane (c, r): G1_r, G2_r of the class; role 0, lane k: the
+//      detector's terms of lnL and of the gradient, summed over the detectors
+//      by a fixed shuffle tree (compensated pairs merged exactly)
+//   7  role 1, lane (c, j): the iota and phi_ref derivatives through mode j,
+//      summed over the lanes by a fixed shuffle tree (while role 0 runs the
+//      second half of phase 6)
+//   8  role 0, lanes 0..7: the outputs
 // The per-point tables (split whitening, gm1, detector and mode tables) are
 // copied flat from the point's image at block start.
 // Reductions run in fixed orders, so results are reproducible; they differ
 // from the one-thread-per-draw kernel's by rounding only (e^{i |m| phi} is
-// taken by the anchored sine/cosine for every |m| rather than by recurrence,
-// and the direction sums are grouped differently).
+// taken by the sine/cosine for every |m| rather than by recurrence, and the
+// direction sums are grouped differently).
 #pragma once
 
-constexpr int kWarpDrawWarps = 4;  // warps (draws in flight) per block
+constexpr int kWarpDrawWarps = 4;  // warps per block
+constexpr int kWarpDrawsPerBlock = kWarpDrawWarps / 2;  // two warps per draw
 
 template <int MM, int RR>
 struct WarpScratch {
@@ -175,6 +182,40 @@ __device__ __forceinline__ void sincos_df_notable(df a, df& s_out, df& c_out) {
   c_out = co;
 }
 
+// e^a for a double-float a without a table: a = k ln2 + r, |r| <= ln2/2 (k ln2
+// as a pair), e^r by its Taylor series to r^13 (truncation < 2e-16), the terms
+// of order r^5 and up by FP32 Horner, the five lowest by double-float Horner;
+// then the exact scaling by 2^k.  Relative error ~1e-14.
+__device__ __forceinline__ df exp_df_notable(df a) {
+  const float kLn2Hi = 0.693147182464599609f;
+  const float kLn2Lo = -1.904654323148236e-09f;
+  const float k = rintf(a.hi * 1.44269504088896341f);
+  df kp = two_prod(k, kLn2Hi);
+  kp.lo = fmaf(k, kLn2Lo, kp.lo);
+  const df r = df_add(a, df_neg(kp));
+  const float rh = r.hi;
+  constexpr double e5 = 1.0 / 120, e6 = 1.0 / 720, e7 = 1.0 / 5040, e8 = 1.0 / 40320,
+                   e9 = 1.0 / 362880, e10 = 1.0 / 3628800, e11 = 1.0 / 39916800,
+                   e12 = 1.0 / 479001600, e13 = 1.0 / 6227020800.0;
+  constexpr double e2 = 0.5, e3 = 1.0 / 6, e4 = 1.0 / 24;
+  float t = fmaf((float)e13, rh, (float)e12);
+  t = fmaf(t, rh, (float)e11);
+  t = fmaf(t, rh, (float)e10);
+  t = fmaf(t, rh, (float)e9);
+  t = fmaf(t, rh, (float)e8);
+  t = fmaf(t, rh, (float)e7);
+  t = fmaf(t, rh, (float)e6);
+  t = fmaf(t, rh, (float)e5);
+  df E = df{t, 0.f};
+  E = horner_df_step(E, r, (float)e4, (float)(e4 - (double)(float)e4));
+  E = horner_df_step(E, r, (float)e3, (float)(e3 - (double)(float)e3));
+  E = horner_df_step(E, r, (float)e2, 0.f);
+  E = horner_df_step(E, r, 1.f, 0.f);
+  E = horner_df_step(E, r, 1.f, 0.f);
+  const int ki = (int)k;
+  return df{ldexpf(E.hi, ki), ldexpf(E.lo, ki)};
+}
+
 // Merge of two compensated accumulators (the sum of their values).
 __device__ __forceinline__ dacc dacc_merge(dacc a, dacc b) {
   const df t = two_sum(a.s, b.s);
@@ -185,7 +226,7 @@ template <int MM, int RR>
 __host__ __device__ inline size_t warp_smem_bytes(int ncls, int R, int M) {
   // the point's image (split whitening, gm1, staged tables), then one
   // scratch slice per warp
-  return image_bytes(ncls, R, M) + (size_t)kWarpDrawWarps * sizeof(WarpScratch<MM, RR>);
+  return image_bytes(ncls, R, M) + (size_t)kWarpDrawsPerBlock * sizeof(WarpScratch<MM, RR>);
 }
 
 template <int MM, int RR, bool GRAD>
@@ -210,13 +251,18 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
   const MixedTables& T = *reinterpret_cast<const MixedTables*>(
       reinterpret_cast<const char*>(smem4) + split_a_bytes(P.ncls, P.R, P.M));
   const size_t aoff = (size_t)P.img_f4 * 16;
+  // two warps per draw: role 0 takes the sky, the detectors and the sums, role
+  // 1 the harmonics, the mat-vec and the mode terms of the adjoint; the pair
+  // meets at named barriers (id 1 + pair, 64 threads)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = warp >> 1, role = warp & 1;
   WarpScratch<MM, RR>& W =
-      reinterpret_cast<WarpScratch<MM, RR>*>(reinterpret_cast<char*>(smem4) + aoff)[warp];
+      reinterpret_cast<WarpScratch<MM, RR>*>(reinterpret_cast<char*>(smem4) + aoff)[pair];
+  auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory"); };
   const int K = P.K, M = P.M, n = P.n, ncls = P.ncls;
   constexpr int NP = RR / 2;  // direction pairs
 
-  // ---- 1 (a function of the draw): the anchored sines and cosines, and the
+  // ---- 1 (a function of the draw): the sines and cosines, and the
   // distance factor; leaves the draw's t_c in tc
   df tc;
   auto angles = [&](long long i) {
@@ -225,10 +271,10 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     const float phi = load_param_f(dp, 4, i), lnD = load_param_f(dp, 5, i);
     tc = load_param_df(dp, 6, i);
     // every lane takes the exponential in the same instruction stream as its
-    // sine and cosine, so the two anchor-table reads are in flight together
+    // sine and cosine (both without tables: no dependent load)
     df lx = two_sum(P.ln_dref_hi, -lnD);
     lx.lo = __fadd_rn(lx.lo, P.ln_dref_lo);
-    const df x = exp_df(fast_two_sum(lx.hi, lx.lo));
+    const df x = exp_df_notable(fast_two_sum(lx.hi, lx.lo));
     {
       df a;
       if (lane == 0) {
@@ -254,14 +300,17 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     __syncwarp();
   };
 
-  const long long i0 = blockIdx.x * (long long)kWarpDrawWarps + warp;
-  const long long stride = (long long)gridDim.x * kWarpDrawWarps;
-  if (i0 < dp.n) angles(i0);  // uniform over the warp
+  const long long i0 = blockIdx.x * (long long)kWarpDrawsPerBlock + pair;
+  const long long stride = (long long)gridDim.x * kWarpDrawsPerBlock;
+  if (i0 < dp.n && role == 0) angles(i0);  // uniform over the warp
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 
   for (long long i = i0; i < dp.n; i += stride) {
-    if (i != i0) angles(i);
+    if (i != i0) {
+      if (role == 0) angles(i);
+      pair_sync();
+    }
 
     // ---- 2: sky direction, antenna basis (every lane), x e^{2 i psi}
     const float4 a0 = W.ang[0], a1v = W.ang[1], a2v = W.ang[2], a3v = W.ang[3];
@@ -270,274 +319,284 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     const df x{W.x.x, W.x.y};
     const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
     const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
-    // the antenna basis: six products on lanes 0..5, ten terms on lanes 0..9
-    if (lane < 6) {
-      // (sl, sl), (cl, cl), (sl, cl), (sd, sd), (sd, cd), (cd, cd)
-      const df u = lane < 2 ? (lane == 0 ? sl : cl) : lane == 2 ? sl : lane == 5 ? cd : sd;
-      const df v = lane == 0 ? sl : lane < 3 ? cl : lane == 3 ? sd : cd;
-      const df pr = df_mul(u, v);
-      W.base[4 + lane] = make_float2(pr.hi, pr.lo);
-    } else if (lane < 10) {
-      const df b = lane == 6 ? sl : lane == 7 ? cl : lane == 8 ? sd : cd;
-      W.base[lane - 6] = make_float2(b.hi, b.lo);
-    } else if (lane == 10) {
-      W.base[10] = make_float2(1.f, 0.f);
-      W.base[11] = make_float2(0.f, 0.f);
-    }
-    __syncwarp();
-    if (lane < 10) {
-      const unsigned code = s_basis[lane];
-      const int X = (int)(code & 15u), Y = (int)((code >> 4) & 15u);
-      const int Z = (int)((code >> 8) & 15u), Wd = (int)((code >> 12) & 15u);
-      const float sig = (float)((int)((code >> 16) & 15u) - 1);
-      const float kap = (float)((int)((code >> 20) & 15u) - 2);
-      const float2 bx = W.base[X], by = W.base[Y], bz = W.base[Z], bw = W.base[Wd];
-      const df p1 = df_mul(df{bx.x, bx.y}, df{by.x, by.y});
-      const df p2 = df_mul(df{bz.x, bz.y}, df{bw.x, bw.y});
-      const df q = df_add(p1, df{sig * p2.hi, sig * p2.lo});
-      // kappa is 0, +-1 or +-2: the scaling is exact; then the split of
-      // split_antenna_basis (head on the 2^-8 grid, tail = rest + low part)
-      const float qh = kap * q.hi, ql = kap * q.lo;
-      const float h = head_of(qh, 49152.0f);
-      W.bs[lane] = make_float2(h, __fadd_rn(__fsub_rn(qh, h), ql));
-    }
-
-    // ---- 3a: lane j < M: the harmonic of mode j (visiting order), split
-    if (lane < M) {
-      const int4 md = T.mode[lane];  // (mode index, m, l, ypar)
-      const int m = md.y, am = m < 0 ? -m : m;
-      df cm{1.f, 0.f}, sm{0.f, 0.f};
-      if (am > 0) {
-        const float4 e = W.ang[3 + am];
-        sm = df{e.x, e.y};
-        cm = df{e.z, e.w};
+    if (role == 0) {
+      // the antenna basis: six products on lanes 0..5, ten terms on lanes 0..9
+      if (lane < 6) {
+        // (sl, sl), (cl, cl), (sl, cl), (sd, sd), (sd, cd), (cd, cd)
+        const df u = lane < 2 ? (lane == 0 ? sl : cl) : lane == 2 ? sl : lane == 5 ? cd : sd;
+        const df v = lane == 0 ? sl : lane < 3 ? cl : lane == 3 ? sd : cd;
+        const df pr = df_mul(u, v);
+        W.base[4 + lane] = make_float2(pr.hi, pr.lo);
+      } else if (lane < 10) {
+        const df b = lane == 6 ? sl : lane == 7 ? cl : lane == 8 ? sd : cd;
+        W.base[lane - 6] = make_float2(b.hi, b.lo);
+      } else if (lane == 10) {
+        W.base[10] = make_float2(1.f, 0.f);
+        W.base[11] = make_float2(0.f, 0.f);
       }
-      const df amp = sylm_amp_df_unrolled(T, lane, md.z, md.w, z, sz);
-      const df yr = df_mul(amp, cm);
-      const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
-      float yr1, yr2, yi1, yi2;
-      split_y(yr.hi, yr1, yr2);
-      split_y(yi.hi, yi1, yi2);
-      W.ys[lane] = make_float4(yr1, __fadd_rn(yr2, yr.lo), yi1, __fadd_rn(yi2, yi.lo));
-      W.yh[lane] = make_float2(yr.hi, yi.hi);
-    }
-    __syncwarp();
-    // ---- 3b: lane (c, r): row r of class c's mat-vec, packed as in the per-thread kernel
-    for (int it = lane; it < ncls * RR; it += 32) {
-      const int c = it / RR, r = it - c * RR;
-      const float4* Ac = sA + (size_t)c * RR * M * 2;
-      float2 ex = make_float2(0.f, 0.f), co = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < MM; ++j) {
-        if (j >= M) break;
-        const float4 y = W.ys[j];
-        const float2 yh = W.yh[j];
-        const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
-        ex = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.x, y.x), ex);
-        ex = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.z, y.z), ex);
-        co = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.y, y.y), co);
-        co = __ffma2_rn(make_float2(ap.z, ap.w), make_float2(yh.x, yh.x), co);
-        co = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.w, y.w), co);
-        co = __ffma2_rn(make_float2(an.z, an.w), make_float2(yh.y, yh.y), co);
+      __syncwarp();
+      if (lane < 10) {
+        const unsigned code = s_basis[lane];
+        const int X = (int)(code & 15u), Y = (int)((code >> 4) & 15u);
+        const int Z = (int)((code >> 8) & 15u), Wd = (int)((code >> 12) & 15u);
+        const float sig = (float)((int)((code >> 16) & 15u) - 1);
+        const float kap = (float)((int)((code >> 20) & 15u) - 2);
+        const float2 bx = W.base[X], by = W.base[Y], bz = W.base[Z], bw = W.base[Wd];
+        const df p1 = df_mul(df{bx.x, bx.y}, df{by.x, by.y});
+        const df p2 = df_mul(df{bz.x, bz.y}, df{bw.x, bw.y});
+        const df q = df_add(p1, df{sig * p2.hi, sig * p2.lo});
+        // kappa is 0, +-1 or +-2: the scaling is exact; then the split of
+        // split_antenna_basis (head on the 2^-8 grid, tail = rest + low part)
+        const float qh = kap * q.hi, ql = kap * q.lo;
+        const float h = head_of(qh, 49152.0f);
+        W.bs[lane] = make_float2(h, __fadd_rn(__fsub_rn(qh, h), ql));
       }
-      const df u = two_sum(ex.x, co.x), v = two_sum(ex.y, co.y);
-      const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
-      const float uh = head_of(u.hi, C), vh = head_of(v.hi, C);
-      W.a12[c][r] = make_float4(uh, __fadd_rn(__fsub_rn(u.hi, uh), u.lo), vh,
-                                __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
     }
 
-    // ---- 4: lane k < K: arrival time and table position first, so that the
-    // interval polynomial's coefficients and the tap rows are in flight while
-    // the antenna factor is formed; then 1/2|e|^2, the weights, the derivatives
-    if (lane < K) {
-      const int k = lane;
-      const float4 ph = T.pos_hi[k], pl = T.pos_lo[k];
-      df delay = df_mul(df{ph.x, pl.x}, s0);
-      delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
-      delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
-      const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
-      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
-      const int bad = isfinite(u.hi) ? 0 : 1;
-      float f = 0.f, jf = 0.f;
-      if (!bad) {
-        jf = floorf(u.hi);
-        if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
-        f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
-      }
-      const bool inpoly = !bad && jf >= -2.f && jf <= (float)n;
-      float2 cf[kPolyDeg + 1];
-      if (inpoly) {
-        const float2* pc =
-            P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
-#pragma unroll
-        for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
-      }
-      const int jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-      {  // the four tap rows (contiguous) into L1 for the residual phase
-        const char* row = reinterpret_cast<const char*>(
-            P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (jck - 1)) * RR);
-        for (int off = 0; off < 4 * RR * 8; off += 128)
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(row + off));
-      }
-      AntennaSplit AS;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        AS.bh[q] = W.bs[q].x;
-        AS.bt[q] = W.bs[q].y;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        AS.gh[q] = W.bs[6 + q].x;
-        AS.gt[q] = W.bs[6 + q].y;
-      }
-      df xFr, xFi;
-      antenna_df(T, k, AS, xer, xei, xFr, xFi);
-      const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
-      const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
-      W.xf[k] = make_float4(xrh, __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo), xih,
-                            __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo));
-      if (GRAD) {
-        AntennaBasisGrad ABG;
-        antenna_basis_grad(sl.hi, cl.hi, sd.hi, cd.hi, ABG);
-        float dfpa = 0.f, dfpd = 0.f, dfxa = 0.f, dfxd = 0.f;
-        float ac[12];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          const float4 a4 = T.ah[k][v], b4 = T.at[k][v];
-          ac[4 * v] = a4.x + b4.x;
-          ac[4 * v + 1] = a4.y + b4.y;
-          ac[4 * v + 2] = a4.z + b4.z;
-          ac[4 * v + 3] = a4.w + b4.w;
+    if (role == 1) {
+      // ---- 3a: lane j < M: the harmonic of mode j (visiting order), split
+      if (lane < M) {
+        const int4 md = T.mode[lane];  // (mode index, m, l, ypar)
+        const int m = md.y, am = m < 0 ? -m : m;
+        df cm{1.f, 0.f}, sm{0.f, 0.f};
+        if (am > 0) {
+          const float4 e = W.ang[3 + am];
+          sm = df{e.x, e.y};
+          cm = df{e.z, e.w};
         }
-#pragma unroll
+        const df amp = sylm_amp_df_unrolled(T, lane, md.z, md.w, z, sz);
+        const df yr = df_mul(amp, cm);
+        const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
+        float yr1, yr2, yi1, yi2;
+        split_y(yr.hi, yr1, yr2);
+        split_y(yi.hi, yi1, yi2);
+        W.ys[lane] = make_float4(yr1, __fadd_rn(yr2, yr.lo), yi1, __fadd_rn(yi2, yi.lo));
+        W.yh[lane] = make_float2(yr.hi, yi.hi);
+      }
+      __syncwarp();
+      // ---- 3b: lane (c, r): row r of class c's mat-vec, packed as in the per-thread kernel
+      for (int it = lane; it < ncls * RR; it += 32) {
+        const int c = it / RR, r = it - c * RR;
+        const float4* Ac = sA + (size_t)c * RR * M * 2;
+        float2 ex = make_float2(0.f, 0.f), co = make_float2(0.f, 0.f);
+  #pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          if (j >= M) break;
+          const float4 y = W.ys[j];
+          const float2 yh = W.yh[j];
+          const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
+          ex = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.x, y.x), ex);
+          ex = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.z, y.z), ex);
+          co = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.y, y.y), co);
+          co = __ffma2_rn(make_float2(ap.z, ap.w), make_float2(yh.x, yh.x), co);
+          co = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.w, y.w), co);
+          co = __ffma2_rn(make_float2(an.z, an.w), make_float2(yh.y, yh.y), co);
+        }
+        const df u = two_sum(ex.x, co.x), v = two_sum(ex.y, co.y);
+        const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
+        const float uh = head_of(u.hi, C), vh = head_of(v.hi, C);
+        W.a12[c][r] = make_float4(uh, __fadd_rn(__fsub_rn(u.hi, uh), u.lo), vh,
+                                  __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
+      }
+    }
+
+    if (role == 0) {
+      // ---- 4: lane k < K: arrival time and table position first, so that the
+      // interval polynomial's coefficients and the tap rows are in flight while
+      // the antenna factor is formed; then 1/2|e|^2, the weights, the derivatives
+      if (lane < K) {
+        const int k = lane;
+        const float4 ph = T.pos_hi[k], pl = T.pos_lo[k];
+        df delay = df_mul(df{ph.x, pl.x}, s0);
+        delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
+        delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
+        const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
+        const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
+        const int bad = isfinite(u.hi) ? 0 : 1;
+        float f = 0.f, jf = 0.f;
+        if (!bad) {
+          jf = floorf(u.hi);
+          if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
+          f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
+        }
+        const bool inpoly = !bad && jf >= -2.f && jf <= (float)n;
+        float2 cf[kPolyDeg + 1];
+        if (inpoly) {
+          const float2* pc =
+              P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
+  #pragma unroll
+          for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
+        }
+        const int jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
+        {  // the four tap rows (contiguous) into L1 for the residual phase
+          const char* row = reinterpret_cast<const char*>(
+              P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (jck - 1)) * RR);
+          for (int off = 0; off < 4 * RR * 8; off += 128)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(row + off));
+        }
+        AntennaSplit AS;
+  #pragma unroll
         for (int q = 0; q < 6; ++q) {
-          dfpa = fmaf(ac[q], ABG.ba[q], dfpa);
-          dfpd = fmaf(ac[q], ABG.bd[q], dfpd);
+          AS.bh[q] = W.bs[q].x;
+          AS.bt[q] = W.bs[q].y;
         }
-#pragma unroll
+  #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          dfxa = fmaf(ac[6 + q], ABG.ga[q], dfxa);
-          dfxd = fmaf(ac[6 + q], ABG.gd[q], dfxd);
+          AS.gh[q] = W.bs[6 + q].x;
+          AS.gt[q] = W.bs[6 + q].y;
         }
-        W.dx[k] = make_float4(dfpa * xer.hi + dfxa * xei.hi, dfpa * xei.hi - dfxa * xer.hi,
-                              dfpd * xer.hi + dfxd * xei.hi, dfpd * xei.hi - dfxd * xer.hi);
-        // ds/d ra = (-cd sl, cd cl, 0), ds/d dec = (-sd cl, -sd sl, cd)
-        W.dk[k] = make_float2(-(ph.x * (-cd.hi * sl.hi) + ph.y * (cd.hi * cl.hi)),
-                              -(ph.x * (-sd.hi * cl.hi) + ph.y * (-sd.hi * sl.hi) + ph.z * cd.hi));
-      }
-      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the
-      // table) and its slope in f, Horner on both as in the per-thread kernel
-      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
-      if (inpoly) {
-        df acc = df{cf[kPolyDeg].x, cf[kPolyDeg].y};
-        df dacc_p = df{0.f, 0.f};
-#pragma unroll
-        for (int p = kPolyDeg - 1; p >= 0; --p) {
-          if (GRAD) {
-            df pr = two_prod(dacc_p.hi, f);
-            pr.lo = fmaf(dacc_p.lo, f, pr.lo);
-            const df sm3 = two_sum(pr.hi, acc.hi);
-            dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
+        df xFr, xFi;
+        antenna_df(T, k, AS, xer, xei, xFr, xFi);
+        const float Cx = head_constant(fmaxf(fabsf(xFr.hi), fabsf(xFi.hi)));
+        const float xrh = head_of(xFr.hi, Cx), xih = head_of(xFi.hi, Cx);
+        W.xf[k] = make_float4(xrh, __fadd_rn(__fsub_rn(xFr.hi, xrh), xFr.lo), xih,
+                              __fadd_rn(__fsub_rn(xFi.hi, xih), xFi.lo));
+        if (GRAD) {
+          AntennaBasisGrad ABG;
+          antenna_basis_grad(sl.hi, cl.hi, sd.hi, cd.hi, ABG);
+          float dfpa = 0.f, dfpd = 0.f, dfxa = 0.f, dfxd = 0.f;
+          float ac[12];
+  #pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            const float4 a4 = T.ah[k][v], b4 = T.at[k][v];
+            ac[4 * v] = a4.x + b4.x;
+            ac[4 * v + 1] = a4.y + b4.y;
+            ac[4 * v + 2] = a4.z + b4.z;
+            ac[4 * v + 3] = a4.w + b4.w;
           }
-          df pr = two_prod(acc.hi, f);
-          pr.lo = fmaf(acc.lo, f, pr.lo);
-          const df sm2 = two_sum(pr.hi, cf[p].x);
-          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf[p].y));
+  #pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            dfpa = fmaf(ac[q], ABG.ba[q], dfpa);
+            dfpd = fmaf(ac[q], ABG.bd[q], dfpd);
+          }
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            dfxa = fmaf(ac[6 + q], ABG.ga[q], dfxa);
+            dfxd = fmaf(ac[6 + q], ABG.gd[q], dfxd);
+          }
+          W.dx[k] = make_float4(dfpa * xer.hi + dfxa * xei.hi, dfpa * xei.hi - dfxa * xer.hi,
+                                dfpd * xer.hi + dfxd * xei.hi, dfpd * xei.hi - dfxd * xer.hi);
+          // ds/d ra = (-cd sl, cd cl, 0), ds/d dec = (-sd cl, -sd sl, cd)
+          W.dk[k] = make_float2(-(ph.x * (-cd.hi * sl.hi) + ph.y * (cd.hi * cl.hi)),
+                                -(ph.x * (-sd.hi * cl.hi) + ph.y * (-sd.hi * sl.hi) + ph.z * cd.hi));
         }
-        half_e2 = acc;
-        dhalf = dacc_p;
+        // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the
+        // table) and its slope in f, Horner on both as in the per-thread kernel
+        df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
+        if (inpoly) {
+          df acc = df{cf[kPolyDeg].x, cf[kPolyDeg].y};
+          df dacc_p = df{0.f, 0.f};
+  #pragma unroll
+          for (int p = kPolyDeg - 1; p >= 0; --p) {
+            if (GRAD) {
+              df pr = two_prod(dacc_p.hi, f);
+              pr.lo = fmaf(dacc_p.lo, f, pr.lo);
+              const df sm3 = two_sum(pr.hi, acc.hi);
+              dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
+            }
+            df pr = two_prod(acc.hi, f);
+            pr.lo = fmaf(acc.lo, f, pr.lo);
+            const df sm2 = two_sum(pr.hi, cf[p].x);
+            acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf[p].y));
+          }
+          half_e2 = acc;
+          dhalf = dacc_p;
+        }
+        const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
+        const float w0 = -(f * fc * fd) * (1.f / 6.f), w1 = (fa * fc * fd) * 0.5f;
+        const float w2 = -(fa * f * fd) * 0.5f, w3 = (fa * f * fc) * (1.f / 6.f);
+        const df ws = df_add(two_sum(w0, w1), two_sum(w2, w3));
+        W.sigma[k] = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
+        W.wt[k] = make_float4(w0, w1, w2, w3);
+        if (GRAD) {
+          W.wtd[k] = make_float4(-(fc * fd + f * fd + f * fc) * (1.f / 6.f),
+                                 (fc * fd + fa * fd + fa * fc) * 0.5f,
+                                 -(f * fd + fa * fd + fa * f) * 0.5f,
+                                 (f * fc + fa * fc + fa * f) * (1.f / 6.f));
+        }
+        W.jc[k] = jck;
+        W.bad[k] = bad;
+        W.he2[k] = make_float2(half_e2.hi, half_e2.lo);
+        W.dhe2[k] = make_float2(dhalf.hi, dhalf.lo);
       }
-      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
-      const float w0 = -(f * fc * fd) * (1.f / 6.f), w1 = (fa * fc * fd) * 0.5f;
-      const float w2 = -(fa * f * fd) * 0.5f, w3 = (fa * f * fc) * (1.f / 6.f);
-      const df ws = df_add(two_sum(w0, w1), two_sum(w2, w3));
-      W.sigma[k] = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
-      W.wt[k] = make_float4(w0, w1, w2, w3);
-      if (GRAD) {
-        W.wtd[k] = make_float4(-(fc * fd + f * fd + f * fc) * (1.f / 6.f),
-                               (fc * fd + fa * fd + fa * fc) * 0.5f,
-                               -(f * fd + fa * fd + fa * f) * 0.5f,
-                               (f * fc + fa * fc + fa * f) * (1.f / 6.f));
-      }
-      W.jc[k] = jck;
-      W.bad[k] = bad;
-      W.he2[k] = make_float2(half_e2.hi, half_e2.lo);
-      W.dhe2[k] = make_float2(dhalf.hi, dhalf.lo);
+      __syncwarp();
     }
-    __syncwarp();
+    pair_sync();  // a12 from role 1, the detectors' tables from role 0
 
-    // ---- 5: lane (k, pair): the residual of two directions (packed, as in
-    // the per-thread kernel's loop body)
-    for (int it = lane; it < K * NP; it += 32) {
-      const int k = it / NP, pr = it - k * NP, r = 2 * pr;
-      if (W.bad[k]) continue;
-      const int c = P.cls_of[k];
-      const float4 xfq = W.xf[k];
-      const float2 nxrh = make_float2(-xfq.x, -xfq.x), nxrt = make_float2(-xfq.y, -xfq.y);
-      const float2 nxih = make_float2(-xfq.z, -xfq.z), nxit = make_float2(-xfq.w, -xfq.w);
-      const float4 qa0 = W.a12[c][r], qa1 = W.a12[c][r + 1];
-      const float2 a1h = make_float2(qa0.x, qa1.x), a1t = make_float2(qa0.y, qa1.y);
-      const float2 a2h = make_float2(qa0.z, qa1.z), a2t = make_float2(qa0.w, qa1.w);
-      float2 nlo = __fmul2_rn(nxrh, a1t);
-      nlo = __ffma2_rn(nxrt, a1h, nlo);
-      nlo = __ffma2_rn(nxrt, a1t, nlo);
-      nlo = __ffma2_rn(nxih, a2t, nlo);
-      nlo = __ffma2_rn(nxit, a2h, nlo);
-      nlo = __ffma2_rn(nxit, a2t, nlo);
-      const float2 nhi = __ffma2_rn(nxrh, a1h, __fmul2_rn(nxih, a2h));
-      const float4 w4 = W.wt[k];
-      const float wtv[4] = {w4.x, w4.y, w4.z, w4.w};
-      float wdv[4] = {0.f, 0.f, 0.f, 0.f};
-      if (GRAD) {
-        const float4 d4 = W.wtd[k];
-        wdv[0] = d4.x;
-        wdv[1] = d4.y;
-        wdv[2] = d4.z;
-        wdv[3] = d4.w;
+    if (role == 0) {
+      // ---- 5: lane (k, pair): the residual of two directions (packed, as in
+      // the per-thread kernel's loop body)
+      for (int it = lane; it < K * NP; it += 32) {
+        const int k = it / NP, pr = it - k * NP, r = 2 * pr;
+        if (W.bad[k]) continue;
+        const int c = P.cls_of[k];
+        const float4 xfq = W.xf[k];
+        const float2 nxrh = make_float2(-xfq.x, -xfq.x), nxrt = make_float2(-xfq.y, -xfq.y);
+        const float2 nxih = make_float2(-xfq.z, -xfq.z), nxit = make_float2(-xfq.w, -xfq.w);
+        const float4 qa0 = W.a12[c][r], qa1 = W.a12[c][r + 1];
+        const float2 a1h = make_float2(qa0.x, qa1.x), a1t = make_float2(qa0.y, qa1.y);
+        const float2 a2h = make_float2(qa0.z, qa1.z), a2t = make_float2(qa0.w, qa1.w);
+        float2 nlo = __fmul2_rn(nxrh, a1t);
+        nlo = __ffma2_rn(nxrt, a1h, nlo);
+        nlo = __ffma2_rn(nxrt, a1t, nlo);
+        nlo = __ffma2_rn(nxih, a2t, nlo);
+        nlo = __ffma2_rn(nxit, a2h, nlo);
+        nlo = __ffma2_rn(nxit, a2t, nlo);
+        const float2 nhi = __ffma2_rn(nxrh, a1h, __fmul2_rn(nxih, a2h));
+        const float4 w4 = W.wt[k];
+        const float wtv[4] = {w4.x, w4.y, w4.z, w4.w};
+        float wdv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (GRAD) {
+          const float4 d4 = W.wtd[k];
+          wdv[0] = d4.x;
+          wdv[1] = d4.y;
+          wdv[2] = d4.z;
+          wdv[3] = d4.w;
+        }
+        const float nsg = -W.sigma[k];
+        const float2* Ej = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * RR +
+                           (ptrdiff_t)(W.jc[k] - 1) * RR;
+        float2 rs = make_float2(0.f, 0.f), ed = make_float2(0.f, 0.f);
+  #pragma unroll
+        for (int tap = 0; tap < 4; ++tap) {
+          const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + tap * RR + r));
+          const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
+                                      make_float2(e4.z, e4.w));
+          rs = __ffma2_rn(make_float2(wtv[tap], wtv[tap]), d, rs);
+          if (tap == 1) rs = __ffma2_rn(make_float2(nsg, nsg), d, rs);
+          if (GRAD) ed = __ffma2_rn(make_float2(wdv[tap], wdv[tap]), d, ed);
+        }
+        const float2 rsv = __fadd2_rn(rs, nlo);
+        const float2 q2 = __fmul2_rn(rsv, rsv);
+        const float2 nwf = __fadd2_rn(nhi, nlo);
+        float2 gm = make_float2(0.f, 0.f), nul = make_float2(0.f, 0.f);
+        const float* gc = sg + c * RR;
+        if (GRAD || P.has_null[c]) {
+          gm = make_float2(gc[r], gc[r + 1]);
+          nul = __fmul2_rn(__fmul2_rn(gm, nwf), nwf);
+        }
+        float4 pt = make_float4(__fadd_rn(q2.x, q2.y), __fadd_rn(nul.x, nul.y), 0.f, 0.f);
+        if (GRAD) {
+          const float2 red = __fmul2_rn(rsv, ed);
+          const float2 rho = __ffma2_rn(make_float2(-gm.x, -gm.y), nwf, rsv);
+          const float2 g1 = __fmul2_rn(rho, __fadd2_rn(a1h, a1t));
+          const float2 g2 = __fmul2_rn(rho, __fadd2_rn(a2h, a2t));
+          pt.z = __fadd_rn(red.x, red.y);
+          pt.w = __fadd_rn(g1.x, g1.y);
+          W.part5[k][pr] = __fadd_rn(g2.x, g2.y);
+          const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
+          W.gp[k][r] = make_float2(xFr * rho.x, xFi * rho.x);
+          W.gp[k][r + 1] = make_float2(xFr * rho.y, xFi * rho.y);
+        }
+        W.part[k][pr] = pt;
       }
-      const float nsg = -W.sigma[k];
-      const float2* Ej = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * RR +
-                         (ptrdiff_t)(W.jc[k] - 1) * RR;
-      float2 rs = make_float2(0.f, 0.f), ed = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int tap = 0; tap < 4; ++tap) {
-        const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + tap * RR + r));
-        const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
-                                    make_float2(e4.z, e4.w));
-        rs = __ffma2_rn(make_float2(wtv[tap], wtv[tap]), d, rs);
-        if (tap == 1) rs = __ffma2_rn(make_float2(nsg, nsg), d, rs);
-        if (GRAD) ed = __ffma2_rn(make_float2(wdv[tap], wdv[tap]), d, ed);
-      }
-      const float2 rsv = __fadd2_rn(rs, nlo);
-      const float2 q2 = __fmul2_rn(rsv, rsv);
-      const float2 nwf = __fadd2_rn(nhi, nlo);
-      float2 gm = make_float2(0.f, 0.f), nul = make_float2(0.f, 0.f);
-      const float* gc = sg + c * RR;
-      if (GRAD || P.has_null[c]) {
-        gm = make_float2(gc[r], gc[r + 1]);
-        nul = __fmul2_rn(__fmul2_rn(gm, nwf), nwf);
-      }
-      float4 pt = make_float4(__fadd_rn(q2.x, q2.y), __fadd_rn(nul.x, nul.y), 0.f, 0.f);
-      if (GRAD) {
-        const float2 red = __fmul2_rn(rsv, ed);
-        const float2 rho = __ffma2_rn(make_float2(-gm.x, -gm.y), nwf, rsv);
-        const float2 g1 = __fmul2_rn(rho, __fadd2_rn(a1h, a1t));
-        const float2 g2 = __fmul2_rn(rho, __fadd2_rn(a2h, a2t));
-        pt.z = __fadd_rn(red.x, red.y);
-        pt.w = __fadd_rn(g1.x, g1.y);
-        W.part5[k][pr] = __fadd_rn(g2.x, g2.y);
-        const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
-        W.gp[k][r] = make_float2(xFr * rho.x, xFi * rho.x);
-        W.gp[k][r + 1] = make_float2(xFr * rho.y, xFi * rho.y);
-      }
-      W.part[k][pr] = pt;
+      __syncwarp();
     }
-    __syncwarp();
+    pair_sync();  // the residual terms
 
-    // ---- 6: lane (c, r): G1_r, G2_r of class c over its detectors in order;
-    // lane k: the detector's terms
-    if (GRAD) {
+    // ---- 6: role 1, lane (c, r): G1_r, G2_r of class c over its detectors in
+    // order; role 0, lane k: the detector's terms
+    if (GRAD && role == 1) {
       for (int it = lane; it < ncls * RR; it += 32) {
         const int c = it / RR, r = it - c * RR;
         float g1 = 0.f, g2 = 0.f;
@@ -555,67 +614,69 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     dacc tk = dacc_zero(), gk_t = dacc_zero(), gk_ra = dacc_zero(), gk_dec = dacc_zero();
     float gk[4] = {0.f, 0.f, 0.f, 0.f};  // ra, dec, psi, lnD through the antenna factor
     int badk = 0;
-    if (lane < K) badk = W.bad[lane];
-    if (lane < K && !badk) {
-      const int k = lane, c = P.cls_of[k];
-      float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
-#pragma unroll
-      for (int pr = 0; pr < NP; ++pr) {
-        const float4 v = W.part[k][pr];
-        q2 += v.x;
-        nul += v.y;
+    if (role == 0) {
+      if (lane < K) badk = W.bad[lane];
+      if (lane < K && !badk) {
+        const int k = lane, c = P.cls_of[k];
+        float q2 = 0.f, nul = 0.f, red = 0.f, g1 = 0.f, g2 = 0.f;
+  #pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+          const float4 v = W.part[k][pr];
+          q2 += v.x;
+          nul += v.y;
+          if (GRAD) {
+            red += v.z;
+            g1 += v.w;
+            g2 += W.part5[k][pr];
+          }
+        }
+        const float2 he = W.he2[k];
+        dacc_add(tk, df{he.x, he.y});
+        dacc_add(tk, df{-0.5f * q2, 0.f});
+        if (P.has_null[c]) dacc_add(tk, df{0.5f * nul, 0.f});
         if (GRAD) {
-          red += v.z;
-          g1 += v.w;
-          g2 += W.part5[k][pr];
+          const float2 dh = W.dhe2[k];
+          const df dtk = df_mul(df_add_f(df{dh.x, dh.y}, -red), df{P.inv_dt_hi, P.inv_dt_lo});
+          const float2 dkk = W.dk[k];
+          const df dra = df_mul_f(dtk, dkk.x), ddec = df_mul_f(dtk, dkk.y);
+          gk_t = dacc{dtk.hi, dtk.lo};
+          gk_ra = dacc{dra.hi, dra.lo};
+          gk_dec = dacc{ddec.hi, ddec.lo};
+          const float4 d = W.dx[k];
+          const float4 xfq = W.xf[k];
+          const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
+          gk[0] = fmaf(d.x, g1, d.y * g2);
+          gk[1] = fmaf(d.z, g1, d.w * g2);
+          gk[2] = fmaf(-2.f * xFi, g1, 2.f * xFr * g2);
+          gk[3] = fmaf(-xFr, g1, -xFi * g2);
         }
       }
-      const float2 he = W.he2[k];
-      dacc_add(tk, df{he.x, he.y});
-      dacc_add(tk, df{-0.5f * q2, 0.f});
-      if (P.has_null[c]) dacc_add(tk, df{0.5f * nul, 0.f});
-      if (GRAD) {
-        const float2 dh = W.dhe2[k];
-        const df dtk = df_mul(df_add_f(df{dh.x, dh.y}, -red), df{P.inv_dt_hi, P.inv_dt_lo});
-        const float2 dkk = W.dk[k];
-        const df dra = df_mul_f(dtk, dkk.x), ddec = df_mul_f(dtk, dkk.y);
-        gk_t = dacc{dtk.hi, dtk.lo};
-        gk_ra = dacc{dra.hi, dra.lo};
-        gk_dec = dacc{ddec.hi, ddec.lo};
-        const float4 d = W.dx[k];
-        const float4 xfq = W.xf[k];
-        const float xFr = __fadd_rn(xfq.x, xfq.y), xFi = __fadd_rn(xfq.z, xfq.w);
-        gk[0] = fmaf(d.x, g1, d.y * g2);
-        gk[1] = fmaf(d.z, g1, d.w * g2);
-        gk[2] = fmaf(-2.f * xFi, g1, 2.f * xFr * g2);
-        gk[3] = fmaf(-xFr, g1, -xFi * g2);
-      }
-    }
-    // the sums over detectors: a fixed shuffle tree over lanes 0..7
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) {
-      dacc o;
-      o.s = __shfl_down_sync(0xffffffffu, tk.s, off, 8);
-      o.c = __shfl_down_sync(0xffffffffu, tk.c, off, 8);
-      tk = dacc_merge(tk, o);
-      badk |= __shfl_down_sync(0xffffffffu, badk, off, 8);
-      if (GRAD) {
-        o.s = __shfl_down_sync(0xffffffffu, gk_t.s, off, 8);
-        o.c = __shfl_down_sync(0xffffffffu, gk_t.c, off, 8);
-        gk_t = dacc_merge(gk_t, o);
-        o.s = __shfl_down_sync(0xffffffffu, gk_ra.s, off, 8);
-        o.c = __shfl_down_sync(0xffffffffu, gk_ra.c, off, 8);
-        gk_ra = dacc_merge(gk_ra, o);
-        o.s = __shfl_down_sync(0xffffffffu, gk_dec.s, off, 8);
-        o.c = __shfl_down_sync(0xffffffffu, gk_dec.c, off, 8);
-        gk_dec = dacc_merge(gk_dec, o);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gk[q] += __shfl_down_sync(0xffffffffu, gk[q], off, 8);
+      // the sums over detectors: a fixed shuffle tree over lanes 0..7
+  #pragma unroll
+      for (int off = 4; off > 0; off >>= 1) {
+        dacc o;
+        o.s = __shfl_down_sync(0xffffffffu, tk.s, off, 8);
+        o.c = __shfl_down_sync(0xffffffffu, tk.c, off, 8);
+        tk = dacc_merge(tk, o);
+        badk |= __shfl_down_sync(0xffffffffu, badk, off, 8);
+        if (GRAD) {
+          o.s = __shfl_down_sync(0xffffffffu, gk_t.s, off, 8);
+          o.c = __shfl_down_sync(0xffffffffu, gk_t.c, off, 8);
+          gk_t = dacc_merge(gk_t, o);
+          o.s = __shfl_down_sync(0xffffffffu, gk_ra.s, off, 8);
+          o.c = __shfl_down_sync(0xffffffffu, gk_ra.c, off, 8);
+          gk_ra = dacc_merge(gk_ra, o);
+          o.s = __shfl_down_sync(0xffffffffu, gk_dec.s, off, 8);
+          o.c = __shfl_down_sync(0xffffffffu, gk_dec.c, off, 8);
+          gk_dec = dacc_merge(gk_dec, o);
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) gk[q] += __shfl_down_sync(0xffffffffu, gk[q], off, 8);
+        }
       }
     }
     __syncwarp();
-    if (GRAD) {
-      // ---- 7: lane (c, j): iota and phi_ref through mode j of class c
+    if (GRAD && role == 1) {
+      // ---- 7: role 1, lane (c, j): iota and phi_ref through mode j of class c
       float gph = 0.f, gin = 0.f;
       for (int it = lane; it < ncls * M; it += 32) {
         const int c = it / M, j = it - c * M;
@@ -656,10 +717,11 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       if (lane == 0) W.gmode = make_float2(gph, gin);
       __syncwarp();
     }
+    pair_sync();  // the mode terms of role 1
 
     // ---- 8: lane 0 holds the sums; lanes 0..7 then form one output each in
     // FP64 (a warp-wide FP64 instruction costs the same for one lane or eight)
-    if (lane == 0) {
+    if (role == 0 && lane == 0) {
       const df lnl = dacc_result(tk);
       W.out[0] = make_float4(lnl.hi, lnl.lo, 0.f, __int_as_float(badk));
       if (GRAD) {
@@ -674,7 +736,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       }
     }
     __syncwarp();
-    if (lane < (GRAD ? 8 : 1)) {
+    if (role == 0 && lane < (GRAD ? 8 : 1)) {
       const float4 o = W.out[lane];
       const bool bad = __float_as_int(W.out[0].w) != 0;
       const double v = bad ? CUDART_NAN : (double)o.x + (double)o.y + (double)o.z;
@@ -684,6 +746,6 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         grad_out[(size_t)(lane - 1) * dp.n + i] = v;
       }
     }
-    __syncwarp();  // the scratch is reused by this warp's next draw
+    pair_sync();  // the scratch is reused by the pair's next draw
   }
 }
