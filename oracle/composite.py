@@ -33,9 +33,9 @@ Two responses are covered.
   source; the frequency weights W_p live in the precomputed tables.
   Composite order: a = p = 0..p_max.
 
-Composite index A = a * M + i (a-major), i the mode.  Parity unpinned: no
-value of this likelihood is printed in the paper for a reproducible input;
-the tests pin it by the limits the paper names (Omega -> 0 and p_max = 0
+Composite index A = a * M + i (a-major), i the mode.  The paper prints no
+value of this likelihood for a reproducible input; the tests pin it by the
+limits the paper names (Omega -> 0 and p_max = 0
 recover the static likelihood), by the coefficient identities above at
 off-grid sidereal angles, by the Cauchy-Schwarz bound lnL <= <d|d>/2 with
 equality at the injected parameters, and by convergence in p_max.
