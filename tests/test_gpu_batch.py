@@ -1,7 +1,8 @@
 """GPU parity of the batched lnZ over many intrinsic points (config-3 shapes:
 2-5 detectors, 2-10 modes, 8k-65k-sample tables, uneven draw counts).
 
-FP32-mixed batch: each point's lnZ matches the FP64 oracle within 1e-4 and
+FP32-mixed batch: each point's lnZ matches the FP64 oracle within 1e-4 (six
+points, and 64 points in one launch against the oracle as well) and
 the single-point rift_ile_lnZ within 1e-6; FP64 batch matches the oracle
 within 1e-9 max(1, |lnZ|).  The launch replays identically from a captured
 CUDA graph and is deterministic.
@@ -133,3 +134,18 @@ def test_fp64_batch_tune_is_a_no_op(R, batch_inputs):
     b = R.Batch(points, draws, R.FP64)
     tile, blocks, ms = b.tune(reps=1)
     assert ms == -1.0
+
+
+def test_batch_64_points_against_oracle(R):
+    """64 config-3 points (2-5 detectors, 2-10 modes, uneven draw counts) in
+    one batched launch, both precisions, every point's lnZ against the
+    oracle: FP32-mixed within 1e-4, FP64 within 1e-9 max(1, |lnZ|)."""
+    inputs = [W.config3_point(i) for i in range(64)]
+    points = [R.Point(p[0]) for p in inputs]
+    draws = [R.Draws(p[3], p[4]) for p in inputs]
+    o32 = R.Batch(points, draws, R.FP32_MIXED).launch().cpu().numpy()
+    o64 = R.Batch(points, draws, R.FP64).launch().cpu().numpy()
+    for i, (point, exact, info, d, logw) in enumerate(inputs):
+        ref = O.lnZ(O.lnL(O.OraclePoint(point), d), np.asarray(logw, dtype=np.float64))
+        assert abs(o32[i, 0] - ref[0]) <= 1e-4, (i, o32[i], ref)
+        assert abs(o64[i, 0] - ref[0]) <= 1e-9 * max(1, abs(ref[0])), (i, o64[i], ref)
