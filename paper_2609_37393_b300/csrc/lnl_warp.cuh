@@ -14,24 +14,26 @@
 //      table: quadrant reduction and Taylor series in double-float); lanes
 //      4..15: of |m| phi for |m| = 1..12; every lane the distance factor
 //      (the exponential, also without a table)
+//   4a role 0, lane k < K: the arrival time and table position; the interval
+//      polynomial's coefficients loaded and the four tap rows prefetched into
+//      L1, in flight during phase 2
 //   2  role 0: the sky direction and x e^{2 i psi}; lanes 0..5 the six
 //      products of the sky sines and cosines, lanes 0..9 the ten antenna-basis
 //      terms from them, split for the exact products
 //   3  role 1, lane j < M: the harmonic of mode j, split for the exact
 //      products; lane (c, r): row r of the class-c mat-vec a1 = A y, a2 = A J y
-//   4  role 0, lane k < K: x F_k, the arrival time and table position (the
-//      table rows of the four taps are prefetched into L1), 1/2 |e|^2 and its
-//      slope, the cubic's weights, the detector's antenna derivatives
-//      (phases 2 and 4 run while role 1 runs phase 3)
+//   4  role 0, lane k < K: x F_k, 1/2 |e|^2 and its slope, the cubic's
+//      weights, the detector's antenna derivatives (phases 4a, 2 and 4 run
+//      while role 1 runs phase 3)
 //   5  role 0, lane (k, direction pair): the template, the residual over the
 //      four taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
 //   6  role 1, lane (c, r): G1_r, G2_r of the class; role 0, lane k: the
 //      detector's terms of lnL and of the gradient, summed over the detectors
 //      by a fixed shuffle tree (compensated pairs merged exactly)
 //   7  role 1, lane (c, j): the iota and phi_ref derivatives through mode j,
-//      summed over the lanes by a fixed shuffle tree (while role 0 runs the
-//      second half of phase 6)
-//   8  role 0, lanes 0..7: the outputs
+//      summed over the lanes by a fixed shuffle tree, and written out by its
+//      lane 0 (while role 0 runs the second half of phase 6 and phase 8)
+//   8  role 0, lanes 0..3, 6, 7: lnL and the other five gradient outputs
 // The per-point tables (split whitening, gm1, detector and mode tables) are
 // copied flat from the point's image at block start.
 // Reductions run in fixed orders, so results are reproducible; they differ
@@ -64,7 +66,6 @@ struct WarpScratch {
   float part5[kMaxDet][RR / 2];    // per (k, pair): rho.a2
   float2 gp[kMaxDet][RR];          // per (k, r): (Re xF_k rho_r, Im xF_k rho_r)
   float2 G[kMaxDet][RR];           // per class c, direction r: (G1, G2)
-  float2 gmode;                    // d lnL/d phi_ref, d lnL/d iota
   float4 out[8];                   // lnL and the gradient as (hi, lo, extra, bad flag)
 };
 
@@ -319,6 +320,45 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     const df x{W.x.x, W.x.y};
     const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
     const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
+    // ---- 4a: role 0, lane k < K: the arrival time and table position, so
+    // that the interval polynomial's coefficients and the tap rows are in
+    // flight while phase 2 forms the antenna basis
+    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
+    int bad = 0, jck = 0;
+    float f = 0.f, jf = 0.f;
+    bool inpoly = false;
+    float2 cf[kPolyDeg + 1];
+    if (role == 0 && lane < K) {
+      const int k = lane;
+      ph = T.pos_hi[k];
+      pl = T.pos_lo[k];
+      df delay = df_mul(df{ph.x, pl.x}, s0);
+      delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
+      delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
+      const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
+      const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
+      bad = isfinite(u.hi) ? 0 : 1;
+      if (!bad) {
+        jf = floorf(u.hi);
+        if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
+        f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
+      }
+      inpoly = !bad && jf >= -2.f && jf <= (float)n;
+      if (inpoly) {
+        const float2* pc =
+            P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
+#pragma unroll
+        for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
+      }
+      jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
+      {  // the four tap rows (contiguous) into L1 for the residual phase
+        const char* row = reinterpret_cast<const char*>(
+            P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (jck - 1)) * RR);
+        for (int off = 0; off < 4 * RR * 8; off += 128)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(row + off));
+      }
+    }
+
     if (role == 0) {
       // the antenna basis: six products on lanes 0..5, ten terms on lanes 0..9
       if (lane < 6) {
@@ -401,39 +441,10 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     }
 
     if (role == 0) {
-      // ---- 4: lane k < K: arrival time and table position first, so that the
-      // interval polynomial's coefficients and the tap rows are in flight while
-      // the antenna factor is formed; then 1/2|e|^2, the weights, the derivatives
+      // ---- 4: lane k < K (the arrival time and the table loads of phase 4a):
+      // the antenna factor, 1/2|e|^2, the weights, the derivatives
       if (lane < K) {
         const int k = lane;
-        const float4 ph = T.pos_hi[k], pl = T.pos_lo[k];
-        df delay = df_mul(df{ph.x, pl.x}, s0);
-        delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
-        delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
-        const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
-        const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
-        const int bad = isfinite(u.hi) ? 0 : 1;
-        float f = 0.f, jf = 0.f;
-        if (!bad) {
-          jf = floorf(u.hi);
-          if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
-          f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
-        }
-        const bool inpoly = !bad && jf >= -2.f && jf <= (float)n;
-        float2 cf[kPolyDeg + 1];
-        if (inpoly) {
-          const float2* pc =
-              P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
-  #pragma unroll
-          for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
-        }
-        const int jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-        {  // the four tap rows (contiguous) into L1 for the residual phase
-          const char* row = reinterpret_cast<const char*>(
-              P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (jck - 1)) * RR);
-          for (int off = 0; off < 4 * RR * 8; off += 128)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(row + off));
-        }
         AntennaSplit AS;
   #pragma unroll
         for (int q = 0; q < 6; ++q) {
@@ -714,13 +725,19 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         gph += __shfl_down_sync(0xffffffffu, gph, off);
         gin += __shfl_down_sync(0xffffffffu, gin, off);
       }
-      if (lane == 0) W.gmode = make_float2(gph, gin);
-      __syncwarp();
+      // role 1 writes its two outputs itself (the draw is NaN if any
+      // detector's arrival time was not finite), while role 0 forms the rest
+      if (lane == 0) {
+        int badany = 0;
+        for (int k = 0; k < K; ++k) badany |= W.bad[k];
+        grad_out[(size_t)3 * dp.n + i] = badany ? CUDART_NAN : (double)gin;
+        grad_out[(size_t)4 * dp.n + i] = badany ? CUDART_NAN : (double)gph;
+      }
     }
-    pair_sync();  // the mode terms of role 1
 
-    // ---- 8: lane 0 holds the sums; lanes 0..7 then form one output each in
-    // FP64 (a warp-wide FP64 instruction costs the same for one lane or eight)
+    // ---- 8: lane 0 holds the sums; lanes 0..3, 6, 7 then form one output each
+    // in FP64 (a warp-wide FP64 instruction costs the same for one lane or
+    // eight; the iota and phase outputs come from role 1)
     if (role == 0 && lane == 0) {
       const df lnl = dacc_result(tk);
       W.out[0] = make_float4(lnl.hi, lnl.lo, 0.f, __int_as_float(badk));
@@ -729,14 +746,12 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         W.out[1] = make_float4(a.hi, a.lo, gk[0], 0.f);
         W.out[2] = make_float4(b.hi, b.lo, gk[1], 0.f);
         W.out[3] = make_float4(gk[2], 0.f, 0.f, 0.f);
-        W.out[4] = make_float4(W.gmode.y, 0.f, 0.f, 0.f);
-        W.out[5] = make_float4(W.gmode.x, 0.f, 0.f, 0.f);
         W.out[6] = make_float4(gk[3], 0.f, 0.f, 0.f);
         W.out[7] = make_float4(t.hi, t.lo, 0.f, 0.f);
       }
     }
     __syncwarp();
-    if (role == 0 && lane < (GRAD ? 8 : 1)) {
+    if (role == 0 && lane < (GRAD ? 8 : 1) && lane != 4 && lane != 5) {
       const float4 o = W.out[lane];
       const bool bad = __float_as_int(W.out[0].w) != 0;
       const double v = bad ? CUDART_NAN : (double)o.x + (double)o.y + (double)o.z;
