@@ -657,6 +657,14 @@ def run_response(args):
             lf = R.rift_ile_comp_lnL(cp, d)
             lm = R.rift_ile_comp_lnL_mixed(cp, d)
             near = lf > lf.max() - 50.0
+            # the FP32-mixed adjoint, against the FP64 adjoint's gradient (in grad)
+            lnl_m = torch.empty(n, dtype=torch.float64, device="cuda")
+            grad_m = torch.empty((7, n), dtype=torch.float64, device="cuda")
+            ms_gm = timed_events(
+                torch, lambda: R.rift_ile_comp_lnL_grad_mixed(cp, d, lnl_m, grad_m), 3, stream)
+            gscale = grad.abs() + grad[:, near].pow(2).mean(dim=1, keepdim=True).sqrt()
+            grel = ((grad_m - grad).abs() / gscale)[:, near].max(dim=1).values.tolist()
+            del lnl_m, grad_m, gscale
             ops = comp_mixed_fp32_ops(cp.K, cp.M, cp.na, info_m[0], info_m[2])
             row = {"response": name, "kind": kind, "p_max": p_max, "composite_dim": cp.A,
                    "draws_per_s": n / (ms * 1e-3), "ms_per_step": ms, "lnZ": z[0],
@@ -671,7 +679,11 @@ def run_response(args):
                              "classes": info_m[2], "threads_per_block": info_m[3],
                              "eig_tol": 1e-14, "build_s": build_s,
                              "loop_fp32_lane_ops_per_draw": ops,
-                             "fp32_issue_frac": ops * n / (ms_m * 1e-3) / fp32_fma}}
+                             "fp32_issue_frac": ops * n / (ms_m * 1e-3) / fp32_fma,
+                             "fwd_bwd_draws_per_s": n / (ms_gm * 1e-3),
+                             "fwd_bwd_speedup_vs_fp64": ms_g / ms_gm,
+                             "max_rel_grad_err_within_50nat_vs_fp64":
+                                 dict(zip(W_PARAMS, grel))}}
             rows.append(row)
             if head is None:
                 head = row

@@ -173,6 +173,19 @@ int rift_ile_comp_mixed_info(const rift_ile_comp* cp, int32_t out[4]);
 int rift_ile_comp_lnL_mixed(const rift_ile_comp* cp, const rift_ile_draws* draws, double* lnL_out,
                             void* stream);
 
+/* lnL (DEVICE [n], may be NULL) and d lnL / d theta into DEVICE grad_out [7][n]
+ * (double; parameter-major: ra, dec, psi, incl, phase, lnD, t) from the
+ * FP32-mixed form, on `stream`: the chain rule of rift_ile_comp_lnL_grad taken
+ * in the whitened coordinates.  lnL is the value rift_ile_comp_lnL_mixed gives;
+ * the terms of the gradient that multiply the residual e_k - w_k (coefficient
+ * and harmonic derivatives) are FP32, the slope of 1/2 |e_k|^2 in t_k is
+ * double-float.  A draw whose arrival time is not finite gets NaN throughout.
+ * Errors: INVALID_ARG (also: the mixed form is not built, grad_out NULL),
+ * UNSUPPORTED (the adjoint's per-thread slots exceed the device's shared
+ * memory), CUDA. */
+int rift_ile_comp_lnL_grad_mixed(const rift_ile_comp* cp, const rift_ile_draws* draws,
+                                 double* lnL_out, double* grad_out, void* stream);
+
 /* LSE state of the draws (fused lnL -> LSE, FP32-mixed lnL, FP64 combine) to
  * HOST *state; synchronises; out-of-table taps as rift_ile_comp_lnZ_state. */
 int rift_ile_comp_lnZ_state_mixed(const rift_ile_comp* cp, const rift_ile_draws* draws,

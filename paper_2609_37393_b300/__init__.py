@@ -605,6 +605,7 @@ _lib.rift_ile_comp_lnZ_state_async.argtypes = [_P, _P, _P, _P]
 _lib.rift_ile_comp_mixed_build.argtypes = [_P, ctypes.c_double, _P]
 _lib.rift_ile_comp_mixed_info.argtypes = [_P, _P]
 _lib.rift_ile_comp_lnL_mixed.argtypes = [_P, _P, _P, _P]
+_lib.rift_ile_comp_lnL_grad_mixed.argtypes = [_P, _P, _P, _P, _P]
 _lib.rift_ile_comp_lnZ_state_mixed.argtypes = [_P, _P, _P, _P]
 _lib.rift_ile_comp_lnZ_state_mixed_async.argtypes = [_P, _P, _P, _P]
 
@@ -755,6 +756,21 @@ def rift_ile_comp_lnL_mixed(cp: CompPoint, draws, out=None, stream=None):
     _check(_lib.rift_ile_comp_lnL_mixed(cp.handle, d.ref, out.data_ptr() if d.n else None,
                                         _stream(stream)))
     return out
+
+
+def rift_ile_comp_lnL_grad_mixed(cp: CompPoint, draws, lnl_out=None, grad_out=None, stream=None):
+    """(lnL[n], grad[7, n]) of the composite response as float64 CUDA tensors,
+    FP32-mixed (rift_ile_comp_mixed_build first)."""
+    torch = _torch()
+    d = _as_draws(draws)
+    if lnl_out is None:
+        lnl_out = torch.empty(d.n, dtype=torch.float64, device=cp.device)
+    if grad_out is None:
+        grad_out = torch.empty((7, d.n), dtype=torch.float64, device=cp.device)
+    _check(_lib.rift_ile_comp_lnL_grad_mixed(cp.handle, d.ref, lnl_out.data_ptr() if d.n else None,
+                                             grad_out.data_ptr() if d.n else None,
+                                             _stream(stream)))
+    return lnl_out, grad_out
 
 
 def rift_ile_comp_lnZ_state_mixed(cp: CompPoint, draws, stream=None):

@@ -124,9 +124,19 @@ __host__ __device__ inline size_t comp_mixed_b_f4(const CompMixed& C) {
 __host__ __device__ inline size_t comp_mixed_ag_f4(const CompMixed& C) {
   return ((size_t)C.ncls * C.R + 3) / 4;
 }
-__host__ __device__ inline size_t comp_mixed_smem(const CompMixed& C, bool bsmem, int threads) {
+// Per-thread float4 slots: the coefficients (K na) and the taps (2 K); the
+// adjoint adds three tap slots per detector (derivative weights, arrival-time
+// derivatives, post-phase step), the residual products rho (K na float2), the
+// current direction pair's a1, a2 (na) and d lnL / dY of the mode pairs (JP).
+__host__ __device__ inline size_t comp_mixed_thread_f4(const CompMixed& C, bool grad) {
+  size_t f = (size_t)C.K * C.na + 2 * C.K;
+  if (grad) f += 3 * C.K + ((size_t)C.K * C.na + 1) / 2 + C.na + C.JP;
+  return f;
+}
+__host__ __device__ inline size_t comp_mixed_smem(const CompMixed& C, bool bsmem, int threads,
+                                                  bool grad = false) {
   return ((bsmem ? comp_mixed_b_f4(C) : 0) + comp_mixed_ag_f4(C) +
-          (size_t)(C.K * C.na + 2 * C.K) * threads) * 16;
+          comp_mixed_thread_f4(C, grad) * threads) * 16;
 }
 
 }  // namespace rift
@@ -143,6 +153,7 @@ struct rift_ile_comp {
   int mixed_built;
   int mixed_R[rift::kMaxDet];   // kept directions of each class
   int mixed_threads, mixed_bsmem;  // launch shape: block size, split whitening in shared memory
+  int grad_threads, grad_bsmem;    // the same for the adjoint
   double mixed_tol;
   rift::CompMixed mixed;        // host copy (pointers are device pointers)
   rift::CompMixed* mixed_dev;   // device copy

@@ -29,6 +29,9 @@ template <int MM>
 cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
                            double* lnl_out, LseState* partials, unsigned long long* oob,
                            int* blocks, cudaStream_t st);
+template <int MM>
+cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
+                            double* lnl_out, double* grad_out, cudaStream_t st);
 
 namespace {
 
@@ -44,6 +47,18 @@ cudaError_t launch_comp_mixed(const rift_ile_comp* cp, const DrawsParams& dp, do
     case 4: return comp_mixed_lnl<4>(C, bs, th, dp, lnl_out, partials, oob, blocks, st);
     case 10: return comp_mixed_lnl<10>(C, bs, th, dp, lnl_out, partials, oob, blocks, st);
     default: return comp_mixed_lnl<16>(C, bs, th, dp, lnl_out, partials, oob, blocks, st);
+  }
+}
+
+cudaError_t launch_comp_mixed_grad(const rift_ile_comp* cp, const DrawsParams& dp,
+                                   double* lnl_out, double* grad_out, cudaStream_t st) {
+  const CompMixed& C = cp->mixed;
+  const bool bs = cp->grad_bsmem != 0;
+  const int th = cp->grad_threads;
+  switch (mm_bucket(C.M)) {
+    case 4: return comp_mixed_grad<4>(C, bs, th, dp, lnl_out, grad_out, st);
+    case 10: return comp_mixed_grad<10>(C, bs, th, dp, lnl_out, grad_out, st);
+    default: return comp_mixed_grad<16>(C, bs, th, dp, lnl_out, grad_out, st);
   }
 }
 
@@ -372,13 +387,22 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
     free_mixed(cp);
     return rc;
   }
-  cp->mixed_threads = 0;
+  cp->mixed_threads = cp->grad_threads = 0;
   const size_t static_smem = 2048;  // the LSE kernels' static shared memory, with margin
   const int shapes[6][2] = {{128, 1}, {128, 0}, {64, 1}, {64, 0}, {32, 1}, {32, 0}};
   for (const auto& sh : shapes) {
     if (comp_mixed_smem(C, sh[1] != 0, sh[0]) + static_smem <= (size_t)optin) {
       cp->mixed_threads = sh[0];
       cp->mixed_bsmem = sh[1];
+      break;
+    }
+  }
+  // the adjoint's (more slots per thread; without a fitting shape only the
+  // gradient entry point reports UNSUPPORTED)
+  for (const auto& sh : shapes) {
+    if (comp_mixed_smem(C, sh[1] != 0, sh[0], true) + static_smem <= (size_t)optin) {
+      cp->grad_threads = sh[0];
+      cp->grad_bsmem = sh[1];
       break;
     }
   }
@@ -424,6 +448,26 @@ extern "C" int rift_ile_comp_lnL_mixed(const rift_ile_comp* cp, const rift_ile_d
   return check_cuda(launch_comp_mixed(cp, draws_params(draws), lnL_out, nullptr, nullptr, &blocks,
                                       (cudaStream_t)stream),
                     "rift_ile_comp_lnL_mixed launch");
+}
+
+extern "C" int rift_ile_comp_lnL_grad_mixed(const rift_ile_comp* cp, const rift_ile_draws* draws,
+                                            double* lnL_out, double* grad_out, void* stream) {
+  int rc = mixed_args(cp, draws);
+  if (rc) return rc;
+  if (draws->n == 0) return RIFT_ILE_OK;
+  if (!grad_out) {
+    rift_ile_set_error("rift_ile_comp_lnL_grad_mixed: grad_out is NULL");
+    return RIFT_ILE_ERR_INVALID_ARG;
+  }
+  if (!cp->grad_threads) {
+    rift_ile_set_error("rift_ile_comp_lnL_grad_mixed: %d detectors x %d response indices need "
+                       "more shared memory per thread than the device has",
+                       cp->mixed.K, cp->mixed.na);
+    return RIFT_ILE_ERR_UNSUPPORTED;
+  }
+  return check_cuda(launch_comp_mixed_grad(cp, draws_params(draws), lnL_out, grad_out,
+                                           (cudaStream_t)stream),
+                    "rift_ile_comp_lnL_grad_mixed launch");
 }
 
 extern "C" int rift_ile_comp_lnZ_state_mixed_async(const rift_ile_comp* cp,

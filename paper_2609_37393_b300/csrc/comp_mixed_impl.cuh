@@ -82,7 +82,7 @@ struct CompSky {
 // Dxx + Dyy, Dzz), and C_(0,n) = e^{2 i psi} A_n e^{i n g}, g = gmst - ra.
 __device__ __noinline__ float rot_coeffs(const CompMixed& C, int k, const CompSky& S,
                                          const cdf* G, df f0a, df f0b, df tk, float4* slot,
-                                         int bd) {
+                                         int bd, float2* ep_out) {
   const float2* rc = C.rc[k];
   const df r1 = df_of(rc[0]), r2 = df_of(rc[1]), r3 = df_of(rc[2]), r4 = df_of(rc[3]);
   const df r5 = df_of(rc[4]), r6 = df_of(rc[5]);
@@ -99,6 +99,7 @@ __device__ __noinline__ float rot_coeffs(const CompMixed& C, int k, const CompSk
   cdf ep;
   sincos_df_call(df_mul(df{C.omega_hi, C.omega_lo}, tk), ep.im, ep.re);
   const cdf epc = cdf_conj(ep);
+  if (ep_out) *ep_out = make_float2(ep.re.hi, ep.im.hi);
   float mx = 0.f;
   if (C.p_max == 0) {  // Path A: C~_(0,n) = C_(0,n) e^{i n Omega t_k}, n = -2..2
     const cdf e2 = cdf_mul(ep, ep);
@@ -189,14 +190,306 @@ __device__ __noinline__ float arm_coeffs(const CompMixed& C, int k, const CompSk
   return mx;
 }
 
+// ---- the adjoint's coefficient terms (FP32: they multiply the residual)
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float dotf2(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+
+struct CompSkyF {
+  float sl, cl, sd, cd;  // of ra - gmst and dec
+  float2 xe2p;           // x e^{2 i psi}
+};
+
+// Adds sum_a (d C~_a / d theta) . rho_a / sigma_a of detector k for theta = ra,
+// dec, t_c (rho_a = (r . a1_a, r . a2_a) with the scaled a-values, slot k na + a;
+// ep = e^{i Omega t_k}, dtk_* = d t_k / d ra, d dec).
+// Rotation: C_(0,n) = x e^{2 i psi} A_n(dec) e^{i n g} with d/d ra = -i n C_(0,n)
+// (g = gmst - ra) and d/d dec through A_n; the drift harmonics move with
+// w = (x + i y) e^{i g} and cos(dec); d P^(p) = d P^(p-1) * E + P^(p-1) * d E;
+// the post-phase adds i nn Omega (d t_k / d theta) C~ and is the t_c term.
+// Finite arms: b_p through the arm projections of e1, e2 and s.
+__device__ __noinline__ void comp_coeff_grad_contract(const CompMixed& C, int k, const CompSkyF& S,
+                                                      float2 ep, float dtk_ra, float dtk_dec,
+                                                      const float2* rho, int bd, float& g_ra,
+                                                      float& g_dec, float& g_tc) {
+  const int na = C.na;
+  const float2* rc = C.rc[k];
+  const float sl = S.sl, cl = S.cl, sd = S.sd, cd = S.cd;
+  if (C.kind == RIFT_ILE_RESP_FINITE_ARM) {
+    // e1 = (-sl, cl, 0), e2 = (-sd cl, -sd sl, cd), s = (cd cl, cd sl, sd) and
+    // their ra, dec derivatives
+    float q2[2][2], dq[2][2][2], u[2], du[2][2];  // per arm: q (complex), dq/d(ra, dec), u, du
+    for (int v = 0; v < 2; ++v) {
+      const float X0 = rc[3 * v].x, X1 = rc[3 * v + 1].x, X2 = rc[3 * v + 2].x;
+      const float a = -sl * X0 + cl * X1, b = -sd * (cl * X0 + sl * X1) + cd * X2;
+      u[v] = cd * (cl * X0 + sl * X1) + sd * X2;
+      const float da[2] = {-cl * X0 - sl * X1, 0.f};
+      const float db[2] = {sd * (sl * X0 - cl * X1), -cd * (cl * X0 + sl * X1) - sd * X2};
+      du[v][0] = cd * (-sl * X0 + cl * X1);
+      du[v][1] = -sd * (cl * X0 + sl * X1) + cd * X2;
+      const float2 q = cmulf(S.xe2p, make_float2(a * a - b * b, -2.f * a * b));
+      q2[v][0] = q.x;
+      q2[v][1] = q.y;
+      for (int j = 0; j < 2; ++j) {
+        const float2 d = cmulf(S.xe2p, cmulf(make_float2(2.f * a, -2.f * b), make_float2(da[j], -db[j])));
+        dq[v][j][0] = d.x;
+        dq[v][j][1] = d.y;
+      }
+    }
+    float px = 0.5f, py = 0.5f, pxm = 0.f, pym = 0.f;  // u^p / 2 and p u^(p-1) / 2
+    for (int p = 0; p < na; ++p) {
+      const float2 r = rho[(size_t)(k * na + p) * bd];
+      const float isg = C.inv_sigma[p];
+      float g[2];
+      for (int j = 0; j < 2; ++j) {
+        const float cx = pxm * du[0][j], cy = pym * du[1][j];
+        const float dre = cx * q2[0][0] + px * dq[0][j][0] - cy * q2[1][0] - py * dq[1][j][0];
+        const float dim = cx * q2[0][1] + px * dq[0][j][1] - cy * q2[1][1] - py * dq[1][j][1];
+        g[j] = isg * fmaf(dre, r.x, dim * r.y);
+      }
+      g_ra += g[0];
+      g_dec += g[1];
+      pxm = (float)(p + 1) * px;
+      pym = (float)(p + 1) * py;
+      px *= u[0];
+      py *= u[1];
+    }
+    return;
+  }
+  const float r1 = rc[0].x, r2 = rc[1].x, r3 = rc[2].x, r4 = rc[3].x, r5 = rc[4].x, r6 = rc[5].x;
+  const float al = 0.5f * (1.f + sd), be = 0.5f * (1.f - sd), dal = 0.5f * cd, dbe = -0.5f * cd;
+  const float dcd = -sd;
+  float2 A[5], dA[5];
+  A[0] = make_float2(al * al * r1, al * al * r2);
+  dA[0] = make_float2(2.f * al * dal * r1, 2.f * al * dal * r2);
+  A[4] = make_float2(be * be * r1, -be * be * r2);
+  dA[4] = make_float2(2.f * be * dbe * r1, -2.f * be * dbe * r2);
+  A[1] = make_float2(al * cd * r3, -al * cd * r4);
+  {
+    const float f = dal * cd + al * dcd;
+    dA[1] = make_float2(f * r3, -f * r4);
+  }
+  A[3] = make_float2(-be * cd * r3, -be * cd * r4);
+  {
+    const float f = dbe * cd + be * dcd;
+    dA[3] = make_float2(-f * r3, -f * r4);
+  }
+  A[2] = make_float2(2.f * al * be * r5 - cd * cd * r6, 0.f);
+  dA[2] = make_float2(2.f * (dal * be + al * dbe) * r5 - 2.f * cd * dcd * r6, 0.f);
+  const float2 eg = make_float2(cl, -sl);
+  float2 egn[5];
+  egn[2] = make_float2(1.f, 0.f);
+  egn[3] = eg;
+  egn[4] = cmulf(eg, eg);
+  egn[1] = conjf2(eg);
+  egn[0] = conjf2(egn[4]);
+  float2 C0[5], dC0[2][5];
+  for (int j = 0; j < 5; ++j) {
+    const float n = (float)(j - 2);
+    C0[j] = cmulf(cmulf(S.xe2p, A[j]), egn[j]);
+    dC0[0][j] = make_float2(n * C0[j].y, -n * C0[j].x);  // -i n C0
+    dC0[1][j] = cmulf(cmulf(S.xe2p, dA[j]), egn[j]);
+  }
+  float2 E[3], dE[2][3];
+  if (C.p_max > 0) {
+    const float2 w = cmulf(make_float2(C.pos_hi[k].x, C.pos_hi[k].y), eg);
+    E[0] = make_float2(0.5f * cd * w.x, -0.5f * cd * w.y);
+    E[1] = make_float2(-cd * w.x, 0.f);
+    E[2] = make_float2(0.5f * cd * w.x, 0.5f * cd * w.y);
+    dE[0][0] = make_float2(-E[0].y, E[0].x);
+    dE[0][1] = make_float2(-cd * w.y, 0.f);
+    dE[0][2] = make_float2(E[2].y, -E[2].x);
+    dE[1][0] = make_float2(0.5f * dcd * w.x, -0.5f * dcd * w.y);
+    dE[1][1] = make_float2(-dcd * w.x, 0.f);
+    dE[1][2] = make_float2(0.5f * dcd * w.x, 0.5f * dcd * w.y);
+  }
+  const float om = C.omega_hi;
+  const float dtk[2] = {dtk_ra, dtk_dec};
+  float2 P[2 * RIFT_ILE_MAX_ROT_PMAX + 1], dP[2][2 * RIFT_ILE_MAX_ROT_PMAX + 1];
+  P[0] = make_float2(1.f, 0.f);
+  dP[0][0] = dP[1][0] = make_float2(0.f, 0.f);
+  int off = 0;
+  for (int p = 0; p <= C.p_max; ++p) {
+    if (p > 0) {
+      float2 Pn[2 * RIFT_ILE_MAX_ROT_PMAX + 1], dPn[2][2 * RIFT_ILE_MAX_ROT_PMAX + 1];
+      for (int j = 0; j < 2 * p + 1; ++j) {
+        float2 acc = make_float2(0.f, 0.f), d0 = acc, d1 = acc;
+        for (int e = 0; e < 3; ++e) {
+          const int src = j - e;
+          if (src >= 0 && src < 2 * p - 1) {
+            const float2 t = cmulf(P[src], E[e]);
+            acc.x += t.x;
+            acc.y += t.y;
+            const float2 a0 = cmulf(dP[0][src], E[e]), b0 = cmulf(P[src], dE[0][e]);
+            const float2 a1 = cmulf(dP[1][src], E[e]), b1 = cmulf(P[src], dE[1][e]);
+            d0.x += a0.x + b0.x;
+            d0.y += a0.y + b0.y;
+            d1.x += a1.x + b1.x;
+            d1.y += a1.y + b1.y;
+          }
+        }
+        Pn[j] = acc;
+        dPn[0][j] = d0;
+        dPn[1][j] = d1;
+      }
+      for (int j = 0; j < 2 * p + 1; ++j) {
+        P[j] = Pn[j];
+        dP[0][j] = dPn[0][j];
+        dP[1][j] = dPn[1][j];
+      }
+    }
+    const float inv_fact = C.inv_fact[p];
+    float2 ph = make_float2(1.f, 0.f);
+    for (int q = 0; q < 2 + p; ++q) ph = cmulf(ph, conjf2(ep));
+    const int width = 2 * (2 + p) + 1;
+    for (int j = 0; j < width; ++j) {
+      const int nn = j - (2 + p);
+      float2 acc = make_float2(0.f, 0.f), d0 = acc, d1 = acc;
+      for (int n = -2; n <= 2; ++n) {
+        const int m = nn - n;
+        if (m >= -p && m <= p) {
+          const float2 t = cmulf(C0[n + 2], P[m + p]);
+          acc.x += t.x;
+          acc.y += t.y;
+          const float2 a0 = cmulf(dC0[0][n + 2], P[m + p]), b0 = cmulf(C0[n + 2], dP[0][m + p]);
+          const float2 a1 = cmulf(dC0[1][n + 2], P[m + p]), b1 = cmulf(C0[n + 2], dP[1][m + p]);
+          d0.x += a0.x + b0.x;
+          d0.y += a0.y + b0.y;
+          d1.x += a1.x + b1.x;
+          d1.y += a1.y + b1.y;
+        }
+      }
+      const float2 c = cmulf(make_float2(acc.x * inv_fact, acc.y * inv_fact), ph);
+      const float2 ct = make_float2(-(float)nn * om * c.y, (float)nn * om * c.x);  // i nn Omega c
+      const float2 dra = cmulf(make_float2(d0.x * inv_fact, d0.y * inv_fact), ph);
+      const float2 ddec = cmulf(make_float2(d1.x * inv_fact, d1.y * inv_fact), ph);
+      const int a = off + j;
+      const float2 r = rho[(size_t)(k * na + a) * bd];
+      const float isg = C.inv_sigma[a];
+      g_ra += isg * dotf2(make_float2(fmaf(dtk[0], ct.x, dra.x), fmaf(dtk[0], ct.y, dra.y)), r);
+      g_dec += isg * dotf2(make_float2(fmaf(dtk[1], ct.x, ddec.x), fmaf(dtk[1], ct.y, ddec.y)), r);
+      g_tc += isg * dotf2(ct, r);
+      ph = cmulf(ph, ep);
+    }
+    off += width;
+  }
+}
+
+// This thread's adjoint slots (stride: the block size): rho_(k,a) = (r . a1,
+// r . a2) summed over the directions, the current direction pair's a-values,
+// and d lnL / d(Re Y, Im Y) of the mode pairs.
+struct CompGradSlots {
+  float2* rho;  // [K na]
+  float4* af;   // [na] (a1 row 0, a1 row 1, a2 row 0, a2 row 1)
+  float4* dy;   // [JP] (d Re Y lanes, d Im Y lanes)
+};
+
+// Tap slots per detector: the weights, (sigma, first tap, and for the adjoint
+// the slope of 1/2 |e|^2), then (adjoint) the derivative weights, (d t_k / d ra,
+// d t_k / d dec, r . de/du) and e^{i Omega t_k}.
+template <bool GRAD>
+constexpr int comp_tap_slots() { return GRAD ? 5 : 2; }
+
+// The adjoint's last pass over a draw's detectors and modes: the arrival-time
+// terms (d/dt 1/2 |e_k|^2 - r_k . de_k/dt) d t_k (double-float), the coefficient
+// terms through rho (psi: d C~ = 2 i C~ d psi; lnD: d C~ = -C~ d lnD; sky and
+// t_c by comp_coeff_grad_contract), and the harmonic terms from d lnL / d Y
+// with Y_j = amp_j(iota) e^{i m phase} (FP32 amplitude and its iota slope).
+template <int MM>
+__device__ __noinline__ void comp_mixed_grad_tail(const CompMixed& C, const CompSkyF S,
+                                                  const float4* tslot, const float4* cslot,
+                                                  const CompGradSlots gs, float incl, float phi,
+                                                  bool bad, double* gout) {
+  constexpr int TS = comp_tap_slots<true>();
+  const int bd = blockDim.x, K = C.K, na = C.na;
+  dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
+  float g_ra = 0.f, g_dec = 0.f, g_tc = 0.f, g_psi = 0.f, g_lnd = 0.f;
+  for (int k = 0; k < K; ++k) {
+    const float4 t1 = tslot[(size_t)(TS * k + 1) * bd], t3 = tslot[(size_t)(TS * k + 3) * bd];
+    const float4 t4 = tslot[(size_t)(TS * k + 4) * bd];
+    const df dtk = df_mul(df_add_f(df{t1.z, t1.w}, -t3.z), df{C.inv_dt_hi, C.inv_dt_lo});
+    dacc_add(gt_t, dtk);
+    dacc_add(gt_ra, df_mul_f(dtk, t3.x));
+    dacc_add(gt_dec, df_mul_f(dtk, t3.y));
+    comp_coeff_grad_contract(C, k, S, make_float2(t4.x, t4.y), t3.x, t3.y, gs.rho, bd, g_ra, g_dec,
+                             g_tc);
+    for (int a = 0; a < na; ++a) {
+      const size_t e = (size_t)(k * na + a) * bd;
+      const float4 cs = cslot[e];
+      const float cre = cs.x + cs.z, cim = cs.y + cs.w;
+      const float2 r = gs.rho[e];
+      g_psi = fmaf(2.f, fmaf(cre, r.y, -cim * r.x), g_psi);
+      g_lnd -= fmaf(cre, r.x, cim * r.y);
+    }
+  }
+  float g_incl = 0.f, g_phase = 0.f, si, ci;
+  sincosf(incl, &si, &ci);
+  for (int j = 0; j < C.M; ++j) {
+    const float4 y4 = gs.dy[(size_t)(j / 2) * bd];
+    const float Hre = (j & 1) ? y4.y : y4.x, Him = (j & 1) ? y4.w : y4.z;
+    const int4 md = C.mode[j];
+    const int m = md.y, l = md.z;
+    float pz = C.yz[j][l].x, dpz = 0.f;
+    for (int q = l - 1; q >= 0; --q) {
+      dpz = fmaf(dpz, ci, pz);
+      pz = fmaf(pz, ci, C.yz[j][q].x);
+    }
+    float amp, damp;  // d/d iota through z = cos(iota): dz = -sin(iota) d iota
+    if (md.w) {
+      amp = si * pz;
+      damp = fmaf(ci, pz, -si * si * dpz);
+    } else {
+      amp = pz;
+      damp = -si * dpz;
+    }
+    float sm, cm;
+    sincosf((float)m * phi, &sm, &cm);
+    const float yre = amp * cm, yim = amp * sm;
+    g_phase = fmaf((float)m, fmaf(-yim, Hre, yre * Him), g_phase);
+    g_incl = fmaf(damp * cm, Hre, fmaf(damp * sm, Him, g_incl));
+  }
+  const df a = dacc_result(gt_ra), b = dacc_result(gt_dec), t = dacc_result(gt_t);
+  gout[0] = (double)a.hi + (double)a.lo + (double)g_ra;
+  gout[1] = (double)b.hi + (double)b.lo + (double)g_dec;
+  gout[2] = g_psi;
+  gout[3] = g_incl;
+  gout[4] = g_phase;
+  gout[5] = g_lnd;
+  gout[6] = (double)t.hi + (double)t.lo + (double)g_tc;
+  if (bad)
+    for (int p = 0; p < kNpar; ++p) gout[p] = CUDART_NAN;
+}
+
+__device__ __forceinline__ CompSkyF comp_sky_f(const CompSky& S) {
+  CompSkyF f;
+  f.sl = S.sl.hi;
+  f.cl = S.cl.hi;
+  f.sd = S.sd.hi;
+  f.cd = S.cd.hi;
+  f.xe2p = make_float2(S.xe2p.re.hi, S.xe2p.im.hi);
+  return f;
+}
+
 // One draw of the composite FP32-mixed likelihood.  B: split whitening (shared
 // or global), AG: head constants of a1, a2; cslot/tslot: this thread's slots.
-template <int MM>
+// With GRAD also d lnL / d (ra, dec, psi, incl, phase, lnD, t) into gout: the
+// chain rule of the FP64 adjoint taken in the whitened coordinates,
+//   d lnL = sum_k [(d/dt 1/2 |e_k|^2 - r_k . de_k/dt) d t_k + r_k . d w_k],
+// with r_k = e_k - w_k; d w_k splits into the coefficient derivatives
+// (contracted with rho) and the harmonic derivatives (through d lnL / d Y).
+// Those terms multiply the residual and are FP32; the arrival-time slope of
+// 1/2 |e|^2 is double-float.
+template <int MM, bool GRAD>
 __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* __restrict__ B,
                                               const float* __restrict__ AG, float4* cslot,
-                                              float4* tslot, const DrawsParams& dp, long long i,
-                                              int& oob) {
+                                              float4* tslot, const CompGradSlots& gs,
+                                              const DrawsParams& dp, long long i, int& oob,
+                                              double* gout) {
   constexpr int JPM = MM / 2;
+  constexpr int TS = comp_tap_slots<GRAD>();
   const int bd = blockDim.x;
   const float ra = load_param_f(dp, 0, i), dec = load_param_f(dp, 1, i);
   const float psi = load_param_f(dp, 2, i), incl = load_param_f(dp, 3, i);
@@ -249,8 +542,9 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
     delay = df_add(delay, df_mul(df{ph.y, pl.y}, S.s[1]));
     delay = df_add(delay, df_mul(df{ph.z, pl.z}, S.s[2]));
     const df tk = df_sub(tc, delay);
+    float2 ep = make_float2(1.f, 0.f);
     const float mx = (C.kind == RIFT_ILE_RESP_ROTATION)
-                         ? rot_coeffs(C, k, S, G, f0a, f0b, tk, cslot, bd)
+                         ? rot_coeffs(C, k, S, G, f0a, f0b, tk, cslot, bd, GRAD ? &ep : nullptr)
                          : arm_coeffs(C, k, S, cslot, bd);
     {
       // heads on the grid 2^(E-8) of the largest component (one step coarser
@@ -268,7 +562,8 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
     }
     const df rel = df_add(tk, df{-ph.w, -pl.w});
     const df u = df_mul(rel, df{C.inv_dt_hi, C.inv_dt_lo});
-    float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f), wd4 = w4;
+    df dhalf = df{0.f, 0.f};
     float nsig = 0.f;
     int jc = -3;  // zero rows: a detector without a finite position adds nothing but NaN
     if (!isfinite(u.hi)) {
@@ -284,6 +579,12 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
         df acc = df{cf.x, cf.y};
 #pragma unroll
         for (int p = kPolyDeg - 1; p >= 0; --p) {
+          if (GRAD) {  // the slope by Horner alongside: d = d f + acc
+            df pr = two_prod(dhalf.hi, f);
+            pr.lo = fmaf(dhalf.lo, f, pr.lo);
+            const df sm3 = two_sum(pr.hi, acc.hi);
+            dhalf = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
+          }
           cf = __ldg(pc + p);
           df pr = two_prod(acc.hi, f);
           pr.lo = fmaf(acc.lo, f, pr.lo);
@@ -297,6 +598,12 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
       w4.y = (fa * fc * fd) * 0.5f;
       w4.z = -(fa * f * fd) * 0.5f;
       w4.w = (fa * f * fc) * (1.f / 6.f);
+      if (GRAD) {  // d wt_i / df
+        wd4.x = -(fc * fd + f * fd + f * fc) * (1.f / 6.f);
+        wd4.y = (fc * fd + fa * fd + fa * fc) * 0.5f;
+        wd4.z = -(f * fd + fa * fd + fa * f) * 0.5f;
+        wd4.w = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
+      }
       const df ws = df_add(two_sum(w4.x, w4.y), two_sum(w4.z, w4.w));
       nsig = -__fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
       const float nb = fminf(fmaxf(1.f - jf, 0.f), 4.f);
@@ -304,9 +611,21 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
       oob += (int)fminf(nb + nab, 4.f);
       jc = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
     }
-    tslot[(size_t)(2 * k) * bd] = w4;
-    tslot[(size_t)(2 * k + 1) * bd] = make_float4(nsig, __int_as_float(jc), 0.f, 0.f);
+    tslot[(size_t)(TS * k) * bd] = w4;
+    tslot[(size_t)(TS * k + 1) * bd] = make_float4(nsig, __int_as_float(jc), dhalf.hi, dhalf.lo);
+    if (GRAD) {
+      // d t_k / d ra = -pos . ds/d ra, d t_k / d dec = -pos . ds/d dec
+      const float sl = S.sl.hi, cl = S.cl.hi, sd = S.sd.hi, cd = S.cd.hi;
+      const float dka = -(ph.x * (-cd * sl) + ph.y * (cd * cl));
+      const float dkd = -(ph.x * (-sd * cl) + ph.y * (-sd * sl) + ph.z * cd);
+      tslot[(size_t)(TS * k + 2) * bd] = wd4;
+      tslot[(size_t)(TS * k + 3) * bd] = make_float4(dka, dkd, 0.f, 0.f);
+      tslot[(size_t)(TS * k + 4) * bd] = make_float4(ep.x, ep.y, 0.f, 0.f);
+      for (int a = 0; a < na; ++a) gs.rho[(size_t)(k * na + a) * bd] = make_float2(0.f, 0.f);
+    }
   }
+  if (GRAD)
+    for (int q = 0; q < JPM; ++q) gs.dy[(size_t)q * bd] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   // ---- harmonics in visiting order j, split: (head on 2^-8, tail with the
   // low part); lanes (j even, j odd) of pair j / 2
@@ -379,8 +698,12 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
       int kd[kCompMixedKG];
 #pragma unroll
       for (int kk = 0; kk < kCompMixedKG; ++kk) kd[kk] = C.det_order[kk < nk ? g0 + kk : g0];
+      float red[kCompMixedKG];  // r . de/du of the group's detectors
+#pragma unroll
+      for (int kk = 0; kk < kCompMixedKG; ++kk) red[kk] = 0.f;
       for (int r0 = 0; r0 < R; r0 += 2) {
         float2 whp[kCompMixedKG][2], wcp[kCompMixedKG][2];
+        float2 rsk[kCompMixedKG];
 #pragma unroll
         for (int kk = 0; kk < kCompMixedKG; ++kk)
           whp[kk][0] = whp[kk][1] = wcp[kk][0] = wcp[kk][1] = make_float2(0.f, 0.f);
@@ -430,6 +753,7 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
             at[h] = __fadd2_rn(sub2(ex, ah[h]), co);
             af[h] = __fadd2_rn(ah[h], at[h]);
           }
+          if (GRAD) gs.af[(size_t)a * bd] = make_float4(af[0].x, af[1].x, af[0].y, af[1].y);
           // w_k += Re C a1 + Im C a2 as lanes (Re, Im): heads exact, tails in FP32
 #pragma unroll
           for (int kk = 0; kk < kCompMixedKG; ++kk) {
@@ -451,8 +775,12 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
         for (int kk = 0; kk < kCompMixedKG; ++kk) {
           if (kk < nk) {
             const int k = kd[kk];
-            const float4 w4 = tslot[(size_t)(2 * k) * bd];
-            const float4 t1 = tslot[(size_t)(2 * k + 1) * bd];
+            const float4 w4 = tslot[(size_t)(TS * k) * bd];
+            const float4 t1 = tslot[(size_t)(TS * k + 1) * bd];
+            float4 wd4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (GRAD) wd4 = tslot[(size_t)(TS * k + 2) * bd];
+            const float wtd[4] = {wd4.x, wd4.y, wd4.z, wd4.w};
+            float2 ed = make_float2(0.f, 0.f);
             const int jc = __float_as_int(t1.y);
             const float2 nhi = make_float2(-__fadd_rn(whp[kk][0].x, whp[kk][0].y),
                                            -__fadd_rn(whp[kk][1].x, whp[kk][1].y));
@@ -469,17 +797,71 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
                                           make_float2(e4.z, e4.w));
               rs = __ffma2_rn(make_float2(wt[tap], wt[tap]), d, rs);
               if (tap == 1) rs = __ffma2_rn(make_float2(t1.x, t1.x), d, rs);
+              if (GRAD) ed = __ffma2_rn(make_float2(wtd[tap], wtd[tap]), d, ed);
             }
             const float2 rsv = __fadd2_rn(rs, nlo);
             q2p = __ffma2_rn(rsv, rsv, q2p);
+            if (GRAD) {
+              rsk[kk] = rsv;
+              red[kk] = fmaf(rsv.x, ed.x, fmaf(rsv.y, ed.y, red[kk]));
+            }
+          } else if (GRAD) {
+            rsk[kk] = make_float2(0.f, 0.f);
           }
         }
+        if (GRAD) {
+          // per response index: rho_(k,a) += (r . a1_a, r . a2_a) and, with
+          // G = sum_k C~'_k r_k, d lnL / d Y += G (t + i b) conj-linear terms:
+          // d/d Re Y_i += G1 t_i + G2 b_i,  d/d Im Y_i += G1 b_i - G2 t_i
+          for (int a = 0; a < na; ++a) {
+            const float4 av = gs.af[(size_t)a * bd];
+            float2 G1 = make_float2(0.f, 0.f), G2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < kCompMixedKG; ++kk) {
+              if (kk < nk) {
+                const size_t e = (size_t)(kd[kk] * na + a) * bd;
+                const float4 cs = cslot[e];
+                const float cre = cs.x + cs.z, cim = cs.y + cs.w;
+                G1 = __ffma2_rn(make_float2(cre, cre), rsk[kk], G1);
+                G2 = __ffma2_rn(make_float2(cim, cim), rsk[kk], G2);
+                float2 rh = gs.rho[e];
+                rh.x = fmaf(rsk[kk].x, av.x, fmaf(rsk[kk].y, av.y, rh.x));
+                rh.y = fmaf(rsk[kk].x, av.z, fmaf(rsk[kk].y, av.w, rh.y));
+                gs.rho[e] = rh;
+              }
+            }
+            const float4* Ba = Bc + (size_t)a * bstride_a;
+            for (int jp = 0; jp < JPM; ++jp) {
+              const float4 y4 = gs.dy[(size_t)jp * bd];
+              float2 dyr = make_float2(y4.x, y4.y), dyi = make_float2(y4.z, y4.w);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const float4 u0 = Ba[(h * JPM + jp) * 3], u1 = Ba[(h * JPM + jp) * 3 + 1];
+                const float4 u2 = Ba[(h * JPM + jp) * 3 + 2];
+                const float2 tf = __fadd2_rn(make_float2(u0.x, u0.y), make_float2(u1.z, u1.w));
+                const float2 bf = __fadd2_rn(make_float2(u0.z, u0.w), make_float2(u2.x, u2.y));
+                const float g1 = h ? G1.y : G1.x, g2 = h ? G2.y : G2.x;
+                dyr = __ffma2_rn(make_float2(g1, g1), tf, dyr);
+                dyr = __ffma2_rn(make_float2(g2, g2), bf, dyr);
+                dyi = __ffma2_rn(make_float2(g1, g1), bf, dyi);
+                dyi = __ffma2_rn(make_float2(-g2, -g2), tf, dyi);
+              }
+              gs.dy[(size_t)jp * bd] = make_float4(dyr.x, dyr.y, dyi.x, dyi.y);
+            }
+          }
+        }
+      }
+      if (GRAD) {
+#pragma unroll
+        for (int kk = 0; kk < kCompMixedKG; ++kk)
+          if (kk < nk) tslot[(size_t)(TS * kd[kk] + 3) * bd].z = red[kk];
       }
     }
   }
   dacc_fma_ff(T, -0.5f, __fadd_rn(q2p.x, q2p.y));
   df out = dacc_result(T);
   if (bad) out = df{CUDART_NAN_F, 0.f};
+  if (GRAD) comp_mixed_grad_tail<MM>(C, comp_sky_f(S), tslot, cslot, gs, incl, phi, bad, gout);
   return out;
 }
 
@@ -490,7 +872,7 @@ __global__ void __launch_bounds__(kCompMixedThreads, 2)
                       unsigned long long* __restrict__ oob_count) {
   extern __shared__ float4 smem4[];
   const size_t nb = BSMEM ? comp_mixed_b_f4(C) : 0, ng = comp_mixed_ag_f4(C);
-  if (BSMEM)
+  if constexpr (BSMEM)
     for (size_t q = threadIdx.x; q < nb; q += blockDim.x) smem4[q] = __ldg(C.Bs + q);
   float* sAG = reinterpret_cast<float*>(smem4 + nb);
   for (size_t q = threadIdx.x; q < (size_t)C.ncls * C.R; q += blockDim.x)
@@ -506,7 +888,8 @@ __global__ void __launch_bounds__(kCompMixedThreads, 2)
     float lw = 0.f;
     if (LSE && dp.logw)
       lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
-    const df l = comp_mixed_draw<MM>(C, B, sAG, cslot, tslot, dp, i, oob);
+    const df l = comp_mixed_draw<MM, false>(C, B, sAG, cslot, tslot, CompGradSlots{}, dp, i, oob,
+                                            nullptr);
     if (LSE)
       tlse_push_lw(st, l, lw);
     else
@@ -519,48 +902,111 @@ __global__ void __launch_bounds__(kCompMixedThreads, 2)
   }
 }
 
+// Resident blocks per SM of a composite mixed kernel at (block size, shared
+// memory), cached per (kernel, device, shape); the kernel's shared-memory
+// attribute is set once to the device's opt-in maximum less its static shared
+// memory.
+template <typename KernelT>
+cudaError_t comp_blocks_per_sm(KernelT kern, int threads, size_t smem, int* per_sm) {
+  struct Entry {
+    const void* fn;
+    int dev, threads, nb;
+    size_t smem;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  static std::vector<std::pair<const void*, int>> attr_set;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const void* fn = reinterpret_cast<const void*>(kern);
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.fn == fn && e.dev == dev && e.threads == threads && e.smem == smem) {
+      *per_sm = e.nb;
+      return cudaSuccess;
+    }
+  bool have_attr = false;
+  for (const auto& a : attr_set) have_attr |= (a.first == fn && a.second == dev);
+  if (!have_attr) {
+    int optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    attr_set.emplace_back(fn, dev);
+  }
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (nb < 1) return cudaErrorInvalidConfiguration;
+  nb = nb < kMaxPartialsPerSM ? nb : kMaxPartialsPerSM;
+  cache.push_back(Entry{fn, dev, threads, nb, smem});
+  *per_sm = nb;
+  return cudaSuccess;
+}
+
 template <int MM, bool BSMEM, bool LSE>
 cudaError_t launch_comp_mixed_k(const CompMixed& C, int threads, const DrawsParams& dp,
                                 double* lnl_out, LseState* partials, unsigned long long* oob,
                                 int* blocks, cudaStream_t st) {
   auto kern = comp_mixed_kernel<MM, BSMEM, LSE>;
   const size_t smem = comp_mixed_smem(C, BSMEM, threads);
-  // the shared-memory attribute (the device's opt-in maximum) once per device,
-  // the occupancy once per (device, shared-memory size, block size)
-  static std::mutex mu;
-  static bool attr_set[64] = {false};
-  static size_t last_smem[64] = {0};
-  static int last_threads[64] = {0}, last_nb[64] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   int per_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!attr_set[dev]) {
-      // the opt-in maximum less the kernel's static shared memory
-      int optin = 0;
-      cudaFuncAttributes fa;
-      cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin - (int)fa.sharedSizeBytes);
-      if (e != cudaSuccess) return e;
-      attr_set[dev] = true;
-    }
-    if (last_nb[dev] == 0 || last_smem[dev] != smem || last_threads[dev] != threads) {
-      int nb = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
-      if (e != cudaSuccess) return e;
-      if (nb < 1) return cudaErrorInvalidConfiguration;
-      last_nb[dev] = nb < kMaxPartialsPerSM ? nb : kMaxPartialsPerSM;
-      last_smem[dev] = smem;
-      last_threads[dev] = threads;
-    }
-    per_sm = last_nb[dev];
-  }
+  const cudaError_t e = comp_blocks_per_sm(kern, threads, smem, &per_sm);
+  if (e != cudaSuccess) return e;
   *blocks = grid_cap(device_sms() * per_sm, dp.n, threads);
   kern<<<*blocks, threads, smem, st>>>(C, dp, lnl_out, partials, oob);
+  return cudaGetLastError();
+}
+
+// lnL (when lnl_out is non-NULL) and its gradient, grad_out[7][n]; the slots
+// of comp_mixed_thread_f4(C, true) per thread after the coefficient and tap
+// slots.
+template <int MM, bool BSMEM>
+__global__ void __launch_bounds__(kCompMixedThreads, 2)
+    comp_mixed_grad_kernel(const __grid_constant__ CompMixed C, DrawsParams dp,
+                           double* __restrict__ lnl_out, double* __restrict__ grad_out) {
+  extern __shared__ float4 smem4[];
+  const size_t nb = BSMEM ? comp_mixed_b_f4(C) : 0, ng = comp_mixed_ag_f4(C);
+  if constexpr (BSMEM)
+    for (size_t q = threadIdx.x; q < nb; q += blockDim.x) smem4[q] = __ldg(C.Bs + q);
+  float* sAG = reinterpret_cast<float*>(smem4 + nb);
+  for (size_t q = threadIdx.x; q < (size_t)C.ncls * C.R; q += blockDim.x)
+    sAG[q] = __ldg(C.agrid + q);
+  __syncthreads();
+  const float4* B = BSMEM ? smem4 : C.Bs;
+  const size_t bd = blockDim.x, kna = (size_t)C.K * C.na;
+  float4* cslot = smem4 + nb + ng + threadIdx.x;
+  float4* tslot = cslot + kna * bd;
+  float4* gbase = smem4 + nb + ng + (kna + (size_t)comp_tap_slots<true>() * C.K) * bd;
+  CompGradSlots gs;
+  gs.rho = reinterpret_cast<float2*>(gbase) + threadIdx.x;
+  gs.af = gbase + ((kna + 1) / 2) * bd + threadIdx.x;
+  gs.dy = gs.af + (size_t)C.na * bd;
+  int oob = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
+    double g[kNpar];
+    const df l = comp_mixed_draw<MM, true>(C, B, sAG, cslot, tslot, gs, dp, i, oob, g);
+    if (lnl_out) lnl_out[i] = (double)l.hi + (double)l.lo;
+#pragma unroll
+    for (int p = 0; p < kNpar; ++p) grad_out[(size_t)p * dp.n + i] = g[p];
+  }
+}
+
+template <int MM, bool BSMEM>
+cudaError_t launch_comp_mixed_grad_k(const CompMixed& C, int threads, const DrawsParams& dp,
+                                     double* lnl_out, double* grad_out, cudaStream_t st) {
+  auto kern = comp_mixed_grad_kernel<MM, BSMEM>;
+  const size_t smem = comp_mixed_smem(C, BSMEM, threads, true);
+  int per_sm = 0;
+  const cudaError_t e = comp_blocks_per_sm(kern, threads, smem, &per_sm);
+  if (e != cudaSuccess) return e;
+  const int blocks = grid_cap(device_sms() * per_sm, dp.n, threads);
+  kern<<<blocks, threads, smem, st>>>(C, dp, lnl_out, grad_out);
   return cudaGetLastError();
 }
 
@@ -580,9 +1026,20 @@ cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, const Dr
                : launch_comp_mixed_k<MM, false, false>(C, threads, dp, lnl_out, partials, oob, blocks, st);
 }
 
+// The adjoint's entry point of one bucket (launch shape chosen by the build
+// for comp_mixed_smem(C, bsmem, threads, true)).
+template <int MM>
+cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
+                            double* lnl_out, double* grad_out, cudaStream_t st) {
+  return bsmem ? launch_comp_mixed_grad_k<MM, true>(C, threads, dp, lnl_out, grad_out, st)
+               : launch_comp_mixed_grad_k<MM, false>(C, threads, dp, lnl_out, grad_out, st);
+}
+
 #define RIFT_INSTANTIATE_COMP_MIXED(MM)                                                        \
   template cudaError_t comp_mixed_lnl<MM>(const CompMixed&, bool, int, const DrawsParams&,      \
                                           double*, LseState*, unsigned long long*, int*,         \
-                                          cudaStream_t);
+                                          cudaStream_t);                                         \
+  template cudaError_t comp_mixed_grad<MM>(const CompMixed&, bool, int, const DrawsParams&,     \
+                                           double*, double*, cudaStream_t);
 
 }  // namespace rift

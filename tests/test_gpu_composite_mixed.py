@@ -17,6 +17,10 @@ against the composite oracle:
   tables;
 * ragged draw counts, float32 draws, out-of-table taps (counted as the FP64
   path counts them), a non-finite arrival time (NaN), the empty draw set;
+* the adjoint (rift_ile_comp_lnL_grad_mixed): lnL as the forward gives it, and
+  each gradient component against the oracle's chain rule within TOL_G of
+  |g| + RMS g (the terms that multiply the residual are FP32); NaN rows for a
+  non-finite arrival time; the empty draw set;
 * calls before the build, and tol outside (0, 1), are errors;
 * on the 3G network at full size (2^22 draws, the bench's launch), sampled
   draws against the oracle and the fused lnZ against the FP64 path's.
@@ -41,6 +45,7 @@ TOL_Z = 1e-5      # nat
 EIG_TOL = 1e-14
 # (near, far) for the stress-rate Path B fixture
 TOL_CASE = {(WC.ROTATION, 1): (1e-3, 1e-2)}
+TOL_G = 1e-4     # gradient, relative to |g| + RMS g over the draws
 
 
 @pytest.fixture(scope="module")
@@ -93,6 +98,41 @@ def test_mixed_lnl_and_lnz_match_oracle(R, kind, p_max):
     assert abs(z[2] - zr[2]) <= 1e-3 * zr[2]
     st = R.rift_ile_comp_lnZ_state_mixed_async(cp, d).cpu().numpy()
     assert np.array_equal(st, np.array(R.rift_ile_comp_lnZ_state_mixed(cp, d)))
+
+
+@pytest.mark.parametrize("kind,p_max", CASES)
+def test_mixed_gradient_matches_oracle(R, kind, p_max):
+    point, draws, logw, ref = fixture(kind, p_max)
+    n = 160
+    sub = {p: np.asarray(draws[p])[:n] for p in W.PARAMS}
+    cp = R.CompPoint(point)
+    R.rift_ile_comp_mixed_build(cp, EIG_TOL)
+    lnl, g = R.rift_ile_comp_lnL_grad_mixed(cp, R.Draws(sub))
+    lnl, g = lnl.cpu().numpy(), g.cpu().numpy()
+    fwd = R.rift_ile_comp_lnL_mixed(cp, R.Draws(sub)).cpu().numpy()
+    assert np.max(np.abs(lnl - fwd)) <= 1e-12 * np.max(np.abs(fwd))
+    ref_l, ref_g = OC.lnL_grad(OC.CompPoint(point), sub)
+    for j, p in enumerate(W.PARAMS):
+        s = np.abs(ref_g[:, j]) + np.sqrt(np.mean(ref_g[:, j] ** 2))
+        err = np.max(np.abs(g[j] - ref_g[:, j]) / s)
+        assert err <= TOL_G, (p, err)
+
+
+def test_mixed_gradient_nonfinite_empty_and_errors(R):
+    point, draws, logw, ref = fixture(WC.FINITE_ARM, 3)
+    cp = R.CompPoint(point)
+    bad = {p: np.asarray(draws[p])[:8].copy() for p in W.PARAMS}
+    bad["t"][3] = np.nan
+    with pytest.raises(R.RiftError):
+        R.rift_ile_comp_lnL_grad_mixed(cp, R.Draws(bad))
+    R.rift_ile_comp_mixed_build(cp, EIG_TOL)
+    lnl, g = R.rift_ile_comp_lnL_grad_mixed(cp, R.Draws(bad))
+    lnl, g = lnl.cpu().numpy(), g.cpu().numpy()
+    assert np.isnan(lnl[3]) and np.all(np.isnan(g[:, 3]))
+    assert np.all(np.isfinite(np.delete(lnl, 3))) and np.all(np.isfinite(np.delete(g, 3, axis=1)))
+    empty = {p: np.zeros(0) for p in W.PARAMS}
+    lnl, g = R.rift_ile_comp_lnL_grad_mixed(cp, R.Draws(empty))
+    assert lnl.numel() == 0 and tuple(g.shape) == (7, 0)
 
 
 def test_width_follows_tol_and_rebuild(R):
@@ -193,6 +233,26 @@ def test_full_size_path_a_sampled(R, big):
     zm = R.rift_ile_comp_lnZ_mixed(cp, d)
     zf = R.rift_ile_comp_lnZ(cp, d)
     assert abs(zm[0] - zf[0]) <= TOL_Z
+
+
+def test_full_size_path_a_gradient_vs_fp64(R, big):
+    """3G network, ten modes, Path A: the adjoint of the first 2^20 draws
+    against the FP64 adjoint (itself pinned to the oracle), every component
+    within TOL_G of |g| + RMS g for the draws within 50 nat of the best."""
+    point, exact, info, draws, logw = big
+    n = 1 << 20
+    sub = {p: np.asarray(draws[p])[:n] for p in W.PARAMS}
+    cp = R.CompPoint(point)
+    R.rift_ile_comp_mixed_build(cp, EIG_TOL)
+    d = R.Draws(sub)
+    lm, gm = R.rift_ile_comp_lnL_grad_mixed(cp, d)
+    lf, gf = R.rift_ile_comp_lnL_grad(cp, d)
+    near = lf > lf.max() - 50.0
+    assert int(near.sum()) > 100
+    for j, p in enumerate(W.PARAMS):
+        s = gf[j].abs() + gf[j][near].pow(2).mean().sqrt()
+        err = float(((gm[j] - gf[j]).abs() / s)[near].max())
+        assert err <= TOL_G, (p, err)
 
 
 @pytest.mark.parametrize("kind,p_max,tol_near", [(WC.ROTATION, 1, 5e-4), (WC.FINITE_ARM, 3, 1e-4)])
