@@ -1170,8 +1170,21 @@ cudaError_t launch_warp_k(const PointParams& hp, const DrawsParams& dp, double* 
   const long long need = (dp.n + kWarpDrawsPerBlock - 1) / kWarpDrawsPerBlock;
   const long long cap = (long long)device_sms() * cached_blocks_per_sm(kern, 32 * kWarpDrawWarps, smem);
   const int blocks = (int)(need < cap ? need : cap);
-  kern<<<blocks, 32 * kWarpDrawWarps, smem, st>>>(hp, dp, lnl_out, grad_out);
-  return cudaGetLastError();
+  // with programmatic stream serialisation: the kernel's prologue (the
+  // point's image into shared memory) overlaps the previous kernel, which
+  // matters in a chain of sampler calls; the kernel waits for that kernel
+  // (griddepcontrol.wait) before it reads the draws or writes anything
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(32 * kWarpDrawWarps);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, hp, dp, lnl_out, grad_out);
 }
 
 // Serves lnL (GRAD false) or lnL and its gradient with one warp per draw when

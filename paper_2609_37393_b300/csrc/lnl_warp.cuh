@@ -247,6 +247,13 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
                    : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
+  // programmatic dependent launch (the host launches this kernel with it):
+  // the point's image and parameters are immutable once the point exists, so
+  // the copies above may overlap the previous kernel in the stream; the draws
+  // (possibly that kernel's output) are read, and the outputs written, only
+  // after it has completed.  The next kernel may likewise begin its prologue.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const float4* sA = smem4;
   const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
   const MixedTables& T = *reinterpret_cast<const MixedTables*>(

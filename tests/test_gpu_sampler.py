@@ -8,6 +8,8 @@ both kernels are run here on the same draws:
   8192 draws: lnL within 1e-3 nat of the FP64 oracle on draws within 50 nat
   of the best, every gradient component within 1e-4 of |g| + RMS g there, and
   within rounding of the one-thread-per-draw kernel;
+* chained calls (programmatic dependent launch) reading draws that the
+  kernel before them wrote, eagerly and in a CUDA graph;
 * forward-only lnL, the full-event network (K=5, two detector classes,
   wider whitened width), odd mode counts, a NaN draw and draws whose taps
   leave the table, an empty batch.
@@ -151,3 +153,60 @@ def test_warp_kernel_empty_batch(R, cfg2):
     pt = R.Point(point)
     lw, gw = run(R, pt, sub(draws, 0), warp=True)
     assert lw.shape == (0,) and gw.shape == (0, 7)
+
+
+def test_chained_calls_see_their_predecessors_writes(R, cfg2):
+    """The warp kernel is launched with programmatic stream serialisation: its
+    prologue may overlap the previous kernel, but it reads the draws and
+    writes its outputs only after that kernel completes.  Eight calls, each
+    preceded by a copy kernel that writes its draws into the same buffers and
+    all writing the same output buffers, eagerly and captured in one CUDA
+    graph: each call's result equals the same call made alone."""
+    point, exact, info, draws, logw = cfg2
+    pt = R.Point(point)
+    n = 128
+    sets = [{p: torch.tensor(np.asarray(draws[p])[n * s:n * (s + 1)], dtype=torch.float64,
+                             device="cuda") for p in W.PARAMS} for s in range(8)]
+    R.rift_ile_set_small_batch(1 << 20)
+    try:
+        alone = [R.rift_ile_lnL_grad(pt, R.Draws(s), R.FP32_MIXED) for s in sets]
+        buf = {p: torch.empty(n, dtype=torch.float64, device="cuda") for p in W.PARAMS}
+        d = R.Draws(buf)
+        lnl = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty((7, n), dtype=torch.float64, device="cuda")
+        keep_l = torch.empty((8, n), dtype=torch.float64, device="cuda")
+        keep_g = torch.empty((8, 7, n), dtype=torch.float64, device="cuda")
+
+        def chain():
+            for s in range(8):
+                for p in W.PARAMS:
+                    buf[p].copy_(sets[s][p])
+                R.rift_ile_lnL_grad(pt, d, R.FP32_MIXED, lnl, g)
+                keep_l[s].copy_(lnl)
+                keep_g[s].copy_(g)
+
+        def check():
+            torch.cuda.synchronize()
+            for s in range(8):
+                assert torch.equal(keep_l[s], alone[s][0]), s
+                assert torch.equal(keep_g[s], alone[s][1]), s
+
+        chain()
+        check()
+        keep_l.zero_()
+        keep_g.zero_()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            chain()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            chain()
+        keep_l.zero_()
+        keep_g.zero_()
+        graph.replay()
+        check()
+    finally:
+        R.rift_ile_set_small_batch(4096)
