@@ -299,9 +299,14 @@ int rift_ile_lnZ_batch(const rift_ile_point* const* pts, const rift_ile_draws* d
  * which cuts the latency of a small batch, the regime of a gradient-based
  * extrinsic sampler (App. H of the paper: tens to thousands of draws per
  * call).  Larger batches use the one-thread-per-draw kernels, whose
- * throughput is higher.  The two agree to rounding.  Default 2048; 0
- * disables the warp kernel.  Process-wide; returns the previous value.  Host
- * only, no GPU call. */
+ * throughput is higher.  The two agree to rounding.  The warp-pair kernel is
+ * launched with programmatic stream serialisation: its prologue (the point's
+ * tables into shared memory) may overlap the previous kernel in the stream,
+ * and it reads the draws and writes its outputs only after that kernel has
+ * completed; it lets the next kernel in the stream do the same (a kernel
+ * launched after it with that attribute must itself wait before reading its
+ * outputs).  Default 2048; 0 disables the warp kernel.  Process-wide; returns
+ * the previous value.  Host only, no GPU call. */
 int64_t rift_ile_set_small_batch(int64_t max_draws);
 
 /* Number of Q taps that fell outside their tables in the last completed
