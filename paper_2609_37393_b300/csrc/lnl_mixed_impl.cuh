@@ -123,7 +123,7 @@ void sincos_df(df a, df& s_out, df& c_out) {
   float k = rintf(a.hi * 0.159154943091895336f);
   df kp = two_prod(k, kTwoPiHi);
   kp.lo = fmaf(k, kTwoPiLo, kp.lo);
-  df r = df_add(a, df_neg(kp));
+  df r = df_sub_reduce(a, kp);
   int j = __float2int_rn(r.hi * kAnchorInvStep);
   j = max(-kAnchorHalf, min(kAnchorHalf, j));
   const float dh = __fsub_rn(r.hi, (float)j * kAnchorStep);  // exact
@@ -153,7 +153,7 @@ RIFT_HELPER df exp_df(df a) {
   float k = rintf(a.hi * 1.44269504088896341f);
   df kp = two_prod(k, kLn2Hi);
   kp.lo = fmaf(k, kLn2Lo, kp.lo);
-  df r = df_add(a, df_neg(kp));
+  df r = df_sub_reduce(a, kp);
   int j = __float2int_rn(r.hi * 128.f);
   j = max(-kExpHalf, min(kExpHalf, j));
   const float dh = __fsub_rn(r.hi, (float)j * (1.f / 128.f));

@@ -140,9 +140,9 @@ __device__ __forceinline__ void sincos_df_notable(df a, df& s_out, df& c_out) {
   const float k = rintf(a.hi * 0.159154943091895336f);
   df kp = two_prod(k, kTwoPiHi);
   kp.lo = fmaf(k, kTwoPiLo, kp.lo);
-  const df r = df_add(a, df_neg(kp));
+  const df r = df_sub_reduce(a, kp);
   const float q = rintf(r.hi * 0.636619772367581343f);  // -2..2
-  const df d = df_add(r, df{-q * kHalfPiHi, -q * kHalfPiLo});  // q pi/2 exact in the pair
+  const df d = df_sub_reduce(r, df{q * kHalfPiHi, q * kHalfPiLo});  // q pi/2 exact in the pair
   df u = two_prod(d.hi, d.hi);
   u.lo = fmaf(2.f * d.hi, d.lo, u.lo);
   u = fast_two_sum(u.hi, u.lo);
@@ -193,7 +193,7 @@ __device__ __forceinline__ df exp_df_notable(df a) {
   const float k = rintf(a.hi * 1.44269504088896341f);
   df kp = two_prod(k, kLn2Hi);
   kp.lo = fmaf(k, kLn2Lo, kp.lo);
-  const df r = df_add(a, df_neg(kp));
+  const df r = df_sub_reduce(a, kp);
   const float rh = r.hi;
   constexpr double e5 = 1.0 / 120, e6 = 1.0 / 720, e7 = 1.0 / 5040, e8 = 1.0 / 40320,
                    e9 = 1.0 / 362880, e10 = 1.0 / 3628800, e11 = 1.0 / 39916800,
