@@ -538,9 +538,7 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
   bool bad = false;
   for (int k = 0; k < K; ++k) {
     const float4 ph = C.pos_hi[k], pl = C.pos_lo[k];
-    df delay = df_mul(df{ph.x, pl.x}, S.s[0]);
-    delay = df_add(delay, df_mul(df{ph.y, pl.y}, S.s[1]));
-    delay = df_add(delay, df_mul(df{ph.z, pl.z}, S.s[2]));
+    const df delay = dot3_df(ph, pl, S.s[0], S.s[1], S.s[2]);
     const df tk = df_sub(tc, delay);
     float2 ep = make_float2(1.f, 0.f);
     const float mx = (C.kind == RIFT_ILE_RESP_ROTATION)
@@ -579,17 +577,9 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
         df acc = df{cf.x, cf.y};
 #pragma unroll
         for (int p = kPolyDeg - 1; p >= 0; --p) {
-          if (GRAD) {  // the slope by Horner alongside: d = d f + acc
-            df pr = two_prod(dhalf.hi, f);
-            pr.lo = fmaf(dhalf.lo, f, pr.lo);
-            const df sm3 = two_sum(pr.hi, acc.hi);
-            dhalf = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
-          }
+          if (GRAD) dhalf = horner_step_f(dhalf, f, acc.hi, acc.lo);  // the slope: d f + acc
           cf = __ldg(pc + p);
-          df pr = two_prod(acc.hi, f);
-          pr.lo = fmaf(acc.lo, f, pr.lo);
-          const df sm2 = two_sum(pr.hi, cf.x);
-          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf.y));
+          acc = horner_step_f(acc, f, cf.x, cf.y);
         }
         dacc_add(T, acc);
       }
@@ -665,12 +655,9 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
         df acc = df{c.x, c.y};
         for (int q = l - 1; q >= 0; --q) {
           c = C.yz[j][q];
-          df pr = two_prod(acc.hi, z.hi);
-          pr.lo = fmaf(acc.hi, z.lo, fmaf(acc.lo, z.hi, pr.lo));
-          const df sm2 = two_sum(pr.hi, c.x);
-          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), c.y));
+          acc = horner_step(acc, z, c.x, c.y);
         }
-        const df amp = md.w ? df_mul(acc, sz) : acc;
+        const df amp = md.w ? df_mul(acc, sz) : fast_two_sum(acc.hi, acc.lo);
         const df yr = df_mul(amp, cm);
         const df yi = m < 0 ? df_neg(df_mul(amp, sm)) : df_mul(amp, sm);
         float yr1, yr2, yi1, yi2;

@@ -208,22 +208,50 @@ __device__ __forceinline__ void stage_tables(const PointParams& P, MixedTables& 
   }
 }
 
+// One double-float Horner step acc x + c: the product and the sum of the high
+// parts exact, the low parts added in FP32, the result left unnormalised (after
+// cancellation its low part can exceed half an ulp of the high part; the next
+// step takes acc.lo through an FMA, so the absolute error stays at
+// u^2 |terms| and only the final value needs normalising, if at all).
+__device__ __forceinline__ df horner_step(df acc, df x, float ch, float cl) {
+  df pr = two_prod(acc.hi, x.hi);
+  pr.lo = fmaf(acc.hi, x.lo, fmaf(acc.lo, x.hi, pr.lo));
+  const df sm = two_sum(pr.hi, ch);
+  return df{sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), cl)};
+}
+
+// The same with x a float (no low part).
+__device__ __forceinline__ df horner_step_f(df acc, float x, float ch, float cl) {
+  df pr = two_prod(acc.hi, x);
+  pr.lo = fmaf(acc.lo, x, pr.lo);
+  const df sm = two_sum(pr.hi, ch);
+  return df{sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), cl)};
+}
+
 // The real amplitude of -2Y_lm(iota, 0) of the mode visited j-th (degree l,
 // parity par) in double-float from z = cos(iota) and sz = sin(iota):
-// sz^par sum_q yz[q] z^q by Horner, each
-// step an exact product of the high parts and an exact sum with the
-// coefficient's high part.
+// sz^par sum_q yz[q] z^q by Horner (horner_step), normalised at the end.
 RIFT_HELPER df sylm_amp_df(const MixedTables& T, int j, int l, int par, df z, df sz) {
   float2 c = T.yz[j][l];
   df acc = df{c.x, c.y};
   for (int q = l - 1; q >= 0; --q) {
     c = T.yz[j][q];
-    df pr = two_prod(acc.hi, z.hi);
-    pr.lo = fmaf(acc.hi, z.lo, fmaf(acc.lo, z.hi, pr.lo));
-    const df sm = two_sum(pr.hi, c.x);
-    acc = fast_two_sum(sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), c.y));
+    acc = horner_step(acc, z, c.x, c.y);
   }
-  return par ? df_mul(acc, sz) : acc;
+  return par ? df_mul(acc, sz) : fast_two_sum(acc.hi, acc.lo);
+}
+
+// pos . s for a position (hi, lo vectors) and a direction of pairs: the three
+// high products exact and summed by TwoSum, every low term once in FP32
+// (absolute error ~u^2 |pos|).
+__device__ __forceinline__ df dot3_df(float4 ph, float4 pl, df s0, df s1, df s2) {
+  const df p0 = two_prod(ph.x, s0.hi), p1 = two_prod(ph.y, s1.hi), p2 = two_prod(ph.z, s2.hi);
+  const df a = two_sum(p0.hi, p1.hi), b = two_sum(a.hi, p2.hi);
+  float lo = __fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, __fadd_rn(a.lo, b.lo)));
+  lo = fmaf(ph.x, s0.lo, fmaf(pl.x, s0.hi, lo));
+  lo = fmaf(ph.y, s1.lo, fmaf(pl.y, s1.hi, lo));
+  lo = fmaf(ph.z, s2.lo, fmaf(pl.z, s2.hi, lo));
+  return fast_two_sum(b.hi, lo);
 }
 
 // Complex product of pairs.
@@ -698,11 +726,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const df xFr = df{__fadd_rn(xrh, xrt), 0.f}, xFi = df{__fadd_rn(xih, xit), 0.f};  // FP32 uses
       // arrival time (shared by co-located detectors) and table position
       const float4 ph = TB.pos_hi[k], pl = TB.pos_lo[k];  // (position, t0) pairs
-      if (!P.same_pos_prev[q]) {
-        delay = df_mul(df{ph.x, pl.x}, s0);
-        delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
-        delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
-      }
+      if (!P.same_pos_prev[q]) delay = dot3_df(ph, pl, s0, s1, s2);
       const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
       const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
       if (!isfinite(u.hi)) {
@@ -723,18 +747,11 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         df dacc_p = df{0.f, 0.f};
 #pragma unroll
         for (int p = kPolyDeg - 1; p >= 0; --p) {
-          if (GRAD) {  // slope: d = d f + acc
-            df pr = two_prod(dacc_p.hi, f);
-            pr.lo = fmaf(dacc_p.lo, f, pr.lo);
-            const df sm3 = two_sum(pr.hi, acc.hi);
-            dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
-          }
-          // acc = acc f + c_p: exact product and sum of the high parts
+          // acc = acc f + c_p and, for the adjoint, the slope d = d f + acc
+          // (horner_step, f exact in FP32; both sums absorb unnormalised pairs)
+          if (GRAD) dacc_p = horner_step_f(dacc_p, f, acc.hi, acc.lo);
           cf = __ldg(pc + p);
-          df pr = two_prod(acc.hi, f);
-          pr.lo = fmaf(acc.lo, f, pr.lo);
-          const df sm2 = two_sum(pr.hi, cf.x);
-          acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf.y));
+          acc = horner_step_f(acc, f, cf.x, cf.y);
         }
         half_e2 = acc;
         dhalf = dacc_p;

@@ -108,12 +108,9 @@ __device__ __forceinline__ df sylm_amp_df_unrolled(const MixedTables& T, int j, 
       started = true;
       continue;
     }
-    df pr = two_prod(acc.hi, z.hi);
-    pr.lo = fmaf(acc.hi, z.lo, fmaf(acc.lo, z.hi, pr.lo));
-    const df sm = two_sum(pr.hi, cq[q].x);
-    acc = fast_two_sum(sm.hi, __fadd_rn(__fadd_rn(pr.lo, sm.lo), cq[q].y));
+    acc = horner_step(acc, z, cq[q].x, cq[q].y);
   }
-  return par ? df_mul(acc, sz) : acc;
+  return par ? df_mul(acc, sz) : fast_two_sum(acc.hi, acc.lo);
 }
 
 // Sine and cosine of a double-float angle without a table, for the
@@ -339,9 +336,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       const int k = lane;
       ph = T.pos_hi[k];
       pl = T.pos_lo[k];
-      df delay = df_mul(df{ph.x, pl.x}, s0);
-      delay = df_add(delay, df_mul(df{ph.y, pl.y}, s1));
-      delay = df_add(delay, df_mul(df{ph.z, pl.z}, s2));
+      const df delay = dot3_df(ph, pl, s0, s1, s2);
       const df rel = df_add(df_sub(tc, delay), df{-ph.w, -pl.w});
       const df u = df_mul(rel, df{P.inv_dt_hi, P.inv_dt_lo});
       bad = isfinite(u.hi) ? 0 : 1;
@@ -506,16 +501,8 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
           df dacc_p = df{0.f, 0.f};
   #pragma unroll
           for (int p = kPolyDeg - 1; p >= 0; --p) {
-            if (GRAD) {
-              df pr = two_prod(dacc_p.hi, f);
-              pr.lo = fmaf(dacc_p.lo, f, pr.lo);
-              const df sm3 = two_sum(pr.hi, acc.hi);
-              dacc_p = fast_two_sum(sm3.hi, __fadd_rn(__fadd_rn(pr.lo, sm3.lo), acc.lo));
-            }
-            df pr = two_prod(acc.hi, f);
-            pr.lo = fmaf(acc.lo, f, pr.lo);
-            const df sm2 = two_sum(pr.hi, cf[p].x);
-            acc = fast_two_sum(sm2.hi, __fadd_rn(__fadd_rn(pr.lo, sm2.lo), cf[p].y));
+            if (GRAD) dacc_p = horner_step_f(dacc_p, f, acc.hi, acc.lo);
+            acc = horner_step_f(acc, f, cf[p].x, cf[p].y);
           }
           half_e2 = acc;
           dhalf = dacc_p;
