@@ -756,44 +756,26 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         half_e2 = acc;
         dhalf = dacc_p;
       }
-      // residual e - w = sum_i wt_i (e_i - w) - sigma (e_j - w) with FP32
-      // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
-      // weights' sum: sum_i wt_i e_i = e + sigma e_j + O(u |e_i - e_j|)
-      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
-      float wt[4];
-      wt[0] = -(f * fc * fd) * (1.f / 6.f);
-      wt[1] = (fa * fc * fd) * 0.5f;
-      wt[2] = -(fa * f * fd) * 0.5f;
-      wt[3] = (fa * f * fc) * (1.f / 6.f);
-      const df ws = df_add(two_sum(wt[0], wt[1]), two_sum(wt[2], wt[3]));
-      const float sigma = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
-      // derivative weights (adjoint only): d wt_i / df
-      float wtd[4] = {0.f, 0.f, 0.f, 0.f};
-      if (GRAD) {
-        wtd[0] = -(fc * fd + f * fd + f * fc) * (1.f / 6.f);
-        wtd[1] = (fc * fd + fa * fd + fa * fc) * 0.5f;
-        wtd[2] = -(f * fd + fa * fd + fa * f) * 0.5f;
-        wtd[3] = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
-      }
-      // taps j-1 .. j+2 read the zero-padded table with j clamped to
-      // [-3, n + 1]: every tap outside the table lands on a zero row, so
-      // the loads need no test (taps outside are only counted)
-      const float2* Ek = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * R;
+      // the interval's cubic: j clamped to [-3, n + 1], where every tap
+      // outside the table is a zero row of the padded table the coefficients
+      // were formed from, so the loads need no test (taps outside are only
+      // counted)
       {  // taps outside the table: 1 - j below it, j + 3 - n above it (each in [0, 4])
         const float nb = fminf(fmaxf(1.f - jf, 0.f), 4.f);
         const float na = fminf(fmaxf(jf + 3.f - (float)n, 0.f), 4.f);
         oob += (int)fminf(nb + na, 4.f);
       }
       const int jc = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-      const float2* Ej = Ek + (ptrdiff_t)(jc - 1) * R;
+      const float4* Cj = P.ecub + ((size_t)k * (n + 5) + (size_t)(jc + 3)) * (size_t)(R / 2) * 3;
+      const float2 f2 = make_float2(f, f), f3 = make_float2(3.f * f, 3.f * f);
       // Per pair of directions: the template w_r = xFr a1_r + xFi a2_r (heads
       // of xF on the grid of its larger part; head x head products of 10 x 10
       // bits and their sum exact, the cross terms >= 2^8 smaller; w kept as
       // the unnormalised pair (exact head sum, FP32 correction)), then the
-      // residual r = e - w = sum_i wt_i (e_i - w) - sigma (e_j - w) with FP32
-      // weights wt_i and sigma = sum_i wt_i - 1, their excess over the exact
-      // weights' sum, the low part of w taken out of the taps and subtracted
-      // once (the weights with sigma removed sum to one).
+      // residual r = e(f) - w = (c0.hi - w_head) + (c0.lo + f (c1 + f (c2 + f c3)))
+      // - w_tail: the tap row's high part meets the exact head sum of w first
+      // (the large terms cancel there), the cubic's f-dependent part and the
+      // low parts are FP32 (rounding u |e_i - e_j| as with FP32 tap weights).
       // Both directions of a pair advance together in packed FP32 pairs
       // (FFMA2 / FADD2 / FMUL2 issue two operations each).  The template is
       // formed negated, nw = -w (negation is exact, so every rounding is the
@@ -801,13 +783,6 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const float2 nxrh = make_float2(-xrh, -xrh), nxrt = make_float2(-xrt, -xrt);
       const float2 nxih = make_float2(-xih, -xih), nxit = make_float2(-xit, -xit);
       const float2 xFr2 = make_float2(xFr.hi, xFr.hi), xFi2 = make_float2(xFi.hi, xFi.hi);
-      float2 wt2[4], wtd2[4];
-#pragma unroll
-      for (int tap = 0; tap < 4; ++tap) {
-        wt2[tap] = make_float2(wt[tap], wt[tap]);
-        wtd2[tap] = make_float2(wtd[tap], wtd[tap]);
-      }
-      const float2 nsig = make_float2(-sigma, -sigma);
       const float2 zero2 = make_float2(0.f, 0.f);
       float2 q2p = zero2, nulp = zero2, redp = zero2, g1p = zero2, g2p = zero2, g1Bp = zero2,
              g2Bp = zero2;
@@ -825,18 +800,19 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
           nlo = __ffma2_rn(nxit, a2h, nlo);
           nlo = __ffma2_rn(nxit, a2t, nlo);
           const float2 nhi = __ffma2_rn(nxrh, a1h, __fmul2_rn(nxih, a2h));
-          float2 rs = zero2, ed = zero2;
-#pragma unroll
-          for (int tap = 0; tap < 4; ++tap) {
-            // rows hold R directions in pairs: (hi_r, hi_r+1, lo_r, lo_r+1)
-            const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + tap * R + r));
-            const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
-                                        make_float2(e4.z, e4.w));
-            rs = __ffma2_rn(wt2[tap], d, rs);
-            if (tap == 1) rs = __ffma2_rn(nsig, d, rs);  // sigma is ~1 ulp of wt: applied apart
-            if (GRAD) ed = __ffma2_rn(wtd2[tap], d, ed);  // dt edot = sum_i wtd_i (e_i - w)
-          }
-          const float2 rsv = __fadd2_rn(rs, nlo);
+          // (c0 hi, c0 lo) of directions r, r + 1, then (c1, c2), (c3, -)
+          const float4 c0 = __ldg(Cj + 3 * (r / 2)), c12 = __ldg(Cj + 3 * (r / 2) + 1);
+          const float4 c3v = __ldg(Cj + 3 * (r / 2) + 2);
+          const float2 c1 = make_float2(c12.x, c12.y), c2 = make_float2(c12.z, c12.w);
+          const float2 c3 = make_float2(c3v.x, c3v.y);
+          float2 hp = __ffma2_rn(c3, f2, c2);
+          hp = __ffma2_rn(hp, f2, c1);
+          const float2 tl = __ffma2_rn(hp, f2, make_float2(c0.z, c0.w));
+          const float2 d0 = __fadd2_rn(make_float2(c0.x, c0.y), nhi);
+          const float2 rsv = __fadd2_rn(__fadd2_rn(d0, tl), nlo);
+          // the adjoint's de/df = c1 + f (2 c2 + 3 f c3)
+          float2 ed = zero2;
+          if (GRAD) ed = __ffma2_rn(__ffma2_rn(c3, f3, __fadd2_rn(c2, c2)), f2, c1);
           q2p = __ffma2_rn(rsv, rsv, q2p);
           const float2 nwf = __fadd2_rn(nhi, nlo);  // -w rounded to FP32
           // gm1 is zero unless the class keeps near-null directions: the

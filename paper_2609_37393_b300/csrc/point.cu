@@ -226,6 +226,50 @@ __global__ void whiten_kernel(const double* __restrict__ proj, const double* __r
   }
 }
 
+// The interpolating cubic of each interval j = -3..n+1 (taps j-1..j+2 of the
+// zero-padded table): e(f) = c0 + c1 f + c2 f^2 + c3 f^3 with, for the tap
+// values e_{-1}, e_0, e_1, e_2 (nodes -1, 0, 1, 2),
+//   c0 = e_0,  c1 = -e_{-1}/3 - e_0/2 + e_1 - e_2/6,  c2 = e_{-1}/2 - e_0 + e_1/2,
+//   c3 = -e_{-1}/6 + e_0/2 - e_1/2 + e_2/6
+// (the monomial coefficients of the four Lagrange cubics), formed in FP64 from
+// the (hi, lo) rows; c0 is copied as its (hi, lo) pair, c1..c3 rounded to FP32
+// (their rounding is of the order of the FP32 tap weights' in the four-tap
+// sum they replace).  Entry ((k (n + 5) + j + 3) (R/2) + p) 3 + {0, 1, 2} for
+// direction pair p: (c0 hi r, c0 hi r+1, c0 lo r, c0 lo r+1), (c1 r, c1 r+1,
+// c2 r, c2 r+1), (c3 r, c3 r+1, 0, 0).
+__global__ void cubic_table_kernel(const float2* __restrict__ ehat, int K, int n, int R,
+                                   float4* __restrict__ ecub) {
+  const int NP = R / 2, per = n + 5;
+  const long long total = (long long)K * per * NP;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(idx % NP);
+    const long long kq = idx / NP;
+    const int k = (int)(kq / per), j = (int)(kq % per) - 3;
+    // rows j - 1 .. j + 2 lie in [-4, n + 3], inside the padded table
+    const float* rows = reinterpret_cast<const float*>(
+        ehat + ((long long)k * (n + 2 * kEhatPad) + kEhatPad + (j - 1)) * R);
+    double c[4][2];
+    float4 a0;
+    for (int h = 0; h < 2; ++h) {
+      double e[4];
+      for (int i = 0; i < 4; ++i) {
+        const float* row = rows + (long long)i * 2 * R;
+        e[i] = (double)row[4 * p + h] + (double)row[4 * p + 2 + h];
+      }
+      c[1][h] = -e[0] / 3.0 - 0.5 * e[1] + e[2] - e[3] / 6.0;
+      c[2][h] = 0.5 * e[0] - e[1] + 0.5 * e[2];
+      c[3][h] = (e[3] - e[0]) / 6.0 + 0.5 * (e[1] - e[2]);
+    }
+    const float* r0 = rows + 2 * R;  // row j
+    a0 = make_float4(r0[4 * p], r0[4 * p + 1], r0[4 * p + 2], r0[4 * p + 3]);
+    float4* o = ecub + idx * 3;
+    o[0] = a0;
+    o[1] = make_float4((float)c[1][0], (float)c[1][1], (float)c[2][0], (float)c[2][1]);
+    o[2] = make_float4((float)c[3][0], (float)c[3][1], 0.f, 0.f);
+  }
+}
+
 // Coefficients of 1/2 |e(f)|^2 on interval j (taps j-1..j+2, zero outside
 // the table): with e(f) = sum_i L_i(f) e_{j-1+i} and the Lagrange cubics
 // L_i(f) on nodes -1, 0, 1, 2, it is 1/2 sum_{i,i'} G_ii' L_i(f) L_i'(f), a
@@ -406,6 +450,7 @@ extern "C" int rift_ile_point_destroy(rift_ile_point* pt) {
   cudaFree(pt->gm1);
   cudaFree(pt->ehat);
   cudaFree(pt->epoly);
+  cudaFree(pt->ecub);
   cudaFree(pt->img);
   delete pt;
   return RIFT_ILE_OK;
@@ -694,6 +739,7 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
                                          stream), "table padding")))
       break;
     if ((rc = dev_alloc(&pt->epoly, (size_t)K * (n + 3) * (kPolyDeg + 1)))) break;
+    if ((rc = dev_alloc(&pt->ecub, ecub_f4(K, n, R)))) break;
     if ((rc = dev_alloc(&dinv_s, inv_s.size()))) break;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->A, A.data(), A.size() * sizeof(float2),
                                          cudaMemcpyHostToDevice, stream), "copy of A")))
@@ -710,6 +756,9 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     const long long tp = (long long)K * (n + 3);
     halfnorm_poly_kernel<<<(int)std::min<long long>((tp + 127) / 128, 148LL * 16), 128, 0, stream>>>(
         dproj, dinv_s, K, n, D, R, pt->epoly);
+    const long long tc3 = (long long)K * (n + 5) * (R / 2);
+    cubic_table_kernel<<<(int)std::min<long long>((tc3 + 127) / 128, 148LL * 16), 128, 0, stream>>>(
+        pt->ehat, K, n, R, pt->ecub);
     if ((rc = check_cuda(cudaGetLastError(), "table kernels"))) break;
     P.Q = pt->q_copy;
     P.U = pt->uv;
@@ -718,6 +767,7 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     P.gm1 = pt->gm1;
     P.ehat = pt->ehat;
     P.epoly = pt->epoly;
+    P.ecub = pt->ecub;
     if ((rc = build_mixed_image(P, &pt->img, &P.img_f4, stream))) break;
     P.img = pt->img;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->dev, &P, sizeof(PointParams), cudaMemcpyHostToDevice,

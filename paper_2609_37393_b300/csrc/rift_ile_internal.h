@@ -26,6 +26,8 @@ constexpr int kPolyDeg = 6;  // 1/2 |e(f)|^2 on one table interval is a sextic i
 // Zero rows stored before and after each detector's whitened table, so that
 // any tap window whose first tap lies in [-kEhatPad, n] reads rows in memory.
 constexpr int kEhatPad = 4;
+// Length in float4 of the cubic coefficient table (PointParams::ecub).
+inline size_t ecub_f4(int K, int n, int R) { return (size_t)K * (n + 5) * (R / 2) * 3; }
 
 // Everything a kernel needs about one intrinsic point.  Lives in device
 // memory (one record per point) and is staged into shared memory by each
@@ -78,6 +80,10 @@ struct PointParams {
   const float* gm1;     // [ncls][R]     1 - lam_r/s_r^2 (0 except kept null directions)
   const float2* ehat;   // [K][n + 2 kEhatPad][R] whitened Q table, zero rows around it
   const float2* epoly;  // [K][n+3][7]   1/2|e(f)|^2 on interval j (index j+2), coefficients of f^0..f^6
+  // [K][n + 5][R/2][3] the four-tap cubic of each table interval j = -3..n+1
+  // (index j + 3) as coefficients of f, per direction pair: (c0 hi, c0 lo),
+  // (c1, c2), (c3, 0) with c0 the tap row j itself (see ecub_f4)
+  const float4* ecub;
   // The shared-memory image of the FP32-mixed kernels' per-point tables (the
   // split whitening, gm1 and the staged detector and mode tables, built once
   // at point creation): the warp-per-draw kernel copies it flat.
@@ -127,6 +133,7 @@ struct rift_ile_point {
   float* gm1;                    // owned
   float2* ehat;                  // owned
   float2* epoly;                 // owned
+  float4* ecub;                  // owned
   float4* img;                   // owned
   int device;
 };
