@@ -666,11 +666,13 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         }
       }
     }
-    // a1_r, a2_r as (head, tail) on the grid of the larger of the two: the
-    // template product below takes head x head exactly.  Stored by direction
-    // pairs (r, r + 1), r even: slot r = (a1 heads, a1 tails) and slot r + 1 =
-    // (a2 heads, a2 tails), each component pair (r, r + 1) adjacent for the
-    // packed instructions of the residual loop
+    // a1_r, a2_r as (head, tail) on the grid of the larger of the two exact
+    // head sums: the template product below takes head x head exactly; the
+    // tail is (ex - head) (exact) + co rounded once, whatever the size of co
+    // against ex.  Stored by direction pairs (r, r + 1), r even: slot r =
+    // (a1 heads, a1 tails) and slot r + 1 = (a2 heads, a2 tails), each
+    // component pair (r, r + 1) adjacent for the packed instructions of the
+    // residual loop
     constexpr bool kA12S = A12Smem<RR>::on;
     float4 a12r[kA12S ? 1 : RR];
 #pragma unroll
@@ -678,12 +680,15 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       float uh[2], ut[2], vh[2], vt[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const df u = two_sum(ex[r + h].x, co[r + h].x), v = two_sum(ex[r + h].y, co[r + h].y);
-        const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
-        uh[h] = head_of(u.hi, C);
-        vh[h] = head_of(v.hi, C);
-        ut[h] = __fadd_rn(__fsub_rn(u.hi, uh[h]), u.lo);
-        vt[h] = __fadd_rn(__fsub_rn(v.hi, vh[h]), v.lo);
+        const float2 e = ex[r + h];
+        const float C = head_constant(fmaxf(fabsf(e.x), fabsf(e.y)));
+        const float2 C2 = make_float2(C, C);
+        const float2 hd = sub2(__fadd2_rn(e, C2), C2);
+        const float2 tl = __fadd2_rn(sub2(e, hd), co[r + h]);
+        uh[h] = hd.x;
+        vh[h] = hd.y;
+        ut[h] = tl.x;
+        vt[h] = tl.y;
       }
       const float4 qa = make_float4(uh[0], uh[1], ut[0], ut[1]);
       const float4 qb = make_float4(vh[0], vh[1], vt[0], vt[1]);

@@ -434,11 +434,13 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
           co = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.w, y.w), co);
           co = __ffma2_rn(make_float2(an.z, an.w), make_float2(yh.y, yh.y), co);
         }
-        const df u = two_sum(ex.x, co.x), v = two_sum(ex.y, co.y);
-        const float C = head_constant(fmaxf(fabsf(u.hi), fabsf(v.hi)));
-        const float uh = head_of(u.hi, C), vh = head_of(v.hi, C);
-        W.a12[c][r] = make_float4(uh, __fadd_rn(__fsub_rn(u.hi, uh), u.lo), vh,
-                                  __fadd_rn(__fsub_rn(v.hi, vh), v.lo));
+        // heads on the grid of the larger exact head sum, tails (ex - head) + co
+        // (as in the per-thread kernel)
+        const float C = head_constant(fmaxf(fabsf(ex.x), fabsf(ex.y)));
+        const float2 C2 = make_float2(C, C);
+        const float2 hd = sub2(__fadd2_rn(ex, C2), C2);
+        const float2 tl = __fadd2_rn(sub2(ex, hd), co);
+        W.a12[c][r] = make_float4(hd.x, tl.x, hd.y, tl.y);
       }
     }
 
