@@ -16,24 +16,26 @@ __device__ __forceinline__ void stage_point(PointParams& dst, const PointParams*
   for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
+// The draws are read once: streaming loads (evict-first in L1 and L2), so that
+// they do not displace the point's tables from L1.
 __device__ __forceinline__ double load_param_d(const DrawsParams& dp, int which, long long i) {
-  return dp.f64 ? __ldg((const double*)dp.p[which] + i) : (double)__ldg((const float*)dp.p[which] + i);
+  return dp.f64 ? __ldcs((const double*)dp.p[which] + i) : (double)__ldcs((const float*)dp.p[which] + i);
 }
 
 __device__ __forceinline__ float load_param_f(const DrawsParams& dp, int which, long long i) {
-  return dp.f64 ? (float)__ldg((const double*)dp.p[which] + i) : __ldg((const float*)dp.p[which] + i);
+  return dp.f64 ? (float)__ldcs((const double*)dp.p[which] + i) : __ldcs((const float*)dp.p[which] + i);
 }
 
 __device__ __forceinline__ double load_logw_d(const DrawsParams& dp, long long i) {
   if (!dp.logw) return 0.0;
-  return dp.f64 ? __ldg((const double*)dp.logw + i) : (double)__ldg((const float*)dp.logw + i);
+  return dp.f64 ? __ldcs((const double*)dp.logw + i) : (double)__ldcs((const float*)dp.logw + i);
 }
 
 // The t parameter of an FP32 draw set is exact in a float; an FP64 draw set
 // keeps its double value as a (hi, lo) pair.
 __device__ __forceinline__ df load_param_df(const DrawsParams& dp, int which, long long i) {
-  if (dp.f64) return df_from_double(__ldg((const double*)dp.p[which] + i));
-  return df{__ldg((const float*)dp.p[which] + i), 0.f};
+  if (dp.f64) return df_from_double(__ldcs((const double*)dp.p[which] + i));
+  return df{__ldcs((const float*)dp.p[which] + i), 0.f};
 }
 
 // -2Y_lm(iota, phi) of mode i from the polynomial coefficients of the point:

@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(kCompMixedThreads, 2)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
     float lw = 0.f;
     if (LSE && dp.logw)
-      lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
+      lw = dp.f64 ? (float)__ldcs((const double*)dp.logw + i) : __ldcs((const float*)dp.logw + i);
     const df l = comp_mixed_draw<MM, false>(C, B, sAG, cslot, tslot, CompGradSlots{}, dp, i, oob,
                                             nullptr);
     if (LSE)

@@ -1057,7 +1057,7 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dp.n; i += stride) {
     float lw = 0.f;
     if (LSE && dp.logw)
-      lw = dp.f64 ? (float)__ldg((const double*)dp.logw + i) : __ldg((const float*)dp.logw + i);
+      lw = dp.f64 ? (float)__ldcs((const double*)dp.logw + i) : __ldcs((const float*)dp.logw + i);
     if (LSE && pend) tlse_push_lw(st, pend_l, pend_w);
     MixedDraw o;
     if (DIST && GRAD) {
@@ -1370,7 +1370,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
     float pend_w = 0.f;
     for (long long i = it.begin + threadIdx.x; i < end; i += blockDim.x) {
       float lw = 0.f;
-      if (sdp.logw) lw = sdp.f64 ? (float)__ldg((const double*)sdp.logw + i) : __ldg((const float*)sdp.logw + i);
+      if (sdp.logw) lw = sdp.f64 ? (float)__ldcs((const double*)sdp.logw + i) : __ldcs((const float*)sdp.logw + i);
       if (pend) tlse_push_lw(st, pend_l, pend_w);
       MixedDraw o = lnl_mixed_draw<MM, RR, false, false, true>(P, T, sA, sg, a12s, xfs, sdp, i);
       oob += o.oob;
