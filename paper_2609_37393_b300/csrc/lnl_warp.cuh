@@ -15,18 +15,18 @@
 //      4..15: of |m| phi for |m| = 1..12; every lane the distance factor
 //      (the exponential, also without a table)
 //   4a role 0, lane k < K: the arrival time and table position; the interval
-//      polynomial's coefficients loaded and the four tap rows prefetched into
-//      L1, in flight during phase 2
+//      polynomial's coefficients loaded and the interval's cubic coefficients
+//      prefetched into L1, in flight during phase 2
 //   2  role 0: the sky direction and x e^{2 i psi}; lanes 0..5 the six
 //      products of the sky sines and cosines, lanes 0..9 the ten antenna-basis
 //      terms from them, split for the exact products
 //   3  role 1, lane j < M: the harmonic of mode j, split for the exact
 //      products; lane (c, r): row r of the class-c mat-vec a1 = A y, a2 = A J y
-//   4  role 0, lane k < K: x F_k, 1/2 |e|^2 and its slope, the cubic's
-//      weights, the detector's antenna derivatives (phases 4a, 2 and 4 run
-//      while role 1 runs phase 3)
-//   5  role 0, lane (k, direction pair): the template, the residual over the
-//      four taps and the pair's shares of |r|^2, r . edot, rho . a1, rho . a2
+//   4  role 0, lane k < K: x F_k, 1/2 |e|^2 and its slope, the detector's
+//      antenna derivatives (phases 4a, 2 and 4 run while role 1 runs phase 3)
+//   5  role 0, lane (k, direction pair): the template, the residual from the
+//      interval's cubic and the pair's shares of |r|^2, r . edot, rho . a1,
+//      rho . a2
 //   6  role 1, lane (c, r): G1_r, G2_r of the class; role 0, lane k: the
 //      detector's terms of lnL and of the gradient, summed over the detectors
 //      by a fixed shuffle tree (compensated pairs merged exactly)
@@ -55,8 +55,7 @@ struct WarpScratch {
   float2 yh[MM];                   // (yr.hi, yi.hi)
   float4 a12[kMaxDet][RR];         // class c, direction r: (a1 head, a1 tail, a2 head, a2 tail)
   float4 xf[kMaxDet];              // x F_k: (re head, re tail, im head, im tail)
-  float4 wt[kMaxDet], wtd[kMaxDet];
-  float sigma[kMaxDet];
+  float fpos[kMaxDet];             // position in the table interval
   int jc[kMaxDet];
   int bad[kMaxDet];
   float2 he2[kMaxDet], dhe2[kMaxDet];  // 1/2 |e|^2 and its slope in f (hi, lo)
@@ -325,7 +324,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
     const df s0 = df_mul(cd, cl), s1 = df_mul(cd, sl), s2 = sd;
     const df xer = df_mul(x, c2p), xei = df_mul(x, s2p);
     // ---- 4a: role 0, lane k < K: the arrival time and table position, so
-    // that the interval polynomial's coefficients and the tap rows are in
+    // that the interval polynomial's coefficients and the cubic's are in
     // flight while phase 2 forms the antenna basis
     float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
     int bad = 0, jck = 0;
@@ -353,11 +352,13 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
       }
       jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-      {  // the four tap rows (contiguous) into L1 for the residual phase
-        const char* row = reinterpret_cast<const char*>(
-            P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (jck - 1)) * RR);
-        for (int off = 0; off < 4 * RR * 8; off += 128)
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(row + off));
+      {  // the interval's cubic coefficients (contiguous) into L1 for the residual phase
+        const char* cb = reinterpret_cast<const char*>(
+            P.ecub + ((size_t)k * (n + 5) + (size_t)(jck + 3)) * (RR / 2) * 3);
+        constexpr int kBytes = (RR / 2) * 48;
+        for (int off = 0; off < kBytes; off += 128)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(cb + off));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(cb + kBytes - 16));
       }
     }
 
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
 
     if (role == 0) {
       // ---- 4: lane k < K (the arrival time and the table loads of phase 4a):
-      // the antenna factor, 1/2|e|^2, the weights, the derivatives
+      // the antenna factor, 1/2|e|^2, the derivatives
       if (lane < K) {
         const int k = lane;
         AntennaSplit AS;
@@ -509,18 +510,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
           half_e2 = acc;
           dhalf = dacc_p;
         }
-        const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
-        const float w0 = -(f * fc * fd) * (1.f / 6.f), w1 = (fa * fc * fd) * 0.5f;
-        const float w2 = -(fa * f * fd) * 0.5f, w3 = (fa * f * fc) * (1.f / 6.f);
-        const df ws = df_add(two_sum(w0, w1), two_sum(w2, w3));
-        W.sigma[k] = __fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
-        W.wt[k] = make_float4(w0, w1, w2, w3);
-        if (GRAD) {
-          W.wtd[k] = make_float4(-(fc * fd + f * fd + f * fc) * (1.f / 6.f),
-                                 (fc * fd + fa * fd + fa * fc) * 0.5f,
-                                 -(f * fd + fa * fd + fa * f) * 0.5f,
-                                 (f * fc + fa * fc + fa * f) * (1.f / 6.f));
-        }
+        W.fpos[k] = f;
         W.jc[k] = jck;
         W.bad[k] = bad;
         W.he2[k] = make_float2(half_e2.hi, half_e2.lo);
@@ -550,30 +540,22 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         nlo = __ffma2_rn(nxit, a2h, nlo);
         nlo = __ffma2_rn(nxit, a2t, nlo);
         const float2 nhi = __ffma2_rn(nxrh, a1h, __fmul2_rn(nxih, a2h));
-        const float4 w4 = W.wt[k];
-        const float wtv[4] = {w4.x, w4.y, w4.z, w4.w};
-        float wdv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (GRAD) {
-          const float4 d4 = W.wtd[k];
-          wdv[0] = d4.x;
-          wdv[1] = d4.y;
-          wdv[2] = d4.z;
-          wdv[3] = d4.w;
-        }
-        const float nsg = -W.sigma[k];
-        const float2* Ej = P.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad) * RR +
-                           (ptrdiff_t)(W.jc[k] - 1) * RR;
-        float2 rs = make_float2(0.f, 0.f), ed = make_float2(0.f, 0.f);
-  #pragma unroll
-        for (int tap = 0; tap < 4; ++tap) {
-          const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + tap * RR + r));
-          const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
-                                      make_float2(e4.z, e4.w));
-          rs = __ffma2_rn(make_float2(wtv[tap], wtv[tap]), d, rs);
-          if (tap == 1) rs = __ffma2_rn(make_float2(nsg, nsg), d, rs);
-          if (GRAD) ed = __ffma2_rn(make_float2(wdv[tap], wdv[tap]), d, ed);
-        }
-        const float2 rsv = __fadd2_rn(rs, nlo);
+        // the interval's cubic e(f) = c0 + f (c1 + f (c2 + f c3)) (as in the
+        // per-thread kernel): c0.hi meets the exact head of w first
+        const float fk = W.fpos[k];
+        const float2 f2 = make_float2(fk, fk);
+        const float4* Cj = P.ecub + (((size_t)k * (n + 5) + (size_t)(W.jc[k] + 3)) * (RR / 2) + pr) * 3;
+        const float4 c0 = __ldg(Cj), c12 = __ldg(Cj + 1), c3v = __ldg(Cj + 2);
+        const float2 c1 = make_float2(c12.x, c12.y), c2 = make_float2(c12.z, c12.w);
+        const float2 c3 = make_float2(c3v.x, c3v.y);
+        float2 hp = __ffma2_rn(c3, f2, c2);
+        hp = __ffma2_rn(hp, f2, c1);
+        const float2 tl = __ffma2_rn(hp, f2, make_float2(c0.z, c0.w));
+        const float2 d0 = __fadd2_rn(make_float2(c0.x, c0.y), nhi);
+        const float2 rsv = __fadd2_rn(__fadd2_rn(d0, tl), nlo);
+        float2 ed = make_float2(0.f, 0.f);  // de/df = c1 + f (2 c2 + 3 f c3)
+        if (GRAD)
+          ed = __ffma2_rn(__ffma2_rn(c3, make_float2(3.f * fk, 3.f * fk), __fadd2_rn(c2, c2)), f2, c1);
         const float2 q2 = __fmul2_rn(rsv, rsv);
         const float2 nwf = __fadd2_rn(nhi, nlo);
         float2 gm = make_float2(0.f, 0.f), nul = make_float2(0.f, 0.f);
