@@ -113,24 +113,25 @@ struct CompMixed {
   const float* agrid;  // [ncls][R] head constants of a1_a, a2_a per direction (every a)
   const float2* ehat;  // [K][n + 2 kEhatPad][R] whitened table, direction pairs
   const float2* epoly; // [K][n + 3][7] 1/2 |e(f)|^2 per interval
+  const float4* ecub;  // [K][n + 5][R/2][3] the intervals' cubic coefficients (PointParams::ecub)
 };
 
 // Dynamic shared memory of the mixed composite kernel (float4 units): the
 // split whitening (when staged), the head constants, and per thread the
-// coefficient slots (K na) and the tap slots (2 K).
+// coefficient slots (K na) and the table-position slots (K).
 __host__ __device__ inline size_t comp_mixed_b_f4(const CompMixed& C) {
   return (size_t)C.ncls * C.na * C.R * C.JP * 3;
 }
 __host__ __device__ inline size_t comp_mixed_ag_f4(const CompMixed& C) {
   return ((size_t)C.ncls * C.R + 3) / 4;
 }
-// Per-thread float4 slots: the coefficients (K na) and the taps (2 K); the
-// adjoint adds three tap slots per detector (derivative weights, arrival-time
-// derivatives, post-phase step), the residual products rho (K na float2), the
-// current direction pair's a1, a2 (na) and d lnL / dY of the mode pairs (JP).
+// Per-thread float4 slots: the coefficients (K na) and one table-position slot
+// per detector; the adjoint adds two per detector (arrival-time derivatives,
+// post-phase step), the residual products rho (K na float2), the current
+// direction pair's a1, a2 (na) and d lnL / dY of the mode pairs (JP).
 __host__ __device__ inline size_t comp_mixed_thread_f4(const CompMixed& C, bool grad) {
-  size_t f = (size_t)C.K * C.na + 2 * C.K;
-  if (grad) f += 3 * C.K + ((size_t)C.K * C.na + 1) / 2 + C.na + C.JP;
+  size_t f = (size_t)C.K * C.na + C.K;
+  if (grad) f += 2 * C.K + ((size_t)C.K * C.na + 1) / 2 + C.na + C.JP;
   return f;
 }
 __host__ __device__ inline size_t comp_mixed_smem(const CompMixed& C, bool bsmem, int threads,
@@ -161,4 +162,5 @@ struct rift_ile_comp {
   float* agrid;
   float2* ehat;
   float2* epoly;
+  float4* ecub;
 };

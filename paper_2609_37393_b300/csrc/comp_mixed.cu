@@ -77,10 +77,12 @@ void free_mixed(rift_ile_comp* cp) {
   cudaFree(cp->agrid);
   cudaFree(cp->ehat);
   cudaFree(cp->epoly);
+  cudaFree(cp->ecub);
   cp->Bs = nullptr;
   cp->agrid = nullptr;
   cp->ehat = nullptr;
   cp->epoly = nullptr;
+  cp->ecub = nullptr;
   cp->mixed_built = 0;
 }
 
@@ -356,6 +358,7 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
     e = cudaMalloc((void**)&cp->ehat, (size_t)K * (n + 2 * kEhatPad) * R * sizeof(float2));
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&cp->epoly, (size_t)K * (n + 3) * (kPolyDeg + 1) * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&cp->ecub, ecub_f4(K, n, R) * sizeof(float4));
   if (e != cudaSuccess) {
     free_mixed(cp);
     rift_ile_set_error("rift_ile_comp_mixed_build: allocation failed: %s", cudaGetErrorString(e));
@@ -369,7 +372,7 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
     return check_cuda(e, "rift_ile_comp_mixed_build upload");
   }
   if ((rc = whitened_tables(cp->q, 1, K, n, A, ncls, P.cls_of, Vt.data(), inv_s.data(), R, cp->ehat,
-                            cp->epoly, st))) {
+                            cp->epoly, cp->ecub, st))) {
     free_mixed(cp);
     return rc;
   }
@@ -377,6 +380,7 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
   C.agrid = cp->agrid;
   C.ehat = cp->ehat;
   C.epoly = cp->epoly;
+  C.ecub = cp->ecub;
 
   // ---- launch shape: 128 threads with the split whitening in shared memory
   // when it fits (staging beat reading it through L1 with one more resident

@@ -16,13 +16,14 @@
 // terms >= 2^8 smaller summed in FP32); only the residual e - w is FP32.
 //
 // Loop order: the coefficients x C~^k_a of every detector (as head/tail
-// pairs on the grid of the detector's largest) and each detector's tap
-// weights go to this thread's slots in shared memory; the harmonics stay in
+// pairs on the grid of the detector's largest) and each detector's table
+// position go to this thread's slots in shared memory; the harmonics stay in
 // registers as mode pairs (j, j + 1), which are the lanes of the packed
 // FFMA2 instructions of the a1/a2 sums.  Then, per class and pair of
 // directions (r, r + 1): for each response index a the two rows of a1_a, a2_a,
 // their split, and their products with the coefficients of up to
-// kCompMixedKG detectors; then those detectors' residuals over the four taps.
+// kCompMixedKG detectors; then those detectors' residuals from the table
+// interval's cubic coefficients.
 #pragma once
 #include "comp.cuh"
 
@@ -387,11 +388,11 @@ struct CompGradSlots {
   float4* dy;   // [JP] (d Re Y lanes, d Im Y lanes)
 };
 
-// Tap slots per detector: the weights, (sigma, first tap, and for the adjoint
-// the slope of 1/2 |e|^2), then (adjoint) the derivative weights, (d t_k / d ra,
-// d t_k / d dec, r . de/du) and e^{i Omega t_k}.
+// Table slots per detector: (position f in the interval, the interval, and
+// for the adjoint the slope of 1/2 |e|^2 as a pair), then (adjoint)
+// (d t_k / d ra, d t_k / d dec, r . de/du) and e^{i Omega t_k}.
 template <bool GRAD>
-constexpr int comp_tap_slots() { return GRAD ? 5 : 2; }
+constexpr int comp_tap_slots() { return GRAD ? 3 : 1; }
 
 // The adjoint's last pass over a draw's detectors and modes: the arrival-time
 // terms (d/dt 1/2 |e_k|^2 - r_k . de_k/dt) d t_k (double-float), the coefficient
@@ -408,8 +409,8 @@ __device__ __noinline__ void comp_mixed_grad_tail(const CompMixed& C, const Comp
   dacc gt_ra = dacc_zero(), gt_dec = dacc_zero(), gt_t = dacc_zero();
   float g_ra = 0.f, g_dec = 0.f, g_tc = 0.f, g_psi = 0.f, g_lnd = 0.f;
   for (int k = 0; k < K; ++k) {
-    const float4 t1 = tslot[(size_t)(TS * k + 1) * bd], t3 = tslot[(size_t)(TS * k + 3) * bd];
-    const float4 t4 = tslot[(size_t)(TS * k + 4) * bd];
+    const float4 t1 = tslot[(size_t)(TS * k) * bd], t3 = tslot[(size_t)(TS * k + 1) * bd];
+    const float4 t4 = tslot[(size_t)(TS * k + 2) * bd];
     const df dtk = df_mul(df_add_f(df{t1.z, t1.w}, -t3.z), df{C.inv_dt_hi, C.inv_dt_lo});
     dacc_add(gt_t, dtk);
     dacc_add(gt_ra, df_mul_f(dtk, t3.x));
@@ -532,7 +533,7 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
     f0b = df_mul(S.cd, S.cd);
   }
 
-  // ---- per detector: arrival time, table position, 1/2 |e|^2, tap weights,
+  // ---- per detector: arrival time, table position, 1/2 |e|^2,
   // and the coefficients (df pairs first, then split on the detector's grid)
   dacc T = dacc_zero();
   bool bad = false;
@@ -560,17 +561,16 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
     }
     const df rel = df_add(tk, df{-ph.w, -pl.w});
     const df u = df_mul(rel, df{C.inv_dt_hi, C.inv_dt_lo});
-    float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f), wd4 = w4;
     df dhalf = df{0.f, 0.f};
-    float nsig = 0.f;
-    int jc = -3;  // zero rows: a detector without a finite position adds nothing but NaN
+    float f = 0.f;
+    int jc = -3;  // zero coefficients: a detector without a finite position adds nothing but NaN
     if (!isfinite(u.hi)) {
       bad = true;
       oob += 4;
     } else {
       float jf = floorf(u.hi);
       if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
-      const float f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
+      f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
       if (jf >= -2.f && jf <= (float)n) {
         const float2* pc = C.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
         float2 cf = __ldg(pc + kPolyDeg);
@@ -583,34 +583,19 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
         }
         dacc_add(T, acc);
       }
-      const float fa = f + 1.f, fc = f - 1.f, fd = f - 2.f;
-      w4.x = -(f * fc * fd) * (1.f / 6.f);
-      w4.y = (fa * fc * fd) * 0.5f;
-      w4.z = -(fa * f * fd) * 0.5f;
-      w4.w = (fa * f * fc) * (1.f / 6.f);
-      if (GRAD) {  // d wt_i / df
-        wd4.x = -(fc * fd + f * fd + f * fc) * (1.f / 6.f);
-        wd4.y = (fc * fd + fa * fd + fa * fc) * 0.5f;
-        wd4.z = -(f * fd + fa * fd + fa * f) * 0.5f;
-        wd4.w = (f * fc + fa * fc + fa * f) * (1.f / 6.f);
-      }
-      const df ws = df_add(two_sum(w4.x, w4.y), two_sum(w4.z, w4.w));
-      nsig = -__fadd_rn(__fsub_rn(ws.hi, 1.f), ws.lo);
       const float nb = fminf(fmaxf(1.f - jf, 0.f), 4.f);
       const float nab = fminf(fmaxf(jf + 3.f - (float)n, 0.f), 4.f);
       oob += (int)fminf(nb + nab, 4.f);
       jc = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
     }
-    tslot[(size_t)(TS * k) * bd] = w4;
-    tslot[(size_t)(TS * k + 1) * bd] = make_float4(nsig, __int_as_float(jc), dhalf.hi, dhalf.lo);
+    tslot[(size_t)(TS * k) * bd] = make_float4(f, __int_as_float(jc), dhalf.hi, dhalf.lo);
     if (GRAD) {
       // d t_k / d ra = -pos . ds/d ra, d t_k / d dec = -pos . ds/d dec
       const float sl = S.sl.hi, cl = S.cl.hi, sd = S.sd.hi, cd = S.cd.hi;
       const float dka = -(ph.x * (-cd * sl) + ph.y * (cd * cl));
       const float dkd = -(ph.x * (-sd * cl) + ph.y * (-sd * sl) + ph.z * cd);
-      tslot[(size_t)(TS * k + 2) * bd] = wd4;
-      tslot[(size_t)(TS * k + 3) * bd] = make_float4(dka, dkd, 0.f, 0.f);
-      tslot[(size_t)(TS * k + 4) * bd] = make_float4(ep.x, ep.y, 0.f, 0.f);
+      tslot[(size_t)(TS * k + 1) * bd] = make_float4(dka, dkd, 0.f, 0.f);
+      tslot[(size_t)(TS * k + 2) * bd] = make_float4(ep.x, ep.y, 0.f, 0.f);
       for (int a = 0; a < na; ++a) gs.rho[(size_t)(k * na + a) * bd] = make_float2(0.f, 0.f);
     }
   }
@@ -756,37 +741,34 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
             }
           }
         }
-        // residuals of rows r0, r0 + 1: r = sum_i wt_i (e_i - w) - sigma (e_j - w)
-        // with -w = nhi + nlo (nhi the exact head sum), as in the static path
+        // residuals of rows r0, r0 + 1 from the interval's cubic,
+        // r = (c0.hi + nhi) + (c0.lo + f (c1 + f (c2 + f c3))) + nlo with
+        // -w = nhi + nlo (nhi the exact head sum), as in the static path
 #pragma unroll
         for (int kk = 0; kk < kCompMixedKG; ++kk) {
           if (kk < nk) {
             const int k = kd[kk];
-            const float4 w4 = tslot[(size_t)(TS * k) * bd];
-            const float4 t1 = tslot[(size_t)(TS * k + 1) * bd];
-            float4 wd4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (GRAD) wd4 = tslot[(size_t)(TS * k + 2) * bd];
-            const float wtd[4] = {wd4.x, wd4.y, wd4.z, wd4.w};
-            float2 ed = make_float2(0.f, 0.f);
-            const int jc = __float_as_int(t1.y);
+            const float4 t0 = tslot[(size_t)(TS * k) * bd];
+            const int jc = __float_as_int(t0.y);
+            const float2 f2 = make_float2(t0.x, t0.x);
             const float2 nhi = make_float2(-__fadd_rn(whp[kk][0].x, whp[kk][0].y),
                                            -__fadd_rn(whp[kk][1].x, whp[kk][1].y));
             const float2 nlo = make_float2(-__fadd_rn(wcp[kk][0].x, wcp[kk][0].y),
                                            -__fadd_rn(wcp[kk][1].x, wcp[kk][1].y));
-            const float2* Ej =
-                C.ehat + ((size_t)k * (n + 2 * kEhatPad) + kEhatPad + (ptrdiff_t)(jc - 1)) * R + r0;
-            const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
-            float2 rs = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int tap = 0; tap < 4; ++tap) {
-              const float4 e4 = __ldg(reinterpret_cast<const float4*>(Ej + (size_t)tap * R));
-              const float2 d = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), nhi),
-                                          make_float2(e4.z, e4.w));
-              rs = __ffma2_rn(make_float2(wt[tap], wt[tap]), d, rs);
-              if (tap == 1) rs = __ffma2_rn(make_float2(t1.x, t1.x), d, rs);
-              if (GRAD) ed = __ffma2_rn(make_float2(wtd[tap], wtd[tap]), d, ed);
-            }
-            const float2 rsv = __fadd2_rn(rs, nlo);
+            const float4* Cj =
+                C.ecub + (((size_t)k * (n + 5) + (size_t)(jc + 3)) * (R / 2) + r0 / 2) * 3;
+            const float4 c0 = __ldg(Cj), c12 = __ldg(Cj + 1), c3v = __ldg(Cj + 2);
+            const float2 c1 = make_float2(c12.x, c12.y), c2 = make_float2(c12.z, c12.w);
+            const float2 c3 = make_float2(c3v.x, c3v.y);
+            float2 hp = __ffma2_rn(c3, f2, c2);
+            hp = __ffma2_rn(hp, f2, c1);
+            const float2 tl = __ffma2_rn(hp, f2, make_float2(c0.z, c0.w));
+            const float2 d0 = __fadd2_rn(make_float2(c0.x, c0.y), nhi);
+            const float2 rsv = __fadd2_rn(__fadd2_rn(d0, tl), nlo);
+            float2 ed = make_float2(0.f, 0.f);  // de/df = c1 + f (2 c2 + 3 f c3)
+            if (GRAD)
+              ed = __ffma2_rn(__ffma2_rn(c3, make_float2(3.f * t0.x, 3.f * t0.x), __fadd2_rn(c2, c2)),
+                              f2, c1);
             q2p = __ffma2_rn(rsv, rsv, q2p);
             if (GRAD) {
               rsk[kk] = rsv;
@@ -841,7 +823,7 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
       if (GRAD) {
 #pragma unroll
         for (int kk = 0; kk < kCompMixedKG; ++kk)
-          if (kk < nk) tslot[(size_t)(TS * kd[kk] + 3) * bd].z = red[kk];
+          if (kk < nk) tslot[(size_t)(TS * kd[kk] + 1) * bd].z = red[kk];
       }
     }
   }

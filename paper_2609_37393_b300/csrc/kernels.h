@@ -72,12 +72,13 @@ void split_df(double x, float* hi, float* lo);
 // The whitened tables of K detectors from a complex table Q [K][n][Mq]
 // (complex128 if q_c128, else complex64; device): with the eigenvectors Vt
 // [ncls][2 Mq][2 Mq] (rows, host) and the scales inv_s [K][R] (host; zero for
-// dropped or padding directions), writes ehat [K][n + 2 kEhatPad][R] and the
-// interval polynomials epoly [K][n + 3][7] (device, caller-allocated) and
+// dropped or padding directions), writes ehat [K][n + 2 kEhatPad][R], the
+// interval polynomials epoly [K][n + 3][7] and the intervals' cubic
+// coefficients ecub [ecub_f4(K, n, R)] (device, caller-allocated; R even) and
 // synchronises st.
 int whitened_tables(const void* Q, int q_c128, int K, int n, int Mq, int ncls, const int* cls_of,
                     const double* Vt, const double* inv_s, int R, float2* ehat, float2* epoly,
-                    cudaStream_t st);
+                    float4* ecub, cudaStream_t st);
 // SM count of the current device (cached).
 int device_sms();
 // Draw count up to which FP32-mixed lnL and lnL + gradient calls (no

@@ -393,7 +393,7 @@ int harmonic_coefficients(int l, int m, int* k0, double* coef) {
 
 int whitened_tables(const void* Q, int q_c128, int K, int n, int Mq, int ncls, const int* cls_of,
                     const double* Vt, const double* inv_s, int R, float2* ehat, float2* epoly,
-                    cudaStream_t st) {
+                    float4* ecub, cudaStream_t st) {
   const int D = 2 * Mq;
   double *dVt = nullptr, *dproj = nullptr, *dinv_s = nullptr;
   int* dcls = nullptr;
@@ -427,6 +427,9 @@ int whitened_tables(const void* Q, int q_c128, int K, int n, int Mq, int ncls, c
     const long long tp = (long long)K * (n + 3);
     halfnorm_poly_kernel<<<(int)std::min<long long>((tp + 127) / 128, 148LL * 16), 128, 0, st>>>(
         dproj, dinv_s, K, n, D, R, epoly);
+    const long long tc3 = (long long)K * (n + 5) * (R / 2);
+    cubic_table_kernel<<<(int)std::min<long long>((tc3 + 127) / 128, 148LL * 16), 128, 0, st>>>(
+        ehat, K, n, R, ecub);
     if ((rc = check_cuda(cudaGetLastError(), "whitened table kernels"))) break;
     rc = check_cuda(cudaStreamSynchronize(st), "whitened tables");
   } while (0);
