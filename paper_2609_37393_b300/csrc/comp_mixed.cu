@@ -17,6 +17,7 @@
 #include <math_constants.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -32,6 +33,8 @@ cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, const Dr
 template <int MM>
 cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
                             double* lnl_out, double* grad_out, cudaStream_t st);
+template <int MM>
+int comp_mixed_grad_regs();
 
 namespace {
 
@@ -401,13 +404,36 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
       break;
     }
   }
-  // the adjoint's (more slots per thread; without a fitting shape only the
-  // gradient entry point reports UNSUPPORTED)
-  for (const auto& sh : shapes) {
-    if (comp_mixed_smem(C, sh[1] != 0, sh[0], true) + static_smem <= (size_t)optin) {
-      cp->grad_threads = sh[0];
-      cp->grad_bsmem = sh[1];
-      break;
+  // the adjoint's: more slots per thread, so that shared memory rather than
+  // registers bounds its residency; the shape with the most resident warps
+  // per SM (ties: the whitening staged, then the larger block).  Without a
+  // fitting shape only the gradient entry point reports UNSUPPORTED.
+  {
+    int smem_sm = 0, regs = 0;
+    if ((rc = check_cuda(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                                cp->device), "device attribute"))) {
+      free_mixed(cp);
+      return rc;
+    }
+    switch (mm_bucket(C.M)) {
+      case 4: regs = comp_mixed_grad_regs<4>(); break;
+      case 10: regs = comp_mixed_grad_regs<10>(); break;
+      default: regs = comp_mixed_grad_regs<16>(); break;
+    }
+    if (regs <= 0) regs = 255;
+    const int regs_r = (regs + 7) & ~7;  // allocation granularity
+    int best = 0;
+    for (const auto& sh : shapes) {
+      const size_t sm = comp_mixed_smem(C, sh[1] != 0, sh[0], true) + static_smem;
+      if (sm > (size_t)optin) continue;
+      const int by_smem = (int)((size_t)smem_sm / (sm + 1024));  // 1 KB reserved per block
+      const int by_regs = 65536 / (regs_r * sh[0]);
+      const int warps = std::min(by_smem, by_regs) * (sh[0] / 32);
+      if (warps > best) {
+        best = warps;
+        cp->grad_threads = sh[0];
+        cp->grad_bsmem = sh[1];
+      }
     }
   }
   if (!cp->mixed_threads) {

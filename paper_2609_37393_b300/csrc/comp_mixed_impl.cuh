@@ -1004,11 +1004,23 @@ cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const D
                : launch_comp_mixed_grad_k<MM, false>(C, threads, dp, lnl_out, grad_out, st);
 }
 
+// Registers per thread of the adjoint kernel of one bucket (the larger of its
+// two variants; 0 on error), for the build's choice of launch shape.
+template <int MM>
+int comp_mixed_grad_regs() {
+  cudaFuncAttributes a, b;
+  if (cudaFuncGetAttributes(&a, comp_mixed_grad_kernel<MM, true>) != cudaSuccess ||
+      cudaFuncGetAttributes(&b, comp_mixed_grad_kernel<MM, false>) != cudaSuccess)
+    return 0;
+  return a.numRegs > b.numRegs ? a.numRegs : b.numRegs;
+}
+
 #define RIFT_INSTANTIATE_COMP_MIXED(MM)                                                        \
   template cudaError_t comp_mixed_lnl<MM>(const CompMixed&, bool, int, const DrawsParams&,      \
                                           double*, LseState*, unsigned long long*, int*,         \
                                           cudaStream_t);                                         \
   template cudaError_t comp_mixed_grad<MM>(const CompMixed&, bool, int, const DrawsParams&,     \
-                                           double*, double*, cudaStream_t);
+                                           double*, double*, cudaStream_t);                      \
+  template int comp_mixed_grad_regs<MM>();
 
 }  // namespace rift
