@@ -34,7 +34,7 @@ template <int MM>
 cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
                             double* lnl_out, double* grad_out, cudaStream_t st);
 template <int MM>
-int comp_mixed_grad_regs();
+int comp_mixed_regs(bool grad);
 
 namespace {
 
@@ -385,9 +385,8 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
   C.epoly = cp->epoly;
   C.ecub = cp->ecub;
 
-  // ---- launch shape: 128 threads with the split whitening in shared memory
-  // when it fits (staging beat reading it through L1 with one more resident
-  // block), else through L1; fewer threads for large slot counts
+  // ---- launch shapes (block size, split whitening in shared memory or read
+  // through L1)
   int optin = 0;
   if ((rc = check_cuda(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                               cp->device), "device attribute"))) {
@@ -397,42 +396,38 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
   cp->mixed_threads = cp->grad_threads = 0;
   const size_t static_smem = 2048;  // the LSE kernels' static shared memory, with margin
   const int shapes[6][2] = {{128, 1}, {128, 0}, {64, 1}, {64, 0}, {32, 1}, {32, 0}};
-  for (const auto& sh : shapes) {
-    if (comp_mixed_smem(C, sh[1] != 0, sh[0]) + static_smem <= (size_t)optin) {
-      cp->mixed_threads = sh[0];
-      cp->mixed_bsmem = sh[1];
-      break;
-    }
-  }
-  // the adjoint's: more slots per thread, so that shared memory rather than
-  // registers bounds its residency; the shape with the most resident warps
-  // per SM (ties: the whitening staged, then the larger block).  Without a
-  // fitting shape only the gradient entry point reports UNSUPPORTED.
+  // for the lnL kernels and for the adjoint, the shape with the most resident
+  // warps per SM given the kernel's registers and shared memory (ties: the
+  // whitening staged, then the larger block).  Without a fitting shape for
+  // the adjoint only the gradient entry point reports UNSUPPORTED.
   {
-    int smem_sm = 0, regs = 0;
+    int smem_sm = 0;
     if ((rc = check_cuda(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
                                                 cp->device), "device attribute"))) {
       free_mixed(cp);
       return rc;
     }
-    switch (mm_bucket(C.M)) {
-      case 4: regs = comp_mixed_grad_regs<4>(); break;
-      case 10: regs = comp_mixed_grad_regs<10>(); break;
-      default: regs = comp_mixed_grad_regs<16>(); break;
-    }
-    if (regs <= 0) regs = 255;
-    const int regs_r = (regs + 7) & ~7;  // allocation granularity
-    int best = 0;
-    for (const auto& sh : shapes) {
-      const size_t sm = comp_mixed_smem(C, sh[1] != 0, sh[0], true) + static_smem;
-      if (sm > (size_t)optin) continue;
-      const int by_smem = (int)((size_t)smem_sm / (sm + 1024));  // 1 KB reserved per block
-      const int by_regs = 65536 / (regs_r * sh[0]);
-      const int warps = std::min(by_smem, by_regs) * (sh[0] / 32);
-      if (warps > best) {
-        best = warps;
-        cp->grad_threads = sh[0];
-        cp->grad_bsmem = sh[1];
+    for (int grad = 0; grad < 2; ++grad) {
+      int regs = 0;
+      switch (mm_bucket(C.M)) {
+        case 4: regs = comp_mixed_regs<4>(grad != 0); break;
+        case 10: regs = comp_mixed_regs<10>(grad != 0); break;
+        default: regs = comp_mixed_regs<16>(grad != 0); break;
+      }
+      if (regs <= 0) regs = 255;
+      const int regs_r = (regs + 7) & ~7;  // allocation granularity
+      int best = 0;
+      for (const auto& sh : shapes) {
+        const size_t sm = comp_mixed_smem(C, sh[1] != 0, sh[0], grad != 0) + static_smem;
+        if (sm > (size_t)optin) continue;
+        const int by_smem = (int)((size_t)smem_sm / (sm + 1024));  // 1 KB reserved per block
+        const int by_regs = 65536 / (regs_r * sh[0]);
+        const int warps = std::min(by_smem, by_regs) * (sh[0] / 32);
+        if (warps > best) {
+          best = warps;
+          (grad ? cp->grad_threads : cp->mixed_threads) = sh[0];
+          (grad ? cp->grad_bsmem : cp->mixed_bsmem) = sh[1];
+        }
       }
     }
   }

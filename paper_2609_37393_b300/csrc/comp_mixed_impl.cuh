@@ -1004,14 +1004,18 @@ cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const D
                : launch_comp_mixed_grad_k<MM, false>(C, threads, dp, lnl_out, grad_out, st);
 }
 
-// Registers per thread of the adjoint kernel of one bucket (the larger of its
-// two variants; 0 on error), for the build's choice of launch shape.
+// Registers per thread of the adjoint kernel (grad) or of the fused lnZ kernel
+// of one bucket (the larger of the two variants; 0 on error), for the build's
+// choice of launch shape.
 template <int MM>
-int comp_mixed_grad_regs() {
+int comp_mixed_regs(bool grad) {
   cudaFuncAttributes a, b;
-  if (cudaFuncGetAttributes(&a, comp_mixed_grad_kernel<MM, true>) != cudaSuccess ||
-      cudaFuncGetAttributes(&b, comp_mixed_grad_kernel<MM, false>) != cudaSuccess)
-    return 0;
+  cudaError_t e = grad ? cudaFuncGetAttributes(&a, comp_mixed_grad_kernel<MM, true>)
+                       : cudaFuncGetAttributes(&a, comp_mixed_kernel<MM, true, true>);
+  if (e == cudaSuccess)
+    e = grad ? cudaFuncGetAttributes(&b, comp_mixed_grad_kernel<MM, false>)
+             : cudaFuncGetAttributes(&b, comp_mixed_kernel<MM, false, true>);
+  if (e != cudaSuccess) return 0;
   return a.numRegs > b.numRegs ? a.numRegs : b.numRegs;
 }
 
@@ -1021,6 +1025,6 @@ int comp_mixed_grad_regs() {
                                           cudaStream_t);                                         \
   template cudaError_t comp_mixed_grad<MM>(const CompMixed&, bool, int, const DrawsParams&,     \
                                            double*, double*, cudaStream_t);                      \
-  template int comp_mixed_grad_regs<MM>();
+  template int comp_mixed_regs<MM>(bool);
 
 }  // namespace rift
