@@ -61,43 +61,44 @@ WORKLOAD = "3G ILE: ET triangle + CE40 (K=4), 10 modes, SNR 600, 2^22 float32 dr
 def kernel_fp32_ops(point: dict, R: int, ncls: int) -> dict:
     """FP32-pipe operations the FP32-mixed kernel issues per draw of the lnL ->
     LSE pass for this point, built from its own arithmetic: every FP32 add,
-    multiply and fused multiply-add (one op each), the double-float steps at
-    their operation counts (TwoSum 6, FastTwoSum 3, TwoProduct 2, pair product
-    7, pair sum 20, compensated multiply-add 12, anchored sine/cosine 82,
-    anchored exponential 44); addressing, loads, comparisons and control not
-    counted.  This measures how busy the FP32 pipe is (fp32_issue_frac), not
-    the method's work: the roofline's numerator is the algorithmic count of
-    oracle/flops.json."""
+    multiply and fused multiply-add (one op each, a packed pair two), the
+    double-float steps at their operation counts (TwoSum 6, FastTwoSum 3,
+    TwoProduct 2, pair product 7, pair sum 11, Horner step 12, compensated
+    dot product of three 31, anchored sine/cosine 51, anchored exponential 28);
+    addressing, loads, comparisons and control not counted.  This measures how
+    busy the FP32 pipe is (fp32_issue_frac), not the method's work: the
+    roofline's numerator is the algorithmic count of oracle/flops.json."""
     K, M = int(point["K"]), int(point["M"])
     ell = [int(v) for v in point["ell"]]
     em = [int(v) for v in point["em"]]
-    sincos, expo, df_mul, df_add = 82, 44, 7, 20
+    sincos, expo, df_mul, df_add, horner = 51, 28, 7, 11, 12
     # distance factor, sky angles, sky direction, antenna basis, 2 psi, iota
     # (the antenna basis is also split into heads and tails once per draw: 40)
     fixed = (10 + expo) + (10 + 2 * sincos + 2 * df_mul) + 187 + 40 + (sincos + 2 * df_mul) + sincos
-    # modes: Horner in cos(iota) (15 per degree), sin(iota) factor for odd m,
-    # Y = amp e^{i m phi} and its split; the modes are visited by increasing
-    # |m|: e^{i |m| phi} by one pair complex product (68) when |m| grows by
-    # one after |m| = 1 was met, otherwise by an anchored sine/cosine
-    modes = sum(15 * l for l in ell) + df_mul * sum(1 for m in em if m % 2) + M * (2 * df_mul + 8)
+    # modes: Horner in cos(iota) (one step per degree), sin(iota) factor for
+    # odd m, Y = amp e^{i m phi} and its split; the modes are visited by
+    # increasing |m|: e^{i |m| phi} by one pair complex product (4 products,
+    # 2 sums) when |m| grows by one after |m| = 1 was met, otherwise by an
+    # anchored sine/cosine
+    modes = sum(horner * l + 3 for l in ell) + df_mul * sum(1 for m in em if m % 2) + M * (2 * df_mul + 8)
     prev, have1 = -1, False
     for am in sorted({abs(m) for m in em}):
-        modes += 68 if (have1 and am == prev + 1) else sincos
+        modes += (4 * df_mul + 2 * df_add) if (have1 and am == prev + 1) else sincos
         have1 = have1 or am == 1
         prev = am
-    # split product a1, a2 (12 per entry); per direction two TwoSums and the
-    # head/tail split of the pair (20)
-    matvec = 12 * R * M + 20 * R
+    # split product a1, a2 (12 per entry); per direction the head/tail split
+    # of the pair on the grid of the exact head sums (10)
+    matvec = 12 * R * M + 10 * R
     # F_+(0), F_x(0) by head x head products and FP32 cross terms (4 per
     # coefficient), x e^{2 i psi} F as two compensated complex parts (19 each)
     antenna = 10 * 4 + 2 * 19
     template = 8 + 8 * R  # split of x F, then 8 per direction
-    timing = 2 * df_add + df_mul + 3 + 6 * 14 + 3 + 16 + 32 + 2  # position, 1/2|e|^2 sextic, weights
-    residual = 4 * 3 * R + 2 * R + R + 16                  # taps, sigma and low part, |r|^2, T
+    timing = 2 * df_add + df_mul + 3 + 6 * horner + 2  # position, 1/2|e|^2 sextic
+    residual = 6 * R + R + 16  # the interval's cubic and the residual, |r|^2, T
     per_det = antenna + template + timing + residual
     n_pos = len({tuple(np.round(np.asarray(point["det_pos"], dtype=np.float64)[k], 12))
                  for k in range(K)})
-    delay = n_pos * (3 * df_mul + 2 * df_add)
+    delay = n_pos * 31
     lse = 17
     total = fixed + ncls * (modes + matvec) + K * per_det + delay + lse
     return {"ops_per_draw": int(total), "per_detector": int(per_det),
@@ -608,9 +609,10 @@ def comp_mixed_fp32_ops(K: int, M: int, na: int, R: int, ncls: int) -> int:
     pair the a1/a2 sums (12 packed FMAs, 24 lane ops, on the kernel's mode
     bucket); per class, index and direction the split (6 packed ops); per
     detector, index and direction the template products (3 packed FMAs); per
-    detector and direction pair the residual over four taps (14 packed ops)."""
+    detector and direction pair the residual from the interval's cubic
+    coefficients (7 packed ops)."""
     jp = (4 if M <= 4 else 10 if M <= 10 else 16) // 2
-    return (ncls * na * R * (jp * 24 + 12) + K * na * R * 6 + K * (R // 2) * 28)
+    return (ncls * na * R * (jp * 24 + 12) + K * na * R * 6 + K * (R // 2) * 14)
 
 
 def run_response(args):

@@ -227,7 +227,8 @@ __global__ void whiten_kernel(const double* __restrict__ proj, const double* __r
 }
 
 // The interpolating cubic of each interval j = -3..n+1 (taps j-1..j+2 of the
-// zero-padded table): e(f) = c0 + c1 f + c2 f^2 + c3 f^3 with, for the tap
+// zero-padded table; the four-point cubic C_3 of eq. q-time-pregrid):
+// e(f) = c0 + c1 f + c2 f^2 + c3 f^3 with, for the tap
 // values e_{-1}, e_0, e_1, e_2 (nodes -1, 0, 1, 2),
 //   c0 = e_0,  c1 = -e_{-1}/3 - e_0/2 + e_1 - e_2/6,  c2 = e_{-1}/2 - e_0 + e_1/2,
 //   c3 = -e_{-1}/6 + e_0/2 - e_1/2 + e_2/6
