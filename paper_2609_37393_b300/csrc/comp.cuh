@@ -154,6 +154,7 @@ struct rift_ile_comp {
   int mixed_built;
   int mixed_R[rift::kMaxDet];   // kept directions of each class
   int mixed_threads, mixed_bsmem;  // launch shape: block size, split whitening in shared memory
+  int mixed_minb;                  // lnL kernel variant: sized for 2 or 3 resident blocks per SM
   int grad_threads, grad_bsmem;    // the same for the adjoint
   double mixed_tol;
   rift::CompMixed mixed;        // host copy (pointers are device pointers)

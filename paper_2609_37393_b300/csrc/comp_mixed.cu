@@ -27,14 +27,14 @@
 namespace rift {
 
 template <int MM>
-cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
-                           double* lnl_out, LseState* partials, unsigned long long* oob,
-                           int* blocks, cudaStream_t st);
+cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, int minb,
+                           const DrawsParams& dp, double* lnl_out, LseState* partials,
+                           unsigned long long* oob, int* blocks, cudaStream_t st);
 template <int MM>
 cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
                             double* lnl_out, double* grad_out, cudaStream_t st);
 template <int MM>
-int comp_mixed_regs(bool grad);
+int comp_mixed_regs(bool grad, int minb);
 
 namespace {
 
@@ -45,11 +45,11 @@ cudaError_t launch_comp_mixed(const rift_ile_comp* cp, const DrawsParams& dp, do
                               cudaStream_t st) {
   const CompMixed& C = cp->mixed;
   const bool bs = cp->mixed_bsmem != 0;
-  const int th = cp->mixed_threads;
+  const int th = cp->mixed_threads, mb = cp->mixed_minb;
   switch (mm_bucket(C.M)) {
-    case 4: return comp_mixed_lnl<4>(C, bs, th, dp, lnl_out, partials, oob, blocks, st);
-    case 10: return comp_mixed_lnl<10>(C, bs, th, dp, lnl_out, partials, oob, blocks, st);
-    default: return comp_mixed_lnl<16>(C, bs, th, dp, lnl_out, partials, oob, blocks, st);
+    case 4: return comp_mixed_lnl<4>(C, bs, th, mb, dp, lnl_out, partials, oob, blocks, st);
+    case 10: return comp_mixed_lnl<10>(C, bs, th, mb, dp, lnl_out, partials, oob, blocks, st);
+    default: return comp_mixed_lnl<16>(C, bs, th, mb, dp, lnl_out, partials, oob, blocks, st);
   }
 }
 
@@ -398,7 +398,9 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
   const int shapes[6][2] = {{128, 1}, {128, 0}, {64, 1}, {64, 0}, {32, 1}, {32, 0}};
   // for the lnL kernels and for the adjoint, the shape with the most resident
   // warps per SM given the kernel's registers and shared memory (ties: the
-  // whitening staged, then the larger block).  Without a fitting shape for
+  // whitening staged, then the larger block; for the lnL kernels also the
+  // variant sized for two or three blocks per SM, ties to two, whose larger
+  // register budget costs fewer instructions).  Without a fitting shape for
   // the adjoint only the gradient entry point reports UNSUPPORTED.
   {
     int smem_sm = 0;
@@ -408,25 +410,36 @@ extern "C" int rift_ile_comp_mixed_build(rift_ile_comp* cp, double tol, void* st
       return rc;
     }
     for (int grad = 0; grad < 2; ++grad) {
-      int regs = 0;
-      switch (mm_bucket(C.M)) {
-        case 4: regs = comp_mixed_regs<4>(grad != 0); break;
-        case 10: regs = comp_mixed_regs<10>(grad != 0); break;
-        default: regs = comp_mixed_regs<16>(grad != 0); break;
-      }
-      if (regs <= 0) regs = 255;
-      const int regs_r = (regs + 7) & ~7;  // allocation granularity
       int best = 0;
-      for (const auto& sh : shapes) {
-        const size_t sm = comp_mixed_smem(C, sh[1] != 0, sh[0], grad != 0) + static_smem;
-        if (sm > (size_t)optin) continue;
-        const int by_smem = (int)((size_t)smem_sm / (sm + 1024));  // 1 KB reserved per block
-        const int by_regs = 65536 / (regs_r * sh[0]);
-        const int warps = std::min(by_smem, by_regs) * (sh[0] / 32);
-        if (warps > best) {
-          best = warps;
-          (grad ? cp->grad_threads : cp->mixed_threads) = sh[0];
-          (grad ? cp->grad_bsmem : cp->mixed_bsmem) = sh[1];
+      for (int minb = 2; minb <= (grad ? 2 : 3); ++minb) {
+        int regs = 0;
+        switch (mm_bucket(C.M)) {
+          case 4: regs = comp_mixed_regs<4>(grad != 0, minb); break;
+          case 10: regs = comp_mixed_regs<10>(grad != 0, minb); break;
+          default: regs = comp_mixed_regs<16>(grad != 0, minb); break;
+        }
+        if (regs <= 0) {
+          if (minb > 2) continue;  // no such variant for this bucket
+          regs = 255;
+        }
+        const int regs_r = (regs + 7) & ~7;  // allocation granularity
+        for (const auto& sh : shapes) {
+          const size_t sm = comp_mixed_smem(C, sh[1] != 0, sh[0], grad != 0) + static_smem;
+          if (sm > (size_t)optin) continue;
+          const int by_smem = (int)((size_t)smem_sm / (sm + 1024));  // 1 KB reserved per block
+          const int by_regs = 65536 / (regs_r * sh[0]);
+          const int warps = std::min(by_smem, by_regs) * (sh[0] / 32);
+          if (warps > best) {
+            best = warps;
+            if (grad) {
+              cp->grad_threads = sh[0];
+              cp->grad_bsmem = sh[1];
+            } else {
+              cp->mixed_threads = sh[0];
+              cp->mixed_bsmem = sh[1];
+              cp->mixed_minb = minb;
+            }
+          }
         }
       }
     }

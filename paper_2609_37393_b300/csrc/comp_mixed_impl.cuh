@@ -834,8 +834,10 @@ __device__ __forceinline__ df comp_mixed_draw(const CompMixed& C, const float4* 
   return out;
 }
 
-template <int MM, bool BSMEM, bool LSE>
-__global__ void __launch_bounds__(kCompMixedThreads, 2)
+// MINB: the resident blocks per SM the registers are sized for (2, or 3 where
+// shared memory admits three blocks: up to ten modes that fits without spills).
+template <int MM, bool BSMEM, bool LSE, int MINB>
+__global__ void __launch_bounds__(kCompMixedThreads, MINB)
     comp_mixed_kernel(const __grid_constant__ CompMixed C, DrawsParams dp,
                       double* __restrict__ lnl_out, LseState* __restrict__ partials,
                       unsigned long long* __restrict__ oob_count) {
@@ -917,11 +919,11 @@ cudaError_t comp_blocks_per_sm(KernelT kern, int threads, size_t smem, int* per_
   return cudaSuccess;
 }
 
-template <int MM, bool BSMEM, bool LSE>
+template <int MM, bool BSMEM, bool LSE, int MINB>
 cudaError_t launch_comp_mixed_k(const CompMixed& C, int threads, const DrawsParams& dp,
                                 double* lnl_out, LseState* partials, unsigned long long* oob,
                                 int* blocks, cudaStream_t st) {
-  auto kern = comp_mixed_kernel<MM, BSMEM, LSE>;
+  auto kern = comp_mixed_kernel<MM, BSMEM, LSE, MINB>;
   const size_t smem = comp_mixed_smem(C, BSMEM, threads);
   int per_sm = 0;
   const cudaError_t e = comp_blocks_per_sm(kern, threads, smem, &per_sm);
@@ -979,20 +981,33 @@ cudaError_t launch_comp_mixed_grad_k(const CompMixed& C, int threads, const Draw
   return cudaGetLastError();
 }
 
+template <int MM, int MINB>
+cudaError_t comp_mixed_lnl_b(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
+                             double* lnl_out, LseState* partials, unsigned long long* oob,
+                             int* blocks, cudaStream_t st) {
+  if (partials)
+    return bsmem ? launch_comp_mixed_k<MM, true, true, MINB>(C, threads, dp, lnl_out, partials, oob, blocks, st)
+                 : launch_comp_mixed_k<MM, false, true, MINB>(C, threads, dp, lnl_out, partials, oob, blocks, st);
+  return bsmem ? launch_comp_mixed_k<MM, true, false, MINB>(C, threads, dp, lnl_out, partials, oob, blocks, st)
+               : launch_comp_mixed_k<MM, false, false, MINB>(C, threads, dp, lnl_out, partials, oob, blocks, st);
+}
+
 }  // namespace
 
 // Entry point of one mode-count bucket (explicitly instantiated by the
 // lnl_mixed_m4/m10/m16 translation units, dispatched in comp_mixed.cu): B is
-// staged in shared memory when bsmem; `threads` per block (128, 64 or 32).
+// staged in shared memory when bsmem; `threads` per block (128, 64 or 32);
+// the kernel variant sized for minb resident blocks per SM (3 only up to ten
+// modes, else 2).
 template <int MM>
-cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, const DrawsParams& dp,
-                           double* lnl_out, LseState* partials, unsigned long long* oob,
-                           int* blocks, cudaStream_t st) {
-  if (partials)
-    return bsmem ? launch_comp_mixed_k<MM, true, true>(C, threads, dp, lnl_out, partials, oob, blocks, st)
-                 : launch_comp_mixed_k<MM, false, true>(C, threads, dp, lnl_out, partials, oob, blocks, st);
-  return bsmem ? launch_comp_mixed_k<MM, true, false>(C, threads, dp, lnl_out, partials, oob, blocks, st)
-               : launch_comp_mixed_k<MM, false, false>(C, threads, dp, lnl_out, partials, oob, blocks, st);
+cudaError_t comp_mixed_lnl(const CompMixed& C, bool bsmem, int threads, int minb,
+                           const DrawsParams& dp, double* lnl_out, LseState* partials,
+                           unsigned long long* oob, int* blocks, cudaStream_t st) {
+  if constexpr (MM <= 10) {
+    if (minb == 3)
+      return comp_mixed_lnl_b<MM, 3>(C, bsmem, threads, dp, lnl_out, partials, oob, blocks, st);
+  }
+  return comp_mixed_lnl_b<MM, 2>(C, bsmem, threads, dp, lnl_out, partials, oob, blocks, st);
 }
 
 // The adjoint's entry point of one bucket (launch shape chosen by the build
@@ -1005,26 +1020,35 @@ cudaError_t comp_mixed_grad(const CompMixed& C, bool bsmem, int threads, const D
 }
 
 // Registers per thread of the adjoint kernel (grad) or of the fused lnZ kernel
-// of one bucket (the larger of the two variants; 0 on error), for the build's
-// choice of launch shape.
+// variant sized for minb blocks per SM of one bucket (the larger of the
+// staged and unstaged variants; 0 on error, or when the bucket has no such
+// variant), for the build's choice of launch shape.
 template <int MM>
-int comp_mixed_regs(bool grad) {
+int comp_mixed_regs(bool grad, int minb) {
   cudaFuncAttributes a, b;
-  cudaError_t e = grad ? cudaFuncGetAttributes(&a, comp_mixed_grad_kernel<MM, true>)
-                       : cudaFuncGetAttributes(&a, comp_mixed_kernel<MM, true, true>);
-  if (e == cudaSuccess)
-    e = grad ? cudaFuncGetAttributes(&b, comp_mixed_grad_kernel<MM, false>)
-             : cudaFuncGetAttributes(&b, comp_mixed_kernel<MM, false, true>);
+  cudaError_t e = cudaErrorInvalidValue;
+  if (grad) {
+    e = cudaFuncGetAttributes(&a, comp_mixed_grad_kernel<MM, true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, comp_mixed_grad_kernel<MM, false>);
+  } else if (minb == 2) {
+    e = cudaFuncGetAttributes(&a, comp_mixed_kernel<MM, true, true, 2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, comp_mixed_kernel<MM, false, true, 2>);
+  } else if constexpr (MM <= 10) {
+    if (minb == 3) {
+      e = cudaFuncGetAttributes(&a, comp_mixed_kernel<MM, true, true, 3>);
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, comp_mixed_kernel<MM, false, true, 3>);
+    }
+  }
   if (e != cudaSuccess) return 0;
   return a.numRegs > b.numRegs ? a.numRegs : b.numRegs;
 }
 
 #define RIFT_INSTANTIATE_COMP_MIXED(MM)                                                        \
-  template cudaError_t comp_mixed_lnl<MM>(const CompMixed&, bool, int, const DrawsParams&,      \
+  template cudaError_t comp_mixed_lnl<MM>(const CompMixed&, bool, int, int, const DrawsParams&, \
                                           double*, LseState*, unsigned long long*, int*,         \
                                           cudaStream_t);                                         \
   template cudaError_t comp_mixed_grad<MM>(const CompMixed&, bool, int, const DrawsParams&,     \
                                            double*, double*, cudaStream_t);                      \
-  template int comp_mixed_regs<MM>(bool);
+  template int comp_mixed_regs<MM>(bool, int);
 
 }  // namespace rift
