@@ -439,6 +439,12 @@ class Batch:
             pass
 
 
+def _comp_mixed(cp, precision) -> bool:
+    """Whether a composite point evaluates in its FP32-mixed form: asked for
+    and built (rift_ile_comp_mixed_build)."""
+    return precision == FP32_MIXED and rift_ile_comp_mixed_info(cp)[0] > 0
+
+
 def _make_autograd():
     torch = _torch()
 
@@ -465,10 +471,12 @@ def _make_autograd():
             if isinstance(point, CompPoint):
                 if dist is not None:
                     raise ValueError("distance marginalisation is not built for CompPoint")
+                mixed = _comp_mixed(point, precision)
                 if need and not recompute:
-                    lnl, ctx.grad = rift_ile_comp_lnL_grad(point, draws)
+                    lnl, ctx.grad = (rift_ile_comp_lnL_grad_mixed if mixed
+                                     else rift_ile_comp_lnL_grad)(point, draws)
                 else:
-                    lnl = rift_ile_comp_lnL(point, draws)
+                    lnl = (rift_ile_comp_lnL_mixed if mixed else rift_ile_comp_lnL)(point, draws)
             elif dist is not None:
                 if need and not recompute:
                     lnl, ctx.grad = rift_ile_lnL_dist(point, draws, dist, precision, grad=True)
@@ -487,7 +495,8 @@ def _make_autograd():
                 theta = ctx.saved_tensors
                 draws = Draws(dict(zip(PARAMS, theta)))
                 if isinstance(ctx.point, CompPoint):
-                    _, g = rift_ile_comp_lnL_grad(ctx.point, draws)
+                    _, g = (rift_ile_comp_lnL_grad_mixed if _comp_mixed(ctx.point, ctx.precision)
+                            else rift_ile_comp_lnL_grad)(ctx.point, draws)
                 elif ctx.dist is not None:
                     _, g = rift_ile_lnL_dist(ctx.point, draws, ctx.dist, ctx.precision, grad=True)
                 else:
@@ -508,8 +517,9 @@ def lnL(point: Point, ra, dec, psi, incl, phase, lnD, t, precision: int = FP32_M
         dist=None, recompute: bool = False):
     """Differentiable lnL[n] (float64) of CUDA tensors of draws (torch autograd);
     dist = (x_nodes, lnw_nodes) marginalises the distance (eq. ap:dexp).  A
-    CompPoint (composite-index response, Sec. III) evaluates in FP64 whatever
-    `precision` says."""
+    CompPoint (composite-index response, Sec. III) evaluates in its FP32-mixed
+    form when `precision` is FP32_MIXED and that form is built
+    (rift_ile_comp_mixed_build), else in FP64."""
     global _LnLFunction
     if _LnLFunction is None:
         _LnLFunction = _make_autograd()

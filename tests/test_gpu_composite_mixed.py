@@ -23,7 +23,9 @@ against the composite oracle:
   non-finite arrival time; the empty draw set;
 * calls before the build, and tol outside (0, 1), are errors;
 * on the 3G network at full size (2^22 draws, the bench's launch), sampled
-  draws against the oracle and the fused lnZ against the FP64 path's.
+  draws against the oracle and the fused lnZ against the FP64 path's; the
+  adjoint of Paths A, B and D against the FP64 adjoint; torch.autograd
+  through a CompPoint switching to the mixed form once it is built.
 """
 import math
 
@@ -116,6 +118,34 @@ def test_mixed_gradient_matches_oracle(R, kind, p_max):
         s = np.abs(ref_g[:, j]) + np.sqrt(np.mean(ref_g[:, j] ** 2))
         err = np.max(np.abs(g[j] - ref_g[:, j]) / s)
         assert err <= TOL_G, (p, err)
+
+
+def test_autograd_uses_the_mixed_form_once_built(R):
+    """torch.autograd through a CompPoint: FP64 until the mixed form is built,
+    then (precision FP32_MIXED) the mixed adjoint, bit for bit; FP64 asked for
+    explicitly stays FP64."""
+    point, draws, logw, ref = fixture(WC.ROTATION, 0)
+    cp = R.CompPoint(point)
+    n = 48
+    sub = {p: np.asarray(draws[p])[:n] for p in W.PARAMS}
+    wts = torch.linspace(-1.0, 2.0, n, dtype=torch.float64, device="cuda")
+
+    def grads(precision):
+        th = [torch.tensor(sub[p], dtype=torch.float64, device="cuda", requires_grad=True)
+              for p in W.PARAMS]
+        lnl = R.lnL(cp, *th, precision=precision)
+        (lnl * wts).sum().backward()
+        return lnl.detach(), [t.grad for t in th]
+
+    l64, g64 = grads(R.FP32_MIXED)
+    rl, rg = R.rift_ile_comp_lnL_grad(cp, R.Draws(sub))
+    assert torch.equal(l64, rl) and all(torch.equal(g64[j], rg[j] * wts) for j in range(7))
+    R.rift_ile_comp_mixed_build(cp, EIG_TOL)
+    lm, gm = grads(R.FP32_MIXED)
+    rl, rg = R.rift_ile_comp_lnL_grad_mixed(cp, R.Draws(sub))
+    assert torch.equal(lm, rl) and all(torch.equal(gm[j], rg[j] * wts) for j in range(7))
+    lf, gf = grads(R.FP64)
+    assert torch.equal(lf, l64)
 
 
 def test_mixed_gradient_nonfinite_empty_and_errors(R):
@@ -245,6 +275,24 @@ def test_full_size_path_a_gradient_vs_fp64(R, big):
     cp = R.CompPoint(point)
     R.rift_ile_comp_mixed_build(cp, EIG_TOL)
     d = R.Draws(sub)
+    lm, gm = R.rift_ile_comp_lnL_grad_mixed(cp, d)
+    lf, gf = R.rift_ile_comp_lnL_grad(cp, d)
+    near = lf > lf.max() - 50.0
+    assert int(near.sum()) > 100
+    for j, p in enumerate(W.PARAMS):
+        s = gf[j].abs() + gf[j][near].pow(2).mean().sqrt()
+        err = float(((gm[j] - gf[j]).abs() / s)[near].max())
+        assert err <= TOL_G, (p, err)
+
+
+@pytest.mark.parametrize("kind,p_max", [(WC.ROTATION, 1), (WC.FINITE_ARM, 3)])
+def test_full_size_paths_b_and_d_gradient_vs_fp64(R, kind, p_max):
+    """3G network, Paths B and D, 2^18 float32 draws: the mixed adjoint
+    against the FP64 adjoint within TOL_G of |g| + RMS g within 50 nat."""
+    point, exact, info, draws, logw = WC.comp_3g(kind, p_max, n_draws=1 << 18)
+    cp = R.CompPoint(point)
+    R.rift_ile_comp_mixed_build(cp, EIG_TOL)
+    d = R.Draws(draws)
     lm, gm = R.rift_ile_comp_lnL_grad_mixed(cp, d)
     lf, gf = R.rift_ile_comp_lnL_grad(cp, d)
     near = lf > lf.max() - 50.0
