@@ -518,7 +518,8 @@ def run_sampler(args):
     of draws, as a gradient-based extrinsic sampler issues them; per-call
     latency through the Python API (eager), replayed from a captured CUDA graph
     (one call per replay), and as 32 calls chained in one graph (the device
-    time per call of a sampler loop captured whole), for the warp-per-draw
+    time per call of a sampler loop captured whole), and eagerly through a
+    prepared call (arguments marshalled once), for the warp-per-draw
     kernel (two warps per draw; the default up to 2048 draws) and the
     one-thread-per-draw kernel."""
     import torch
@@ -556,6 +557,9 @@ def run_sampler(args):
             for name, limit in (("warp", 1 << 20), ("thread", 0)):
                 R.rift_ile_set_small_batch(limit)
                 r = {"eager_us_per_call": timed_events(torch, call, 200, stream) * 1e3}
+                # the same call with its arguments marshalled once (prepare_lnL_grad)
+                prep = R.prepare_lnL_grad(pt, d, R.FP32_MIXED, lnl, g)
+                r["eager_prepared_us_per_call"] = timed_events(torch, prep, 200, stream) * 1e3
                 try:
                     g1 = graph_of(call, 1)
                     r["graph_us_per_call"] = timed_events(torch, g1.replay, 200, stream) * 1e3

@@ -100,9 +100,17 @@ def _torch():
 
 
 def _stream(stream=None) -> int:
+    """The raw CUDA stream handle of `stream`, or of torch's current stream
+    (looked up without building a Stream object, which costs a few
+    microseconds per call, where this torch exposes the raw lookup)."""
     torch = _torch()
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return int(s.cuda_stream)
+    if stream is not None:
+        return int(stream.cuda_stream)
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+    dev = getattr(torch._C, "_cuda_getDevice", None)
+    if raw is not None and dev is not None:
+        return int(raw(dev()))
+    return int(torch.cuda.current_stream().cuda_stream)
 
 
 def _dev_tensor(x, dtype, device):
@@ -300,6 +308,61 @@ def rift_ile_lnL_grad(point: Point, draws, precision: int = FP32_MIXED, lnl_out=
                                   lnl_out.data_ptr() if d.n else None,
                                   grad_out.data_ptr() if d.n else None, _stream(stream)))
     return lnl_out, grad_out
+
+
+class PreparedCall:
+    """One lnL (+ gradient) launch with its C-ABI arguments marshalled once,
+    for a caller that evaluates the same point on the same device buffers
+    again and again (a sampler updating its draws in place): calling the
+    object launches rift_ile_lnL_grad (or rift_ile_lnL) on the stream given
+    at preparation and returns the output tensors, with no host
+    synchronisation and no per-call argument conversion.  The draws' buffers
+    and the outputs must stay alive and keep their size."""
+
+    def __init__(self, point: Point, draws, precision: int, grad: bool, lnl_out=None,
+                 grad_out=None, stream=None):
+        torch = _torch()
+        self.draws = _as_draws(draws)
+        n = self.draws.n
+        if n == 0:
+            raise ValueError("PreparedCall needs at least one draw")
+        self.lnl = lnl_out if lnl_out is not None else torch.empty(
+            n, dtype=torch.float64, device=point.device)
+        self.grad = None
+        if grad:
+            self.grad = grad_out if grad_out is not None else torch.empty(
+                (7, n), dtype=torch.float64, device=point.device)
+        self.point = point
+        P = ctypes.c_void_p
+        s = P(_stream(stream))
+        if grad:
+            fn = _lib.rift_ile_lnL_grad
+            args = (point.handle, self.draws.ref, ctypes.c_int(precision),
+                    P(self.lnl.data_ptr()), P(self.grad.data_ptr()), s)
+        else:
+            fn = _lib.rift_ile_lnL
+            args = (point.handle, self.draws.ref, ctypes.c_int(precision),
+                    P(self.lnl.data_ptr()), s)
+        self._fn, self._args = fn, args
+
+    def __call__(self):
+        rc = self._fn(*self._args)
+        if rc != 0:
+            _check(rc)
+        return (self.lnl, self.grad) if self.grad is not None else self.lnl
+
+
+def prepare_lnL_grad(point: Point, draws, precision: int = FP32_MIXED, lnl_out=None,
+                     grad_out=None, stream=None) -> PreparedCall:
+    """A PreparedCall of rift_ile_lnL_grad: each call launches lnL and its
+    gradient into the same outputs."""
+    return PreparedCall(point, draws, precision, True, lnl_out, grad_out, stream)
+
+
+def prepare_lnL(point: Point, draws, precision: int = FP32_MIXED, lnl_out=None,
+                stream=None) -> PreparedCall:
+    """A PreparedCall of rift_ile_lnL."""
+    return PreparedCall(point, draws, precision, False, lnl_out, None, stream)
 
 
 def _dist_struct(dist):

@@ -210,3 +210,33 @@ def test_chained_calls_see_their_predecessors_writes(R, cfg2):
         check()
     finally:
         R.rift_ile_set_small_batch(4096)
+
+
+def test_prepared_call_matches_and_follows_its_buffers(R, cfg2):
+    """prepare_lnL_grad / prepare_lnL: the marshalled-once launch gives the
+    plain call's results bit for bit, and a later call sees draws written
+    into the same buffers in place."""
+    point, exact, info, draws, logw = cfg2
+    pt = R.Point(point)
+    n = 128
+    a = {p: torch.tensor(np.asarray(draws[p])[:n], dtype=torch.float64, device="cuda")
+         for p in W.PARAMS}
+    b = {p: torch.tensor(np.asarray(draws[p])[n:2 * n], dtype=torch.float64, device="cuda")
+         for p in W.PARAMS}
+    buf = {p: a[p].clone() for p in W.PARAMS}
+    d = R.Draws(buf)
+    R.rift_ile_set_small_batch(1 << 20)
+    try:
+        call = R.prepare_lnL_grad(pt, d, R.FP32_MIXED)
+        fwd = R.prepare_lnL(pt, d, R.FP32_MIXED)
+        l, g = call()
+        ref_l, ref_g = R.rift_ile_lnL_grad(pt, R.Draws(a), R.FP32_MIXED)
+        assert torch.equal(l, ref_l) and torch.equal(g, ref_g)
+        assert torch.equal(fwd(), R.rift_ile_lnL(pt, R.Draws(a), R.FP32_MIXED))
+        for p in W.PARAMS:
+            buf[p].copy_(b[p])
+        l, g = call()
+        ref_l, ref_g = R.rift_ile_lnL_grad(pt, R.Draws(b), R.FP32_MIXED)
+        assert torch.equal(l, ref_l) and torch.equal(g, ref_g)
+    finally:
+        R.rift_ile_set_small_batch(4096)
