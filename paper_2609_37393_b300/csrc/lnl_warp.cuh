@@ -640,9 +640,11 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
           gk[3] = fmaf(-xFr, g1, -xFi * g2);
         }
       }
-      // the sums over detectors: a fixed shuffle tree over lanes 0..7
+      // the sums over detectors: a fixed shuffle tree over lanes 0..7 (the
+      // levels whose upper half holds no detector only add zeros: skipped)
   #pragma unroll
       for (int off = 4; off > 0; off >>= 1) {
+        if (off >= K) continue;  // uniform over the warp
         dacc o;
         o.s = __shfl_down_sync(0xffffffffu, tk.s, off, 8);
         o.c = __shfl_down_sync(0xffffffffu, tk.c, off, 8);
@@ -697,9 +699,12 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         gph = fmaf((float)m, fmaf(-yim, Hre, yre * Him), gph);
         gin = fmaf(damp * cmf, Hre, fmaf(sgn * damp * smf, Him, gin));
       }
-      // a fixed shuffle tree over the 32 lanes
+      // a fixed shuffle tree over the 32 lanes (levels above the lanes that
+      // hold terms only add zeros: skipped)
+      const int nact = ncls * M < 32 ? ncls * M : 32;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
+        if (off >= nact) continue;  // uniform over the warp
         gph += __shfl_down_sync(0xffffffffu, gph, off);
         gin += __shfl_down_sync(0xffffffffu, gin, off);
       }
