@@ -79,6 +79,8 @@ struct DirectParams {
   double hi_lo;           // hi / lo
   double lnnorm_lo;       // lnnorm - 4 ln lo (the sum taken in y = x / lo)
   float wf[RIFT_ILE_MAX_GH];
+  float xif[RIFT_ILE_MAX_GH];  // the nodes in float, and hi / lo
+  float hi_lof;
   double2 e2[kPsiTab];    // e^{2 i psi_b}, psi_b = pi b / n_psi (n_psi <= kPsiTab)
   double2 e4[kPsiTab];    // e^{4 i psi_b}
   float2 e2f[kPsiTab];    // the same in float, for the first pass
@@ -303,25 +305,36 @@ __device__ __forceinline__ void direct_node(const double2& D, double A, const do
 // ln of the Gauss-Hermite distance integral at one node (eq. ap:dgh).
 __device__ double direct_distance(const DirectParams& Q, double K, double R) {
   if (!(R > 0.0)) return -CUDART_INF;
-  const double sig = rsqrt(R), xs = K / R;
+  const double sig = rsqrt(R);
   const double h = 1.4142135623730951 * sig;
   if (Q.mixed) {
-    // y = x / lo in [1, hi / lo] inside the prior, so y^-4 lies in [(lo/hi)^4, 1]
-    const double ys = xs * Q.inv_lo, hy = h * Q.inv_lo;
+    // y = x / lo in [1, hi / lo] inside the prior, so y^-4 lies in [(lo/hi)^4, 1];
+    // x* = K / R as K sig^2.  The nodes y in float (error ~1e-6, far below
+    // the integrand's needs); a node within 1e-5 of either edge of the prior
+    // is placed in double, so that every in/out decision is the double one
+    const double ys = K * (sig * sig) * Q.inv_lo, hy = h * Q.inv_lo;
+    const float ysf = (float)ys, hyf = (float)hy, hlf = Q.hi_lof;
     float sf = 0.0f;
     for (int j = 0; j < Q.n_gh; ++j) {
-      const double y = fma(hy, Q.xi[j], ys);
-      if (y >= 1.0 && y <= Q.hi_lo) {
-        const float r = __frcp_rn((float)y), r2 = r * r;
+      float y = fmaf(hyf, Q.xif[j], ysf);
+      bool in = y >= 1.0f && y <= hlf;
+      if (fabsf(y - 1.0f) < 1e-5f || fabsf(y - hlf) < 1e-5f * hlf) {
+        const double yd = fma(hy, Q.xi[j], ys);
+        in = yd >= 1.0 && yd <= Q.hi_lo;
+        y = (float)yd;
+      }
+      if (in) {
+        const float r = __frcp_rn(y), r2 = r * r;
         sf = fmaf(Q.wf[j], r2 * r2, sf);
       }
     }
     if (!(sf > 0.0f)) return -CUDART_INF;
-    // K^2/(2R) = (K sig)^2 / 2 in double (sig = R^-1/2 above); the logarithm
-    // of the O(1) factor h sf in float (absolute error ~1e-7 nat)
+    // K^2/(2R) = (K sig)^2 / 2 in double; the logarithm of the O(1) factor
+    // h sf in float (absolute error ~1e-7 nat)
     const double ks = K * sig;
     return 0.5 * ks * ks + (double)__logf((float)h * sf) + Q.lnnorm_lo;
   }
+  const double xs = K / R;
   double s = 0.0;
   for (int j = 0; j < Q.n_gh; ++j) {
     const double x = fma(h, Q.xi[j], xs);
@@ -893,7 +906,11 @@ extern "C" int rift_ile_lnL_direct(const rift_ile_point* pt, const rift_ile_draw
   Q.inv_lo = 1.0 / Q.lo;
   Q.hi_lo = Q.hi / Q.lo;
   Q.lnnorm_lo = Q.lnnorm - 4.0 * std::log(Q.lo);
-  for (int j = 0; j < Q.n_gh; ++j) Q.wf[j] = (float)Q.w[j];
+  for (int j = 0; j < Q.n_gh; ++j) {
+    Q.wf[j] = (float)Q.w[j];
+    Q.xif[j] = (float)Q.xi[j];
+  }
+  Q.hi_lof = (float)Q.hi_lo;
   if (Q.n_psi <= kPsiTab)
     for (int b = 0; b < Q.n_psi; ++b) {
       const double ang = 2.0 * M_PI * b / Q.n_psi;
