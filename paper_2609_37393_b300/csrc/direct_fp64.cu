@@ -370,6 +370,20 @@ __device__ double envelope_at(const PointParams& P, const DirDraw<MM>& g, double
   return u_sum;
 }
 
+// The same with the exponential of the (non-positive) offset in float, for the
+// mixed form: the running maximum and sum stay double; every term the sum
+// takes lies within the skip depth (~45 nat) of the maximum, where a float
+// exponential errs by ~1e-7 relative.
+__device__ __forceinline__ void lse_add_f(double& m, double& s, double v) {
+  if (!(v > -CUDART_INF)) return;
+  if (v > m) {
+    s = fma(s, (double)__expf((float)(m - v)), 1.0);
+    m = v;
+  } else {
+    s += (double)__expf((float)(v - m));
+  }
+}
+
 __device__ __forceinline__ void lse_add(double& m, double& s, double v) {
   if (!(v > -CUDART_INF)) return;
   if (v > m) {
@@ -526,7 +540,10 @@ __device__ __noinline__ void direct_time_node(const DirCoef& C, const DirectPara
       } else if (K * K < 2.0 * R * (c0 + 0.5 * log(R))) {
         continue;
       }
-      lse_add(m, s, direct_distance(Q, K, R));
+      if (Q.mixed)
+        lse_add_f(m, s, direct_distance(Q, K, R));
+      else
+        lse_add(m, s, direct_distance(Q, K, R));
     }
   }
 }
