@@ -742,36 +742,37 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       float jf = floorf(u.hi);
       if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
       const float f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
-      // 1/2 |e(f)|^2 from the interval polynomial (zero when no tap is in the
-      // table) and, for the adjoint, its slope in f (Horner on both)
-      df half_e2 = df{0.f, 0.f}, dhalf = df{0.f, 0.f};
-      if (jf >= -2.f && jf <= (float)n) {
-        const float2* pc = P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
-        float2 cf = __ldg(pc + kPolyDeg);
-        df acc = df{cf.x, cf.y};
-        df dacc_p = df{0.f, 0.f};
-#pragma unroll
-        for (int p = kPolyDeg - 1; p >= 0; --p) {
-          // acc = acc f + c_p and, for the adjoint, the slope d = d f + acc
-          // (horner_step, f exact in FP32; both sums absorb unnormalised pairs)
-          if (GRAD) dacc_p = horner_step_f(dacc_p, f, acc.hi, acc.lo);
-          cf = __ldg(pc + p);
-          acc = horner_step_f(acc, f, cf.x, cf.y);
-        }
-        half_e2 = acc;
-        dhalf = dacc_p;
-      }
-      // the interval's cubic: j clamped to [-3, n + 1], where every tap
+      // the interval's record: j clamped to [-3, n + 1], where every tap
       // outside the table is a zero row of the padded table the coefficients
-      // were formed from, so the loads need no test (taps outside are only
-      // counted)
+      // were formed from and the sextic is zero, so the loads need no test
+      // (taps outside are only counted)
       {  // taps outside the table: 1 - j below it, j + 3 - n above it (each in [0, 4])
         const float nb = fminf(fmaxf(1.f - jf, 0.f), 4.f);
         const float na = fminf(fmaxf(jf + 3.f - (float)n, 0.f), 4.f);
         oob += (int)fminf(nb + na, 4.f);
       }
       const int jc = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-      const float4* Cj = P.ecub + ((size_t)k * (n + 5) + (size_t)(jc + 3)) * (size_t)(R / 2) * 3;
+      const float4* Cj = P.erec + ((size_t)k * (n + 5) + (size_t)(jc + 3)) * (size_t)(3 * (R / 2) + 4);
+      // 1/2 |e(f)|^2 from the interval's sextic (pairs (c0, c1), (c2, c3),
+      // (c4, c5), (c6, -) after the cubic) and, for the adjoint, its slope in
+      // f (Horner on both: horner_step, f exact in FP32; both sums absorb
+      // unnormalised pairs)
+      df half_e2, dhalf = df{0.f, 0.f};
+      {
+        const float4* pe = Cj + 3 * (R / 2);
+        const float4 e01 = __ldg(pe), e23 = __ldg(pe + 1), e45 = __ldg(pe + 2), e6 = __ldg(pe + 3);
+        const float2 cf[kPolyDeg + 1] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
+                                         make_float2(e23.x, e23.y), make_float2(e23.z, e23.w),
+                                         make_float2(e45.x, e45.y), make_float2(e45.z, e45.w),
+                                         make_float2(e6.x, e6.y)};
+        df acc = df{cf[kPolyDeg].x, cf[kPolyDeg].y};
+#pragma unroll
+        for (int p = kPolyDeg - 1; p >= 0; --p) {
+          if (GRAD) dhalf = horner_step_f(dhalf, f, acc.hi, acc.lo);
+          acc = horner_step_f(acc, f, cf[p].x, cf[p].y);
+        }
+        half_e2 = acc;
+      }
       const float2 f2 = make_float2(f, f), f3 = make_float2(3.f * f, 3.f * f);
       // Per pair of directions: the template w_r = xFr a1_r + xFi a2_r (heads
       // of xF on the grid of its larger part; head x head products of 10 x 10

@@ -271,6 +271,33 @@ __global__ void cubic_table_kernel(const float2* __restrict__ ehat, int K, int n
   }
 }
 
+// The per-interval records of PointParams::erec from ecub and epoly.
+__global__ void interval_record_kernel(const float4* __restrict__ ecub,
+                                       const float2* __restrict__ epoly, int K, int n, int R,
+                                       float4* __restrict__ erec) {
+  const int NP = R / 2, rec = 3 * NP + 4, per = n + 5;
+  const long long total = (long long)K * per * rec;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(idx % rec);
+    const long long kq = idx / rec;
+    const int k = (int)(kq / per), q = (int)(kq % per);  // interval j = q - 3
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (w < 3 * NP) {
+      v = ecub[kq * 3 * NP + w];
+    } else {
+      const int j = q - 3, c = 2 * (w - 3 * NP);  // sextic coefficients c, c + 1
+      if (j >= -2 && j <= n) {
+        const float2* pc = epoly + ((size_t)k * (n + 3) + (size_t)(j + 2)) * (kPolyDeg + 1);
+        const float2 a = pc[c];
+        const float2 b = c + 1 <= kPolyDeg ? pc[c + 1] : make_float2(0.f, 0.f);
+        v = make_float4(a.x, a.y, b.x, b.y);
+      }
+    }
+    erec[idx] = v;
+  }
+}
+
 // Coefficients of 1/2 |e(f)|^2 on interval j (taps j-1..j+2, zero outside
 // the table): with e(f) = sum_i L_i(f) e_{j-1+i} and the Lagrange cubics
 // L_i(f) on nodes -1, 0, 1, 2, it is 1/2 sum_{i,i'} G_ii' L_i(f) L_i'(f), a
@@ -455,6 +482,7 @@ extern "C" int rift_ile_point_destroy(rift_ile_point* pt) {
   cudaFree(pt->ehat);
   cudaFree(pt->epoly);
   cudaFree(pt->ecub);
+  cudaFree(pt->erec);
   cudaFree(pt->img);
   delete pt;
   return RIFT_ILE_OK;
@@ -744,6 +772,7 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
       break;
     if ((rc = dev_alloc(&pt->epoly, (size_t)K * (n + 3) * (kPolyDeg + 1)))) break;
     if ((rc = dev_alloc(&pt->ecub, ecub_f4(K, n, R)))) break;
+    if ((rc = dev_alloc(&pt->erec, erec_f4(K, n, R)))) break;
     if ((rc = dev_alloc(&dinv_s, inv_s.size()))) break;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->A, A.data(), A.size() * sizeof(float2),
                                          cudaMemcpyHostToDevice, stream), "copy of A")))
@@ -763,6 +792,9 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     const long long tc3 = (long long)K * (n + 5) * (R / 2);
     cubic_table_kernel<<<(int)std::min<long long>((tc3 + 127) / 128, 148LL * 16), 128, 0, stream>>>(
         pt->ehat, K, n, R, pt->ecub);
+    const long long tr = (long long)erec_f4(K, n, R);
+    interval_record_kernel<<<(int)std::min<long long>((tr + 255) / 256, 148LL * 16), 256, 0, stream>>>(
+        pt->ecub, pt->epoly, K, n, R, pt->erec);
     if ((rc = check_cuda(cudaGetLastError(), "table kernels"))) break;
     P.Q = pt->q_copy;
     P.U = pt->uv;
@@ -772,6 +804,7 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     P.ehat = pt->ehat;
     P.epoly = pt->epoly;
     P.ecub = pt->ecub;
+    P.erec = pt->erec;
     if ((rc = build_mixed_image(P, &pt->img, &P.img_f4, stream))) break;
     P.img = pt->img;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->dev, &P, sizeof(PointParams), cudaMemcpyHostToDevice,

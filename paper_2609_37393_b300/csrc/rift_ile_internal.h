@@ -28,6 +28,10 @@ constexpr int kPolyDeg = 6;  // 1/2 |e(f)|^2 on one table interval is a sextic i
 constexpr int kEhatPad = 4;
 // Length in float4 of the cubic coefficient table (PointParams::ecub).
 inline size_t ecub_f4(int K, int n, int R) { return (size_t)K * (n + 5) * (R / 2) * 3; }
+// Float4 per interval record of PointParams::erec: the interval's cubic
+// coefficients (as in ecub) followed by its 1/2 |e|^2 sextic (7 pairs + 1).
+inline int erec_rec_f4(int R) { return 3 * (R / 2) + 4; }
+inline size_t erec_f4(int K, int n, int R) { return (size_t)K * (n + 5) * erec_rec_f4(R); }
 
 // Everything a kernel needs about one intrinsic point.  Lives in device
 // memory (one record per point) and is staged into shared memory by each
@@ -84,6 +88,10 @@ struct PointParams {
   // (index j + 3) as coefficients of f, per direction pair: (c0 hi, c0 lo),
   // (c1, c2), (c3, 0) with c0 the tap row j itself (see ecub_f4)
   const float4* ecub;
+  // [K][n + 5][erec_rec_f4(R)]: per interval j = -3..n+1 (index j + 3) the
+  // ecub coefficients then the epoly sextic (zero for j = -3 and n + 1), so
+  // that one draw's reads for a detector lie in one contiguous record
+  const float4* erec;
   // The shared-memory image of the FP32-mixed kernels' per-point tables (the
   // split whitening, gm1 and the staged detector and mode tables, built once
   // at point creation): the warp-per-draw kernel copies it flat.
@@ -134,6 +142,7 @@ struct rift_ile_point {
   float2* ehat;                  // owned
   float2* epoly;                 // owned
   float4* ecub;                  // owned
+  float4* erec;                  // owned
   float4* img;                   // owned
   int device;
 };
