@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
       {  // the interval's cubic coefficients (contiguous) into L1 for the residual phase
         const char* cb = reinterpret_cast<const char*>(
-            P.ecub + ((size_t)k * (n + 5) + (size_t)(jck + 3)) * (RR / 2) * 3);
+            P.erec + ((size_t)k * (n + 5) + (size_t)(jck + 3)) * (3 * (RR / 2) + 4));
         constexpr int kBytes = (RR / 2) * 48;
         for (int off = 0; off < kBytes; off += 128)
           asm volatile("prefetch.global.L1 [%0];" ::"l"(cb + off));
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         // per-thread kernel): c0.hi meets the exact head of w first
         const float fk = W.fpos[k];
         const float2 f2 = make_float2(fk, fk);
-        const float4* Cj = P.ecub + (((size_t)k * (n + 5) + (size_t)(W.jc[k] + 3)) * (RR / 2) + pr) * 3;
+        const float4* Cj = P.erec + ((size_t)k * (n + 5) + (size_t)(W.jc[k] + 3)) * (3 * (RR / 2) + 4) + 3 * pr;
         const float4 c0 = __ldg(Cj), c12 = __ldg(Cj + 1), c3v = __ldg(Cj + 2);
         const float2 c1 = make_float2(c12.x, c12.y), c2 = make_float2(c12.z, c12.w);
         const float2 c3 = make_float2(c3v.x, c3v.y);

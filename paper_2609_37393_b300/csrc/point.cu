@@ -235,11 +235,12 @@ __global__ void whiten_kernel(const double* __restrict__ proj, const double* __r
 // (the monomial coefficients of the four Lagrange cubics), formed in FP64 from
 // the (hi, lo) rows; c0 is copied as its (hi, lo) pair, c1..c3 rounded to FP32
 // (their rounding is of the order of the FP32 tap weights' in the four-tap
-// sum they replace).  Entry ((k (n + 5) + j + 3) (R/2) + p) 3 + {0, 1, 2} for
-// direction pair p: (c0 hi r, c0 hi r+1, c0 lo r, c0 lo r+1), (c1 r, c1 r+1,
-// c2 r, c2 r+1), (c3 r, c3 r+1, 0, 0).
+// sum they replace).  Interval records of rec_f4 float4 (3 R/2, or more where
+// the record carries more after the cubic), entry (k (n + 5) + j + 3) rec_f4 +
+// 3 p + {0, 1, 2} for direction pair p: (c0 hi r, c0 hi r+1, c0 lo r,
+// c0 lo r+1), (c1 r, c1 r+1, c2 r, c2 r+1), (c3 r, c3 r+1, 0, 0).
 __global__ void cubic_table_kernel(const float2* __restrict__ ehat, int K, int n, int R,
-                                   float4* __restrict__ ecub) {
+                                   int rec_f4, float4* __restrict__ ecub) {
   const int NP = R / 2, per = n + 5;
   const long long total = (long long)K * per * NP;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -264,37 +265,33 @@ __global__ void cubic_table_kernel(const float2* __restrict__ ehat, int K, int n
     }
     const float* r0 = rows + 2 * R;  // row j
     a0 = make_float4(r0[4 * p], r0[4 * p + 1], r0[4 * p + 2], r0[4 * p + 3]);
-    float4* o = ecub + idx * 3;
+    float4* o = ecub + kq * rec_f4 + 3 * p;
     o[0] = a0;
     o[1] = make_float4((float)c[1][0], (float)c[1][1], (float)c[2][0], (float)c[2][1]);
     o[2] = make_float4((float)c[3][0], (float)c[3][1], 0.f, 0.f);
   }
 }
 
-// The per-interval records of PointParams::erec from ecub and epoly.
-__global__ void interval_record_kernel(const float4* __restrict__ ecub,
-                                       const float2* __restrict__ epoly, int K, int n, int R,
+// The sextic tails of the interval records of PointParams::erec (after the
+// cubic): the epoly coefficients of interval j = -2..n as pairs (c0, c1),
+// (c2, c3), (c4, c5), (c6, 0); zero for j = -3 and n + 1.
+__global__ void interval_sextic_kernel(const float2* __restrict__ epoly, int K, int n, int R,
                                        float4* __restrict__ erec) {
   const int NP = R / 2, rec = 3 * NP + 4, per = n + 5;
-  const long long total = (long long)K * per * rec;
+  const long long total = (long long)K * per * 4;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int w = (int)(idx % rec);
-    const long long kq = idx / rec;
-    const int k = (int)(kq / per), q = (int)(kq % per);  // interval j = q - 3
+    const int w = (int)(idx % 4);
+    const long long kq = idx / 4;
+    const int k = (int)(kq / per), j = (int)(kq % per) - 3;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (w < 3 * NP) {
-      v = ecub[kq * 3 * NP + w];
-    } else {
-      const int j = q - 3, c = 2 * (w - 3 * NP);  // sextic coefficients c, c + 1
-      if (j >= -2 && j <= n) {
-        const float2* pc = epoly + ((size_t)k * (n + 3) + (size_t)(j + 2)) * (kPolyDeg + 1);
-        const float2 a = pc[c];
-        const float2 b = c + 1 <= kPolyDeg ? pc[c + 1] : make_float2(0.f, 0.f);
-        v = make_float4(a.x, a.y, b.x, b.y);
-      }
+    if (j >= -2 && j <= n) {
+      const float2* pc = epoly + ((size_t)k * (n + 3) + (size_t)(j + 2)) * (kPolyDeg + 1);
+      const float2 a = pc[2 * w];
+      const float2 b = 2 * w + 1 <= kPolyDeg ? pc[2 * w + 1] : make_float2(0.f, 0.f);
+      v = make_float4(a.x, a.y, b.x, b.y);
     }
-    erec[idx] = v;
+    erec[kq * rec + 3 * NP + w] = v;
   }
 }
 
@@ -457,7 +454,7 @@ int whitened_tables(const void* Q, int q_c128, int K, int n, int Mq, int ncls, c
         dproj, dinv_s, K, n, D, R, epoly);
     const long long tc3 = (long long)K * (n + 5) * (R / 2);
     cubic_table_kernel<<<(int)std::min<long long>((tc3 + 127) / 128, 148LL * 16), 128, 0, st>>>(
-        ehat, K, n, R, ecub);
+        ehat, K, n, R, 3 * (R / 2), ecub);
     if ((rc = check_cuda(cudaGetLastError(), "whitened table kernels"))) break;
     rc = check_cuda(cudaStreamSynchronize(st), "whitened tables");
   } while (0);
@@ -481,7 +478,6 @@ extern "C" int rift_ile_point_destroy(rift_ile_point* pt) {
   cudaFree(pt->gm1);
   cudaFree(pt->ehat);
   cudaFree(pt->epoly);
-  cudaFree(pt->ecub);
   cudaFree(pt->erec);
   cudaFree(pt->img);
   delete pt;
@@ -771,7 +767,6 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
                                          stream), "table padding")))
       break;
     if ((rc = dev_alloc(&pt->epoly, (size_t)K * (n + 3) * (kPolyDeg + 1)))) break;
-    if ((rc = dev_alloc(&pt->ecub, ecub_f4(K, n, R)))) break;
     if ((rc = dev_alloc(&pt->erec, erec_f4(K, n, R)))) break;
     if ((rc = dev_alloc(&dinv_s, inv_s.size()))) break;
     if ((rc = check_cuda(cudaMemcpyAsync(pt->A, A.data(), A.size() * sizeof(float2),
@@ -791,10 +786,10 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
         dproj, dinv_s, K, n, D, R, pt->epoly);
     const long long tc3 = (long long)K * (n + 5) * (R / 2);
     cubic_table_kernel<<<(int)std::min<long long>((tc3 + 127) / 128, 148LL * 16), 128, 0, stream>>>(
-        pt->ehat, K, n, R, pt->ecub);
-    const long long tr = (long long)erec_f4(K, n, R);
-    interval_record_kernel<<<(int)std::min<long long>((tr + 255) / 256, 148LL * 16), 256, 0, stream>>>(
-        pt->ecub, pt->epoly, K, n, R, pt->erec);
+        pt->ehat, K, n, R, erec_rec_f4(R), pt->erec);
+    const long long tr = (long long)K * (n + 5) * 4;
+    interval_sextic_kernel<<<(int)std::min<long long>((tr + 255) / 256, 148LL * 16), 256, 0, stream>>>(
+        pt->epoly, K, n, R, pt->erec);
     if ((rc = check_cuda(cudaGetLastError(), "table kernels"))) break;
     P.Q = pt->q_copy;
     P.U = pt->uv;
@@ -803,7 +798,6 @@ extern "C" int rift_ile_point_create(const rift_ile_point_desc* d, rift_ile_poin
     P.gm1 = pt->gm1;
     P.ehat = pt->ehat;
     P.epoly = pt->epoly;
-    P.ecub = pt->ecub;
     P.erec = pt->erec;
     if ((rc = build_mixed_image(P, &pt->img, &P.img_f4, stream))) break;
     P.img = pt->img;

@@ -26,10 +26,11 @@ constexpr int kPolyDeg = 6;  // 1/2 |e(f)|^2 on one table interval is a sextic i
 // Zero rows stored before and after each detector's whitened table, so that
 // any tap window whose first tap lies in [-kEhatPad, n] reads rows in memory.
 constexpr int kEhatPad = 4;
-// Length in float4 of the cubic coefficient table (PointParams::ecub).
+// Length in float4 of a table of the intervals' cubic coefficients alone
+// (3 float4 per direction pair and interval; the composite response's).
 inline size_t ecub_f4(int K, int n, int R) { return (size_t)K * (n + 5) * (R / 2) * 3; }
 // Float4 per interval record of PointParams::erec: the interval's cubic
-// coefficients (as in ecub) followed by its 1/2 |e|^2 sextic (7 pairs + 1).
+// coefficients followed by its 1/2 |e|^2 sextic (7 pairs + 1).
 inline int erec_rec_f4(int R) { return 3 * (R / 2) + 4; }
 inline size_t erec_f4(int K, int n, int R) { return (size_t)K * (n + 5) * erec_rec_f4(R); }
 
@@ -84,13 +85,11 @@ struct PointParams {
   const float* gm1;     // [ncls][R]     1 - lam_r/s_r^2 (0 except kept null directions)
   const float2* ehat;   // [K][n + 2 kEhatPad][R] whitened Q table, zero rows around it
   const float2* epoly;  // [K][n+3][7]   1/2|e(f)|^2 on interval j (index j+2), coefficients of f^0..f^6
-  // [K][n + 5][R/2][3] the four-tap cubic of each table interval j = -3..n+1
-  // (index j + 3) as coefficients of f, per direction pair: (c0 hi, c0 lo),
-  // (c1, c2), (c3, 0) with c0 the tap row j itself (see ecub_f4)
-  const float4* ecub;
   // [K][n + 5][erec_rec_f4(R)]: per interval j = -3..n+1 (index j + 3) the
-  // ecub coefficients then the epoly sextic (zero for j = -3 and n + 1), so
-  // that one draw's reads for a detector lie in one contiguous record
+  // four-tap cubic as coefficients of f, per direction pair (c0 hi, c0 lo),
+  // (c1, c2), (c3, 0) with c0 the tap row j itself, then the epoly sextic
+  // (zero for j = -3 and n + 1), so that one draw's reads for a detector lie
+  // in one contiguous record
   const float4* erec;
   // The shared-memory image of the FP32-mixed kernels' per-point tables (the
   // split whitening, gm1 and the staged detector and mode tables, built once
@@ -141,7 +140,6 @@ struct rift_ile_point {
   float* gm1;                    // owned
   float2* ehat;                  // owned
   float2* epoly;                 // owned
-  float4* ecub;                  // owned
   float4* erec;                  // owned
   float4* img;                   // owned
   int device;
