@@ -344,17 +344,25 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
         if (u.hi == jf && u.lo < 0.f) jf -= 1.f;
         f = __fadd_rn(__fsub_rn(u.hi, jf), u.lo);
       }
-      inpoly = !bad && jf >= -2.f && jf <= (float)n;
-      if (inpoly) {
-        const float2* pc =
-            P.epoly + ((size_t)k * (n + 3) + (size_t)((int)jf + 2)) * (kPolyDeg + 1);
-#pragma unroll
-        for (int p = 0; p <= kPolyDeg; ++p) cf[p] = __ldg(pc + p);
-      }
       jck = (int)fminf(fmaxf(jf, -3.f), (float)(n + 1));
-      {  // the interval's cubic coefficients (contiguous) into L1 for the residual phase
-        const char* cb = reinterpret_cast<const char*>(
-            P.erec + ((size_t)k * (n + 5) + (size_t)(jck + 3)) * (3 * (RR / 2) + 4));
+      // the interval's record: the sextic loaded now (zero outside the
+      // table), the cubic coefficients before it prefetched into L1 for the
+      // residual phase
+      const float4* rec = P.erec + ((size_t)k * (n + 5) + (size_t)(jck + 3)) * (3 * (RR / 2) + 4);
+      inpoly = !bad;
+      if (inpoly) {
+        const float4* pe = rec + 3 * (RR / 2);
+        const float4 e01 = __ldg(pe), e23 = __ldg(pe + 1), e45 = __ldg(pe + 2), e6 = __ldg(pe + 3);
+        cf[0] = make_float2(e01.x, e01.y);
+        cf[1] = make_float2(e01.z, e01.w);
+        cf[2] = make_float2(e23.x, e23.y);
+        cf[3] = make_float2(e23.z, e23.w);
+        cf[4] = make_float2(e45.x, e45.y);
+        cf[5] = make_float2(e45.z, e45.w);
+        cf[6] = make_float2(e6.x, e6.y);
+      }
+      {
+        const char* cb = reinterpret_cast<const char*>(rec);
         constexpr int kBytes = (RR / 2) * 48;
         for (int off = 0; off < kBytes; off += 128)
           asm volatile("prefetch.global.L1 [%0];" ::"l"(cb + off));
