@@ -71,12 +71,22 @@ struct A12Smem {
   static constexpr bool on = RIFT_MIXED_A_SMEM && RR <= 12;
 };
 
+// Float4 count of the split whitening of every class (two per direction pair
+// and mode), and bytes of it plus gm1 at the start of the shared memory of the
+// FP32-mixed kernels.
+__host__ __device__ inline size_t split_a_f4(int ncls, int R, int M) {
+  return (size_t)ncls * R * M;
+}
+__host__ __device__ inline size_t split_a_bytes(int ncls, int R, int M) {
+  return split_a_f4(ncls, R, M) * 16 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+}
+
 // Bytes of dynamic shared memory of a FP32-mixed kernel: the split whitening
 // of every class, gm1, (A12Smem) the per-thread a1, a2 slices, and the
 // per-thread x F_k of the K detectors.
 template <int RR>
 __host__ __device__ inline size_t mixed_smem_bytes(int ncls, int R, int M, int K) {
-  size_t b = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  size_t b = split_a_bytes(ncls, R, M);
   if (A12Smem<RR>::on) b += (size_t)RR * kMixedThreads * 16;
   return b + (size_t)K * kMixedThreads * 16;
 }
@@ -84,14 +94,14 @@ __host__ __device__ inline size_t mixed_smem_bytes(int ncls, int R, int M, int K
 template <int RR>
 __device__ __forceinline__ float4* a12_slice(float4* smem4, int ncls, int R, int M) {
   if (!A12Smem<RR>::on) return nullptr;
-  const size_t off = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  const size_t off = split_a_bytes(ncls, R, M);
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + off) + threadIdx.x;
 }
 
 // This thread's slots of x F_k (as head/tail pairs), slot k at [k * kMixedThreads].
 template <int RR>
 __device__ __forceinline__ float4* xf_slice(float4* smem4, int ncls, int R, int M) {
-  size_t off = (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
+  size_t off = split_a_bytes(ncls, R, M);
   if (A12Smem<RR>::on) off += (size_t)RR * kMixedThreads * 16;
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(smem4) + off) + threadIdx.x;
 }
@@ -605,12 +615,13 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     // a1 = A y, a2 = A J y by the split product: the products of the 10-bit
     // head of A with the 9-bit head of y are exact and their sum stays below
     // 2^24 quanta, so ex1/ex2 are exact; every other term is ~2^-9 smaller.
-    // (ex1, ex2) and (co1, co2) of each direction advance together as packed
-    // pairs (one FFMA2 issues both FMAs)
-    float2 ex[RR], co[RR];
+    // Directions advance by pairs (r, r + 1) as the two lanes of the packed
+    // FMAs (one FFMA2 issues both): ex1[r/2] = (ex1 of r, of r + 1), and
+    // likewise ex2, co1, co2
+    float2 ex1[RR / 2], ex2[RR / 2], co1[RR / 2], co2[RR / 2];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) ex[r] = co[r] = make_float2(0.f, 0.f);
-    const float4* Ac = sA + (size_t)c * R * M * 2;
+    for (int p = 0; p < RR / 2; ++p) ex1[p] = ex2[p] = co1[p] = co2[p] = make_float2(0.f, 0.f);
+    const float4* Ac = sA + (size_t)c * R * M;
     // modes in order of increasing |m| (P.morder): e^{i |m| phi} is reused
     // across modes of equal |m| and stepped by one complex product with
     // e^{i phi} when |m| grows by one; otherwise an anchored sine/cosine
@@ -650,19 +661,29 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const float2 pr1 = make_float2(yr1, yr1), pi1 = make_float2(yi1, yi1);
       const float2 pr2 = make_float2(yr2, yr2), pi2 = make_float2(yi2, yi2);
       const float2 prh = make_float2(yr.hi, yr.hi), pih = make_float2(yi.hi, yi.hi);
+      const float2 ni1 = make_float2(-yi1, -yi1), ni2 = make_float2(-yi2, -yi2);
+      const float2 nih = make_float2(-yi.hi, -yi.hi);
 #pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        if (EXACT || r < R) {
-          // with t = A[r][a], b = A[r][M + a] as (head, tail):
-          // ap = (t_h, b_h, t_t, b_t), an = (b_h, -t_h, b_t, -t_t);
+      for (int p = 0; p < RR / 2; ++p) {
+        if (EXACT || 2 * p < R) {
+          // with t = A[r][a], b = A[r][M + a] as (head, tail), lanes (r, r + 1):
+          // hd = (t_h, t_h, b_h, b_h), tl = (t_t, t_t, b_t, b_t);
           // a1_r += t yr + b yi ;  a2_r += b yr - t yi
-          const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
-          ex[r] = __ffma2_rn(make_float2(ap.x, ap.y), pr1, ex[r]);
-          ex[r] = __ffma2_rn(make_float2(an.x, an.y), pi1, ex[r]);
-          co[r] = __ffma2_rn(make_float2(ap.x, ap.y), pr2, co[r]);
-          co[r] = __ffma2_rn(make_float2(ap.z, ap.w), prh, co[r]);
-          co[r] = __ffma2_rn(make_float2(an.x, an.y), pi2, co[r]);
-          co[r] = __ffma2_rn(make_float2(an.z, an.w), pih, co[r]);
+          const float4 hd = Ac[2 * (p * M + j)], tl = Ac[2 * (p * M + j) + 1];
+          const float2 th = make_float2(hd.x, hd.y), bh = make_float2(hd.z, hd.w);
+          const float2 tt = make_float2(tl.x, tl.y), bt = make_float2(tl.z, tl.w);
+          ex1[p] = __ffma2_rn(th, pr1, ex1[p]);
+          ex1[p] = __ffma2_rn(bh, pi1, ex1[p]);
+          ex2[p] = __ffma2_rn(bh, pr1, ex2[p]);
+          ex2[p] = __ffma2_rn(th, ni1, ex2[p]);
+          co1[p] = __ffma2_rn(th, pr2, co1[p]);
+          co1[p] = __ffma2_rn(tt, prh, co1[p]);
+          co1[p] = __ffma2_rn(bh, pi2, co1[p]);
+          co1[p] = __ffma2_rn(bt, pih, co1[p]);
+          co2[p] = __ffma2_rn(bh, pr2, co2[p]);
+          co2[p] = __ffma2_rn(bt, prh, co2[p]);
+          co2[p] = __ffma2_rn(th, ni2, co2[p]);
+          co2[p] = __ffma2_rn(tt, nih, co2[p]);
         }
       }
     }
@@ -677,21 +698,14 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     float4 a12r[kA12S ? 1 : RR];
 #pragma unroll
     for (int r = 0; r < RR; r += 2) {
-      float uh[2], ut[2], vh[2], vt[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float2 e = ex[r + h];
-        const float C = head_constant(fmaxf(fabsf(e.x), fabsf(e.y)));
-        const float2 C2 = make_float2(C, C);
-        const float2 hd = sub2(__fadd2_rn(e, C2), C2);
-        const float2 tl = __fadd2_rn(sub2(e, hd), co[r + h]);
-        uh[h] = hd.x;
-        vh[h] = hd.y;
-        ut[h] = tl.x;
-        vt[h] = tl.y;
-      }
-      const float4 qa = make_float4(uh[0], uh[1], ut[0], ut[1]);
-      const float4 qb = make_float4(vh[0], vh[1], vt[0], vt[1]);
+      const int p = r / 2;
+      const float2 C2 = make_float2(head_constant(fmaxf(fabsf(ex1[p].x), fabsf(ex2[p].x))),
+                                    head_constant(fmaxf(fabsf(ex1[p].y), fabsf(ex2[p].y))));
+      const float2 h1 = sub2(__fadd2_rn(ex1[p], C2), C2), h2 = sub2(__fadd2_rn(ex2[p], C2), C2);
+      const float2 t1 = __fadd2_rn(sub2(ex1[p], h1), co1[p]);
+      const float2 t2 = __fadd2_rn(sub2(ex2[p], h2), co2[p]);
+      const float4 qa = make_float4(h1.x, h1.y, t1.x, t1.y);
+      const float4 qb = make_float4(h2.x, h2.y, t2.x, t2.y);
       if constexpr (kA12S) {
         a12s[r * kMixedThreads] = qa;
         a12s[(r + 1) * kMixedThreads] = qb;
@@ -917,7 +931,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
     }
     if (GRAD) {
       // iota and phase through the modes: H = A^T G1 + J^T A^T G2 (FP32)
-      const float4* Ac2 = sA + (size_t)c * R * M * 2;
+      const float4* Ac2 = sA + (size_t)c * R * M;
       const float ci = z.hi, si = sz.hi;
       float cmf = 1.f, smf = 0.f;
       int prev = -1;
@@ -928,17 +942,20 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
           if (EXACT || r < R) {
-            const float4 ah = Ac2[2 * (r * M + j)];  // (t_h, b_h, t_t, b_t)
-            const float ath = ah.x + ah.z, abh = ah.y + ah.w;
-            const float g1r = (r & 1) ? G1[r / 2].y : G1[r / 2].x;
-            const float g2r = (r & 1) ? G2[r / 2].y : G2[r / 2].x;
+            // heads (t_h, t_h, b_h, b_h) and tails of the pair (r, r + 1)
+            const float4 hd = Ac2[2 * ((r / 2) * M + j)], tl = Ac2[2 * ((r / 2) * M + j) + 1];
+            const bool odd = r & 1;
+            const float ath = odd ? hd.y + tl.y : hd.x + tl.x;
+            const float abh = odd ? hd.w + tl.w : hd.z + tl.z;
+            const float g1r = odd ? G1[r / 2].y : G1[r / 2].x;
+            const float g2r = odd ? G2[r / 2].y : G2[r / 2].x;
             h1t = fmaf(g1r, ath, h1t);
             h1b = fmaf(g1r, abh, h1b);
             h2t = fmaf(g2r, ath, h2t);
             h2b = fmaf(g2r, abh, h2b);
             if (TWO) {
-              const float g1Br = (r & 1) ? G1B[r / 2].y : G1B[r / 2].x;
-              const float g2Br = (r & 1) ? G2B[r / 2].y : G2B[r / 2].x;
+              const float g1Br = odd ? G1B[r / 2].y : G1B[r / 2].x;
+              const float g2Br = odd ? G2B[r / 2].y : G2B[r / 2].x;
               k1t = fmaf(g1Br, ath, k1t);
               k1b = fmaf(g1Br, abh, k1b);
               k2t = fmaf(g2Br, ath, k2t);
@@ -996,18 +1013,19 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 }
 
 // Stages the whitening matrices of all classes into shared memory in split
-// form: entry (r, j < M) is two float4, (t_h, b_h, t_t, b_t) and
-// (b_h, -t_h, b_t, -t_t), with (t_h, t_t) the (head, tail) of A[r][a] and
-// (b_h, b_t) of A[r][M + a], for mode a = morder[j] (modes in the kernels'
-// order of increasing |m|; the pairs feed the packed FMAs of the mat-vec),
-// head = A_hi rounded to a multiple of 2^-9 of a power of two >= max_a
-// |A[r][a]| (10 significant bits; the error-free product of lnl_mixed_draw
-// relies on it), tail = (A_hi - head) + A_lo rounded to FP32; then gm1.
-// Whole block.
+// form, by direction pairs (r, r + 1) with r even (R is even: the tables are
+// padded to the kernel's width): entry (pair, j < M) is two float4,
+// (t_h[r], t_h[r+1], b_h[r], b_h[r+1]) and (t_t[r], t_t[r+1], b_t[r], b_t[r+1]),
+// with (t_h, t_t) the (head, tail) of A[r][a] and (b_h, b_t) of A[r][M + a],
+// for mode a = morder[j] (modes in the kernels' order of increasing |m|; the
+// direction pairs feed the packed FMAs of the mat-vec), head = A_hi rounded
+// to a multiple of 2^-9 of a power of two >= max_a |A[r][a]| (10 significant
+// bits; the error-free product of lnl_mixed_draw relies on it), tail =
+// (A_hi - head) + A_lo rounded to FP32; then gm1.  Whole block.
 __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem4) {
   const int R = P.R, D = P.D, M = P.M, ncls = P.ncls;
-  float4* sA = smem4;
-  float* sg = reinterpret_cast<float*>(smem4 + (size_t)ncls * R * M * 2);
+  float* sAf = reinterpret_cast<float*>(smem4);
+  float* sg = reinterpret_cast<float*>(smem4 + split_a_f4(ncls, R, M));
   for (int t = threadIdx.x; t < ncls * R; t += blockDim.x) {
     const float2* row = P.A + (size_t)t * D;
     float mx = 0.f;
@@ -1015,14 +1033,19 @@ __device__ __forceinline__ void stage_split_A(const PointParams& P, float4* smem
     int e = 0;
     frexpf(mx, &e);  // mx < 2^e
     const float C = ldexpf(1.5f, e + 14);  // ulp(C) = 2^(e - 9)
+    // row t = c R + r: pair t / 2, lane t % 2 within it
+    float* dst = sAf + (size_t)(t >> 1) * M * 8 + (t & 1);
     for (int j = 0; j < M; ++j) {
       const int a = P.morder[j];
       const float2 v = __ldg(row + a), u = __ldg(row + M + a);
       const float hv = __fsub_rn(__fadd_rn(v.x, C), C);
       const float hu = __fsub_rn(__fadd_rn(u.x, C), C);
       const float tv = __fadd_rn(__fsub_rn(v.x, hv), v.y), tu = __fadd_rn(__fsub_rn(u.x, hu), u.y);
-      sA[2 * ((size_t)t * M + j)] = make_float4(hv, hu, tv, tu);
-      sA[2 * ((size_t)t * M + j) + 1] = make_float4(hu, -hv, tu, -tv);
+      float* e8 = dst + (size_t)j * 8;
+      e8[0] = hv;
+      e8[2] = hu;
+      e8[4] = tv;
+      e8[6] = tu;
     }
     sg[t] = __ldg(P.gm1 + t);
   }
@@ -1043,7 +1066,7 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   stage_tables(P, T);
   __syncthreads();
   const float4* sA = smem4;
-  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
+  const float* sg = reinterpret_cast<const float*>(smem4 + split_a_f4(P.ncls, P.R, P.M));
   float4* a12s = a12_slice<RR>(smem4, P.ncls, P.R, P.M);
   float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
   ThreadLse st = tlse_init();
@@ -1097,12 +1120,8 @@ __global__ void __launch_bounds__(128, GRAD ? RIFT_MIXED_MIN_BLOCKS_GRAD : RIFT_
   }
 }
 
-// Bytes of the split whitening and gm1 at the start of the shared memory of
-// the FP32-mixed kernels, and of the per-point image (those plus the staged
+// Bytes of the per-point image (the split whitening, gm1 and the staged
 // tables) that the warp-per-draw kernel copies flat.
-__host__ __device__ inline size_t split_a_bytes(int ncls, int R, int M) {
-  return (size_t)ncls * R * M * 32 + (((size_t)ncls * R * 4 + 15) & ~(size_t)15);
-}
 __host__ __device__ inline size_t image_bytes(int ncls, int R, int M) {
   return split_a_bytes(ncls, R, M) + ((sizeof(MixedTables) + 15) & ~(size_t)15);
 }
@@ -1361,7 +1380,7 @@ __global__ void __launch_bounds__(128, RIFT_MIXED_MIN_BLOCKS)
       cur = it.point;
     }
     const float4* sA = smem4;
-    const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
+    const float* sg = reinterpret_cast<const float*>(smem4 + split_a_f4(P.ncls, P.R, P.M));
     float4* a12s = a12_slice<RR>(smem4, P.ncls, P.R, P.M);
     float4* xfs = xf_slice<RR>(smem4, P.ncls, P.R, P.M);
     ThreadLse st = tlse_init();

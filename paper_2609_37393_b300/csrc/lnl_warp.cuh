@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const float4* sA = smem4;
-  const float* sg = reinterpret_cast<const float*>(smem4 + (size_t)P.ncls * P.R * P.M * 2);
+  const float* sg = reinterpret_cast<const float*>(smem4 + split_a_f4(P.ncls, P.R, P.M));
   const MixedTables& T = *reinterpret_cast<const MixedTables*>(
       reinterpret_cast<const char*>(smem4) + split_a_bytes(P.ncls, P.R, P.M));
   const size_t aoff = (size_t)P.img_f4 * 16;
@@ -428,14 +428,20 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       // ---- 3b: lane (c, r): row r of class c's mat-vec, packed as in the per-thread kernel
       for (int it = lane; it < ncls * RR; it += 32) {
         const int c = it / RR, r = it - c * RR;
-        const float4* Ac = sA + (size_t)c * RR * M * 2;
+        const float4* Ac = sA + (size_t)c * RR * M + (size_t)(r / 2) * M * 2;
+        const bool odd = r & 1;
         float2 ex = make_float2(0.f, 0.f), co = make_float2(0.f, 0.f);
   #pragma unroll
         for (int j = 0; j < MM; ++j) {
           if (j >= M) break;
           const float4 y = W.ys[j];
           const float2 yh = W.yh[j];
-          const float4 ap = Ac[2 * (r * M + j)], an = Ac[2 * (r * M + j) + 1];
+          // this direction's lane of the pair's heads and tails (t = A[r][a],
+          // b = A[r][M + a]): ap = (t_h, b_h, t_t, b_t), an = (b_h, -t_h, b_t, -t_t)
+          const float4 hp = Ac[2 * j], tp = Ac[2 * j + 1];
+          const float th = odd ? hp.y : hp.x, bh = odd ? hp.w : hp.z;
+          const float tt = odd ? tp.y : tp.x, bt = odd ? tp.w : tp.z;
+          const float4 ap = make_float4(th, bh, tt, bt), an = make_float4(bh, -th, bt, -tt);
           ex = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.x, y.x), ex);
           ex = __ffma2_rn(make_float2(an.x, an.y), make_float2(y.z, y.z), ex);
           co = __ffma2_rn(make_float2(ap.x, ap.y), make_float2(y.y, y.y), co);
@@ -679,12 +685,14 @@ __global__ void __launch_bounds__(32 * kWarpDrawWarps)
       float gph = 0.f, gin = 0.f;
       for (int it = lane; it < ncls * M; it += 32) {
         const int c = it / M, j = it - c * M;
-        const float4* Ac2 = sA + (size_t)c * RR * M * 2;
+        const float4* Ac2 = sA + (size_t)c * RR * M;
         float h1t = 0.f, h1b = 0.f, h2t = 0.f, h2b = 0.f;
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
-          const float4 ah = Ac2[2 * (r * M + j)];  // (t_h, b_h, t_t, b_t)
-          const float ath = ah.x + ah.z, abh = ah.y + ah.w;
+          // heads (t_h, t_h, b_h, b_h) and tails of the pair (r, r + 1)
+          const float4 hp = Ac2[2 * ((r / 2) * M + j)], tp = Ac2[2 * ((r / 2) * M + j) + 1];
+          const float ath = (r & 1) ? hp.y + tp.y : hp.x + tp.x;
+          const float abh = (r & 1) ? hp.w + tp.w : hp.z + tp.z;
           const float2 g = W.G[c][r];
           h1t = fmaf(g.x, ath, h1t);
           h1b = fmaf(g.x, abh, h1b);
