@@ -181,6 +181,21 @@ int upload_dist(Workspace* ws, const rift_ile_dist* dist, cudaStream_t st, DistP
   out->lnwf = ws->dist_lnwf;
   out->n = n;
   out->lnw_max = lnw_max;
+  out->guess = 0;
+  out->lnx0 = 0.f;
+  out->inv_dlnx = 0.f;
+  if (n >= 3 && dist->x[n - 1] > 0.0) {
+    const double l0 = std::log(dist->x[0]);
+    const double d = (l0 - std::log(dist->x[n - 1])) / (n - 1);
+    bool ok = d > 0.0;
+    for (int j = 1; ok && j < n - 1; ++j)
+      ok = std::fabs(std::log(dist->x[j]) - (l0 - j * d)) <= 0.5 * d;
+    if (ok) {
+      out->guess = 1;
+      out->lnx0 = (float)l0;
+      out->inv_dlnx = (float)(1.0 / d);
+    }
+  }
   return RIFT_ILE_OK;
 }
 

@@ -480,13 +480,25 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
   pr.lo = fmaf(q0, R.lo, pr.lo);
   const df rem = df_sub(K, pr);
   const df xs = fast_two_sum(q0, rem.hi / R.hi);
-  // nearest node by bisection on the hi parts (x decreasing)
+  // nearest node by bisection on the hi parts (x decreasing): the bracket
+  // x[lo] > xs >= x[hi] narrows to the unique adjacent pair; on a table
+  // uniform in ln x it starts from the estimated position when the estimate's
+  // bracket holds (two independent loads instead of a chain of ~log2 n)
   int lo = 0, hi = dp.n - 1;
   if (!(xs.hi < dp.xdf[0].x)) {
     hi = 0;
   } else if (!(xs.hi > dp.xdf[dp.n - 1].x)) {
     lo = dp.n - 1;
   } else {
+    if (dp.guess) {  // here x[n - 1] < xs.hi < x[0] and x[n - 1] > 0
+      const float g = fminf(fmaxf((dp.lnx0 - __logf(xs.hi)) * dp.inv_dlnx, 0.f), (float)(dp.n - 2));
+      const int jg = (int)g;
+      const int l2 = max(jg - 1, 0), h2 = min(jg + 2, dp.n - 1);
+      if (__ldg(&dp.xdf[l2].x) > xs.hi && !(__ldg(&dp.xdf[h2].x) > xs.hi)) {
+        lo = l2;
+        hi = h2;
+      }
+    }
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (dp.xdf[mid].x > xs.hi) lo = mid;
@@ -498,12 +510,25 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
   const float halfR = 0.5f * R.hi;
   const float lnw_max = (float)dp.lnw_max;
   for (int dir = -1; dir <= 1; dir += 2) {
-    for (int j = (dir < 0 ? j0 : j0 + 1); j >= 0 && j < dp.n; j += dir) {
-      const float2 xj = __ldg(dp.xdf + j);
+    int j = dir < 0 ? j0 : j0 + 1;
+    if (j < 0 || j >= dp.n) continue;
+    // the next node's loads are issued before this node's test (software
+    // pipelined: the scan's loads do not wait on its exit test)
+    float2 xj = __ldg(dp.xdf + j);
+    float lwj = __ldg(dp.lnwf + j);
+    for (;;) {
+      const int jn = j + dir;
+      const bool more = jn >= 0 && jn < dp.n;
+      float2 xn = xj;
+      float lwn = lwj;
+      if (more) {
+        xn = __ldg(dp.xdf + jn);
+        lwn = __ldg(dp.lnwf + jn);
+      }
       const float d = __fadd_rn(__fsub_rn(xj.x, xs.hi), __fsub_rn(xj.y, xs.lo));
       const float q = halfR * d * d;
       if (lnw_max - q < m - 40.f) break;
-      const float t = __ldg(dp.lnwf + j) - q;
+      const float t = lwj - q;
       const float xq = xj.x * __fsub_rn(1.f, xj.x);  // x (1 - x) without cancellation
       if (t > m) {
         const float r = __expf(m - t);
@@ -519,6 +544,10 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
         s2 = fmaf(e * xj.x, xj.x, s2);
         s3 = fmaf(e, xq, s3);
       }
+      if (!more) break;
+      j = jn;
+      xj = xn;
+      lwj = lwn;
     }
   }
   if (ex) {
@@ -806,7 +835,9 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const float2 zero2 = make_float2(0.f, 0.f);
       float2 q2p = zero2, nulp = zero2, redp = zero2, g1p = zero2, g2p = zero2, g1Bp = zero2,
              g2Bp = zero2;
-      dacc w2 = dacc_zero();
+      // DIST: |w|^2 of the two directions of each pair as the two lanes of a
+      // packed compensated sum (sum, error)
+      float2 w2s = zero2, w2c = zero2;
 #pragma unroll
       for (int r = 0; r < RR; r += 2) {
         if (EXACT || r < R) {
@@ -842,14 +873,14 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
             gm = make_float2(gc[r], gc[r + 1]);
             nulp = __ffma2_rn(__fmul2_rn(gm, nwf), nwf, nulp);
           }
-          if (DIST) {  // |w|^2 with the head square exact
-            const float hi2[2] = {nhi.x, nhi.y}, lo2[2] = {nlo.x, nlo.y};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              dacc_fma_ff(w2, hi2[h], hi2[h]);
-              w2.c = fmaf(2.f * hi2[h], lo2[h], w2.c);
-              w2.c = fmaf(lo2[h], lo2[h], w2.c);
-            }
+          if (DIST) {  // |w|^2 with the head square exact: lane sums by packed TwoSum
+            const df2 p = two_prod2(nhi, nhi);
+            const df2 t = two_sum2(w2s, p.hi);
+            w2s = t.hi;
+            float2 cc = __fadd2_rn(t.lo, p.lo);
+            cc = __ffma2_rn(__fadd2_rn(nhi, nhi), nlo, cc);
+            cc = __ffma2_rn(nlo, nlo, cc);
+            w2c = __fadd2_rn(w2c, cc);
           }
           if (GRAD) {
             redp = __ffma2_rn(rsv, ed, redp);
@@ -881,7 +912,8 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       if (DIST) {
         // K_k = e.w = 1/2|e|^2 + 1/2|w|^2 - 1/2|e - w|^2 (the first and last are in T
         // already); R_k = |w|^2 - sum_r gm1_r w_r^2
-        const df w2d = dacc_result(w2);
+        const df w2t = two_sum(w2s.x, w2s.y);
+        const df w2d = fast_two_sum(w2t.hi, __fadd_rn(w2t.lo, __fadd_rn(w2c.x, w2c.y)));
         dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
         dacc_add(Racc, w2d);
         if (P.has_null[c]) dacc_add(Racc, df{-nul, 0.f});

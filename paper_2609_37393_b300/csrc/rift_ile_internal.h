@@ -116,6 +116,11 @@ struct DistParams {
   const float* lnwf;   // ln w_j in FP32
   int n;
   double lnw_max;
+  // ln x nearly uniform in j (every node within half a step of the line
+  // ln x_0 - j dlnx, x > 0): the FP32-mixed kernels then start the node search
+  // from the estimate j = (lnx0 - ln x) inv_dlnx, checked against the table
+  int guess;
+  float lnx0, inv_dlnx;
 };
 
 struct LseState {

@@ -79,3 +79,30 @@ def test_marginal_gradient_matches_oracle(R, cfg4, nodes):
         sel = slice(None) if prec == 0 else near
         assert err[sel].max() < tol, (prec, err[sel].max(axis=0))
         assert np.max(np.abs(lnl - ref)[near]) <= (1e-6 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("kind", ["thinned", "jittered"])
+def test_marginal_on_irregular_tables(R, cfg4, nodes, kind):
+    """The node search on tables not uniform in ln x: thinned (every other
+    node of the lower half dropped; the kernels bisect the whole table) and
+    jittered (each ln x moved by up to 0.4 of the step; the kernels start
+    from the estimated position and fall back where its bracket fails)."""
+    point, exact, info, draws, logw = cfg4
+    x, lnw = nodes
+    if kind == "thinned":
+        h = len(x) // 2
+        keep = np.r_[np.arange(0, h, 2), np.arange(h, len(x))]
+        x2, lnw2 = x[keep].copy(), lnw[keep].copy()
+    else:
+        step = np.log(x[0] / x[-1]) / (len(x) - 1)
+        u = np.random.default_rng(7).uniform(-0.4, 0.4, len(x))
+        x2, lnw2 = x * np.exp(u * step), lnw.copy()
+        assert np.all(np.diff(x2) < 0)
+    pt = R.Point(point)
+    ref = O.lnL_distmarg(O.OraclePoint(point), draws, x2, lnw2)
+    got32 = R.rift_ile_lnL_dist(pt, draws, (x2, lnw2), R.FP32_MIXED).cpu().numpy()
+    near = ref >= ref.max() - 50
+    assert np.max(np.abs(got32 - ref)[near]) <= 1e-3, np.max(np.abs(got32 - ref)[near])
+    _, td, tq, _ = O.lnL(O.OraclePoint(point), {**draws, "lnD": np.full(len(ref), np.log(100.0))},
+                         terms=True)
+    assert np.all(np.abs(got32 - ref) <= 1e-4 * (np.abs(td) + np.abs(tq)) + 1e-6)
