@@ -621,6 +621,11 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
 
   dacc T = dacc_zero();
   dacc Racc = dacc_zero();  // DIST: R = sum_k (|w_k|^2 - sum_r gm1_r w_kr^2)
+  // DIST: |w_k|^2 of the direction pairs as the two lanes of a packed
+  // compensated sum (sum, error), over all detectors of the draw in the
+  // forward pass and per detector in the adjoint (fewer live registers there)
+  constexpr bool kW2Draw = DIST && !GRAD;
+  float2 w2s = make_float2(0.f, 0.f), w2c = make_float2(0.f, 0.f);
   int oob = 0;
   bool bad = false;
   // gradient accumulators: time-driven parts of (ra, dec, t) as pairs, the rest in FP32
@@ -835,9 +840,7 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       const float2 zero2 = make_float2(0.f, 0.f);
       float2 q2p = zero2, nulp = zero2, redp = zero2, g1p = zero2, g2p = zero2, g1Bp = zero2,
              g2Bp = zero2;
-      // DIST: |w|^2 of the two directions of each pair as the two lanes of a
-      // packed compensated sum (sum, error)
-      float2 w2s = zero2, w2c = zero2;
+      if (!kW2Draw) w2s = w2c = zero2;
 #pragma unroll
       for (int r = 0; r < RR; r += 2) {
         if (EXACT || r < R) {
@@ -912,10 +915,12 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
       if (DIST) {
         // K_k = e.w = 1/2|e|^2 + 1/2|w|^2 - 1/2|e - w|^2 (the first and last are in T
         // already); R_k = |w|^2 - sum_r gm1_r w_r^2
-        const df w2t = two_sum(w2s.x, w2s.y);
-        const df w2d = fast_two_sum(w2t.hi, __fadd_rn(w2t.lo, __fadd_rn(w2c.x, w2c.y)));
-        dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
-        dacc_add(Racc, w2d);
+        if (!kW2Draw) {
+          const df w2t = two_sum(w2s.x, w2s.y);
+          const df w2d = fast_two_sum(w2t.hi, __fadd_rn(w2t.lo, __fadd_rn(w2c.x, w2c.y)));
+          dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
+          dacc_add(Racc, w2d);
+        }
         if (P.has_null[c]) dacc_add(Racc, df{-nul, 0.f});
       }
       if (GRAD) {
@@ -1014,6 +1019,12 @@ __device__ __forceinline__ MixedDraw lnl_mixed_draw(const PointParams& P, const 
         }
       }
     }
+  }
+  if (kW2Draw) {  // 1/2 |w|^2 into K and |w|^2 into R, summed over every detector
+    const df w2t = two_sum(w2s.x, w2s.y);
+    const df w2d = fast_two_sum(w2t.hi, __fadd_rn(w2t.lo, __fadd_rn(w2c.x, w2c.y)));
+    dacc_add(T, df{0.5f * w2d.hi, 0.5f * w2d.lo});
+    dacc_add(Racc, w2d);
   }
   MixedDraw o;
   o.lnl = dacc_result(T);
