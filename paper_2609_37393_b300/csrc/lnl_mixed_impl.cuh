@@ -506,7 +506,16 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
     }
   }
   const int j0 = (dp.xdf[lo].x - xs.hi < xs.hi - dp.xdf[hi].x) ? lo : hi;
-  float m = -CUDART_INF_F, s = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  // the nearest node's offset qn = R (x_j0 - x*)^2 / 2 in double-float; every
+  // node enters relative to it, q_j - qn = R/2 (x_j - x_j0)(x_j + x_j0 - 2 x*)
+  // in FP32 (a difference of at most a few tens of nats over the nodes that
+  // count), so that a table far from x* (qn large) keeps the precision
+  const float2 x0 = __ldg(dp.xdf + j0);
+  df d0 = two_sum(x0.x, -xs.hi);
+  d0.lo = __fadd_rn(d0.lo, __fsub_rn(x0.y, xs.lo));
+  d0 = fast_two_sum(d0.hi, d0.lo);
+  const df qn = df_mul(df{0.5f * R.hi, 0.5f * R.lo}, df_mul(d0, d0));
+  float m = -CUDART_INF_F, s = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // m, t relative to -qn
   const float halfR = 0.5f * R.hi;
   const float lnw_max = (float)dp.lnw_max;
   for (int dir = -1; dir <= 1; dir += 2) {
@@ -525,8 +534,9 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
         xn = __ldg(dp.xdf + jn);
         lwn = __ldg(dp.lnwf + jn);
       }
-      const float d = __fadd_rn(__fsub_rn(xj.x, xs.hi), __fsub_rn(xj.y, xs.lo));
-      const float q = halfR * d * d;
+      const float d = __fadd_rn(__fsub_rn(xj.x, xs.hi), __fsub_rn(xj.y, xs.lo));  // x_j - x*
+      const float dr = __fadd_rn(__fsub_rn(xj.x, x0.x), __fsub_rn(xj.y, x0.y));  // x_j - x_j0
+      const float q = halfR * dr * __fadd_rn(d, d0.hi);                          // q_j - qn
       if (lnw_max - q < m - 40.f) break;
       const float t = lwj - q;
       const float xq = xj.x * __fsub_rn(1.f, xj.x);  // x (1 - x) without cancellation
@@ -556,7 +566,7 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
     ex[2] = s3 / s;
   }
   const df peak = df_mul(K, xs);
-  return df_add_f(df{0.5f * peak.hi, 0.5f * peak.lo}, m + __logf(s));
+  return df_add_f(df_sub(df{0.5f * peak.hi, 0.5f * peak.lo}, qn), m + __logf(s));
 }
 
 // One draw: lnL, and with GRAD its gradient in (ra, dec, psi, incl, phase, lnD, t).

@@ -106,3 +106,26 @@ def test_marginal_on_irregular_tables(R, cfg4, nodes, kind):
     _, td, tq, _ = O.lnL(O.OraclePoint(point), {**draws, "lnD": np.full(len(ref), np.log(100.0))},
                          terms=True)
     assert np.all(np.abs(got32 - ref) <= 1e-4 * (np.abs(td) + np.abs(tq)) + 1e-6)
+
+
+@pytest.mark.parametrize("kind", ["beyond", "below", "one", "two"])
+def test_marginal_on_tables_away_from_the_peak(R, cfg4, kind):
+    """Node tables that do not bracket x* = K/R of the draws (the injected
+    distance is D_ref, x* ~ 1): every node at larger D (x < x*), every node
+    at smaller D (x > x*), and tables of one and two nodes."""
+    point, exact, info, draws, logw = cfg4
+    if kind == "beyond":
+        x, lnw = R.rift_ile_dist_nodes(150.0, 200.0, 100.0, 1e-4, 1000.0)
+    elif kind == "below":
+        x, lnw = R.rift_ile_dist_nodes(40.0, 80.0, 100.0, 1e-4, 1000.0)
+    elif kind == "one":
+        x, lnw = np.array([0.9]), np.array([0.0])
+    else:
+        x, lnw = np.array([1.05, 0.95]), np.array([-0.1, 0.2])
+    pt = R.Point(point)
+    ref = O.lnL_distmarg(O.OraclePoint(point), draws, x, lnw)
+    got64 = R.rift_ile_lnL_dist(pt, draws, (x, lnw), R.FP64).cpu().numpy()
+    assert np.all(np.abs(got64 - ref) <= 1e-9 * np.maximum(1, np.abs(ref))), np.max(np.abs(got64 - ref))
+    got32 = R.rift_ile_lnL_dist(pt, draws, (x, lnw), R.FP32_MIXED).cpu().numpy()
+    near = ref >= ref.max() - 50
+    assert np.max(np.abs(got32 - ref)[near]) <= 1e-3, np.max(np.abs(got32 - ref)[near])
