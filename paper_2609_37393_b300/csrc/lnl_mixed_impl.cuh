@@ -548,7 +548,7 @@ __device__ __forceinline__ df dist_marg_df(const DistParams& dp, df K, df R, flo
         s3 = fmaf(s3, r, xq);
         m = t;
       } else {
-        const float e = __expf(t - m);
+        const float e = t > -CUDART_INF_F ? __expf(t - m) : 0.f;  // a zero-weight node adds 0
         s += e;
         s1 = fmaf(e, xj.x, s1);
         s2 = fmaf(e * xj.x, xj.x, s2);

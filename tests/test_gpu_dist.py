@@ -129,3 +129,23 @@ def test_marginal_on_tables_away_from_the_peak(R, cfg4, kind):
     got32 = R.rift_ile_lnL_dist(pt, draws, (x, lnw), R.FP32_MIXED).cpu().numpy()
     near = ref >= ref.max() - 50
     assert np.max(np.abs(got32 - ref)[near]) <= 1e-3, np.max(np.abs(got32 - ref)[near])
+
+
+def test_marginal_with_zero_weight_nodes(R, cfg4, nodes):
+    """Nodes of zero weight (ln w = -inf) where the peak draws' x* falls,
+    so that the scan starts on one: their terms add nothing, in both
+    precisions, as in the oracle's sum."""
+    point, exact, info, draws, logw = cfg4
+    x, lnw = nodes
+    lnw = lnw.copy()
+    lnw[np.abs(np.log(x)) < 0.01] = -np.inf
+    assert np.isinf(lnw).sum() >= 3
+    pt = R.Point(point)
+    ref = O.lnL_distmarg(O.OraclePoint(point), draws, x, lnw)
+    assert np.all(np.isfinite(ref))
+    got64 = R.rift_ile_lnL_dist(pt, draws, (x, lnw), R.FP64).cpu().numpy()
+    assert np.all(np.abs(got64 - ref) <= 1e-9 * np.maximum(1, np.abs(ref))), np.max(np.abs(got64 - ref))
+    got32 = R.rift_ile_lnL_dist(pt, draws, (x, lnw), R.FP32_MIXED).cpu().numpy()
+    assert np.all(np.isfinite(got32))
+    near = ref >= ref.max() - 50
+    assert np.max(np.abs(got32 - ref)[near]) <= 1e-3, np.max(np.abs(got32 - ref)[near])
